@@ -1,0 +1,435 @@
+"""Pins of the oracle against facts fixed outside it (CPU only).
+
+Each test pins one part of the oracle to something the paper, the
+mathematics or an independent library fixes, chosen so that a plausible slip
+(a dropped term, a wrong sign or index, a swapped operand) fails one of them.
+"""
+
+import ctypes
+import math
+import os
+from collections import Counter
+from fractions import Fraction
+from itertools import combinations
+
+import numpy as np
+import pytest
+
+from conftest import random_graph
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------------ RNG
+def _curand():
+    for name in ("libcurand.so", "libcurand.so.10", "/usr/local/cuda/lib64/libcurand.so"):
+        try:
+            return ctypes.CDLL(name)
+        except OSError:
+            continue
+    return None
+
+
+def test_philox_matches_curand_host_generator(orc):
+    """Philox4x32-10 (Salmon et al. 2011) equals cuRAND's host Philox stream.
+
+    cuRAND's host generator returns, for seed S, the blocks
+    philox(key=(S_lo, S_hi), counter=(0, 0, i, 0)) for i = 0, 1, 2, ...;
+    the oracle's round function must reproduce them word for word.
+    """
+    lib = _curand()
+    if lib is None:
+        pytest.skip("libcurand not available")
+    gen = ctypes.c_void_p()
+    CURAND_RNG_PSEUDO_PHILOX4_32_10 = 161
+    assert lib.curandCreateGeneratorHost(ctypes.byref(gen), CURAND_RNG_PSEUDO_PHILOX4_32_10) == 0
+    try:
+        for seed in (0, 1, 0x123456789ABCDEF, 2**64 - 1, 0xDEADBEEFCAFEF00D):
+            assert lib.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed)) == 0
+            assert lib.curandSetGeneratorOffset(gen, ctypes.c_ulonglong(0)) == 0
+            nblk = 2048
+            out = np.zeros(4 * nblk, dtype=np.uint32)
+            assert lib.curandGenerate(gen, out.ctypes.data_as(ctypes.c_void_p), ctypes.c_size_t(out.size)) == 0
+            k0, k1 = seed & 0xFFFFFFFF, seed >> 32
+            for i in range(nblk):
+                got = orc.philox_raw(k0, k1, [0, 0, i, 0])
+                assert np.array_equal(got, out[4 * i:4 * i + 4]), (seed, i)
+    finally:
+        lib.curandDestroyGenerator(gen)
+
+
+def test_sample_counter_layout(orc):
+    """The sample RNG is philox(key=seed, counter=(idx_lo, idx_hi, j, domain))."""
+    seed, idx = 0x0123456789ABCDEF, (7 << 32) | 5
+    for j, dom in ((0, 0), (1, 0), (5, 1), (3, 2)):
+        a = orc.philox(seed, dom, idx, j)
+        b = orc.philox_raw(seed & 0xFFFFFFFF, seed >> 32, [5, 7, j, dom])
+        assert np.array_equal(a, b)
+
+
+def test_scale128_is_exact_floor(orc):
+    """floor(U * S / 2^128) against Python big integers."""
+    rng = np.random.default_rng(3)
+    for _ in range(3000):
+        w = rng.integers(0, 2**32, size=4, dtype=np.uint64).astype(np.uint32)
+        S = int(rng.integers(1, 2**63, dtype=np.int64)) * int(rng.integers(1, 3))
+        S = min(S, 2**64 - 1)
+        U = int(w[0]) | int(w[1]) << 32 | int(w[2]) << 64 | int(w[3]) << 96
+        assert orc.scale128(w, S) == (U * S) >> 128
+    for S in (1, 2, 3, 2**64 - 1):
+        w = np.array([0xFFFFFFFF] * 4, dtype=np.uint32)
+        assert orc.scale128(w, S) == S - 1
+        assert orc.scale128(np.zeros(4, dtype=np.uint32), S) == 0
+
+
+def test_pair_draw_is_uniform_over_ordered_pairs(orc, gg):
+    """(s,t) uniform over the n(n-1) ordered pairs with s != t (Sec. 2 normalisation)."""
+    from scipy.stats import chisquare
+    g = gg.complete_graph(7)
+    smp = orc.sample_paths(g, seed=11, domain=0, first_idx=0, count=42000)
+    s, t = smp.st[:, 0], smp.st[:, 1]
+    assert np.all(s != t)
+    cnt = Counter(zip(s.tolist(), t.tolist()))
+    assert len(cnt) == 42
+    obs = np.array([cnt[(a, b)] for a in range(7) for b in range(7) if a != b])
+    assert chisquare(obs).pvalue > 1e-4
+
+
+# ------------------------------------------------------------------ omega
+def _rk_rows():
+    rows = []
+    with open(os.path.join(GOLDEN, "rk_iterations.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            p = line.split()
+            rows.append((p[0], float(p[1]), int(p[2]), int(p[3])))
+    return rows
+
+
+def test_omega_reproduces_printed_rk_counts(orc):
+    """RK's count is c/lambda^2 (floor(log2(VD-2)) + 1 + ln(1/delta)) with c = 0.5
+    (Sec. 6); KADABRA's omega has ln(2/delta) in its place (Alg. 1), so
+    ceil(omega(lambda, 2*delta, VD)) must give the printed RK numbers, with
+    one VD per graph across all six lambdas."""
+    rows = _rk_rows()
+    assert len(rows) == 18
+    vd_of = {"advogato": 10, "ca-GrQc": 18, "dip20090126_MAX": 34}  # floor(log2(VD-2)) + 1 = 4, 5, 6
+    for name, lam, rk, kad in rows:
+        got = math.ceil(orc.omega(lam, 2 * 0.1, vd_of[name]))
+        assert got == rk, (name, lam, got, rk)
+        # the printed KADABRA sample count never exceeds its own cap omega
+        assert kad <= math.ceil(orc.omega(lam, 0.1, vd_of[name]))
+    # the VD boundaries of floor(log2(VD-2))
+    assert math.ceil(orc.omega(0.005, 0.2, 17)) == 126052
+    assert math.ceil(orc.omega(0.005, 0.2, 33)) == 146052
+    assert math.ceil(orc.omega(0.005, 0.2, 66)) == 186052
+    assert orc.omega(0.01, 0.1, 2) == orc.omega(0.01, 0.1, 3)  # VD-2 < 1 uses 0
+
+
+def test_vd_heuristic_is_an_upper_bound(orc, gg):
+    """VD = 2 ecc(r) + 1 bounds the node count of every shortest path."""
+    import networkx as nx
+    for g in (gg.path_graph(9), gg.star_graph(8), gg.grid_graph(5, 7), random_graph(gg, 40, 0.08, 1)):
+        vd = orc.vd_heuristic(g)
+        G = nx.Graph()
+        G.add_nodes_from(range(g.n))
+        for v in range(g.n):
+            for w in g.col[g.row_ptr[v]:g.row_ptr[v + 1]]:
+                G.add_edge(v, int(w))
+        longest = max(max(d.values()) for _, d in nx.all_pairs_shortest_path_length(G))
+        assert vd >= longest + 1
+    # path P9: max degree 2 at node 1 (lowest id), ecc(1) = 7
+    assert orc.vd_heuristic(gg.path_graph(9)) == 15
+
+
+# ------------------------------------------------------------------ Brandes
+def test_brandes_closed_forms(orc, gg):
+    n = 9
+    bc = orc.brandes(gg.path_graph(n))
+    for i in range(n):
+        assert bc[i] == pytest.approx(2 * i * (n - 1 - i) / (n * (n - 1)), abs=1e-15)
+    bc = orc.brandes(gg.star_graph(n))
+    assert bc[0] == pytest.approx((n - 2) / n, abs=1e-15)
+    assert np.all(bc[1:] == 0)
+    assert np.all(orc.brandes(gg.complete_graph(6)) == 0)
+    for n in (7, 8):
+        bc = orc.brandes(gg.cycle_graph(n))
+        assert np.allclose(bc, bc[0], atol=1e-15)
+
+
+def _bfs_all_pairs(g):
+    D = np.full((g.n, g.n), -1, dtype=np.int64)
+    for s in range(g.n):
+        D[s, s] = 0
+        q = [s]
+        for v in q:
+            for w in g.col[g.row_ptr[v]:g.row_ptr[v + 1]]:
+                if D[s, w] < 0:
+                    D[s, w] = D[s, v] + 1
+                    q.append(int(w))
+    return D
+
+
+def test_brandes_sum_identity(orc, gg):
+    """sum_v bc(v) = E_{s != t}[(d(s,t) - 1) 1{connected}] (each path has d-1 interior nodes)."""
+    for g in (random_graph(gg, 30, 0.1, 2), random_graph(gg, 25, 0.12, 3, directed=True), gg.cycle_graph(9)):
+        D = _bfs_all_pairs(g)
+        mask = (D > 0)
+        expect = (D[mask] - 1).sum() / (g.n * (g.n - 1))
+        assert orc.brandes(g).sum() == pytest.approx(expect, rel=1e-12)
+
+
+def test_brandes_matches_networkx(orc, gg):
+    """networkx's normalised betweenness divides by (n-1)(n-2) (x2 for undirected
+    pairs); the paper's by n(n-1) over ordered pairs: ours = nx * (n-2)/n."""
+    import networkx as nx
+    for directed in (False, True):
+        g = random_graph(gg, 28, 0.12, 5, directed=directed)
+        G = nx.DiGraph() if directed else nx.Graph()
+        G.add_nodes_from(range(g.n))
+        for v in range(g.n):
+            for w in g.col[g.row_ptr[v]:g.row_ptr[v + 1]]:
+                G.add_edge(v, int(w))
+        ref = nx.betweenness_centrality(G, normalized=True)
+        bc = orc.brandes(g)
+        for v in range(g.n):
+            assert bc[v] == pytest.approx(ref[v] * (g.n - 2) / g.n, abs=1e-12)
+
+
+# ------------------------------------------------------------------ sampler
+def _path_index(paths_all):
+    return {tuple(int(x) for x in p if x >= 0): i for i, p in enumerate(paths_all)}
+
+
+def _chisq_fixed_pair(orc, g, s, t, seed, per_path=1000):
+    from scipy.stats import chisquare
+    allp = orc.enumerate_paths(g, s, t)
+    k = len(allp)
+    idx = _path_index(allp)
+    rc, pl, paths, stats = orc.sample_fixed_pair(g, s, t, seed, per_path * k)
+    assert rc == orc.OK
+    obs = np.zeros(k, dtype=np.int64)
+    for i in range(paths.shape[0]):
+        key = tuple(int(x) for x in paths[i, :pl[i]])
+        assert key in idx, key  # every sample is a shortest s-t path
+        obs[idx[key]] += 1
+    sig = (stats[:, 9].astype(np.uint64) << np.uint64(32)) | stats[:, 8].astype(np.uint64)
+    assert np.all(sig == k)  # sigma_st of the bb-BFS equals the brute-force count
+    return k, chisquare(obs).pvalue
+
+
+def test_sampler_uniform_hypercube_antipodes(orc, gg):
+    """Q4, antipodal corners: 4! = 24 shortest paths, each with probability 1/24."""
+    for seed in (1, 2):
+        k, p = _chisq_fixed_pair(orc, gg.hypercube_graph(4), 0, 15, seed)
+        assert k == 24 and p > 1e-3
+
+
+def test_sampler_uniform_grid_corners(orc, gg):
+    """4x4 grid, opposite corners: C(6,3) = 20 shortest paths."""
+    for seed in (3, 4):
+        k, p = _chisq_fixed_pair(orc, gg.grid_graph(4, 4), 0, 15, seed)
+        assert k == 20 and p > 1e-3
+
+
+def test_sampler_uniform_random_graphs(orc, gg):
+    """Random graphs: pairs with several shortest paths, both directions of search."""
+    tested = 0
+    for gs, directed in ((7, False), (8, True), (9, False)):
+        g = random_graph(gg, 24, 0.15, gs, directed=directed)
+        D = _bfs_all_pairs(g)
+        for s in range(g.n):
+            for t in range(g.n):
+                if s == t or D[s, t] < 2:
+                    continue
+                allp = orc.enumerate_paths(g, s, t)
+                if 4 <= len(allp) <= 30:
+                    k, p = _chisq_fixed_pair(orc, g, s, t, seed=100 + tested, per_path=600)
+                    assert p > 1e-3, (gs, s, t, k, p)
+                    tested += 1
+                    break
+            if tested and tested % 2 == 0:
+                break
+    assert tested >= 3
+
+
+def test_node_frequencies_match_brandes(orc, gg):
+    """E[count(v)/tau] = bc(v) (Sec. 2); z-test at tau = 10^6 on small graphs."""
+    tau = 1_000_000
+    for g in (random_graph(gg, 30, 0.1, 21), random_graph(gg, 22, 0.15, 22, directed=True), gg.grid_graph(4, 6)):
+        bc = orc.brandes(g)
+        rc, counts, totals = orc.accumulate(g, seed=77, domain=0, first_idx=0, count=tau)
+        assert rc == orc.OK
+        p = np.clip(bc, 1e-12, 1 - 1e-12)
+        z = (counts - tau * bc) / np.sqrt(tau * p * (1 - p))
+        z[bc == 0] = 0
+        assert np.all(counts[bc == 0] == 0)
+        assert np.abs(z).max() < 5.0, np.abs(z).max()
+
+
+def test_sample_invariants(orc, gg, er2000):
+    smp = orc.sample_paths(er2000, seed=5, domain=0, first_idx=0, count=3000)
+    assert np.all(smp.status == 0)
+    rp, ci = er2000.row_ptr, er2000.col
+    for i in range(300):
+        L = smp.path_len[i]
+        p = smp.paths[i, :L]
+        assert p[0] == smp.st[i, 0] and p[-1] == smp.st[i, 1]
+        for a, b in zip(p[:-1], p[1:]):
+            assert b in ci[rp[a]:rp[a + 1]]
+        assert smp.stat("dist")[i] == L - 1
+    # sum of interior hits equals the sum over samples of (path nodes - 2)
+    rc, counts, totals = orc.accumulate(er2000, seed=5, domain=0, first_idx=0, count=3000)
+    conn = smp.path_len > 0
+    assert counts.sum() == (smp.path_len[conn] - 2).sum()
+    assert totals[0] == smp.stat("edges").sum()
+
+
+def test_sampled_distance_is_shortest(orc, gg):
+    g = random_graph(gg, 60, 0.05, 31)
+    D = _bfs_all_pairs(g)
+    smp = orc.sample_paths(g, seed=9, domain=0, first_idx=0, count=2000)
+    for i in range(2000):
+        s, t = smp.st[i]
+        if D[s, t] < 0:
+            assert smp.path_len[i] == 0 and smp.stat("dist")[i] == -1
+        else:
+            assert smp.path_len[i] == D[s, t] + 1
+
+
+def test_complete_and_star_counts(orc, gg):
+    """K_n: every pair adjacent, no interior nodes.  Star: the centre is hit
+    exactly by the leaf-leaf samples."""
+    rc, counts, _ = orc.accumulate(gg.complete_graph(6), 1, 0, 0, 5000)
+    assert rc == 0 and counts.sum() == 0
+    g = gg.star_graph(10)
+    smp = orc.sample_paths(g, seed=2, domain=0, first_idx=0, count=5000)
+    rc, counts, _ = orc.accumulate(g, 2, 0, 0, 5000)
+    leaf_leaf = np.sum((smp.st[:, 0] != 0) & (smp.st[:, 1] != 0))
+    assert counts[0] == leaf_leaf and counts[1:].sum() == 0
+
+
+def test_sigma_overflow_boundary(orc, gg):
+    """k x k grid, corner to corner: sigma_st = C(2k-2, k-1).  k=34 gives
+    C(66,33) < 2^64 (exact); k=35 gives C(68,34) > 2^64 - 1 (must fail)."""
+    g = gg.grid_graph(34, 34)
+    rc, pl, paths, stats = orc.sample_fixed_pair(g, 0, 34 * 34 - 1, 1, 3, max_len=80)
+    assert rc == orc.OK
+    sig = (int(stats[0, 9]) << 32) | int(stats[0, 8])
+    assert sig == math.comb(66, 33) and sig < 2**64
+    g = gg.grid_graph(35, 35)
+    rc, pl, paths, stats = orc.sample_fixed_pair(g, 0, 35 * 35 - 1, 1, 1, max_len=80)
+    assert rc == orc.ERR_SIGMA_OVERFLOW and math.comb(68, 34) > 2**64 - 1
+
+
+# ------------------------------------------------------------------ f, g
+def test_f_g_satisfy_the_martingale_tail_bound(orc):
+    """Thm. 2 derives f from McDiarmid's bound exp(-l^2 / (2(omega*beta + l/3))) = delta_L
+    with l = tau*f and beta = b - f (and g with l = tau*g, beta = b + g).  The
+    oracle's f and g must solve those equations, and f = 0 iff b = 0."""
+    rng = np.random.default_rng(8)
+    for _ in range(2000):
+        tau = int(rng.integers(1, 10**6))
+        omega = float(tau) * float(rng.uniform(1.0, 50.0))
+        cnt = int(rng.integers(0, tau + 1))
+        L = float(rng.uniform(0.5, 40.0))
+        U = float(rng.uniform(0.5, 40.0))
+        f, g = orc.f_and_g(cnt, tau, omega, L, U)
+        b = cnt / tau
+        lf, lg = tau * f, tau * g
+        assert f >= 0 and g > 0
+        if cnt == 0:
+            assert f == 0.0
+        else:
+            lhs = lf * lf / (2 * (omega * (b - f) + lf / 3))
+            assert lhs == pytest.approx(L, rel=1e-7)
+        lhs = lg * lg / (2 * (omega * (b + g) + lg / 3))
+        assert lhs == pytest.approx(U, rel=1e-7)
+
+
+def test_f_g_exact_rationals(orc):
+    """Cases where f and g are rational: check against exact arithmetic."""
+    # b = 0: f = 0, g = 2 L (1/3 + omega/tau) / tau
+    for tau, omega, L in ((1000, 4000.0, 3.0), (37, 370.0, 7.5)):
+        f, g = orc.f_and_g(0, tau, omega, L, L)
+        assert f == 0.0
+        exact = 2 * Fraction(L) * (Fraction(1, 3) + Fraction(omega) / tau) / tau
+        assert g == pytest.approx(float(exact), rel=1e-15)
+
+
+def test_check_stop_rule(orc):
+    n = 50
+    rng = np.random.default_rng(4)
+    counts = rng.integers(0, 30, size=n).astype(np.uint32)
+    L = np.full(n, 12.0)
+    stop, mf, mg = orc.check_stop(counts, 10**7, 2e7, L, L, 0.01)
+    assert stop and mf <= 0.01 and mg <= 0.01
+    stop, mf, mg = orc.check_stop(counts, 1000, 2e7, L, L, 0.01)
+    assert not stop and mg > 0.01
+    # maxima are the maxima of the per-node values
+    fs = [orc.f_and_g(int(c), 1000, 2e7, 12.0, 12.0) for c in counts]
+    assert mf == max(f for f, _ in fs) and mg == max(g for _, g in fs)
+
+
+# ------------------------------------------------------------------ computeDelta
+def test_compute_delta_single_level_closed_form(orc):
+    """N nodes with the same warm-up count c0 (rest 0): the bisection must hit
+    2N exp(-C/c) = delta/2 - eps*delta, i.e. C = c ln(2N/target) (App. D)."""
+    n, N, c0, alpha = 500, 37, 5, 300
+    lam, delta, eps = 0.01, 0.1, 0.001
+    omega = orc.omega(lam, delta, 15)
+    count0 = np.zeros(n, dtype=np.uint32)
+    count0[::13][:N] = c0
+    assert (count0 > 0).sum() == N
+    C, dl, du = orc.compute_delta(count0, alpha, omega, lam, delta, eps)
+    c = 2 * (c0 / alpha) * omega / lam**2
+    target = delta / 2 - eps * delta
+    assert C == pytest.approx(c * math.log(2 * N / target), rel=1e-13)
+    d = np.exp(-dl) + np.exp(-du)
+    assert d.sum() <= delta / 2 * (1 + 1e-12)
+    assert d.sum() == pytest.approx(delta / 2, rel=1e-9)
+    assert np.all(dl == du)
+    # zero-count nodes get exactly eps*delta/(2n)
+    assert np.allclose(np.exp(-dl[count0 == 0]), eps * delta / (2 * n), rtol=1e-14)
+
+
+def test_compute_delta_general(orc):
+    rng = np.random.default_rng(5)
+    n, alpha, lam, delta, eps = 3000, 400, 0.01, 0.1, 0.001
+    omega = orc.omega(lam, delta, 21)
+    count0 = rng.poisson(0.3, size=n).astype(np.uint32) * rng.integers(1, 9, size=n).astype(np.uint32)
+    C, dl, du = orc.compute_delta(count0, alpha, omega, lam, delta, eps)
+    d = np.exp(-dl) + np.exp(-du)
+    assert d.sum() <= delta / 2 * (1 + 1e-12)
+    assert d.sum() == pytest.approx(delta / 2, rel=1e-9)
+    # larger warm-up counts get larger delta (smaller ln 1/delta)
+    order = np.argsort(count0, kind="stable")
+    assert np.all(np.diff(dl[order]) <= 1e-12)
+    # all-zero warm-up: C = 0 and every delta is eps*delta/(2n)
+    C0, dl0, du0 = orc.compute_delta(np.zeros(n, dtype=np.uint32), alpha, omega, lam, delta, eps)
+    assert C0 == 0.0 and np.allclose(np.exp(-dl0), eps * delta / (2 * n), rtol=1e-14)
+
+
+# ------------------------------------------------------------------ guarantee
+@pytest.mark.slow
+def test_lambda_delta_guarantee_over_seeds(orc, gg):
+    """Thm. 1: P(exists v: |b~(v) - bc(v)| > lambda) <= delta.  200 seeds on
+    five small graphs at lambda in {0.05, 0.02}; one-sided binomial test."""
+    from scipy.stats import binomtest
+    graphs = [random_graph(gg, 30, 0.1, 41), random_graph(gg, 26, 0.13, 42, directed=True),
+              gg.grid_graph(5, 6), gg.star_graph(25), gg.barabasi_albert(40, 2, 43)]
+    delta = 0.1
+    for lam in (0.05, 0.02):
+        fails = trials = 0
+        for g in graphs:
+            bc = orc.brandes(g)
+            seeds = 200 if lam == 0.05 else 60
+            for seed in range(seeds):
+                r = orc.run(g, lam, delta, seed=1000 + seed, K=100)
+                assert r.status == 0
+                err = np.abs(r.counts / r.tau - bc).max()
+                fails += int(err > lam)
+                trials += 1
+        assert binomtest(fails, trials, delta, alternative="greater").pvalue > 1e-3
+        assert fails / trials <= delta
