@@ -1,0 +1,340 @@
+"""Benchmark of the KADABRA adaptive sampling loop on one GB300.
+
+One step = one full run of the hot path (warm-up sampling, computeDelta, then
+sample batches of K with the FP64 stop test after each, until the stop rule
+holds or ceil(omega) samples) on the plain single-graph workload:
+
+    Chung-Lu power-law graph, n = 10^6, beta = 2.5, mean degree 16,
+    max expected degree 10^4, largest component (seeded, synthetic), int32
+    CSR; lambda = 0.005, delta = 0.1, stop test every 2^16 samples.
+
+Prints ONE JSON line (rank 0).  `value` is sampled paths per second over the
+whole run (warm-up + main loop) with the graph resident on the device;
+`e2e` repeats the measurement through the C ABI with host buffers (CSR
+upload, run, host copy of the counts) inside the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "paths/sec & time-to-(lambda,delta) per graph, batched vs plain on GPU; % HBM roofline"
+WORKLOAD = dict(family="chung_lu", n=1_000_000, beta=2.5, mean_deg=16.0, max_deg=10_000.0, graph_seed=1,
+                lcc=True, lam=0.005, delta=0.1, check_interval=1 << 16)
+L2_FLUSH_BYTES = 512 << 20
+
+
+def make_graph():
+    from paper_1604_08553_gb300 import graphgen
+    w = WORKLOAD
+    return graphgen.chung_lu(w["n"], w["beta"], w["mean_deg"], w["max_deg"], w["graph_seed"], lcc=w["lcc"])
+
+
+def workload_config(g, extra=None):
+    w = WORKLOAD
+    cfg = {
+        "workload": (f"chung_lu n={w['n']} beta={w['beta']} mean_deg={w['mean_deg']:g} max_deg={w['max_deg']:g} "
+                     f"lcc; lambda={w['lam']} delta={w['delta']} K={w['check_interval']}"),
+        "nodes": int(g.n), "arcs": int(g.m), "lambda": w["lam"], "delta": w["delta"],
+        "check_interval": w["check_interval"], "graph_seed": w["graph_seed"],
+        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write)",
+    }
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=5)
+        sm, smax, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                smax = float(p[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_bytes(totals, hits):
+    """Bytes the sampler must touch (per batch): 8 B per expanded node (two
+    offsets), 4 B per scanned arc (adjacency) + 4 B per scanned arc (visited
+    probe), 12 B per node kept in a level (state + sigma), 8 B per sigma
+    addition, 4 B per hit-counter update, 4 B per adjacency entry read while
+    backtracking."""
+    t = totals
+    return (8 * t[1] + 8 * t[0] + 12 * t[2] + 8 * t[3] + 4 * hits + 4 * t[6])
+
+
+def cpu_baseline(g, seconds_cap=20.0):
+    """The oracle (single-threaded, as it stands) on a bounded sample of the
+    same workload: the first main-loop samples of seed 1."""
+    import oracle
+    w = WORKLOAD
+    count = 0
+    t0 = time.perf_counter()
+    chunk = 1000
+    first = 0
+    while time.perf_counter() - t0 < seconds_cap * 0.5 and count < 50_000:
+        rc, _, _ = oracle.accumulate(g, 1, 0, first, chunk)
+        if rc != 0:
+            raise RuntimeError(f"oracle status {rc}")
+        first += chunk
+        count += chunk
+    dt = time.perf_counter() - t0
+    return {"value": count / dt, "unit": "paths/s", "cores": 1, "kind": "oracle",
+            "sample": f"main-loop samples 0..{count - 1} (seed 1) of the Chung-Lu n=1e6 workload, "
+                      f"single-threaded oracle, {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    """The oracle on the host cores (the reference arm for this paper-only tier)."""
+    g = make_graph()
+    import oracle
+    per_step = 3000
+    for i in range(args.warmup):
+        oracle.accumulate(g, 100 + i, 0, 0, 300)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        rc, _, _ = oracle.accumulate(g, 1, 0, i * per_step, per_step)
+        assert rc == 0
+    dt = time.perf_counter() - t0
+    value = args.steps * per_step / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64+f64",
+        "data": "synthetic",
+        "config": workload_config(g, {"sample": f"{per_step} main-loop samples per step"}),
+        "cpu_baseline": {"value": value, "unit": "paths/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{per_step} main-loop samples per step, single-threaded oracle"},
+        "e2e": {"value": value, "unit": "paths/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, rank, world)
+        return
+
+    import torch
+    from paper_1604_08553_gb300 import kadabra as kd
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    g = make_graph()
+    w = WORKLOAD
+    G = kd.kadabra_load_csr(g)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    d_counts = torch.zeros(g.n, dtype=torch.int32, device="cuda")
+    d_btilde = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step(seed):
+        return kd.kadabra_run(G, w["lam"], w["delta"], 0, seed, check_interval=w["check_interval"], stream=sp,
+                              d_counts=d_counts, d_btilde=d_btilde, want_host=False)
+
+    for i in range(args.warmup):
+        step(1000 + i)
+
+    # ---- timed region: device-resident graph, one full adaptive run per step
+    clocks = ClockSampler(local_rank)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    times, paths, launches, results = [], 0, 0, []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        r = step(1 + i + 7919 * rank)
+        ev1.record(stream)
+        ev1.synchronize()
+        times.append(ev0.elapsed_time(ev1) / 1e3)
+        paths += r.alpha + r.tau
+        launches += 2 + 2 * (r.checks + 1) + r.checks + 1 + 1
+        results.append(r)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    total = sum(times)
+    if dist is not None:
+        t = torch.tensor([total, float(paths)], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        total, paths = float(tmax[0]), float(t[1])
+    value = paths / total
+
+    # ---- dominant kernel: the sampler, timed per launch on its stream
+    K = w["check_interval"]
+    d_tot = torch.zeros(kd.NSTAT, dtype=torch.int64, device="cuda")
+    samp_times, samp_bytes = [], []
+    for i in range(4):
+        flush.fill_(float(i))
+        d_counts.zero_()
+        d_tot.zero_()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        kd.kadabra_sample_batch(G, 1, 0, i * K, K, d_counts, d_tot, stream=sp)
+        ev1.record(stream)
+        ev1.synchronize()
+        kd.kadabra_sync_status(G, sp)
+        if i == 0:
+            continue  # first launch of this shape: warm-up
+        samp_times.append(ev0.elapsed_time(ev1) / 1e3)
+        hits = int(d_counts.sum().item())
+        samp_bytes.append(algorithmic_bytes(d_tot.cpu().numpy(), hits))
+    avg_t = sum(samp_times) / len(samp_times)
+    avg_b = sum(samp_bytes) / len(samp_bytes)
+    peak, peak_src = peaks()
+    achieved = avg_b / avg_t / 1e9
+    tot_np = d_tot.cpu().numpy()
+
+    # ---- end to end through the C ABI with host buffers
+    e2e_steps = max(2, min(args.steps, 3))
+    counts_h = np.zeros(g.n, dtype=np.uint32)
+    btilde_h = np.zeros(g.n, dtype=np.float64)
+    h2d = 4 * (g.n + 1) + 4 * g.m
+    d2h = 4 * g.n + 8 * g.n
+    torch.cuda.synchronize()
+    e2e_paths = 0
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        Gh = kd.kadabra_load_csr(g)
+        r = kd.kadabra_run(Gh, w["lam"], w["delta"], 0, 500 + i, check_interval=K, counts=counts_h,
+                           btilde=btilde_h)
+        Gh.free()
+        e2e_paths += r.alpha + r.tau
+    torch.cuda.synchronize()
+    e2e_dt = time.perf_counter() - t0
+    e2e_value = e2e_paths / e2e_dt * world
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(g)
+
+    if rank == 0:
+        r0 = results[0]
+        line = {
+            "metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64+f64", "data": "synthetic",
+            "config": workload_config(g, {
+                "parallelism": "replicas" if world > 1 else "single",
+                "time_to_lambda_delta_ms": [round(1e3 * t, 3) for t in times],
+                "tau": [int(r.tau) for r in results], "alpha": int(r0.alpha), "omega": r0.omega,
+                "checks": [int(r.checks) for r in results],
+                "edges_per_sample": float(tot_np[0]) / K,
+            }),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "k_sample (sampler batch)",
+                         "bytes_per_launch": avg_b, "launch_ms": 1e3 * avg_t, "samples_per_launch": K,
+                         "peak_source": peak_src},
+            "e2e": {"value": e2e_value, "unit": "paths/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+        }
+        if clk:
+            line["clocks"] = clk
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    G.free()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

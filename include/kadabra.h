@@ -1,0 +1,190 @@
+/*
+ * kadabra.h -- C ABI of the GB300 (sm_103a) implementation of KADABRA's
+ * adaptive sampling loop (Borassi & Natale, "KADABRA is an ADaptive
+ * Algorithm for Betweenness via Random Approximation").
+ *
+ * The library estimates the normalised betweenness centrality
+ *     bc(v) = 1/(n(n-1)) * sum_{s != v != t} sigma_st(v) / sigma_st    (Sec. 2)
+ * of every node of an unweighted graph by sampling shortest paths with a
+ * balanced bidirectional BFS (Sec. 4) and stopping adaptively once every
+ * node's confidence interval is within lambda (Alg. 1, Thm. 1 and 2).
+ *
+ * Conventions
+ *   - Every call returns a kadabra_status; nothing throws across the ABI.
+ *   - Graph arrays are int32 CSR: row_ptr has n+1 entries starting at 0,
+ *     col has m = row_ptr[n] entries, every row strictly increasing, no
+ *     self-loops, all ids in [0, n).  n >= 2, m < 2^31, n <= 2^24.
+ *   - Undirected graphs store both arcs of every edge; directed graphs also
+ *     pass the reverse CSR (in-arcs) that the backward search reads.
+ *   - Pointers named d_* are CUDA device pointers; all others are host
+ *     pointers.  The caller owns every buffer it passes; the library owns
+ *     the kadabra_graph object and the device memory it allocates.
+ *   - `stream` arguments are cudaStream_t values passed as void* (NULL =
+ *     the legacy default stream).  Calls are synchronous with respect to the
+ *     host unless stated otherwise.
+ *   - Randomness: Philox4x32-10 (Salmon et al., SC'11), key = seed, counter
+ *     = (sample index lo, hi, draw, domain); domain 0 = main loop,
+ *     1 = warm-up.  Results depend only on (graph, parameters, seed).
+ */
+#ifndef KADABRA_H
+#define KADABRA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  KADABRA_OK = 0,
+  KADABRA_ERR_ARG = 1,            /* invalid argument (NULL, range, lambda/delta)   */
+  KADABRA_ERR_CSR = 2,            /* malformed CSR (offsets, ids, order, loops)     */
+  KADABRA_ERR_OOM = 3,            /* device allocation failed                       */
+  KADABRA_ERR_SIGMA_OVERFLOW = 4, /* a shortest-path count exceeded 2^64-1          */
+  KADABRA_ERR_CAPACITY = 5,       /* an internal bound was exceeded (see message)   */
+  KADABRA_ERR_TIMEOUT = 6,        /* a bounded device wait gave up                  */
+  KADABRA_ERR_CUDA = 7,           /* a CUDA runtime call failed                     */
+  KADABRA_ERR_UNSUPPORTED = 8,    /* requested mode not implemented                 */
+  KADABRA_ERR_INTERNAL = 9        /* an invariant of the method failed (a bug)      */
+} kadabra_status;
+
+/* Per-sample work counters, summed in kadabra_result.totals and returned
+ * per sample by kadabra_sample_paths.  Only levels that did not touch the
+ * other search contribute NEW and SIGMA_ADDS (a touching level ends the
+ * BFS, Sec. 4). */
+enum {
+  KADABRA_STAT_EDGES = 0,      /* arcs scanned while expanding levels          */
+  KADABRA_STAT_EXPANDED = 1,   /* frontier nodes expanded                       */
+  KADABRA_STAT_NEW = 2,        /* nodes added by non-touching levels            */
+  KADABRA_STAT_SIGMA_ADDS = 3, /* repeat discoveries in those levels            */
+  KADABRA_STAT_PI = 4,         /* candidate (touch) edges                       */
+  KADABRA_STAT_LEVELS = 5,     /* levels expanded                               */
+  KADABRA_STAT_BT_SCANNED = 6, /* adjacency positions up to each backtrack pick */
+  KADABRA_STAT_PATH_NODES = 7, /* nodes on the sampled path incl. s and t       */
+  KADABRA_STAT_SIGMA_LO = 8,   /* sigma_st low 32 bits (per sample only)        */
+  KADABRA_STAT_SIGMA_HI = 9,   /* sigma_st high 32 bits (per sample only)       */
+  KADABRA_STAT_DIST = 10,      /* d(s,t) in arcs, -1 if disconnected            */
+  KADABRA_NSTAT = 11
+};
+
+/* Opaque device-resident graph plus its cached sampler workspace. */
+typedef struct kadabra_graph kadabra_graph;
+
+/* Optional knobs (kadabra_config_default fills the defaults). */
+typedef struct {
+  int64_t vd;              /* vertex-diameter bound VD for omega; 0 = the library's
+                              heuristic 2*ecc(r)+1 (r = lowest-id max-degree node,
+                              underlying undirected graph)                        */
+  double eps;              /* computeDelta epsilon (App. D; default 0.001)        */
+  uint64_t check_interval; /* K: samples between stop tests (default 1000)        */
+  void* stream;            /* cudaStream_t for all work of the call (NULL = default) */
+  int32_t ctas_per_sm;     /* resident sampler CTAs per SM (0 = default)          */
+  int32_t reserved[7];
+} kadabra_config;
+
+void kadabra_config_default(kadabra_config* cfg);
+
+/* Result of kadabra_run.  The caller sets the output buffer pointers (any
+ * may be NULL); the library fills the rest. */
+typedef struct {
+  /* outputs */
+  uint64_t tau;        /* main-loop samples taken (Alg. 1 tau)                    */
+  uint64_t omega_cap;  /* ceil(omega), the sample cap                             */
+  uint64_t alpha;      /* warm-up samples, max(1, floor(omega/100)) (Alg. 2)      */
+  uint64_t checks;     /* stop tests evaluated                                    */
+  int64_t vd;          /* VD used                                                 */
+  double omega;        /* 0.5/lambda^2 * (floor(log2(VD-2)) + 1 + ln(2/delta))    */
+  double C;            /* computeDelta bisection constant                         */
+  double max_f;        /* max_v f(v) at the final tau (Thm. 2)                    */
+  double max_g;        /* max_v g(v) at the final tau                             */
+  int64_t totals[KADABRA_NSTAT]; /* work counters, warm-up + main loop              */
+  int32_t stopped_early; /* 1 if the stop test held before ceil(omega) samples    */
+  int32_t status;        /* same as the call's return value                       */
+  /* caller-owned buffers (inputs; NULL = not wanted) */
+  uint32_t* counts;    /* host, n: main-loop hits per node (b~ * tau)             */
+  double* btilde;      /* host, n: b~(v) = counts / tau                           */
+  uint32_t* d_counts;  /* device, n                                               */
+  double* d_btilde;    /* device, n                                               */
+  int32_t* topk;       /* host, k: reserved for top-k mode (k > 0)                */
+} kadabra_result;
+
+/* Copies a host CSR to the device and prepares the graph (Sec. 2 graph
+ * G=(V,E); directed graphs need the reverse CSR, Sec. 4).  Validates the
+ * CSR (KADABRA_ERR_CSR on any violation) and computes the default VD bound.
+ * rrow_ptr/rcol must be NULL when directed == 0. */
+kadabra_status kadabra_load_csr(int32_t n, int64_t m, const int32_t* row_ptr, const int32_t* col, int directed,
+                                const int32_t* rrow_ptr, const int32_t* rcol, kadabra_graph** out);
+
+/* Same, for a CSR already in device memory (e.g. torch tensors).  The
+ * arrays are not copied and must outlive the graph object. */
+kadabra_status kadabra_load_csr_device(int32_t n, int64_t m, const int32_t* d_row_ptr, const int32_t* d_col,
+                                       int directed, const int32_t* d_rrow_ptr, const int32_t* d_rcol,
+                                       kadabra_graph** out);
+
+/* Releases the graph and all device memory the library allocated for it. */
+void kadabra_free_graph(kadabra_graph* g);
+
+kadabra_status kadabra_graph_info(const kadabra_graph* g, int32_t* n, int64_t* m, int* directed, int64_t* vd);
+
+/* KADABRA, all-nodes mode (Alg. 1 with Alg. 2 and the rule f,g <= lambda
+ * for every node): warm-up, computeDelta, then sample batches of K with a
+ * stop test after each, until the test holds or ceil(omega) samples.
+ * lambda in (0,1), delta in (0,1).  k must be 0 (top-k mode, Alg. 3, is
+ * KADABRA_ERR_UNSUPPORTED).  cfg may be NULL.  Blocking. */
+kadabra_status kadabra_run(kadabra_graph* g, double lambda, double delta, int32_t k, uint64_t seed,
+                           const kadabra_config* cfg, kadabra_result* out);
+
+/* One batch of the sampler (Sec. 4 plus Alg. 1 hit update): samples indices
+ * [first_idx, first_idx+count) of `domain`, adding each path's interior
+ * hits into d_counts (device, n) and the work counters into d_totals
+ * (device, KADABRA_NSTAT int64, may be NULL).  Asynchronous on `stream`;
+ * errors found on the device (sigma overflow, capacity) are reported by the
+ * next kadabra_sync_status. */
+kadabra_status kadabra_sample_batch(kadabra_graph* g, uint64_t seed, uint32_t domain, uint64_t first_idx,
+                                    uint64_t count, uint32_t* d_counts, int64_t* d_totals, void* stream);
+
+/* Waits for `stream` and returns (then clears) the device error word of g. */
+kadabra_status kadabra_sync_status(kadabra_graph* g, void* stream);
+
+/* Test hook: samples [first_idx, first_idx+count) of `domain` and returns,
+ * per sample, (s,t) in st_out (host, 2*count), the path s..t in paths (host,
+ * count*max_len, -1 padded; may be NULL), its node count in path_len (host,
+ * count), the work counters in stats (host, count*KADABRA_NSTAT, may be
+ * NULL) and a per-sample status (host, count). */
+kadabra_status kadabra_sample_paths(kadabra_graph* g, uint64_t seed, uint32_t domain, uint64_t first_idx,
+                                    uint32_t count, int32_t* st_out, int32_t* path_len, int32_t* paths,
+                                    int32_t max_len, int64_t* stats, int32_t* status);
+
+/* Test hook: the device Philox4x32-10 block for counters
+ * (idx, idx_hi, j, domain), idx in [first_idx, first_idx+count), written
+ * to out (host, 4*count uint32). */
+kadabra_status kadabra_philox(uint64_t seed, uint32_t domain, uint32_t j, uint64_t first_idx, uint32_t count,
+                              uint32_t* out);
+
+/* Stop test of the all-nodes mode on the device (Thm. 2 f and g in FP64,
+ * rule f <= lambda and g <= lambda for all v).  Host inputs counts (n),
+ * ln_inv_dl/ln_inv_du (n, ln(1/delta_L(v)), ln(1/delta_U(v))); outputs the
+ * maxima of f and g and the decision. */
+kadabra_status kadabra_check(int64_t n, const uint32_t* counts, uint64_t tau, double omega,
+                             const double* ln_inv_dl, const double* ln_inv_du, double lambda, double* max_f,
+                             double* max_g, int* stop);
+
+/* computeDelta (Alg. 2, App. D) with lambda_L = lambda_U = lambda: from the
+ * warm-up hits count0 (host, n) of alpha samples, finds C by bisection and
+ * writes ln(1/delta_L(v)) and ln(1/delta_U(v)) (host, n each). */
+kadabra_status kadabra_compute_delta(int64_t n, const uint32_t* count0, uint64_t alpha, double omega,
+                                     double lambda, double delta, double eps, double* ln_inv_dl,
+                                     double* ln_inv_du, double* C);
+
+/* omega of Alg. 1 for the given VD (c = 0.5, natural log). */
+double kadabra_omega(double lambda, double delta, int64_t vd);
+
+/* Human-readable text of the last error raised in this thread. */
+const char* kadabra_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KADABRA_H */

@@ -1,0 +1,1799 @@
+// KADABRA adaptive sampling loop for GB300 (sm_103a): kernels and C ABI.
+//
+// Paper: Borassi & Natale, "KADABRA is an ADaptive Algorithm for Betweenness
+// via Random Approximation".  The method (Alg. 1) samples shortest paths
+// between uniform node pairs and stops once every node's estimate b~(v) is
+// within lambda with probability 1-delta:
+//   * k_sample   -- one sample per CTA (Sec. 4): (s,t) draw, balanced
+//                   bidirectional BFS with exact uint64 sigma, candidate-edge
+//                   choice proportional to sigma_sv*sigma_wt, backtracking to
+//                   a uniform shortest path, hit counters (Alg. 1 l.5).
+//   * k_check    -- the all-nodes stop test: f and g of Thm. 2 in FP64 for
+//                   every node, rule f <= lambda and g <= lambda.
+//   * host code  -- omega (Alg. 1), computeDelta (Alg. 2, App. D), the
+//                   batch / check schedule, VD bound, CSR validation.
+//
+// Sampler design (GB300-first, not the paper's CPU design):
+//   * A CTA of 128 threads owns one sample at a time; CTAs pull sample
+//     indices from a device counter (persistent grid, sized to the SMs).
+//   * The visited set of both searches is an open-addressing hash table in
+//     shared memory (node -> side | dist | list slot), and sigma lives in
+//     per-level node lists, also in shared memory.  Most of a sample's arcs
+//     (over 90% on power-law graphs) lie in the level that touches the other
+//     search; that level only reads the hash table.  Every level runs as
+//     pass 1 = touch test, and only a level that does not touch runs pass 2
+//     (insert new nodes) and pass 3 (accumulate sigma).
+//   * Frontiers are kept sorted by node id, and each warp scans a contiguous
+//     slice of the level's flattened arc range, so candidate edges come out
+//     in the canonical (x, y) order without a sort.
+//   * A sample whose visited set outgrows shared memory is deferred and
+//     re-run by the same kernel compiled against global-memory tables.
+//   * The RNG is counter-based Philox4x32-10 keyed by (seed, sample index),
+//     so results do not depend on scheduling; hit counts are integer atomics.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/kadabra.h"
+
+namespace {
+
+// ============================================================== constants
+constexpr int NT = 128;            // threads per sampler CTA
+constexpr int NW = NT / 32;        // warps per sampler CTA
+constexpr int MAXD = 126;          // deepest level per side (7-bit field, 127 reserved)
+constexpr int FAST_HLOG = 12;      // shared-memory hash: 4096 slots
+constexpr int FAST_LCAP = 2048;    // shared-memory level lists: 2048 nodes
+constexpr int FAST_PCAP = 2048;    // candidate edges per warp (global memory)
+constexpr unsigned long long EMPTY = ~0ull;
+constexpr uint32_t NONE = 0xFFFFFFFFu;
+constexpr uint32_t SLOT_MASK = 0x00FFFFFFu;
+constexpr uint32_t SLOT_PENDING = 0x00FFFFFFu;
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+// sample flags
+constexpr int F_CAP = 1;       // a capacity bound was hit
+constexpr int F_SIGMA = 2;     // sigma overflowed uint64
+constexpr int F_INTERNAL = 4;  // an invariant failed
+
+// ============================================================== Philox
+// Philox4x32-10, Salmon, Moraes, Dror, Shaw (SC'11): ten rounds of two
+// 32x32 multiplications (counter words 0 and 2) whose high halves are
+// xor-ed into the other words with the round key; Weyl key schedule.
+__device__ __forceinline__ uint4 philox(uint32_t k0, uint32_t k1, uint4 x) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * x.x;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, x.x);
+    const uint32_t lo1 = 0xCD9E8D57u * x.z;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, x.z);
+    x = make_uint4(hi1 ^ x.y ^ k0, lo1, hi0 ^ x.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return x;
+}
+
+__device__ __forceinline__ uint4 draw(uint64_t seed, uint32_t domain, uint64_t idx, uint32_t j) {
+  return philox((uint32_t)seed, (uint32_t)(seed >> 32),
+                make_uint4((uint32_t)idx, (uint32_t)(idx >> 32), j, domain));
+}
+
+// floor(U * S / 2^128) for the 128-bit block U (x least significant)
+__device__ __forceinline__ uint64_t below128(uint4 b, uint64_t S) {
+  const uint64_t lo = (uint64_t)b.x | ((uint64_t)b.y << 32);
+  const uint64_t hi = (uint64_t)b.z | ((uint64_t)b.w << 32);
+  const uint64_t carry_in = __umul64hi(lo, S);
+  const uint64_t hl = hi * S;
+  const uint64_t hh = __umul64hi(hi, S);
+  const uint64_t sum = hl + carry_in;
+  return hh + (sum < hl ? 1ull : 0ull);
+}
+
+// ============================================================== tables
+struct PiEntry {
+  int32_t x, y;          // x on the expanding side, y the scanned neighbour
+  unsigned long long w;  // sigma_x * sigma_y (exact; overflow flagged)
+};
+
+struct Tables {
+  unsigned long long* hkv;  // (node << 32) | (side << 31 | dist << 24 | slot)
+  uint32_t hmask;
+  int hlog;
+  int32_t* lnode;           // level lists: node ids
+  unsigned long long* lsig; // level lists: sigma
+  int32_t* pre;             // frontier degree prefix / scratch (lcap+1)
+  int lcap;
+  PiEntry* pi;              // NW segments of pcap entries
+  int pcap;
+};
+
+__device__ __forceinline__ uint32_t pack_val(int side, int dist, uint32_t slot) {
+  return ((uint32_t)side << 31) | ((uint32_t)dist << 24) | slot;
+}
+__device__ __forceinline__ int val_side(uint32_t v) { return (int)(v >> 31); }
+__device__ __forceinline__ int val_dist(uint32_t v) { return (int)((v >> 24) & 0x7F); }
+__device__ __forceinline__ uint32_t val_slot(uint32_t v) { return v & SLOT_MASK; }
+
+__device__ __forceinline__ uint32_t hash_pos(int32_t v, int hlog) {
+  return ((uint32_t)v * 2654435761u) >> (32 - hlog);
+}
+
+__device__ __forceinline__ uint32_t tab_find(const Tables& T, int32_t v) {
+  uint32_t pos = hash_pos(v, T.hlog);
+  for (uint32_t k = 0; k <= T.hmask; ++k) {
+    const unsigned long long w = T.hkv[pos];
+    if (w == EMPTY) return NONE;
+    if ((int32_t)(w >> 32) == v) return (uint32_t)w;
+    pos = (pos + 1) & T.hmask;
+  }
+  return NONE;
+}
+
+__device__ __forceinline__ int64_t tab_findpos(const Tables& T, int32_t v) {
+  uint32_t pos = hash_pos(v, T.hlog);
+  for (uint32_t k = 0; k <= T.hmask; ++k) {
+    const unsigned long long w = T.hkv[pos];
+    if (w == EMPTY) return -1;
+    if ((int32_t)(w >> 32) == v) return pos;
+    pos = (pos + 1) & T.hmask;
+  }
+  return -1;
+}
+
+// 1 = inserted at *pos_out, 0 = already present, -1 = table full
+__device__ __forceinline__ int tab_insert(const Tables& T, int32_t v, uint32_t val, uint32_t* pos_out) {
+  const unsigned long long want = ((unsigned long long)(uint32_t)v << 32) | val;
+  uint32_t pos = hash_pos(v, T.hlog);
+  for (uint32_t k = 0; k <= T.hmask; ++k) {
+    unsigned long long w = T.hkv[pos];
+    if (w == EMPTY) {
+      const unsigned long long old = atomicCAS(&T.hkv[pos], EMPTY, want);
+      if (old == EMPTY) {
+        *pos_out = pos;
+        return 1;
+      }
+      w = old;
+    }
+    if ((int32_t)(w >> 32) == v) return 0;
+    pos = (pos + 1) & T.hmask;
+  }
+  return -1;
+}
+
+// ============================================================== parameters
+struct GraphDev {
+  int32_t n;
+  int64_t m;
+  const int32_t* rp;   // out-arc offsets
+  const int32_t* ci;   // out-arc targets
+  const int32_t* rrp;  // in-arc offsets
+  const int32_t* rci;  // in-arc sources
+};
+
+struct SampleParams {
+  GraphDev g;
+  uint64_t seed;
+  uint32_t domain;
+  uint64_t first_idx;
+  uint64_t count;
+  uint32_t* counts;                 // hit counters (n) or null
+  unsigned long long* ctr;          // [0] next (fast), [1] next (global), [2] deferred count
+  unsigned long long* deferred;     // deferred sample indices
+  uint64_t deferred_cap;
+  int32_t* status;                  // run-wide error word (kadabra_status values)
+  long long* totals;                // KADABRA_NSTAT or null
+  // per-sample outputs (test hook) or null
+  int32_t* st_out;
+  int32_t* path_len;
+  int32_t* paths;
+  int32_t max_len;
+  long long* stats;
+  int32_t* sstatus;
+  // tables
+  PiEntry* pi_base;                 // per CTA: NW * pcap
+  int pcap;
+  unsigned char* gm_base;           // global-memory tables, per CTA
+  size_t gm_stride;
+  int gm_hlog;
+  int gm_lcap;
+};
+
+// per-CTA control block in shared memory
+struct Ctl {
+  int lo[2][MAXD + 2];
+  int hi[2][MAXD + 2];
+  long long cost[2];
+  long long stat[KADABRA_NSTAT];
+  long long tot[KADABRA_NSTAT];
+  unsigned long long wsum[NW];
+  unsigned long long wsum_hi[NW];
+  unsigned long long r;
+  unsigned long long sel_off;
+  int depth[2];
+  int npi[NW];
+  int scan_tmp[NW];
+  long long scan_tmp64[NW];
+  int s, t;
+  int nlist;
+  int flags;
+  int side;
+  int f0, fcount, ecount;
+  int done;       // 0 = continue, 1 = touch, 2 = disconnected
+  int sel_warp;
+  int pick, pick_pos;
+  int cv, cw;     // chosen candidate edge (v on the s side, w on the t side)
+  int path_nodes;
+  int list_before;
+  unsigned long long cur;
+  unsigned long long ntotal;
+};
+
+// ============================================================== block helpers
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+__device__ __forceinline__ int warp_id() { return threadIdx.x >> 5; }
+
+// exclusive scan of one int per thread; *total gets the block sum
+__device__ __forceinline__ int block_exscan(int x, int* tmp, int* total) {
+  const int lane = lane_id(), w = warp_id();
+  int v = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(FULL, v, o);
+    if (lane >= o) v += y;
+  }
+  if (lane == 31) tmp[w] = v;
+  __syncthreads();
+  int wpre = 0, tot = 0;
+#pragma unroll
+  for (int i = 0; i < NW; ++i) {
+    const int t = tmp[i];
+    if (i < w) wpre += t;
+    tot += t;
+  }
+  __syncthreads();
+  *total = tot;
+  return wpre + v - x;
+}
+
+__device__ __forceinline__ long long block_sum64(long long x, long long* tmp) {
+  const int lane = lane_id(), w = warp_id();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+  if (lane == 0) tmp[w] = x;
+  __syncthreads();
+  long long tot = 0;
+#pragma unroll
+  for (int i = 0; i < NW; ++i) tot += tmp[i];
+  __syncthreads();
+  return tot;
+}
+
+__device__ __forceinline__ unsigned long long warp_incl_scan_u64(unsigned long long v) {
+  const int lane = lane_id();
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(FULL, v, o);
+    if (lane >= o) v += y;
+  }
+  return v;
+}
+
+// largest p in [0, cnt) with pre[p] <= e (pre non-decreasing, pre[0] = 0)
+__device__ __forceinline__ int frontier_pos(const int32_t* pre, int cnt, int e) {
+  int lo = 0, hi = cnt;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (pre[mid] <= e)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// ============================================================== one sample
+// All threads of the CTA call this with the same idx.  Returns with the
+// tables clean.  Flags in c.flags tell the caller what happened.
+template <bool GM>
+__device__ void run_sample(const SampleParams& P, const Tables& T, Ctl& c, uint64_t idx, int64_t out_i) {
+  const int tid = threadIdx.x, lane = lane_id(), wid = warp_id();
+  const GraphDev& G = P.g;
+
+  if (tid == 0) {
+    const uint4 b0 = draw(P.seed, P.domain, idx, 0);
+    const uint64_t u = (uint64_t)b0.x | ((uint64_t)b0.y << 32);
+    const uint64_t u2 = (uint64_t)b0.z | ((uint64_t)b0.w << 32);
+    const int s = (int)__umul64hi(u, (uint64_t)G.n);
+    const int tp = (int)__umul64hi(u2, (uint64_t)(G.n - 1));
+    const int t = tp + (tp >= s ? 1 : 0);
+    c.s = s;
+    c.t = t;
+    for (int k = 0; k < KADABRA_NSTAT; ++k) c.stat[k] = 0;
+    c.stat[KADABRA_STAT_DIST] = -1;
+    c.flags = 0;
+    c.done = 0;
+    uint32_t pos;
+    if (tab_insert(T, s, pack_val(0, 0, 0), &pos) != 1) c.flags |= F_INTERNAL;
+    if (tab_insert(T, t, pack_val(1, 0, 1), &pos) != 1) c.flags |= F_INTERNAL;
+    T.lnode[0] = s;
+    T.lsig[0] = 1ull;
+    T.lnode[1] = t;
+    T.lsig[1] = 1ull;
+    c.nlist = 2;
+    c.lo[0][0] = 0;
+    c.hi[0][0] = 1;
+    c.lo[1][0] = 1;
+    c.hi[1][0] = 2;
+    c.depth[0] = 0;
+    c.depth[1] = 0;
+    c.cost[0] = G.rp[s + 1] - G.rp[s];
+    c.cost[1] = G.rrp[t + 1] - G.rrp[t];
+  }
+  __syncthreads();
+
+  // ------------------------------------------------ bb-BFS (Sec. 4)
+  for (int iter = 0; iter < 2 * (MAXD + 1); ++iter) {
+    if (tid == 0) {
+      const int side = c.cost[0] <= c.cost[1] ? 0 : 1;
+      const int d = c.depth[side];
+      c.side = side;
+      c.f0 = c.lo[side][d];
+      c.fcount = c.hi[side][d] - c.lo[side][d];
+      c.stat[KADABRA_STAT_LEVELS] += 1;
+      c.stat[KADABRA_STAT_EXPANDED] += c.fcount;
+      c.list_before = c.nlist;
+    }
+    __syncthreads();
+    const int side = c.side;
+    const int f0 = c.f0, fcount = c.fcount;
+    const int32_t* rowp = side == 0 ? G.rp : G.rrp;
+    const int32_t* cols = side == 0 ? G.ci : G.rci;
+
+    // degree prefix over the (sorted) frontier
+    {
+      int carry = 0;
+      for (int base = 0; base < fcount; base += NT) {
+        const int i = base + tid;
+        int deg = 0;
+        if (i < fcount) {
+          const int x = T.lnode[f0 + i];
+          deg = rowp[x + 1] - rowp[x];
+        }
+        int tot;
+        const int ex = block_exscan(deg, c.scan_tmp, &tot);
+        if (i < fcount) T.pre[i] = carry + ex;
+        carry += tot;
+      }
+      if (tid == 0) {
+        T.pre[fcount] = carry;
+        c.ecount = carry;
+        c.stat[KADABRA_STAT_EDGES] += carry;
+      }
+      __syncthreads();
+    }
+    const int E = c.ecount;
+
+    // pass 1: touch test; each warp scans a contiguous slice in order
+    {
+      const int per = (E + NW - 1) / NW;
+      const int c0 = min(E, wid * per), c1 = min(E, c0 + per);
+      int npi = 0;
+      bool sigma_of = false;
+      PiEntry* seg = T.pi + (size_t)wid * T.pcap;
+      for (int base = c0; base < c1; base += 32) {
+        const int e = base + lane;
+        bool touch = false;
+        int x = 0, y = 0;
+        unsigned long long wgt = 0;
+        if (e < c1) {
+          const int p = frontier_pos(T.pre, fcount, e);
+          x = T.lnode[f0 + p];
+          y = __ldg(&cols[__ldg(&rowp[x]) + (e - T.pre[p])]);
+          const uint32_t v = tab_find(T, y);
+          if (v != NONE && val_side(v) != side) {
+            touch = true;
+            const unsigned long long sx = T.lsig[f0 + p];
+            const unsigned long long sy = T.lsig[val_slot(v)];
+            wgt = sx * sy;
+            if (__umul64hi(sx, sy) != 0ull) sigma_of = true;
+          }
+        }
+        const unsigned m = __ballot_sync(FULL, touch);
+        if (touch) {
+          const int pos = npi + __popc(m & ((1u << lane) - 1u));
+          if (pos < T.pcap) {
+            seg[pos].x = x;
+            seg[pos].y = y;
+            seg[pos].w = wgt;
+          }
+        }
+        npi += __popc(m);
+      }
+      if (__any_sync(FULL, sigma_of) && lane == 0) atomicOr(&c.flags, F_SIGMA);
+      if (lane == 0) {
+        c.npi[wid] = npi;
+        if (npi > T.pcap) atomicOr(&c.flags, F_CAP);
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      int tot = 0;
+      for (int w = 0; w < NW; ++w) tot += c.npi[w];
+      if (tot > 0) {
+        c.done = 1;
+        c.stat[KADABRA_STAT_PI] = tot;
+      }
+    }
+    __syncthreads();
+    if (c.flags) return;
+    if (c.done) break;
+
+    // pass 2: insert the nodes of the next level
+    const int dnew = c.depth[side] + 1;
+    if (dnew > MAXD) {
+      if (tid == 0) c.flags |= F_CAP;
+      __syncthreads();
+      return;
+    }
+    const int list_before = c.list_before;
+    for (int e = tid; e < E; e += NT) {
+      const int p = frontier_pos(T.pre, fcount, e);
+      const int x = T.lnode[f0 + p];
+      const int y = __ldg(&cols[__ldg(&rowp[x]) + (e - T.pre[p])]);
+      uint32_t pos;
+      const int r = tab_insert(T, y, pack_val(side, dnew, SLOT_PENDING), &pos);
+      if (r == 1) {
+        const int slot = atomicAdd(&c.nlist, 1);
+        if (slot < T.lcap) {
+          T.lnode[slot] = y;
+          T.lsig[slot] = 0ull;
+          T.hkv[pos] = ((unsigned long long)(uint32_t)y << 32) | pack_val(side, dnew, (uint32_t)slot);
+        } else {
+          atomicOr(&c.flags, F_CAP);
+        }
+      } else if (r < 0) {
+        atomicOr(&c.flags, F_CAP);
+      }
+    }
+    __syncthreads();
+    if (c.flags) return;
+
+    // pass 3: sigma of the new level (Brandes-style accumulation)
+    long long hits = 0;
+    {
+      bool of = false;
+      for (int e = tid; e < E; e += NT) {
+        const int p = frontier_pos(T.pre, fcount, e);
+        const int x = T.lnode[f0 + p];
+        const int y = __ldg(&cols[__ldg(&rowp[x]) + (e - T.pre[p])]);
+        const uint32_t v = tab_find(T, y);
+        if (v != NONE && val_side(v) == side && val_dist(v) == dnew) {
+          const unsigned long long add = T.lsig[f0 + p];
+          const unsigned long long old = atomicAdd(&T.lsig[val_slot(v)], add);
+          if (old + add < old) of = true;
+          ++hits;
+        }
+      }
+      if (of) atomicOr(&c.flags, F_SIGMA);
+    }
+    hits = block_sum64(hits, c.scan_tmp64);
+    if (c.flags) return;
+    const int nb = list_before, cnt = c.nlist - list_before;
+    if (cnt == 0) {  // frontier exhausted: s and t are not connected
+      if (tid == 0) c.done = 2;
+      __syncthreads();
+      break;
+    }
+
+    // sort the new level by node id (bitonic, +inf padding past cnt)
+    {
+      int P2 = 1;
+      while (P2 < cnt) P2 <<= 1;
+      for (int k = 2; k <= P2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+          for (int q = tid; q < (P2 >> 1); q += NT) {
+            int i, partner;
+            if (j == (k >> 1)) {  // mirror step of block size k
+              i = (q / j) * k + (q % j);
+              partner = i ^ (k - 1);
+            } else {
+              i = (q / j) * (2 * j) + (q % j);
+              partner = i + j;
+            }
+            if (partner < cnt) {
+              const int a = T.lnode[nb + i], b = T.lnode[nb + partner];
+              if (a > b) {
+                T.lnode[nb + i] = b;
+                T.lnode[nb + partner] = a;
+                const unsigned long long sa = T.lsig[nb + i];
+                T.lsig[nb + i] = T.lsig[nb + partner];
+                T.lsig[nb + partner] = sa;
+              }
+            }
+          }
+          __syncthreads();
+        }
+      }
+    }
+    // point the hash entries at the sorted slots; degree sum of the new frontier
+    long long cost = 0;
+    for (int i = tid; i < cnt; i += NT) {
+      const int y = T.lnode[nb + i];
+      const int64_t pos = tab_findpos(T, y);
+      if (pos < 0) {
+        atomicOr(&c.flags, F_INTERNAL);
+      } else {
+        T.hkv[pos] = ((unsigned long long)(uint32_t)y << 32) | pack_val(side, dnew, (uint32_t)(nb + i));
+      }
+      cost += rowp[y + 1] - rowp[y];
+    }
+    cost = block_sum64(cost, c.scan_tmp64);
+    if (tid == 0) {
+      c.lo[side][dnew] = nb;
+      c.hi[side][dnew] = nb + cnt;
+      c.depth[side] = dnew;
+      c.cost[side] = cost;
+      c.stat[KADABRA_STAT_NEW] += cnt;
+      c.stat[KADABRA_STAT_SIGMA_ADDS] += hits - cnt;
+    }
+    __syncthreads();
+    if (c.flags) return;
+  }
+  if (c.done == 0) {  // loop bound reached (cannot happen below MAXD levels)
+    if (tid == 0) c.flags |= F_CAP;
+    __syncthreads();
+    return;
+  }
+  if (c.done == 2) return;  // disconnected: no hits
+
+  // ------------------------------------------------ candidate-edge choice
+  {
+    unsigned long long lo = 0, hi = 0;
+    const int npi = c.npi[wid];
+    const PiEntry* seg = T.pi + (size_t)wid * T.pcap;
+    for (int i = lane; i < npi; i += 32) {
+      const unsigned long long w = seg[i].w;
+      lo += w;
+      if (lo < w) ++hi;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long lo2 = __shfl_xor_sync(FULL, lo, o);
+      const unsigned long long hi2 = __shfl_xor_sync(FULL, hi, o);
+      const unsigned long long s = lo + lo2;
+      hi = hi + hi2 + (s < lo ? 1ull : 0ull);
+      lo = s;
+    }
+    if (lane == 0) {
+      c.wsum[wid] = lo;
+      c.wsum_hi[wid] = hi;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long lo = 0, hi = 0;
+    for (int w = 0; w < NW; ++w) {
+      const unsigned long long s = lo + c.wsum[w];
+      hi += c.wsum_hi[w] + (s < lo ? 1ull : 0ull);
+      lo = s;
+    }
+    if (hi != 0) {
+      c.flags |= F_SIGMA;
+    } else {
+      c.stat[KADABRA_STAT_SIGMA_LO] = (long long)(lo & 0xFFFFFFFFull);
+      c.stat[KADABRA_STAT_SIGMA_HI] = (long long)(lo >> 32);
+      const unsigned long long r = below128(draw(P.seed, P.domain, idx, 1), lo);
+      unsigned long long acc = 0;
+      c.sel_warp = -1;
+      for (int w = 0; w < NW; ++w) {
+        if (r < acc + c.wsum[w]) {
+          c.sel_warp = w;
+          c.sel_off = r - acc;
+          break;
+        }
+        acc += c.wsum[w];
+      }
+      if (c.sel_warp < 0) c.flags |= F_INTERNAL;
+    }
+  }
+  __syncthreads();
+  if (c.flags) return;
+  if (wid == c.sel_warp) {
+    const int npi = c.npi[wid];
+    const PiEntry* seg = T.pi + (size_t)wid * T.pcap;
+    const unsigned long long target = c.sel_off;
+    unsigned long long run = 0;
+    bool found = false;
+    for (int base = 0; base < npi && !found; base += 32) {
+      const int i = base + lane;
+      const unsigned long long w = i < npi ? seg[i].w : 0ull;
+      const unsigned long long incl = warp_incl_scan_u64(w);
+      const bool hit = (i < npi) && (run + incl > target);
+      const unsigned m = __ballot_sync(FULL, hit);
+      if (m) {
+        const int first = __ffs(m) - 1;
+        if (lane == first) {
+          const PiEntry pe = seg[i];
+          if (c.side == 0) {
+            c.cv = pe.x;
+            c.cw = pe.y;
+          } else {
+            c.cv = pe.y;
+            c.cw = pe.x;
+          }
+        }
+        found = true;
+      }
+      run += __shfl_sync(FULL, incl, 31);
+    }
+    if (!found && lane == 0) atomicOr(&c.flags, F_INTERNAL);
+  }
+  __syncthreads();
+  if (c.flags) return;
+
+  // ------------------------------------------------ backtracking
+  uint32_t j = 2;
+  int dv = 0, dw = 0;
+  if (tid == 0) {
+    const uint32_t a = tab_find(T, c.cv), b = tab_find(T, c.cw);
+    if (a == NONE || b == NONE || val_side(a) != 0 || val_side(b) != 1) {
+      c.flags |= F_INTERNAL;
+    } else {
+      c.pick = val_dist(a);   // temporarily: dist_s(v)
+      c.pick_pos = val_dist(b);  // dist_t(w)
+    }
+  }
+  __syncthreads();
+  if (c.flags) return;
+  dv = c.pick;
+  dw = c.pick_pos;
+  __syncthreads();
+  const int total_nodes = dv + dw + 2;
+  const bool want_path = P.paths != nullptr && out_i >= 0;
+  if (tid == 0) {
+    c.stat[KADABRA_STAT_DIST] = dv + 1 + dw;
+    c.stat[KADABRA_STAT_PATH_NODES] = total_nodes;
+    if (want_path) {
+      int32_t* row = P.paths + out_i * (int64_t)P.max_len;
+      if (dv < P.max_len) row[dv] = c.cv;
+      if (dv + 1 < P.max_len) row[dv + 1] = c.cw;
+    }
+    if (P.counts) {
+      if (dv > 0) atomicAdd(&P.counts[c.cv], 1u);
+      if (dw > 0) atomicAdd(&P.counts[c.cw], 1u);
+    }
+  }
+  for (int half = 0; half < 2; ++half) {
+    // half 0: v -> s over in-arcs (weights sigma_s); half 1: w -> t over out-arcs
+    int x = half == 0 ? c.cv : c.cw;
+    int dx = half == 0 ? dv : dw;
+    const int32_t* brow = half == 0 ? G.rrp : G.rp;
+    const int32_t* bcol = half == 0 ? G.rci : G.ci;
+    while (dx > 0) {
+      if (tid == 0) {
+        const uint32_t vx = tab_find(T, x);
+        if (vx == NONE || (int)val_slot(vx) >= T.lcap) {
+          c.flags |= F_INTERNAL;
+          c.r = 0;
+        } else {
+          c.r = below128(draw(P.seed, P.domain, idx, j), T.lsig[val_slot(vx)]);
+        }
+      }
+      ++j;
+      __syncthreads();
+      if (c.flags) return;
+      const int r0 = brow[x], deg = brow[x + 1] - r0;
+      const int per = (deg + NW - 1) / NW;
+      const int c0 = min(deg, wid * per), c1 = min(deg, c0 + per);
+      unsigned long long part = 0;
+      for (int e = c0 + lane; e < c1; e += 32) {
+        const int y = __ldg(&bcol[r0 + e]);
+        const uint32_t v = tab_find(T, y);
+        if (v != NONE && val_side(v) == half && val_dist(v) == dx - 1) part += T.lsig[val_slot(v)];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
+      if (lane == 0) c.wsum[wid] = part;
+      __syncthreads();
+      if (tid == 0) {
+        unsigned long long acc = 0;
+        c.sel_warp = -1;
+        for (int w = 0; w < NW; ++w) {
+          if (c.r < acc + c.wsum[w]) {
+            c.sel_warp = w;
+            c.sel_off = c.r - acc;
+            break;
+          }
+          acc += c.wsum[w];
+        }
+        if (c.sel_warp < 0) c.flags |= F_INTERNAL;
+      }
+      __syncthreads();
+      if (c.flags) return;
+      if (wid == c.sel_warp) {
+        unsigned long long run = 0;
+        bool found = false;
+        for (int base = c0; base < c1 && !found; base += 32) {
+          const int e = base + lane;
+          unsigned long long w = 0;
+          int y = -1;
+          if (e < c1) {
+            y = __ldg(&bcol[r0 + e]);
+            const uint32_t v = tab_find(T, y);
+            if (v != NONE && val_side(v) == half && val_dist(v) == dx - 1) w = T.lsig[val_slot(v)];
+          }
+          const unsigned long long incl = warp_incl_scan_u64(w);
+          const bool hit = (e < c1) && w != 0 && (run + incl > c.sel_off);
+          const unsigned m = __ballot_sync(FULL, hit);
+          if (m) {
+            const int first = __ffs(m) - 1;
+            if (lane == first) {
+              c.pick = y;
+              c.pick_pos = e;
+            }
+            found = true;
+          }
+          run += __shfl_sync(FULL, incl, 31);
+        }
+        if (!found && lane == 0) atomicOr(&c.flags, F_INTERNAL);
+      }
+      __syncthreads();
+      if (c.flags) return;
+      x = c.pick;
+      dx -= 1;
+      if (tid == 0) {
+        c.stat[KADABRA_STAT_BT_SCANNED] += c.pick_pos + 1;
+        if (dx > 0 && P.counts) atomicAdd(&P.counts[x], 1u);
+        if (want_path) {
+          const int at = half == 0 ? dx : (dv + 1) + (dw - dx);
+          if (at < P.max_len) P.paths[out_i * (int64_t)P.max_len + at] = x;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// clears every hash entry the sample inserted (global tables) or the whole
+// table (shared memory, cheaper than locating the entries)
+template <bool GM>
+__device__ void reset_tables(const Tables& T, Ctl& c) {
+  const int tid = threadIdx.x;
+  if (!GM || (c.flags & F_CAP)) {
+    for (uint32_t i = tid; i <= T.hmask; i += NT) T.hkv[i] = EMPTY;
+    __syncthreads();
+    return;
+  }
+  const int nl = min(c.nlist, T.lcap);
+  for (int i = tid; i < nl; i += NT) T.pre[i] = (int32_t)tab_findpos(T, T.lnode[i]);
+  __syncthreads();
+  for (int i = tid; i < nl; i += NT)
+    if (T.pre[i] >= 0) T.hkv[T.pre[i]] = EMPTY;
+  __syncthreads();
+}
+
+template <bool GM>
+__global__ void __launch_bounds__(NT) k_sample(SampleParams P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Ctl& c = *reinterpret_cast<Ctl*>(smem);
+  Tables T;
+  if (!GM) {
+    unsigned char* p = smem + ((sizeof(Ctl) + 15) & ~size_t(15));
+    T.hkv = reinterpret_cast<unsigned long long*>(p);
+    p += sizeof(unsigned long long) << FAST_HLOG;
+    T.lsig = reinterpret_cast<unsigned long long*>(p);
+    p += sizeof(unsigned long long) * FAST_LCAP;
+    T.lnode = reinterpret_cast<int32_t*>(p);
+    p += sizeof(int32_t) * FAST_LCAP;
+    T.pre = reinterpret_cast<int32_t*>(p);
+    T.hlog = FAST_HLOG;
+    T.hmask = (1u << FAST_HLOG) - 1u;
+    T.lcap = FAST_LCAP;
+  } else {
+    unsigned char* p = P.gm_base + (size_t)blockIdx.x * P.gm_stride;
+    T.hkv = reinterpret_cast<unsigned long long*>(p);
+    p += sizeof(unsigned long long) << P.gm_hlog;
+    T.lsig = reinterpret_cast<unsigned long long*>(p);
+    p += sizeof(unsigned long long) * (size_t)P.gm_lcap;
+    T.lnode = reinterpret_cast<int32_t*>(p);
+    p += sizeof(int32_t) * (size_t)P.gm_lcap;
+    T.pre = reinterpret_cast<int32_t*>(p);
+    T.hlog = P.gm_hlog;
+    T.hmask = (1u << P.gm_hlog) - 1u;
+    T.lcap = P.gm_lcap;
+  }
+  T.pi = P.pi_base + (size_t)blockIdx.x * NW * P.pcap;
+  T.pcap = P.pcap;
+
+  const int tid = threadIdx.x;
+  if (!GM)
+    for (uint32_t i = tid; i <= T.hmask; i += NT) T.hkv[i] = EMPTY;
+  if (tid == 0) {
+    for (int k = 0; k < KADABRA_NSTAT; ++k) c.tot[k] = 0;
+    c.ntotal = GM ? min(P.ctr[2], (unsigned long long)P.deferred_cap) : P.count;
+  }
+  __syncthreads();
+  const unsigned long long ntotal = c.ntotal;
+
+  for (;;) {
+    if (tid == 0) c.cur = atomicAdd(&P.ctr[GM ? 1 : 0], 1ull);
+    __syncthreads();
+    const unsigned long long k = c.cur;
+    if (k >= ntotal) break;
+    const uint64_t idx = GM ? P.deferred[k] : P.first_idx + k;
+    const int64_t out_i = P.st_out ? (int64_t)(idx - P.first_idx) : -1;
+    if (tid == 0 && out_i >= 0 && P.paths) {
+      int32_t* row = P.paths + out_i * (int64_t)P.max_len;
+      for (int q = 0; q < P.max_len; ++q) row[q] = -1;
+    }
+    __syncthreads();
+    run_sample<GM>(P, T, c, idx, out_i);
+    __syncthreads();
+    const int flags = c.flags;
+    if (tid == 0) {
+      if (!GM && (flags & F_CAP) && !(flags & (F_SIGMA | F_INTERNAL))) {
+        const unsigned long long d = atomicAdd(&P.ctr[2], 1ull);
+        if (d < P.deferred_cap)
+          P.deferred[d] = idx;
+        else
+          atomicCAS(P.status, 0, (int)KADABRA_ERR_CAPACITY);
+      } else {
+        int st = KADABRA_OK;
+        if (flags & F_INTERNAL)
+          st = KADABRA_ERR_INTERNAL;
+        else if (flags & F_SIGMA)
+          st = KADABRA_ERR_SIGMA_OVERFLOW;
+        else if (flags & F_CAP)
+          st = KADABRA_ERR_CAPACITY;
+        if (st != KADABRA_OK) atomicCAS(P.status, 0, st);
+        for (int q = 0; q < KADABRA_NSTAT; ++q)
+          if (q != KADABRA_STAT_SIGMA_LO && q != KADABRA_STAT_SIGMA_HI && q != KADABRA_STAT_DIST)
+            c.tot[q] += c.stat[q];
+        if (out_i >= 0) {
+          P.st_out[2 * out_i] = c.s;
+          P.st_out[2 * out_i + 1] = c.t;
+          if (P.path_len) P.path_len[out_i] = (int32_t)c.stat[KADABRA_STAT_PATH_NODES];
+          if (P.stats)
+            for (int q = 0; q < KADABRA_NSTAT; ++q) P.stats[out_i * KADABRA_NSTAT + q] = c.stat[q];
+          if (P.sstatus) P.sstatus[out_i] = st;
+        }
+      }
+    }
+    __syncthreads();
+    reset_tables<GM>(T, c);
+  }
+  if (tid == 0 && P.totals)
+    for (int q = 0; q < KADABRA_NSTAT; ++q)
+      if (c.tot[q]) atomicAdd((unsigned long long*)&P.totals[q], (unsigned long long)c.tot[q]);
+}
+
+size_t fast_smem_bytes() {
+  return ((sizeof(Ctl) + 15) & ~size_t(15)) + (sizeof(unsigned long long) << FAST_HLOG) +
+         sizeof(unsigned long long) * FAST_LCAP + sizeof(int32_t) * FAST_LCAP + sizeof(int32_t) * (FAST_LCAP + 1);
+}
+
+// ============================================================== stop test
+struct CheckOut {
+  unsigned long long max_f_bits;
+  unsigned long long max_g_bits;
+  unsigned int fail;
+  unsigned int pad;
+};
+
+// f and g of Thm. 2; this expression tree is part of the specification
+// (FP64, no contraction: the file is compiled with --fmad=false).
+__device__ __forceinline__ void f_and_g(uint32_t count, double t, double omega, double lnL, double lnU, double* f,
+                                        double* g) {
+  const double b = (double)count / t;
+  const double aL = (1.0 / 3.0) - omega / t;
+  const double aU = (1.0 / 3.0) + omega / t;
+  *f = (lnL / t) * (aL + sqrt(aL * aL + ((2.0 * b) * omega) / lnL));
+  *g = (lnU / t) * (aU + sqrt(aU * aU + ((2.0 * b) * omega) / lnU));
+}
+
+__global__ void __launch_bounds__(256) k_check(const uint32_t* __restrict__ counts, const double* __restrict__ lnL,
+                                               const double* __restrict__ lnU, int64_t n, uint64_t tau,
+                                               double omega, double lambda, CheckOut* out) {
+  const double t = (double)tau;
+  unsigned long long mf = 0, mg = 0;
+  unsigned fail = 0;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    double f, g;
+    f_and_g(counts[v], t, omega, lnL[v], lnU[v], &f, &g);
+    if (!(f <= lambda) || !(g <= lambda)) fail = 1;
+    const unsigned long long fb = (unsigned long long)__double_as_longlong(f);
+    const unsigned long long gb = (unsigned long long)__double_as_longlong(g);
+    mf = fb > mf ? fb : mf;
+    mg = gb > mg ? gb : mg;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long a = __shfl_xor_sync(FULL, mf, o);
+    const unsigned long long b = __shfl_xor_sync(FULL, mg, o);
+    mf = a > mf ? a : mf;
+    mg = b > mg ? b : mg;
+    fail |= __shfl_xor_sync(FULL, fail, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (mf) atomicMax(&out->max_f_bits, mf);
+    if (mg) atomicMax(&out->max_g_bits, mg);
+    if (fail) atomicOr(&out->fail, 1u);
+  }
+}
+
+__global__ void k_btilde(const uint32_t* __restrict__ counts, int64_t n, uint64_t tau, double* __restrict__ out) {
+  const double t = (double)tau;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    out[v] = (double)counts[v] / t;
+}
+
+__global__ void k_philox(uint64_t seed, uint32_t domain, uint32_t j, uint64_t first, uint32_t count, uint4* out) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) out[i] = draw(seed, domain, first + i, j);
+}
+
+// ============================================================== graph checks, VD
+// error bits: 1 offsets, 2 id range, 4 order/duplicate, 8 self-loop, 16 reverse mismatch
+__global__ void k_validate_rows(const int32_t* rp, const int32_t* ci, int32_t n, int64_t m, unsigned* err) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t a = rp[v], b = rp[v + 1];
+    if (a < 0 || b < a || b > m) {
+      atomicOr(err, 1u);
+      continue;
+    }
+    int32_t prev = -1;
+    for (int32_t e = a; e < b; ++e) {
+      const int32_t y = ci[e];
+      if (y < 0 || y >= n) {
+        atomicOr(err, 2u);
+        break;
+      }
+      if (y <= prev) atomicOr(err, 4u);
+      if (y == v) atomicOr(err, 8u);
+      prev = y;
+    }
+  }
+}
+
+__device__ __forceinline__ bool row_has(const int32_t* rp, const int32_t* ci, int32_t v, int32_t y) {
+  int32_t lo = rp[v], hi = rp[v + 1];
+  while (lo < hi) {
+    const int32_t mid = (lo + hi) >> 1;
+    const int32_t z = ci[mid];
+    if (z == y) return true;
+    if (z < y)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return false;
+}
+
+// every out-arc (u,y) must appear as in-arc of y (directed) or as (y,u) (undirected)
+__global__ void k_validate_mirror(const int32_t* rp, const int32_t* ci, const int32_t* rrp, const int32_t* rci,
+                                  int32_t n, unsigned* err) {
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
+    for (int32_t e = rp[u]; e < rp[u + 1]; ++e)
+      if (!row_has(rrp, rci, ci[e], (int32_t)u)) {
+        atomicOr(err, 16u);
+        return;
+      }
+}
+
+__global__ void k_und_degree_key(const int32_t* rp, const int32_t* ci, const int32_t* rrp, const int32_t* rci,
+                                 int32_t n, int directed, unsigned long long* best) {
+  unsigned long long mine = 0;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    int64_t d;
+    if (!directed) {
+      d = rp[v + 1] - rp[v];
+    } else {  // |out(v) U in(v)| by merging the two sorted rows
+      int32_t a = rp[v], ae = rp[v + 1], b = rrp[v], be = rrp[v + 1];
+      d = 0;
+      while (a < ae || b < be) {
+        if (b >= be || (a < ae && ci[a] < rci[b]))
+          ++a;
+        else if (a >= ae || rci[b] < ci[a])
+          ++b;
+        else {
+          ++a;
+          ++b;
+        }
+        ++d;
+      }
+    }
+    const unsigned long long key = ((unsigned long long)d << 32) | (0xFFFFFFFFu - (uint32_t)v);
+    mine = key > mine ? key : mine;
+  }
+  atomicMax(best, mine);
+}
+
+// one BFS level over the underlying undirected graph; one warp per frontier node
+__global__ void k_bfs_level(const int32_t* rp, const int32_t* ci, const int32_t* rrp, const int32_t* rci, int directed,
+                            const int32_t* front, int32_t nfront, int32_t* next, int32_t* nnext, int32_t* dist,
+                            int32_t level) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = w0; i < nfront; i += nwarps) {
+    const int32_t v = front[i];
+    for (int pass = 0; pass < (directed ? 2 : 1); ++pass) {
+      const int32_t* r = pass ? rrp : rp;
+      const int32_t* c = pass ? rci : ci;
+      for (int32_t e = r[v] + lane; e < r[v + 1]; e += 32) {
+        const int32_t y = c[e];
+        if (dist[y] < 0 && atomicCAS(&dist[y], -1, level + 1) == -1) next[atomicAdd(nnext, 1)] = y;
+      }
+    }
+  }
+}
+
+// ============================================================== host side
+thread_local std::string g_last_error;
+
+kadabra_status fail(kadabra_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+#define KCK(call)                                                                                   \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess)                                                                          \
+      return fail(e_ == cudaErrorMemoryAllocation ? KADABRA_ERR_OOM : KADABRA_ERR_CUDA,             \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                              \
+  } while (0)
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+int ceil_log2(uint64_t x) {
+  int k = 0;
+  while ((1ull << k) < x) ++k;
+  return k;
+}
+
+}  // namespace
+
+// graph object (opaque in the ABI)
+struct kadabra_graph {
+  int32_t n = 0;
+  int64_t m = 0;
+  int directed = 0;
+  int32_t *rp = nullptr, *ci = nullptr, *rrp = nullptr, *rci = nullptr;
+  bool owns_csr = false;
+  int64_t vd = 0;
+  int device = 0;
+  int num_sms = 0;
+  // sampler workspace (allocated on first use)
+  bool ws_ready = false;
+  int grid_fast = 0, grid_gm = 0;
+  size_t smem_fast = 0;
+  unsigned long long* ctr = nullptr;
+  int32_t* status = nullptr;
+  unsigned long long* deferred = nullptr;
+  uint64_t deferred_cap = 0;
+  PiEntry* pi_fast = nullptr;
+  PiEntry* pi_gm = nullptr;
+  int pcap_gm = 0;
+  unsigned char* gm_base = nullptr;
+  size_t gm_stride = 0;
+  int gm_hlog = 0;
+  int gm_lcap = 0;
+  // run buffers
+  uint32_t *counts = nullptr, *count0 = nullptr;
+  double *lnL = nullptr, *lnU = nullptr, *btilde = nullptr;
+  CheckOut* chk = nullptr;
+  long long* totals = nullptr;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+kadabra_status dev_alloc(kadabra_graph* g, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+  if (e != cudaSuccess)
+    return fail(KADABRA_ERR_OOM, std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+  g->allocs.push_back(*p);
+  return KADABRA_OK;
+}
+
+#define KTRY(expr)                        \
+  do {                                    \
+    kadabra_status s_ = (expr);           \
+    if (s_ != KADABRA_OK) return s_;      \
+  } while (0)
+
+kadabra_status ensure_workspace(kadabra_graph* g, uint64_t deferred_need) {
+  if (!g->ws_ready) {
+    KCK(cudaSetDevice(g->device));
+    g->smem_fast = fast_smem_bytes();
+    KCK(cudaFuncSetAttribute(k_sample<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g->smem_fast));
+    int per_sm = 0;
+    KCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample<false>, NT, g->smem_fast));
+    if (per_sm < 1) return fail(KADABRA_ERR_CAPACITY, "sampler does not fit on an SM");
+    g->grid_fast = g->num_sms * per_sm;
+    // global-memory tables for deferred samples: hash of >= 2n slots, lists of n
+    g->gm_hlog = std::max(12, ceil_log2(2ull * (uint64_t)g->n));
+    g->gm_lcap = g->n;
+    g->pcap_gm = (int)std::min<int64_t>(std::max<int64_t>(g->m, 1024), 1 << 18);
+    g->gm_stride = (sizeof(unsigned long long) << g->gm_hlog) + sizeof(unsigned long long) * (size_t)g->gm_lcap +
+                   sizeof(int32_t) * (size_t)g->gm_lcap + sizeof(int32_t) * ((size_t)g->gm_lcap + 1);
+    g->gm_stride = (g->gm_stride + 255) & ~size_t(255);
+    const size_t per_cta = g->gm_stride + sizeof(PiEntry) * NW * (size_t)g->pcap_gm;
+    const size_t budget = (size_t)4 << 30;
+    g->grid_gm = (int)std::max<size_t>(1, std::min<size_t>((size_t)g->num_sms, budget / per_cta));
+    void* p;
+    KTRY(dev_alloc(g, &p, 4 * sizeof(unsigned long long)));
+    g->ctr = (unsigned long long*)p;
+    KTRY(dev_alloc(g, &p, sizeof(int32_t)));
+    g->status = (int32_t*)p;
+    KCK(cudaMemset(g->status, 0, sizeof(int32_t)));
+    KTRY(dev_alloc(g, &p, sizeof(PiEntry) * NW * (size_t)FAST_PCAP * g->grid_fast));
+    g->pi_fast = (PiEntry*)p;
+    KTRY(dev_alloc(g, &p, sizeof(PiEntry) * NW * (size_t)g->pcap_gm * g->grid_gm));
+    g->pi_gm = (PiEntry*)p;
+    KTRY(dev_alloc(g, &p, g->gm_stride * g->grid_gm));
+    g->gm_base = (unsigned char*)p;
+    for (int b = 0; b < g->grid_gm; ++b)
+      KCK(cudaMemset(g->gm_base + (size_t)b * g->gm_stride, 0xFF, sizeof(unsigned long long) << g->gm_hlog));
+    KTRY(dev_alloc(g, &p, sizeof(uint32_t) * (size_t)g->n));
+    g->counts = (uint32_t*)p;
+    KTRY(dev_alloc(g, &p, sizeof(uint32_t) * (size_t)g->n));
+    g->count0 = (uint32_t*)p;
+    KTRY(dev_alloc(g, &p, sizeof(double) * (size_t)g->n));
+    g->lnL = (double*)p;
+    KTRY(dev_alloc(g, &p, sizeof(double) * (size_t)g->n));
+    g->lnU = (double*)p;
+    KTRY(dev_alloc(g, &p, sizeof(double) * (size_t)g->n));
+    g->btilde = (double*)p;
+    KTRY(dev_alloc(g, &p, sizeof(CheckOut)));
+    g->chk = (CheckOut*)p;
+    KTRY(dev_alloc(g, &p, sizeof(long long) * KADABRA_NSTAT));
+    g->totals = (long long*)p;
+    KCK(cudaDeviceSynchronize());
+    g->ws_ready = true;
+  }
+  if (deferred_need > g->deferred_cap) {
+    KCK(cudaDeviceSynchronize());
+    if (g->deferred) {
+      for (auto& a : g->allocs)
+        if (a == g->deferred) a = nullptr;
+      cudaFree(g->deferred);
+      g->deferred = nullptr;
+    }
+    uint64_t cap = std::max<uint64_t>(deferred_need, 1 << 16);
+    void* p;
+    KTRY(dev_alloc(g, &p, sizeof(unsigned long long) * cap));
+    g->deferred = (unsigned long long*)p;
+    g->deferred_cap = cap;
+  }
+  return KADABRA_OK;
+}
+
+SampleParams base_params(kadabra_graph* g) {
+  SampleParams P;
+  std::memset(&P, 0, sizeof(P));
+  P.g.n = g->n;
+  P.g.m = g->m;
+  P.g.rp = g->rp;
+  P.g.ci = g->ci;
+  P.g.rrp = g->directed ? g->rrp : g->rp;
+  P.g.rci = g->directed ? g->rci : g->ci;
+  P.ctr = g->ctr;
+  P.deferred = g->deferred;
+  P.deferred_cap = g->deferred_cap;
+  P.status = g->status;
+  P.gm_base = g->gm_base;
+  P.gm_stride = g->gm_stride;
+  P.gm_hlog = g->gm_hlog;
+  P.gm_lcap = g->gm_lcap;
+  return P;
+}
+
+// launches the shared-memory sampler and then the global-memory pass for
+// any deferred samples (the second launch exits at once when none are)
+kadabra_status launch_sampler(kadabra_graph* g, SampleParams P, cudaStream_t st) {
+  KCK(cudaMemsetAsync(g->ctr, 0, 4 * sizeof(unsigned long long), st));
+  P.pi_base = g->pi_fast;
+  P.pcap = FAST_PCAP;
+  k_sample<false><<<g->grid_fast, NT, g->smem_fast, st>>>(P);
+  KCK(cudaGetLastError());
+  P.pi_base = g->pi_gm;
+  P.pcap = g->pcap_gm;
+  k_sample<true><<<g->grid_gm, NT, sizeof(Ctl), st>>>(P);
+  KCK(cudaGetLastError());
+  return KADABRA_OK;
+}
+
+kadabra_status read_status(kadabra_graph* g, cudaStream_t st) {
+  int32_t h = 0;
+  KCK(cudaMemcpyAsync(&h, g->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  KCK(cudaStreamSynchronize(st));
+  if (h != 0) {
+    KCK(cudaMemsetAsync(g->status, 0, sizeof(int32_t), st));
+    KCK(cudaStreamSynchronize(st));
+    const char* what = h == KADABRA_ERR_SIGMA_OVERFLOW ? "a shortest-path count exceeded 2^64-1"
+                       : h == KADABRA_ERR_CAPACITY     ? "a sampler capacity bound was exceeded"
+                                                       : "the sampler reported an internal error";
+    return fail((kadabra_status)h, what);
+  }
+  return KADABRA_OK;
+}
+
+// ---------------------------------------------------------------- omega
+int64_t floor_log2_pos(int64_t x) {  // x >= 1
+  int64_t k = -1;
+  while (x > 0) {
+    x >>= 1;
+    ++k;
+  }
+  return k;
+}
+
+double omega_host(double lambda, double delta, int64_t vd) {
+  const int64_t fl = vd - 2 >= 1 ? floor_log2_pos(vd - 2) : 0;
+  return (0.5 / (lambda * lambda)) * ((double)(fl + 1) + std::log(2.0 / delta));
+}
+
+// ---------------------------------------------------------------- computeDelta
+// Alg. 2 with lambda_L = lambda_U = lambda.  Only nodes with a non-zero
+// warm-up count contribute to the sum (the others add exact zeros), and the
+// exponential of each distinct count is evaluated once per bisection step;
+// the sum runs over nodes in increasing id order.
+kadabra_status compute_delta_host(int64_t n, const uint32_t* count0, uint64_t alpha, double omega, double lambda,
+                                  double delta, double eps, double* lnL, double* lnU, double* C_out) {
+  std::vector<int64_t> nz;
+  std::unordered_map<uint32_t, size_t> idx_of;
+  std::vector<uint32_t> distinct;
+  std::vector<size_t> which;
+  for (int64_t v = 0; v < n; ++v)
+    if (count0[v]) {
+      nz.push_back(v);
+      auto it = idx_of.find(count0[v]);
+      if (it == idx_of.end()) {
+        it = idx_of.emplace(count0[v], distinct.size()).first;
+        distinct.push_back(count0[v]);
+      }
+      which.push_back(it->second);
+    }
+  std::vector<double> cval(distinct.size()), ex(distinct.size());
+  for (size_t k = 0; k < distinct.size(); ++k) {
+    const double b0 = (double)distinct[k] / (double)alpha;
+    cval[k] = ((2.0 * b0) * omega) / (lambda * lambda);
+  }
+  const double target = (delta / 2.0) - (eps * delta);
+  auto sum_at = [&](double C) {
+    for (size_t k = 0; k < distinct.size(); ++k) ex[k] = std::exp(-C / cval[k]);
+    double sum = 0.0;
+    for (size_t i = 0; i < nz.size(); ++i) {
+      const double e = ex[which[i]];
+      sum += e + e;
+    }
+    return sum;
+  };
+  double C = 0.0;
+  if (!nz.empty()) {
+    double lo = 0.0, hi = 1.0;
+    int guard = 0;
+    while (!(sum_at(hi) <= target)) {
+      lo = hi;
+      hi = 2.0 * hi;
+      if (++guard > 2100) return fail(KADABRA_ERR_INTERNAL, "computeDelta: no bracket for C");
+    }
+    for (guard = 0; guard < 4000; ++guard) {
+      const double mid = 0.5 * (lo + hi);
+      if (mid <= lo || mid >= hi) break;
+      if (sum_at(mid) <= target)
+        hi = mid;
+      else
+        lo = mid;
+    }
+    C = hi;
+  }
+  const double floor_term = (eps * delta) / (2.0 * (double)n);
+  const double ln_zero = -std::log(0.0 + floor_term);
+  for (size_t k = 0; k < distinct.size(); ++k) ex[k] = -std::log(std::exp(-C / cval[k]) + floor_term);
+  for (int64_t v = 0; v < n; ++v) {
+    lnL[v] = ln_zero;
+    lnU[v] = ln_zero;
+  }
+  for (size_t i = 0; i < nz.size(); ++i) {
+    lnL[nz[i]] = ex[which[i]];
+    lnU[nz[i]] = ex[which[i]];
+  }
+  *C_out = C;
+  return KADABRA_OK;
+}
+
+kadabra_status compute_vd(kadabra_graph* g) {
+  const int32_t n = g->n;
+  const int32_t* rrp = g->directed ? g->rrp : g->rp;
+  const int32_t* rci = g->directed ? g->rci : g->ci;
+  unsigned long long* best;
+  int32_t *dist, *qa, *qb, *cnt;
+  KCK(cudaMalloc(&best, sizeof(unsigned long long)));
+  KCK(cudaMalloc(&dist, sizeof(int32_t) * (size_t)n));
+  KCK(cudaMalloc(&qa, sizeof(int32_t) * (size_t)n));
+  KCK(cudaMalloc(&qb, sizeof(int32_t) * (size_t)n));
+  KCK(cudaMalloc(&cnt, sizeof(int32_t)));
+  kadabra_status st = KADABRA_OK;
+  do {
+    if (cudaMemset(best, 0, sizeof(unsigned long long)) != cudaSuccess) {
+      st = fail(KADABRA_ERR_CUDA, "memset");
+      break;
+    }
+    const int blocks = std::max(1, std::min(4 * g->num_sms, (n + 255) / 256));
+    k_und_degree_key<<<blocks, 256>>>(g->rp, g->ci, rrp, rci, n, g->directed, best);
+    unsigned long long hb = 0;
+    if (cudaMemcpy(&hb, best, sizeof(hb), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      st = fail(KADABRA_ERR_CUDA, std::string("vd: ") + cudaGetErrorString(cudaGetLastError()));
+      break;
+    }
+    const int32_t r = (int32_t)(0xFFFFFFFFu - (uint32_t)(hb & 0xFFFFFFFFull));
+    cudaMemset(dist, 0xFF, sizeof(int32_t) * (size_t)n);
+    const int32_t zero = 0;
+    cudaMemcpy(dist + r, &zero, sizeof(int32_t), cudaMemcpyHostToDevice);
+    cudaMemcpy(qa, &r, sizeof(int32_t), cudaMemcpyHostToDevice);
+    int32_t nfront = 1, level = 0;
+    while (nfront > 0 && level <= n) {
+      cudaMemset(cnt, 0, sizeof(int32_t));
+      const int bl = std::max(1, std::min(8 * g->num_sms, (nfront * 32 + 255) / 256));
+      k_bfs_level<<<bl, 256>>>(g->rp, g->ci, rrp, rci, g->directed, qa, nfront, qb, cnt, dist, level);
+      if (cudaMemcpy(&nfront, cnt, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        st = fail(KADABRA_ERR_CUDA, std::string("vd bfs: ") + cudaGetErrorString(cudaGetLastError()));
+        break;
+      }
+      std::swap(qa, qb);
+      if (nfront > 0) ++level;
+    }
+    g->vd = 2 * (int64_t)level + 1;
+  } while (0);
+  cudaFree(best);
+  cudaFree(dist);
+  cudaFree(qa);
+  cudaFree(qb);
+  cudaFree(cnt);
+  return st;
+}
+
+kadabra_status finish_load(kadabra_graph* g) {
+  unsigned* err;
+  KCK(cudaMalloc(&err, sizeof(unsigned)));
+  KCK(cudaMemset(err, 0, sizeof(unsigned)));
+  const int blocks = std::max(1, std::min(4 * g->num_sms, (g->n + 255) / 256));
+  k_validate_rows<<<blocks, 256>>>(g->rp, g->ci, g->n, g->m, err);
+  if (g->directed) k_validate_rows<<<blocks, 256>>>(g->rrp, g->rci, g->n, g->m, err);
+  unsigned h = 0;
+  KCK(cudaMemcpy(&h, err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (!h) {
+    const int32_t* rrp = g->directed ? g->rrp : g->rp;
+    const int32_t* rci = g->directed ? g->rci : g->ci;
+    k_validate_mirror<<<blocks, 256>>>(g->rp, g->ci, rrp, rci, g->n, err);
+    KCK(cudaMemcpy(&h, err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  }
+  cudaFree(err);
+  if (h) {
+    std::string why;
+    if (h & 1) why += " bad row offsets;";
+    if (h & 2) why += " node id out of range;";
+    if (h & 4) why += " row not strictly increasing;";
+    if (h & 8) why += " self-loop;";
+    if (h & 16) why += (g->directed ? " reverse CSR does not mirror the forward CSR;" : " adjacency not symmetric;");
+    return fail(KADABRA_ERR_CSR, "invalid CSR:" + why);
+  }
+  return compute_vd(g);
+}
+
+kadabra_status new_graph(int32_t n, int64_t m, int directed, kadabra_graph** out, kadabra_graph** g_out) {
+  if (!out) return fail(KADABRA_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n < 2 || n > (1 << 24)) return fail(KADABRA_ERR_ARG, "n must be in [2, 2^24]");
+  if (m < 0 || m >= ((int64_t)1 << 31)) return fail(KADABRA_ERR_ARG, "m must be in [0, 2^31)");
+  kadabra_graph* g = new kadabra_graph;
+  g->n = n;
+  g->m = m;
+  g->directed = directed ? 1 : 0;
+  if (cudaGetDevice(&g->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess) {
+    delete g;
+    return fail(KADABRA_ERR_CUDA, "no CUDA device");
+  }
+  *g_out = g;
+  return KADABRA_OK;
+}
+
+}  // namespace
+
+// ================================================================ C ABI
+extern "C" {
+
+const char* kadabra_last_error(void) { return g_last_error.c_str(); }
+
+void kadabra_config_default(kadabra_config* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->eps = 0.001;
+  cfg->check_interval = 1000;
+}
+
+double kadabra_omega(double lambda, double delta, int64_t vd) { return omega_host(lambda, delta, vd); }
+
+kadabra_status kadabra_load_csr(int32_t n, int64_t m, const int32_t* row_ptr, const int32_t* col, int directed,
+                                const int32_t* rrow_ptr, const int32_t* rcol, kadabra_graph** out) {
+  kadabra_graph* g = nullptr;
+  KTRY(new_graph(n, m, directed, out, &g));
+  if (!row_ptr || (m > 0 && !col) || (directed && (!rrow_ptr || (m > 0 && !rcol))) ||
+      (!directed && (rrow_ptr || rcol))) {
+    delete g;
+    return fail(KADABRA_ERR_ARG, "missing or unexpected CSR arrays");
+  }
+  if (row_ptr[0] != 0 || row_ptr[n] != m || (directed && (rrow_ptr[0] != 0 || rrow_ptr[n] != m))) {
+    delete g;
+    return fail(KADABRA_ERR_CSR, "row_ptr[0] must be 0 and row_ptr[n] must equal m");
+  }
+  g->owns_csr = true;
+  kadabra_status st = KADABRA_OK;
+  void* p;
+  const size_t rb = sizeof(int32_t) * ((size_t)n + 1), cb = sizeof(int32_t) * (size_t)m;
+  if ((st = dev_alloc(g, &p, rb)) != KADABRA_OK) goto bad;
+  g->rp = (int32_t*)p;
+  if ((st = dev_alloc(g, &p, cb)) != KADABRA_OK) goto bad;
+  g->ci = (int32_t*)p;
+  if (cudaMemcpy(g->rp, row_ptr, rb, cudaMemcpyHostToDevice) != cudaSuccess ||
+      (m > 0 && cudaMemcpy(g->ci, col, cb, cudaMemcpyHostToDevice) != cudaSuccess)) {
+    st = fail(KADABRA_ERR_CUDA, "CSR upload failed");
+    goto bad;
+  }
+  if (directed) {
+    if ((st = dev_alloc(g, &p, rb)) != KADABRA_OK) goto bad;
+    g->rrp = (int32_t*)p;
+    if ((st = dev_alloc(g, &p, cb)) != KADABRA_OK) goto bad;
+    g->rci = (int32_t*)p;
+    if (cudaMemcpy(g->rrp, rrow_ptr, rb, cudaMemcpyHostToDevice) != cudaSuccess ||
+        (m > 0 && cudaMemcpy(g->rci, rcol, cb, cudaMemcpyHostToDevice) != cudaSuccess)) {
+      st = fail(KADABRA_ERR_CUDA, "reverse CSR upload failed");
+      goto bad;
+    }
+  }
+  if ((st = finish_load(g)) != KADABRA_OK) goto bad;
+  *out = g;
+  return KADABRA_OK;
+bad:
+  kadabra_free_graph(g);
+  return st;
+}
+
+kadabra_status kadabra_load_csr_device(int32_t n, int64_t m, const int32_t* d_row_ptr, const int32_t* d_col,
+                                       int directed, const int32_t* d_rrow_ptr, const int32_t* d_rcol,
+                                       kadabra_graph** out) {
+  kadabra_graph* g = nullptr;
+  KTRY(new_graph(n, m, directed, out, &g));
+  if (!d_row_ptr || (m > 0 && !d_col) || (directed && (!d_rrow_ptr || (m > 0 && !d_rcol))) ||
+      (!directed && (d_rrow_ptr || d_rcol))) {
+    delete g;
+    return fail(KADABRA_ERR_ARG, "missing or unexpected CSR arrays");
+  }
+  int32_t ends[2];
+  if (cudaMemcpy(&ends[0], d_row_ptr, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(&ends[1], d_row_ptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    delete g;
+    return fail(KADABRA_ERR_ARG, "row_ptr is not readable device memory");
+  }
+  if (ends[0] != 0 || ends[1] != m) {
+    delete g;
+    return fail(KADABRA_ERR_CSR, "row_ptr[0] must be 0 and row_ptr[n] must equal m");
+  }
+  if (directed) {
+    if (cudaMemcpy(&ends[0], d_rrow_ptr, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&ends[1], d_rrow_ptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        ends[0] != 0 || ends[1] != m) {
+      delete g;
+      return fail(KADABRA_ERR_CSR, "reverse row_ptr[0] must be 0 and row_ptr[n] must equal m");
+    }
+  }
+  g->rp = const_cast<int32_t*>(d_row_ptr);
+  g->ci = const_cast<int32_t*>(d_col);
+  g->rrp = const_cast<int32_t*>(d_rrow_ptr);
+  g->rci = const_cast<int32_t*>(d_rcol);
+  kadabra_status st = finish_load(g);
+  if (st != KADABRA_OK) {
+    kadabra_free_graph(g);
+    return st;
+  }
+  *out = g;
+  return KADABRA_OK;
+}
+
+void kadabra_free_graph(kadabra_graph* g) {
+  if (!g) return;
+  cudaDeviceSynchronize();
+  for (void* p : g->allocs)
+    if (p) cudaFree(p);
+  delete g;
+}
+
+kadabra_status kadabra_graph_info(const kadabra_graph* g, int32_t* n, int64_t* m, int* directed, int64_t* vd) {
+  if (!g) return fail(KADABRA_ERR_ARG, "graph is NULL");
+  if (n) *n = g->n;
+  if (m) *m = g->m;
+  if (directed) *directed = g->directed;
+  if (vd) *vd = g->vd;
+  return KADABRA_OK;
+}
+
+kadabra_status kadabra_sample_batch(kadabra_graph* g, uint64_t seed, uint32_t domain, uint64_t first_idx,
+                                    uint64_t count, uint32_t* d_counts, int64_t* d_totals, void* stream) {
+  if (!g) return fail(KADABRA_ERR_ARG, "graph is NULL");
+  if (count == 0) return KADABRA_OK;
+  KTRY(ensure_workspace(g, count));
+  SampleParams P = base_params(g);
+  P.seed = seed;
+  P.domain = domain;
+  P.first_idx = first_idx;
+  P.count = count;
+  P.counts = d_counts;
+  P.totals = reinterpret_cast<long long*>(d_totals);
+  return launch_sampler(g, P, as_stream(stream));
+}
+
+kadabra_status kadabra_sync_status(kadabra_graph* g, void* stream) {
+  if (!g) return fail(KADABRA_ERR_ARG, "graph is NULL");
+  if (!g->ws_ready) {
+    KCK(cudaStreamSynchronize(as_stream(stream)));
+    return KADABRA_OK;
+  }
+  return read_status(g, as_stream(stream));
+}
+
+kadabra_status kadabra_sample_paths(kadabra_graph* g, uint64_t seed, uint32_t domain, uint64_t first_idx,
+                                    uint32_t count, int32_t* st_out, int32_t* path_len, int32_t* paths,
+                                    int32_t max_len, int64_t* stats, int32_t* status) {
+  if (!g || !st_out || !path_len || !status || (paths && max_len <= 0))
+    return fail(KADABRA_ERR_ARG, "bad sample_paths arguments");
+  if (count == 0) return KADABRA_OK;
+  KTRY(ensure_workspace(g, count));
+  int32_t *d_st = nullptr, *d_pl = nullptr, *d_paths = nullptr, *d_ss = nullptr;
+  long long* d_stats = nullptr;
+  kadabra_status rc = KADABRA_OK;
+  auto cleanup = [&]() {
+    cudaFree(d_st);
+    cudaFree(d_pl);
+    cudaFree(d_paths);
+    cudaFree(d_ss);
+    cudaFree(d_stats);
+  };
+  if (cudaMalloc(&d_st, sizeof(int32_t) * 2 * count) != cudaSuccess ||
+      cudaMalloc(&d_pl, sizeof(int32_t) * count) != cudaSuccess ||
+      cudaMalloc(&d_ss, sizeof(int32_t) * count) != cudaSuccess ||
+      cudaMalloc(&d_stats, sizeof(long long) * KADABRA_NSTAT * count) != cudaSuccess ||
+      (paths && cudaMalloc(&d_paths, sizeof(int32_t) * (size_t)count * max_len) != cudaSuccess)) {
+    cleanup();
+    return fail(KADABRA_ERR_OOM, "sample_paths buffers");
+  }
+  SampleParams P = base_params(g);
+  P.seed = seed;
+  P.domain = domain;
+  P.first_idx = first_idx;
+  P.count = count;
+  P.st_out = d_st;
+  P.path_len = d_pl;
+  P.paths = d_paths;
+  P.max_len = max_len;
+  P.stats = d_stats;
+  P.sstatus = d_ss;
+  rc = launch_sampler(g, P, 0);
+  if (rc == KADABRA_OK) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) rc = fail(KADABRA_ERR_CUDA, std::string("sampler: ") + cudaGetErrorString(e));
+  }
+  if (rc == KADABRA_OK) {
+    std::vector<long long> hs((size_t)KADABRA_NSTAT * count);
+    if (cudaMemcpy(st_out, d_st, sizeof(int32_t) * 2 * count, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(path_len, d_pl, sizeof(int32_t) * count, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(status, d_ss, sizeof(int32_t) * count, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(hs.data(), d_stats, sizeof(long long) * hs.size(), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        (paths && cudaMemcpy(paths, d_paths, sizeof(int32_t) * (size_t)count * max_len, cudaMemcpyDeviceToHost) !=
+                      cudaSuccess))
+      rc = fail(KADABRA_ERR_CUDA, "sample_paths copy-back");
+    else if (stats)
+      for (size_t i = 0; i < hs.size(); ++i) stats[i] = hs[i];
+  }
+  cleanup();
+  if (rc == KADABRA_OK) rc = read_status(g, 0);
+  return rc;
+}
+
+kadabra_status kadabra_philox(uint64_t seed, uint32_t domain, uint32_t j, uint64_t first_idx, uint32_t count,
+                              uint32_t* out) {
+  if (!out) return fail(KADABRA_ERR_ARG, "out is NULL");
+  if (count == 0) return KADABRA_OK;
+  uint4* d = nullptr;
+  KCK(cudaMalloc(&d, sizeof(uint4) * count));
+  k_philox<<<(count + 255) / 256, 256>>>(seed, domain, j, first_idx, count, d);
+  cudaError_t e = cudaMemcpy(out, d, sizeof(uint4) * count, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(KADABRA_ERR_CUDA, cudaGetErrorString(e));
+  return KADABRA_OK;
+}
+
+kadabra_status kadabra_check(int64_t n, const uint32_t* counts, uint64_t tau, double omega, const double* ln_inv_dl,
+                             const double* ln_inv_du, double lambda, double* max_f, double* max_g, int* stop) {
+  if (n < 1 || !counts || !ln_inv_dl || !ln_inv_du || !max_f || !max_g || !stop || tau == 0)
+    return fail(KADABRA_ERR_ARG, "bad check arguments");
+  uint32_t* dc = nullptr;
+  double *dl = nullptr, *du = nullptr;
+  CheckOut* dout = nullptr;
+  kadabra_status rc = KADABRA_OK;
+  CheckOut h;
+  if (cudaMalloc(&dc, sizeof(uint32_t) * n) != cudaSuccess || cudaMalloc(&dl, sizeof(double) * n) != cudaSuccess ||
+      cudaMalloc(&du, sizeof(double) * n) != cudaSuccess || cudaMalloc(&dout, sizeof(CheckOut)) != cudaSuccess) {
+    rc = fail(KADABRA_ERR_OOM, "check buffers");
+    goto done;
+  }
+  cudaMemcpy(dc, counts, sizeof(uint32_t) * n, cudaMemcpyHostToDevice);
+  cudaMemcpy(dl, ln_inv_dl, sizeof(double) * n, cudaMemcpyHostToDevice);
+  cudaMemcpy(du, ln_inv_du, sizeof(double) * n, cudaMemcpyHostToDevice);
+  cudaMemset(dout, 0, sizeof(CheckOut));
+  {
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(4 * (int64_t)sms, (n + 255) / 256));
+    k_check<<<blocks, 256>>>(dc, dl, du, n, tau, omega, lambda, dout);
+  }
+  if (cudaMemcpy(&h, dout, sizeof(CheckOut), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    rc = fail(KADABRA_ERR_CUDA, std::string("check: ") + cudaGetErrorString(cudaGetLastError()));
+    goto done;
+  }
+  std::memcpy(max_f, &h.max_f_bits, sizeof(double));
+  std::memcpy(max_g, &h.max_g_bits, sizeof(double));
+  *stop = h.fail ? 0 : 1;
+done:
+  cudaFree(dc);
+  cudaFree(dl);
+  cudaFree(du);
+  cudaFree(dout);
+  return rc;
+}
+
+kadabra_status kadabra_compute_delta(int64_t n, const uint32_t* count0, uint64_t alpha, double omega, double lambda,
+                                     double delta, double eps, double* ln_inv_dl, double* ln_inv_du, double* C) {
+  if (n < 1 || !count0 || !ln_inv_dl || !ln_inv_du || !C || alpha == 0)
+    return fail(KADABRA_ERR_ARG, "bad compute_delta arguments");
+  return compute_delta_host(n, count0, alpha, omega, lambda, delta, eps, ln_inv_dl, ln_inv_du, C);
+}
+
+kadabra_status kadabra_run(kadabra_graph* g, double lambda, double delta, int32_t k, uint64_t seed,
+                           const kadabra_config* cfg_in, kadabra_result* out) {
+  if (!g || !out) return fail(KADABRA_ERR_ARG, "graph or result is NULL");
+  uint32_t* counts_host = out->counts;
+  double* btilde_host = out->btilde;
+  uint32_t* counts_dev = out->d_counts;
+  double* btilde_dev = out->d_btilde;
+  int32_t* topk = out->topk;
+  std::memset(out, 0, sizeof(*out));
+  out->counts = counts_host;
+  out->btilde = btilde_host;
+  out->d_counts = counts_dev;
+  out->d_btilde = btilde_dev;
+  out->topk = topk;
+  kadabra_config cfg;
+  kadabra_config_default(&cfg);
+  if (cfg_in) cfg = *cfg_in;
+  if (cfg.check_interval == 0) cfg.check_interval = 1000;
+  auto finish = [&](kadabra_status s) {
+    out->status = s;
+    return s;
+  };
+  if (k != 0) return finish(fail(KADABRA_ERR_UNSUPPORTED, "top-k mode (k > 0) is not implemented"));
+  if (!(lambda > 0.0 && lambda < 1.0) || !(delta > 0.0 && delta < 1.0) || !(cfg.eps >= 0.0 && cfg.eps < 0.5))
+    return finish(fail(KADABRA_ERR_ARG, "lambda and delta must be in (0,1), eps in [0,0.5)"));
+  cudaStream_t st = as_stream(cfg.stream);
+  const int64_t n = g->n;
+
+  out->vd = cfg.vd > 0 ? cfg.vd : g->vd;
+  out->omega = omega_host(lambda, delta, out->vd);
+  const double cap_d = std::ceil(out->omega);
+  if (!(cap_d >= 1.0 && cap_d < 1e15)) return finish(fail(KADABRA_ERR_ARG, "omega out of range"));
+  out->omega_cap = (uint64_t)cap_d;
+  uint64_t alpha = (uint64_t)std::floor(out->omega / 100.0);
+  if (alpha < 1) alpha = 1;
+  out->alpha = alpha;
+  const uint64_t K = cfg.check_interval;
+
+  kadabra_status rc = ensure_workspace(g, std::max<uint64_t>(alpha, std::min<uint64_t>(K, out->omega_cap)));
+  if (rc != KADABRA_OK) return finish(rc);
+  SampleParams P = base_params(g);
+  P.seed = seed;
+  P.totals = g->totals;
+#define RUN_CK(call)                                                                     \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) return finish(fail(KADABRA_ERR_CUDA, cudaGetErrorString(e_))); \
+  } while (0)
+  RUN_CK(cudaMemsetAsync(g->totals, 0, sizeof(long long) * KADABRA_NSTAT, st));
+  RUN_CK(cudaMemsetAsync(g->count0, 0, sizeof(uint32_t) * n, st));
+  RUN_CK(cudaMemsetAsync(g->counts, 0, sizeof(uint32_t) * n, st));
+
+  // warm-up (Alg. 2 lines 1-5): alpha samples in RNG domain 1
+  P.domain = 1;
+  P.first_idx = 0;
+  P.count = alpha;
+  P.counts = g->count0;
+  if ((rc = launch_sampler(g, P, st)) != KADABRA_OK) return finish(rc);
+  std::vector<uint32_t> c0((size_t)n);
+  RUN_CK(cudaMemcpyAsync(c0.data(), g->count0, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, st));
+  if ((rc = read_status(g, st)) != KADABRA_OK) return finish(rc);
+
+  // computeDelta (Alg. 2 lines 6-14)
+  std::vector<double> hL((size_t)n), hU((size_t)n);
+  if ((rc = compute_delta_host(n, c0.data(), alpha, out->omega, lambda, delta, cfg.eps, hL.data(), hU.data(),
+                               &out->C)) != KADABRA_OK)
+    return finish(rc);
+  RUN_CK(cudaMemcpyAsync(g->lnL, hL.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  RUN_CK(cudaMemcpyAsync(g->lnU, hU.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
+
+  // main loop (Alg. 1): batches of K samples in domain 0, stop test after each
+  const int check_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(4 * (int64_t)g->num_sms, (n + 255) / 256));
+  uint64_t tau = 0;
+  const uint64_t cap = out->omega_cap;
+  CheckOut h;
+  P.domain = 0;
+  P.counts = g->counts;
+  for (;;) {
+    const uint64_t B = std::min<uint64_t>(K, cap - tau);
+    P.first_idx = tau;
+    P.count = B;
+    if ((rc = launch_sampler(g, P, st)) != KADABRA_OK) return finish(rc);
+    tau += B;
+    if (tau >= cap) break;
+    out->checks++;
+    RUN_CK(cudaMemsetAsync(g->chk, 0, sizeof(CheckOut), st));
+    k_check<<<check_blocks, 256, 0, st>>>(g->counts, g->lnL, g->lnU, n, tau, out->omega, lambda, g->chk);
+    RUN_CK(cudaGetLastError());
+    RUN_CK(cudaMemcpyAsync(&h, g->chk, sizeof(CheckOut), cudaMemcpyDeviceToHost, st));
+    if ((rc = read_status(g, st)) != KADABRA_OK) return finish(rc);
+    if (!h.fail) {
+      out->stopped_early = 1;
+      break;
+    }
+  }
+  out->tau = tau;
+  // f and g maxima at the final tau; b~ = counts / tau (Alg. 1 last line)
+  RUN_CK(cudaMemsetAsync(g->chk, 0, sizeof(CheckOut), st));
+  k_check<<<check_blocks, 256, 0, st>>>(g->counts, g->lnL, g->lnU, n, tau, out->omega, lambda, g->chk);
+  RUN_CK(cudaGetLastError());
+  RUN_CK(cudaMemcpyAsync(&h, g->chk, sizeof(CheckOut), cudaMemcpyDeviceToHost, st));
+  const int bt_blocks = check_blocks;
+  if (btilde_host || btilde_dev) {
+    k_btilde<<<bt_blocks, 256, 0, st>>>(g->counts, n, tau, btilde_dev ? btilde_dev : g->btilde);
+    RUN_CK(cudaGetLastError());
+  }
+  if (counts_dev)
+    RUN_CK(cudaMemcpyAsync(counts_dev, g->counts, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st));
+  if (counts_host)
+    RUN_CK(cudaMemcpyAsync(counts_host, g->counts, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, st));
+  if (btilde_host)
+    RUN_CK(cudaMemcpyAsync(btilde_host, btilde_dev ? btilde_dev : g->btilde, sizeof(double) * n,
+                           cudaMemcpyDeviceToHost, st));
+  long long tot[KADABRA_NSTAT];
+  RUN_CK(cudaMemcpyAsync(tot, g->totals, sizeof(tot), cudaMemcpyDeviceToHost, st));
+  if ((rc = read_status(g, st)) != KADABRA_OK) return finish(rc);
+  std::memcpy(&out->max_f, &h.max_f_bits, sizeof(double));
+  std::memcpy(&out->max_g, &h.max_g_bits, sizeof(double));
+  for (int q = 0; q < KADABRA_NSTAT; ++q) out->totals[q] = tot[q];
+#undef RUN_CK
+  return finish(KADABRA_OK);
+}
+
+}  // extern "C"

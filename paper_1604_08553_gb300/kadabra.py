@@ -1,0 +1,296 @@
+"""Thin Python binding of ``libkadabra.so`` (the C ABI in include/kadabra.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels (or, for computeDelta and omega, in the library's own host
+code).  There is no CPU fallback: if the library cannot be loaded, every call
+raises.  PyTorch is used only for device memory and streams (tensors whose
+pointers are passed to the ``*_device`` / ``d_*`` arguments, and
+``torch.cuda.current_stream()``).
+
+Function names mirror the C ABI.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+from . import _build
+
+_lock = threading.Lock()
+_lib = None
+
+OK = 0
+ERR_ARG = 1
+ERR_CSR = 2
+ERR_OOM = 3
+ERR_SIGMA_OVERFLOW = 4
+ERR_CAPACITY = 5
+ERR_TIMEOUT = 6
+ERR_CUDA = 7
+ERR_UNSUPPORTED = 8
+ERR_INTERNAL = 9
+
+STAT_NAMES = (
+    "edges", "expanded", "new", "sigma_adds", "pi", "levels",
+    "bt_scanned", "path_nodes", "sigma_lo", "sigma_hi", "dist",
+)
+NSTAT = len(STAT_NAMES)
+
+
+class KadabraError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"kadabra status {status}: {msg}")
+        self.status = status
+
+
+class kadabra_config(C.Structure):
+    _fields_ = [
+        ("vd", C.c_int64), ("eps", C.c_double), ("check_interval", C.c_uint64),
+        ("stream", C.c_void_p), ("ctas_per_sm", C.c_int32), ("reserved", C.c_int32 * 7),
+    ]
+
+
+class kadabra_result(C.Structure):
+    _fields_ = [
+        ("tau", C.c_uint64), ("omega_cap", C.c_uint64), ("alpha", C.c_uint64), ("checks", C.c_uint64),
+        ("vd", C.c_int64), ("omega", C.c_double), ("C", C.c_double), ("max_f", C.c_double),
+        ("max_g", C.c_double), ("totals", C.c_int64 * NSTAT), ("stopped_early", C.c_int32),
+        ("status", C.c_int32), ("counts", C.c_void_p), ("btilde", C.c_void_p), ("d_counts", C.c_void_p),
+        ("d_btilde", C.c_void_p), ("topk", C.c_void_p),
+    ]
+
+
+def load_library():
+    """Builds (if needed) and loads libkadabra.so; raises if that fails."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build_kadabra()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libkadabra.so missing at {path}")
+        lib = C.CDLL(path)
+        p = C.c_void_p
+        i32, i64, u32, u64, dbl = C.c_int32, C.c_int64, C.c_uint32, C.c_uint64, C.c_double
+        st = C.c_int
+        lib.kadabra_last_error.restype = C.c_char_p
+        lib.kadabra_config_default.argtypes = [C.POINTER(kadabra_config)]
+        lib.kadabra_omega.argtypes = [dbl, dbl, i64]
+        lib.kadabra_omega.restype = dbl
+        lib.kadabra_load_csr.argtypes = [i32, i64, p, p, C.c_int, p, p, C.POINTER(C.c_void_p)]
+        lib.kadabra_load_csr.restype = st
+        lib.kadabra_load_csr_device.argtypes = [i32, i64, p, p, C.c_int, p, p, C.POINTER(C.c_void_p)]
+        lib.kadabra_load_csr_device.restype = st
+        lib.kadabra_free_graph.argtypes = [p]
+        lib.kadabra_graph_info.argtypes = [p, C.POINTER(i32), C.POINTER(i64), C.POINTER(C.c_int), C.POINTER(i64)]
+        lib.kadabra_graph_info.restype = st
+        lib.kadabra_run.argtypes = [p, dbl, dbl, i32, u64, C.POINTER(kadabra_config), C.POINTER(kadabra_result)]
+        lib.kadabra_run.restype = st
+        lib.kadabra_sample_batch.argtypes = [p, u64, u32, u64, u64, p, p, p]
+        lib.kadabra_sample_batch.restype = st
+        lib.kadabra_sync_status.argtypes = [p, p]
+        lib.kadabra_sync_status.restype = st
+        lib.kadabra_sample_paths.argtypes = [p, u64, u32, u64, u32, p, p, p, i32, p, p]
+        lib.kadabra_sample_paths.restype = st
+        lib.kadabra_philox.argtypes = [u64, u32, u32, u64, u32, p]
+        lib.kadabra_philox.restype = st
+        lib.kadabra_check.argtypes = [i64, p, u64, dbl, p, p, dbl, C.POINTER(dbl), C.POINTER(dbl),
+                                      C.POINTER(C.c_int)]
+        lib.kadabra_check.restype = st
+        lib.kadabra_compute_delta.argtypes = [i64, p, u64, dbl, dbl, dbl, dbl, p, p, C.POINTER(dbl)]
+        lib.kadabra_compute_delta.restype = st
+        _lib = lib
+        return lib
+
+
+def _raise(status: int):
+    if status != OK:
+        msg = load_library().kadabra_last_error().decode(errors="replace")
+        raise KadabraError(status, msg)
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def config_default() -> kadabra_config:
+    cfg = kadabra_config()
+    load_library().kadabra_config_default(C.byref(cfg))
+    return cfg
+
+
+def kadabra_omega(lam: float, delta: float, vd: int) -> float:
+    return float(load_library().kadabra_omega(lam, delta, vd))
+
+
+class Graph:
+    """Owns a kadabra_graph handle (device-resident CSR + sampler workspace)."""
+
+    def __init__(self, handle: int, n: int, m: int, directed: bool, keepalive=None):
+        self.handle = C.c_void_p(handle)
+        self.n, self.m, self.directed = n, m, directed
+        self._keepalive = keepalive
+
+    @property
+    def vd(self) -> int:
+        vd = C.c_int64()
+        _raise(load_library().kadabra_graph_info(self.handle, None, None, None, C.byref(vd)))
+        return vd.value
+
+    def free(self):
+        if self.handle:
+            load_library().kadabra_free_graph(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def kadabra_load_csr(g) -> Graph:
+    """Copies a host CSR (an object with n, row_ptr, col, directed, rrow_ptr, rcol) to the device."""
+    lib = load_library()
+    rp = np.ascontiguousarray(g.row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(g.col, dtype=np.int32)
+    rrp = np.ascontiguousarray(g.rrow_ptr, dtype=np.int32) if g.directed else None
+    rci = np.ascontiguousarray(g.rcol, dtype=np.int32) if g.directed else None
+    h = C.c_void_p()
+    _raise(lib.kadabra_load_csr(int(g.n), int(ci.shape[0]), _ptr(rp), _ptr(ci), int(bool(g.directed)),
+                                _ptr(rrp), _ptr(rci), C.byref(h)))
+    return Graph(h.value, int(g.n), int(ci.shape[0]), bool(g.directed))
+
+
+def kadabra_load_csr_device(n: int, row_ptr, col, directed: bool = False, rrow_ptr=None, rcol=None) -> Graph:
+    """Wraps int32 CUDA tensors (not copied; kept alive by the returned Graph)."""
+    lib = load_library()
+    ptr = lambda t: None if t is None else C.c_void_p(t.data_ptr())
+    h = C.c_void_p()
+    _raise(lib.kadabra_load_csr_device(int(n), int(col.numel()), ptr(row_ptr), ptr(col), int(bool(directed)),
+                                       ptr(rrow_ptr), ptr(rcol), C.byref(h)))
+    return Graph(h.value, int(n), int(col.numel()), bool(directed), keepalive=(row_ptr, col, rrow_ptr, rcol))
+
+
+@dataclass
+class RunResult:
+    tau: int
+    omega_cap: int
+    alpha: int
+    checks: int
+    vd: int
+    omega: float
+    C: float
+    max_f: float
+    max_g: float
+    totals: np.ndarray
+    stopped_early: bool
+    counts: Optional[np.ndarray]
+    btilde: Optional[np.ndarray]
+
+
+def kadabra_run(g: Graph, lam: float, delta: float, k: int = 0, seed: int = 0, *, vd: int = 0,
+                eps: float = 0.001, check_interval: int = 1000, stream: Optional[int] = None,
+                counts: Optional[np.ndarray] = None, btilde: Optional[np.ndarray] = None,
+                d_counts=None, d_btilde=None, want_host: bool = True) -> RunResult:
+    """Runs KADABRA (all-nodes mode).  Host outputs are numpy arrays (allocated
+    here unless given); device outputs are optional CUDA tensors."""
+    lib = load_library()
+    cfg = config_default()
+    cfg.vd = vd
+    cfg.eps = eps
+    cfg.check_interval = check_interval
+    cfg.stream = stream
+    res = kadabra_result()
+    if want_host:
+        if counts is None:
+            counts = np.zeros(g.n, dtype=np.uint32)
+        if btilde is None:
+            btilde = np.zeros(g.n, dtype=np.float64)
+        res.counts = counts.ctypes.data
+        res.btilde = btilde.ctypes.data
+    if d_counts is not None:
+        res.d_counts = d_counts.data_ptr()
+    if d_btilde is not None:
+        res.d_btilde = d_btilde.data_ptr()
+    _raise(lib.kadabra_run(g.handle, lam, delta, k, seed, C.byref(cfg), C.byref(res)))
+    return RunResult(res.tau, res.omega_cap, res.alpha, res.checks, res.vd, res.omega, res.C, res.max_f,
+                     res.max_g, np.array(res.totals[:], dtype=np.int64), bool(res.stopped_early),
+                     counts if want_host else None, btilde if want_host else None)
+
+
+def kadabra_sample_batch(g: Graph, seed: int, domain: int, first_idx: int, count: int, d_counts,
+                         d_totals=None, stream: Optional[int] = None) -> None:
+    """Enqueues one sampler batch; d_counts (uint32/int32, n) and d_totals (int64, NSTAT) are CUDA tensors."""
+    lib = load_library()
+    _raise(lib.kadabra_sample_batch(g.handle, seed, domain, first_idx, count, C.c_void_p(d_counts.data_ptr()),
+                                    None if d_totals is None else C.c_void_p(d_totals.data_ptr()), stream))
+
+
+def kadabra_sync_status(g: Graph, stream: Optional[int] = None) -> None:
+    _raise(load_library().kadabra_sync_status(g.handle, stream))
+
+
+@dataclass
+class Samples:
+    st: np.ndarray
+    path_len: np.ndarray
+    paths: np.ndarray
+    stats: np.ndarray
+    status: np.ndarray
+
+    def stat(self, name: str) -> np.ndarray:
+        return self.stats[:, STAT_NAMES.index(name)]
+
+
+def kadabra_sample_paths(g: Graph, seed: int, domain: int, first_idx: int, count: int,
+                         max_len: int = 64, raise_on_error: bool = True):
+    """Per-sample (s,t), paths, work counters and status.  With
+    raise_on_error=False returns (Samples, status) instead of raising."""
+    lib = load_library()
+    st = np.zeros((count, 2), dtype=np.int32)
+    pl = np.zeros(count, dtype=np.int32)
+    paths = np.full((count, max_len), -1, dtype=np.int32)
+    stats = np.zeros((count, NSTAT), dtype=np.int64)
+    status = np.zeros(count, dtype=np.int32)
+    rc = lib.kadabra_sample_paths(g.handle, seed, domain, first_idx, count, _ptr(st), _ptr(pl), _ptr(paths),
+                                  max_len, _ptr(stats), _ptr(status))
+    smp = Samples(st, pl, paths, stats, status)
+    if not raise_on_error:
+        return smp, rc
+    _raise(rc)
+    return smp
+
+
+def kadabra_philox(seed: int, domain: int, j: int, first_idx: int, count: int) -> np.ndarray:
+    out = np.zeros((count, 4), dtype=np.uint32)
+    _raise(load_library().kadabra_philox(seed, domain, j, first_idx, count, _ptr(out)))
+    return out
+
+
+def kadabra_check(counts: np.ndarray, tau: int, omega: float, ln_inv_dl: np.ndarray, ln_inv_du: np.ndarray,
+                  lam: float):
+    c = np.ascontiguousarray(counts, dtype=np.uint32)
+    L = np.ascontiguousarray(ln_inv_dl, dtype=np.float64)
+    U = np.ascontiguousarray(ln_inv_du, dtype=np.float64)
+    mf, mg, stop = C.c_double(), C.c_double(), C.c_int()
+    _raise(load_library().kadabra_check(c.shape[0], _ptr(c), tau, omega, _ptr(L), _ptr(U), lam, C.byref(mf),
+                                        C.byref(mg), C.byref(stop)))
+    return bool(stop.value), mf.value, mg.value
+
+
+def kadabra_compute_delta(count0: np.ndarray, alpha: int, omega: float, lam: float, delta: float, eps: float):
+    c0 = np.ascontiguousarray(count0, dtype=np.uint32)
+    n = c0.shape[0]
+    dl = np.zeros(n, dtype=np.float64)
+    du = np.zeros(n, dtype=np.float64)
+    Cv = C.c_double()
+    _raise(load_library().kadabra_compute_delta(n, _ptr(c0), alpha, omega, lam, delta, eps, _ptr(dl), _ptr(du),
+                                                C.byref(Cv)))
+    return Cv.value, dl, du
