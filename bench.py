@@ -179,6 +179,27 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def sampler_only(kd, G, g, launches):
+    """Times `launches` sampler batches of K main-loop samples (the dominant kernel)."""
+    import torch
+    K = WORKLOAD["check_interval"]
+    d_counts = torch.zeros(g.n, dtype=torch.int32, device="cuda")
+    d_tot = torch.zeros(kd.NSTAT, dtype=torch.int64, device="cuda")
+    out = []
+    for i in range(launches):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        kd.kadabra_sample_batch(G, 1, 0, i * K, K, d_counts, d_tot)
+        ev1.record()
+        ev1.synchronize()
+        kd.kadabra_sync_status(G)
+        out.append(ev0.elapsed_time(ev1))
+    tot = d_tot.cpu().numpy()
+    print(json.dumps({"sampler_ms": out, "samples": K * launches, "edges": int(tot[0]),
+                      "bt_scanned": int(tot[6]), "workload": workload_config(g)["workload"]}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -186,6 +207,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sampler-only", type=int, default=0, metavar="LAUNCHES",
+                    help="only time LAUNCHES sampler batches of K samples (for profilers)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -214,6 +237,10 @@ def main():
     g = make_graph()
     w = WORKLOAD
     G = kd.kadabra_load_csr(g)
+    if args.sampler_only:
+        sampler_only(kd, G, g, args.sampler_only)
+        G.free()
+        return
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
     d_counts = torch.zeros(g.n, dtype=torch.int32, device="cuda")

@@ -127,6 +127,14 @@ void kadabra_free_graph(kadabra_graph* g);
 
 kadabra_status kadabra_graph_info(const kadabra_graph* g, int32_t* n, int64_t* m, int* directed, int64_t* vd);
 
+/* Graph flags.  KADABRA_FLAG_GLOBAL_TABLES runs every sample on the
+ * global-memory tables instead of first trying shared memory (the results
+ * are identical; this exists to test that path and for graphs whose
+ * searches are known to be deep or wide).  Returns KADABRA_ERR_ARG for
+ * unknown bits. */
+enum { KADABRA_FLAG_GLOBAL_TABLES = 1 };
+kadabra_status kadabra_graph_set_flags(kadabra_graph* g, uint32_t flags);
+
 /* KADABRA, all-nodes mode (Alg. 1 with Alg. 2 and the rule f,g <= lambda
  * for every node): warm-up, computeDelta, then sample batches of K with a
  * stop test after each, until the test holds or ceil(omega) samples.

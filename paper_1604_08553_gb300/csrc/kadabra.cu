@@ -48,16 +48,18 @@
 namespace {
 
 // ============================================================== constants
-constexpr int NT = 128;            // threads per sampler CTA
+constexpr int NT = 256;            // threads per sampler CTA
 constexpr int NW = NT / 32;        // warps per sampler CTA
-constexpr int MAXD = 126;          // deepest level per side (7-bit field, 127 reserved)
+constexpr int U = 4;               // independent items per thread per step (memory-level parallelism)
 constexpr int FAST_HLOG = 12;      // shared-memory hash: 4096 slots
 constexpr int FAST_LCAP = 2048;    // shared-memory level lists: 2048 nodes
+constexpr int FAST_MAXD = 254;     // levels per side with shared-memory tables
+constexpr int GM_MAXD = 65534;     // levels per side with global-memory tables
 constexpr int FAST_PCAP = 2048;    // candidate edges per warp (global memory)
 constexpr unsigned long long EMPTY = ~0ull;
 constexpr uint32_t NONE = 0xFFFFFFFFu;
-constexpr uint32_t SLOT_MASK = 0x00FFFFFFu;
-constexpr uint32_t SLOT_PENDING = 0x00FFFFFFu;
+constexpr uint32_t SLOT_MASK = 0x7FFFFFFFu;
+constexpr uint32_t SLOT_PENDING = 0x7FFFFFFFu;
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
 // sample flags
@@ -105,23 +107,30 @@ struct PiEntry {
   unsigned long long w;  // sigma_x * sigma_y (exact; overflow flagged)
 };
 
+// Per-sample state.  The hash maps a visited node to (side, list slot); the
+// lists hold one level after another, each sorted by node id, with sigma;
+// lvl holds each side's level bounds in the lists.
 struct Tables {
-  unsigned long long* hkv;  // (node << 32) | (side << 31 | dist << 24 | slot)
+  unsigned long long* hkv;  // (node << 32) | (side << 31 | slot), EMPTY = free
   uint32_t hmask;
   int hlog;
   int32_t* lnode;           // level lists: node ids
   unsigned long long* lsig; // level lists: sigma
-  int32_t* pre;             // frontier degree prefix / scratch (lcap+1)
+  int2* pr;                 // frontier: {degree prefix, row start}; lcap+1 entries
   int lcap;
+  int* lvl;                 // [side][lo|hi][maxd+2]
+  int maxd;
   PiEntry* pi;              // NW segments of pcap entries
   int pcap;
 };
 
-__device__ __forceinline__ uint32_t pack_val(int side, int dist, uint32_t slot) {
-  return ((uint32_t)side << 31) | ((uint32_t)dist << 24) | slot;
+__device__ __forceinline__ int& lvl_lo(const Tables& T, int side, int d) { return T.lvl[(2 * side) * (T.maxd + 2) + d]; }
+__device__ __forceinline__ int& lvl_hi(const Tables& T, int side, int d) {
+  return T.lvl[(2 * side + 1) * (T.maxd + 2) + d];
 }
+
+__device__ __forceinline__ uint32_t pack_val(int side, uint32_t slot) { return ((uint32_t)side << 31) | slot; }
 __device__ __forceinline__ int val_side(uint32_t v) { return (int)(v >> 31); }
-__device__ __forceinline__ int val_dist(uint32_t v) { return (int)((v >> 24) & 0x7F); }
 __device__ __forceinline__ uint32_t val_slot(uint32_t v) { return v & SLOT_MASK; }
 
 __device__ __forceinline__ uint32_t hash_pos(int32_t v, int hlog) {
@@ -192,6 +201,7 @@ struct SampleParams {
   uint64_t deferred_cap;
   int32_t* status;                  // run-wide error word (kadabra_status values)
   long long* totals;                // KADABRA_NSTAT or null
+  int force_global;                 // defer every sample to the global-memory tables
   // per-sample outputs (test hook) or null
   int32_t* st_out;
   int32_t* path_len;
@@ -210,13 +220,12 @@ struct SampleParams {
 
 // per-CTA control block in shared memory
 struct Ctl {
-  int lo[2][MAXD + 2];
-  int hi[2][MAXD + 2];
   long long cost[2];
   long long stat[KADABRA_NSTAT];
   long long tot[KADABRA_NSTAT];
   unsigned long long wsum[NW];
   unsigned long long wsum_hi[NW];
+  unsigned long long u64tmp[NW];
   unsigned long long r;
   unsigned long long sel_off;
   int depth[2];
@@ -231,8 +240,9 @@ struct Ctl {
   int done;       // 0 = continue, 1 = touch, 2 = disconnected
   int sel_warp;
   int pick, pick_pos;
+  int mode;       // backtracking: 0 = scan the row of x, 1 = scan the previous level
+  int next_x;     // backtracking: the node picked at this step
   int cv, cw;     // chosen candidate edge (v on the s side, w on the t side)
-  int path_nodes;
   int list_before;
   unsigned long long cur;
   unsigned long long ntotal;
@@ -265,6 +275,30 @@ __device__ __forceinline__ int block_exscan(int x, int* tmp, int* total) {
   return wpre + v - x;
 }
 
+// inclusive scan of one u64 per thread; *total gets the block sum
+__device__ __forceinline__ unsigned long long block_inscan_u64(unsigned long long x, unsigned long long* tmp,
+                                                               unsigned long long* total) {
+  const int lane = lane_id(), w = warp_id();
+  unsigned long long v = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(FULL, v, o);
+    if (lane >= o) v += y;
+  }
+  if (lane == 31) tmp[w] = v;
+  __syncthreads();
+  unsigned long long wpre = 0, tot = 0;
+#pragma unroll
+  for (int i = 0; i < NW; ++i) {
+    const unsigned long long t = tmp[i];
+    if (i < w) wpre += t;
+    tot += t;
+  }
+  __syncthreads();
+  *total = tot;
+  return wpre + v;
+}
+
 __device__ __forceinline__ long long block_sum64(long long x, long long* tmp) {
   const int lane = lane_id(), w = warp_id();
 #pragma unroll
@@ -288,12 +322,12 @@ __device__ __forceinline__ unsigned long long warp_incl_scan_u64(unsigned long l
   return v;
 }
 
-// largest p in [0, cnt) with pre[p] <= e (pre non-decreasing, pre[0] = 0)
-__device__ __forceinline__ int frontier_pos(const int32_t* pre, int cnt, int e) {
+// largest p in [0, cnt) with pr[p].x <= e (prefixes non-decreasing, pr[0].x = 0)
+__device__ __forceinline__ int frontier_pos(const int2* pr, int cnt, int e) {
   int lo = 0, hi = cnt;
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
-    if (pre[mid] <= e)
+    if (pr[mid].x <= e)
       lo = mid;
     else
       hi = mid;
@@ -301,9 +335,58 @@ __device__ __forceinline__ int frontier_pos(const int32_t* pre, int cnt, int e) 
   return lo;
 }
 
+// first position of y in the sorted row col[a, b) (b if absent)
+__device__ __forceinline__ int lower_bound_row(const int32_t* col, int a, int b, int32_t y) {
+  while (a < b) {
+    const int mid = (a + b) >> 1;
+    if (__ldg(&col[mid]) < y)
+      a = mid + 1;
+    else
+      b = mid;
+  }
+  return a;
+}
+
+// Weighted choice over items 0..N-1 in order: the first item whose inclusive
+// prefix sum of weights exceeds r (r < total weight).  Each thread weighs U
+// consecutive items per step so their memory accesses overlap.  Returns the
+// item index (all threads), or -1 if r is not below the total.
+template <class WF>
+__device__ __forceinline__ int block_pick(int N, unsigned long long r, Ctl& c, WF wf) {
+  const int tid = threadIdx.x;
+  if (tid == 0) c.pick = -1;
+  __syncthreads();
+  unsigned long long carry = 0;
+  for (int base = 0; base < N; base += NT * U) {
+    unsigned long long w[U];
+    unsigned long long tsum = 0;
+    wf(base + tid * U, N, w);
+#pragma unroll
+    for (int k = 0; k < U; ++k) tsum += w[k];
+    unsigned long long tot;
+    const unsigned long long incl = block_inscan_u64(tsum, c.u64tmp, &tot);
+    const unsigned long long excl = incl - tsum;
+    if (tsum != 0 && carry + excl <= r && r < carry + incl) {
+      unsigned long long acc = carry + excl;
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        acc += w[k];
+        if (acc > r) {
+          c.pick = base + tid * U + k;
+          break;
+        }
+      }
+    }
+    carry += tot;
+    if (carry > r) break;
+  }
+  __syncthreads();
+  return c.pick;
+}
+
 // ============================================================== one sample
-// All threads of the CTA call this with the same idx.  Returns with the
-// tables clean.  Flags in c.flags tell the caller what happened.
+// All threads of the CTA call this with the same idx.  Flags in c.flags tell
+// the caller what happened; the caller resets the tables afterwards.
 template <bool GM>
 __device__ void run_sample(const SampleParams& P, const Tables& T, Ctl& c, uint64_t idx, int64_t out_i) {
   const int tid = threadIdx.x, lane = lane_id(), wid = warp_id();
@@ -320,35 +403,36 @@ __device__ void run_sample(const SampleParams& P, const Tables& T, Ctl& c, uint6
     c.t = t;
     for (int k = 0; k < KADABRA_NSTAT; ++k) c.stat[k] = 0;
     c.stat[KADABRA_STAT_DIST] = -1;
-    c.flags = 0;
+    c.flags = (!GM && P.force_global) ? F_CAP : 0;
     c.done = 0;
     uint32_t pos;
-    if (tab_insert(T, s, pack_val(0, 0, 0), &pos) != 1) c.flags |= F_INTERNAL;
-    if (tab_insert(T, t, pack_val(1, 0, 1), &pos) != 1) c.flags |= F_INTERNAL;
+    if (tab_insert(T, s, pack_val(0, 0), &pos) != 1) c.flags |= F_INTERNAL;
+    if (tab_insert(T, t, pack_val(1, 1), &pos) != 1) c.flags |= F_INTERNAL;
     T.lnode[0] = s;
     T.lsig[0] = 1ull;
     T.lnode[1] = t;
     T.lsig[1] = 1ull;
     c.nlist = 2;
-    c.lo[0][0] = 0;
-    c.hi[0][0] = 1;
-    c.lo[1][0] = 1;
-    c.hi[1][0] = 2;
+    lvl_lo(T, 0, 0) = 0;
+    lvl_hi(T, 0, 0) = 1;
+    lvl_lo(T, 1, 0) = 1;
+    lvl_hi(T, 1, 0) = 2;
     c.depth[0] = 0;
     c.depth[1] = 0;
     c.cost[0] = G.rp[s + 1] - G.rp[s];
     c.cost[1] = G.rrp[t + 1] - G.rrp[t];
   }
   __syncthreads();
+  if (c.flags) return;
 
   // ------------------------------------------------ bb-BFS (Sec. 4)
-  for (int iter = 0; iter < 2 * (MAXD + 1); ++iter) {
+  for (int iter = 0; iter <= 2 * T.maxd + 2; ++iter) {
     if (tid == 0) {
       const int side = c.cost[0] <= c.cost[1] ? 0 : 1;
       const int d = c.depth[side];
       c.side = side;
-      c.f0 = c.lo[side][d];
-      c.fcount = c.hi[side][d] - c.lo[side][d];
+      c.f0 = lvl_lo(T, side, d);
+      c.fcount = lvl_hi(T, side, d) - lvl_lo(T, side, d);
       c.stat[KADABRA_STAT_LEVELS] += 1;
       c.stat[KADABRA_STAT_EXPANDED] += c.fcount;
       c.list_before = c.nlist;
@@ -359,23 +443,24 @@ __device__ void run_sample(const SampleParams& P, const Tables& T, Ctl& c, uint6
     const int32_t* rowp = side == 0 ? G.rp : G.rrp;
     const int32_t* cols = side == 0 ? G.ci : G.rci;
 
-    // degree prefix over the (sorted) frontier
+    // degree prefix and row starts over the (sorted) frontier
     {
       int carry = 0;
       for (int base = 0; base < fcount; base += NT) {
         const int i = base + tid;
-        int deg = 0;
+        int deg = 0, rs = 0;
         if (i < fcount) {
           const int x = T.lnode[f0 + i];
-          deg = rowp[x + 1] - rowp[x];
+          rs = __ldg(&rowp[x]);
+          deg = __ldg(&rowp[x + 1]) - rs;
         }
         int tot;
         const int ex = block_exscan(deg, c.scan_tmp, &tot);
-        if (i < fcount) T.pre[i] = carry + ex;
+        if (i < fcount) T.pr[i] = make_int2(carry + ex, rs);
         carry += tot;
       }
       if (tid == 0) {
-        T.pre[fcount] = carry;
+        T.pr[fcount] = make_int2(carry, 0);
         c.ecount = carry;
         c.stat[KADABRA_STAT_EDGES] += carry;
       }
@@ -390,34 +475,45 @@ __device__ void run_sample(const SampleParams& P, const Tables& T, Ctl& c, uint6
       int npi = 0;
       bool sigma_of = false;
       PiEntry* seg = T.pi + (size_t)wid * T.pcap;
-      for (int base = c0; base < c1; base += 32) {
-        const int e = base + lane;
-        bool touch = false;
-        int x = 0, y = 0;
-        unsigned long long wgt = 0;
-        if (e < c1) {
-          const int p = frontier_pos(T.pre, fcount, e);
-          x = T.lnode[f0 + p];
-          y = __ldg(&cols[__ldg(&rowp[x]) + (e - T.pre[p])]);
-          const uint32_t v = tab_find(T, y);
-          if (v != NONE && val_side(v) != side) {
-            touch = true;
-            const unsigned long long sx = T.lsig[f0 + p];
-            const unsigned long long sy = T.lsig[val_slot(v)];
-            wgt = sx * sy;
-            if (__umul64hi(sx, sy) != 0ull) sigma_of = true;
+      for (int base = c0; base < c1; base += 32 * U) {
+        int xs[U], ys[U], ps[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+          const int e = base + 32 * k + lane;
+          xs[k] = -1;
+          if (e < c1) {
+            const int p = frontier_pos(T.pr, fcount, e);
+            const int2 q = T.pr[p];
+            ps[k] = p;
+            xs[k] = T.lnode[f0 + p];
+            ys[k] = __ldg(&cols[q.y + (e - q.x)]);
           }
         }
-        const unsigned m = __ballot_sync(FULL, touch);
-        if (touch) {
-          const int pos = npi + __popc(m & ((1u << lane) - 1u));
-          if (pos < T.pcap) {
-            seg[pos].x = x;
-            seg[pos].y = y;
-            seg[pos].w = wgt;
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+          bool touch = false;
+          unsigned long long wgt = 0;
+          if (xs[k] >= 0) {
+            const uint32_t v = tab_find(T, ys[k]);
+            if (v != NONE && val_side(v) != side) {
+              touch = true;
+              const unsigned long long sx = T.lsig[f0 + ps[k]];
+              const unsigned long long sy = T.lsig[val_slot(v)];
+              wgt = sx * sy;
+              if (__umul64hi(sx, sy) != 0ull) sigma_of = true;
+            }
           }
+          const unsigned m = __ballot_sync(FULL, touch);
+          if (touch) {
+            const int pos = npi + __popc(m & ((1u << lane) - 1u));
+            if (pos < T.pcap) {
+              seg[pos].x = xs[k];
+              seg[pos].y = ys[k];
+              seg[pos].w = wgt;
+            }
+          }
+          npi += __popc(m);
         }
-        npi += __popc(m);
       }
       if (__any_sync(FULL, sigma_of) && lane == 0) atomicOr(&c.flags, F_SIGMA);
       if (lane == 0) {
@@ -440,24 +536,24 @@ __device__ void run_sample(const SampleParams& P, const Tables& T, Ctl& c, uint6
 
     // pass 2: insert the nodes of the next level
     const int dnew = c.depth[side] + 1;
-    if (dnew > MAXD) {
+    if (dnew > T.maxd) {
       if (tid == 0) c.flags |= F_CAP;
       __syncthreads();
       return;
     }
     const int list_before = c.list_before;
     for (int e = tid; e < E; e += NT) {
-      const int p = frontier_pos(T.pre, fcount, e);
-      const int x = T.lnode[f0 + p];
-      const int y = __ldg(&cols[__ldg(&rowp[x]) + (e - T.pre[p])]);
+      const int p = frontier_pos(T.pr, fcount, e);
+      const int2 q = T.pr[p];
+      const int y = __ldg(&cols[q.y + (e - q.x)]);
       uint32_t pos;
-      const int r = tab_insert(T, y, pack_val(side, dnew, SLOT_PENDING), &pos);
+      const int r = tab_insert(T, y, pack_val(side, SLOT_PENDING), &pos);
       if (r == 1) {
         const int slot = atomicAdd(&c.nlist, 1);
         if (slot < T.lcap) {
           T.lnode[slot] = y;
           T.lsig[slot] = 0ull;
-          T.hkv[pos] = ((unsigned long long)(uint32_t)y << 32) | pack_val(side, dnew, (uint32_t)slot);
+          T.hkv[pos] = ((unsigned long long)(uint32_t)y << 32) | pack_val(side, (uint32_t)slot);
         } else {
           atomicOr(&c.flags, F_CAP);
         }
@@ -473,11 +569,11 @@ __device__ void run_sample(const SampleParams& P, const Tables& T, Ctl& c, uint6
     {
       bool of = false;
       for (int e = tid; e < E; e += NT) {
-        const int p = frontier_pos(T.pre, fcount, e);
-        const int x = T.lnode[f0 + p];
-        const int y = __ldg(&cols[__ldg(&rowp[x]) + (e - T.pre[p])]);
+        const int p = frontier_pos(T.pr, fcount, e);
+        const int2 q = T.pr[p];
+        const int y = __ldg(&cols[q.y + (e - q.x)]);
         const uint32_t v = tab_find(T, y);
-        if (v != NONE && val_side(v) == side && val_dist(v) == dnew) {
+        if (v != NONE && val_side(v) == side && (int)val_slot(v) >= list_before) {
           const unsigned long long add = T.lsig[f0 + p];
           const unsigned long long old = atomicAdd(&T.lsig[val_slot(v)], add);
           if (old + add < old) of = true;
@@ -533,14 +629,14 @@ __device__ void run_sample(const SampleParams& P, const Tables& T, Ctl& c, uint6
       if (pos < 0) {
         atomicOr(&c.flags, F_INTERNAL);
       } else {
-        T.hkv[pos] = ((unsigned long long)(uint32_t)y << 32) | pack_val(side, dnew, (uint32_t)(nb + i));
+        T.hkv[pos] = ((unsigned long long)(uint32_t)y << 32) | pack_val(side, (uint32_t)(nb + i));
       }
-      cost += rowp[y + 1] - rowp[y];
+      cost += __ldg(&rowp[y + 1]) - __ldg(&rowp[y]);
     }
     cost = block_sum64(cost, c.scan_tmp64);
     if (tid == 0) {
-      c.lo[side][dnew] = nb;
-      c.hi[side][dnew] = nb + cnt;
+      lvl_lo(T, side, dnew) = nb;
+      lvl_hi(T, side, dnew) = nb + cnt;
       c.depth[side] = dnew;
       c.cost[side] = cost;
       c.stat[KADABRA_STAT_NEW] += cnt;
@@ -549,7 +645,7 @@ __device__ void run_sample(const SampleParams& P, const Tables& T, Ctl& c, uint6
     __syncthreads();
     if (c.flags) return;
   }
-  if (c.done == 0) {  // loop bound reached (cannot happen below MAXD levels)
+  if (c.done == 0) {  // loop bound reached (cannot happen within maxd levels)
     if (tid == 0) c.flags |= F_CAP;
     __syncthreads();
     return;
@@ -642,27 +738,23 @@ __device__ void run_sample(const SampleParams& P, const Tables& T, Ctl& c, uint6
   if (c.flags) return;
 
   // ------------------------------------------------ backtracking
-  uint32_t j = 2;
-  int dv = 0, dw = 0;
+  // The candidate edge joins the two current frontiers, so v is at depth[0]
+  // on the s side and w at depth[1] on the t side.
+  const int dv = c.depth[0], dw = c.depth[1];
   if (tid == 0) {
     const uint32_t a = tab_find(T, c.cv), b = tab_find(T, c.cw);
-    if (a == NONE || b == NONE || val_side(a) != 0 || val_side(b) != 1) {
-      c.flags |= F_INTERNAL;
-    } else {
-      c.pick = val_dist(a);   // temporarily: dist_s(v)
-      c.pick_pos = val_dist(b);  // dist_t(w)
-    }
+    const bool ok_a = a != NONE && val_side(a) == 0 && (int)val_slot(a) >= lvl_lo(T, 0, dv) &&
+                      (int)val_slot(a) < lvl_hi(T, 0, dv);
+    const bool ok_b = b != NONE && val_side(b) == 1 && (int)val_slot(b) >= lvl_lo(T, 1, dw) &&
+                      (int)val_slot(b) < lvl_hi(T, 1, dw);
+    if (!ok_a || !ok_b) c.flags |= F_INTERNAL;
   }
   __syncthreads();
   if (c.flags) return;
-  dv = c.pick;
-  dw = c.pick_pos;
-  __syncthreads();
-  const int total_nodes = dv + dw + 2;
   const bool want_path = P.paths != nullptr && out_i >= 0;
   if (tid == 0) {
     c.stat[KADABRA_STAT_DIST] = dv + 1 + dw;
-    c.stat[KADABRA_STAT_PATH_NODES] = total_nodes;
+    c.stat[KADABRA_STAT_PATH_NODES] = dv + dw + 2;
     if (want_path) {
       int32_t* row = P.paths + out_i * (int64_t)P.max_len;
       if (dv < P.max_len) row[dv] = c.cv;
@@ -673,13 +765,20 @@ __device__ void run_sample(const SampleParams& P, const Tables& T, Ctl& c, uint6
       if (dw > 0) atomicAdd(&P.counts[c.cw], 1u);
     }
   }
+  uint32_t j = 2;
   for (int half = 0; half < 2; ++half) {
-    // half 0: v -> s over in-arcs (weights sigma_s); half 1: w -> t over out-arcs
+    // half 0: v -> s over predecessors (weights sigma_s); half 1: w -> t over successors
     int x = half == 0 ? c.cv : c.cw;
     int dx = half == 0 ? dv : dw;
+    // the row of x that holds its neighbours one level closer to the root
     const int32_t* brow = half == 0 ? G.rrp : G.rp;
     const int32_t* bcol = half == 0 ? G.rci : G.ci;
+    // the opposite direction, to test adjacency from a previous-level node
+    const int32_t* frow = half == 0 ? G.rp : G.rrp;
+    const int32_t* fcol = half == 0 ? G.ci : G.rci;
     while (dx > 0) {
+      const int plo = lvl_lo(T, half, dx - 1), phi = lvl_hi(T, half, dx - 1);
+      const int r0 = __ldg(&brow[x]), deg = __ldg(&brow[x + 1]) - r0;
       if (tid == 0) {
         const uint32_t vx = tab_find(T, x);
         if (vx == NONE || (int)val_slot(vx) >= T.lcap) {
@@ -688,77 +787,70 @@ __device__ void run_sample(const SampleParams& P, const Tables& T, Ctl& c, uint6
         } else {
           c.r = below128(draw(P.seed, P.domain, idx, j), T.lsig[val_slot(vx)]);
         }
+        // scan whichever is shorter: the row of x, or the previous level
+        // (sorted, so its order is the row's order restricted to it)
+        c.mode = ((long long)(phi - plo) * 16 < (long long)deg) ? 1 : 0;
       }
       ++j;
       __syncthreads();
       if (c.flags) return;
-      const int r0 = brow[x], deg = brow[x + 1] - r0;
-      const int per = (deg + NW - 1) / NW;
-      const int c0 = min(deg, wid * per), c1 = min(deg, c0 + per);
-      unsigned long long part = 0;
-      for (int e = c0 + lane; e < c1; e += 32) {
-        const int y = __ldg(&bcol[r0 + e]);
-        const uint32_t v = tab_find(T, y);
-        if (v != NONE && val_side(v) == half && val_dist(v) == dx - 1) part += T.lsig[val_slot(v)];
-      }
+      const unsigned long long r = c.r;
+      int pick;
+      if (c.mode == 0) {
+        pick = block_pick(deg, r, c, [&](int i0, int N, unsigned long long* w) {
+          int ys[U];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
-      if (lane == 0) c.wsum[wid] = part;
-      __syncthreads();
-      if (tid == 0) {
-        unsigned long long acc = 0;
-        c.sel_warp = -1;
-        for (int w = 0; w < NW; ++w) {
-          if (c.r < acc + c.wsum[w]) {
-            c.sel_warp = w;
-            c.sel_off = c.r - acc;
-            break;
-          }
-          acc += c.wsum[w];
-        }
-        if (c.sel_warp < 0) c.flags |= F_INTERNAL;
-      }
-      __syncthreads();
-      if (c.flags) return;
-      if (wid == c.sel_warp) {
-        unsigned long long run = 0;
-        bool found = false;
-        for (int base = c0; base < c1 && !found; base += 32) {
-          const int e = base + lane;
-          unsigned long long w = 0;
-          int y = -1;
-          if (e < c1) {
-            y = __ldg(&bcol[r0 + e]);
-            const uint32_t v = tab_find(T, y);
-            if (v != NONE && val_side(v) == half && val_dist(v) == dx - 1) w = T.lsig[val_slot(v)];
-          }
-          const unsigned long long incl = warp_incl_scan_u64(w);
-          const bool hit = (e < c1) && w != 0 && (run + incl > c.sel_off);
-          const unsigned m = __ballot_sync(FULL, hit);
-          if (m) {
-            const int first = __ffs(m) - 1;
-            if (lane == first) {
-              c.pick = y;
-              c.pick_pos = e;
+          for (int k = 0; k < U; ++k) ys[k] = (i0 + k < N) ? __ldg(&bcol[r0 + i0 + k]) : -1;
+#pragma unroll
+          for (int k = 0; k < U; ++k) {
+            w[k] = 0;
+            if (ys[k] >= 0) {
+              const uint32_t v = tab_find(T, ys[k]);
+              const int sl = (int)val_slot(v);
+              if (v != NONE && val_side(v) == half && sl >= plo && sl < phi) w[k] = T.lsig[sl];
             }
-            found = true;
           }
-          run += __shfl_sync(FULL, incl, 31);
+        });
+      } else {
+        pick = block_pick(phi - plo, r, c, [&](int i0, int N, unsigned long long* w) {
+#pragma unroll
+          for (int k = 0; k < U; ++k) {
+            w[k] = 0;
+            if (i0 + k < N) {
+              const int y = T.lnode[plo + i0 + k];
+              const int a = __ldg(&frow[y]), b = __ldg(&frow[y + 1]);
+              const int at = lower_bound_row(fcol, a, b, x);
+              if (at < b && __ldg(&fcol[at]) == x) w[k] = T.lsig[plo + i0 + k];
+            }
+          }
+        });
+      }
+      if (pick < 0) {
+        if (tid == 0) c.flags |= F_INTERNAL;
+        __syncthreads();
+        return;
+      }
+      if (tid == 0) {
+        int y, pos;
+        if (c.mode == 0) {
+          pos = pick;
+          y = __ldg(&bcol[r0 + pick]);
+        } else {
+          y = T.lnode[plo + pick];
+          pos = lower_bound_row(bcol, r0, r0 + deg, y) - r0;
         }
-        if (!found && lane == 0) atomicOr(&c.flags, F_INTERNAL);
+        c.next_x = y;
+        c.stat[KADABRA_STAT_BT_SCANNED] += pos + 1;
+        const int dn = dx - 1;
+        if (dn > 0 && P.counts) atomicAdd(&P.counts[y], 1u);
+        if (want_path) {
+          const int at = half == 0 ? dn : (dv + 1) + (dw - dn);
+          if (at < P.max_len) P.paths[out_i * (int64_t)P.max_len + at] = y;
+        }
       }
       __syncthreads();
-      if (c.flags) return;
-      x = c.pick;
+      x = c.next_x;
       dx -= 1;
-      if (tid == 0) {
-        c.stat[KADABRA_STAT_BT_SCANNED] += c.pick_pos + 1;
-        if (dx > 0 && P.counts) atomicAdd(&P.counts[x], 1u);
-        if (want_path) {
-          const int at = half == 0 ? dx : (dv + 1) + (dw - dx);
-          if (at < P.max_len) P.paths[out_i * (int64_t)P.max_len + at] = x;
-        }
-      }
       __syncthreads();
     }
   }
@@ -775,42 +867,84 @@ __device__ void reset_tables(const Tables& T, Ctl& c) {
     return;
   }
   const int nl = min(c.nlist, T.lcap);
-  for (int i = tid; i < nl; i += NT) T.pre[i] = (int32_t)tab_findpos(T, T.lnode[i]);
+  for (int i = tid; i < nl; i += NT) T.pr[i].x = (int32_t)tab_findpos(T, T.lnode[i]);
   __syncthreads();
   for (int i = tid; i < nl; i += NT)
-    if (T.pre[i] >= 0) T.hkv[T.pre[i]] = EMPTY;
+    if (T.pr[i].x >= 0) T.hkv[T.pr[i].x] = EMPTY;
   __syncthreads();
 }
 
+size_t fast_smem_layout(size_t* off_hkv, size_t* off_lsig, size_t* off_pr, size_t* off_lnode, size_t* off_lvl) {
+  size_t o = (sizeof(Ctl) + 15) & ~size_t(15);
+  *off_hkv = o;
+  o += sizeof(unsigned long long) << FAST_HLOG;
+  *off_lsig = o;
+  o += sizeof(unsigned long long) * FAST_LCAP;
+  *off_pr = o;
+  o += sizeof(int2) * (FAST_LCAP + 1);
+  *off_lnode = o;
+  o += sizeof(int32_t) * FAST_LCAP;
+  *off_lvl = o;
+  o += sizeof(int) * 4 * (FAST_MAXD + 2);
+  return o;
+}
+
+size_t gm_layout(int hlog, int lcap, size_t* off_lsig, size_t* off_pr, size_t* off_lnode, size_t* off_lvl) {
+  size_t o = sizeof(unsigned long long) << hlog;
+  *off_lsig = o;
+  o += sizeof(unsigned long long) * (size_t)lcap;
+  *off_pr = o;
+  o += sizeof(int2) * ((size_t)lcap + 1);
+  *off_lnode = o;
+  o += sizeof(int32_t) * (size_t)lcap;
+  *off_lvl = o;
+  o += sizeof(int) * 4 * (size_t)(GM_MAXD + 2);
+  return (o + 255) & ~size_t(255);
+}
+
 template <bool GM>
-__global__ void __launch_bounds__(NT) k_sample(SampleParams P) {
+__global__ void __launch_bounds__(NT, 2) k_sample(SampleParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   Ctl& c = *reinterpret_cast<Ctl*>(smem);
   Tables T;
   if (!GM) {
-    unsigned char* p = smem + ((sizeof(Ctl) + 15) & ~size_t(15));
-    T.hkv = reinterpret_cast<unsigned long long*>(p);
-    p += sizeof(unsigned long long) << FAST_HLOG;
-    T.lsig = reinterpret_cast<unsigned long long*>(p);
-    p += sizeof(unsigned long long) * FAST_LCAP;
-    T.lnode = reinterpret_cast<int32_t*>(p);
-    p += sizeof(int32_t) * FAST_LCAP;
-    T.pre = reinterpret_cast<int32_t*>(p);
+    // offsets of fast_smem_layout, recomputed here (all compile-time constants)
+    constexpr size_t o_hkv = (sizeof(Ctl) + 15) & ~size_t(15);
+    constexpr size_t o_lsig = o_hkv + (sizeof(unsigned long long) << FAST_HLOG);
+    constexpr size_t o_pr = o_lsig + sizeof(unsigned long long) * FAST_LCAP;
+    constexpr size_t o_lnode = o_pr + sizeof(int2) * (FAST_LCAP + 1);
+    constexpr size_t o_lvl = o_lnode + sizeof(int32_t) * FAST_LCAP;
+    T.hkv = reinterpret_cast<unsigned long long*>(smem + o_hkv);
+    T.lsig = reinterpret_cast<unsigned long long*>(smem + o_lsig);
+    T.pr = reinterpret_cast<int2*>(smem + o_pr);
+    T.lnode = reinterpret_cast<int32_t*>(smem + o_lnode);
+    T.lvl = reinterpret_cast<int*>(smem + o_lvl);
     T.hlog = FAST_HLOG;
     T.hmask = (1u << FAST_HLOG) - 1u;
     T.lcap = FAST_LCAP;
+    T.maxd = FAST_MAXD;
   } else {
     unsigned char* p = P.gm_base + (size_t)blockIdx.x * P.gm_stride;
+    size_t o_lsig, o_pr, o_lnode, o_lvl;
+    {
+      size_t o = sizeof(unsigned long long) << P.gm_hlog;
+      o_lsig = o;
+      o += sizeof(unsigned long long) * (size_t)P.gm_lcap;
+      o_pr = o;
+      o += sizeof(int2) * ((size_t)P.gm_lcap + 1);
+      o_lnode = o;
+      o += sizeof(int32_t) * (size_t)P.gm_lcap;
+      o_lvl = o;
+    }
     T.hkv = reinterpret_cast<unsigned long long*>(p);
-    p += sizeof(unsigned long long) << P.gm_hlog;
-    T.lsig = reinterpret_cast<unsigned long long*>(p);
-    p += sizeof(unsigned long long) * (size_t)P.gm_lcap;
-    T.lnode = reinterpret_cast<int32_t*>(p);
-    p += sizeof(int32_t) * (size_t)P.gm_lcap;
-    T.pre = reinterpret_cast<int32_t*>(p);
+    T.lsig = reinterpret_cast<unsigned long long*>(p + o_lsig);
+    T.pr = reinterpret_cast<int2*>(p + o_pr);
+    T.lnode = reinterpret_cast<int32_t*>(p + o_lnode);
+    T.lvl = reinterpret_cast<int*>(p + o_lvl);
     T.hlog = P.gm_hlog;
     T.hmask = (1u << P.gm_hlog) - 1u;
     T.lcap = P.gm_lcap;
+    T.maxd = GM_MAXD;
   }
   T.pi = P.pi_base + (size_t)blockIdx.x * NW * P.pcap;
   T.pcap = P.pcap;
@@ -878,8 +1012,8 @@ __global__ void __launch_bounds__(NT) k_sample(SampleParams P) {
 }
 
 size_t fast_smem_bytes() {
-  return ((sizeof(Ctl) + 15) & ~size_t(15)) + (sizeof(unsigned long long) << FAST_HLOG) +
-         sizeof(unsigned long long) * FAST_LCAP + sizeof(int32_t) * FAST_LCAP + sizeof(int32_t) * (FAST_LCAP + 1);
+  size_t a, b, c, d, e;
+  return fast_smem_layout(&a, &b, &c, &d, &e);
 }
 
 // ============================================================== stop test
@@ -1089,6 +1223,7 @@ struct kadabra_graph {
   size_t gm_stride = 0;
   int gm_hlog = 0;
   int gm_lcap = 0;
+  uint32_t flags = 0;
   // run buffers
   uint32_t *counts = nullptr, *count0 = nullptr;
   double *lnL = nullptr, *lnU = nullptr, *btilde = nullptr;
@@ -1126,11 +1261,14 @@ kadabra_status ensure_workspace(kadabra_graph* g, uint64_t deferred_need) {
     g->gm_hlog = std::max(12, ceil_log2(2ull * (uint64_t)g->n));
     g->gm_lcap = g->n;
     g->pcap_gm = (int)std::min<int64_t>(std::max<int64_t>(g->m, 1024), 1 << 18);
-    g->gm_stride = (sizeof(unsigned long long) << g->gm_hlog) + sizeof(unsigned long long) * (size_t)g->gm_lcap +
-                   sizeof(int32_t) * (size_t)g->gm_lcap + sizeof(int32_t) * ((size_t)g->gm_lcap + 1);
-    g->gm_stride = (g->gm_stride + 255) & ~size_t(255);
+    {
+      size_t a, b, c2, d;
+      g->gm_stride = gm_layout(g->gm_hlog, g->gm_lcap, &a, &b, &c2, &d);
+    }
     const size_t per_cta = g->gm_stride + sizeof(PiEntry) * NW * (size_t)g->pcap_gm;
-    const size_t budget = (size_t)4 << 30;
+    // deferred samples are rare on small-world graphs; 1 GiB of tables
+    // keeps at least a few CTAs busy on them
+    const size_t budget = (size_t)1 << 30;
     g->grid_gm = (int)std::max<size_t>(1, std::min<size_t>((size_t)g->num_sms, budget / per_cta));
     void* p;
     KTRY(dev_alloc(g, &p, 4 * sizeof(unsigned long long)));
@@ -1197,6 +1335,7 @@ SampleParams base_params(kadabra_graph* g) {
   P.gm_stride = g->gm_stride;
   P.gm_hlog = g->gm_hlog;
   P.gm_lcap = g->gm_lcap;
+  P.force_global = (g->flags & KADABRA_FLAG_GLOBAL_TABLES) ? 1 : 0;
   return P;
 }
 
@@ -1520,6 +1659,13 @@ void kadabra_free_graph(kadabra_graph* g) {
   for (void* p : g->allocs)
     if (p) cudaFree(p);
   delete g;
+}
+
+kadabra_status kadabra_graph_set_flags(kadabra_graph* g, uint32_t flags) {
+  if (!g) return fail(KADABRA_ERR_ARG, "graph is NULL");
+  if (flags & ~(uint32_t)KADABRA_FLAG_GLOBAL_TABLES) return fail(KADABRA_ERR_ARG, "unknown flag");
+  g->flags = flags;
+  return KADABRA_OK;
 }
 
 kadabra_status kadabra_graph_info(const kadabra_graph* g, int32_t* n, int64_t* m, int* directed, int64_t* vd) {

@@ -41,6 +41,7 @@ STAT_NAMES = (
     "bt_scanned", "path_nodes", "sigma_lo", "sigma_hi", "dist",
 )
 NSTAT = len(STAT_NAMES)
+FLAG_GLOBAL_TABLES = 1
 
 
 class KadabraError(RuntimeError):
@@ -90,6 +91,8 @@ def load_library():
         lib.kadabra_free_graph.argtypes = [p]
         lib.kadabra_graph_info.argtypes = [p, C.POINTER(i32), C.POINTER(i64), C.POINTER(C.c_int), C.POINTER(i64)]
         lib.kadabra_graph_info.restype = st
+        lib.kadabra_graph_set_flags.argtypes = [p, u32]
+        lib.kadabra_graph_set_flags.restype = st
         lib.kadabra_run.argtypes = [p, dbl, dbl, i32, u64, C.POINTER(kadabra_config), C.POINTER(kadabra_result)]
         lib.kadabra_run.restype = st
         lib.kadabra_sample_batch.argtypes = [p, u64, u32, u64, u64, p, p, p]
@@ -142,6 +145,9 @@ class Graph:
         vd = C.c_int64()
         _raise(load_library().kadabra_graph_info(self.handle, None, None, None, C.byref(vd)))
         return vd.value
+
+    def set_flags(self, flags: int) -> None:
+        _raise(load_library().kadabra_graph_set_flags(self.handle, flags))
 
     def free(self):
         if self.handle:

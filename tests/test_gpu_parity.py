@@ -114,15 +114,33 @@ def test_sigma_overflow_is_reported_per_sample(kd, orc, gg):
     assert_samples_equal(got, ref, "diamonds")
 
 
-def test_depth_beyond_limit_fails_loudly(kd, gg):
-    g = gg.path_graph(600)
+def test_deep_searches_use_global_tables(kd, orc, gg):
+    """Distances far beyond the shared-memory level limit (254 per side):
+    such samples are deferred to the global-memory tables."""
+    compare_paths(kd, orc, gg.path_graph(1500), 1, 0, 0, 300, max_len=1600, tag="path1500")
+    compare_paths(kd, orc, gg.cycle_graph(2001), 2, 0, 0, 300, max_len=1100, tag="cycle2001")
+
+
+def compare_paths_global(kd, orc, g, seed, domain, first, count, max_len=64, tag=""):
     G = kd.kadabra_load_csr(g)
     try:
-        with pytest.raises(kd.KadabraError) as e:
-            kd.kadabra_sample_paths(G, 1, 0, 0, 200, max_len=700)
-        assert e.value.status == kd.ERR_CAPACITY
+        G.set_flags(kd.FLAG_GLOBAL_TABLES)
+        got = kd.kadabra_sample_paths(G, seed, domain, first, count, max_len=max_len)
     finally:
         G.free()
+    ref = orc.sample_paths(g, seed, domain, first, count, max_len=max_len)
+    assert_samples_equal(got, ref, tag)
+
+
+@pytest.mark.parametrize("name,make", [s for s in SMALL if s[0] in ("Q6", "drand300", "ba3000", "rmat12", "star30")],
+                         ids=["Q6", "drand300", "ba3000", "rmat12", "star30"])
+def test_global_tables_match_oracle(kd, orc, gg, name, make):
+    compare_paths_global(kd, orc, make(gg), 23, 0, 0, 1500, max_len=256, tag=name)
+
+
+def test_global_tables_er_and_power_law(kd, orc, er2000, chung_lu_1m):
+    compare_paths_global(kd, orc, er2000, 24, 0, 0, 3000, tag="er2000")
+    compare_paths_global(kd, orc, chung_lu_1m, 25, 0, 777, 400, tag="chung-lu")
 
 
 def test_sample_batch_ragged_and_order_independent(kd, orc, er2000):
@@ -184,14 +202,6 @@ def test_invalid_csr_rejected(kd, gg):
     with pytest.raises(kd.KadabraError) as e:
         kd.kadabra_load_csr(d)
     assert e.value.status == kd.ERR_CSR
-
-
-def test_sample_paths_grid_uses_global_tables(kd, orc, gg):
-    """100x100 grid: both searches grow diamonds of thousands of nodes before
-    they touch, beyond the shared-memory tables, so most samples run on the
-    global-memory tables."""
-    got = compare_paths(kd, orc, gg.grid_graph(100, 100), 4, 0, 0, 600, max_len=256, tag="grid100")
-    assert (got.stat("new") + 2 > 2048).sum() > 100
 
 
 # ------------------------------------------------------------------ stop test
