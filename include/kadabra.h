@@ -127,12 +127,14 @@ void kadabra_free_graph(kadabra_graph* g);
 
 kadabra_status kadabra_graph_info(const kadabra_graph* g, int32_t* n, int64_t* m, int* directed, int64_t* vd);
 
-/* Graph flags.  KADABRA_FLAG_GLOBAL_TABLES runs every sample on the
- * global-memory tables instead of first trying shared memory (the results
- * are identical; this exists to test that path and for graphs whose
- * searches are known to be deep or wide).  Returns KADABRA_ERR_ARG for
- * unknown bits. */
-enum { KADABRA_FLAG_GLOBAL_TABLES = 1 };
+/* Graph flags.  A sample's visited set lives in shared memory while it fits,
+ * then in medium per-CTA global tables, then in n-sized global tables (each
+ * sample goes as far as it needs; results are identical in every tier).
+ * KADABRA_FLAG_GLOBAL_TABLES runs every sample on the n-sized tables and
+ * KADABRA_FLAG_MEDIUM_TABLES starts every sample on the medium tables; both
+ * exist to test those paths and for graphs whose searches are known to be
+ * deep or wide.  Returns KADABRA_ERR_ARG for unknown bits. */
+enum { KADABRA_FLAG_GLOBAL_TABLES = 1, KADABRA_FLAG_MEDIUM_TABLES = 2 };
 kadabra_status kadabra_graph_set_flags(kadabra_graph* g, uint32_t flags);
 
 /* KADABRA, all-nodes mode (Alg. 1 with Alg. 2 and the rule f,g <= lambda

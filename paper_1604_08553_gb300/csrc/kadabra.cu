@@ -48,14 +48,20 @@
 namespace {
 
 // ============================================================== constants
-constexpr int NT = 256;            // threads per sampler CTA
+constexpr int NT = 128;            // threads per sampler CTA
 constexpr int NW = NT / 32;        // warps per sampler CTA
 constexpr int U = 4;               // independent items per thread per step (memory-level parallelism)
-constexpr int FAST_HLOG = 12;      // shared-memory hash: 4096 slots
-constexpr int FAST_LCAP = 2048;    // shared-memory level lists: 2048 nodes
-constexpr int FAST_MAXD = 254;     // levels per side with shared-memory tables
-constexpr int GM_MAXD = 65534;     // levels per side with global-memory tables
-constexpr int FAST_PCAP = 2048;    // candidate edges per warp (global memory)
+// three tiers of per-sample tables: a sample starts in shared memory, is
+// retried by the same CTA on its medium global tables if it outgrows them,
+// and only beyond those is deferred to a launch with n-sized tables
+constexpr int FAST_HLOG = 11;      // tier S, shared memory: 2048 hash slots
+constexpr int FAST_LCAP = 1024;    //   level lists: 1024 nodes
+constexpr int FAST_MAXD = 126;     //   levels per side
+constexpr int MED_HLOG = 15;       // tier M, global memory per CTA: 32768 hash slots
+constexpr int MED_LCAP = 16384;    //   level lists: 16384 nodes
+constexpr int MED_MAXD = 1022;     //   levels per side
+constexpr int GM_MAXD = 65534;     // tier L, global memory, hash >= 2n slots, lists of n
+constexpr int FAST_PCAP = 2048;    // candidate edges per warp, tiers S and M (global memory)
 constexpr unsigned long long EMPTY = ~0ull;
 constexpr uint32_t NONE = 0xFFFFFFFFu;
 constexpr uint32_t SLOT_MASK = 0x7FFFFFFFu;
@@ -201,7 +207,7 @@ struct SampleParams {
   uint64_t deferred_cap;
   int32_t* status;                  // run-wide error word (kadabra_status values)
   long long* totals;                // KADABRA_NSTAT or null
-  int force_global;                 // defer every sample to the global-memory tables
+  int tier_flags;                   // TF_* test switches for the table tiers
   // per-sample outputs (test hook) or null
   int32_t* st_out;
   int32_t* path_len;
@@ -212,7 +218,9 @@ struct SampleParams {
   // tables
   PiEntry* pi_base;                 // per CTA: NW * pcap
   int pcap;
-  unsigned char* gm_base;           // global-memory tables, per CTA
+  unsigned char* med_base;          // tier M tables, per CTA of the main grid
+  size_t med_stride;
+  unsigned char* gm_base;           // tier L tables, per CTA of the deferred launch
   size_t gm_stride;
   int gm_hlog;
   int gm_lcap;
@@ -387,8 +395,8 @@ __device__ __forceinline__ int block_pick(int N, unsigned long long r, Ctl& c, W
 // ============================================================== one sample
 // All threads of the CTA call this with the same idx.  Flags in c.flags tell
 // the caller what happened; the caller resets the tables afterwards.
-template <bool GM>
-__device__ void run_sample(const SampleParams& P, const Tables& T, Ctl& c, uint64_t idx, int64_t out_i) {
+__device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& T, Ctl& c, uint64_t idx,
+                                           int64_t out_i) {
   const int tid = threadIdx.x, lane = lane_id(), wid = warp_id();
   const GraphDev& G = P.g;
 
@@ -403,7 +411,7 @@ __device__ void run_sample(const SampleParams& P, const Tables& T, Ctl& c, uint6
     c.t = t;
     for (int k = 0; k < KADABRA_NSTAT; ++k) c.stat[k] = 0;
     c.stat[KADABRA_STAT_DIST] = -1;
-    c.flags = (!GM && P.force_global) ? F_CAP : 0;
+    c.flags = 0;
     c.done = 0;
     uint32_t pos;
     if (tab_insert(T, s, pack_val(0, 0), &pos) != 1) c.flags |= F_INTERNAL;
@@ -475,18 +483,25 @@ __device__ void run_sample(const SampleParams& P, const Tables& T, Ctl& c, uint6
       int npi = 0;
       bool sigma_of = false;
       PiEntry* seg = T.pi + (size_t)wid * T.pcap;
+      // frontier row of the first arc of the current window (warp-uniform)
+      int pcur = c0 < c1 ? frontier_pos(T.pr, fcount, c0) : 0;
       for (int base = c0; base < c1; base += 32 * U) {
         int xs[U], ys[U], ps[U];
 #pragma unroll
         for (int k = 0; k < U; ++k) {
-          const int e = base + 32 * k + lane;
+          const int wb = base + 32 * k;
           xs[k] = -1;
-          if (e < c1) {
-            const int p = frontier_pos(T.pr, fcount, e);
-            const int2 q = T.pr[p];
-            ps[k] = p;
-            xs[k] = T.lnode[f0 + p];
-            ys[k] = __ldg(&cols[q.y + (e - q.x)]);
+          if (wb < c1) {
+            if (T.pr[pcur + 1].x <= wb) pcur = pcur + 1 + frontier_pos(T.pr + pcur + 1, fcount - pcur - 1, wb - 0);
+            const int e = wb + lane;
+            if (e < c1) {
+              int p = pcur;
+              if (T.pr[p + 1].x <= e) p = p + 1 + frontier_pos(T.pr + p + 1, fcount - p - 1, e);
+              const int2 q = T.pr[p];
+              ps[k] = p;
+              xs[k] = T.lnode[f0 + p];
+              ys[k] = __ldg(&cols[q.y + (e - q.x)]);
+            }
           }
         }
 #pragma unroll
@@ -856,12 +871,12 @@ __device__ void run_sample(const SampleParams& P, const Tables& T, Ctl& c, uint6
   }
 }
 
-// clears every hash entry the sample inserted (global tables) or the whole
-// table (shared memory, cheaper than locating the entries)
-template <bool GM>
-__device__ void reset_tables(const Tables& T, Ctl& c) {
+// Clears the hash entries of the last sample: the whole table (shared memory,
+// cheaper than locating the entries, or after a capacity failure that may
+// have left entries outside the lists), else only the listed nodes' entries.
+__device__ void reset_tables(const Tables& T, Ctl& c, bool whole) {
   const int tid = threadIdx.x;
-  if (!GM || (c.flags & F_CAP)) {
+  if (whole || (c.flags & F_CAP)) {
     for (uint32_t i = tid; i <= T.hmask; i += NT) T.hkv[i] = EMPTY;
     __syncthreads();
     return;
@@ -874,22 +889,15 @@ __device__ void reset_tables(const Tables& T, Ctl& c) {
   __syncthreads();
 }
 
-size_t fast_smem_layout(size_t* off_hkv, size_t* off_lsig, size_t* off_pr, size_t* off_lnode, size_t* off_lvl) {
-  size_t o = (sizeof(Ctl) + 15) & ~size_t(15);
-  *off_hkv = o;
-  o += sizeof(unsigned long long) << FAST_HLOG;
-  *off_lsig = o;
-  o += sizeof(unsigned long long) * FAST_LCAP;
-  *off_pr = o;
-  o += sizeof(int2) * (FAST_LCAP + 1);
-  *off_lnode = o;
-  o += sizeof(int32_t) * FAST_LCAP;
-  *off_lvl = o;
-  o += sizeof(int) * 4 * (FAST_MAXD + 2);
-  return o;
+// global-memory tiers share one body compiled once, outside the kernel
+__device__ __noinline__ void run_sample_global(const SampleParams& P, const Tables& T, Ctl& c, uint64_t idx,
+                                               int64_t out_i) {
+  run_sample(P, T, c, idx, out_i);
 }
 
-size_t gm_layout(int hlog, int lcap, size_t* off_lsig, size_t* off_pr, size_t* off_lnode, size_t* off_lvl) {
+// layout of one CTA's tables in global memory (tiers M and L)
+__host__ __device__ inline size_t gm_layout(int hlog, int lcap, int maxd, size_t* off_lsig, size_t* off_pr,
+                                            size_t* off_lnode, size_t* off_lvl) {
   size_t o = sizeof(unsigned long long) << hlog;
   *off_lsig = o;
   o += sizeof(unsigned long long) * (size_t)lcap;
@@ -898,123 +906,158 @@ size_t gm_layout(int hlog, int lcap, size_t* off_lsig, size_t* off_pr, size_t* o
   *off_lnode = o;
   o += sizeof(int32_t) * (size_t)lcap;
   *off_lvl = o;
-  o += sizeof(int) * 4 * (size_t)(GM_MAXD + 2);
+  o += sizeof(int) * 4 * (size_t)(maxd + 2);
   return (o + 255) & ~size_t(255);
 }
 
-template <bool GM>
-__global__ void __launch_bounds__(NT, 2) k_sample(SampleParams P) {
+__device__ inline Tables gm_tables(unsigned char* base, int hlog, int lcap, int maxd) {
+  size_t o_lsig, o_pr, o_lnode, o_lvl;
+  gm_layout(hlog, lcap, maxd, &o_lsig, &o_pr, &o_lnode, &o_lvl);
+  Tables T;
+  T.hkv = reinterpret_cast<unsigned long long*>(base);
+  T.lsig = reinterpret_cast<unsigned long long*>(base + o_lsig);
+  T.pr = reinterpret_cast<int2*>(base + o_pr);
+  T.lnode = reinterpret_cast<int32_t*>(base + o_lnode);
+  T.lvl = reinterpret_cast<int*>(base + o_lvl);
+  T.hlog = hlog;
+  T.hmask = (1u << hlog) - 1u;
+  T.lcap = lcap;
+  T.maxd = maxd;
+  return T;
+}
+
+// shared-memory layout of the main sampler (tier S)
+constexpr size_t S_OFF_HKV = (sizeof(Ctl) + 15) & ~size_t(15);
+constexpr size_t S_OFF_LSIG = S_OFF_HKV + (sizeof(unsigned long long) << FAST_HLOG);
+constexpr size_t S_OFF_PR = S_OFF_LSIG + sizeof(unsigned long long) * FAST_LCAP;
+constexpr size_t S_OFF_LNODE = S_OFF_PR + sizeof(int2) * (FAST_LCAP + 1);
+constexpr size_t S_OFF_LVL = S_OFF_LNODE + sizeof(int32_t) * FAST_LCAP;
+constexpr size_t S_BYTES = S_OFF_LVL + sizeof(int) * 4 * (FAST_MAXD + 2);
+
+// flags of SampleParams::tier_flags
+constexpr int TF_SKIP_SHARED = 1;   // start in tier M
+constexpr int TF_ONLY_LARGE = 2;    // defer every sample to tier L
+
+// Records the outcome of one sample (per-sample outputs, totals, status).
+__device__ void finish_sample(const SampleParams& P, Ctl& c, uint64_t idx, int64_t out_i) {
+  const int flags = c.flags;
+  int st = KADABRA_OK;
+  if (flags & F_INTERNAL)
+    st = KADABRA_ERR_INTERNAL;
+  else if (flags & F_SIGMA)
+    st = KADABRA_ERR_SIGMA_OVERFLOW;
+  else if (flags & F_CAP)
+    st = KADABRA_ERR_CAPACITY;
+  if (st != KADABRA_OK) atomicCAS(P.status, 0, st);
+  for (int q = 0; q < KADABRA_NSTAT; ++q)
+    if (q != KADABRA_STAT_SIGMA_LO && q != KADABRA_STAT_SIGMA_HI && q != KADABRA_STAT_DIST) c.tot[q] += c.stat[q];
+  if (out_i >= 0) {
+    P.st_out[2 * out_i] = c.s;
+    P.st_out[2 * out_i + 1] = c.t;
+    if (P.path_len) P.path_len[out_i] = (int32_t)c.stat[KADABRA_STAT_PATH_NODES];
+    if (P.stats)
+      for (int q = 0; q < KADABRA_NSTAT; ++q) P.stats[out_i * KADABRA_NSTAT + q] = c.stat[q];
+    if (P.sstatus) P.sstatus[out_i] = st;
+  }
+}
+
+__device__ void clear_path_row(const SampleParams& P, int64_t out_i) {
+  if (threadIdx.x == 0 && out_i >= 0 && P.paths) {
+    int32_t* row = P.paths + out_i * (int64_t)P.max_len;
+    for (int q = 0; q < P.max_len; ++q) row[q] = -1;
+  }
+  __syncthreads();
+}
+
+// MODE 0: the main grid.  Each sample runs on the CTA's shared-memory tables
+// (tier S); if it outgrows them, the same CTA re-runs it on its medium
+// global tables (tier M); beyond those it is queued for MODE 1.
+// MODE 1: the queued samples on n-sized global tables (tier L).
+template <int MODE>
+__global__ void __launch_bounds__(NT) k_sample(SampleParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   Ctl& c = *reinterpret_cast<Ctl*>(smem);
-  Tables T;
-  if (!GM) {
-    // offsets of fast_smem_layout, recomputed here (all compile-time constants)
-    constexpr size_t o_hkv = (sizeof(Ctl) + 15) & ~size_t(15);
-    constexpr size_t o_lsig = o_hkv + (sizeof(unsigned long long) << FAST_HLOG);
-    constexpr size_t o_pr = o_lsig + sizeof(unsigned long long) * FAST_LCAP;
-    constexpr size_t o_lnode = o_pr + sizeof(int2) * (FAST_LCAP + 1);
-    constexpr size_t o_lvl = o_lnode + sizeof(int32_t) * FAST_LCAP;
-    T.hkv = reinterpret_cast<unsigned long long*>(smem + o_hkv);
-    T.lsig = reinterpret_cast<unsigned long long*>(smem + o_lsig);
-    T.pr = reinterpret_cast<int2*>(smem + o_pr);
-    T.lnode = reinterpret_cast<int32_t*>(smem + o_lnode);
-    T.lvl = reinterpret_cast<int*>(smem + o_lvl);
-    T.hlog = FAST_HLOG;
-    T.hmask = (1u << FAST_HLOG) - 1u;
-    T.lcap = FAST_LCAP;
-    T.maxd = FAST_MAXD;
+  Tables TS, TM;
+  if (MODE == 0) {
+    TS.hkv = reinterpret_cast<unsigned long long*>(smem + S_OFF_HKV);
+    TS.lsig = reinterpret_cast<unsigned long long*>(smem + S_OFF_LSIG);
+    TS.pr = reinterpret_cast<int2*>(smem + S_OFF_PR);
+    TS.lnode = reinterpret_cast<int32_t*>(smem + S_OFF_LNODE);
+    TS.lvl = reinterpret_cast<int*>(smem + S_OFF_LVL);
+    TS.hlog = FAST_HLOG;
+    TS.hmask = (1u << FAST_HLOG) - 1u;
+    TS.lcap = FAST_LCAP;
+    TS.maxd = FAST_MAXD;
+    TS.pi = P.pi_base + (size_t)blockIdx.x * NW * P.pcap;
+    TS.pcap = P.pcap;
+    TM = gm_tables(P.med_base + (size_t)blockIdx.x * P.med_stride, MED_HLOG, MED_LCAP, MED_MAXD);
+    TM.pi = TS.pi;
+    TM.pcap = TS.pcap;
   } else {
-    unsigned char* p = P.gm_base + (size_t)blockIdx.x * P.gm_stride;
-    size_t o_lsig, o_pr, o_lnode, o_lvl;
-    {
-      size_t o = sizeof(unsigned long long) << P.gm_hlog;
-      o_lsig = o;
-      o += sizeof(unsigned long long) * (size_t)P.gm_lcap;
-      o_pr = o;
-      o += sizeof(int2) * ((size_t)P.gm_lcap + 1);
-      o_lnode = o;
-      o += sizeof(int32_t) * (size_t)P.gm_lcap;
-      o_lvl = o;
-    }
-    T.hkv = reinterpret_cast<unsigned long long*>(p);
-    T.lsig = reinterpret_cast<unsigned long long*>(p + o_lsig);
-    T.pr = reinterpret_cast<int2*>(p + o_pr);
-    T.lnode = reinterpret_cast<int32_t*>(p + o_lnode);
-    T.lvl = reinterpret_cast<int*>(p + o_lvl);
-    T.hlog = P.gm_hlog;
-    T.hmask = (1u << P.gm_hlog) - 1u;
-    T.lcap = P.gm_lcap;
-    T.maxd = GM_MAXD;
+    TM = gm_tables(P.gm_base + (size_t)blockIdx.x * P.gm_stride, P.gm_hlog, P.gm_lcap, GM_MAXD);
+    TM.pi = P.pi_base + (size_t)blockIdx.x * NW * P.pcap;
+    TM.pcap = P.pcap;
   }
-  T.pi = P.pi_base + (size_t)blockIdx.x * NW * P.pcap;
-  T.pcap = P.pcap;
 
   const int tid = threadIdx.x;
-  if (!GM)
-    for (uint32_t i = tid; i <= T.hmask; i += NT) T.hkv[i] = EMPTY;
+  if (MODE == 0)
+    for (uint32_t i = tid; i <= TS.hmask; i += NT) TS.hkv[i] = EMPTY;
   if (tid == 0) {
     for (int k = 0; k < KADABRA_NSTAT; ++k) c.tot[k] = 0;
-    c.ntotal = GM ? min(P.ctr[2], (unsigned long long)P.deferred_cap) : P.count;
+    c.ntotal = MODE == 1 ? min(P.ctr[2], (unsigned long long)P.deferred_cap) : P.count;
   }
   __syncthreads();
   const unsigned long long ntotal = c.ntotal;
 
   for (;;) {
-    if (tid == 0) c.cur = atomicAdd(&P.ctr[GM ? 1 : 0], 1ull);
+    if (tid == 0) c.cur = atomicAdd(&P.ctr[MODE == 1 ? 1 : 0], 1ull);
     __syncthreads();
     const unsigned long long k = c.cur;
     if (k >= ntotal) break;
-    const uint64_t idx = GM ? P.deferred[k] : P.first_idx + k;
+    const uint64_t idx = MODE == 1 ? P.deferred[k] : P.first_idx + k;
     const int64_t out_i = P.st_out ? (int64_t)(idx - P.first_idx) : -1;
-    if (tid == 0 && out_i >= 0 && P.paths) {
-      int32_t* row = P.paths + out_i * (int64_t)P.max_len;
-      for (int q = 0; q < P.max_len; ++q) row[q] = -1;
-    }
-    __syncthreads();
-    run_sample<GM>(P, T, c, idx, out_i);
-    __syncthreads();
-    const int flags = c.flags;
-    if (tid == 0) {
-      if (!GM && (flags & F_CAP) && !(flags & (F_SIGMA | F_INTERNAL))) {
-        const unsigned long long d = atomicAdd(&P.ctr[2], 1ull);
-        if (d < P.deferred_cap)
-          P.deferred[d] = idx;
-        else
-          atomicCAS(P.status, 0, (int)KADABRA_ERR_CAPACITY);
-      } else {
-        int st = KADABRA_OK;
-        if (flags & F_INTERNAL)
-          st = KADABRA_ERR_INTERNAL;
-        else if (flags & F_SIGMA)
-          st = KADABRA_ERR_SIGMA_OVERFLOW;
-        else if (flags & F_CAP)
-          st = KADABRA_ERR_CAPACITY;
-        if (st != KADABRA_OK) atomicCAS(P.status, 0, st);
-        for (int q = 0; q < KADABRA_NSTAT; ++q)
-          if (q != KADABRA_STAT_SIGMA_LO && q != KADABRA_STAT_SIGMA_HI && q != KADABRA_STAT_DIST)
-            c.tot[q] += c.stat[q];
-        if (out_i >= 0) {
-          P.st_out[2 * out_i] = c.s;
-          P.st_out[2 * out_i + 1] = c.t;
-          if (P.path_len) P.path_len[out_i] = (int32_t)c.stat[KADABRA_STAT_PATH_NODES];
-          if (P.stats)
-            for (int q = 0; q < KADABRA_NSTAT; ++q) P.stats[out_i * KADABRA_NSTAT + q] = c.stat[q];
-          if (P.sstatus) P.sstatus[out_i] = st;
-        }
+    bool done = false;
+    if (MODE == 0) {
+      if (!(P.tier_flags & (TF_SKIP_SHARED | TF_ONLY_LARGE))) {
+        clear_path_row(P, out_i);
+        run_sample(P, TS, c, idx, out_i);
+        __syncthreads();
+        done = c.flags != F_CAP;
+        reset_tables(TS, c, true);
       }
+      if (!done && !(P.tier_flags & TF_ONLY_LARGE)) {
+        clear_path_row(P, out_i);
+        run_sample_global(P, TM, c, idx, out_i);
+        __syncthreads();
+        done = c.flags != F_CAP;
+        reset_tables(TM, c, false);
+      }
+      if (!done) {  // queue for the n-sized tables
+        if (tid == 0) {
+          const unsigned long long d = atomicAdd(&P.ctr[2], 1ull);
+          if (d < P.deferred_cap)
+            P.deferred[d] = idx;
+          else
+            atomicCAS(P.status, 0, (int)KADABRA_ERR_CAPACITY);
+        }
+        __syncthreads();
+        continue;
+      }
+    } else {
+      clear_path_row(P, out_i);
+      run_sample_global(P, TM, c, idx, out_i);
+      __syncthreads();
+      reset_tables(TM, c, false);
     }
+    if (tid == 0) finish_sample(P, c, idx, out_i);
     __syncthreads();
-    reset_tables<GM>(T, c);
   }
   if (tid == 0 && P.totals)
     for (int q = 0; q < KADABRA_NSTAT; ++q)
       if (c.tot[q]) atomicAdd((unsigned long long*)&P.totals[q], (unsigned long long)c.tot[q]);
 }
 
-size_t fast_smem_bytes() {
-  size_t a, b, c, d, e;
-  return fast_smem_layout(&a, &b, &c, &d, &e);
-}
+size_t fast_smem_bytes() { return S_BYTES; }
 
 // ============================================================== stop test
 struct CheckOut {
@@ -1078,24 +1121,26 @@ __global__ void k_philox(uint64_t seed, uint32_t domain, uint32_t j, uint64_t fi
 
 // ============================================================== graph checks, VD
 // error bits: 1 offsets, 2 id range, 4 order/duplicate, 8 self-loop, 16 reverse mismatch
+// One warp per node; lanes check the row's entries in parallel.
 __global__ void k_validate_rows(const int32_t* rp, const int32_t* ci, int32_t n, int64_t m, unsigned* err) {
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = w0; v < n; v += nw) {
     const int32_t a = rp[v], b = rp[v + 1];
     if (a < 0 || b < a || b > m) {
-      atomicOr(err, 1u);
+      if (lane == 0) atomicOr(err, 1u);
       continue;
     }
-    int32_t prev = -1;
-    for (int32_t e = a; e < b; ++e) {
+    unsigned bits = 0;
+    for (int32_t e = a + lane; e < b; e += 32) {
       const int32_t y = ci[e];
-      if (y < 0 || y >= n) {
-        atomicOr(err, 2u);
-        break;
-      }
-      if (y <= prev) atomicOr(err, 4u);
-      if (y == v) atomicOr(err, 8u);
-      prev = y;
+      if (y < 0 || y >= n) bits |= 2u;
+      if (e > a && y <= ci[e - 1]) bits |= 4u;
+      if (y == v) bits |= 8u;
     }
+    bits = __reduce_or_sync(FULL, bits);
+    if (bits && lane == 0) atomicOr(err, bits);
   }
 }
 
@@ -1113,15 +1158,19 @@ __device__ __forceinline__ bool row_has(const int32_t* rp, const int32_t* ci, in
   return false;
 }
 
-// every out-arc (u,y) must appear as in-arc of y (directed) or as (y,u) (undirected)
+// every out-arc (u,y) must appear as in-arc of y (directed) or as (y,u)
+// (undirected); one warp per node u
 __global__ void k_validate_mirror(const int32_t* rp, const int32_t* ci, const int32_t* rrp, const int32_t* rci,
                                   int32_t n, unsigned* err) {
-  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
-    for (int32_t e = rp[u]; e < rp[u + 1]; ++e)
-      if (!row_has(rrp, rci, ci[e], (int32_t)u)) {
-        atomicOr(err, 16u);
-        return;
-      }
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t u = w0; u < n; u += nw) {
+    bool bad = false;
+    for (int32_t e = rp[u] + lane; e < rp[u + 1]; e += 32)
+      if (!row_has(rrp, rci, ci[e], (int32_t)u)) bad = true;
+    if (__any_sync(FULL, bad) && lane == 0) atomicOr(err, 16u);
+  }
 }
 
 __global__ void k_und_degree_key(const int32_t* rp, const int32_t* ci, const int32_t* rrp, const int32_t* rci,
@@ -1219,6 +1268,8 @@ struct kadabra_graph {
   PiEntry* pi_fast = nullptr;
   PiEntry* pi_gm = nullptr;
   int pcap_gm = 0;
+  unsigned char* med_base = nullptr;
+  size_t med_stride = 0;
   unsigned char* gm_base = nullptr;
   size_t gm_stride = 0;
   int gm_hlog = 0;
@@ -1252,9 +1303,9 @@ kadabra_status ensure_workspace(kadabra_graph* g, uint64_t deferred_need) {
   if (!g->ws_ready) {
     KCK(cudaSetDevice(g->device));
     g->smem_fast = fast_smem_bytes();
-    KCK(cudaFuncSetAttribute(k_sample<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g->smem_fast));
+    KCK(cudaFuncSetAttribute(k_sample<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g->smem_fast));
     int per_sm = 0;
-    KCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample<false>, NT, g->smem_fast));
+    KCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample<0>, NT, g->smem_fast));
     if (per_sm < 1) return fail(KADABRA_ERR_CAPACITY, "sampler does not fit on an SM");
     g->grid_fast = g->num_sms * per_sm;
     // global-memory tables for deferred samples: hash of >= 2n slots, lists of n
@@ -1263,7 +1314,8 @@ kadabra_status ensure_workspace(kadabra_graph* g, uint64_t deferred_need) {
     g->pcap_gm = (int)std::min<int64_t>(std::max<int64_t>(g->m, 1024), 1 << 18);
     {
       size_t a, b, c2, d;
-      g->gm_stride = gm_layout(g->gm_hlog, g->gm_lcap, &a, &b, &c2, &d);
+      g->gm_stride = gm_layout(g->gm_hlog, g->gm_lcap, GM_MAXD, &a, &b, &c2, &d);
+      g->med_stride = gm_layout(MED_HLOG, MED_LCAP, MED_MAXD, &a, &b, &c2, &d);
     }
     const size_t per_cta = g->gm_stride + sizeof(PiEntry) * NW * (size_t)g->pcap_gm;
     // deferred samples are rare on small-world graphs; 1 GiB of tables
@@ -1284,6 +1336,10 @@ kadabra_status ensure_workspace(kadabra_graph* g, uint64_t deferred_need) {
     g->gm_base = (unsigned char*)p;
     for (int b = 0; b < g->grid_gm; ++b)
       KCK(cudaMemset(g->gm_base + (size_t)b * g->gm_stride, 0xFF, sizeof(unsigned long long) << g->gm_hlog));
+    KTRY(dev_alloc(g, &p, g->med_stride * g->grid_fast));
+    g->med_base = (unsigned char*)p;
+    for (int b = 0; b < g->grid_fast; ++b)
+      KCK(cudaMemset(g->med_base + (size_t)b * g->med_stride, 0xFF, sizeof(unsigned long long) << MED_HLOG));
     KTRY(dev_alloc(g, &p, sizeof(uint32_t) * (size_t)g->n));
     g->counts = (uint32_t*)p;
     KTRY(dev_alloc(g, &p, sizeof(uint32_t) * (size_t)g->n));
@@ -1331,25 +1387,28 @@ SampleParams base_params(kadabra_graph* g) {
   P.deferred = g->deferred;
   P.deferred_cap = g->deferred_cap;
   P.status = g->status;
+  P.med_base = g->med_base;
+  P.med_stride = g->med_stride;
   P.gm_base = g->gm_base;
   P.gm_stride = g->gm_stride;
   P.gm_hlog = g->gm_hlog;
   P.gm_lcap = g->gm_lcap;
-  P.force_global = (g->flags & KADABRA_FLAG_GLOBAL_TABLES) ? 1 : 0;
+  P.tier_flags = ((g->flags & KADABRA_FLAG_GLOBAL_TABLES) ? TF_ONLY_LARGE : 0) |
+                 ((g->flags & KADABRA_FLAG_MEDIUM_TABLES) ? TF_SKIP_SHARED : 0);
   return P;
 }
 
-// launches the shared-memory sampler and then the global-memory pass for
-// any deferred samples (the second launch exits at once when none are)
+// launches the main sampler grid and then the n-sized-table pass for any
+// samples it queued (that launch exits at once when there are none)
 kadabra_status launch_sampler(kadabra_graph* g, SampleParams P, cudaStream_t st) {
   KCK(cudaMemsetAsync(g->ctr, 0, 4 * sizeof(unsigned long long), st));
   P.pi_base = g->pi_fast;
   P.pcap = FAST_PCAP;
-  k_sample<false><<<g->grid_fast, NT, g->smem_fast, st>>>(P);
+  k_sample<0><<<g->grid_fast, NT, g->smem_fast, st>>>(P);
   KCK(cudaGetLastError());
   P.pi_base = g->pi_gm;
   P.pcap = g->pcap_gm;
-  k_sample<true><<<g->grid_gm, NT, sizeof(Ctl), st>>>(P);
+  k_sample<1><<<g->grid_gm, NT, sizeof(Ctl), st>>>(P);
   KCK(cudaGetLastError());
   return KADABRA_OK;
 }
@@ -1509,7 +1568,7 @@ kadabra_status finish_load(kadabra_graph* g) {
   unsigned* err;
   KCK(cudaMalloc(&err, sizeof(unsigned)));
   KCK(cudaMemset(err, 0, sizeof(unsigned)));
-  const int blocks = std::max(1, std::min(4 * g->num_sms, (g->n + 255) / 256));
+  const int blocks = std::max(1, std::min(16 * g->num_sms, (g->n + 7) / 8));
   k_validate_rows<<<blocks, 256>>>(g->rp, g->ci, g->n, g->m, err);
   if (g->directed) k_validate_rows<<<blocks, 256>>>(g->rrp, g->rci, g->n, g->m, err);
   unsigned h = 0;
@@ -1663,7 +1722,8 @@ void kadabra_free_graph(kadabra_graph* g) {
 
 kadabra_status kadabra_graph_set_flags(kadabra_graph* g, uint32_t flags) {
   if (!g) return fail(KADABRA_ERR_ARG, "graph is NULL");
-  if (flags & ~(uint32_t)KADABRA_FLAG_GLOBAL_TABLES) return fail(KADABRA_ERR_ARG, "unknown flag");
+  if (flags & ~(uint32_t)(KADABRA_FLAG_GLOBAL_TABLES | KADABRA_FLAG_MEDIUM_TABLES))
+    return fail(KADABRA_ERR_ARG, "unknown flag");
   g->flags = flags;
   return KADABRA_OK;
 }

@@ -42,6 +42,7 @@ STAT_NAMES = (
 )
 NSTAT = len(STAT_NAMES)
 FLAG_GLOBAL_TABLES = 1
+FLAG_MEDIUM_TABLES = 2
 
 
 class KadabraError(RuntimeError):

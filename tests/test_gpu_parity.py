@@ -121,10 +121,10 @@ def test_deep_searches_use_global_tables(kd, orc, gg):
     compare_paths(kd, orc, gg.cycle_graph(2001), 2, 0, 0, 300, max_len=1100, tag="cycle2001")
 
 
-def compare_paths_global(kd, orc, g, seed, domain, first, count, max_len=64, tag=""):
+def compare_paths_global(kd, orc, g, seed, domain, first, count, max_len=64, tag="", flag=None):
     G = kd.kadabra_load_csr(g)
     try:
-        G.set_flags(kd.FLAG_GLOBAL_TABLES)
+        G.set_flags(kd.FLAG_GLOBAL_TABLES if flag is None else flag)
         got = kd.kadabra_sample_paths(G, seed, domain, first, count, max_len=max_len)
     finally:
         G.free()
@@ -135,12 +135,33 @@ def compare_paths_global(kd, orc, g, seed, domain, first, count, max_len=64, tag
 @pytest.mark.parametrize("name,make", [s for s in SMALL if s[0] in ("Q6", "drand300", "ba3000", "rmat12", "star30")],
                          ids=["Q6", "drand300", "ba3000", "rmat12", "star30"])
 def test_global_tables_match_oracle(kd, orc, gg, name, make):
-    compare_paths_global(kd, orc, make(gg), 23, 0, 0, 1500, max_len=256, tag=name)
+    g = make(gg)
+    compare_paths_global(kd, orc, g, 23, 0, 0, 1500, max_len=256, tag=name)
+    compare_paths_global(kd, orc, g, 26, 0, 0, 1500, max_len=256, tag=name + "/medium", flag=kd.FLAG_MEDIUM_TABLES)
 
 
 def test_global_tables_er_and_power_law(kd, orc, er2000, chung_lu_1m):
     compare_paths_global(kd, orc, er2000, 24, 0, 0, 3000, tag="er2000")
     compare_paths_global(kd, orc, chung_lu_1m, 25, 0, 777, 400, tag="chung-lu")
+    compare_paths_global(kd, orc, er2000, 27, 1, 0, 3000, tag="er2000/medium", flag=kd.FLAG_MEDIUM_TABLES)
+    compare_paths_global(kd, orc, chung_lu_1m, 28, 0, 5000, 1500, tag="chung-lu/medium",
+                         flag=kd.FLAG_MEDIUM_TABLES)
+
+
+def test_run_with_forced_tiers_matches_plain(kd, er2000):
+    """Whole runs give identical results whichever table tier holds the samples."""
+    out = []
+    for flag in (0, kd.FLAG_MEDIUM_TABLES, kd.FLAG_GLOBAL_TABLES):
+        G = kd.kadabra_load_csr(er2000)
+        try:
+            G.set_flags(flag)
+            r = kd.kadabra_run(G, 0.02, 0.1, 0, 9, check_interval=500)
+        finally:
+            G.free()
+        out.append(r)
+    for r in out[1:]:
+        assert r.tau == out[0].tau and np.array_equal(r.counts, out[0].counts)
+        assert np.array_equal(r.totals, out[0].totals)
 
 
 def test_sample_batch_ragged_and_order_independent(kd, orc, er2000):
