@@ -48,14 +48,27 @@
 namespace {
 
 // ============================================================== constants
-constexpr int NT = 128;            // threads per sampler CTA
+// Tuning constants (overridable at build time with -D for sweeps).
+#ifndef KD_NT
+#define KD_NT 128
+#endif
+#ifndef KD_U
+#define KD_U 4
+#endif
+#ifndef KD_FAST_HLOG
+#define KD_FAST_HLOG 11
+#endif
+#ifndef KD_MIN_BLOCKS
+#define KD_MIN_BLOCKS 1
+#endif
+constexpr int NT = KD_NT;          // threads per sampler CTA
 constexpr int NW = NT / 32;        // warps per sampler CTA
-constexpr int U = 4;               // independent items per thread per step (memory-level parallelism)
+constexpr int U = KD_U;            // independent items per thread per step (memory-level parallelism)
 // three tiers of per-sample tables: a sample starts in shared memory, is
 // retried by the same CTA on its medium global tables if it outgrows them,
 // and only beyond those is deferred to a launch with n-sized tables
-constexpr int FAST_HLOG = 11;      // tier S, shared memory: 2048 hash slots
-constexpr int FAST_LCAP = 1024;    //   level lists: 1024 nodes
+constexpr int FAST_HLOG = KD_FAST_HLOG;        // tier S, shared memory: 2^FAST_HLOG hash slots
+constexpr int FAST_LCAP = 1 << (FAST_HLOG - 1);  //   level lists: half as many nodes
 constexpr int FAST_MAXD = 126;     //   levels per side
 constexpr int MED_HLOG = 15;       // tier M, global memory per CTA: 32768 hash slots
 constexpr int MED_LCAP = 16384;    //   level lists: 16384 nodes
@@ -63,9 +76,6 @@ constexpr int MED_MAXD = 1022;     //   levels per side
 constexpr int GM_MAXD = 65534;     // tier L, global memory, hash >= 2n slots, lists of n
 constexpr int FAST_PCAP = 2048;    // candidate edges per warp, tiers S and M (global memory)
 constexpr unsigned long long EMPTY = ~0ull;
-constexpr uint32_t NONE = 0xFFFFFFFFu;
-constexpr uint32_t SLOT_MASK = 0x7FFFFFFFu;
-constexpr uint32_t SLOT_PENDING = 0x7FFFFFFFu;
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
 // sample flags
@@ -113,20 +123,22 @@ struct PiEntry {
   unsigned long long w;  // sigma_x * sigma_y (exact; overflow flagged)
 };
 
-// Per-sample state.  The hash maps a visited node to (side, list slot); the
-// lists hold one level after another, each sorted by node id, with sigma;
-// lvl holds each side's level bounds in the lists.
+// Per-sample state.  The hash maps a visited node to (side, dist) in hkv
+// and keeps its shortest-path count at the same position in hsig; the
+// level lists hold, level after level, each node and the position of its
+// hash entry; lvl holds each side's level bounds in the lists.
 struct Tables {
-  unsigned long long* hkv;  // (node << 32) | (side << 31 | slot), EMPTY = free
+  unsigned long long* hkv;  // (node << 32) | (side << 31 | dist), EMPTY = free
+  unsigned long long* hsig; // sigma of the node at the same position
   uint32_t hmask;
   int hlog;
   int32_t* lnode;           // level lists: node ids
-  unsigned long long* lsig; // level lists: sigma
+  uint32_t* lpos;           // level lists: hash positions
   int2* pr;                 // frontier: {degree prefix, row start}; lcap+1 entries
   int lcap;
   int* lvl;                 // [side][lo|hi][maxd+2]
   int maxd;
-  PiEntry* pi;              // NW segments of pcap entries
+  PiEntry* pi;              // 2*NW segments of pcap entries (the second half is scratch)
   int pcap;
 };
 
@@ -135,37 +147,26 @@ __device__ __forceinline__ int& lvl_hi(const Tables& T, int side, int d) {
   return T.lvl[(2 * side + 1) * (T.maxd + 2) + d];
 }
 
-__device__ __forceinline__ uint32_t pack_val(int side, uint32_t slot) { return ((uint32_t)side << 31) | slot; }
+__device__ __forceinline__ uint32_t pack_val(int side, int dist) { return ((uint32_t)side << 31) | (uint32_t)dist; }
 __device__ __forceinline__ int val_side(uint32_t v) { return (int)(v >> 31); }
-__device__ __forceinline__ uint32_t val_slot(uint32_t v) { return v & SLOT_MASK; }
 
 __device__ __forceinline__ uint32_t hash_pos(int32_t v, int hlog) {
   return ((uint32_t)v * 2654435761u) >> (32 - hlog);
 }
 
-__device__ __forceinline__ uint32_t tab_find(const Tables& T, int32_t v) {
-  uint32_t pos = hash_pos(v, T.hlog);
-  for (uint32_t k = 0; k <= T.hmask; ++k) {
-    const unsigned long long w = T.hkv[pos];
-    if (w == EMPTY) return NONE;
-    if ((int32_t)(w >> 32) == v) return (uint32_t)w;
-    pos = (pos + 1) & T.hmask;
-  }
-  return NONE;
-}
-
-__device__ __forceinline__ int64_t tab_findpos(const Tables& T, int32_t v) {
+// position of v's entry, or -1
+__device__ __forceinline__ int tab_find_pos(const Tables& T, int32_t v) {
   uint32_t pos = hash_pos(v, T.hlog);
   for (uint32_t k = 0; k <= T.hmask; ++k) {
     const unsigned long long w = T.hkv[pos];
     if (w == EMPTY) return -1;
-    if ((int32_t)(w >> 32) == v) return pos;
+    if ((int32_t)(w >> 32) == v) return (int)pos;
     pos = (pos + 1) & T.hmask;
   }
   return -1;
 }
 
-// 1 = inserted at *pos_out, 0 = already present, -1 = table full
+// 1 = inserted at *pos_out, 0 = already present at *pos_out, -1 = table full
 __device__ __forceinline__ int tab_insert(const Tables& T, int32_t v, uint32_t val, uint32_t* pos_out) {
   const unsigned long long want = ((unsigned long long)(uint32_t)v << 32) | val;
   uint32_t pos = hash_pos(v, T.hlog);
@@ -179,7 +180,10 @@ __device__ __forceinline__ int tab_insert(const Tables& T, int32_t v, uint32_t v
       }
       w = old;
     }
-    if ((int32_t)(w >> 32) == v) return 0;
+    if ((int32_t)(w >> 32) == v) {
+      *pos_out = pos;
+      return 0;
+    }
     pos = (pos + 1) & T.hmask;
   }
   return -1;
@@ -320,16 +324,6 @@ __device__ __forceinline__ long long block_sum64(long long x, long long* tmp) {
   return tot;
 }
 
-__device__ __forceinline__ unsigned long long warp_incl_scan_u64(unsigned long long v) {
-  const int lane = lane_id();
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned long long y = __shfl_up_sync(FULL, v, o);
-    if (lane >= o) v += y;
-  }
-  return v;
-}
-
 // largest p in [0, cnt) with pr[p].x <= e (prefixes non-decreasing, pr[0].x = 0)
 __device__ __forceinline__ int frontier_pos(const int2* pr, int cnt, int e) {
   int lo = 0, hi = cnt;
@@ -393,6 +387,100 @@ __device__ __forceinline__ int block_pick(int N, unsigned long long r, Ctl& c, W
 }
 
 // ============================================================== one sample
+// Scans the arcs of the current frontier level: each warp takes a contiguous
+// slice of the flattened arc range and walks it in windows of 32 arcs, U
+// windows at a time so their loads overlap.  For every window position it
+// calls f(k, ok, p, x, y): ok = the lane holds an arc, p = frontier position
+// of its tail x, y = its head.  All lanes of the warp call f together, in
+// increasing arc order (so f may use warp collectives).
+template <class F>
+__device__ __forceinline__ void scan_level(const Tables& T, int f0, int fcount, int E, const int32_t* cols, F f) {
+  const int lane = lane_id(), wid = warp_id();
+  const int per = (E + NW - 1) / NW;
+  const int c0 = min(E, wid * per), c1 = min(E, c0 + per);
+  int pcur = c0 < c1 ? frontier_pos(T.pr, fcount, c0) : 0;  // warp-uniform
+  for (int base = c0; base < c1; base += 32 * U) {
+    int xs[U], ys[U], ps[U];
+    bool oks[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int wb = base + 32 * k;
+      oks[k] = false;
+      xs[k] = ys[k] = ps[k] = 0;
+      if (wb < c1) {
+        if (T.pr[pcur + 1].x <= wb) pcur = pcur + 1 + frontier_pos(T.pr + pcur + 1, fcount - pcur - 1, wb);
+        const int e = wb + lane;
+        if (e < c1) {
+          int p = pcur;
+          if (T.pr[p + 1].x <= e) p = p + 1 + frontier_pos(T.pr + p + 1, fcount - p - 1, e);
+          const int2 q = T.pr[p];
+          ps[k] = p;
+          xs[k] = T.lnode[f0 + p];
+          ys[k] = __ldg(&cols[q.y + (e - q.x)]);
+          oks[k] = true;
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) f(k, oks[k], ps[k], xs[k], ys[k]);
+  }
+}
+
+// Weighted choice among n items held in any order, in the order of their
+// 64-bit keys (distinct): the item whose key-order prefix interval contains r.
+// Quadratic in n: each thread ranks its items against all others.
+template <class KF, class WF>
+__device__ __forceinline__ int block_pick_by_key(int n, unsigned long long r, Ctl& c, KF key, WF w) {
+  const int tid = threadIdx.x;
+  if (tid == 0) c.pick = -1;
+  __syncthreads();
+  for (int i = tid; i < n; i += NT) {
+    const unsigned long long ki = key(i);
+    const unsigned long long wi = w(i);
+    if (wi == 0) continue;
+    unsigned long long below = 0;
+    for (int j = 0; j < n; ++j)
+      if (key(j) < ki) below += w(j);
+    if (below <= r && r - below < wi) c.pick = i;
+  }
+  __syncthreads();
+  return c.pick;
+}
+
+// Sorts n (key, payload) pairs in global scratch by key (bitonic network,
+// +inf padding past n), then finds the pair whose prefix interval of
+// weights contains r.  For candidate sets too large for the quadratic pick.
+__device__ int block_pick_sorted(PiEntry* buf, int n, unsigned long long r, Ctl& c) {
+  const int tid = threadIdx.x;
+  auto key = [&](int i) { return ((unsigned long long)(uint32_t)buf[i].x << 32) | (uint32_t)buf[i].y; };
+  int P2 = 1;
+  while (P2 < n) P2 <<= 1;
+  for (int k = 2; k <= P2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int q = tid; q < (P2 >> 1); q += NT) {
+        int i, partner;
+        if (j == (k >> 1)) {  // mirror step of block size k
+          i = (q / j) * k + (q % j);
+          partner = i ^ (k - 1);
+        } else {
+          i = (q / j) * (2 * j) + (q % j);
+          partner = i + j;
+        }
+        if (partner < n && key(i) > key(partner)) {
+          const PiEntry a = buf[i];
+          buf[i] = buf[partner];
+          buf[partner] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  return block_pick(n, r, c, [&](int i0, int N, unsigned long long* w) {
+#pragma unroll
+    for (int k = 0; k < U; ++k) w[k] = (i0 + k < N) ? buf[i0 + k].w : 0ull;
+  });
+}
+
 // All threads of the CTA call this with the same idx.  Flags in c.flags tell
 // the caller what happened; the caller resets the tables afterwards.
 __device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& T, Ctl& c, uint64_t idx,
@@ -413,13 +501,15 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& 
     c.stat[KADABRA_STAT_DIST] = -1;
     c.flags = 0;
     c.done = 0;
-    uint32_t pos;
-    if (tab_insert(T, s, pack_val(0, 0), &pos) != 1) c.flags |= F_INTERNAL;
-    if (tab_insert(T, t, pack_val(1, 1), &pos) != 1) c.flags |= F_INTERNAL;
+    uint32_t ps, pt;
+    if (tab_insert(T, s, pack_val(0, 0), &ps) != 1) c.flags |= F_INTERNAL;
+    if (tab_insert(T, t, pack_val(1, 0), &pt) != 1) c.flags |= F_INTERNAL;
+    T.hsig[ps] = 1ull;
+    T.hsig[pt] = 1ull;
     T.lnode[0] = s;
-    T.lsig[0] = 1ull;
+    T.lpos[0] = ps;
     T.lnode[1] = t;
-    T.lsig[1] = 1ull;
+    T.lpos[1] = pt;
     c.nlist = 2;
     lvl_lo(T, 0, 0) = 0;
     lvl_hi(T, 0, 0) = 1;
@@ -451,7 +541,7 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& 
     const int32_t* rowp = side == 0 ? G.rp : G.rrp;
     const int32_t* cols = side == 0 ? G.ci : G.rci;
 
-    // degree prefix and row starts over the (sorted) frontier
+    // degree prefix and row starts over the frontier
     {
       int carry = 0;
       for (int base = 0; base < fcount; base += NT) {
@@ -476,60 +566,35 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& 
     }
     const int E = c.ecount;
 
-    // pass 1: touch test; each warp scans a contiguous slice in order
+    // pass 1: touch test against the other search
     {
-      const int per = (E + NW - 1) / NW;
-      const int c0 = min(E, wid * per), c1 = min(E, c0 + per);
       int npi = 0;
       bool sigma_of = false;
       PiEntry* seg = T.pi + (size_t)wid * T.pcap;
-      // frontier row of the first arc of the current window (warp-uniform)
-      int pcur = c0 < c1 ? frontier_pos(T.pr, fcount, c0) : 0;
-      for (int base = c0; base < c1; base += 32 * U) {
-        int xs[U], ys[U], ps[U];
-#pragma unroll
-        for (int k = 0; k < U; ++k) {
-          const int wb = base + 32 * k;
-          xs[k] = -1;
-          if (wb < c1) {
-            if (T.pr[pcur + 1].x <= wb) pcur = pcur + 1 + frontier_pos(T.pr + pcur + 1, fcount - pcur - 1, wb - 0);
-            const int e = wb + lane;
-            if (e < c1) {
-              int p = pcur;
-              if (T.pr[p + 1].x <= e) p = p + 1 + frontier_pos(T.pr + p + 1, fcount - p - 1, e);
-              const int2 q = T.pr[p];
-              ps[k] = p;
-              xs[k] = T.lnode[f0 + p];
-              ys[k] = __ldg(&cols[q.y + (e - q.x)]);
-            }
+      scan_level(T, f0, fcount, E, cols, [&](int, bool ok, int p, int x, int y) {
+        bool touch = false;
+        unsigned long long wgt = 0;
+        if (ok) {
+          const int pos = tab_find_pos(T, y);
+          if (pos >= 0 && val_side((uint32_t)T.hkv[pos]) != side) {
+            touch = true;
+            const unsigned long long sx = T.hsig[T.lpos[f0 + p]];
+            const unsigned long long sy = T.hsig[pos];
+            wgt = sx * sy;
+            if (__umul64hi(sx, sy) != 0ull) sigma_of = true;
           }
         }
-#pragma unroll
-        for (int k = 0; k < U; ++k) {
-          bool touch = false;
-          unsigned long long wgt = 0;
-          if (xs[k] >= 0) {
-            const uint32_t v = tab_find(T, ys[k]);
-            if (v != NONE && val_side(v) != side) {
-              touch = true;
-              const unsigned long long sx = T.lsig[f0 + ps[k]];
-              const unsigned long long sy = T.lsig[val_slot(v)];
-              wgt = sx * sy;
-              if (__umul64hi(sx, sy) != 0ull) sigma_of = true;
-            }
+        const unsigned m = __ballot_sync(FULL, touch);
+        if (touch) {
+          const int at = npi + __popc(m & ((1u << lane) - 1u));
+          if (at < T.pcap) {
+            seg[at].x = x;
+            seg[at].y = y;
+            seg[at].w = wgt;
           }
-          const unsigned m = __ballot_sync(FULL, touch);
-          if (touch) {
-            const int pos = npi + __popc(m & ((1u << lane) - 1u));
-            if (pos < T.pcap) {
-              seg[pos].x = xs[k];
-              seg[pos].y = ys[k];
-              seg[pos].w = wgt;
-            }
-          }
-          npi += __popc(m);
         }
-      }
+        npi += __popc(m);
+      });
       if (__any_sync(FULL, sigma_of) && lane == 0) atomicOr(&c.flags, F_SIGMA);
       if (lane == 0) {
         c.npi[wid] = npi;
@@ -549,116 +614,85 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& 
     if (c.flags) return;
     if (c.done) break;
 
-    // pass 2: insert the nodes of the next level
+    // pass 2: the next level.  The first discoverer of an unvisited head y
+    // publishes (y, side, dist) with one CAS and appends y to the level
+    // list; every discoverer adds sigma_x to the sigma field of y's hash
+    // entry (zero until then), so the order of discoveries does not matter.
     const int dnew = c.depth[side] + 1;
     if (dnew > T.maxd) {
       if (tid == 0) c.flags |= F_CAP;
       __syncthreads();
       return;
     }
-    const int list_before = c.list_before;
-    for (int e = tid; e < E; e += NT) {
-      const int p = frontier_pos(T.pr, fcount, e);
-      const int2 q = T.pr[p];
-      const int y = __ldg(&cols[q.y + (e - q.x)]);
-      uint32_t pos;
-      const int r = tab_insert(T, y, pack_val(side, SLOT_PENDING), &pos);
-      if (r == 1) {
-        const int slot = atomicAdd(&c.nlist, 1);
-        if (slot < T.lcap) {
-          T.lnode[slot] = y;
-          T.lsig[slot] = 0ull;
-          T.hkv[pos] = ((unsigned long long)(uint32_t)y << 32) | pack_val(side, (uint32_t)slot);
-        } else {
-          atomicOr(&c.flags, F_CAP);
-        }
-      } else if (r < 0) {
-        atomicOr(&c.flags, F_CAP);
-      }
-    }
-    __syncthreads();
-    if (c.flags) return;
-
-    // pass 3: sigma of the new level (Brandes-style accumulation)
-    long long hits = 0;
+    long long hits = 0, fresh = 0, cost = 0;
     {
-      bool of = false;
-      for (int e = tid; e < E; e += NT) {
-        const int p = frontier_pos(T.pr, fcount, e);
-        const int2 q = T.pr[p];
-        const int y = __ldg(&cols[q.y + (e - q.x)]);
-        const uint32_t v = tab_find(T, y);
-        if (v != NONE && val_side(v) == side && (int)val_slot(v) >= list_before) {
-          const unsigned long long add = T.lsig[f0 + p];
-          const unsigned long long old = atomicAdd(&T.lsig[val_slot(v)], add);
-          if (old + add < old) of = true;
-          ++hits;
+      bool of = false, cap = false;
+      const uint32_t want_val = pack_val(side, dnew);
+      const volatile int* nlist_now = &c.nlist;
+      scan_level(T, f0, fcount, E, cols, [&](int, bool ok, int p, int, int y) {
+        if (!ok || cap) return;
+        const unsigned long long add = T.hsig[T.lpos[f0 + p]];
+        uint32_t pos = hash_pos(y, T.hlog);
+        for (uint32_t k = 0; k <= T.hmask; ++k) {
+          unsigned long long w = T.hkv[pos];
+          if (w == EMPTY) {
+            // stop inserting once the lists are full, so the table never
+            // fills beyond lcap + NT keys and probes stay short
+            if (*nlist_now >= T.lcap) {
+              cap = true;
+              return;
+            }
+            const unsigned long long want = ((unsigned long long)(uint32_t)y << 32) | want_val;
+            const unsigned long long old = atomicCAS(&T.hkv[pos], EMPTY, want);
+            if (old == EMPTY) {
+              const int slot = atomicAdd(&c.nlist, 1);
+              if (slot >= T.lcap) {
+                cap = true;
+                return;
+              }
+              T.lnode[slot] = y;
+              T.lpos[slot] = pos;
+              ++fresh;
+              cost += __ldg(&rowp[y + 1]) - __ldg(&rowp[y]);
+              const unsigned long long o = atomicAdd(&T.hsig[pos], add);
+              if (o + add < o) of = true;
+              return;
+            }
+            w = old;
+          }
+          if ((int32_t)(w >> 32) == y) {
+            if ((uint32_t)w == want_val) {  // also discovered at this level
+              ++hits;
+              const unsigned long long o = atomicAdd(&T.hsig[pos], add);
+              if (o + add < o) of = true;
+            }
+            return;
+          }
+          pos = (pos + 1) & T.hmask;
         }
-      }
+        cap = true;  // table full
+      });
       if (of) atomicOr(&c.flags, F_SIGMA);
+      if (cap) atomicOr(&c.flags, F_CAP);
     }
     hits = block_sum64(hits, c.scan_tmp64);
+    fresh = block_sum64(fresh, c.scan_tmp64);
+    cost = block_sum64(cost, c.scan_tmp64);
     if (c.flags) return;
-    const int nb = list_before, cnt = c.nlist - list_before;
-    if (cnt == 0) {  // frontier exhausted: s and t are not connected
+    if (fresh == 0) {  // frontier exhausted: s and t are not connected
       if (tid == 0) c.done = 2;
       __syncthreads();
       break;
     }
-
-    // sort the new level by node id (bitonic, +inf padding past cnt)
-    {
-      int P2 = 1;
-      while (P2 < cnt) P2 <<= 1;
-      for (int k = 2; k <= P2; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-          for (int q = tid; q < (P2 >> 1); q += NT) {
-            int i, partner;
-            if (j == (k >> 1)) {  // mirror step of block size k
-              i = (q / j) * k + (q % j);
-              partner = i ^ (k - 1);
-            } else {
-              i = (q / j) * (2 * j) + (q % j);
-              partner = i + j;
-            }
-            if (partner < cnt) {
-              const int a = T.lnode[nb + i], b = T.lnode[nb + partner];
-              if (a > b) {
-                T.lnode[nb + i] = b;
-                T.lnode[nb + partner] = a;
-                const unsigned long long sa = T.lsig[nb + i];
-                T.lsig[nb + i] = T.lsig[nb + partner];
-                T.lsig[nb + partner] = sa;
-              }
-            }
-          }
-          __syncthreads();
-        }
-      }
-    }
-    // point the hash entries at the sorted slots; degree sum of the new frontier
-    long long cost = 0;
-    for (int i = tid; i < cnt; i += NT) {
-      const int y = T.lnode[nb + i];
-      const int64_t pos = tab_findpos(T, y);
-      if (pos < 0) {
-        atomicOr(&c.flags, F_INTERNAL);
-      } else {
-        T.hkv[pos] = ((unsigned long long)(uint32_t)y << 32) | pack_val(side, (uint32_t)(nb + i));
-      }
-      cost += __ldg(&rowp[y + 1]) - __ldg(&rowp[y]);
-    }
-    cost = block_sum64(cost, c.scan_tmp64);
     if (tid == 0) {
-      lvl_lo(T, side, dnew) = nb;
-      lvl_hi(T, side, dnew) = nb + cnt;
+      lvl_lo(T, side, dnew) = c.list_before;
+      lvl_hi(T, side, dnew) = c.nlist;
       c.depth[side] = dnew;
       c.cost[side] = cost;
-      c.stat[KADABRA_STAT_NEW] += cnt;
-      c.stat[KADABRA_STAT_SIGMA_ADDS] += hits - cnt;
+      c.stat[KADABRA_STAT_NEW] += fresh;
+      c.stat[KADABRA_STAT_SIGMA_ADDS] += hits;
     }
     __syncthreads();
-    if (c.flags) return;
   }
   if (c.done == 0) {  // loop bound reached (cannot happen within maxd levels)
     if (tid == 0) c.flags |= F_CAP;
@@ -668,6 +702,7 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& 
   if (c.done == 2) return;  // disconnected: no hits
 
   // ------------------------------------------------ candidate-edge choice
+  // Candidates are ordered by (x, y), x on the expanding side.
   {
     unsigned long long lo = 0, hi = 0;
     const int npi = c.npi[wid];
@@ -703,65 +738,61 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& 
     } else {
       c.stat[KADABRA_STAT_SIGMA_LO] = (long long)(lo & 0xFFFFFFFFull);
       c.stat[KADABRA_STAT_SIGMA_HI] = (long long)(lo >> 32);
-      const unsigned long long r = below128(draw(P.seed, P.domain, idx, 1), lo);
-      unsigned long long acc = 0;
-      c.sel_warp = -1;
-      for (int w = 0; w < NW; ++w) {
-        if (r < acc + c.wsum[w]) {
-          c.sel_warp = w;
-          c.sel_off = r - acc;
-          break;
-        }
-        acc += c.wsum[w];
-      }
-      if (c.sel_warp < 0) c.flags |= F_INTERNAL;
+      c.r = below128(draw(P.seed, P.domain, idx, 1), lo);
     }
+    int acc = 0;  // segment starts of the flat candidate index
+    for (int w = 0; w < NW; ++w) {
+      const int n_w = c.npi[w];
+      c.npi[w] = acc;
+      acc += n_w;
+    }
+    c.ecount = acc;
   }
   __syncthreads();
   if (c.flags) return;
-  if (wid == c.sel_warp) {
-    const int npi = c.npi[wid];
-    const PiEntry* seg = T.pi + (size_t)wid * T.pcap;
-    const unsigned long long target = c.sel_off;
-    unsigned long long run = 0;
-    bool found = false;
-    for (int base = 0; base < npi && !found; base += 32) {
-      const int i = base + lane;
-      const unsigned long long w = i < npi ? seg[i].w : 0ull;
-      const unsigned long long incl = warp_incl_scan_u64(w);
-      const bool hit = (i < npi) && (run + incl > target);
-      const unsigned m = __ballot_sync(FULL, hit);
-      if (m) {
-        const int first = __ffs(m) - 1;
-        if (lane == first) {
-          const PiEntry pe = seg[i];
-          if (c.side == 0) {
-            c.cv = pe.x;
-            c.cw = pe.y;
-          } else {
-            c.cv = pe.y;
-            c.cw = pe.x;
-          }
-        }
-        found = true;
-      }
-      run += __shfl_sync(FULL, incl, 31);
+  {
+    const int total = c.ecount;
+    // gather the candidates into the scratch half of this CTA's buffer
+    PiEntry* buf = T.pi + (size_t)NW * T.pcap;
+    for (int w = 0; w < NW; ++w) {
+      const int a = c.npi[w], b = (w + 1 < NW) ? c.npi[w + 1] : total;
+      for (int i = a + tid; i < b; i += NT) buf[i] = T.pi[(size_t)w * T.pcap + (i - a)];
     }
-    if (!found && lane == 0) atomicOr(&c.flags, F_INTERNAL);
+    __syncthreads();
+    int pick;
+    if (total <= 128) {
+      pick = block_pick_by_key(
+          total, c.r, c, [&](int i) { return ((unsigned long long)(uint32_t)buf[i].x << 32) | (uint32_t)buf[i].y; },
+          [&](int i) { return buf[i].w; });
+    } else {
+      pick = block_pick_sorted(buf, total, c.r, c);
+    }
+    if (pick < 0) {
+      if (tid == 0) c.flags |= F_INTERNAL;
+      __syncthreads();
+      return;
+    }
+    if (tid == 0) {
+      const PiEntry pe = buf[pick];
+      if (c.side == 0) {
+        c.cv = pe.x;
+        c.cw = pe.y;
+      } else {
+        c.cv = pe.y;
+        c.cw = pe.x;
+      }
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  if (c.flags) return;
 
   // ------------------------------------------------ backtracking
   // The candidate edge joins the two current frontiers, so v is at depth[0]
   // on the s side and w at depth[1] on the t side.
   const int dv = c.depth[0], dw = c.depth[1];
   if (tid == 0) {
-    const uint32_t a = tab_find(T, c.cv), b = tab_find(T, c.cw);
-    const bool ok_a = a != NONE && val_side(a) == 0 && (int)val_slot(a) >= lvl_lo(T, 0, dv) &&
-                      (int)val_slot(a) < lvl_hi(T, 0, dv);
-    const bool ok_b = b != NONE && val_side(b) == 1 && (int)val_slot(b) >= lvl_lo(T, 1, dw) &&
-                      (int)val_slot(b) < lvl_hi(T, 1, dw);
+    const int a = tab_find_pos(T, c.cv), b = tab_find_pos(T, c.cw);
+    const bool ok_a = a >= 0 && (uint32_t)T.hkv[a] == pack_val(0, dv);
+    const bool ok_b = b >= 0 && (uint32_t)T.hkv[b] == pack_val(1, dw);
     if (!ok_a || !ok_b) c.flags |= F_INTERNAL;
   }
   __syncthreads();
@@ -793,26 +824,51 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& 
     const int32_t* fcol = half == 0 ? G.ci : G.rci;
     while (dx > 0) {
       const int plo = lvl_lo(T, half, dx - 1), phi = lvl_hi(T, half, dx - 1);
+      const uint32_t want = pack_val(half, dx - 1);
       const int r0 = __ldg(&brow[x]), deg = __ldg(&brow[x + 1]) - r0;
       if (tid == 0) {
-        const uint32_t vx = tab_find(T, x);
-        if (vx == NONE || (int)val_slot(vx) >= T.lcap) {
+        const int px = tab_find_pos(T, x);
+        if (px < 0) {
           c.flags |= F_INTERNAL;
           c.r = 0;
         } else {
-          c.r = below128(draw(P.seed, P.domain, idx, j), T.lsig[val_slot(vx)]);
+          c.r = below128(draw(P.seed, P.domain, idx, j), T.hsig[px]);
         }
         // scan whichever is shorter: the row of x, or the previous level
-        // (sorted, so its order is the row's order restricted to it)
         c.mode = ((long long)(phi - plo) * 16 < (long long)deg) ? 1 : 0;
+        c.ecount = 0;  // candidates found in the previous level (mode 1)
       }
       ++j;
       __syncthreads();
       if (c.flags) return;
       const unsigned long long r = c.r;
-      int pick;
-      if (c.mode == 0) {
-        pick = block_pick(deg, r, c, [&](int i0, int N, unsigned long long* w) {
+      if (c.mode == 1) {
+        // previous-level nodes adjacent to x, collected as (node, hash position)
+        for (int i = plo + tid; i < phi; i += NT) {
+          const int y = T.lnode[i];
+          const int a = __ldg(&frow[y]), b = __ldg(&frow[y + 1]);
+          const int at = lower_bound_row(fcol, a, b, x);
+          if (at < b && __ldg(&fcol[at]) == x) {
+            const int q = atomicAdd(&c.ecount, 1);
+            if (q < T.lcap) T.pr[q] = make_int2(y, (int)T.lpos[i]);
+          }
+        }
+        __syncthreads();
+        if (c.ecount > min(T.lcap, 128)) {
+          if (tid == 0) c.mode = 0;  // many predecessors: scan the row instead
+          __syncthreads();
+        }
+      }
+      int y_pick = -1, pos_pick = 0;
+      if (c.mode == 1) {
+        const int nc = c.ecount;
+        const int pick = block_pick_by_key(
+            nc, r, c, [&](int i) { return (unsigned long long)(uint32_t)T.pr[i].x; },
+            [&](int i) { return T.hsig[T.pr[i].y]; });
+        if (pick >= 0) y_pick = T.pr[pick].x;
+        if (tid == 0 && pick >= 0) pos_pick = lower_bound_row(bcol, r0, r0 + deg, y_pick) - r0;
+      } else {
+        const int pick = block_pick(deg, r, c, [&](int i0, int N, unsigned long long* w) {
           int ys[U];
 #pragma unroll
           for (int k = 0; k < U; ++k) ys[k] = (i0 + k < N) ? __ldg(&bcol[r0 + i0 + k]) : -1;
@@ -820,47 +876,29 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& 
           for (int k = 0; k < U; ++k) {
             w[k] = 0;
             if (ys[k] >= 0) {
-              const uint32_t v = tab_find(T, ys[k]);
-              const int sl = (int)val_slot(v);
-              if (v != NONE && val_side(v) == half && sl >= plo && sl < phi) w[k] = T.lsig[sl];
+              const int pos = tab_find_pos(T, ys[k]);
+              if (pos >= 0 && (uint32_t)T.hkv[pos] == want) w[k] = T.hsig[pos];
             }
           }
         });
-      } else {
-        pick = block_pick(phi - plo, r, c, [&](int i0, int N, unsigned long long* w) {
-#pragma unroll
-          for (int k = 0; k < U; ++k) {
-            w[k] = 0;
-            if (i0 + k < N) {
-              const int y = T.lnode[plo + i0 + k];
-              const int a = __ldg(&frow[y]), b = __ldg(&frow[y + 1]);
-              const int at = lower_bound_row(fcol, a, b, x);
-              if (at < b && __ldg(&fcol[at]) == x) w[k] = T.lsig[plo + i0 + k];
-            }
-          }
-        });
+        if (pick >= 0) {
+          y_pick = __ldg(&bcol[r0 + pick]);
+          pos_pick = pick;
+        }
       }
-      if (pick < 0) {
+      if (y_pick < 0) {
         if (tid == 0) c.flags |= F_INTERNAL;
         __syncthreads();
         return;
       }
       if (tid == 0) {
-        int y, pos;
-        if (c.mode == 0) {
-          pos = pick;
-          y = __ldg(&bcol[r0 + pick]);
-        } else {
-          y = T.lnode[plo + pick];
-          pos = lower_bound_row(bcol, r0, r0 + deg, y) - r0;
-        }
-        c.next_x = y;
-        c.stat[KADABRA_STAT_BT_SCANNED] += pos + 1;
+        c.next_x = y_pick;
+        c.stat[KADABRA_STAT_BT_SCANNED] += pos_pick + 1;
         const int dn = dx - 1;
-        if (dn > 0 && P.counts) atomicAdd(&P.counts[y], 1u);
+        if (dn > 0 && P.counts) atomicAdd(&P.counts[y_pick], 1u);
         if (want_path) {
           const int at = half == 0 ? dn : (dv + 1) + (dw - dn);
-          if (at < P.max_len) P.paths[out_i * (int64_t)P.max_len + at] = y;
+          if (at < P.max_len) P.paths[out_i * (int64_t)P.max_len + at] = y_pick;
         }
       }
       __syncthreads();
@@ -871,21 +909,25 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& 
   }
 }
 
-// Clears the hash entries of the last sample: the whole table (shared memory,
-// cheaper than locating the entries, or after a capacity failure that may
-// have left entries outside the lists), else only the listed nodes' entries.
+// Clears what the last sample left in the hash table (key and sigma of every
+// entry it inserted): the whole table in shared memory (cheaper than
+// locating the entries) or after a capacity failure (entries beyond the
+// lists), else the entries at the positions the lists recorded.
 __device__ void reset_tables(const Tables& T, Ctl& c, bool whole) {
   const int tid = threadIdx.x;
   if (whole || (c.flags & F_CAP)) {
-    for (uint32_t i = tid; i <= T.hmask; i += NT) T.hkv[i] = EMPTY;
-    __syncthreads();
-    return;
+    for (uint32_t i = tid; i <= T.hmask; i += NT) {
+      T.hkv[i] = EMPTY;
+      T.hsig[i] = 0ull;
+    }
+  } else {
+    const int nl = min(c.nlist, T.lcap);
+    for (int i = tid; i < nl; i += NT) {
+      const uint32_t pos = T.lpos[i];
+      T.hkv[pos] = EMPTY;
+      T.hsig[pos] = 0ull;
+    }
   }
-  const int nl = min(c.nlist, T.lcap);
-  for (int i = tid; i < nl; i += NT) T.pr[i].x = (int32_t)tab_findpos(T, T.lnode[i]);
-  __syncthreads();
-  for (int i = tid; i < nl; i += NT)
-    if (T.pr[i].x >= 0) T.hkv[T.pr[i].x] = EMPTY;
   __syncthreads();
 }
 
@@ -896,28 +938,29 @@ __device__ __noinline__ void run_sample_global(const SampleParams& P, const Tabl
 }
 
 // layout of one CTA's tables in global memory (tiers M and L)
-__host__ __device__ inline size_t gm_layout(int hlog, int lcap, int maxd, size_t* off_lsig, size_t* off_pr,
-                                            size_t* off_lnode, size_t* off_lvl) {
-  size_t o = sizeof(unsigned long long) << hlog;
-  *off_lsig = o;
-  o += sizeof(unsigned long long) * (size_t)lcap;
+__host__ __device__ inline size_t gm_layout(int hlog, int lcap, int maxd, size_t* off_pr, size_t* off_lnode,
+                                            size_t* off_lpos, size_t* off_lvl) {
+  size_t o = (2 * sizeof(unsigned long long)) << hlog;  // hkv, then hsig
   *off_pr = o;
   o += sizeof(int2) * ((size_t)lcap + 1);
   *off_lnode = o;
   o += sizeof(int32_t) * (size_t)lcap;
+  *off_lpos = o;
+  o += sizeof(uint32_t) * (size_t)lcap;
   *off_lvl = o;
   o += sizeof(int) * 4 * (size_t)(maxd + 2);
   return (o + 255) & ~size_t(255);
 }
 
 __device__ inline Tables gm_tables(unsigned char* base, int hlog, int lcap, int maxd) {
-  size_t o_lsig, o_pr, o_lnode, o_lvl;
-  gm_layout(hlog, lcap, maxd, &o_lsig, &o_pr, &o_lnode, &o_lvl);
+  size_t o_pr, o_lnode, o_lpos, o_lvl;
+  gm_layout(hlog, lcap, maxd, &o_pr, &o_lnode, &o_lpos, &o_lvl);
   Tables T;
   T.hkv = reinterpret_cast<unsigned long long*>(base);
-  T.lsig = reinterpret_cast<unsigned long long*>(base + o_lsig);
+  T.hsig = reinterpret_cast<unsigned long long*>(base + (sizeof(unsigned long long) << hlog));
   T.pr = reinterpret_cast<int2*>(base + o_pr);
   T.lnode = reinterpret_cast<int32_t*>(base + o_lnode);
+  T.lpos = reinterpret_cast<uint32_t*>(base + o_lpos);
   T.lvl = reinterpret_cast<int*>(base + o_lvl);
   T.hlog = hlog;
   T.hmask = (1u << hlog) - 1u;
@@ -928,10 +971,11 @@ __device__ inline Tables gm_tables(unsigned char* base, int hlog, int lcap, int 
 
 // shared-memory layout of the main sampler (tier S)
 constexpr size_t S_OFF_HKV = (sizeof(Ctl) + 15) & ~size_t(15);
-constexpr size_t S_OFF_LSIG = S_OFF_HKV + (sizeof(unsigned long long) << FAST_HLOG);
-constexpr size_t S_OFF_PR = S_OFF_LSIG + sizeof(unsigned long long) * FAST_LCAP;
+constexpr size_t S_OFF_HSIG = S_OFF_HKV + (sizeof(unsigned long long) << FAST_HLOG);
+constexpr size_t S_OFF_PR = S_OFF_HSIG + (sizeof(unsigned long long) << FAST_HLOG);
 constexpr size_t S_OFF_LNODE = S_OFF_PR + sizeof(int2) * (FAST_LCAP + 1);
-constexpr size_t S_OFF_LVL = S_OFF_LNODE + sizeof(int32_t) * FAST_LCAP;
+constexpr size_t S_OFF_LPOS = S_OFF_LNODE + sizeof(int32_t) * FAST_LCAP;
+constexpr size_t S_OFF_LVL = S_OFF_LPOS + sizeof(uint32_t) * FAST_LCAP;
 constexpr size_t S_BYTES = S_OFF_LVL + sizeof(int) * 4 * (FAST_MAXD + 2);
 
 // flags of SampleParams::tier_flags
@@ -974,34 +1018,38 @@ __device__ void clear_path_row(const SampleParams& P, int64_t out_i) {
 // global tables (tier M); beyond those it is queued for MODE 1.
 // MODE 1: the queued samples on n-sized global tables (tier L).
 template <int MODE>
-__global__ void __launch_bounds__(NT) k_sample(SampleParams P) {
+__global__ void __launch_bounds__(NT, KD_MIN_BLOCKS) k_sample(SampleParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   Ctl& c = *reinterpret_cast<Ctl*>(smem);
   Tables TS, TM;
   if (MODE == 0) {
     TS.hkv = reinterpret_cast<unsigned long long*>(smem + S_OFF_HKV);
-    TS.lsig = reinterpret_cast<unsigned long long*>(smem + S_OFF_LSIG);
+    TS.hsig = reinterpret_cast<unsigned long long*>(smem + S_OFF_HSIG);
     TS.pr = reinterpret_cast<int2*>(smem + S_OFF_PR);
     TS.lnode = reinterpret_cast<int32_t*>(smem + S_OFF_LNODE);
+    TS.lpos = reinterpret_cast<uint32_t*>(smem + S_OFF_LPOS);
     TS.lvl = reinterpret_cast<int*>(smem + S_OFF_LVL);
     TS.hlog = FAST_HLOG;
     TS.hmask = (1u << FAST_HLOG) - 1u;
     TS.lcap = FAST_LCAP;
     TS.maxd = FAST_MAXD;
-    TS.pi = P.pi_base + (size_t)blockIdx.x * NW * P.pcap;
+    TS.pi = P.pi_base + (size_t)blockIdx.x * 2 * NW * P.pcap;
     TS.pcap = P.pcap;
     TM = gm_tables(P.med_base + (size_t)blockIdx.x * P.med_stride, MED_HLOG, MED_LCAP, MED_MAXD);
     TM.pi = TS.pi;
     TM.pcap = TS.pcap;
   } else {
     TM = gm_tables(P.gm_base + (size_t)blockIdx.x * P.gm_stride, P.gm_hlog, P.gm_lcap, GM_MAXD);
-    TM.pi = P.pi_base + (size_t)blockIdx.x * NW * P.pcap;
+    TM.pi = P.pi_base + (size_t)blockIdx.x * 2 * NW * P.pcap;
     TM.pcap = P.pcap;
   }
 
   const int tid = threadIdx.x;
   if (MODE == 0)
-    for (uint32_t i = tid; i <= TS.hmask; i += NT) TS.hkv[i] = EMPTY;
+    for (uint32_t i = tid; i <= TS.hmask; i += NT) {
+      TS.hkv[i] = EMPTY;
+      TS.hsig[i] = 0ull;
+    }
   if (tid == 0) {
     for (int k = 0; k < KADABRA_NSTAT; ++k) c.tot[k] = 0;
     c.ntotal = MODE == 1 ? min(P.ctr[2], (unsigned long long)P.deferred_cap) : P.count;
@@ -1317,7 +1365,7 @@ kadabra_status ensure_workspace(kadabra_graph* g, uint64_t deferred_need) {
       g->gm_stride = gm_layout(g->gm_hlog, g->gm_lcap, GM_MAXD, &a, &b, &c2, &d);
       g->med_stride = gm_layout(MED_HLOG, MED_LCAP, MED_MAXD, &a, &b, &c2, &d);
     }
-    const size_t per_cta = g->gm_stride + sizeof(PiEntry) * NW * (size_t)g->pcap_gm;
+    const size_t per_cta = g->gm_stride + sizeof(PiEntry) * 2 * NW * (size_t)g->pcap_gm;
     // deferred samples are rare on small-world graphs; 1 GiB of tables
     // keeps at least a few CTAs busy on them
     const size_t budget = (size_t)1 << 30;
@@ -1328,16 +1376,18 @@ kadabra_status ensure_workspace(kadabra_graph* g, uint64_t deferred_need) {
     KTRY(dev_alloc(g, &p, sizeof(int32_t)));
     g->status = (int32_t*)p;
     KCK(cudaMemset(g->status, 0, sizeof(int32_t)));
-    KTRY(dev_alloc(g, &p, sizeof(PiEntry) * NW * (size_t)FAST_PCAP * g->grid_fast));
+    KTRY(dev_alloc(g, &p, sizeof(PiEntry) * 2 * NW * (size_t)FAST_PCAP * g->grid_fast));
     g->pi_fast = (PiEntry*)p;
-    KTRY(dev_alloc(g, &p, sizeof(PiEntry) * NW * (size_t)g->pcap_gm * g->grid_gm));
+    KTRY(dev_alloc(g, &p, sizeof(PiEntry) * 2 * NW * (size_t)g->pcap_gm * g->grid_gm));
     g->pi_gm = (PiEntry*)p;
     KTRY(dev_alloc(g, &p, g->gm_stride * g->grid_gm));
     g->gm_base = (unsigned char*)p;
-    for (int b = 0; b < g->grid_gm; ++b)
+    KCK(cudaMemset(g->gm_base, 0, g->gm_stride * g->grid_gm));
+    for (int b = 0; b < g->grid_gm; ++b)  // every key word EMPTY (sigma stays 0)
       KCK(cudaMemset(g->gm_base + (size_t)b * g->gm_stride, 0xFF, sizeof(unsigned long long) << g->gm_hlog));
     KTRY(dev_alloc(g, &p, g->med_stride * g->grid_fast));
     g->med_base = (unsigned char*)p;
+    KCK(cudaMemset(g->med_base, 0, g->med_stride * g->grid_fast));
     for (int b = 0; b < g->grid_fast; ++b)
       KCK(cudaMemset(g->med_base + (size_t)b * g->med_stride, 0xFF, sizeof(unsigned long long) << MED_HLOG));
     KTRY(dev_alloc(g, &p, sizeof(uint32_t) * (size_t)g->n));
