@@ -50,16 +50,16 @@ namespace {
 // ============================================================== constants
 // Tuning constants (overridable at build time with -D for sweeps).
 #ifndef KD_NT
-#define KD_NT 128
+#define KD_NT 256
 #endif
 #ifndef KD_U
-#define KD_U 4
+#define KD_U 2
 #endif
 #ifndef KD_FAST_HLOG
-#define KD_FAST_HLOG 11
+#define KD_FAST_HLOG 12
 #endif
 #ifndef KD_MIN_BLOCKS
-#define KD_MIN_BLOCKS 1
+#define KD_MIN_BLOCKS 3
 #endif
 constexpr int NT = KD_NT;          // threads per sampler CTA
 constexpr int NW = NT / 32;        // warps per sampler CTA
@@ -69,7 +69,7 @@ constexpr int U = KD_U;            // independent items per thread per step (mem
 // and only beyond those is deferred to a launch with n-sized tables
 constexpr int FAST_HLOG = KD_FAST_HLOG;        // tier S, shared memory: 2^FAST_HLOG hash slots
 constexpr int FAST_LCAP = 1 << (FAST_HLOG - 1);  //   level lists: half as many nodes
-constexpr int FAST_MAXD = 126;     //   levels per side
+constexpr int FAST_MAXD = 126;     //   levels per side (the packed entry's dist field)
 constexpr int MED_HLOG = 15;       // tier M, global memory per CTA: 32768 hash slots
 constexpr int MED_LCAP = 16384;    //   level lists: 16384 nodes
 constexpr int MED_MAXD = 1022;     //   levels per side
@@ -150,6 +150,46 @@ __device__ __forceinline__ int& lvl_hi(const Tables& T, int side, int d) {
 __device__ __forceinline__ uint32_t pack_val(int side, int dist) { return ((uint32_t)side << 31) | (uint32_t)dist; }
 __device__ __forceinline__ int val_side(uint32_t v) { return (int)(v >> 31); }
 
+// Two entry formats.  Split (tiers M, L): the hkv word is
+// node << 32 | side << 31 | dist and sigma sits in hsig at the same
+// position.  Packed (tier S): one word node << 32 | side << 31 | dist << 24 |
+// sigma, with dist < 128 and sigma < 2^24; a sigma that would not fit sends
+// the sample on to the split tiers, so results do not depend on the format.
+constexpr unsigned long long PK_SIG_MASK = (1ull << 24) - 1;
+
+template <bool PK>
+__device__ __forceinline__ uint32_t ent_val(unsigned long long w) {
+  if (PK) {
+    const uint32_t lo = (uint32_t)w;
+    return (lo & 0x80000000u) | ((lo >> 24) & 0x7Fu);
+  }
+  return (uint32_t)w;
+}
+
+template <bool PK>
+__device__ __forceinline__ unsigned long long ent_sig(const Tables& T, unsigned long long w, uint32_t pos) {
+  return PK ? (w & PK_SIG_MASK) : T.hsig[pos];
+}
+
+// the word a first discoverer publishes (packed: with its sigma included)
+template <bool PK>
+__device__ __forceinline__ unsigned long long ent_word(int32_t node, uint32_t val, unsigned long long sig0) {
+  const unsigned long long hi = (unsigned long long)(uint32_t)node << 32;
+  if (PK) return hi | (val & 0x80000000u) | ((unsigned long long)(val & 0x7Fu) << 24) | sig0;
+  return hi | val;
+}
+
+// adds to a node's sigma; returns false if the sum no longer fits the format
+template <bool PK>
+__device__ __forceinline__ bool ent_add(const Tables& T, uint32_t pos, unsigned long long add) {
+  if (PK) {
+    const unsigned long long o = atomicAdd(&T.hkv[pos], add);
+    return (o & PK_SIG_MASK) + add <= PK_SIG_MASK;
+  }
+  const unsigned long long o = atomicAdd(&T.hsig[pos], add);
+  return o + add >= o;
+}
+
 __device__ __forceinline__ uint32_t hash_pos(int32_t v, int hlog) {
   return ((uint32_t)v * 2654435761u) >> (32 - hlog);
 }
@@ -167,8 +207,7 @@ __device__ __forceinline__ int tab_find_pos(const Tables& T, int32_t v) {
 }
 
 // 1 = inserted at *pos_out, 0 = already present at *pos_out, -1 = table full
-__device__ __forceinline__ int tab_insert(const Tables& T, int32_t v, uint32_t val, uint32_t* pos_out) {
-  const unsigned long long want = ((unsigned long long)(uint32_t)v << 32) | val;
+__device__ __forceinline__ int tab_insert(const Tables& T, int32_t v, unsigned long long want, uint32_t* pos_out) {
   uint32_t pos = hash_pos(v, T.hlog);
   for (uint32_t k = 0; k <= T.hmask; ++k) {
     unsigned long long w = T.hkv[pos];
@@ -483,6 +522,7 @@ __device__ int block_pick_sorted(PiEntry* buf, int n, unsigned long long r, Ctl&
 
 // All threads of the CTA call this with the same idx.  Flags in c.flags tell
 // the caller what happened; the caller resets the tables afterwards.
+template <bool PK>
 __device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& T, Ctl& c, uint64_t idx,
                                            int64_t out_i) {
   const int tid = threadIdx.x, lane = lane_id(), wid = warp_id();
@@ -502,10 +542,12 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& 
     c.flags = 0;
     c.done = 0;
     uint32_t ps, pt;
-    if (tab_insert(T, s, pack_val(0, 0), &ps) != 1) c.flags |= F_INTERNAL;
-    if (tab_insert(T, t, pack_val(1, 0), &pt) != 1) c.flags |= F_INTERNAL;
-    T.hsig[ps] = 1ull;
-    T.hsig[pt] = 1ull;
+    if (tab_insert(T, s, ent_word<PK>(s, pack_val(0, 0), 1ull), &ps) != 1) c.flags |= F_INTERNAL;
+    if (tab_insert(T, t, ent_word<PK>(t, pack_val(1, 0), 1ull), &pt) != 1) c.flags |= F_INTERNAL;
+    if (!PK) {
+      T.hsig[ps] = 1ull;
+      T.hsig[pt] = 1ull;
+    }
     T.lnode[0] = s;
     T.lpos[0] = ps;
     T.lnode[1] = t;
@@ -576,10 +618,12 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& 
         unsigned long long wgt = 0;
         if (ok) {
           const int pos = tab_find_pos(T, y);
-          if (pos >= 0 && val_side((uint32_t)T.hkv[pos]) != side) {
+          const unsigned long long hy = pos >= 0 ? T.hkv[pos] : 0ull;
+          if (pos >= 0 && val_side(ent_val<PK>(hy)) != side) {
             touch = true;
-            const unsigned long long sx = T.hsig[T.lpos[f0 + p]];
-            const unsigned long long sy = T.hsig[pos];
+            const uint32_t px = T.lpos[f0 + p];
+            const unsigned long long sx = ent_sig<PK>(T, T.hkv[px], px);
+            const unsigned long long sy = ent_sig<PK>(T, hy, (uint32_t)pos);
             wgt = sx * sy;
             if (__umul64hi(sx, sy) != 0ull) sigma_of = true;
           }
@@ -631,7 +675,8 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& 
       const volatile int* nlist_now = &c.nlist;
       scan_level(T, f0, fcount, E, cols, [&](int, bool ok, int p, int, int y) {
         if (!ok || cap) return;
-        const unsigned long long add = T.hsig[T.lpos[f0 + p]];
+        const uint32_t px = T.lpos[f0 + p];
+        const unsigned long long add = ent_sig<PK>(T, T.hkv[px], px);
         uint32_t pos = hash_pos(y, T.hlog);
         for (uint32_t k = 0; k <= T.hmask; ++k) {
           unsigned long long w = T.hkv[pos];
@@ -642,7 +687,7 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& 
               cap = true;
               return;
             }
-            const unsigned long long want = ((unsigned long long)(uint32_t)y << 32) | want_val;
+            const unsigned long long want = ent_word<PK>(y, want_val, PK ? add : 0ull);
             const unsigned long long old = atomicCAS(&T.hkv[pos], EMPTY, want);
             if (old == EMPTY) {
               const int slot = atomicAdd(&c.nlist, 1);
@@ -654,17 +699,20 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& 
               T.lpos[slot] = pos;
               ++fresh;
               cost += __ldg(&rowp[y + 1]) - __ldg(&rowp[y]);
-              const unsigned long long o = atomicAdd(&T.hsig[pos], add);
-              if (o + add < o) of = true;
+              if (!PK && !ent_add<PK>(T, pos, add)) of = true;
               return;
             }
             w = old;
           }
           if ((int32_t)(w >> 32) == y) {
-            if ((uint32_t)w == want_val) {  // also discovered at this level
+            if (ent_val<PK>(w) == want_val) {  // also discovered at this level
               ++hits;
-              const unsigned long long o = atomicAdd(&T.hsig[pos], add);
-              if (o + add < o) of = true;
+              if (!ent_add<PK>(T, pos, add)) {
+                if (PK)
+                  cap = true;  // sigma outgrew the packed field
+                else
+                  of = true;
+              }
             }
             return;
           }
@@ -791,8 +839,8 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& 
   const int dv = c.depth[0], dw = c.depth[1];
   if (tid == 0) {
     const int a = tab_find_pos(T, c.cv), b = tab_find_pos(T, c.cw);
-    const bool ok_a = a >= 0 && (uint32_t)T.hkv[a] == pack_val(0, dv);
-    const bool ok_b = b >= 0 && (uint32_t)T.hkv[b] == pack_val(1, dw);
+    const bool ok_a = a >= 0 && ent_val<PK>(T.hkv[a]) == pack_val(0, dv);
+    const bool ok_b = b >= 0 && ent_val<PK>(T.hkv[b]) == pack_val(1, dw);
     if (!ok_a || !ok_b) c.flags |= F_INTERNAL;
   }
   __syncthreads();
@@ -832,7 +880,7 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& 
           c.flags |= F_INTERNAL;
           c.r = 0;
         } else {
-          c.r = below128(draw(P.seed, P.domain, idx, j), T.hsig[px]);
+          c.r = below128(draw(P.seed, P.domain, idx, j), ent_sig<PK>(T, T.hkv[px], (uint32_t)px));
         }
         // scan whichever is shorter: the row of x, or the previous level
         c.mode = ((long long)(phi - plo) * 16 < (long long)deg) ? 1 : 0;
@@ -864,7 +912,10 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& 
         const int nc = c.ecount;
         const int pick = block_pick_by_key(
             nc, r, c, [&](int i) { return (unsigned long long)(uint32_t)T.pr[i].x; },
-            [&](int i) { return T.hsig[T.pr[i].y]; });
+            [&](int i) {
+              const uint32_t q = (uint32_t)T.pr[i].y;
+              return ent_sig<PK>(T, T.hkv[q], q);
+            });
         if (pick >= 0) y_pick = T.pr[pick].x;
         if (tid == 0 && pick >= 0) pos_pick = lower_bound_row(bcol, r0, r0 + deg, y_pick) - r0;
       } else {
@@ -877,7 +928,10 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& 
             w[k] = 0;
             if (ys[k] >= 0) {
               const int pos = tab_find_pos(T, ys[k]);
-              if (pos >= 0 && (uint32_t)T.hkv[pos] == want) w[k] = T.hsig[pos];
+              if (pos >= 0) {
+                const unsigned long long hw = T.hkv[pos];
+                if (ent_val<PK>(hw) == want) w[k] = ent_sig<PK>(T, hw, (uint32_t)pos);
+              }
             }
           }
         });
@@ -913,19 +967,20 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& 
 // entry it inserted): the whole table in shared memory (cheaper than
 // locating the entries) or after a capacity failure (entries beyond the
 // lists), else the entries at the positions the lists recorded.
+template <bool PK>
 __device__ void reset_tables(const Tables& T, Ctl& c, bool whole) {
   const int tid = threadIdx.x;
   if (whole || (c.flags & F_CAP)) {
     for (uint32_t i = tid; i <= T.hmask; i += NT) {
       T.hkv[i] = EMPTY;
-      T.hsig[i] = 0ull;
+      if (!PK) T.hsig[i] = 0ull;
     }
   } else {
     const int nl = min(c.nlist, T.lcap);
     for (int i = tid; i < nl; i += NT) {
       const uint32_t pos = T.lpos[i];
       T.hkv[pos] = EMPTY;
-      T.hsig[pos] = 0ull;
+      if (!PK) T.hsig[pos] = 0ull;
     }
   }
   __syncthreads();
@@ -934,7 +989,7 @@ __device__ void reset_tables(const Tables& T, Ctl& c, bool whole) {
 // global-memory tiers share one body compiled once, outside the kernel
 __device__ __noinline__ void run_sample_global(const SampleParams& P, const Tables& T, Ctl& c, uint64_t idx,
                                                int64_t out_i) {
-  run_sample(P, T, c, idx, out_i);
+  run_sample<false>(P, T, c, idx, out_i);
 }
 
 // layout of one CTA's tables in global memory (tiers M and L)
@@ -971,8 +1026,7 @@ __device__ inline Tables gm_tables(unsigned char* base, int hlog, int lcap, int 
 
 // shared-memory layout of the main sampler (tier S)
 constexpr size_t S_OFF_HKV = (sizeof(Ctl) + 15) & ~size_t(15);
-constexpr size_t S_OFF_HSIG = S_OFF_HKV + (sizeof(unsigned long long) << FAST_HLOG);
-constexpr size_t S_OFF_PR = S_OFF_HSIG + (sizeof(unsigned long long) << FAST_HLOG);
+constexpr size_t S_OFF_PR = S_OFF_HKV + (sizeof(unsigned long long) << FAST_HLOG);
 constexpr size_t S_OFF_LNODE = S_OFF_PR + sizeof(int2) * (FAST_LCAP + 1);
 constexpr size_t S_OFF_LPOS = S_OFF_LNODE + sizeof(int32_t) * FAST_LCAP;
 constexpr size_t S_OFF_LVL = S_OFF_LPOS + sizeof(uint32_t) * FAST_LCAP;
@@ -1024,7 +1078,7 @@ __global__ void __launch_bounds__(NT, KD_MIN_BLOCKS) k_sample(SampleParams P) {
   Tables TS, TM;
   if (MODE == 0) {
     TS.hkv = reinterpret_cast<unsigned long long*>(smem + S_OFF_HKV);
-    TS.hsig = reinterpret_cast<unsigned long long*>(smem + S_OFF_HSIG);
+    TS.hsig = nullptr;  // packed entries
     TS.pr = reinterpret_cast<int2*>(smem + S_OFF_PR);
     TS.lnode = reinterpret_cast<int32_t*>(smem + S_OFF_LNODE);
     TS.lpos = reinterpret_cast<uint32_t*>(smem + S_OFF_LPOS);
@@ -1046,10 +1100,7 @@ __global__ void __launch_bounds__(NT, KD_MIN_BLOCKS) k_sample(SampleParams P) {
 
   const int tid = threadIdx.x;
   if (MODE == 0)
-    for (uint32_t i = tid; i <= TS.hmask; i += NT) {
-      TS.hkv[i] = EMPTY;
-      TS.hsig[i] = 0ull;
-    }
+    for (uint32_t i = tid; i <= TS.hmask; i += NT) TS.hkv[i] = EMPTY;
   if (tid == 0) {
     for (int k = 0; k < KADABRA_NSTAT; ++k) c.tot[k] = 0;
     c.ntotal = MODE == 1 ? min(P.ctr[2], (unsigned long long)P.deferred_cap) : P.count;
@@ -1068,17 +1119,17 @@ __global__ void __launch_bounds__(NT, KD_MIN_BLOCKS) k_sample(SampleParams P) {
     if (MODE == 0) {
       if (!(P.tier_flags & (TF_SKIP_SHARED | TF_ONLY_LARGE))) {
         clear_path_row(P, out_i);
-        run_sample(P, TS, c, idx, out_i);
+        run_sample<true>(P, TS, c, idx, out_i);
         __syncthreads();
         done = c.flags != F_CAP;
-        reset_tables(TS, c, true);
+        reset_tables<true>(TS, c, true);
       }
       if (!done && !(P.tier_flags & TF_ONLY_LARGE)) {
         clear_path_row(P, out_i);
         run_sample_global(P, TM, c, idx, out_i);
         __syncthreads();
         done = c.flags != F_CAP;
-        reset_tables(TM, c, false);
+        reset_tables<false>(TM, c, false);
       }
       if (!done) {  // queue for the n-sized tables
         if (tid == 0) {
@@ -1095,7 +1146,7 @@ __global__ void __launch_bounds__(NT, KD_MIN_BLOCKS) k_sample(SampleParams P) {
       clear_path_row(P, out_i);
       run_sample_global(P, TM, c, idx, out_i);
       __syncthreads();
-      reset_tables(TM, c, false);
+      reset_tables<false>(TM, c, false);
     }
     if (tid == 0) finish_sample(P, c, idx, out_i);
     __syncthreads();
