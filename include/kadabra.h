@@ -127,14 +127,16 @@ void kadabra_free_graph(kadabra_graph* g);
 
 kadabra_status kadabra_graph_info(const kadabra_graph* g, int32_t* n, int64_t* m, int* directed, int64_t* vd);
 
-/* Graph flags.  A sample's visited set lives in shared memory while it fits,
- * then in medium per-CTA global tables, then in n-sized global tables (each
- * sample goes as far as it needs; results are identical in every tier).
- * KADABRA_FLAG_GLOBAL_TABLES runs every sample on the n-sized tables and
- * KADABRA_FLAG_MEDIUM_TABLES starts every sample on the medium tables; both
+/* Graph flags.  A sample's visited set lives in a small shared-memory table
+ * while it fits, then in a large shared-memory table, then in medium
+ * per-CTA global tables, then in n-sized global tables (each sample goes as
+ * far as it needs; results are identical in every tier).  The flags make
+ * every sample start further down that list: KADABRA_FLAG_LARGE_SHARED_TABLES
+ * at the large shared-memory table, KADABRA_FLAG_MEDIUM_TABLES at the medium
+ * global tables, KADABRA_FLAG_GLOBAL_TABLES at the n-sized tables.  They
  * exist to test those paths and for graphs whose searches are known to be
  * deep or wide.  Returns KADABRA_ERR_ARG for unknown bits. */
-enum { KADABRA_FLAG_GLOBAL_TABLES = 1, KADABRA_FLAG_MEDIUM_TABLES = 2 };
+enum { KADABRA_FLAG_GLOBAL_TABLES = 1, KADABRA_FLAG_MEDIUM_TABLES = 2, KADABRA_FLAG_LARGE_SHARED_TABLES = 4 };
 kadabra_status kadabra_graph_set_flags(kadabra_graph* g, uint32_t flags);
 
 /* KADABRA, all-nodes mode (Alg. 1 with Alg. 2 and the rule f,g <= lambda

@@ -26,8 +26,9 @@
 //   * Frontiers are kept sorted by node id, and each warp scans a contiguous
 //     slice of the level's flattened arc range, so candidate edges come out
 //     in the canonical (x, y) order without a sort.
-//   * A sample whose visited set outgrows shared memory is deferred and
-//     re-run by the same kernel compiled against global-memory tables.
+//   * A sample whose visited set outgrows its shared-memory table is re-run
+//     on bigger tables (a one-CTA-per-SM launch with a large shared-memory
+//     table, then global-memory tables), with identical results.
 //   * The RNG is counter-based Philox4x32-10 keyed by (seed, sample index),
 //     so results do not depend on scheduling; hit counts are integer atomics.
 
@@ -64,12 +65,15 @@ namespace {
 constexpr int NT = KD_NT;          // threads per sampler CTA
 constexpr int NW = NT / 32;        // warps per sampler CTA
 constexpr int U = KD_U;            // independent items per thread per step (memory-level parallelism)
-// three tiers of per-sample tables: a sample starts in shared memory, is
-// retried by the same CTA on its medium global tables if it outgrows them,
-// and only beyond those is deferred to a launch with n-sized tables
-constexpr int FAST_HLOG = KD_FAST_HLOG;        // tier S, shared memory: 2^FAST_HLOG hash slots
-constexpr int FAST_LCAP = 1 << (FAST_HLOG - 1);  //   level lists: half as many nodes
-constexpr int FAST_MAXD = 126;     //   levels per side (the packed entry's dist field)
+// Tiers of per-sample tables.  A sample starts in a small shared-memory
+// table (tier S, main launch, several CTAs per SM).  If it outgrows it, it is
+// queued for a second launch with one CTA per SM and a large shared-memory
+// table (tier B); beyond that the same CTA retries it on medium global tables
+// (tier M), and beyond those it is queued for a last launch with n-sized
+// global tables (tier L).  Every tier gives the same result.
+constexpr int FAST_HLOG = KD_FAST_HLOG;        // tier S: 2^FAST_HLOG hash slots
+constexpr int BIG_HLOG = FAST_HLOG + 1;        // tier B: twice as many
+constexpr int FAST_MAXD = 126;     // levels per side in shared memory (the packed entry's dist field)
 constexpr int MED_HLOG = 15;       // tier M, global memory per CTA: 32768 hash slots
 constexpr int MED_LCAP = 16384;    //   level lists: 16384 nodes
 constexpr int MED_MAXD = 1022;     //   levels per side
@@ -245,9 +249,10 @@ struct SampleParams {
   uint64_t first_idx;
   uint64_t count;
   uint32_t* counts;                 // hit counters (n) or null
-  unsigned long long* ctr;          // [0] next (fast), [1] next (global), [2] deferred count
-  unsigned long long* deferred;     // deferred sample indices
-  uint64_t deferred_cap;
+  unsigned long long* ctr;          // queue counters, Q_*
+  unsigned long long* qb;           // sample indices queued for tier B
+  unsigned long long* ql;           // sample indices queued for tier L
+  uint64_t deferred_cap;            // capacity of each queue
   int32_t* status;                  // run-wide error word (kadabra_status values)
   long long* totals;                // KADABRA_NSTAT or null
   int tier_flags;                   // TF_* test switches for the table tiers
@@ -1024,17 +1029,56 @@ __device__ inline Tables gm_tables(unsigned char* base, int hlog, int lcap, int 
   return T;
 }
 
-// shared-memory layout of the main sampler (tier S)
-constexpr size_t S_OFF_HKV = (sizeof(Ctl) + 15) & ~size_t(15);
-constexpr size_t S_OFF_PR = S_OFF_HKV + (sizeof(unsigned long long) << FAST_HLOG);
-constexpr size_t S_OFF_LNODE = S_OFF_PR + sizeof(int2) * (FAST_LCAP + 1);
-constexpr size_t S_OFF_LPOS = S_OFF_LNODE + sizeof(int32_t) * FAST_LCAP;
-constexpr size_t S_OFF_LVL = S_OFF_LPOS + sizeof(uint32_t) * FAST_LCAP;
-constexpr size_t S_BYTES = S_OFF_LVL + sizeof(int) * 4 * (FAST_MAXD + 2);
+// shared-memory layout of a packed tier with 2^HLOG hash slots and lists of
+// 2^(HLOG-1) nodes, after the control block
+template <int HLOG>
+struct SLayout {
+  static constexpr int LCAP = 1 << (HLOG - 1);
+  static constexpr size_t HKV = (sizeof(Ctl) + 15) & ~size_t(15);
+  static constexpr size_t PR = HKV + (sizeof(unsigned long long) << HLOG);
+  static constexpr size_t LNODE = PR + sizeof(int2) * (LCAP + 1);
+  static constexpr size_t LPOS = LNODE + sizeof(int32_t) * LCAP;
+  static constexpr size_t LVL = LPOS + sizeof(uint32_t) * LCAP;
+  static constexpr size_t BYTES = LVL + sizeof(int) * 4 * (FAST_MAXD + 2);
+};
 
-// flags of SampleParams::tier_flags
-constexpr int TF_SKIP_SHARED = 1;   // start in tier M
-constexpr int TF_ONLY_LARGE = 2;    // defer every sample to tier L
+template <int HLOG>
+__device__ inline Tables smem_tables(unsigned char* smem) {
+  using L = SLayout<HLOG>;
+  Tables T;
+  T.hkv = reinterpret_cast<unsigned long long*>(smem + L::HKV);
+  T.hsig = nullptr;  // packed entries
+  T.pr = reinterpret_cast<int2*>(smem + L::PR);
+  T.lnode = reinterpret_cast<int32_t*>(smem + L::LNODE);
+  T.lpos = reinterpret_cast<uint32_t*>(smem + L::LPOS);
+  T.lvl = reinterpret_cast<int*>(smem + L::LVL);
+  T.hlog = HLOG;
+  T.hmask = (1u << HLOG) - 1u;
+  T.lcap = L::LCAP;
+  T.maxd = FAST_MAXD;
+  return T;
+}
+
+// flags of SampleParams::tier_flags (test switches: skip tiers)
+constexpr int TF_SKIP_S = 1;
+constexpr int TF_SKIP_B = 2;
+constexpr int TF_SKIP_M = 4;
+
+// queue counters in SampleParams::ctr
+constexpr int Q_NEXT_A = 0;   // next sample index of the batch
+constexpr int Q_NEXT_B = 1;   // next entry of the tier-B queue
+constexpr int Q_SIZE_B = 2;   // entries in the tier-B queue
+constexpr int Q_NEXT_L = 3;   // next entry of the tier-L queue
+constexpr int Q_SIZE_L = 4;   // entries in the tier-L queue
+constexpr int Q_COUNT = 8;
+
+__device__ void enqueue(const SampleParams& P, int size_ctr, unsigned long long* q, uint64_t idx) {
+  const unsigned long long d = atomicAdd(&P.ctr[size_ctr], 1ull);
+  if (d < P.deferred_cap)
+    q[d] = idx;
+  else
+    atomicCAS(P.status, 0, (int)KADABRA_ERR_CAPACITY);
+}
 
 // Records the outcome of one sample (per-sample outputs, totals, status).
 __device__ void finish_sample(const SampleParams& P, Ctl& c, uint64_t idx, int64_t out_i) {
@@ -1067,78 +1111,74 @@ __device__ void clear_path_row(const SampleParams& P, int64_t out_i) {
   __syncthreads();
 }
 
-// MODE 0: the main grid.  Each sample runs on the CTA's shared-memory tables
-// (tier S); if it outgrows them, the same CTA re-runs it on its medium
-// global tables (tier M); beyond those it is queued for MODE 1.
-// MODE 1: the queued samples on n-sized global tables (tier L).
+// MODE 0: every sample of the batch, on tier S; overflow -> tier-B queue.
+// MODE 2: the tier-B queue, on tier B, then tier M; overflow -> tier-L queue.
+// MODE 1: the tier-L queue, on tier L.
 template <int MODE>
 __global__ void __launch_bounds__(NT, KD_MIN_BLOCKS) k_sample(SampleParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   Ctl& c = *reinterpret_cast<Ctl*>(smem);
   Tables TS, TM;
-  if (MODE == 0) {
-    TS.hkv = reinterpret_cast<unsigned long long*>(smem + S_OFF_HKV);
-    TS.hsig = nullptr;  // packed entries
-    TS.pr = reinterpret_cast<int2*>(smem + S_OFF_PR);
-    TS.lnode = reinterpret_cast<int32_t*>(smem + S_OFF_LNODE);
-    TS.lpos = reinterpret_cast<uint32_t*>(smem + S_OFF_LPOS);
-    TS.lvl = reinterpret_cast<int*>(smem + S_OFF_LVL);
-    TS.hlog = FAST_HLOG;
-    TS.hmask = (1u << FAST_HLOG) - 1u;
-    TS.lcap = FAST_LCAP;
-    TS.maxd = FAST_MAXD;
-    TS.pi = P.pi_base + (size_t)blockIdx.x * 2 * NW * P.pcap;
-    TS.pcap = P.pcap;
+  PiEntry* pi = P.pi_base + (size_t)blockIdx.x * 2 * NW * P.pcap;
+  if (MODE == 0) TS = smem_tables<FAST_HLOG>(smem);
+  if (MODE == 2) {
+    TS = smem_tables<BIG_HLOG>(smem);
     TM = gm_tables(P.med_base + (size_t)blockIdx.x * P.med_stride, MED_HLOG, MED_LCAP, MED_MAXD);
-    TM.pi = TS.pi;
-    TM.pcap = TS.pcap;
-  } else {
-    TM = gm_tables(P.gm_base + (size_t)blockIdx.x * P.gm_stride, P.gm_hlog, P.gm_lcap, GM_MAXD);
-    TM.pi = P.pi_base + (size_t)blockIdx.x * 2 * NW * P.pcap;
-    TM.pcap = P.pcap;
   }
+  if (MODE == 1) TM = gm_tables(P.gm_base + (size_t)blockIdx.x * P.gm_stride, P.gm_hlog, P.gm_lcap, GM_MAXD);
+  TS.pi = TM.pi = pi;
+  TS.pcap = TM.pcap = P.pcap;
 
   const int tid = threadIdx.x;
-  if (MODE == 0)
+  if (MODE != 1)
     for (uint32_t i = tid; i <= TS.hmask; i += NT) TS.hkv[i] = EMPTY;
   if (tid == 0) {
     for (int k = 0; k < KADABRA_NSTAT; ++k) c.tot[k] = 0;
-    c.ntotal = MODE == 1 ? min(P.ctr[2], (unsigned long long)P.deferred_cap) : P.count;
+    c.ntotal = MODE == 0 ? P.count
+               : MODE == 2 ? min(P.ctr[Q_SIZE_B], (unsigned long long)P.deferred_cap)
+                           : min(P.ctr[Q_SIZE_L], (unsigned long long)P.deferred_cap);
   }
   __syncthreads();
   const unsigned long long ntotal = c.ntotal;
 
   for (;;) {
-    if (tid == 0) c.cur = atomicAdd(&P.ctr[MODE == 1 ? 1 : 0], 1ull);
+    if (tid == 0) c.cur = atomicAdd(&P.ctr[MODE == 0 ? Q_NEXT_A : MODE == 2 ? Q_NEXT_B : Q_NEXT_L], 1ull);
     __syncthreads();
     const unsigned long long k = c.cur;
     if (k >= ntotal) break;
-    const uint64_t idx = MODE == 1 ? P.deferred[k] : P.first_idx + k;
+    const uint64_t idx = MODE == 0 ? P.first_idx + k : MODE == 2 ? P.qb[k] : P.ql[k];
     const int64_t out_i = P.st_out ? (int64_t)(idx - P.first_idx) : -1;
     bool done = false;
     if (MODE == 0) {
-      if (!(P.tier_flags & (TF_SKIP_SHARED | TF_ONLY_LARGE))) {
+      if (!(P.tier_flags & TF_SKIP_S)) {
         clear_path_row(P, out_i);
         run_sample<true>(P, TS, c, idx, out_i);
         __syncthreads();
         done = c.flags != F_CAP;
         reset_tables<true>(TS, c, true);
       }
-      if (!done && !(P.tier_flags & TF_ONLY_LARGE)) {
+      if (!done) {
+        if (tid == 0) enqueue(P, Q_SIZE_B, P.qb, idx);
+        __syncthreads();
+        continue;
+      }
+    } else if (MODE == 2) {
+      if (!(P.tier_flags & TF_SKIP_B)) {
+        clear_path_row(P, out_i);
+        run_sample<true>(P, TS, c, idx, out_i);
+        __syncthreads();
+        done = c.flags != F_CAP;
+        reset_tables<true>(TS, c, true);
+      }
+      if (!done && !(P.tier_flags & TF_SKIP_M)) {
         clear_path_row(P, out_i);
         run_sample_global(P, TM, c, idx, out_i);
         __syncthreads();
         done = c.flags != F_CAP;
         reset_tables<false>(TM, c, false);
       }
-      if (!done) {  // queue for the n-sized tables
-        if (tid == 0) {
-          const unsigned long long d = atomicAdd(&P.ctr[2], 1ull);
-          if (d < P.deferred_cap)
-            P.deferred[d] = idx;
-          else
-            atomicCAS(P.status, 0, (int)KADABRA_ERR_CAPACITY);
-        }
+      if (!done) {
+        if (tid == 0) enqueue(P, Q_SIZE_L, P.ql, idx);
         __syncthreads();
         continue;
       }
@@ -1156,7 +1196,8 @@ __global__ void __launch_bounds__(NT, KD_MIN_BLOCKS) k_sample(SampleParams P) {
       if (c.tot[q]) atomicAdd((unsigned long long*)&P.totals[q], (unsigned long long)c.tot[q]);
 }
 
-size_t fast_smem_bytes() { return S_BYTES; }
+size_t fast_smem_bytes() { return SLayout<FAST_HLOG>::BYTES; }
+size_t big_smem_bytes() { return SLayout<BIG_HLOG>::BYTES; }
 
 // ============================================================== stop test
 struct CheckOut {
@@ -1358,11 +1399,12 @@ struct kadabra_graph {
   int num_sms = 0;
   // sampler workspace (allocated on first use)
   bool ws_ready = false;
-  int grid_fast = 0, grid_gm = 0;
-  size_t smem_fast = 0;
+  int grid_fast = 0, grid_big = 0, grid_gm = 0;
+  size_t smem_fast = 0, smem_big = 0;
   unsigned long long* ctr = nullptr;
   int32_t* status = nullptr;
-  unsigned long long* deferred = nullptr;
+  unsigned long long* qb = nullptr;  // queue for tier B
+  unsigned long long* ql = nullptr;  // queue for tier L
   uint64_t deferred_cap = 0;
   PiEntry* pi_fast = nullptr;
   PiEntry* pi_gm = nullptr;
@@ -1407,6 +1449,11 @@ kadabra_status ensure_workspace(kadabra_graph* g, uint64_t deferred_need) {
     KCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample<0>, NT, g->smem_fast));
     if (per_sm < 1) return fail(KADABRA_ERR_CAPACITY, "sampler does not fit on an SM");
     g->grid_fast = g->num_sms * per_sm;
+    g->smem_big = big_smem_bytes();
+    KCK(cudaFuncSetAttribute(k_sample<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g->smem_big));
+    KCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample<2>, NT, g->smem_big));
+    if (per_sm < 1) return fail(KADABRA_ERR_CAPACITY, "large-table sampler does not fit on an SM");
+    g->grid_big = g->num_sms * per_sm;
     // global-memory tables for deferred samples: hash of >= 2n slots, lists of n
     g->gm_hlog = std::max(12, ceil_log2(2ull * (uint64_t)g->n));
     g->gm_lcap = g->n;
@@ -1422,7 +1469,7 @@ kadabra_status ensure_workspace(kadabra_graph* g, uint64_t deferred_need) {
     const size_t budget = (size_t)1 << 30;
     g->grid_gm = (int)std::max<size_t>(1, std::min<size_t>((size_t)g->num_sms, budget / per_cta));
     void* p;
-    KTRY(dev_alloc(g, &p, 4 * sizeof(unsigned long long)));
+    KTRY(dev_alloc(g, &p, Q_COUNT * sizeof(unsigned long long)));
     g->ctr = (unsigned long long*)p;
     KTRY(dev_alloc(g, &p, sizeof(int32_t)));
     g->status = (int32_t*)p;
@@ -1436,10 +1483,10 @@ kadabra_status ensure_workspace(kadabra_graph* g, uint64_t deferred_need) {
     KCK(cudaMemset(g->gm_base, 0, g->gm_stride * g->grid_gm));
     for (int b = 0; b < g->grid_gm; ++b)  // every key word EMPTY (sigma stays 0)
       KCK(cudaMemset(g->gm_base + (size_t)b * g->gm_stride, 0xFF, sizeof(unsigned long long) << g->gm_hlog));
-    KTRY(dev_alloc(g, &p, g->med_stride * g->grid_fast));
+    KTRY(dev_alloc(g, &p, g->med_stride * g->grid_big));
     g->med_base = (unsigned char*)p;
-    KCK(cudaMemset(g->med_base, 0, g->med_stride * g->grid_fast));
-    for (int b = 0; b < g->grid_fast; ++b)
+    KCK(cudaMemset(g->med_base, 0, g->med_stride * g->grid_big));
+    for (int b = 0; b < g->grid_big; ++b)
       KCK(cudaMemset(g->med_base + (size_t)b * g->med_stride, 0xFF, sizeof(unsigned long long) << MED_HLOG));
     KTRY(dev_alloc(g, &p, sizeof(uint32_t) * (size_t)g->n));
     g->counts = (uint32_t*)p;
@@ -1460,16 +1507,20 @@ kadabra_status ensure_workspace(kadabra_graph* g, uint64_t deferred_need) {
   }
   if (deferred_need > g->deferred_cap) {
     KCK(cudaDeviceSynchronize());
-    if (g->deferred) {
-      for (auto& a : g->allocs)
-        if (a == g->deferred) a = nullptr;
-      cudaFree(g->deferred);
-      g->deferred = nullptr;
+    for (unsigned long long** q : {&g->qb, &g->ql}) {
+      if (*q) {
+        for (auto& a : g->allocs)
+          if (a == *q) a = nullptr;
+        cudaFree(*q);
+        *q = nullptr;
+      }
     }
-    uint64_t cap = std::max<uint64_t>(deferred_need, 1 << 16);
+    const uint64_t cap = std::max<uint64_t>(deferred_need, 1 << 16);
     void* p;
     KTRY(dev_alloc(g, &p, sizeof(unsigned long long) * cap));
-    g->deferred = (unsigned long long*)p;
+    g->qb = (unsigned long long*)p;
+    KTRY(dev_alloc(g, &p, sizeof(unsigned long long) * cap));
+    g->ql = (unsigned long long*)p;
     g->deferred_cap = cap;
   }
   return KADABRA_OK;
@@ -1485,7 +1536,8 @@ SampleParams base_params(kadabra_graph* g) {
   P.g.rrp = g->directed ? g->rrp : g->rp;
   P.g.rci = g->directed ? g->rci : g->ci;
   P.ctr = g->ctr;
-  P.deferred = g->deferred;
+  P.qb = g->qb;
+  P.ql = g->ql;
   P.deferred_cap = g->deferred_cap;
   P.status = g->status;
   P.med_base = g->med_base;
@@ -1494,18 +1546,23 @@ SampleParams base_params(kadabra_graph* g) {
   P.gm_stride = g->gm_stride;
   P.gm_hlog = g->gm_hlog;
   P.gm_lcap = g->gm_lcap;
-  P.tier_flags = ((g->flags & KADABRA_FLAG_GLOBAL_TABLES) ? TF_ONLY_LARGE : 0) |
-                 ((g->flags & KADABRA_FLAG_MEDIUM_TABLES) ? TF_SKIP_SHARED : 0);
+  P.tier_flags = 0;
+  if (g->flags & KADABRA_FLAG_GLOBAL_TABLES) P.tier_flags |= TF_SKIP_S | TF_SKIP_B | TF_SKIP_M;
+  if (g->flags & KADABRA_FLAG_MEDIUM_TABLES) P.tier_flags |= TF_SKIP_S | TF_SKIP_B;
+  if (g->flags & KADABRA_FLAG_LARGE_SHARED_TABLES) P.tier_flags |= TF_SKIP_S;
   return P;
 }
 
-// launches the main sampler grid and then the n-sized-table pass for any
-// samples it queued (that launch exits at once when there are none)
+// launches the main sampler grid, then the large-table pass and the
+// n-sized-table pass for the samples queued by the launch before (each exits
+// at once when its queue is empty)
 kadabra_status launch_sampler(kadabra_graph* g, SampleParams P, cudaStream_t st) {
-  KCK(cudaMemsetAsync(g->ctr, 0, 4 * sizeof(unsigned long long), st));
+  KCK(cudaMemsetAsync(g->ctr, 0, Q_COUNT * sizeof(unsigned long long), st));
   P.pi_base = g->pi_fast;
   P.pcap = FAST_PCAP;
   k_sample<0><<<g->grid_fast, NT, g->smem_fast, st>>>(P);
+  KCK(cudaGetLastError());
+  k_sample<2><<<g->grid_big, NT, g->smem_big, st>>>(P);
   KCK(cudaGetLastError());
   P.pi_base = g->pi_gm;
   P.pcap = g->pcap_gm;
@@ -1823,7 +1880,7 @@ void kadabra_free_graph(kadabra_graph* g) {
 
 kadabra_status kadabra_graph_set_flags(kadabra_graph* g, uint32_t flags) {
   if (!g) return fail(KADABRA_ERR_ARG, "graph is NULL");
-  if (flags & ~(uint32_t)(KADABRA_FLAG_GLOBAL_TABLES | KADABRA_FLAG_MEDIUM_TABLES))
+  if (flags & ~(uint32_t)(KADABRA_FLAG_GLOBAL_TABLES | KADABRA_FLAG_MEDIUM_TABLES | KADABRA_FLAG_LARGE_SHARED_TABLES))
     return fail(KADABRA_ERR_ARG, "unknown flag");
   g->flags = flags;
   return KADABRA_OK;

@@ -43,6 +43,7 @@ STAT_NAMES = (
 NSTAT = len(STAT_NAMES)
 FLAG_GLOBAL_TABLES = 1
 FLAG_MEDIUM_TABLES = 2
+FLAG_LARGE_SHARED_TABLES = 4
 
 
 class KadabraError(RuntimeError):

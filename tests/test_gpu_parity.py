@@ -138,6 +138,8 @@ def test_global_tables_match_oracle(kd, orc, gg, name, make):
     g = make(gg)
     compare_paths_global(kd, orc, g, 23, 0, 0, 1500, max_len=256, tag=name)
     compare_paths_global(kd, orc, g, 26, 0, 0, 1500, max_len=256, tag=name + "/medium", flag=kd.FLAG_MEDIUM_TABLES)
+    compare_paths_global(kd, orc, g, 29, 0, 0, 1500, max_len=256, tag=name + "/large-shared",
+                         flag=kd.FLAG_LARGE_SHARED_TABLES)
 
 
 def test_global_tables_er_and_power_law(kd, orc, er2000, chung_lu_1m):
@@ -146,12 +148,14 @@ def test_global_tables_er_and_power_law(kd, orc, er2000, chung_lu_1m):
     compare_paths_global(kd, orc, er2000, 27, 1, 0, 3000, tag="er2000/medium", flag=kd.FLAG_MEDIUM_TABLES)
     compare_paths_global(kd, orc, chung_lu_1m, 28, 0, 5000, 1500, tag="chung-lu/medium",
                          flag=kd.FLAG_MEDIUM_TABLES)
+    compare_paths_global(kd, orc, chung_lu_1m, 30, 0, 9000, 1500, tag="chung-lu/large-shared",
+                         flag=kd.FLAG_LARGE_SHARED_TABLES)
 
 
 def test_run_with_forced_tiers_matches_plain(kd, er2000):
     """Whole runs give identical results whichever table tier holds the samples."""
     out = []
-    for flag in (0, kd.FLAG_MEDIUM_TABLES, kd.FLAG_GLOBAL_TABLES):
+    for flag in (0, kd.FLAG_LARGE_SHARED_TABLES, kd.FLAG_MEDIUM_TABLES, kd.FLAG_GLOBAL_TABLES):
         G = kd.kadabra_load_csr(er2000)
         try:
             G.set_flags(flag)
