@@ -393,6 +393,30 @@ __device__ __forceinline__ int lower_bound_row(const int32_t* col, int a, int b,
   return a;
 }
 
+// lower_bound over a sorted row by one warp: 32 pivots per round narrow the
+// range 32-fold, so a 10^4-entry row takes three rounds of loads instead of
+// fourteen dependent ones.  All lanes get the result.
+__device__ __forceinline__ int warp_lower_bound(const int32_t* col, int a, int b, int32_t y) {
+  const int lane = lane_id();
+  while (b - a > 32) {
+    const long long span = b - a;
+    const int piv = a + (int)((span * lane) / 32);
+    const bool less = __ldg(&col[piv]) < y;
+    const unsigned m = __ballot_sync(FULL, less);
+    // pivots are non-decreasing in lane order: the first lane whose pivot is
+    // not below y bounds the answer
+    const int k = m == FULL ? 32 : __ffs(~m) - 1;
+    const int na = k == 0 ? a : a + (int)((span * (k - 1)) / 32) + 1;
+    const int nb = k == 32 ? b : a + (int)((span * k) / 32);
+    a = na;
+    b = nb;
+  }
+  const int e = a + lane;
+  const bool less = e < b && __ldg(&col[e]) < y;
+  const unsigned m = __ballot_sync(FULL, less);
+  return a + __popc(m);
+}
+
 // Weighted choice over items 0..N-1 in order: the first item whose inclusive
 // prefix sum of weights exceeds r (r < total weight).  Each thread weighs U
 // consecutive items per step so their memory accesses overlap.  Returns the
@@ -813,10 +837,17 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& 
     }
     __syncthreads();
     int pick;
-    if (total <= 128) {
+    // the frontier prefix array is free now: up to lcap/2 (key, weight)
+    // pairs fit in it, ranked there quadratically; larger sets are sorted
+    unsigned long long* kw = reinterpret_cast<unsigned long long*>(T.pr);
+    if (total <= T.lcap / 2) {
+      for (int i = tid; i < total; i += NT) {
+        kw[2 * i] = ((unsigned long long)(uint32_t)buf[i].x << 32) | (uint32_t)buf[i].y;
+        kw[2 * i + 1] = buf[i].w;
+      }
+      __syncthreads();
       pick = block_pick_by_key(
-          total, c.r, c, [&](int i) { return ((unsigned long long)(uint32_t)buf[i].x << 32) | (uint32_t)buf[i].y; },
-          [&](int i) { return buf[i].w; });
+          total, c.r, c, [&](int i) { return kw[2 * i]; }, [&](int i) { return kw[2 * i + 1]; });
     } else {
       pick = block_pick_sorted(buf, total, c.r, c);
     }
@@ -895,7 +926,14 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& 
       __syncthreads();
       if (c.flags) return;
       const unsigned long long r = c.r;
-      if (c.mode == 1) {
+      if (c.mode == 1 && phi - plo == 1) {
+        // a single node one level closer: it is x's only possible predecessor
+        if (tid == 0) {
+          T.pr[0] = make_int2(T.lnode[plo], (int)T.lpos[plo]);
+          c.ecount = 1;
+        }
+        __syncthreads();
+      } else if (c.mode == 1) {
         // previous-level nodes adjacent to x, collected as (node, hash position)
         for (int i = plo + tid; i < phi; i += NT) {
           const int y = T.lnode[i];
@@ -922,7 +960,7 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& 
               return ent_sig<PK>(T, T.hkv[q], q);
             });
         if (pick >= 0) y_pick = T.pr[pick].x;
-        if (tid == 0 && pick >= 0) pos_pick = lower_bound_row(bcol, r0, r0 + deg, y_pick) - r0;
+        if (wid == 0 && pick >= 0) pos_pick = warp_lower_bound(bcol, r0, r0 + deg, y_pick) - r0;
       } else {
         const int pick = block_pick(deg, r, c, [&](int i0, int N, unsigned long long* w) {
           int ys[U];
