@@ -198,6 +198,21 @@ __device__ __forceinline__ uint32_t hash_pos(int32_t v, int hlog) {
   return ((uint32_t)v * 2654435761u) >> (32 - hlog);
 }
 
+// position of v's entry (its word in *wout), or -1
+__device__ __forceinline__ int tab_probe(const Tables& T, int32_t v, unsigned long long* wout) {
+  uint32_t pos = hash_pos(v, T.hlog);
+  for (uint32_t k = 0; k <= T.hmask; ++k) {
+    const unsigned long long w = T.hkv[pos];
+    if (w == EMPTY) return -1;
+    if ((int32_t)(w >> 32) == v) {
+      *wout = w;
+      return (int)pos;
+    }
+    pos = (pos + 1) & T.hmask;
+  }
+  return -1;
+}
+
 // position of v's entry, or -1
 __device__ __forceinline__ int tab_find_pos(const Tables& T, int32_t v) {
   uint32_t pos = hash_pos(v, T.hlog);
@@ -287,19 +302,18 @@ struct Ctl {
   int depth[2];
   int npi[NW];
   int scan_tmp[NW];
-  long long scan_tmp64[NW];
+  long long scan_tmp3[NW][3];
   int s, t;
   int nlist;
   int flags;
   int side;
-  int f0, fcount, ecount;
+  int ecount;
   int done;       // 0 = continue, 1 = touch, 2 = disconnected
   int sel_warp;
   int pick, pick_pos;
   int mode;       // backtracking: 0 = scan the row of x, 1 = scan the previous level
   int next_x;     // backtracking: the node picked at this step
   int cv, cw;     // chosen candidate edge (v on the s side, w on the t side)
-  int list_before;
   unsigned long long cur;
   unsigned long long ntotal;
 };
@@ -355,18 +369,31 @@ __device__ __forceinline__ unsigned long long block_inscan_u64(unsigned long lon
   return wpre + v;
 }
 
-__device__ __forceinline__ long long block_sum64(long long x, long long* tmp) {
+// three block sums in one round (one pair of barriers)
+__device__ __forceinline__ void block_sum3(long long& a, long long& b, long long& d, long long (*tmp)[3]) {
   const int lane = lane_id(), w = warp_id();
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
-  if (lane == 0) tmp[w] = x;
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(FULL, a, o);
+    b += __shfl_xor_sync(FULL, b, o);
+    d += __shfl_xor_sync(FULL, d, o);
+  }
+  if (lane == 0) {
+    tmp[w][0] = a;
+    tmp[w][1] = b;
+    tmp[w][2] = d;
+  }
   __syncthreads();
-  long long tot = 0;
+  a = b = d = 0;
 #pragma unroll
-  for (int i = 0; i < NW; ++i) tot += tmp[i];
+  for (int i = 0; i < NW; ++i) {
+    a += tmp[i][0];
+    b += tmp[i][1];
+    d += tmp[i][2];
+  }
   __syncthreads();
-  return tot;
 }
+
 
 // largest p in [0, cnt) with pr[p].x <= e (prefixes non-decreasing, pr[0].x = 0)
 __device__ __forceinline__ int frontier_pos(const int2* pr, int cnt, int e) {
@@ -458,39 +485,50 @@ __device__ __forceinline__ int block_pick(int N, unsigned long long r, Ctl& c, W
 // Scans the arcs of the current frontier level: each warp takes a contiguous
 // slice of the flattened arc range and walks it in windows of 32 arcs, U
 // windows at a time so their loads overlap.  For every window position it
-// calls f(k, ok, p, x, y): ok = the lane holds an arc, p = frontier position
-// of its tail x, y = its head.  All lanes of the warp call f together, in
-// increasing arc order (so f may use warp collectives).
+// calls f(k, ok, p, y): ok = the lane holds an arc, p = frontier position of
+// its tail, y = its head.  All lanes of the warp call f together, in
+// increasing arc order (so f may use warp collectives).  The warp keeps the
+// frontier row of its current window in registers; only lanes whose arc
+// lies in a later row search the frontier prefix.
 template <class F>
-__device__ __forceinline__ void scan_level(const Tables& T, int f0, int fcount, int E, const int32_t* cols, F f) {
+__device__ __forceinline__ void scan_level(const Tables& T, int fcount, int E, const int32_t* cols, F f) {
   const int lane = lane_id(), wid = warp_id();
   const int per = (E + NW - 1) / NW;
   const int c0 = min(E, wid * per), c1 = min(E, c0 + per);
-  int pcur = c0 < c1 ? frontier_pos(T.pr, fcount, c0) : 0;  // warp-uniform
+  if (c0 >= c1) return;
+  int pcur = frontier_pos(T.pr, fcount, c0);  // warp-uniform
+  int2 cur = T.pr[pcur];                      // {first arc index, row start}
+  int nxt = T.pr[pcur + 1].x;                 // first arc index of the next row
   for (int base = c0; base < c1; base += 32 * U) {
-    int xs[U], ys[U], ps[U];
+    int ys[U], ps[U];
     bool oks[U];
 #pragma unroll
     for (int k = 0; k < U; ++k) {
       const int wb = base + 32 * k;
       oks[k] = false;
-      xs[k] = ys[k] = ps[k] = 0;
+      ys[k] = ps[k] = 0;
       if (wb < c1) {
-        if (T.pr[pcur + 1].x <= wb) pcur = pcur + 1 + frontier_pos(T.pr + pcur + 1, fcount - pcur - 1, wb);
+        if (nxt <= wb) {  // the window starts in a later row
+          pcur = pcur + 1 + frontier_pos(T.pr + pcur + 1, fcount - pcur - 1, wb);
+          cur = T.pr[pcur];
+          nxt = T.pr[pcur + 1].x;
+        }
         const int e = wb + lane;
         if (e < c1) {
           int p = pcur;
-          if (T.pr[p + 1].x <= e) p = p + 1 + frontier_pos(T.pr + p + 1, fcount - p - 1, e);
-          const int2 q = T.pr[p];
+          int2 q = cur;
+          if (e >= nxt) {
+            p = pcur + 1 + frontier_pos(T.pr + pcur + 1, fcount - pcur - 1, e);
+            q = T.pr[p];
+          }
           ps[k] = p;
-          xs[k] = T.lnode[f0 + p];
           ys[k] = __ldg(&cols[q.y + (e - q.x)]);
           oks[k] = true;
         }
       }
     }
 #pragma unroll
-    for (int k = 0; k < U; ++k) f(k, oks[k], ps[k], xs[k], ys[k]);
+    for (int k = 0; k < U; ++k) f(k, oks[k], ps[k], ys[k]);
   }
 }
 
@@ -596,19 +634,17 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& 
 
   // ------------------------------------------------ bb-BFS (Sec. 4)
   for (int iter = 0; iter <= 2 * T.maxd + 2; ++iter) {
+    // every thread derives the frontier from the shared state left by the
+    // previous level (stable since its closing barrier)
+    const int side = c.cost[0] <= c.cost[1] ? 0 : 1;
+    const int f0 = lvl_lo(T, side, c.depth[side]);
+    const int fcount = lvl_hi(T, side, c.depth[side]) - f0;
+    const int list_before = c.nlist;
     if (tid == 0) {
-      const int side = c.cost[0] <= c.cost[1] ? 0 : 1;
-      const int d = c.depth[side];
       c.side = side;
-      c.f0 = lvl_lo(T, side, d);
-      c.fcount = lvl_hi(T, side, d) - lvl_lo(T, side, d);
       c.stat[KADABRA_STAT_LEVELS] += 1;
-      c.stat[KADABRA_STAT_EXPANDED] += c.fcount;
-      c.list_before = c.nlist;
+      c.stat[KADABRA_STAT_EXPANDED] += fcount;
     }
-    __syncthreads();
-    const int side = c.side;
-    const int f0 = c.f0, fcount = c.fcount;
     const int32_t* rowp = side == 0 ? G.rp : G.rrp;
     const int32_t* cols = side == 0 ? G.ci : G.rci;
 
@@ -642,12 +678,12 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& 
       int npi = 0;
       bool sigma_of = false;
       PiEntry* seg = T.pi + (size_t)wid * T.pcap;
-      scan_level(T, f0, fcount, E, cols, [&](int, bool ok, int p, int x, int y) {
+      scan_level(T, fcount, E, cols, [&](int, bool ok, int p, int y) {
         bool touch = false;
         unsigned long long wgt = 0;
         if (ok) {
-          const int pos = tab_find_pos(T, y);
-          const unsigned long long hy = pos >= 0 ? T.hkv[pos] : 0ull;
+          unsigned long long hy = 0;
+          const int pos = tab_probe(T, y, &hy);
           if (pos >= 0 && val_side(ent_val<PK>(hy)) != side) {
             touch = true;
             const uint32_t px = T.lpos[f0 + p];
@@ -661,7 +697,7 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& 
         if (touch) {
           const int at = npi + __popc(m & ((1u << lane) - 1u));
           if (at < T.pcap) {
-            seg[at].x = x;
+            seg[at].x = T.lnode[f0 + p];
             seg[at].y = y;
             seg[at].w = wgt;
           }
@@ -702,7 +738,7 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& 
       bool of = false, cap = false;
       const uint32_t want_val = pack_val(side, dnew);
       const volatile int* nlist_now = &c.nlist;
-      scan_level(T, f0, fcount, E, cols, [&](int, bool ok, int p, int, int y) {
+      scan_level(T, fcount, E, cols, [&](int, bool ok, int p, int y) {
         if (!ok || cap) return;
         const uint32_t px = T.lpos[f0 + p];
         const unsigned long long add = ent_sig<PK>(T, T.hkv[px], px);
@@ -752,9 +788,7 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& 
       if (of) atomicOr(&c.flags, F_SIGMA);
       if (cap) atomicOr(&c.flags, F_CAP);
     }
-    hits = block_sum64(hits, c.scan_tmp64);
-    fresh = block_sum64(fresh, c.scan_tmp64);
-    cost = block_sum64(cost, c.scan_tmp64);
+    block_sum3(hits, fresh, cost, c.scan_tmp3);
     if (c.flags) return;
     if (fresh == 0) {  // frontier exhausted: s and t are not connected
       if (tid == 0) c.done = 2;
@@ -762,7 +796,7 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& 
       break;
     }
     if (tid == 0) {
-      lvl_lo(T, side, dnew) = c.list_before;
+      lvl_lo(T, side, dnew) = list_before;
       lvl_hi(T, side, dnew) = c.nlist;
       c.depth[side] = dnew;
       c.cost[side] = cost;
