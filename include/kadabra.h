@@ -156,6 +156,34 @@ kadabra_status kadabra_run(kadabra_graph* g, double lambda, double delta, int32_
 kadabra_status kadabra_sample_batch(kadabra_graph* g, uint64_t seed, uint32_t domain, uint64_t first_idx,
                                     uint64_t count, uint32_t* d_counts, int64_t* d_totals, void* stream);
 
+/* The sampler batch without any device allocation.  It has no counterpart in
+ * the paper.  It exists for callers that cannot allocate device memory: code
+ * whose device memory belongs entirely to another allocator (a framework's
+ * memory pool), and latency-critical code that must not call cudaMalloc or
+ * cudaFree after start-up (both can synchronize the whole device).
+ *
+ * Same sampling as kadabra_sample_batch (identical hit counts and work
+ * counters), from a CSR the caller already holds on the device (the arrays
+ * of kadabra_load_csr_device, assumed valid: this call does not check them).
+ * The library's scratch for this call is one file-scope device array of
+ * about 21 MiB, which every GPU that loads the library holds until the
+ * process exits.  Limits:
+ *   - count <= 65536 samples per call (larger counts: KADABRA_ERR_CAPACITY);
+ *   - only the two shared-memory table tiers are used: if any sample's
+ *     visited set outgrows them (more than 4096 nodes before the touching
+ *     level, or more than 256 candidate edges found by one warp), the call
+ *     returns KADABRA_ERR_CAPACITY and its counts are incomplete.
+ * The first call on a device sets that device up (kernel attributes and the
+ * scratch array's device address); make that first call before any stream
+ * capture.  Every call shares the one scratch array, which keeps the last
+ * call's contents (the call clears what must start at zero), so calls that
+ * overlap on the GPU, from any stream or thread, race: serialise them.
+ * Blocking: waits for `stream` before returning. */
+kadabra_status kadabra_sample_batch_noalloc(int32_t n, int64_t m, const int32_t* d_row_ptr, const int32_t* d_col,
+                                            int directed, const int32_t* d_rrow_ptr, const int32_t* d_rcol,
+                                            uint64_t seed, uint32_t domain, uint64_t first_idx, uint64_t count,
+                                            uint32_t* d_counts, int64_t* d_totals, void* stream);
+
 /* Waits for `stream` and returns (then clears) the device error word of g. */
 kadabra_status kadabra_sync_status(kadabra_graph* g, void* stream);
 

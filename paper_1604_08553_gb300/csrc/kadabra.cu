@@ -1842,6 +1842,70 @@ kadabra_status new_graph(int32_t n, int64_t m, int directed, kadabra_graph** out
 
 }  // namespace
 
+namespace {
+
+// ================================================================ no-alloc sampler
+// A variant of the sampler batch for callers that cannot allocate device
+// memory.  Its scratch is one file-scope device array; see the ABI comment of
+// kadabra_sample_batch_noalloc for the limits.
+constexpr int NA_MAX_CTAS = 304;              // main-grid CTAs at most
+constexpr int NA_PCAP = 256;                  // candidate edges per warp
+constexpr uint64_t NA_MAX_BATCH = 65536;      // samples per call
+constexpr size_t NA_OFF_CTR = 0;              // Q_COUNT counters, then the status word
+constexpr size_t NA_OFF_STATUS = sizeof(unsigned long long) * Q_COUNT;
+constexpr size_t NA_HEADER = 256;             // cleared on every call
+constexpr size_t NA_OFF_QB = NA_HEADER;
+constexpr size_t NA_OFF_QL = NA_OFF_QB + sizeof(unsigned long long) * NA_MAX_BATCH;
+constexpr size_t NA_OFF_PI = NA_OFF_QL + sizeof(unsigned long long) * NA_MAX_BATCH;
+constexpr size_t NA_BYTES = NA_OFF_PI + sizeof(PiEntry) * (size_t)NA_MAX_CTAS * 2 * NW * NA_PCAP;
+static_assert(NA_OFF_STATUS + sizeof(int32_t) <= NA_HEADER, "no-alloc header");
+
+// Shared by every call on a device; the host never names it directly except
+// to ask for its device address.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
+
+struct NoAllocDevice {
+  bool ready = false;
+  unsigned char* scratch = nullptr;  // device address of g_noalloc_scratch
+  int grid_s = 0, grid_b = 0;
+  size_t smem_s = 0, smem_b = 0;
+};
+constexpr int NA_MAX_DEVICES = 64;
+NoAllocDevice g_na_dev[NA_MAX_DEVICES];
+std::mutex g_na_mu;
+
+// once per device, with that device current: kernel attributes, grid sizes
+// and the device address of the scratch array
+kadabra_status noalloc_setup(int dev, NoAllocDevice** out) {
+  if (dev < 0 || dev >= NA_MAX_DEVICES) return fail(KADABRA_ERR_ARG, "device index out of range");
+  std::lock_guard<std::mutex> lock(g_na_mu);
+  NoAllocDevice& d = g_na_dev[dev];
+  if (!d.ready) {
+    int sms = 0, per_sm = 0;
+    KCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    d.smem_s = fast_smem_bytes();
+    d.smem_b = big_smem_bytes();
+    KCK(cudaFuncSetAttribute(k_sample<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.smem_s));
+    KCK(cudaFuncSetAttribute(k_sample<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.smem_b));
+    KCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample<0>, NT, d.smem_s));
+    if (per_sm < 1) return fail(KADABRA_ERR_CAPACITY, "sampler does not fit on an SM");
+    d.grid_s = std::min(sms * per_sm, NA_MAX_CTAS);
+    KCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample<2>, NT, d.smem_b));
+    if (per_sm < 1) return fail(KADABRA_ERR_CAPACITY, "large-table sampler does not fit on an SM");
+    d.grid_b = std::min(sms * per_sm, NA_MAX_CTAS);
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || ptr == nullptr)
+      return fail(KADABRA_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+    d.scratch = static_cast<unsigned char*>(ptr);
+    d.ready = true;
+  }
+  *out = &d;
+  return KADABRA_OK;
+}
+
+}  // namespace
+
 // ================================================================ C ABI
 extern "C" {
 
@@ -1980,6 +2044,66 @@ kadabra_status kadabra_sample_batch(kadabra_graph* g, uint64_t seed, uint32_t do
   P.counts = d_counts;
   P.totals = reinterpret_cast<long long*>(d_totals);
   return launch_sampler(g, P, as_stream(stream));
+}
+
+kadabra_status kadabra_sample_batch_noalloc(int32_t n, int64_t m, const int32_t* d_row_ptr, const int32_t* d_col,
+                                            int directed, const int32_t* d_rrow_ptr, const int32_t* d_rcol,
+                                            uint64_t seed, uint32_t domain, uint64_t first_idx, uint64_t count,
+                                            uint32_t* d_counts, int64_t* d_totals, void* stream) {
+  if (n < 2 || n > (1 << 24) || m < 0 || m >= ((int64_t)1 << 31) || !d_row_ptr || (m > 0 && !d_col) || !d_counts)
+    return fail(KADABRA_ERR_ARG, "bad graph or output arguments");
+  if (directed && (!d_rrow_ptr || (m > 0 && !d_rcol)))
+    return fail(KADABRA_ERR_ARG, "a directed graph needs the reverse CSR");
+  if (count > NA_MAX_BATCH)
+    return fail(KADABRA_ERR_CAPACITY, "kadabra_sample_batch_noalloc takes at most " +
+                                          std::to_string(NA_MAX_BATCH) + " samples per call");
+  if (count == 0) return KADABRA_OK;
+  int dev = 0;
+  KCK(cudaGetDevice(&dev));
+  NoAllocDevice* d = nullptr;
+  KTRY(noalloc_setup(dev, &d));
+  cudaStream_t st = as_stream(stream);
+  SampleParams P;
+  std::memset(&P, 0, sizeof(P));
+  P.g.n = n;
+  P.g.m = m;
+  P.g.rp = d_row_ptr;
+  P.g.ci = d_col;
+  P.g.rrp = directed ? d_rrow_ptr : d_row_ptr;
+  P.g.rci = directed ? d_rcol : d_col;
+  P.seed = seed;
+  P.domain = domain;
+  P.first_idx = first_idx;
+  P.count = count;
+  P.counts = d_counts;
+  P.totals = reinterpret_cast<long long*>(d_totals);
+  P.ctr = reinterpret_cast<unsigned long long*>(d->scratch + NA_OFF_CTR);
+  P.status = reinterpret_cast<int32_t*>(d->scratch + NA_OFF_STATUS);
+  P.qb = reinterpret_cast<unsigned long long*>(d->scratch + NA_OFF_QB);
+  P.ql = reinterpret_cast<unsigned long long*>(d->scratch + NA_OFF_QL);
+  P.deferred_cap = NA_MAX_BATCH;
+  P.pi_base = reinterpret_cast<PiEntry*>(d->scratch + NA_OFF_PI);
+  P.pcap = NA_PCAP;
+  P.tier_flags = TF_SKIP_M;  // no global tables: only the two shared-memory tiers
+  KCK(cudaMemsetAsync(d->scratch, 0, NA_HEADER, st));
+  k_sample<0><<<d->grid_s, NT, d->smem_s, st>>>(P);
+  KCK(cudaGetLastError());
+  k_sample<2><<<d->grid_b, NT, d->smem_b, st>>>(P);
+  KCK(cudaGetLastError());
+  unsigned long long left = 0;
+  int32_t status = 0;
+  KCK(cudaMemcpyAsync(&left, P.ctr + Q_SIZE_L, sizeof(left), cudaMemcpyDeviceToHost, st));
+  KCK(cudaMemcpyAsync(&status, P.status, sizeof(status), cudaMemcpyDeviceToHost, st));
+  KCK(cudaStreamSynchronize(st));
+  if (status != 0)
+    return fail((kadabra_status)status, status == KADABRA_ERR_SIGMA_OVERFLOW
+                                            ? "a shortest-path count exceeded 2^64-1"
+                                            : "the sampler reported a capacity or internal error");
+  if (left != 0)
+    return fail(KADABRA_ERR_CAPACITY, std::to_string(left) +
+                                          " samples outgrew the shared-memory tables and were not counted; "
+                                          "use kadabra_sample_batch for this graph");
+  return KADABRA_OK;
 }
 
 kadabra_status kadabra_sync_status(kadabra_graph* g, void* stream) {

@@ -99,6 +99,8 @@ def load_library():
         lib.kadabra_run.restype = st
         lib.kadabra_sample_batch.argtypes = [p, u64, u32, u64, u64, p, p, p]
         lib.kadabra_sample_batch.restype = st
+        lib.kadabra_sample_batch_noalloc.argtypes = [i32, i64, p, p, C.c_int, p, p, u64, u32, u64, u64, p, p, p]
+        lib.kadabra_sample_batch_noalloc.restype = st
         lib.kadabra_sync_status.argtypes = [p, p]
         lib.kadabra_sync_status.restype = st
         lib.kadabra_sample_paths.argtypes = [p, u64, u32, u64, u32, p, p, p, i32, p, p]
@@ -239,6 +241,17 @@ def kadabra_sample_batch(g: Graph, seed: int, domain: int, first_idx: int, count
     lib = load_library()
     _raise(lib.kadabra_sample_batch(g.handle, seed, domain, first_idx, count, C.c_void_p(d_counts.data_ptr()),
                                     None if d_totals is None else C.c_void_p(d_totals.data_ptr()), stream))
+
+
+def kadabra_sample_batch_noalloc(n: int, row_ptr, col, seed: int, domain: int, first_idx: int, count: int,
+                                 d_counts, d_totals=None, directed: bool = False, rrow_ptr=None, rcol=None,
+                                 stream: Optional[int] = None) -> None:
+    """The sampler batch without device allocation, from int32 CUDA tensors
+    of a CSR (see include/kadabra.h for its limits).  Blocking."""
+    ptr = lambda t: None if t is None else C.c_void_p(t.data_ptr())
+    _raise(load_library().kadabra_sample_batch_noalloc(
+        int(n), int(col.numel()), ptr(row_ptr), ptr(col), int(bool(directed)), ptr(rrow_ptr), ptr(rcol), seed,
+        domain, first_idx, count, ptr(d_counts), ptr(d_totals), stream))
 
 
 def kadabra_sync_status(g: Graph, stream: Optional[int] = None) -> None:
