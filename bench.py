@@ -36,6 +36,10 @@ METRIC = "paths/sec & time-to-(lambda,delta) per graph, batched vs plain on GPU;
 WORKLOAD = dict(family="chung_lu", n=1_000_000, beta=2.5, mean_deg=16.0, max_deg=10_000.0, graph_seed=1,
                 lcc=True, lam=0.005, delta=0.1, check_interval=1 << 16)
 L2_FLUSH_BYTES = 512 << 20
+# DRAM bytes (read + write) of one sampler batch of this workload, summed over
+# its three launches, from the ncu capture in profiles/k_sample_chung_lu_1m_full.md
+# (set to None whenever the sampler kernels change until re-captured)
+SAMPLER_DRAM_BYTES = 121_185_024 + 6_193_152
 
 
 def make_graph():
@@ -349,7 +353,7 @@ def main():
                 "edges_per_sample": float(tot_np[0]) / K,
             }),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "k_sample (sampler batch)",
+                         "frac": achieved / peak, "traffic": SAMPLER_DRAM_BYTES, "kernel": "k_sample (sampler batch)",
                          "bytes_per_launch": avg_b, "launch_ms": 1e3 * avg_t, "samples_per_launch": K,
                          "peak_source": peak_src},
             "e2e": {"value": e2e_value, "unit": "paths/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
