@@ -77,7 +77,8 @@ typedef struct {
                               heuristic 2*ecc(r)+1 (r = lowest-id max-degree node,
                               underlying undirected graph)                        */
   double eps;              /* computeDelta epsilon (App. D; default 0.001)        */
-  uint64_t check_interval; /* K: samples between stop tests (default 1000)        */
+  uint64_t check_interval; /* K: samples between stop tests (default 1000; 0 = chosen
+                              by the library from omega: max(1024, ceil(omega/32)))  */
   void* stream;            /* cudaStream_t for all work of the call (NULL = default) */
   int32_t ctas_per_sm;     /* resident sampler CTAs per SM (0 = default)          */
   int32_t reserved[7];
@@ -99,6 +100,7 @@ typedef struct {
   double max_f;        /* max_v f(v) at the final tau (Thm. 2)                    */
   double max_g;        /* max_v g(v) at the final tau                             */
   int64_t totals[KADABRA_NSTAT]; /* work counters, warm-up + main loop              */
+  uint64_t check_interval; /* K used                                                */
   int32_t stopped_early; /* 1 if the stop test held before ceil(omega) samples    */
   int32_t status;        /* same as the call's return value                       */
   /* caller-owned buffers (inputs; NULL = not wanted) */
@@ -122,8 +124,42 @@ kadabra_status kadabra_load_csr_device(int32_t n, int64_t m, const int32_t* d_ro
                                        int directed, const int32_t* d_rrow_ptr, const int32_t* d_rcol,
                                        kadabra_graph** out);
 
-/* Releases the graph and all device memory the library allocated for it. */
+/* Releases the graph and all device memory the library allocated for it.
+ * Graph views of a batch (kadabra_batch_graph) are released with the batch;
+ * passing one here does nothing. */
 void kadabra_free_graph(kadabra_graph* g);
+
+/* ---------------------------------------------------------------- batches
+ * Several graphs sampled together (Alg. 1 for each graph, all graphs' sample
+ * batches in one launch per round).  The CSRs of the G graphs are packed
+ * into one device arena.  Each graph's result is identical to kadabra_run on
+ * that graph with the same lambda, delta, seed and check interval. */
+typedef struct kadabra_batch kadabra_batch;
+
+/* Copies G host CSRs (arrays of G pointers / sizes; rrow_ptr/rcol entries
+ * NULL for undirected graphs, the arrays themselves may be NULL if no graph
+ * is directed) into one device arena, validating each (KADABRA_ERR_CSR). */
+kadabra_status kadabra_load_batch(int32_t G, const int32_t* n, const int64_t* m, const int32_t* const* row_ptr,
+                                  const int32_t* const* col, const int* directed, const int32_t* const* rrow_ptr,
+                                  const int32_t* const* rcol, kadabra_batch** out);
+
+/* Releases the batch, its arena and its graph views. */
+void kadabra_free_batch(kadabra_batch* b);
+
+/* A graph object viewing graph i of the batch (for kadabra_run and the
+ * other per-graph calls).  Owned by the batch.  Calls on the views of one
+ * batch and on the batch itself share its workspace: do not overlap them. */
+kadabra_status kadabra_batch_graph(kadabra_batch* b, int32_t i, kadabra_graph** view);
+
+/* KADABRA on every graph of the batch (all-nodes mode), graph i with
+ * lambda[i], delta[i], seed[i].  cfg (may be NULL) gives eps, the check
+ * interval (0 = per graph from its omega, see kadabra_config) and the
+ * stream; cfg->vd must be 0 (each graph uses its own VD bound).  out[i]
+ * receives graph i's result (set its buffer pointers as for kadabra_run).
+ * Rounds: one sampler launch over the next batch of every unfinished graph,
+ * then one stop-test launch over all of them.  Blocking. */
+kadabra_status kadabra_run_batch(kadabra_batch* b, const double* lambda, const double* delta, const uint64_t* seed,
+                                 const kadabra_config* cfg, kadabra_result* out);
 
 kadabra_status kadabra_graph_info(const kadabra_graph* g, int32_t* n, int64_t* m, int* directed, int64_t* vd);
 

@@ -257,19 +257,30 @@ struct GraphDev {
   const int32_t* rci;  // in-arc sources
 };
 
-struct SampleParams {
+// One graph's share of a sampler launch: samples [first_idx, first_idx+count)
+// of one RNG domain, numbered work_begin.. in the launch's work index space.
+struct Job {
   GraphDev g;
   uint64_t seed;
   uint32_t domain;
+  uint32_t pad;
   uint64_t first_idx;
   uint64_t count;
   uint32_t* counts;                 // hit counters (n) or null
+  long long* totals;                // KADABRA_NSTAT work counters or null
+  uint64_t work_begin;
+};
+
+struct SampleParams {
+  Job job0;                         // the job, when the launch has only one
+  const Job* jobs;                  // device array of njobs jobs, or null (then job0)
+  int njobs;
+  uint64_t total_work;              // sum of the jobs' counts
   unsigned long long* ctr;          // queue counters, Q_*
   unsigned long long* qb;           // sample indices queued for tier B
   unsigned long long* ql;           // sample indices queued for tier L
   uint64_t deferred_cap;            // capacity of each queue
   int32_t* status;                  // run-wide error word (kadabra_status values)
-  long long* totals;                // KADABRA_NSTAT or null
   int tier_flags;                   // TF_* test switches for the table tiers
   // per-sample outputs (test hook) or null
   int32_t* st_out;
@@ -291,6 +302,9 @@ struct SampleParams {
 
 // per-CTA control block in shared memory
 struct Ctl {
+  Job job;        // the job of the current sample
+  int job_id;
+  int tot_job;    // the job that tot accumulates for (-1: none)
   long long cost[2];
   long long stat[KADABRA_NSTAT];
   long long tot[KADABRA_NSTAT];
@@ -590,13 +604,13 @@ __device__ int block_pick_sorted(PiEntry* buf, int n, unsigned long long r, Ctl&
 // All threads of the CTA call this with the same idx.  Flags in c.flags tell
 // the caller what happened; the caller resets the tables afterwards.
 template <bool PK>
-__device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& T, Ctl& c, uint64_t idx,
+__device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, const Tables& T, Ctl& c, uint64_t idx,
                                            int64_t out_i) {
   const int tid = threadIdx.x, lane = lane_id(), wid = warp_id();
-  const GraphDev& G = P.g;
+  const GraphDev& G = J.g;
 
   if (tid == 0) {
-    const uint4 b0 = draw(P.seed, P.domain, idx, 0);
+    const uint4 b0 = draw(J.seed, J.domain, idx, 0);
     const uint64_t u = (uint64_t)b0.x | ((uint64_t)b0.y << 32);
     const uint64_t u2 = (uint64_t)b0.z | ((uint64_t)b0.w << 32);
     const int s = (int)__umul64hi(u, (uint64_t)G.n);
@@ -849,7 +863,7 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& 
     } else {
       c.stat[KADABRA_STAT_SIGMA_LO] = (long long)(lo & 0xFFFFFFFFull);
       c.stat[KADABRA_STAT_SIGMA_HI] = (long long)(lo >> 32);
-      c.r = below128(draw(P.seed, P.domain, idx, 1), lo);
+      c.r = below128(draw(J.seed, J.domain, idx, 1), lo);
     }
     int acc = 0;  // segment starts of the flat candidate index
     for (int w = 0; w < NW; ++w) {
@@ -924,9 +938,9 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& 
       if (dv < P.max_len) row[dv] = c.cv;
       if (dv + 1 < P.max_len) row[dv + 1] = c.cw;
     }
-    if (P.counts) {
-      if (dv > 0) atomicAdd(&P.counts[c.cv], 1u);
-      if (dw > 0) atomicAdd(&P.counts[c.cw], 1u);
+    if (J.counts) {
+      if (dv > 0) atomicAdd(&J.counts[c.cv], 1u);
+      if (dw > 0) atomicAdd(&J.counts[c.cw], 1u);
     }
   }
   uint32_t j = 2;
@@ -950,7 +964,7 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& 
           c.flags |= F_INTERNAL;
           c.r = 0;
         } else {
-          c.r = below128(draw(P.seed, P.domain, idx, j), ent_sig<PK>(T, T.hkv[px], (uint32_t)px));
+          c.r = below128(draw(J.seed, J.domain, idx, j), ent_sig<PK>(T, T.hkv[px], (uint32_t)px));
         }
         // scan whichever is shorter: the row of x, or the previous level
         c.mode = ((long long)(phi - plo) * 16 < (long long)deg) ? 1 : 0;
@@ -1026,7 +1040,7 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Tables& 
         c.next_x = y_pick;
         c.stat[KADABRA_STAT_BT_SCANNED] += pos_pick + 1;
         const int dn = dx - 1;
-        if (dn > 0 && P.counts) atomicAdd(&P.counts[y_pick], 1u);
+        if (dn > 0 && J.counts) atomicAdd(&J.counts[y_pick], 1u);
         if (want_path) {
           const int at = half == 0 ? dn : (dv + 1) + (dw - dn);
           if (at < P.max_len) P.paths[out_i * (int64_t)P.max_len + at] = y_pick;
@@ -1064,9 +1078,9 @@ __device__ void reset_tables(const Tables& T, Ctl& c, bool whole) {
 }
 
 // global-memory tiers share one body compiled once, outside the kernel
-__device__ __noinline__ void run_sample_global(const SampleParams& P, const Tables& T, Ctl& c, uint64_t idx,
-                                               int64_t out_i) {
-  run_sample<false>(P, T, c, idx, out_i);
+__device__ __noinline__ void run_sample_global(const SampleParams& P, const Job& J, const Tables& T, Ctl& c,
+                                               uint64_t idx, int64_t out_i) {
+  run_sample<false>(P, J, T, c, idx, out_i);
 }
 
 // layout of one CTA's tables in global memory (tiers M and L)
@@ -1152,6 +1166,17 @@ __device__ void enqueue(const SampleParams& P, int size_ctr, unsigned long long*
     atomicCAS(P.status, 0, (int)KADABRA_ERR_CAPACITY);
 }
 
+// Adds the CTA's accumulated work counters to their job's totals.
+__device__ void flush_totals(const SampleParams& P, Ctl& c) {
+  if (c.tot_job >= 0) {
+    long long* t = P.jobs ? P.jobs[c.tot_job].totals : P.job0.totals;
+    if (t)
+      for (int q = 0; q < KADABRA_NSTAT; ++q)
+        if (c.tot[q]) atomicAdd((unsigned long long*)&t[q], (unsigned long long)c.tot[q]);
+  }
+  for (int q = 0; q < KADABRA_NSTAT; ++q) c.tot[q] = 0;
+}
+
 // Records the outcome of one sample (per-sample outputs, totals, status).
 __device__ void finish_sample(const SampleParams& P, Ctl& c, uint64_t idx, int64_t out_i) {
   const int flags = c.flags;
@@ -1206,7 +1231,8 @@ __global__ void __launch_bounds__(NT, KD_MIN_BLOCKS) k_sample(SampleParams P) {
     for (uint32_t i = tid; i <= TS.hmask; i += NT) TS.hkv[i] = EMPTY;
   if (tid == 0) {
     for (int k = 0; k < KADABRA_NSTAT; ++k) c.tot[k] = 0;
-    c.ntotal = MODE == 0 ? P.count
+    c.tot_job = -1;
+    c.ntotal = MODE == 0 ? P.total_work
                : MODE == 2 ? min(P.ctr[Q_SIZE_B], (unsigned long long)P.deferred_cap)
                            : min(P.ctr[Q_SIZE_L], (unsigned long long)P.deferred_cap);
   }
@@ -1216,56 +1242,76 @@ __global__ void __launch_bounds__(NT, KD_MIN_BLOCKS) k_sample(SampleParams P) {
   for (;;) {
     if (tid == 0) c.cur = atomicAdd(&P.ctr[MODE == 0 ? Q_NEXT_A : MODE == 2 ? Q_NEXT_B : Q_NEXT_L], 1ull);
     __syncthreads();
-    const unsigned long long k = c.cur;
-    if (k >= ntotal) break;
-    const uint64_t idx = MODE == 0 ? P.first_idx + k : MODE == 2 ? P.qb[k] : P.ql[k];
-    const int64_t out_i = P.st_out ? (int64_t)(idx - P.first_idx) : -1;
+    if (c.cur >= ntotal) break;
+    // k: the sample's index in the launch's work space; its job and sample index
+    const unsigned long long k = MODE == 0 ? c.cur : MODE == 2 ? P.qb[c.cur] : P.ql[c.cur];
+    if (tid == 0) {
+      int j = 0;
+      if (P.jobs) {
+        int lo = 0, hi = P.njobs;
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (P.jobs[mid].work_begin <= k)
+            lo = mid;
+          else
+            hi = mid;
+        }
+        j = lo;
+      }
+      if (j != c.tot_job) {  // the counters so far belong to another job
+        flush_totals(P, c);
+        c.tot_job = j;
+      }
+      c.job = P.jobs ? P.jobs[j] : P.job0;
+      c.job_id = j;
+    }
+    __syncthreads();
+    const uint64_t idx = c.job.first_idx + (k - c.job.work_begin);
+    const int64_t out_i = P.st_out ? (int64_t)k : -1;
     bool done = false;
     if (MODE == 0) {
       if (!(P.tier_flags & TF_SKIP_S)) {
         clear_path_row(P, out_i);
-        run_sample<true>(P, TS, c, idx, out_i);
+        run_sample<true>(P, c.job, TS, c, idx, out_i);
         __syncthreads();
         done = c.flags != F_CAP;
         reset_tables<true>(TS, c, true);
       }
       if (!done) {
-        if (tid == 0) enqueue(P, Q_SIZE_B, P.qb, idx);
+        if (tid == 0) enqueue(P, Q_SIZE_B, P.qb, k);
         __syncthreads();
         continue;
       }
     } else if (MODE == 2) {
       if (!(P.tier_flags & TF_SKIP_B)) {
         clear_path_row(P, out_i);
-        run_sample<true>(P, TS, c, idx, out_i);
+        run_sample<true>(P, c.job, TS, c, idx, out_i);
         __syncthreads();
         done = c.flags != F_CAP;
         reset_tables<true>(TS, c, true);
       }
       if (!done && !(P.tier_flags & TF_SKIP_M)) {
         clear_path_row(P, out_i);
-        run_sample_global(P, TM, c, idx, out_i);
+        run_sample_global(P, c.job, TM, c, idx, out_i);
         __syncthreads();
         done = c.flags != F_CAP;
         reset_tables<false>(TM, c, false);
       }
       if (!done) {
-        if (tid == 0) enqueue(P, Q_SIZE_L, P.ql, idx);
+        if (tid == 0) enqueue(P, Q_SIZE_L, P.ql, k);
         __syncthreads();
         continue;
       }
     } else {
       clear_path_row(P, out_i);
-      run_sample_global(P, TM, c, idx, out_i);
+      run_sample_global(P, c.job, TM, c, idx, out_i);
       __syncthreads();
       reset_tables<false>(TM, c, false);
     }
     if (tid == 0) finish_sample(P, c, idx, out_i);
     __syncthreads();
   }
-  if (tid == 0 && P.totals)
-    for (int q = 0; q < KADABRA_NSTAT; ++q)
-      if (c.tot[q]) atomicAdd((unsigned long long*)&P.totals[q], (unsigned long long)c.tot[q]);
+  if (tid == 0) flush_totals(P, c);
 }
 
 size_t fast_smem_bytes() { return SLayout<FAST_HLOG>::BYTES; }
@@ -1317,6 +1363,49 @@ __global__ void __launch_bounds__(256) k_check(const uint32_t* __restrict__ coun
     if (mf) atomicMax(&out->max_f_bits, mf);
     if (mg) atomicMax(&out->max_g_bits, mg);
     if (fail) atomicOr(&out->fail, 1u);
+  }
+}
+
+// The stop test of several graphs in one launch: blockIdx.y selects the
+// graph, blockIdx.x strides over its nodes; each graph has its own tau,
+// omega, lambda and result.
+struct CheckJob {
+  const uint32_t* counts;
+  const double* lnL;
+  const double* lnU;
+  int64_t n;
+  uint64_t tau;
+  double omega;
+  double lambda;
+  CheckOut* out;
+};
+
+__global__ void __launch_bounds__(256) k_check_multi(const CheckJob* __restrict__ jobs) {
+  const CheckJob J = jobs[blockIdx.y];
+  const double t = (double)J.tau;
+  unsigned long long mf = 0, mg = 0;
+  unsigned fail = 0;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < J.n; v += (int64_t)gridDim.x * blockDim.x) {
+    double f, g;
+    f_and_g(J.counts[v], t, J.omega, J.lnL[v], J.lnU[v], &f, &g);
+    if (!(f <= J.lambda) || !(g <= J.lambda)) fail = 1;
+    const unsigned long long fb = (unsigned long long)__double_as_longlong(f);
+    const unsigned long long gb = (unsigned long long)__double_as_longlong(g);
+    mf = fb > mf ? fb : mf;
+    mg = gb > mg ? gb : mg;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long a = __shfl_xor_sync(FULL, mf, o);
+    const unsigned long long b = __shfl_xor_sync(FULL, mg, o);
+    mf = a > mf ? a : mf;
+    mg = b > mg ? b : mg;
+    fail |= __shfl_xor_sync(FULL, fail, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (mf) atomicMax(&J.out->max_f_bits, mf);
+    if (mg) atomicMax(&J.out->max_g_bits, mg);
+    if (fail) atomicOr(&J.out->fail, 1u);
   }
 }
 
@@ -1459,18 +1548,16 @@ int ceil_log2(uint64_t x) {
 
 }  // namespace
 
-// graph object (opaque in the ABI)
-struct kadabra_graph {
-  int32_t n = 0;
-  int64_t m = 0;
-  int directed = 0;
-  int32_t *rp = nullptr, *ci = nullptr, *rrp = nullptr, *rci = nullptr;
-  bool owns_csr = false;
-  int64_t vd = 0;
-  int device = 0;
-  int num_sms = 0;
-  // sampler workspace (allocated on first use)
-  bool ws_ready = false;
+namespace {
+
+// Sampler workspace: everything a sampler launch needs besides the graph and
+// its outputs.  A standalone graph owns one; the graphs of a batch share the
+// batch's, sized for its largest graph (their calls must not overlap).
+struct Workspace {
+  bool ready = false;
+  int device = 0, num_sms = 0;
+  int32_t max_n = 0;
+  int64_t max_m = 0;
   int grid_fast = 0, grid_big = 0, grid_gm = 0;
   size_t smem_fast = 0, smem_big = 0;
   unsigned long long* ctr = nullptr;
@@ -1487,22 +1574,55 @@ struct kadabra_graph {
   size_t gm_stride = 0;
   int gm_hlog = 0;
   int gm_lcap = 0;
+  Job* d_jobs = nullptr;  // job array of multi-graph launches
+  int jobs_cap = 0;
+  void* d_checks = nullptr;  // stop-test descriptors of multi-graph runs
+  int checks_cap = 0;
+  std::vector<void*> allocs;
+  ~Workspace() {
+    for (void* p : allocs)
+      if (p) cudaFree(p);
+  }
+};
+
+}  // namespace
+
+// graph object (opaque in the ABI)
+struct kadabra_graph {
+  int32_t n = 0;
+  int64_t m = 0;
+  int directed = 0;
+  int32_t *rp = nullptr, *ci = nullptr, *rrp = nullptr, *rci = nullptr;
+  int64_t vd = 0;
+  int device = 0;
+  int num_sms = 0;
   uint32_t flags = 0;
+  Workspace* ws = nullptr;
+  bool owns_ws = false;
+  bool is_view = false;  // a batch's view: released with the batch
   // run buffers
   uint32_t *counts = nullptr, *count0 = nullptr;
   double *lnL = nullptr, *lnU = nullptr, *btilde = nullptr;
   CheckOut* chk = nullptr;
   long long* totals = nullptr;
-  std::vector<void*> allocs;
+  std::vector<void*> allocs;  // CSR copies and run buffers
+};
+
+// G graphs whose CSRs share one device arena
+struct kadabra_batch {
+  int32_t G = 0;
+  std::vector<kadabra_graph*> views;
+  Workspace ws;
+  void* arena = nullptr;
 };
 
 namespace {
 
-kadabra_status dev_alloc(kadabra_graph* g, void** p, size_t bytes) {
+kadabra_status dev_alloc(std::vector<void*>& allocs, void** p, size_t bytes) {
   cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
   if (e != cudaSuccess)
     return fail(KADABRA_ERR_OOM, std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
-  g->allocs.push_back(*p);
+  allocs.push_back(*p);
   return KADABRA_OK;
 }
 
@@ -1512,143 +1632,177 @@ kadabra_status dev_alloc(kadabra_graph* g, void** p, size_t bytes) {
     if (s_ != KADABRA_OK) return s_;      \
   } while (0)
 
-kadabra_status ensure_workspace(kadabra_graph* g, uint64_t deferred_need) {
-  if (!g->ws_ready) {
-    KCK(cudaSetDevice(g->device));
-    g->smem_fast = fast_smem_bytes();
-    KCK(cudaFuncSetAttribute(k_sample<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g->smem_fast));
+void dev_free(std::vector<void*>& allocs, void* p) {
+  if (!p) return;
+  for (auto& a : allocs)
+    if (a == p) a = nullptr;
+  cudaFree(p);
+}
+
+kadabra_status ensure_ws(Workspace* w, uint64_t deferred_need, int njobs) {
+  if (!w->ready) {
+    KCK(cudaSetDevice(w->device));
+    w->smem_fast = fast_smem_bytes();
+    KCK(cudaFuncSetAttribute(k_sample<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->smem_fast));
     int per_sm = 0;
-    KCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample<0>, NT, g->smem_fast));
+    KCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample<0>, NT, w->smem_fast));
     if (per_sm < 1) return fail(KADABRA_ERR_CAPACITY, "sampler does not fit on an SM");
-    g->grid_fast = g->num_sms * per_sm;
-    g->smem_big = big_smem_bytes();
-    KCK(cudaFuncSetAttribute(k_sample<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g->smem_big));
-    KCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample<2>, NT, g->smem_big));
+    w->grid_fast = w->num_sms * per_sm;
+    w->smem_big = big_smem_bytes();
+    KCK(cudaFuncSetAttribute(k_sample<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->smem_big));
+    KCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample<2>, NT, w->smem_big));
     if (per_sm < 1) return fail(KADABRA_ERR_CAPACITY, "large-table sampler does not fit on an SM");
-    g->grid_big = g->num_sms * per_sm;
-    // global-memory tables for deferred samples: hash of >= 2n slots, lists of n
-    g->gm_hlog = std::max(12, ceil_log2(2ull * (uint64_t)g->n));
-    g->gm_lcap = g->n;
-    g->pcap_gm = (int)std::min<int64_t>(std::max<int64_t>(g->m, 1024), 1 << 18);
+    w->grid_big = w->num_sms * per_sm;
+    // n-sized tables for the rare samples beyond the others: hash of >= 2n slots, lists of n
+    w->gm_hlog = std::max(12, ceil_log2(2ull * (uint64_t)w->max_n));
+    w->gm_lcap = w->max_n;
+    w->pcap_gm = (int)std::min<int64_t>(std::max<int64_t>(w->max_m, 1024), 1 << 18);
     {
       size_t a, b, c2, d;
-      g->gm_stride = gm_layout(g->gm_hlog, g->gm_lcap, GM_MAXD, &a, &b, &c2, &d);
-      g->med_stride = gm_layout(MED_HLOG, MED_LCAP, MED_MAXD, &a, &b, &c2, &d);
+      w->gm_stride = gm_layout(w->gm_hlog, w->gm_lcap, GM_MAXD, &a, &b, &c2, &d);
+      w->med_stride = gm_layout(MED_HLOG, MED_LCAP, MED_MAXD, &a, &b, &c2, &d);
     }
-    const size_t per_cta = g->gm_stride + sizeof(PiEntry) * 2 * NW * (size_t)g->pcap_gm;
-    // deferred samples are rare on small-world graphs; 1 GiB of tables
-    // keeps at least a few CTAs busy on them
+    const size_t per_cta = w->gm_stride + sizeof(PiEntry) * 2 * NW * (size_t)w->pcap_gm;
+    // such samples are rare on small-world graphs; 1 GiB of tables keeps
+    // at least a few CTAs busy on them
     const size_t budget = (size_t)1 << 30;
-    g->grid_gm = (int)std::max<size_t>(1, std::min<size_t>((size_t)g->num_sms, budget / per_cta));
+    w->grid_gm = (int)std::max<size_t>(1, std::min<size_t>((size_t)w->num_sms, budget / per_cta));
     void* p;
-    KTRY(dev_alloc(g, &p, Q_COUNT * sizeof(unsigned long long)));
-    g->ctr = (unsigned long long*)p;
-    KTRY(dev_alloc(g, &p, sizeof(int32_t)));
-    g->status = (int32_t*)p;
-    KCK(cudaMemset(g->status, 0, sizeof(int32_t)));
-    KTRY(dev_alloc(g, &p, sizeof(PiEntry) * 2 * NW * (size_t)FAST_PCAP * g->grid_fast));
-    g->pi_fast = (PiEntry*)p;
-    KTRY(dev_alloc(g, &p, sizeof(PiEntry) * 2 * NW * (size_t)g->pcap_gm * g->grid_gm));
-    g->pi_gm = (PiEntry*)p;
-    KTRY(dev_alloc(g, &p, g->gm_stride * g->grid_gm));
-    g->gm_base = (unsigned char*)p;
-    KCK(cudaMemset(g->gm_base, 0, g->gm_stride * g->grid_gm));
-    for (int b = 0; b < g->grid_gm; ++b)  // every key word EMPTY (sigma stays 0)
-      KCK(cudaMemset(g->gm_base + (size_t)b * g->gm_stride, 0xFF, sizeof(unsigned long long) << g->gm_hlog));
-    KTRY(dev_alloc(g, &p, g->med_stride * g->grid_big));
-    g->med_base = (unsigned char*)p;
-    KCK(cudaMemset(g->med_base, 0, g->med_stride * g->grid_big));
-    for (int b = 0; b < g->grid_big; ++b)
-      KCK(cudaMemset(g->med_base + (size_t)b * g->med_stride, 0xFF, sizeof(unsigned long long) << MED_HLOG));
-    KTRY(dev_alloc(g, &p, sizeof(uint32_t) * (size_t)g->n));
-    g->counts = (uint32_t*)p;
-    KTRY(dev_alloc(g, &p, sizeof(uint32_t) * (size_t)g->n));
-    g->count0 = (uint32_t*)p;
-    KTRY(dev_alloc(g, &p, sizeof(double) * (size_t)g->n));
-    g->lnL = (double*)p;
-    KTRY(dev_alloc(g, &p, sizeof(double) * (size_t)g->n));
-    g->lnU = (double*)p;
-    KTRY(dev_alloc(g, &p, sizeof(double) * (size_t)g->n));
-    g->btilde = (double*)p;
-    KTRY(dev_alloc(g, &p, sizeof(CheckOut)));
-    g->chk = (CheckOut*)p;
-    KTRY(dev_alloc(g, &p, sizeof(long long) * KADABRA_NSTAT));
-    g->totals = (long long*)p;
+    KTRY(dev_alloc(w->allocs, &p, Q_COUNT * sizeof(unsigned long long)));
+    w->ctr = (unsigned long long*)p;
+    KTRY(dev_alloc(w->allocs, &p, sizeof(int32_t)));
+    w->status = (int32_t*)p;
+    KCK(cudaMemset(w->status, 0, sizeof(int32_t)));
+    KTRY(dev_alloc(w->allocs, &p, sizeof(PiEntry) * 2 * NW * (size_t)FAST_PCAP * w->grid_fast));
+    w->pi_fast = (PiEntry*)p;
+    KTRY(dev_alloc(w->allocs, &p, sizeof(PiEntry) * 2 * NW * (size_t)w->pcap_gm * w->grid_gm));
+    w->pi_gm = (PiEntry*)p;
+    KTRY(dev_alloc(w->allocs, &p, w->gm_stride * w->grid_gm));
+    w->gm_base = (unsigned char*)p;
+    KCK(cudaMemset(w->gm_base, 0, w->gm_stride * w->grid_gm));
+    for (int b = 0; b < w->grid_gm; ++b)  // every key word EMPTY (sigma stays 0)
+      KCK(cudaMemset(w->gm_base + (size_t)b * w->gm_stride, 0xFF, sizeof(unsigned long long) << w->gm_hlog));
+    KTRY(dev_alloc(w->allocs, &p, w->med_stride * w->grid_big));
+    w->med_base = (unsigned char*)p;
+    KCK(cudaMemset(w->med_base, 0, w->med_stride * w->grid_big));
+    for (int b = 0; b < w->grid_big; ++b)
+      KCK(cudaMemset(w->med_base + (size_t)b * w->med_stride, 0xFF, sizeof(unsigned long long) << MED_HLOG));
     KCK(cudaDeviceSynchronize());
-    g->ws_ready = true;
+    w->ready = true;
   }
-  if (deferred_need > g->deferred_cap) {
+  if (deferred_need > w->deferred_cap) {
     KCK(cudaDeviceSynchronize());
-    for (unsigned long long** q : {&g->qb, &g->ql}) {
-      if (*q) {
-        for (auto& a : g->allocs)
-          if (a == *q) a = nullptr;
-        cudaFree(*q);
-        *q = nullptr;
-      }
-    }
+    dev_free(w->allocs, w->qb);
+    dev_free(w->allocs, w->ql);
+    w->qb = w->ql = nullptr;
     const uint64_t cap = std::max<uint64_t>(deferred_need, 1 << 16);
     void* p;
-    KTRY(dev_alloc(g, &p, sizeof(unsigned long long) * cap));
-    g->qb = (unsigned long long*)p;
-    KTRY(dev_alloc(g, &p, sizeof(unsigned long long) * cap));
-    g->ql = (unsigned long long*)p;
-    g->deferred_cap = cap;
+    KTRY(dev_alloc(w->allocs, &p, sizeof(unsigned long long) * cap));
+    w->qb = (unsigned long long*)p;
+    KTRY(dev_alloc(w->allocs, &p, sizeof(unsigned long long) * cap));
+    w->ql = (unsigned long long*)p;
+    w->deferred_cap = cap;
+  }
+  if (njobs > w->jobs_cap) {
+    KCK(cudaDeviceSynchronize());
+    dev_free(w->allocs, w->d_jobs);
+    void* p;
+    KTRY(dev_alloc(w->allocs, &p, sizeof(Job) * (size_t)njobs));
+    w->d_jobs = (Job*)p;
+    w->jobs_cap = njobs;
   }
   return KADABRA_OK;
 }
 
-SampleParams base_params(kadabra_graph* g) {
+// per-graph run buffers (hit counters, computeDelta tables, results)
+kadabra_status ensure_run_buffers(kadabra_graph* g) {
+  if (g->counts) return KADABRA_OK;
+  void* p;
+  KTRY(dev_alloc(g->allocs, &p, sizeof(uint32_t) * (size_t)g->n));
+  g->counts = (uint32_t*)p;
+  KTRY(dev_alloc(g->allocs, &p, sizeof(uint32_t) * (size_t)g->n));
+  g->count0 = (uint32_t*)p;
+  KTRY(dev_alloc(g->allocs, &p, sizeof(double) * (size_t)g->n));
+  g->lnL = (double*)p;
+  KTRY(dev_alloc(g->allocs, &p, sizeof(double) * (size_t)g->n));
+  g->lnU = (double*)p;
+  KTRY(dev_alloc(g->allocs, &p, sizeof(double) * (size_t)g->n));
+  g->btilde = (double*)p;
+  KTRY(dev_alloc(g->allocs, &p, sizeof(CheckOut)));
+  g->chk = (CheckOut*)p;
+  KTRY(dev_alloc(g->allocs, &p, sizeof(long long) * KADABRA_NSTAT));
+  g->totals = (long long*)p;
+  return KADABRA_OK;
+}
+
+kadabra_status ensure_workspace(kadabra_graph* g, uint64_t deferred_need) {
+  KTRY(ensure_ws(g->ws, deferred_need, 0));
+  return ensure_run_buffers(g);
+}
+
+GraphDev graph_dev(const kadabra_graph* g) {
+  GraphDev d;
+  d.n = g->n;
+  d.m = g->m;
+  d.rp = g->rp;
+  d.ci = g->ci;
+  d.rrp = g->directed ? g->rrp : g->rp;
+  d.rci = g->directed ? g->rci : g->ci;
+  return d;
+}
+
+SampleParams ws_params(const Workspace* w, uint32_t flags) {
   SampleParams P;
   std::memset(&P, 0, sizeof(P));
-  P.g.n = g->n;
-  P.g.m = g->m;
-  P.g.rp = g->rp;
-  P.g.ci = g->ci;
-  P.g.rrp = g->directed ? g->rrp : g->rp;
-  P.g.rci = g->directed ? g->rci : g->ci;
-  P.ctr = g->ctr;
-  P.qb = g->qb;
-  P.ql = g->ql;
-  P.deferred_cap = g->deferred_cap;
-  P.status = g->status;
-  P.med_base = g->med_base;
-  P.med_stride = g->med_stride;
-  P.gm_base = g->gm_base;
-  P.gm_stride = g->gm_stride;
-  P.gm_hlog = g->gm_hlog;
-  P.gm_lcap = g->gm_lcap;
+  P.njobs = 1;
+  P.ctr = w->ctr;
+  P.qb = w->qb;
+  P.ql = w->ql;
+  P.deferred_cap = w->deferred_cap;
+  P.status = w->status;
+  P.med_base = w->med_base;
+  P.med_stride = w->med_stride;
+  P.gm_base = w->gm_base;
+  P.gm_stride = w->gm_stride;
+  P.gm_hlog = w->gm_hlog;
+  P.gm_lcap = w->gm_lcap;
   P.tier_flags = 0;
-  if (g->flags & KADABRA_FLAG_GLOBAL_TABLES) P.tier_flags |= TF_SKIP_S | TF_SKIP_B | TF_SKIP_M;
-  if (g->flags & KADABRA_FLAG_MEDIUM_TABLES) P.tier_flags |= TF_SKIP_S | TF_SKIP_B;
-  if (g->flags & KADABRA_FLAG_LARGE_SHARED_TABLES) P.tier_flags |= TF_SKIP_S;
+  if (flags & KADABRA_FLAG_GLOBAL_TABLES) P.tier_flags |= TF_SKIP_S | TF_SKIP_B | TF_SKIP_M;
+  if (flags & KADABRA_FLAG_MEDIUM_TABLES) P.tier_flags |= TF_SKIP_S | TF_SKIP_B;
+  if (flags & KADABRA_FLAG_LARGE_SHARED_TABLES) P.tier_flags |= TF_SKIP_S;
+  return P;
+}
+
+SampleParams base_params(kadabra_graph* g) {
+  SampleParams P = ws_params(g->ws, g->flags);
+  P.job0.g = graph_dev(g);
   return P;
 }
 
 // launches the main sampler grid, then the large-table pass and the
 // n-sized-table pass for the samples queued by the launch before (each exits
 // at once when its queue is empty)
-kadabra_status launch_sampler(kadabra_graph* g, SampleParams P, cudaStream_t st) {
-  KCK(cudaMemsetAsync(g->ctr, 0, Q_COUNT * sizeof(unsigned long long), st));
-  P.pi_base = g->pi_fast;
+kadabra_status launch_sampler(Workspace* w, SampleParams P, cudaStream_t st) {
+  KCK(cudaMemsetAsync(w->ctr, 0, Q_COUNT * sizeof(unsigned long long), st));
+  P.pi_base = w->pi_fast;
   P.pcap = FAST_PCAP;
-  k_sample<0><<<g->grid_fast, NT, g->smem_fast, st>>>(P);
+  k_sample<0><<<w->grid_fast, NT, w->smem_fast, st>>>(P);
   KCK(cudaGetLastError());
-  k_sample<2><<<g->grid_big, NT, g->smem_big, st>>>(P);
+  k_sample<2><<<w->grid_big, NT, w->smem_big, st>>>(P);
   KCK(cudaGetLastError());
-  P.pi_base = g->pi_gm;
-  P.pcap = g->pcap_gm;
-  k_sample<1><<<g->grid_gm, NT, sizeof(Ctl), st>>>(P);
+  P.pi_base = w->pi_gm;
+  P.pcap = w->pcap_gm;
+  k_sample<1><<<w->grid_gm, NT, sizeof(Ctl), st>>>(P);
   KCK(cudaGetLastError());
   return KADABRA_OK;
 }
 
-kadabra_status read_status(kadabra_graph* g, cudaStream_t st) {
+kadabra_status read_status(Workspace* w, cudaStream_t st) {
   int32_t h = 0;
-  KCK(cudaMemcpyAsync(&h, g->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  KCK(cudaMemcpyAsync(&h, w->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   KCK(cudaStreamSynchronize(st));
   if (h != 0) {
-    KCK(cudaMemsetAsync(g->status, 0, sizeof(int32_t), st));
+    KCK(cudaMemsetAsync(w->status, 0, sizeof(int32_t), st));
     KCK(cudaStreamSynchronize(st));
     const char* what = h == KADABRA_ERR_SIGMA_OVERFLOW ? "a shortest-path count exceeded 2^64-1"
                        : h == KADABRA_ERR_CAPACITY     ? "a sampler capacity bound was exceeded"
@@ -1671,6 +1825,14 @@ int64_t floor_log2_pos(int64_t x) {  // x >= 1
 double omega_host(double lambda, double delta, int64_t vd) {
   const int64_t fl = vd - 2 >= 1 ? floor_log2_pos(vd - 2) : 0;
   return (0.5 / (lambda * lambda)) * ((double)(fl + 1) + std::log(2.0 / delta));
+}
+
+// Samples between stop tests when the caller leaves it to the library: about
+// 32 tests up to the cap, at least 1024 samples each.  A function of omega
+// only, so every path that uses it samples and stops identically.
+uint64_t auto_check_interval(double omega) {
+  const double k = std::ceil(omega / 32.0);
+  return k < 1024.0 ? 1024 : (uint64_t)k;
 }
 
 // ---------------------------------------------------------------- computeDelta
@@ -1836,6 +1998,12 @@ kadabra_status new_graph(int32_t n, int64_t m, int directed, kadabra_graph** out
     delete g;
     return fail(KADABRA_ERR_CUDA, "no CUDA device");
   }
+  g->ws = new Workspace;
+  g->ws->device = g->device;
+  g->ws->num_sms = g->num_sms;
+  g->ws->max_n = n;
+  g->ws->max_m = m;
+  g->owns_ws = true;
   *g_out = g;
   return KADABRA_OK;
 }
@@ -1926,20 +2094,19 @@ kadabra_status kadabra_load_csr(int32_t n, int64_t m, const int32_t* row_ptr, co
   KTRY(new_graph(n, m, directed, out, &g));
   if (!row_ptr || (m > 0 && !col) || (directed && (!rrow_ptr || (m > 0 && !rcol))) ||
       (!directed && (rrow_ptr || rcol))) {
-    delete g;
+    kadabra_free_graph(g);
     return fail(KADABRA_ERR_ARG, "missing or unexpected CSR arrays");
   }
   if (row_ptr[0] != 0 || row_ptr[n] != m || (directed && (rrow_ptr[0] != 0 || rrow_ptr[n] != m))) {
-    delete g;
+    kadabra_free_graph(g);
     return fail(KADABRA_ERR_CSR, "row_ptr[0] must be 0 and row_ptr[n] must equal m");
   }
-  g->owns_csr = true;
   kadabra_status st = KADABRA_OK;
   void* p;
   const size_t rb = sizeof(int32_t) * ((size_t)n + 1), cb = sizeof(int32_t) * (size_t)m;
-  if ((st = dev_alloc(g, &p, rb)) != KADABRA_OK) goto bad;
+  if ((st = dev_alloc(g->allocs, &p, rb)) != KADABRA_OK) goto bad;
   g->rp = (int32_t*)p;
-  if ((st = dev_alloc(g, &p, cb)) != KADABRA_OK) goto bad;
+  if ((st = dev_alloc(g->allocs, &p, cb)) != KADABRA_OK) goto bad;
   g->ci = (int32_t*)p;
   if (cudaMemcpy(g->rp, row_ptr, rb, cudaMemcpyHostToDevice) != cudaSuccess ||
       (m > 0 && cudaMemcpy(g->ci, col, cb, cudaMemcpyHostToDevice) != cudaSuccess)) {
@@ -1947,9 +2114,9 @@ kadabra_status kadabra_load_csr(int32_t n, int64_t m, const int32_t* row_ptr, co
     goto bad;
   }
   if (directed) {
-    if ((st = dev_alloc(g, &p, rb)) != KADABRA_OK) goto bad;
+    if ((st = dev_alloc(g->allocs, &p, rb)) != KADABRA_OK) goto bad;
     g->rrp = (int32_t*)p;
-    if ((st = dev_alloc(g, &p, cb)) != KADABRA_OK) goto bad;
+    if ((st = dev_alloc(g->allocs, &p, cb)) != KADABRA_OK) goto bad;
     g->rci = (int32_t*)p;
     if (cudaMemcpy(g->rrp, rrow_ptr, rb, cudaMemcpyHostToDevice) != cudaSuccess ||
         (m > 0 && cudaMemcpy(g->rci, rcol, cb, cudaMemcpyHostToDevice) != cudaSuccess)) {
@@ -1972,24 +2139,24 @@ kadabra_status kadabra_load_csr_device(int32_t n, int64_t m, const int32_t* d_ro
   KTRY(new_graph(n, m, directed, out, &g));
   if (!d_row_ptr || (m > 0 && !d_col) || (directed && (!d_rrow_ptr || (m > 0 && !d_rcol))) ||
       (!directed && (d_rrow_ptr || d_rcol))) {
-    delete g;
+    kadabra_free_graph(g);
     return fail(KADABRA_ERR_ARG, "missing or unexpected CSR arrays");
   }
   int32_t ends[2];
   if (cudaMemcpy(&ends[0], d_row_ptr, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess ||
       cudaMemcpy(&ends[1], d_row_ptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
-    delete g;
+    kadabra_free_graph(g);
     return fail(KADABRA_ERR_ARG, "row_ptr is not readable device memory");
   }
   if (ends[0] != 0 || ends[1] != m) {
-    delete g;
+    kadabra_free_graph(g);
     return fail(KADABRA_ERR_CSR, "row_ptr[0] must be 0 and row_ptr[n] must equal m");
   }
   if (directed) {
     if (cudaMemcpy(&ends[0], d_rrow_ptr, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess ||
         cudaMemcpy(&ends[1], d_rrow_ptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess ||
         ends[0] != 0 || ends[1] != m) {
-      delete g;
+      kadabra_free_graph(g);
       return fail(KADABRA_ERR_CSR, "reverse row_ptr[0] must be 0 and row_ptr[n] must equal m");
     }
   }
@@ -2007,10 +2174,11 @@ kadabra_status kadabra_load_csr_device(int32_t n, int64_t m, const int32_t* d_ro
 }
 
 void kadabra_free_graph(kadabra_graph* g) {
-  if (!g) return;
+  if (!g || g->is_view) return;
   cudaDeviceSynchronize();
   for (void* p : g->allocs)
     if (p) cudaFree(p);
+  if (g->owns_ws) delete g->ws;
   delete g;
 }
 
@@ -2037,13 +2205,14 @@ kadabra_status kadabra_sample_batch(kadabra_graph* g, uint64_t seed, uint32_t do
   if (count == 0) return KADABRA_OK;
   KTRY(ensure_workspace(g, count));
   SampleParams P = base_params(g);
-  P.seed = seed;
-  P.domain = domain;
-  P.first_idx = first_idx;
-  P.count = count;
-  P.counts = d_counts;
-  P.totals = reinterpret_cast<long long*>(d_totals);
-  return launch_sampler(g, P, as_stream(stream));
+  P.job0.seed = seed;
+  P.job0.domain = domain;
+  P.job0.first_idx = first_idx;
+  P.job0.count = count;
+  P.job0.counts = d_counts;
+  P.job0.totals = reinterpret_cast<long long*>(d_totals);
+  P.total_work = count;
+  return launch_sampler(g->ws, P, as_stream(stream));
 }
 
 kadabra_status kadabra_sample_batch_noalloc(int32_t n, int64_t m, const int32_t* d_row_ptr, const int32_t* d_col,
@@ -2065,18 +2234,20 @@ kadabra_status kadabra_sample_batch_noalloc(int32_t n, int64_t m, const int32_t*
   cudaStream_t st = as_stream(stream);
   SampleParams P;
   std::memset(&P, 0, sizeof(P));
-  P.g.n = n;
-  P.g.m = m;
-  P.g.rp = d_row_ptr;
-  P.g.ci = d_col;
-  P.g.rrp = directed ? d_rrow_ptr : d_row_ptr;
-  P.g.rci = directed ? d_rcol : d_col;
-  P.seed = seed;
-  P.domain = domain;
-  P.first_idx = first_idx;
-  P.count = count;
-  P.counts = d_counts;
-  P.totals = reinterpret_cast<long long*>(d_totals);
+  P.job0.g.n = n;
+  P.job0.g.m = m;
+  P.job0.g.rp = d_row_ptr;
+  P.job0.g.ci = d_col;
+  P.job0.g.rrp = directed ? d_rrow_ptr : d_row_ptr;
+  P.job0.g.rci = directed ? d_rcol : d_col;
+  P.job0.seed = seed;
+  P.job0.domain = domain;
+  P.job0.first_idx = first_idx;
+  P.job0.count = count;
+  P.job0.counts = d_counts;
+  P.job0.totals = reinterpret_cast<long long*>(d_totals);
+  P.njobs = 1;
+  P.total_work = count;
   P.ctr = reinterpret_cast<unsigned long long*>(d->scratch + NA_OFF_CTR);
   P.status = reinterpret_cast<int32_t*>(d->scratch + NA_OFF_STATUS);
   P.qb = reinterpret_cast<unsigned long long*>(d->scratch + NA_OFF_QB);
@@ -2108,11 +2279,11 @@ kadabra_status kadabra_sample_batch_noalloc(int32_t n, int64_t m, const int32_t*
 
 kadabra_status kadabra_sync_status(kadabra_graph* g, void* stream) {
   if (!g) return fail(KADABRA_ERR_ARG, "graph is NULL");
-  if (!g->ws_ready) {
+  if (!g->ws->ready) {
     KCK(cudaStreamSynchronize(as_stream(stream)));
     return KADABRA_OK;
   }
-  return read_status(g, as_stream(stream));
+  return read_status(g->ws, as_stream(stream));
 }
 
 kadabra_status kadabra_sample_paths(kadabra_graph* g, uint64_t seed, uint32_t domain, uint64_t first_idx,
@@ -2141,17 +2312,18 @@ kadabra_status kadabra_sample_paths(kadabra_graph* g, uint64_t seed, uint32_t do
     return fail(KADABRA_ERR_OOM, "sample_paths buffers");
   }
   SampleParams P = base_params(g);
-  P.seed = seed;
-  P.domain = domain;
-  P.first_idx = first_idx;
-  P.count = count;
+  P.job0.seed = seed;
+  P.job0.domain = domain;
+  P.job0.first_idx = first_idx;
+  P.job0.count = count;
+  P.total_work = count;
   P.st_out = d_st;
   P.path_len = d_pl;
   P.paths = d_paths;
   P.max_len = max_len;
   P.stats = d_stats;
   P.sstatus = d_ss;
-  rc = launch_sampler(g, P, 0);
+  rc = launch_sampler(g->ws, P, 0);
   if (rc == KADABRA_OK) {
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) rc = fail(KADABRA_ERR_CUDA, std::string("sampler: ") + cudaGetErrorString(e));
@@ -2169,7 +2341,7 @@ kadabra_status kadabra_sample_paths(kadabra_graph* g, uint64_t seed, uint32_t do
       for (size_t i = 0; i < hs.size(); ++i) stats[i] = hs[i];
   }
   cleanup();
-  if (rc == KADABRA_OK) rc = read_status(g, 0);
+  if (rc == KADABRA_OK) rc = read_status(g->ws, 0);
   return rc;
 }
 
@@ -2250,7 +2422,6 @@ kadabra_status kadabra_run(kadabra_graph* g, double lambda, double delta, int32_
   kadabra_config cfg;
   kadabra_config_default(&cfg);
   if (cfg_in) cfg = *cfg_in;
-  if (cfg.check_interval == 0) cfg.check_interval = 1000;
   auto finish = [&](kadabra_status s) {
     out->status = s;
     return s;
@@ -2269,13 +2440,14 @@ kadabra_status kadabra_run(kadabra_graph* g, double lambda, double delta, int32_
   uint64_t alpha = (uint64_t)std::floor(out->omega / 100.0);
   if (alpha < 1) alpha = 1;
   out->alpha = alpha;
-  const uint64_t K = cfg.check_interval;
+  const uint64_t K = cfg.check_interval ? cfg.check_interval : auto_check_interval(out->omega);
+  out->check_interval = K;
 
   kadabra_status rc = ensure_workspace(g, std::max<uint64_t>(alpha, std::min<uint64_t>(K, out->omega_cap)));
   if (rc != KADABRA_OK) return finish(rc);
   SampleParams P = base_params(g);
-  P.seed = seed;
-  P.totals = g->totals;
+  P.job0.seed = seed;
+  P.job0.totals = g->totals;
 #define RUN_CK(call)                                                                     \
   do {                                                                                   \
     cudaError_t e_ = (call);                                                             \
@@ -2286,14 +2458,15 @@ kadabra_status kadabra_run(kadabra_graph* g, double lambda, double delta, int32_
   RUN_CK(cudaMemsetAsync(g->counts, 0, sizeof(uint32_t) * n, st));
 
   // warm-up (Alg. 2 lines 1-5): alpha samples in RNG domain 1
-  P.domain = 1;
-  P.first_idx = 0;
-  P.count = alpha;
-  P.counts = g->count0;
-  if ((rc = launch_sampler(g, P, st)) != KADABRA_OK) return finish(rc);
+  P.job0.domain = 1;
+  P.job0.first_idx = 0;
+  P.job0.count = alpha;
+  P.job0.counts = g->count0;
+  P.total_work = alpha;
+  if ((rc = launch_sampler(g->ws, P, st)) != KADABRA_OK) return finish(rc);
   std::vector<uint32_t> c0((size_t)n);
   RUN_CK(cudaMemcpyAsync(c0.data(), g->count0, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, st));
-  if ((rc = read_status(g, st)) != KADABRA_OK) return finish(rc);
+  if ((rc = read_status(g->ws, st)) != KADABRA_OK) return finish(rc);
 
   // computeDelta (Alg. 2 lines 6-14)
   std::vector<double> hL((size_t)n), hU((size_t)n);
@@ -2308,13 +2481,14 @@ kadabra_status kadabra_run(kadabra_graph* g, double lambda, double delta, int32_
   uint64_t tau = 0;
   const uint64_t cap = out->omega_cap;
   CheckOut h;
-  P.domain = 0;
-  P.counts = g->counts;
+  P.job0.domain = 0;
+  P.job0.counts = g->counts;
   for (;;) {
     const uint64_t B = std::min<uint64_t>(K, cap - tau);
-    P.first_idx = tau;
-    P.count = B;
-    if ((rc = launch_sampler(g, P, st)) != KADABRA_OK) return finish(rc);
+    P.job0.first_idx = tau;
+    P.job0.count = B;
+    P.total_work = B;
+    if ((rc = launch_sampler(g->ws, P, st)) != KADABRA_OK) return finish(rc);
     tau += B;
     if (tau >= cap) break;
     out->checks++;
@@ -2322,7 +2496,7 @@ kadabra_status kadabra_run(kadabra_graph* g, double lambda, double delta, int32_
     k_check<<<check_blocks, 256, 0, st>>>(g->counts, g->lnL, g->lnU, n, tau, out->omega, lambda, g->chk);
     RUN_CK(cudaGetLastError());
     RUN_CK(cudaMemcpyAsync(&h, g->chk, sizeof(CheckOut), cudaMemcpyDeviceToHost, st));
-    if ((rc = read_status(g, st)) != KADABRA_OK) return finish(rc);
+    if ((rc = read_status(g->ws, st)) != KADABRA_OK) return finish(rc);
     if (!h.fail) {
       out->stopped_early = 1;
       break;
@@ -2348,12 +2522,333 @@ kadabra_status kadabra_run(kadabra_graph* g, double lambda, double delta, int32_
                            cudaMemcpyDeviceToHost, st));
   long long tot[KADABRA_NSTAT];
   RUN_CK(cudaMemcpyAsync(tot, g->totals, sizeof(tot), cudaMemcpyDeviceToHost, st));
-  if ((rc = read_status(g, st)) != KADABRA_OK) return finish(rc);
+  if ((rc = read_status(g->ws, st)) != KADABRA_OK) return finish(rc);
   std::memcpy(&out->max_f, &h.max_f_bits, sizeof(double));
   std::memcpy(&out->max_g, &h.max_g_bits, sizeof(double));
   for (int q = 0; q < KADABRA_NSTAT; ++q) out->totals[q] = tot[q];
 #undef RUN_CK
   return finish(KADABRA_OK);
+}
+
+
+kadabra_status kadabra_load_batch(int32_t G, const int32_t* n, const int64_t* m, const int32_t* const* row_ptr,
+                                  const int32_t* const* col, const int* directed, const int32_t* const* rrow_ptr,
+                                  const int32_t* const* rcol, kadabra_batch** out) {
+  if (!out) return fail(KADABRA_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (G < 1 || !n || !m || !row_ptr || !col) return fail(KADABRA_ERR_ARG, "bad batch arguments");
+  kadabra_batch* b = new kadabra_batch;
+  b->G = G;
+  auto bail = [&](kadabra_status st) {
+    kadabra_free_batch(b);
+    return st;
+  };
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return bail(fail(KADABRA_ERR_CUDA, "no CUDA device"));
+  // arena layout: per graph row_ptr, col[, rrow_ptr, rcol], each 256-byte aligned
+  std::vector<size_t> off;
+  size_t total = 0;
+  auto place = [&](size_t bytes) {
+    off.push_back(total);
+    total += (bytes + 255) & ~size_t(255);
+  };
+  for (int32_t i = 0; i < G; ++i) {
+    const bool dir = directed && directed[i];
+    if (n[i] < 2 || n[i] > (1 << 24) || m[i] < 0 || m[i] >= ((int64_t)1 << 31) || !row_ptr[i] ||
+        (m[i] > 0 && !col[i]) || (dir && (!rrow_ptr || !rcol || !rrow_ptr[i] || (m[i] > 0 && !rcol[i]))))
+      return bail(fail(KADABRA_ERR_ARG, "bad arrays or sizes for graph " + std::to_string(i)));
+    if (row_ptr[i][0] != 0 || row_ptr[i][n[i]] != m[i] || (dir && (rrow_ptr[i][0] != 0 || rrow_ptr[i][n[i]] != m[i])))
+      return bail(fail(KADABRA_ERR_CSR, "row_ptr[0] must be 0 and row_ptr[n] must equal m (graph " +
+                                            std::to_string(i) + ")"));
+    place(sizeof(int32_t) * ((size_t)n[i] + 1));
+    place(sizeof(int32_t) * (size_t)m[i]);
+    if (dir) {
+      place(sizeof(int32_t) * ((size_t)n[i] + 1));
+      place(sizeof(int32_t) * (size_t)m[i]);
+    }
+  }
+  {
+    const cudaError_t e = cudaMalloc(&b->arena, total ? total : 16);
+    if (e != cudaSuccess) return bail(fail(KADABRA_ERR_OOM, std::string("batch arena: ") + cudaGetErrorString(e)));
+  }
+  unsigned char* base = static_cast<unsigned char*>(b->arena);
+  size_t k = 0;
+  int32_t max_n = 0;
+  int64_t max_m = 0;
+  for (int32_t i = 0; i < G; ++i) {
+    const bool dir = directed && directed[i];
+    kadabra_graph* g = new kadabra_graph;
+    b->views.push_back(g);
+    g->n = n[i];
+    g->m = m[i];
+    g->directed = dir ? 1 : 0;
+    g->device = dev;
+    g->num_sms = sms;
+    g->ws = &b->ws;
+    g->is_view = true;
+    const size_t rb = sizeof(int32_t) * ((size_t)n[i] + 1), cb = sizeof(int32_t) * (size_t)m[i];
+    g->rp = reinterpret_cast<int32_t*>(base + off[k++]);
+    g->ci = reinterpret_cast<int32_t*>(base + off[k++]);
+    if (cudaMemcpy(g->rp, row_ptr[i], rb, cudaMemcpyHostToDevice) != cudaSuccess ||
+        (m[i] > 0 && cudaMemcpy(g->ci, col[i], cb, cudaMemcpyHostToDevice) != cudaSuccess))
+      return bail(fail(KADABRA_ERR_CUDA, "batch CSR upload failed"));
+    if (dir) {
+      g->rrp = reinterpret_cast<int32_t*>(base + off[k++]);
+      g->rci = reinterpret_cast<int32_t*>(base + off[k++]);
+      if (cudaMemcpy(g->rrp, rrow_ptr[i], rb, cudaMemcpyHostToDevice) != cudaSuccess ||
+          (m[i] > 0 && cudaMemcpy(g->rci, rcol[i], cb, cudaMemcpyHostToDevice) != cudaSuccess))
+        return bail(fail(KADABRA_ERR_CUDA, "batch reverse CSR upload failed"));
+    }
+    const kadabra_status st = finish_load(g);
+    if (st != KADABRA_OK) return bail(fail(st, std::string(kadabra_last_error()) + " (graph " + std::to_string(i) + ")"));
+    max_n = std::max(max_n, n[i]);
+    max_m = std::max(max_m, m[i]);
+  }
+  b->ws.device = dev;
+  b->ws.num_sms = sms;
+  b->ws.max_n = max_n;
+  b->ws.max_m = max_m;
+  *out = b;
+  return KADABRA_OK;
+}
+
+void kadabra_free_batch(kadabra_batch* b) {
+  if (!b) return;
+  cudaDeviceSynchronize();
+  for (kadabra_graph* g : b->views) {
+    for (void* p : g->allocs)
+      if (p) cudaFree(p);
+    delete g;
+  }
+  if (b->arena) cudaFree(b->arena);
+  delete b;
+}
+
+kadabra_status kadabra_batch_graph(kadabra_batch* b, int32_t i, kadabra_graph** view) {
+  if (!b || !view || i < 0 || i >= b->G) return fail(KADABRA_ERR_ARG, "bad batch graph index");
+  *view = b->views[i];
+  return KADABRA_OK;
+}
+
+kadabra_status kadabra_run_batch(kadabra_batch* b, const double* lambda, const double* delta, const uint64_t* seed,
+                                 const kadabra_config* cfg_in, kadabra_result* out) {
+  if (!b || !lambda || !delta || !seed || !out) return fail(KADABRA_ERR_ARG, "bad batch run arguments");
+  kadabra_config cfg;
+  kadabra_config_default(&cfg);
+  if (cfg_in) cfg = *cfg_in;
+  if (cfg.vd != 0) return fail(KADABRA_ERR_ARG, "a batch uses each graph's own VD bound (cfg->vd must be 0)");
+  if (!(cfg.eps >= 0.0 && cfg.eps < 0.5)) return fail(KADABRA_ERR_ARG, "eps must be in [0, 0.5)");
+  const int G = b->G;
+  cudaStream_t st = as_stream(cfg.stream);
+  struct State {
+    kadabra_graph* g;
+    uint64_t cap, alpha, K, tau;
+    bool done;
+  };
+  std::vector<State> S(G);
+  uint64_t sum_alpha = 0, sum_k = 0;
+  for (int i = 0; i < G; ++i) {
+    kadabra_result& r = out[i];
+    uint32_t* ch = r.counts;
+    double* bh = r.btilde;
+    uint32_t* cd = r.d_counts;
+    double* bd = r.d_btilde;
+    int32_t* tk = r.topk;
+    std::memset(&r, 0, sizeof(r));
+    r.counts = ch;
+    r.btilde = bh;
+    r.d_counts = cd;
+    r.d_btilde = bd;
+    r.topk = tk;
+    if (!(lambda[i] > 0.0 && lambda[i] < 1.0) || !(delta[i] > 0.0 && delta[i] < 1.0))
+      return fail(KADABRA_ERR_ARG, "lambda and delta must be in (0,1) (graph " + std::to_string(i) + ")");
+    State& s = S[i];
+    s.g = b->views[i];
+    r.vd = s.g->vd;
+    r.omega = omega_host(lambda[i], delta[i], r.vd);
+    const double cap_d = std::ceil(r.omega);
+    if (!(cap_d >= 1.0 && cap_d < 1e15)) return fail(KADABRA_ERR_ARG, "omega out of range");
+    s.cap = r.omega_cap = (uint64_t)cap_d;
+    s.alpha = r.alpha = std::max<uint64_t>(1, (uint64_t)std::floor(r.omega / 100.0));
+    s.K = r.check_interval = cfg.check_interval ? cfg.check_interval : auto_check_interval(r.omega);
+    s.tau = 0;
+    s.done = false;
+    sum_alpha += s.alpha;
+    sum_k += std::min(s.K, s.cap);
+  }
+  KTRY(ensure_ws(&b->ws, std::max(sum_alpha, sum_k), G));
+  for (State& s : S) KTRY(ensure_run_buffers(s.g));
+  Workspace* w = &b->ws;
+  // device descriptors of the stop tests: G CheckJobs then G CheckOuts
+  if (w->checks_cap < G) {
+    KCK(cudaDeviceSynchronize());
+    dev_free(w->allocs, w->d_checks);
+    void* p;
+    KTRY(dev_alloc(w->allocs, &p, (sizeof(CheckJob) + sizeof(CheckOut)) * (size_t)G));
+    w->d_checks = p;
+    w->checks_cap = G;
+  }
+  CheckJob* d_cj = static_cast<CheckJob*>(w->d_checks);
+  CheckOut* d_co = reinterpret_cast<CheckOut*>(d_cj + G);
+#define BCK(call)                                                                         \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) return fail(KADABRA_ERR_CUDA, cudaGetErrorString(e_));         \
+  } while (0)
+  for (State& s : S) {
+    BCK(cudaMemsetAsync(s.g->totals, 0, sizeof(long long) * KADABRA_NSTAT, st));
+    BCK(cudaMemsetAsync(s.g->count0, 0, sizeof(uint32_t) * s.g->n, st));
+    BCK(cudaMemsetAsync(s.g->counts, 0, sizeof(uint32_t) * s.g->n, st));
+  }
+  std::vector<Job> jobs;
+  auto launch_jobs = [&]() -> kadabra_status {
+    uint64_t work = 0;
+    for (Job& j : jobs) {
+      j.work_begin = work;
+      work += j.count;
+    }
+    if (work == 0) return KADABRA_OK;
+    BCK(cudaMemcpyAsync(w->d_jobs, jobs.data(), sizeof(Job) * jobs.size(), cudaMemcpyHostToDevice, st));
+    SampleParams P = ws_params(w, 0);
+    P.jobs = w->d_jobs;
+    P.njobs = (int)jobs.size();
+    P.total_work = work;
+    return launch_sampler(w, P, st);
+  };
+  auto make_job = [&](const State& s, uint32_t domain, uint64_t first, uint64_t count, uint32_t* counts,
+                      uint64_t seed_i) {
+    Job j;
+    std::memset(&j, 0, sizeof(j));
+    j.g = graph_dev(s.g);
+    j.seed = seed_i;
+    j.domain = domain;
+    j.first_idx = first;
+    j.count = count;
+    j.counts = counts;
+    j.totals = s.g->totals;
+    return j;
+  };
+  // warm-up of every graph in one launch (Alg. 2 lines 1-5)
+  jobs.clear();
+  for (int i = 0; i < G; ++i) jobs.push_back(make_job(S[i], 1, 0, S[i].alpha, S[i].g->count0, seed[i]));
+  KTRY(launch_jobs());
+  std::vector<std::vector<uint32_t>> c0(G);
+  for (int i = 0; i < G; ++i) {
+    c0[i].resize(S[i].g->n);
+    BCK(cudaMemcpyAsync(c0[i].data(), S[i].g->count0, sizeof(uint32_t) * S[i].g->n, cudaMemcpyDeviceToHost, st));
+  }
+  KTRY(read_status(w, st));
+  // computeDelta per graph (Alg. 2 lines 6-14)
+  std::vector<std::vector<double>> hL(G), hU(G);
+  for (int i = 0; i < G; ++i) {
+    hL[i].resize(S[i].g->n);
+    hU[i].resize(S[i].g->n);
+    KTRY(compute_delta_host(S[i].g->n, c0[i].data(), S[i].alpha, out[i].omega, lambda[i], delta[i], cfg.eps,
+                            hL[i].data(), hU[i].data(), &out[i].C));
+    BCK(cudaMemcpyAsync(S[i].g->lnL, hL[i].data(), sizeof(double) * S[i].g->n, cudaMemcpyHostToDevice, st));
+    BCK(cudaMemcpyAsync(S[i].g->lnU, hU[i].data(), sizeof(double) * S[i].g->n, cudaMemcpyHostToDevice, st));
+  }
+  // stop tests of a set of graphs in one launch; returns their results
+  std::vector<CheckJob> cj;
+  std::vector<CheckOut> co;
+  auto check = [&](const std::vector<int>& which) -> kadabra_status {
+    cj.clear();
+    int64_t max_n = 1;
+    for (int i : which) {
+      CheckJob c;
+      c.counts = S[i].g->counts;
+      c.lnL = S[i].g->lnL;
+      c.lnU = S[i].g->lnU;
+      c.n = S[i].g->n;
+      c.tau = S[i].tau;
+      c.omega = out[i].omega;
+      c.lambda = lambda[i];
+      c.out = d_co + cj.size();
+      cj.push_back(c);
+      max_n = std::max<int64_t>(max_n, c.n);
+    }
+    BCK(cudaMemcpyAsync(d_cj, cj.data(), sizeof(CheckJob) * cj.size(), cudaMemcpyHostToDevice, st));
+    BCK(cudaMemsetAsync(d_co, 0, sizeof(CheckOut) * cj.size(), st));
+    const int bx = (int)std::max<int64_t>(1, std::min<int64_t>((4 * (int64_t)w->num_sms + (int64_t)cj.size() - 1) /
+                                                                   (int64_t)cj.size(),
+                                                               (max_n + 255) / 256));
+    k_check_multi<<<dim3(bx, (unsigned)cj.size()), 256, 0, st>>>(d_cj);
+    BCK(cudaGetLastError());
+    co.resize(cj.size());
+    BCK(cudaMemcpyAsync(co.data(), d_co, sizeof(CheckOut) * cj.size(), cudaMemcpyDeviceToHost, st));
+    return read_status(w, st);
+  };
+  // main loop (Alg. 1): every round samples the next batch of every
+  // unfinished graph in one launch, then tests them all in one launch
+  for (;;) {
+    jobs.clear();
+    std::vector<int> sampled;
+    for (int i = 0; i < G; ++i) {
+      State& s = S[i];
+      if (s.done) continue;
+      const uint64_t B = std::min<uint64_t>(s.K, s.cap - s.tau);
+      jobs.push_back(make_job(s, 0, s.tau, B, s.g->counts, seed[i]));
+      sampled.push_back(i);
+    }
+    if (sampled.empty()) break;
+    KTRY(launch_jobs());
+    std::vector<int> to_check;
+    for (size_t q = 0; q < sampled.size(); ++q) {
+      const int i = sampled[q];
+      S[i].tau += jobs[q].count;
+      if (S[i].tau >= S[i].cap)
+        S[i].done = true;
+      else
+        to_check.push_back(i);
+    }
+    if (to_check.empty()) {
+      KTRY(read_status(w, st));
+      continue;
+    }
+    KTRY(check(to_check));
+    for (size_t q = 0; q < to_check.size(); ++q) {
+      const int i = to_check[q];
+      out[i].checks++;
+      if (!co[q].fail) {
+        out[i].stopped_early = 1;
+        S[i].done = true;
+      }
+    }
+  }
+  // f and g maxima at each final tau; b~ = counts / tau; results out
+  std::vector<int> all(G);
+  for (int i = 0; i < G; ++i) all[i] = i;
+  KTRY(check(all));
+  std::vector<long long> tot((size_t)G * KADABRA_NSTAT);
+  for (int i = 0; i < G; ++i) {
+    kadabra_result& r = out[i];
+    kadabra_graph* g = S[i].g;
+    r.tau = S[i].tau;
+    std::memcpy(&r.max_f, &co[i].max_f_bits, sizeof(double));
+    std::memcpy(&r.max_g, &co[i].max_g_bits, sizeof(double));
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(4 * (int64_t)w->num_sms, (g->n + 255) / 256));
+    if (r.btilde || r.d_btilde) {
+      k_btilde<<<blocks, 256, 0, st>>>(g->counts, g->n, r.tau, r.d_btilde ? r.d_btilde : g->btilde);
+      BCK(cudaGetLastError());
+    }
+    if (r.d_counts)
+      BCK(cudaMemcpyAsync(r.d_counts, g->counts, sizeof(uint32_t) * g->n, cudaMemcpyDeviceToDevice, st));
+    if (r.counts) BCK(cudaMemcpyAsync(r.counts, g->counts, sizeof(uint32_t) * g->n, cudaMemcpyDeviceToHost, st));
+    if (r.btilde)
+      BCK(cudaMemcpyAsync(r.btilde, r.d_btilde ? r.d_btilde : g->btilde, sizeof(double) * g->n,
+                          cudaMemcpyDeviceToHost, st));
+    BCK(cudaMemcpyAsync(&tot[(size_t)i * KADABRA_NSTAT], g->totals, sizeof(long long) * KADABRA_NSTAT,
+                        cudaMemcpyDeviceToHost, st));
+  }
+  KTRY(read_status(w, st));
+  for (int i = 0; i < G; ++i) {
+    for (int q = 0; q < KADABRA_NSTAT; ++q) out[i].totals[q] = tot[(size_t)i * KADABRA_NSTAT + q];
+    out[i].status = KADABRA_OK;
+  }
+#undef BCK
+  return KADABRA_OK;
 }
 
 }  // extern "C"

@@ -63,7 +63,8 @@ class kadabra_result(C.Structure):
     _fields_ = [
         ("tau", C.c_uint64), ("omega_cap", C.c_uint64), ("alpha", C.c_uint64), ("checks", C.c_uint64),
         ("vd", C.c_int64), ("omega", C.c_double), ("C", C.c_double), ("max_f", C.c_double),
-        ("max_g", C.c_double), ("totals", C.c_int64 * NSTAT), ("stopped_early", C.c_int32),
+        ("max_g", C.c_double), ("totals", C.c_int64 * NSTAT), ("check_interval", C.c_uint64),
+        ("stopped_early", C.c_int32),
         ("status", C.c_int32), ("counts", C.c_void_p), ("btilde", C.c_void_p), ("d_counts", C.c_void_p),
         ("d_btilde", C.c_void_p), ("topk", C.c_void_p),
     ]
@@ -112,6 +113,14 @@ def load_library():
         lib.kadabra_check.restype = st
         lib.kadabra_compute_delta.argtypes = [i64, p, u64, dbl, dbl, dbl, dbl, p, p, C.POINTER(dbl)]
         lib.kadabra_compute_delta.restype = st
+        pp = C.POINTER(C.c_void_p)
+        lib.kadabra_load_batch.argtypes = [i32, p, p, p, p, p, p, p, C.POINTER(C.c_void_p)]
+        lib.kadabra_load_batch.restype = st
+        lib.kadabra_free_batch.argtypes = [p]
+        lib.kadabra_batch_graph.argtypes = [p, i32, C.POINTER(C.c_void_p)]
+        lib.kadabra_batch_graph.restype = st
+        lib.kadabra_run_batch.argtypes = [p, p, p, p, C.POINTER(kadabra_config), p]
+        lib.kadabra_run_batch.restype = st
         _lib = lib
         return lib
 
@@ -191,6 +200,7 @@ def kadabra_load_csr_device(n: int, row_ptr, col, directed: bool = False, rrow_p
 @dataclass
 class RunResult:
     tau: int
+    check_interval: int
     omega_cap: int
     alpha: int
     checks: int
@@ -230,7 +240,7 @@ def kadabra_run(g: Graph, lam: float, delta: float, k: int = 0, seed: int = 0, *
     if d_btilde is not None:
         res.d_btilde = d_btilde.data_ptr()
     _raise(lib.kadabra_run(g.handle, lam, delta, k, seed, C.byref(cfg), C.byref(res)))
-    return RunResult(res.tau, res.omega_cap, res.alpha, res.checks, res.vd, res.omega, res.C, res.max_f,
+    return RunResult(res.tau, res.check_interval, res.omega_cap, res.alpha, res.checks, res.vd, res.omega, res.C, res.max_f,
                      res.max_g, np.array(res.totals[:], dtype=np.int64), bool(res.stopped_early),
                      counts if want_host else None, btilde if want_host else None)
 
@@ -315,3 +325,69 @@ def kadabra_compute_delta(count0: np.ndarray, alpha: int, omega: float, lam: flo
     _raise(load_library().kadabra_compute_delta(n, _ptr(c0), alpha, omega, lam, delta, eps, _ptr(dl), _ptr(du),
                                                 C.byref(Cv)))
     return Cv.value, dl, du
+
+
+class Batch:
+    """G graphs in one device arena, run together (kadabra_load_batch / kadabra_run_batch)."""
+
+    def __init__(self, graphs):
+        lib = load_library()
+        G = len(graphs)
+        self._keep = []
+        arr = lambda t, vals: (t * G)(*vals)
+        rp = [np.ascontiguousarray(g.row_ptr, dtype=np.int32) for g in graphs]
+        ci = [np.ascontiguousarray(g.col, dtype=np.int32) for g in graphs]
+        rrp = [np.ascontiguousarray(g.rrow_ptr, dtype=np.int32) if g.directed else None for g in graphs]
+        rci = [np.ascontiguousarray(g.rcol, dtype=np.int32) if g.directed else None for g in graphs]
+        self._keep = (rp, ci, rrp, rci)
+        n = arr(C.c_int32, [int(g.n) for g in graphs])
+        m = arr(C.c_int64, [int(c.shape[0]) for c in ci])
+        d = arr(C.c_int, [int(bool(g.directed)) for g in graphs])
+        ptrs = lambda xs: arr(C.c_void_p, [None if x is None else x.ctypes.data for x in xs])
+        h = C.c_void_p()
+        _raise(lib.kadabra_load_batch(G, n, m, ptrs(rp), ptrs(ci), d, ptrs(rrp), ptrs(rci), C.byref(h)))
+        self.handle = h
+        self.G = G
+        self.n = [int(g.n) for g in graphs]
+        self.views = []
+        for i, g in enumerate(graphs):
+            v = C.c_void_p()
+            _raise(lib.kadabra_batch_graph(h, i, C.byref(v)))
+            gv = Graph(v.value, int(g.n), int(ci[i].shape[0]), bool(g.directed))
+            gv.free = lambda: None  # released with the batch
+            self.views.append(gv)
+
+    def run(self, lam, delta, seed, *, check_interval: int = 0, eps: float = 0.001,
+            stream: Optional[int] = None):
+        """KADABRA on every graph; lam/delta/seed are sequences of length G."""
+        lib = load_library()
+        G = self.G
+        cfg = config_default()
+        cfg.eps = eps
+        cfg.check_interval = check_interval
+        cfg.stream = stream
+        res = (kadabra_result * G)()
+        counts = [np.zeros(n, dtype=np.uint32) for n in self.n]
+        btilde = [np.zeros(n, dtype=np.float64) for n in self.n]
+        for i in range(G):
+            res[i].counts = counts[i].ctypes.data
+            res[i].btilde = btilde[i].ctypes.data
+        L = (C.c_double * G)(*lam)
+        D = (C.c_double * G)(*delta)
+        S = (C.c_uint64 * G)(*seed)
+        _raise(lib.kadabra_run_batch(self.handle, L, D, S, C.byref(cfg), res))
+        return [RunResult(r.tau, r.check_interval, r.omega_cap, r.alpha, r.checks, r.vd, r.omega, r.C, r.max_f,
+                          r.max_g, np.array(r.totals[:], dtype=np.int64), bool(r.stopped_early), counts[i],
+                          btilde[i]) for i, r in enumerate(res)]
+
+    def free(self):
+        if self.handle:
+            load_library().kadabra_free_batch(self.handle)
+            self.handle = C.c_void_p()
+            self.views = []
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
