@@ -204,6 +204,81 @@ def sampler_only(kd, G, g, launches):
                       "bt_scanned": int(tot[6]), "workload": workload_config(g)["workload"]}), flush=True)
 
 
+BATCHED = dict(graphs=64, n_lo=10_000, n_hi=2_000_000, m_lo=4, m_hi=16, lam=0.01, delta=0.1, seed=2024)
+
+
+def make_batched_graphs():
+    """64 Barabasi-Albert graphs: n log-uniform in [10^4, 2*10^6], attachment m
+    uniform in {4..16}, one seed per graph (generated in parallel threads)."""
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_1604_08553_gb300 import graphgen
+    b = BATCHED
+    rng = np.random.default_rng(b["seed"])
+    ns = np.exp(rng.uniform(np.log(b["n_lo"]), np.log(b["n_hi"]), b["graphs"])).astype(np.int64)
+    ms = rng.integers(b["m_lo"], b["m_hi"] + 1, b["graphs"])
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        return list(ex.map(lambda i: graphgen.barabasi_albert(int(ns[i]), int(ms[i]), b["seed"] + 1 + i),
+                           range(b["graphs"])))
+
+
+def run_batched(args, kd, rank, world):
+    """Time-to-(lambda, delta) of the whole uneven multi-graph workload: one
+    batched run (all graphs per launch) against the same graphs run one at a
+    time on the same device arena, with identical results required."""
+    import torch
+    b = BATCHED
+    graphs = make_batched_graphs()
+    G = len(graphs)
+    B = kd.Batch(graphs)
+    lam, delta = [b["lam"]] * G, [b["delta"]] * G
+    stream = torch.cuda.current_stream()
+
+    def batched(seed0):
+        return B.run(lam, delta, [seed0 + i for i in range(G)], stream=stream.cuda_stream)
+
+    def plain(seed0):
+        return [kd.kadabra_run(B.views[i], lam[i], delta[i], 0, seed0 + i, check_interval=0,
+                               stream=stream.cuda_stream) for i in range(G)]
+
+    for i in range(args.warmup):
+        batched(100 * (i + 1))
+        plain(100 * (i + 1))
+    tb, tp, paths = [], [], 0
+    for i in range(args.steps):
+        seed0 = 7 + 1000 * i
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rb = batched(seed0)
+        torch.cuda.synchronize()
+        tb.append(time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        rp = plain(seed0)
+        torch.cuda.synchronize()
+        tp.append(time.perf_counter() - t0)
+        for x, y in zip(rb, rp):
+            assert x.tau == y.tau and np.array_equal(x.counts, y.counts), "batched and plain runs differ"
+        paths += sum(r.alpha + r.tau for r in rb)
+    value = paths / sum(tb)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(tb) / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64+f64", "data": "synthetic",
+            "config": {
+                "workload": (f"batched: {G} Barabasi-Albert graphs, n log-uniform in [{b['n_lo']}, {b['n_hi']}], "
+                             f"m uniform in {{{b['m_lo']}..{b['m_hi']}}}; lambda={b['lam']} delta={b['delta']}; "
+                             "check interval max(1024, ceil(omega/32))"),
+                "nodes": int(sum(g.n for g in graphs)), "arcs": int(sum(g.m for g in graphs)),
+                "time_to_lambda_delta_batched_ms": [round(1e3 * t, 2) for t in tb],
+                "time_to_lambda_delta_plain_ms": [round(1e3 * t, 2) for t in tp],
+                "batched_speedup": sum(tp) / sum(tb),
+                "results": "identical per graph (tau, counts) in batched and plain runs",
+            },
+        }
+        print(json.dumps(line), flush=True)
+    B.free()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -213,6 +288,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sampler-only", type=int, default=0, metavar="LAUNCHES",
                     help="only time LAUNCHES sampler batches of K samples (for profilers)")
+    ap.add_argument("--workload", default="plain", choices=["plain", "batched"],
+                    help="plain: one Chung-Lu graph (default); batched: 64 uneven Barabasi-Albert graphs, "
+                         "batched run against one-graph-at-a-time runs")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -229,6 +307,9 @@ def main():
     from paper_1604_08553_gb300 import kadabra as kd
 
     torch.cuda.set_device(local_rank)
+    if args.workload == "batched":
+        run_batched(args, kd, rank, world)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist

@@ -136,9 +136,12 @@ void kadabra_free_graph(kadabra_graph* g);
  * that graph with the same lambda, delta, seed and check interval. */
 typedef struct kadabra_batch kadabra_batch;
 
+#define KADABRA_MAX_BATCH_GRAPHS 65535
+
 /* Copies G host CSRs (arrays of G pointers / sizes; rrow_ptr/rcol entries
  * NULL for undirected graphs, the arrays themselves may be NULL if no graph
- * is directed) into one device arena, validating each (KADABRA_ERR_CSR). */
+ * is directed) into one device arena, validating each (KADABRA_ERR_CSR).
+ * 1 <= G <= KADABRA_MAX_BATCH_GRAPHS, else KADABRA_ERR_ARG. */
 kadabra_status kadabra_load_batch(int32_t G, const int32_t* n, const int64_t* m, const int32_t* const* row_ptr,
                                   const int32_t* const* col, const int* directed, const int32_t* const* rrow_ptr,
                                   const int32_t* const* rcol, kadabra_batch** out);

@@ -1366,13 +1366,16 @@ __global__ void __launch_bounds__(256) k_check(const uint32_t* __restrict__ coun
   }
 }
 
-// The stop test of several graphs in one launch: blockIdx.y selects the
-// graph, blockIdx.x strides over its nodes; each graph has its own tau,
-// omega, lambda and result.
-struct CheckJob {
+// Stop test of several graphs in all-nodes mode, where ln(1/delta_L(v)) =
+// ln(1/delta_U(v)) depends only on v's warm-up count: lnT[count0[v]].  A
+// node with no hit has f = 0 exactly (a_L < 0, so a_L + sqrt(a_L^2) = +0) and
+// g = (L/t)(a_U + a_U), increasing in L, so the block evaluates g once, at
+// the largest L among its unhit nodes; hit nodes take the full formula.  The
+// maxima and the decision equal those of the per-node evaluation bit for bit.
+struct CheckTabJob {
   const uint32_t* counts;
-  const double* lnL;
-  const double* lnU;
+  const uint32_t* count0;
+  const double* lnT;
   int64_t n;
   uint64_t tau;
   double omega;
@@ -1380,14 +1383,22 @@ struct CheckJob {
   CheckOut* out;
 };
 
-__global__ void __launch_bounds__(256) k_check_multi(const CheckJob* __restrict__ jobs) {
-  const CheckJob J = jobs[blockIdx.y];
+__global__ void __launch_bounds__(256) k_check_tab(const CheckTabJob* __restrict__ jobs) {
+  __shared__ unsigned long long s_u[8];
+  const CheckTabJob J = jobs[blockIdx.y];
   const double t = (double)J.tau;
-  unsigned long long mf = 0, mg = 0;
+  unsigned long long mf = 0, mg = 0, mu = 0;  // bit patterns of non-negative doubles
   unsigned fail = 0;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < J.n; v += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t cnt = J.counts[v];
+    const double L = J.lnT[J.count0[v]];
+    if (cnt == 0) {
+      const unsigned long long lb = (unsigned long long)__double_as_longlong(L);
+      mu = lb > mu ? lb : mu;
+      continue;
+    }
     double f, g;
-    f_and_g(J.counts[v], t, J.omega, J.lnL[v], J.lnU[v], &f, &g);
+    f_and_g(cnt, t, J.omega, L, L, &f, &g);
     if (!(f <= J.lambda) || !(g <= J.lambda)) fail = 1;
     const unsigned long long fb = (unsigned long long)__double_as_longlong(f);
     const unsigned long long gb = (unsigned long long)__double_as_longlong(g);
@@ -1398,14 +1409,96 @@ __global__ void __launch_bounds__(256) k_check_multi(const CheckJob* __restrict_
   for (int o = 16; o > 0; o >>= 1) {
     const unsigned long long a = __shfl_xor_sync(FULL, mf, o);
     const unsigned long long b = __shfl_xor_sync(FULL, mg, o);
+    const unsigned long long u = __shfl_xor_sync(FULL, mu, o);
     mf = a > mf ? a : mf;
     mg = b > mg ? b : mg;
+    mu = u > mu ? u : mu;
     fail |= __shfl_xor_sync(FULL, fail, o);
   }
-  if ((threadIdx.x & 31) == 0) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) s_u[w] = mu;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long u = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) u = s_u[i] > u ? s_u[i] : u;
+    if (u) {  // some node of this block has no hit: g at its largest L (f is 0)
+      double f0, g0;
+      f_and_g(0u, t, J.omega, __longlong_as_double((long long)u), __longlong_as_double((long long)u), &f0, &g0);
+      const unsigned long long gb = (unsigned long long)__double_as_longlong(g0);
+      atomicMax(&J.out->max_g_bits, gb);
+      if (!(f0 <= J.lambda) || !(g0 <= J.lambda)) atomicOr(&J.out->fail, 1u);
+    }
+  }
+  if (lane == 0) {
     if (mf) atomicMax(&J.out->max_f_bits, mf);
     if (mg) atomicMax(&J.out->max_g_bits, mg);
     if (fail) atomicOr(&J.out->fail, 1u);
+  }
+}
+
+// Stable compaction of the non-zero warm-up counts of several graphs, in
+// node order (graph = blockIdx.y; each block owns a contiguous chunk).
+struct NzJob {
+  const uint32_t* count0;
+  int64_t n;
+  uint32_t* out;     // non-zero values, node order
+  unsigned* blk;     // per-block counts, then exclusive offsets (gridDim.x entries)
+  unsigned* total;
+};
+
+__global__ void __launch_bounds__(256) k_nz_count(const NzJob* __restrict__ jobs) {
+  __shared__ int tmp[8];
+  const NzJob J = jobs[blockIdx.y];
+  const int64_t chunk = (J.n + gridDim.x - 1) / gridDim.x;
+  const int64_t a = min(J.n, (int64_t)blockIdx.x * chunk), b = min(J.n, a + chunk);
+  int c = 0;
+  for (int64_t v = a + threadIdx.x; v < b; v += blockDim.x) c += J.count0[v] != 0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
+  if ((threadIdx.x & 31) == 0) tmp[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += tmp[i];
+    J.blk[blockIdx.x] = (unsigned)s;
+  }
+}
+
+// one block per graph: exclusive offsets of the per-block counts
+__global__ void k_nz_offsets(const NzJob* __restrict__ jobs, int nblk) {
+  const NzJob J = jobs[blockIdx.x];
+  if (threadIdx.x == 0) {
+    unsigned s = 0;
+    for (int i = 0; i < nblk; ++i) {
+      const unsigned c = J.blk[i];
+      J.blk[i] = s;
+      s += c;
+    }
+    *J.total = s;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_nz_scatter(const NzJob* __restrict__ jobs) {
+  __shared__ int tmp[8];
+  const NzJob J = jobs[blockIdx.y];
+  const int64_t chunk = (J.n + gridDim.x - 1) / gridDim.x;
+  const int64_t a = min(J.n, (int64_t)blockIdx.x * chunk), b = min(J.n, a + chunk);
+  unsigned base = J.blk[blockIdx.x];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t t0 = a; t0 < b; t0 += blockDim.x) {
+    const int64_t v = t0 + threadIdx.x;
+    const uint32_t x = v < b ? J.count0[v] : 0u;
+    const unsigned m = __ballot_sync(FULL, x != 0);
+    if (lane == 0) tmp[w] = __popc(m);
+    __syncthreads();
+    unsigned before = 0, tot = 0;
+    for (int i = 0; i < nw; ++i) {
+      if (i < w) before += tmp[i];
+      tot += tmp[i];
+    }
+    if (x != 0) J.out[base + before + __popc(m & ((1u << lane) - 1u))] = x;
+    base += tot;
+    __syncthreads();
   }
 }
 
@@ -1576,8 +1669,10 @@ struct Workspace {
   int gm_lcap = 0;
   Job* d_jobs = nullptr;  // job array of multi-graph launches
   int jobs_cap = 0;
-  void* d_checks = nullptr;  // stop-test descriptors of multi-graph runs
+  void* d_checks = nullptr;  // stop-test descriptors and results of runs
   int checks_cap = 0;
+  void* d_nz = nullptr;  // warm-up count compaction descriptors of runs
+  int nz_cap = 0;
   std::vector<void*> allocs;
   ~Workspace() {
     for (void* p : allocs)
@@ -1602,9 +1697,10 @@ struct kadabra_graph {
   bool is_view = false;  // a batch's view: released with the batch
   // run buffers
   uint32_t *counts = nullptr, *count0 = nullptr;
-  double *lnL = nullptr, *lnU = nullptr, *btilde = nullptr;
-  CheckOut* chk = nullptr;
+  double* btilde = nullptr;
   long long* totals = nullptr;
+  double* lntab = nullptr;  // computeDelta table, ln(1/delta) by warm-up count
+  uint64_t lntab_cap = 0;
   std::vector<void*> allocs;  // CSR copies and run buffers
 };
 
@@ -1714,7 +1810,7 @@ kadabra_status ensure_ws(Workspace* w, uint64_t deferred_need, int njobs) {
   return KADABRA_OK;
 }
 
-// per-graph run buffers (hit counters, computeDelta tables, results)
+// per-graph run buffers (hit counters, b~, totals)
 kadabra_status ensure_run_buffers(kadabra_graph* g) {
   if (g->counts) return KADABRA_OK;
   void* p;
@@ -1723,13 +1819,7 @@ kadabra_status ensure_run_buffers(kadabra_graph* g) {
   KTRY(dev_alloc(g->allocs, &p, sizeof(uint32_t) * (size_t)g->n));
   g->count0 = (uint32_t*)p;
   KTRY(dev_alloc(g->allocs, &p, sizeof(double) * (size_t)g->n));
-  g->lnL = (double*)p;
-  KTRY(dev_alloc(g->allocs, &p, sizeof(double) * (size_t)g->n));
-  g->lnU = (double*)p;
-  KTRY(dev_alloc(g->allocs, &p, sizeof(double) * (size_t)g->n));
   g->btilde = (double*)p;
-  KTRY(dev_alloc(g->allocs, &p, sizeof(CheckOut)));
-  g->chk = (CheckOut*)p;
   KTRY(dev_alloc(g->allocs, &p, sizeof(long long) * KADABRA_NSTAT));
   g->totals = (long long*)p;
   return KADABRA_OK;
@@ -1836,26 +1926,28 @@ uint64_t auto_check_interval(double omega) {
 }
 
 // ---------------------------------------------------------------- computeDelta
-// Alg. 2 with lambda_L = lambda_U = lambda.  Only nodes with a non-zero
-// warm-up count contribute to the sum (the others add exact zeros), and the
-// exponential of each distinct count is evaluated once per bisection step;
-// the sum runs over nodes in increasing id order.
-kadabra_status compute_delta_host(int64_t n, const uint32_t* count0, uint64_t alpha, double omega, double lambda,
-                                  double delta, double eps, double* lnL, double* lnU, double* C_out) {
-  std::vector<int64_t> nz;
+// Alg. 2 with lambda_L = lambda_U = lambda.  In this mode delta(v) depends
+// only on v's warm-up count k = count0(v) (at most alpha), so the result is a
+// table lnT[k] = ln(1/delta) for k = 0..kmax.  nz holds the non-zero warm-up counts
+// in increasing node order: the bisection's sum runs over them in that order
+// (the other nodes add exact zeros), with the exponential of each distinct
+// count evaluated once per step.
+kadabra_status compute_delta_table(int64_t n, const uint32_t* nz, size_t nnz, uint64_t alpha, uint64_t kmax,
+                                   double omega, double lambda, double delta, double eps, double* lnT,
+                                   double* C_out) {
   std::unordered_map<uint32_t, size_t> idx_of;
   std::vector<uint32_t> distinct;
-  std::vector<size_t> which;
-  for (int64_t v = 0; v < n; ++v)
-    if (count0[v]) {
-      nz.push_back(v);
-      auto it = idx_of.find(count0[v]);
-      if (it == idx_of.end()) {
-        it = idx_of.emplace(count0[v], distinct.size()).first;
-        distinct.push_back(count0[v]);
-      }
-      which.push_back(it->second);
+  std::vector<size_t> which(nnz);
+  for (size_t i = 0; i < nnz; ++i) {
+    auto it = idx_of.find(nz[i]);
+    if (it == idx_of.end()) {
+      it = idx_of.emplace(nz[i], distinct.size()).first;
+      distinct.push_back(nz[i]);
     }
+    which[i] = it->second;
+  }
+  for (uint32_t k : distinct)
+    if (k > kmax) return fail(KADABRA_ERR_INTERNAL, "computeDelta: a warm-up count exceeds the table");
   std::vector<double> cval(distinct.size()), ex(distinct.size());
   for (size_t k = 0; k < distinct.size(); ++k) {
     const double b0 = (double)distinct[k] / (double)alpha;
@@ -1865,14 +1957,14 @@ kadabra_status compute_delta_host(int64_t n, const uint32_t* count0, uint64_t al
   auto sum_at = [&](double C) {
     for (size_t k = 0; k < distinct.size(); ++k) ex[k] = std::exp(-C / cval[k]);
     double sum = 0.0;
-    for (size_t i = 0; i < nz.size(); ++i) {
+    for (size_t i = 0; i < nnz; ++i) {
       const double e = ex[which[i]];
       sum += e + e;
     }
     return sum;
   };
   double C = 0.0;
-  if (!nz.empty()) {
+  if (nnz) {
     double lo = 0.0, hi = 1.0;
     int guard = 0;
     while (!(sum_at(hi) <= target)) {
@@ -1891,17 +1983,26 @@ kadabra_status compute_delta_host(int64_t n, const uint32_t* count0, uint64_t al
     C = hi;
   }
   const double floor_term = (eps * delta) / (2.0 * (double)n);
-  const double ln_zero = -std::log(0.0 + floor_term);
-  for (size_t k = 0; k < distinct.size(); ++k) ex[k] = -std::log(std::exp(-C / cval[k]) + floor_term);
-  for (int64_t v = 0; v < n; ++v) {
-    lnL[v] = ln_zero;
-    lnU[v] = ln_zero;
-  }
-  for (size_t i = 0; i < nz.size(); ++i) {
-    lnL[nz[i]] = ex[which[i]];
-    lnU[nz[i]] = ex[which[i]];
-  }
+  for (uint64_t k = 0; k <= kmax; ++k) lnT[k] = -std::log(0.0 + floor_term);
+  for (size_t k = 0; k < distinct.size(); ++k) lnT[distinct[k]] = -std::log(std::exp(-C / cval[k]) + floor_term);
   *C_out = C;
+  return KADABRA_OK;
+}
+
+// the same, with per-node outputs (ln(1/delta_L) = ln(1/delta_U) for every node)
+kadabra_status compute_delta_host(int64_t n, const uint32_t* count0, uint64_t alpha, double omega, double lambda,
+                                  double delta, double eps, double* lnL, double* lnU, double* C_out) {
+  std::vector<uint32_t> nz;
+  uint64_t top = 0;
+  for (int64_t v = 0; v < n; ++v)
+    if (count0[v]) {
+      nz.push_back(count0[v]);
+      top = std::max<uint64_t>(top, count0[v]);
+    }
+  const uint64_t kmax = std::max<uint64_t>(alpha, top);
+  std::vector<double> lnT(kmax + 1);
+  KTRY(compute_delta_table(n, nz.data(), nz.size(), alpha, kmax, omega, lambda, delta, eps, lnT.data(), C_out));
+  for (int64_t v = 0; v < n; ++v) lnL[v] = lnU[v] = lnT[count0[v]];
   return KADABRA_OK;
 }
 
@@ -2011,6 +2112,266 @@ kadabra_status new_graph(int32_t n, int64_t m, int directed, kadabra_graph** out
 }  // namespace
 
 namespace {
+
+
+// ---------------------------------------------------------------- Alg. 1 runner
+constexpr int NZ_BLK = 128;  // compaction blocks per graph
+
+// KADABRA on G graphs at once (kadabra_run is the case G = 1): warm-up of
+// every graph in one sampler launch, computeDelta per graph on the host from
+// its compacted warm-up counts, then rounds of one sampler launch over every
+// unfinished graph's next batch and one stop-test launch over all of them.
+kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const double* lambda, const double* delta,
+                          const uint64_t* seed, const int64_t* vd_override, const kadabra_config& cfg,
+                          kadabra_result* out) {
+  cudaStream_t st = as_stream(cfg.stream);
+  struct State {
+    kadabra_graph* g;
+    uint64_t cap, alpha, K, tau;
+    bool done;
+  };
+  std::vector<State> S(G);
+  uint64_t sum_alpha = 0, sum_k = 0;
+  for (int i = 0; i < G; ++i) {
+    kadabra_result& r = out[i];
+    State& s = S[i];
+    s.g = gs[i];
+    r.vd = (vd_override && vd_override[i] > 0) ? vd_override[i] : s.g->vd;
+    r.omega = omega_host(lambda[i], delta[i], r.vd);
+    const double cap_d = std::ceil(r.omega);
+    if (!(cap_d >= 1.0 && cap_d < 1e15)) return fail(KADABRA_ERR_ARG, "omega out of range");
+    s.cap = r.omega_cap = (uint64_t)cap_d;
+    s.alpha = r.alpha = std::max<uint64_t>(1, (uint64_t)std::floor(r.omega / 100.0));
+    s.K = r.check_interval = cfg.check_interval ? cfg.check_interval : auto_check_interval(r.omega);
+    s.tau = 0;
+    s.done = false;
+    sum_alpha += s.alpha;
+    sum_k += std::min(s.K, s.cap);
+  }
+  KTRY(ensure_ws(w, std::max(sum_alpha, sum_k), G));
+  for (State& s : S) {
+    KTRY(ensure_run_buffers(s.g));
+    if (s.g->lntab_cap < s.alpha + 1) {
+      KCK(cudaStreamSynchronize(st));
+      dev_free(s.g->allocs, s.g->lntab);
+      void* p;
+      KTRY(dev_alloc(s.g->allocs, &p, sizeof(double) * (s.alpha + 1)));
+      s.g->lntab = (double*)p;
+      s.g->lntab_cap = s.alpha + 1;
+    }
+  }
+  if (w->checks_cap < G) {
+    KCK(cudaDeviceSynchronize());
+    dev_free(w->allocs, w->d_checks);
+    void* p;
+    KTRY(dev_alloc(w->allocs, &p, (sizeof(CheckTabJob) + sizeof(CheckOut)) * (size_t)G));
+    w->d_checks = p;
+    w->checks_cap = G;
+  }
+  if (w->nz_cap < G) {
+    KCK(cudaDeviceSynchronize());
+    dev_free(w->allocs, w->d_nz);
+    void* p;
+    KTRY(dev_alloc(w->allocs, &p, (sizeof(NzJob) + sizeof(unsigned) * (NZ_BLK + 1)) * (size_t)G));
+    w->d_nz = p;
+    w->nz_cap = G;
+  }
+  CheckTabJob* d_cj = static_cast<CheckTabJob*>(w->d_checks);
+  CheckOut* d_co = reinterpret_cast<CheckOut*>(d_cj + G);
+  NzJob* d_nzj = static_cast<NzJob*>(w->d_nz);
+  unsigned* d_blk = reinterpret_cast<unsigned*>(d_nzj + G);
+  unsigned* d_nzt = d_blk + (size_t)NZ_BLK * G;
+#define RCK(call)                                                                         \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) return fail(KADABRA_ERR_CUDA, cudaGetErrorString(e_));         \
+  } while (0)
+  for (State& s : S) {
+    RCK(cudaMemsetAsync(s.g->totals, 0, sizeof(long long) * KADABRA_NSTAT, st));
+    RCK(cudaMemsetAsync(s.g->count0, 0, sizeof(uint32_t) * s.g->n, st));
+    RCK(cudaMemsetAsync(s.g->counts, 0, sizeof(uint32_t) * s.g->n, st));
+  }
+  std::vector<Job> jobs;
+  auto launch_jobs = [&]() -> kadabra_status {
+    uint64_t work = 0;
+    for (Job& j : jobs) {
+      j.work_begin = work;
+      work += j.count;
+    }
+    if (work == 0) return KADABRA_OK;
+    SampleParams P = ws_params(w, jobs.size() == 1 ? gs[0]->flags : 0);
+    P.total_work = work;
+    if (jobs.size() == 1) {
+      P.job0 = jobs[0];
+    } else {
+      RCK(cudaMemcpyAsync(w->d_jobs, jobs.data(), sizeof(Job) * jobs.size(), cudaMemcpyHostToDevice, st));
+      P.jobs = w->d_jobs;
+      P.njobs = (int)jobs.size();
+    }
+    return launch_sampler(w, P, st);
+  };
+  auto make_job = [&](const State& s, uint32_t domain, uint64_t first, uint64_t count, uint32_t* counts,
+                      uint64_t seed_i) {
+    Job j;
+    std::memset(&j, 0, sizeof(j));
+    j.g = graph_dev(s.g);
+    j.seed = seed_i;
+    j.domain = domain;
+    j.first_idx = first;
+    j.count = count;
+    j.counts = counts;
+    j.totals = s.g->totals;
+    return j;
+  };
+  // warm-up of every graph in one launch (Alg. 2 lines 1-5)
+  jobs.clear();
+  for (int i = 0; i < G; ++i) jobs.push_back(make_job(S[i], 1, 0, S[i].alpha, S[i].g->count0, seed[i]));
+  KTRY(launch_jobs());
+  // the non-zero warm-up counts of every graph, in node order, to the host
+  {
+    std::vector<NzJob> nzj(G);
+    for (int i = 0; i < G; ++i) {
+      nzj[i].count0 = S[i].g->count0;
+      nzj[i].n = S[i].g->n;
+      nzj[i].out = reinterpret_cast<uint32_t*>(S[i].g->btilde);  // scratch until b~ is computed
+      nzj[i].blk = d_blk + (size_t)NZ_BLK * i;
+      nzj[i].total = d_nzt + i;
+    }
+    RCK(cudaMemcpyAsync(d_nzj, nzj.data(), sizeof(NzJob) * G, cudaMemcpyHostToDevice, st));
+    k_nz_count<<<dim3(NZ_BLK, G), 256, 0, st>>>(d_nzj);
+    k_nz_offsets<<<G, 32, 0, st>>>(d_nzj, NZ_BLK);
+    k_nz_scatter<<<dim3(NZ_BLK, G), 256, 0, st>>>(d_nzj);
+    RCK(cudaGetLastError());
+  }
+  std::vector<unsigned> nnz(G);
+  RCK(cudaMemcpyAsync(nnz.data(), d_nzt, sizeof(unsigned) * G, cudaMemcpyDeviceToHost, st));
+  KTRY(read_status(w, st));
+  std::vector<std::vector<uint32_t>> nzv(G);
+  for (int i = 0; i < G; ++i) {
+    nzv[i].resize(nnz[i]);
+    if (nnz[i])
+      RCK(cudaMemcpyAsync(nzv[i].data(), S[i].g->btilde, sizeof(uint32_t) * nnz[i], cudaMemcpyDeviceToHost, st));
+  }
+  RCK(cudaStreamSynchronize(st));
+  // computeDelta per graph (Alg. 2 lines 6-14): a table by warm-up count
+  std::vector<std::vector<double>> tab(G);
+  for (int i = 0; i < G; ++i) {
+    tab[i].resize(S[i].alpha + 1);
+    KTRY(compute_delta_table(S[i].g->n, nzv[i].data(), nzv[i].size(), S[i].alpha, S[i].alpha, out[i].omega,
+                             lambda[i], delta[i], cfg.eps, tab[i].data(), &out[i].C));
+    RCK(cudaMemcpyAsync(S[i].g->lntab, tab[i].data(), sizeof(double) * tab[i].size(), cudaMemcpyHostToDevice, st));
+  }
+  // stop tests of a set of graphs in one launch
+  std::vector<CheckTabJob> cj;
+  std::vector<CheckOut> co;
+  auto check = [&](const std::vector<int>& which) -> kadabra_status {
+    cj.clear();
+    int64_t max_n = 1;
+    for (int i : which) {
+      CheckTabJob c;
+      c.counts = S[i].g->counts;
+      c.count0 = S[i].g->count0;
+      c.lnT = S[i].g->lntab;
+      c.n = S[i].g->n;
+      c.tau = S[i].tau;
+      c.omega = out[i].omega;
+      c.lambda = lambda[i];
+      c.out = d_co + cj.size();
+      cj.push_back(c);
+      max_n = std::max<int64_t>(max_n, c.n);
+    }
+    RCK(cudaMemcpyAsync(d_cj, cj.data(), sizeof(CheckTabJob) * cj.size(), cudaMemcpyHostToDevice, st));
+    RCK(cudaMemsetAsync(d_co, 0, sizeof(CheckOut) * cj.size(), st));
+    const int64_t want = (4 * (int64_t)w->num_sms + (int64_t)cj.size() - 1) / (int64_t)cj.size();
+    const int bx = (int)std::max<int64_t>(1, std::min<int64_t>(want, (max_n + 255) / 256));
+    k_check_tab<<<dim3(bx, (unsigned)cj.size()), 256, 0, st>>>(d_cj);
+    RCK(cudaGetLastError());
+    co.resize(cj.size());
+    RCK(cudaMemcpyAsync(co.data(), d_co, sizeof(CheckOut) * cj.size(), cudaMemcpyDeviceToHost, st));
+    return read_status(w, st);
+  };
+  // main loop (Alg. 1)
+  for (;;) {
+    jobs.clear();
+    std::vector<int> sampled;
+    for (int i = 0; i < G; ++i) {
+      State& s = S[i];
+      if (s.done) continue;
+      const uint64_t B = std::min<uint64_t>(s.K, s.cap - s.tau);
+      jobs.push_back(make_job(s, 0, s.tau, B, s.g->counts, seed[i]));
+      sampled.push_back(i);
+    }
+    if (sampled.empty()) break;
+    KTRY(launch_jobs());
+    std::vector<int> to_check;
+    for (size_t q = 0; q < sampled.size(); ++q) {
+      const int i = sampled[q];
+      S[i].tau += jobs[q].count;
+      if (S[i].tau >= S[i].cap)
+        S[i].done = true;
+      else
+        to_check.push_back(i);
+    }
+    if (to_check.empty()) {
+      KTRY(read_status(w, st));
+      continue;
+    }
+    KTRY(check(to_check));
+    for (size_t q = 0; q < to_check.size(); ++q) {
+      const int i = to_check[q];
+      out[i].checks++;
+      if (!co[q].fail) {
+        out[i].stopped_early = 1;
+        S[i].done = true;
+      }
+    }
+  }
+  // f and g maxima at each final tau; b~ = counts / tau (Alg. 1 last line)
+  std::vector<int> all(G);
+  for (int i = 0; i < G; ++i) all[i] = i;
+  KTRY(check(all));
+  std::vector<long long> tot((size_t)G * KADABRA_NSTAT);
+  for (int i = 0; i < G; ++i) {
+    kadabra_result& r = out[i];
+    kadabra_graph* g = S[i].g;
+    r.tau = S[i].tau;
+    std::memcpy(&r.max_f, &co[i].max_f_bits, sizeof(double));
+    std::memcpy(&r.max_g, &co[i].max_g_bits, sizeof(double));
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(4 * (int64_t)w->num_sms, (g->n + 255) / 256));
+    if (r.btilde || r.d_btilde) {
+      k_btilde<<<blocks, 256, 0, st>>>(g->counts, g->n, r.tau, r.d_btilde ? r.d_btilde : g->btilde);
+      RCK(cudaGetLastError());
+    }
+    if (r.d_counts)
+      RCK(cudaMemcpyAsync(r.d_counts, g->counts, sizeof(uint32_t) * g->n, cudaMemcpyDeviceToDevice, st));
+    if (r.counts) RCK(cudaMemcpyAsync(r.counts, g->counts, sizeof(uint32_t) * g->n, cudaMemcpyDeviceToHost, st));
+    if (r.btilde)
+      RCK(cudaMemcpyAsync(r.btilde, r.d_btilde ? r.d_btilde : g->btilde, sizeof(double) * g->n,
+                          cudaMemcpyDeviceToHost, st));
+    RCK(cudaMemcpyAsync(&tot[(size_t)i * KADABRA_NSTAT], g->totals, sizeof(long long) * KADABRA_NSTAT,
+                        cudaMemcpyDeviceToHost, st));
+  }
+  KTRY(read_status(w, st));
+  for (int i = 0; i < G; ++i)
+    for (int q = 0; q < KADABRA_NSTAT; ++q) out[i].totals[q] = tot[(size_t)i * KADABRA_NSTAT + q];
+#undef RCK
+  return KADABRA_OK;
+}
+
+// keeps the caller's buffer pointers, zeroes the rest of a result
+void reset_result(kadabra_result* r) {
+  uint32_t* ch = r->counts;
+  double* bh = r->btilde;
+  uint32_t* cd = r->d_counts;
+  double* bd = r->d_btilde;
+  int32_t* tk = r->topk;
+  std::memset(r, 0, sizeof(*r));
+  r->counts = ch;
+  r->btilde = bh;
+  r->d_counts = cd;
+  r->d_btilde = bd;
+  r->topk = tk;
+}
 
 // ================================================================ no-alloc sampler
 // A variant of the sampler batch for callers that cannot allocate device
@@ -2408,17 +2769,7 @@ kadabra_status kadabra_compute_delta(int64_t n, const uint32_t* count0, uint64_t
 kadabra_status kadabra_run(kadabra_graph* g, double lambda, double delta, int32_t k, uint64_t seed,
                            const kadabra_config* cfg_in, kadabra_result* out) {
   if (!g || !out) return fail(KADABRA_ERR_ARG, "graph or result is NULL");
-  uint32_t* counts_host = out->counts;
-  double* btilde_host = out->btilde;
-  uint32_t* counts_dev = out->d_counts;
-  double* btilde_dev = out->d_btilde;
-  int32_t* topk = out->topk;
-  std::memset(out, 0, sizeof(*out));
-  out->counts = counts_host;
-  out->btilde = btilde_host;
-  out->d_counts = counts_dev;
-  out->d_btilde = btilde_dev;
-  out->topk = topk;
+  reset_result(out);
   kadabra_config cfg;
   kadabra_config_default(&cfg);
   if (cfg_in) cfg = *cfg_in;
@@ -2429,105 +2780,8 @@ kadabra_status kadabra_run(kadabra_graph* g, double lambda, double delta, int32_
   if (k != 0) return finish(fail(KADABRA_ERR_UNSUPPORTED, "top-k mode (k > 0) is not implemented"));
   if (!(lambda > 0.0 && lambda < 1.0) || !(delta > 0.0 && delta < 1.0) || !(cfg.eps >= 0.0 && cfg.eps < 0.5))
     return finish(fail(KADABRA_ERR_ARG, "lambda and delta must be in (0,1), eps in [0,0.5)"));
-  cudaStream_t st = as_stream(cfg.stream);
-  const int64_t n = g->n;
-
-  out->vd = cfg.vd > 0 ? cfg.vd : g->vd;
-  out->omega = omega_host(lambda, delta, out->vd);
-  const double cap_d = std::ceil(out->omega);
-  if (!(cap_d >= 1.0 && cap_d < 1e15)) return finish(fail(KADABRA_ERR_ARG, "omega out of range"));
-  out->omega_cap = (uint64_t)cap_d;
-  uint64_t alpha = (uint64_t)std::floor(out->omega / 100.0);
-  if (alpha < 1) alpha = 1;
-  out->alpha = alpha;
-  const uint64_t K = cfg.check_interval ? cfg.check_interval : auto_check_interval(out->omega);
-  out->check_interval = K;
-
-  kadabra_status rc = ensure_workspace(g, std::max<uint64_t>(alpha, std::min<uint64_t>(K, out->omega_cap)));
-  if (rc != KADABRA_OK) return finish(rc);
-  SampleParams P = base_params(g);
-  P.job0.seed = seed;
-  P.job0.totals = g->totals;
-#define RUN_CK(call)                                                                     \
-  do {                                                                                   \
-    cudaError_t e_ = (call);                                                             \
-    if (e_ != cudaSuccess) return finish(fail(KADABRA_ERR_CUDA, cudaGetErrorString(e_))); \
-  } while (0)
-  RUN_CK(cudaMemsetAsync(g->totals, 0, sizeof(long long) * KADABRA_NSTAT, st));
-  RUN_CK(cudaMemsetAsync(g->count0, 0, sizeof(uint32_t) * n, st));
-  RUN_CK(cudaMemsetAsync(g->counts, 0, sizeof(uint32_t) * n, st));
-
-  // warm-up (Alg. 2 lines 1-5): alpha samples in RNG domain 1
-  P.job0.domain = 1;
-  P.job0.first_idx = 0;
-  P.job0.count = alpha;
-  P.job0.counts = g->count0;
-  P.total_work = alpha;
-  if ((rc = launch_sampler(g->ws, P, st)) != KADABRA_OK) return finish(rc);
-  std::vector<uint32_t> c0((size_t)n);
-  RUN_CK(cudaMemcpyAsync(c0.data(), g->count0, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, st));
-  if ((rc = read_status(g->ws, st)) != KADABRA_OK) return finish(rc);
-
-  // computeDelta (Alg. 2 lines 6-14)
-  std::vector<double> hL((size_t)n), hU((size_t)n);
-  if ((rc = compute_delta_host(n, c0.data(), alpha, out->omega, lambda, delta, cfg.eps, hL.data(), hU.data(),
-                               &out->C)) != KADABRA_OK)
-    return finish(rc);
-  RUN_CK(cudaMemcpyAsync(g->lnL, hL.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
-  RUN_CK(cudaMemcpyAsync(g->lnU, hU.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
-
-  // main loop (Alg. 1): batches of K samples in domain 0, stop test after each
-  const int check_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(4 * (int64_t)g->num_sms, (n + 255) / 256));
-  uint64_t tau = 0;
-  const uint64_t cap = out->omega_cap;
-  CheckOut h;
-  P.job0.domain = 0;
-  P.job0.counts = g->counts;
-  for (;;) {
-    const uint64_t B = std::min<uint64_t>(K, cap - tau);
-    P.job0.first_idx = tau;
-    P.job0.count = B;
-    P.total_work = B;
-    if ((rc = launch_sampler(g->ws, P, st)) != KADABRA_OK) return finish(rc);
-    tau += B;
-    if (tau >= cap) break;
-    out->checks++;
-    RUN_CK(cudaMemsetAsync(g->chk, 0, sizeof(CheckOut), st));
-    k_check<<<check_blocks, 256, 0, st>>>(g->counts, g->lnL, g->lnU, n, tau, out->omega, lambda, g->chk);
-    RUN_CK(cudaGetLastError());
-    RUN_CK(cudaMemcpyAsync(&h, g->chk, sizeof(CheckOut), cudaMemcpyDeviceToHost, st));
-    if ((rc = read_status(g->ws, st)) != KADABRA_OK) return finish(rc);
-    if (!h.fail) {
-      out->stopped_early = 1;
-      break;
-    }
-  }
-  out->tau = tau;
-  // f and g maxima at the final tau; b~ = counts / tau (Alg. 1 last line)
-  RUN_CK(cudaMemsetAsync(g->chk, 0, sizeof(CheckOut), st));
-  k_check<<<check_blocks, 256, 0, st>>>(g->counts, g->lnL, g->lnU, n, tau, out->omega, lambda, g->chk);
-  RUN_CK(cudaGetLastError());
-  RUN_CK(cudaMemcpyAsync(&h, g->chk, sizeof(CheckOut), cudaMemcpyDeviceToHost, st));
-  const int bt_blocks = check_blocks;
-  if (btilde_host || btilde_dev) {
-    k_btilde<<<bt_blocks, 256, 0, st>>>(g->counts, n, tau, btilde_dev ? btilde_dev : g->btilde);
-    RUN_CK(cudaGetLastError());
-  }
-  if (counts_dev)
-    RUN_CK(cudaMemcpyAsync(counts_dev, g->counts, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st));
-  if (counts_host)
-    RUN_CK(cudaMemcpyAsync(counts_host, g->counts, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, st));
-  if (btilde_host)
-    RUN_CK(cudaMemcpyAsync(btilde_host, btilde_dev ? btilde_dev : g->btilde, sizeof(double) * n,
-                           cudaMemcpyDeviceToHost, st));
-  long long tot[KADABRA_NSTAT];
-  RUN_CK(cudaMemcpyAsync(tot, g->totals, sizeof(tot), cudaMemcpyDeviceToHost, st));
-  if ((rc = read_status(g->ws, st)) != KADABRA_OK) return finish(rc);
-  std::memcpy(&out->max_f, &h.max_f_bits, sizeof(double));
-  std::memcpy(&out->max_g, &h.max_g_bits, sizeof(double));
-  for (int q = 0; q < KADABRA_NSTAT; ++q) out->totals[q] = tot[q];
-#undef RUN_CK
-  return finish(KADABRA_OK);
+  const int64_t vd = cfg.vd;
+  return finish(run_graphs(g->ws, &g, 1, &lambda, &delta, &seed, &vd, cfg, out));
 }
 
 
@@ -2537,6 +2791,7 @@ kadabra_status kadabra_load_batch(int32_t G, const int32_t* n, const int64_t* m,
   if (!out) return fail(KADABRA_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (G < 1 || !n || !m || !row_ptr || !col) return fail(KADABRA_ERR_ARG, "bad batch arguments");
+  if (G > KADABRA_MAX_BATCH_GRAPHS) return fail(KADABRA_ERR_ARG, "too many graphs in one batch");
   kadabra_batch* b = new kadabra_batch;
   b->G = G;
   auto bail = [&](kadabra_status st) {
@@ -2640,215 +2895,14 @@ kadabra_status kadabra_run_batch(kadabra_batch* b, const double* lambda, const d
   if (cfg_in) cfg = *cfg_in;
   if (cfg.vd != 0) return fail(KADABRA_ERR_ARG, "a batch uses each graph's own VD bound (cfg->vd must be 0)");
   if (!(cfg.eps >= 0.0 && cfg.eps < 0.5)) return fail(KADABRA_ERR_ARG, "eps must be in [0, 0.5)");
-  const int G = b->G;
-  cudaStream_t st = as_stream(cfg.stream);
-  struct State {
-    kadabra_graph* g;
-    uint64_t cap, alpha, K, tau;
-    bool done;
-  };
-  std::vector<State> S(G);
-  uint64_t sum_alpha = 0, sum_k = 0;
-  for (int i = 0; i < G; ++i) {
-    kadabra_result& r = out[i];
-    uint32_t* ch = r.counts;
-    double* bh = r.btilde;
-    uint32_t* cd = r.d_counts;
-    double* bd = r.d_btilde;
-    int32_t* tk = r.topk;
-    std::memset(&r, 0, sizeof(r));
-    r.counts = ch;
-    r.btilde = bh;
-    r.d_counts = cd;
-    r.d_btilde = bd;
-    r.topk = tk;
+  for (int i = 0; i < b->G; ++i) {
+    reset_result(&out[i]);
     if (!(lambda[i] > 0.0 && lambda[i] < 1.0) || !(delta[i] > 0.0 && delta[i] < 1.0))
       return fail(KADABRA_ERR_ARG, "lambda and delta must be in (0,1) (graph " + std::to_string(i) + ")");
-    State& s = S[i];
-    s.g = b->views[i];
-    r.vd = s.g->vd;
-    r.omega = omega_host(lambda[i], delta[i], r.vd);
-    const double cap_d = std::ceil(r.omega);
-    if (!(cap_d >= 1.0 && cap_d < 1e15)) return fail(KADABRA_ERR_ARG, "omega out of range");
-    s.cap = r.omega_cap = (uint64_t)cap_d;
-    s.alpha = r.alpha = std::max<uint64_t>(1, (uint64_t)std::floor(r.omega / 100.0));
-    s.K = r.check_interval = cfg.check_interval ? cfg.check_interval : auto_check_interval(r.omega);
-    s.tau = 0;
-    s.done = false;
-    sum_alpha += s.alpha;
-    sum_k += std::min(s.K, s.cap);
   }
-  KTRY(ensure_ws(&b->ws, std::max(sum_alpha, sum_k), G));
-  for (State& s : S) KTRY(ensure_run_buffers(s.g));
-  Workspace* w = &b->ws;
-  // device descriptors of the stop tests: G CheckJobs then G CheckOuts
-  if (w->checks_cap < G) {
-    KCK(cudaDeviceSynchronize());
-    dev_free(w->allocs, w->d_checks);
-    void* p;
-    KTRY(dev_alloc(w->allocs, &p, (sizeof(CheckJob) + sizeof(CheckOut)) * (size_t)G));
-    w->d_checks = p;
-    w->checks_cap = G;
-  }
-  CheckJob* d_cj = static_cast<CheckJob*>(w->d_checks);
-  CheckOut* d_co = reinterpret_cast<CheckOut*>(d_cj + G);
-#define BCK(call)                                                                         \
-  do {                                                                                    \
-    cudaError_t e_ = (call);                                                              \
-    if (e_ != cudaSuccess) return fail(KADABRA_ERR_CUDA, cudaGetErrorString(e_));         \
-  } while (0)
-  for (State& s : S) {
-    BCK(cudaMemsetAsync(s.g->totals, 0, sizeof(long long) * KADABRA_NSTAT, st));
-    BCK(cudaMemsetAsync(s.g->count0, 0, sizeof(uint32_t) * s.g->n, st));
-    BCK(cudaMemsetAsync(s.g->counts, 0, sizeof(uint32_t) * s.g->n, st));
-  }
-  std::vector<Job> jobs;
-  auto launch_jobs = [&]() -> kadabra_status {
-    uint64_t work = 0;
-    for (Job& j : jobs) {
-      j.work_begin = work;
-      work += j.count;
-    }
-    if (work == 0) return KADABRA_OK;
-    BCK(cudaMemcpyAsync(w->d_jobs, jobs.data(), sizeof(Job) * jobs.size(), cudaMemcpyHostToDevice, st));
-    SampleParams P = ws_params(w, 0);
-    P.jobs = w->d_jobs;
-    P.njobs = (int)jobs.size();
-    P.total_work = work;
-    return launch_sampler(w, P, st);
-  };
-  auto make_job = [&](const State& s, uint32_t domain, uint64_t first, uint64_t count, uint32_t* counts,
-                      uint64_t seed_i) {
-    Job j;
-    std::memset(&j, 0, sizeof(j));
-    j.g = graph_dev(s.g);
-    j.seed = seed_i;
-    j.domain = domain;
-    j.first_idx = first;
-    j.count = count;
-    j.counts = counts;
-    j.totals = s.g->totals;
-    return j;
-  };
-  // warm-up of every graph in one launch (Alg. 2 lines 1-5)
-  jobs.clear();
-  for (int i = 0; i < G; ++i) jobs.push_back(make_job(S[i], 1, 0, S[i].alpha, S[i].g->count0, seed[i]));
-  KTRY(launch_jobs());
-  std::vector<std::vector<uint32_t>> c0(G);
-  for (int i = 0; i < G; ++i) {
-    c0[i].resize(S[i].g->n);
-    BCK(cudaMemcpyAsync(c0[i].data(), S[i].g->count0, sizeof(uint32_t) * S[i].g->n, cudaMemcpyDeviceToHost, st));
-  }
-  KTRY(read_status(w, st));
-  // computeDelta per graph (Alg. 2 lines 6-14)
-  std::vector<std::vector<double>> hL(G), hU(G);
-  for (int i = 0; i < G; ++i) {
-    hL[i].resize(S[i].g->n);
-    hU[i].resize(S[i].g->n);
-    KTRY(compute_delta_host(S[i].g->n, c0[i].data(), S[i].alpha, out[i].omega, lambda[i], delta[i], cfg.eps,
-                            hL[i].data(), hU[i].data(), &out[i].C));
-    BCK(cudaMemcpyAsync(S[i].g->lnL, hL[i].data(), sizeof(double) * S[i].g->n, cudaMemcpyHostToDevice, st));
-    BCK(cudaMemcpyAsync(S[i].g->lnU, hU[i].data(), sizeof(double) * S[i].g->n, cudaMemcpyHostToDevice, st));
-  }
-  // stop tests of a set of graphs in one launch; returns their results
-  std::vector<CheckJob> cj;
-  std::vector<CheckOut> co;
-  auto check = [&](const std::vector<int>& which) -> kadabra_status {
-    cj.clear();
-    int64_t max_n = 1;
-    for (int i : which) {
-      CheckJob c;
-      c.counts = S[i].g->counts;
-      c.lnL = S[i].g->lnL;
-      c.lnU = S[i].g->lnU;
-      c.n = S[i].g->n;
-      c.tau = S[i].tau;
-      c.omega = out[i].omega;
-      c.lambda = lambda[i];
-      c.out = d_co + cj.size();
-      cj.push_back(c);
-      max_n = std::max<int64_t>(max_n, c.n);
-    }
-    BCK(cudaMemcpyAsync(d_cj, cj.data(), sizeof(CheckJob) * cj.size(), cudaMemcpyHostToDevice, st));
-    BCK(cudaMemsetAsync(d_co, 0, sizeof(CheckOut) * cj.size(), st));
-    const int bx = (int)std::max<int64_t>(1, std::min<int64_t>((4 * (int64_t)w->num_sms + (int64_t)cj.size() - 1) /
-                                                                   (int64_t)cj.size(),
-                                                               (max_n + 255) / 256));
-    k_check_multi<<<dim3(bx, (unsigned)cj.size()), 256, 0, st>>>(d_cj);
-    BCK(cudaGetLastError());
-    co.resize(cj.size());
-    BCK(cudaMemcpyAsync(co.data(), d_co, sizeof(CheckOut) * cj.size(), cudaMemcpyDeviceToHost, st));
-    return read_status(w, st);
-  };
-  // main loop (Alg. 1): every round samples the next batch of every
-  // unfinished graph in one launch, then tests them all in one launch
-  for (;;) {
-    jobs.clear();
-    std::vector<int> sampled;
-    for (int i = 0; i < G; ++i) {
-      State& s = S[i];
-      if (s.done) continue;
-      const uint64_t B = std::min<uint64_t>(s.K, s.cap - s.tau);
-      jobs.push_back(make_job(s, 0, s.tau, B, s.g->counts, seed[i]));
-      sampled.push_back(i);
-    }
-    if (sampled.empty()) break;
-    KTRY(launch_jobs());
-    std::vector<int> to_check;
-    for (size_t q = 0; q < sampled.size(); ++q) {
-      const int i = sampled[q];
-      S[i].tau += jobs[q].count;
-      if (S[i].tau >= S[i].cap)
-        S[i].done = true;
-      else
-        to_check.push_back(i);
-    }
-    if (to_check.empty()) {
-      KTRY(read_status(w, st));
-      continue;
-    }
-    KTRY(check(to_check));
-    for (size_t q = 0; q < to_check.size(); ++q) {
-      const int i = to_check[q];
-      out[i].checks++;
-      if (!co[q].fail) {
-        out[i].stopped_early = 1;
-        S[i].done = true;
-      }
-    }
-  }
-  // f and g maxima at each final tau; b~ = counts / tau; results out
-  std::vector<int> all(G);
-  for (int i = 0; i < G; ++i) all[i] = i;
-  KTRY(check(all));
-  std::vector<long long> tot((size_t)G * KADABRA_NSTAT);
-  for (int i = 0; i < G; ++i) {
-    kadabra_result& r = out[i];
-    kadabra_graph* g = S[i].g;
-    r.tau = S[i].tau;
-    std::memcpy(&r.max_f, &co[i].max_f_bits, sizeof(double));
-    std::memcpy(&r.max_g, &co[i].max_g_bits, sizeof(double));
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(4 * (int64_t)w->num_sms, (g->n + 255) / 256));
-    if (r.btilde || r.d_btilde) {
-      k_btilde<<<blocks, 256, 0, st>>>(g->counts, g->n, r.tau, r.d_btilde ? r.d_btilde : g->btilde);
-      BCK(cudaGetLastError());
-    }
-    if (r.d_counts)
-      BCK(cudaMemcpyAsync(r.d_counts, g->counts, sizeof(uint32_t) * g->n, cudaMemcpyDeviceToDevice, st));
-    if (r.counts) BCK(cudaMemcpyAsync(r.counts, g->counts, sizeof(uint32_t) * g->n, cudaMemcpyDeviceToHost, st));
-    if (r.btilde)
-      BCK(cudaMemcpyAsync(r.btilde, r.d_btilde ? r.d_btilde : g->btilde, sizeof(double) * g->n,
-                          cudaMemcpyDeviceToHost, st));
-    BCK(cudaMemcpyAsync(&tot[(size_t)i * KADABRA_NSTAT], g->totals, sizeof(long long) * KADABRA_NSTAT,
-                        cudaMemcpyDeviceToHost, st));
-  }
-  KTRY(read_status(w, st));
-  for (int i = 0; i < G; ++i) {
-    for (int q = 0; q < KADABRA_NSTAT; ++q) out[i].totals[q] = tot[(size_t)i * KADABRA_NSTAT + q];
-    out[i].status = KADABRA_OK;
-  }
-#undef BCK
-  return KADABRA_OK;
+  const kadabra_status s = run_graphs(&b->ws, b->views.data(), b->G, lambda, delta, seed, nullptr, cfg, out);
+  for (int i = 0; i < b->G; ++i) out[i].status = s;
+  return s;
 }
 
 }  // extern "C"
