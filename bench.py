@@ -2,11 +2,19 @@
 
 One step = one full run of the hot path (warm-up sampling, computeDelta, then
 sample batches of K with the FP64 stop test after each, until the stop rule
-holds or ceil(omega) samples) on the plain single-graph workload:
+holds or ceil(omega) samples) on one graph.  Workloads (--workload):
 
-    Chung-Lu power-law graph, n = 10^6, beta = 2.5, mean degree 16,
-    max expected degree 10^4, largest component (seeded, synthetic), int32
-    CSR; lambda = 0.005, delta = 0.1, stop test every 2^16 samples.
+    chung_lu_1m (default): Chung-Lu power-law graph, n = 10^6, beta = 2.5,
+        mean degree 16, max expected degree 10^4, largest component, int32
+        CSR; lambda = 0.005, delta = 0.1, stop test every 2^16 samples.
+    erdos_renyi_2k: G(n = 2000, mean degree 8), largest component;
+        lambda = 0.01, delta = 0.1, stop test every 1000 samples.
+    rmat_24: directed R-MAT, scale 24, edge factor 16, (a, b, c) = (0.57,
+        0.19, 0.19), self-loops and duplicate arcs removed, all 2^24 ids kept,
+        forward and reverse CSR; all-nodes mode at lambda = 0.0025,
+        delta = 0.1, stop test every 2^16 samples.
+    batched: 64 Barabasi-Albert graphs of uneven sizes, one batched run
+        against the same graphs run one at a time.
 
 Prints ONE JSON line (rank 0).  `value` is sampled paths per second over the
 whole run (warm-up + main loop) with the graph resident on the device;
@@ -33,28 +41,50 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "paths/sec & time-to-(lambda,delta) per graph, batched vs plain on GPU; % HBM roofline"
-WORKLOAD = dict(family="chung_lu", n=1_000_000, beta=2.5, mean_deg=16.0, max_deg=10_000.0, graph_seed=1,
-                lcc=True, lam=0.005, delta=0.1, check_interval=1 << 16)
+# Single-graph workloads.  `sampler_dram_bytes`: DRAM bytes (read + write) of
+# one sampler batch of K samples, summed over its launches, from an ncu capture
+# summarised under profiles/ (None until captured for the current kernels).
+WORKLOADS = {
+    "chung_lu_1m": dict(family="chung_lu", n=1_000_000, beta=2.5, mean_deg=16.0, max_deg=10_000.0, graph_seed=1,
+                        lcc=True, lam=0.005, delta=0.1, check_interval=1 << 16,
+                        sampler_dram_bytes=77_121_792 + 5_952_000 + 43_818_752 + 619_776 + 66_304),
+    "erdos_renyi_2k": dict(family="erdos_renyi", n=2000, mean_deg=8.0, graph_seed=1, lcc=True, lam=0.01,
+                           delta=0.1, check_interval=1000, sampler_dram_bytes=None),
+    "rmat_24": dict(family="rmat", scale=24, edge_factor=16, a=0.57, b=0.19, c=0.19, graph_seed=1, lam=0.0025,
+                    delta=0.1, check_interval=1 << 16, sampler_dram_bytes=None),
+}
+WORKLOAD = WORKLOADS["chung_lu_1m"]
 L2_FLUSH_BYTES = 512 << 20
-# DRAM bytes (read + write) of one sampler batch of this workload, summed over
-# its three launches, from the ncu capture in profiles/k_sample_chung_lu_1m_full.md
-# (set to None whenever the sampler kernels change until re-captured)
-SAMPLER_DRAM_BYTES = 121_185_024 + 6_193_152
 
 
 def make_graph():
     from paper_1604_08553_gb300 import graphgen
     w = WORKLOAD
-    return graphgen.chung_lu(w["n"], w["beta"], w["mean_deg"], w["max_deg"], w["graph_seed"], lcc=w["lcc"])
+    if w["family"] == "chung_lu":
+        return graphgen.chung_lu(w["n"], w["beta"], w["mean_deg"], w["max_deg"], w["graph_seed"], lcc=w["lcc"])
+    if w["family"] == "erdos_renyi":
+        return graphgen.erdos_renyi(w["n"], w["mean_deg"], w["graph_seed"], lcc=w["lcc"])
+    return graphgen.rmat(w["scale"], w["edge_factor"], w["a"], w["b"], w["c"], w["graph_seed"])
+
+
+def workload_name():
+    w = WORKLOAD
+    tail = f"lambda={w['lam']} delta={w['delta']} K={w['check_interval']}"
+    if w["family"] == "chung_lu":
+        return (f"chung_lu n={w['n']} beta={w['beta']} mean_deg={w['mean_deg']:g} max_deg={w['max_deg']:g} "
+                f"lcc; {tail}")
+    if w["family"] == "erdos_renyi":
+        return f"erdos_renyi n={w['n']} mean_deg={w['mean_deg']:g} lcc; {tail}"
+    return (f"rmat scale={w['scale']} edge_factor={w['edge_factor']} a={w['a']} b={w['b']} c={w['c']} directed, "
+            f"all ids; {tail}")
 
 
 def workload_config(g, extra=None):
     w = WORKLOAD
     cfg = {
-        "workload": (f"chung_lu n={w['n']} beta={w['beta']} mean_deg={w['mean_deg']:g} max_deg={w['max_deg']:g} "
-                     f"lcc; lambda={w['lam']} delta={w['delta']} K={w['check_interval']}"),
-        "nodes": int(g.n), "arcs": int(g.m), "lambda": w["lam"], "delta": w["delta"],
-        "check_interval": w["check_interval"], "graph_seed": w["graph_seed"],
+        "workload": workload_name(),
+        "nodes": int(g.n), "arcs": int(g.m), "directed": bool(g.directed), "lambda": w["lam"],
+        "delta": w["delta"], "check_interval": w["check_interval"], "graph_seed": w["graph_seed"],
         "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write)",
     }
     if extra:
@@ -136,6 +166,12 @@ def algorithmic_bytes(totals, hits):
     return (8 * t[1] + 8 * t[0] + 12 * t[2] + 8 * t[3] + 4 * hits + 4 * t[6])
 
 
+def sampler_launches_per_batch():
+    """Kernels of one sampler batch: the shared-memory tier and the two
+    escalation tiers (which exit at once when nothing was queued to them)."""
+    return 3
+
+
 def cpu_baseline(g, seconds_cap=20.0):
     """The oracle (single-threaded, as it stands) on a bounded sample of the
     same workload: the first main-loop samples of seed 1."""
@@ -153,7 +189,7 @@ def cpu_baseline(g, seconds_cap=20.0):
         count += chunk
     dt = time.perf_counter() - t0
     return {"value": count / dt, "unit": "paths/s", "cores": 1, "kind": "oracle",
-            "sample": f"main-loop samples 0..{count - 1} (seed 1) of the Chung-Lu n=1e6 workload, "
+            "sample": f"main-loop samples 0..{count - 1} (seed 1) of the {workload_name()} workload, "
                       f"single-threaded oracle, {dt:.1f} s"}
 
 
@@ -288,10 +324,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sampler-only", type=int, default=0, metavar="LAUNCHES",
                     help="only time LAUNCHES sampler batches of K samples (for profilers)")
-    ap.add_argument("--workload", default="plain", choices=["plain", "batched"],
-                    help="plain: one Chung-Lu graph (default); batched: 64 uneven Barabasi-Albert graphs, "
+    ap.add_argument("--workload", default="chung_lu_1m", choices=[*WORKLOADS, "batched"],
+                    help="one-graph workload (default chung_lu_1m), or batched: 64 uneven Barabasi-Albert graphs, "
                          "batched run against one-graph-at-a-time runs")
     args = ap.parse_args()
+    global WORKLOAD
+    if args.workload in WORKLOADS:
+        WORKLOAD = WORKLOADS[args.workload]
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
 
@@ -357,7 +396,10 @@ def main():
         ev1.synchronize()
         times.append(ev0.elapsed_time(ev1) / 1e3)
         paths += r.alpha + r.tau
-        launches += 2 + 2 * (r.checks + 1) + r.checks + 1 + 1
+        # warm-up batch, warm-up count compaction (3), main-loop batches,
+        # stop tests, the final test and b~
+        rounds = -(-int(r.tau) // w["check_interval"])
+        launches += sampler_launches_per_batch() * (1 + rounds) + 3 + int(r.checks) + 1 + 1
         results.append(r)
     torch.cuda.synchronize()
     barrier()
@@ -401,7 +443,7 @@ def main():
     e2e_steps = max(2, min(args.steps, 3))
     counts_h = np.zeros(g.n, dtype=np.uint32)
     btilde_h = np.zeros(g.n, dtype=np.float64)
-    h2d = 4 * (g.n + 1) + 4 * g.m
+    h2d = (4 * (g.n + 1) + 4 * g.m) * (2 if g.directed else 1)  # forward (+ reverse) CSR
     d2h = 4 * g.n + 8 * g.n
     torch.cuda.synchronize()
     e2e_paths = 0
@@ -434,7 +476,7 @@ def main():
                 "edges_per_sample": float(tot_np[0]) / K,
             }),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": SAMPLER_DRAM_BYTES, "kernel": "k_sample (sampler batch)",
+                         "frac": achieved / peak, "traffic": w["sampler_dram_bytes"], "kernel": "k_sample (sampler batch)",
                          "bytes_per_launch": avg_b, "launch_ms": 1e3 * avg_t, "samples_per_launch": K,
                          "peak_source": peak_src},
             "e2e": {"value": e2e_value, "unit": "paths/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
