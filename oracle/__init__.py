@@ -95,6 +95,12 @@ def _load():
         lib.orc_f_and_g.argtypes = [u32, u64, dbl, dbl, dbl, p, p]
         lib.orc_check_stop.argtypes = [i64, p, u64, dbl, p, p, dbl, p, p]
         lib.orc_run.argtypes = graph + [dbl, dbl, u64, u64, i64, dbl, p, p, p, p, C.POINTER(orc_result)]
+        lib.orc_run_topk.argtypes = graph + [dbl, dbl, u64, u64, i64, dbl, i64, p, p, p, p, p, p, p, p,
+                                             C.POINTER(orc_result)]
+        lib.orc_compute_delta_lv.argtypes = [i64, p, u64, dbl, p, p, dbl, dbl, p, p]
+        lib.orc_compute_delta_lv.restype = dbl
+        lib.orc_topk_lambdas.argtypes = [i64, p, u64, i64, dbl, p, p]
+        lib.orc_check_stop_topk.argtypes = [i64, p, u64, dbl, p, p, dbl, i64, p, p, p]
         lib.orc_brandes.argtypes = graph + [p]
         lib.orc_enumerate_paths.argtypes = graph + [i32, i32, i64, i32, p]
         lib.orc_enumerate_paths.restype = i64
@@ -231,6 +237,45 @@ def check_stop(counts: np.ndarray, tau: int, omega_: float, lnL: np.ndarray, lnU
     return bool(stop), mf.value, mg.value
 
 
+def compute_delta_lv(count0: np.ndarray, alpha: int, omega_: float, lam_l: np.ndarray, lam_u: np.ndarray,
+                     delta: float, eps: float):
+    """Alg. 2 with per-node error targets lambda_L(v), lambda_U(v)."""
+    c0 = np.ascontiguousarray(count0, dtype=np.uint32)
+    ll = np.ascontiguousarray(lam_l, dtype=np.float64)
+    lu = np.ascontiguousarray(lam_u, dtype=np.float64)
+    n = c0.shape[0]
+    dl = np.zeros(n, dtype=np.float64)
+    du = np.zeros(n, dtype=np.float64)
+    Cval = _load().orc_compute_delta_lv(n, _ptr(c0), alpha, omega_, _ptr(ll), _ptr(lu), delta, eps, _ptr(dl),
+                                        _ptr(du))
+    return float(Cval), dl, du
+
+
+def topk_lambdas(count_pre: np.ndarray, alpha_pre: int, k: int, lam: float):
+    """Sec. 5 error targets (lambda_L, lambda_U) for the top-k stop test."""
+    c = np.ascontiguousarray(count_pre, dtype=np.uint32)
+    n = c.shape[0]
+    ll = np.zeros(n, dtype=np.float64)
+    lu = np.zeros(n, dtype=np.float64)
+    _load().orc_topk_lambdas(n, _ptr(c), alpha_pre, k, lam, _ptr(ll), _ptr(lu))
+    return ll, lu
+
+
+def check_stop_topk(counts: np.ndarray, tau: int, omega_: float, lnL: np.ndarray, lnU: np.ndarray, lam: float,
+                    k: int):
+    """Alg. 3: (stop, top-k ids, max f, max g)."""
+    c = np.ascontiguousarray(counts, dtype=np.uint32)
+    L = np.ascontiguousarray(lnL, dtype=np.float64)
+    U = np.ascontiguousarray(lnU, dtype=np.float64)
+    n = c.shape[0]
+    top = np.full(min(k, n), -1, dtype=np.int32)
+    mf = C.c_double()
+    mg = C.c_double()
+    stop = _load().orc_check_stop_topk(n, _ptr(c), tau, omega_, _ptr(L), _ptr(U), lam, k, _ptr(top),
+                                       C.byref(mf), C.byref(mg))
+    return bool(stop), top, mf.value, mg.value
+
+
 @dataclass
 class RunResult:
     res: orc_result
@@ -238,6 +283,10 @@ class RunResult:
     count0: np.ndarray
     ln_inv_dl: np.ndarray
     ln_inv_du: np.ndarray
+    topk: np.ndarray = None
+    count_pre: np.ndarray = None
+    lam_l: np.ndarray = None
+    lam_u: np.ndarray = None
 
     def __getattr__(self, k):
         return getattr(self.res, k)
@@ -255,6 +304,25 @@ def run(g, lam: float, delta: float, seed: int, K: int, vd: int = 0, eps: float 
                     C.byref(res))
     del keep
     return RunResult(res, counts, count0, dl, du)
+
+
+def run_topk(g, lam: float, delta: float, k: int, seed: int, K: int, vd: int = 0, eps: float = 0.001) -> RunResult:
+    """Alg. 1 in top-k mode (Sec. 5 targets, Alg. 2, Alg. 3 every K samples)."""
+    keep, ga = _gargs(g)
+    n = int(g.n)
+    counts = np.zeros(n, dtype=np.uint32)
+    count0 = np.zeros(n, dtype=np.uint32)
+    count_pre = np.zeros(n, dtype=np.uint32)
+    dl = np.zeros(n, dtype=np.float64)
+    du = np.zeros(n, dtype=np.float64)
+    ll = np.zeros(n, dtype=np.float64)
+    lu = np.zeros(n, dtype=np.float64)
+    top = np.full(min(k, n), -1, dtype=np.int32)
+    res = orc_result()
+    _load().orc_run_topk(*ga, lam, delta, seed, K, vd, eps, k, _ptr(counts), _ptr(count0), _ptr(dl), _ptr(du),
+                         _ptr(top), _ptr(count_pre), _ptr(ll), _ptr(lu), C.byref(res))
+    del keep
+    return RunResult(res, counts, count0, dl, du, top, count_pre, ll, lu)
 
 
 def brandes(g) -> np.ndarray:

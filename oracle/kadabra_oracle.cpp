@@ -19,7 +19,11 @@
 //                      c_L, c_U, bisection for C, delta_L, delta_U).
 //   check_stop         Thm. 2 (functions f and g) and the all-nodes stopping
 //                      rule f <= lambda and g <= lambda for every node (Sec. 2).
-//   run                Alg. 1 with the stop test evaluated every K samples.
+//   topk_lambdas       Sec. 5: lambda_L(v), lambda_U(v) from a preliminary
+//                      estimate, for the top-k stopping condition.
+//   check_stop_topk    Alg. 3 (haveToStop for the k most central nodes).
+//   run                Alg. 1 with the stop test evaluated every K samples;
+//                      all-nodes mode, or top-k mode (Sec. 5, Alg. 3).
 //   brandes            exact normalised betweenness (Sec. 2 definition), by
 //                      Brandes' dependency accumulation; used only by tests.
 //   enumerate_paths    brute-force list of all shortest s-t paths; tests only.
@@ -51,6 +55,16 @@
 //     App. D text, 0.0001 in Alg. 2).
 //   * The bisection for C keeps the upper end so sum(delta) <= delta/2 and
 //     stops at the FP64 fixed point; terms with c(v) = 0 are 0.
+//   * Top-k mode: the preliminary estimate of Sec. 5 takes alpha samples in
+//     RNG domain 2.  Nodes are ranked by b~ decreasing, ties by id
+//     increasing.  Undefined neighbours of the ranking: lambda_U(v_1) = 1
+//     (no node lies above v_1, and betweenness is at most 1) and
+//     lambda_L(v_n) = 1; in Alg. 3, b~(v_0) - f = +inf and
+//     b~(v_{n+1}) + g = -inf.  k > n is taken as k = n.  The Sec. 5 rules
+//     apply in the order the text gives them (top-k nodes, the others, then
+//     small gaps); a gap b~(v_i) - b~(v_{i+1}) < 2 lambda (i <= k) is
+//     "small"; finally every lambda_L, lambda_U below lambda is raised to
+//     lambda (the rule for the other nodes can give values <= 0).
 
 #include <cmath>
 #include <cstdint>
@@ -482,16 +496,16 @@ int64_t vd_heuristic(const Graph& g) {
 }
 
 // ---------------------------------------------------------------- computeDelta
-// Alg. 2 with lambda_L = lambda_U = lambda (all-nodes mode).  Writes
+// Alg. 2 with per-node targets lambda_L(v), lambda_U(v).  Writes
 // ln(1/delta_L(v)) and ln(1/delta_U(v)); returns C.
-double compute_delta(int64_t n, const uint32_t* count0, uint64_t alpha, double omega, double lambda,
-                     double delta, double eps, double* ln_inv_dl, double* ln_inv_du) {
+double compute_delta_lv(int64_t n, const uint32_t* count0, uint64_t alpha, double omega, const double* lamL,
+                        const double* lamU, double delta, double eps, double* ln_inv_dl, double* ln_inv_du) {
   std::vector<double> cL(n), cU(n);
   bool any = false;
   for (int64_t v = 0; v < n; ++v) {
     double b0 = (double)count0[v] / (double)alpha;
-    cL[v] = ((2.0 * b0) * omega) / (lambda * lambda);
-    cU[v] = ((2.0 * b0) * omega) / (lambda * lambda);
+    cL[v] = ((2.0 * b0) * omega) / (lamL[v] * lamL[v]);
+    cU[v] = ((2.0 * b0) * omega) / (lamU[v] * lamU[v]);
     if (cL[v] > 0.0 || cU[v] > 0.0) any = true;
   }
   const double target = (delta / 2.0) - (eps * delta);
@@ -531,6 +545,60 @@ double compute_delta(int64_t n, const uint32_t* count0, uint64_t alpha, double o
   return C;
 }
 
+// Alg. 2 in all-nodes mode: lambda_L = lambda_U = lambda for every node.
+double compute_delta(int64_t n, const uint32_t* count0, uint64_t alpha, double omega, double lambda,
+                     double delta, double eps, double* ln_inv_dl, double* ln_inv_du) {
+  std::vector<double> lam(n, lambda);
+  return compute_delta_lv(n, count0, alpha, omega, lam.data(), lam.data(), delta, eps, ln_inv_dl, ln_inv_du);
+}
+
+// ---------------------------------------------------------------- top-k (Sec. 5)
+// Nodes in decreasing order of b~ = count / denom, ties by increasing id.
+std::vector<int64_t> rank_nodes(int64_t n, const uint32_t* count, double denom) {
+  std::vector<int64_t> order(n);
+  for (int64_t v = 0; v < n; ++v) order[v] = v;
+  std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+    double ba = (double)count[a] / denom, bb = (double)count[b] / denom;
+    if (ba != bb) return ba > bb;
+    return a < b;
+  });
+  return order;
+}
+
+// Sec. 5: the error targets that separate the k most central nodes of a
+// preliminary estimate (count_pre / alpha_pre) from one another and from the
+// rest.  Writes lambda_L(v), lambda_U(v) for every node.
+void topk_lambdas(int64_t n, const uint32_t* count_pre, uint64_t alpha_pre, int64_t k, double lambda, double* lamL,
+                  double* lamU) {
+  const double a = (double)alpha_pre;
+  std::vector<int64_t> vv = rank_nodes(n, count_pre, a);  // v_1 .. v_n at vv[0 .. n-1]
+  auto bt = [&](int64_t i) { return (double)count_pre[vv[i - 1]] / a; };  // b~(v_i), 1-based
+  if (k > n) k = n;
+  // the k first nodes: half the gaps to their neighbours in the ranking
+  for (int64_t i = 1; i <= k; ++i) {
+    const int64_t v = vv[i - 1];
+    lamU[v] = i == 1 ? 1.0 : (bt(i - 1) - bt(i)) / 2.0;
+    lamL[v] = i == n ? 1.0 : (bt(i) - bt(i + 1)) / 2.0;
+  }
+  // the other nodes: show that they lie below the k-th node's lower end
+  for (int64_t i = k + 1; i <= n; ++i) {
+    const int64_t v = vv[i - 1];
+    lamL[v] = 1.0;
+    lamU[v] = bt(k) - lamL[vv[k - 1]] - bt(i);
+  }
+  // small gaps: the order of the two nodes is not known, plain lambda for both
+  for (int64_t i = 1; i <= k && i + 1 <= n; ++i) {
+    if (bt(i) - bt(i + 1) < 2.0 * lambda) {
+      lamL[vv[i - 1]] = lamU[vv[i - 1]] = lambda;
+      lamL[vv[i]] = lamU[vv[i]] = lambda;
+    }
+  }
+  for (int64_t v = 0; v < n; ++v) {
+    if (!(lamL[v] >= lambda)) lamL[v] = lambda;
+    if (!(lamU[v] >= lambda)) lamU[v] = lambda;
+  }
+}
+
 // ---------------------------------------------------------------- stop test
 // f and g of Thm. 2 for one node, evaluated with this exact expression tree.
 void f_and_g(uint32_t count, uint64_t tau, double omega, double lnL, double lnU, double* f, double* g) {
@@ -557,6 +625,50 @@ int check_stop(int64_t n, const uint32_t* count, uint64_t tau, double omega, con
   *max_f = mf;
   *max_g = mg;
   return stop;
+}
+
+// Alg. 3: haveToStop for the k most central nodes.  Ranks the nodes by the
+// current b~ = count / tau; a node whose f or g exceeds lambda must have a
+// confidence interval separated from its neighbours' in the ranking (the k
+// first nodes) or from the k-th node's (the others).  Writes the k first
+// nodes of the ranking to topk (if not NULL) and max f, max g over all nodes.
+int check_stop_topk(int64_t n, const uint32_t* count, uint64_t tau, double omega, const double* lnL,
+                    const double* lnU, double lambda, int64_t k, int32_t* topk, double* max_f, double* max_g) {
+  if (k > n) k = n;
+  std::vector<double> f(n), g(n), b(n);
+  double mf = 0.0, mg = 0.0;
+  const double t = (double)tau;
+  for (int64_t v = 0; v < n; ++v) {
+    f_and_g(count[v], tau, omega, lnL[v], lnU[v], &f[v], &g[v]);
+    b[v] = (double)count[v] / t;
+    if (f[v] > mf) mf = f[v];
+    if (g[v] > mg) mg = g[v];
+  }
+  *max_f = mf;
+  *max_g = mg;
+  std::vector<int64_t> vv = rank_nodes(n, count, t);
+  if (topk)
+    for (int64_t i = 0; i < k; ++i) topk[i] = (int32_t)vv[i];
+  auto loose = [&](int64_t v) { return f[v] > lambda || g[v] > lambda; };
+  for (int64_t i = 1; i <= k; ++i) {
+    const int64_t v = vv[i - 1];
+    if (!loose(v)) continue;
+    if (i > 1) {
+      const int64_t u = vv[i - 2];
+      if (b[u] - f[u] < b[v] + g[v]) return 0;
+    }
+    if (i < n) {
+      const int64_t w = vv[i];
+      if (b[v] - f[v] < b[w] + g[w]) return 0;
+    }
+  }
+  const int64_t vk = vv[k - 1];
+  for (int64_t i = k + 1; i <= n; ++i) {
+    const int64_t v = vv[i - 1];
+    if (!loose(v)) continue;
+    if (b[vk] - f[vk] < b[v] + g[v]) return 0;
+  }
+  return 1;
 }
 
 }  // namespace
@@ -700,15 +812,20 @@ int orc_check_stop(int64_t n, const uint32_t* count, uint64_t tau, double omega,
   return check_stop(n, count, tau, omega, lnL, lnU, lambda, max_f, max_g);
 }
 
-// Alg. 1 in all-nodes mode with the stop test every K samples.
+// Alg. 1 with the stop test every K samples: all-nodes mode (k = 0), or the
+// k most central nodes (k > 0: Sec. 5 targets from a preliminary estimate,
+// Alg. 2 with those targets, Alg. 3 as the stop test).
 // counts: n (main-loop hits); count0: n or NULL (warm-up hits);
-// ln_inv_dl/du: n or NULL (the computeDelta tables).
-int orc_run(int64_t n, const int32_t* rp, const int32_t* ci, int directed, const int32_t* rrp, const int32_t* rci,
-            double lambda, double delta, uint64_t seed, uint64_t K, int64_t vd, double eps, uint32_t* counts,
-            uint32_t* count0_out, double* ln_inv_dl_out, double* ln_inv_du_out, orc_result* res) {
+// ln_inv_dl/du: n or NULL (the computeDelta tables); topk: k or NULL;
+// count_pre, lam_l, lam_u: n or NULL (top-k preliminary hits and targets).
+static int run_impl(int64_t n, const int32_t* rp, const int32_t* ci, int directed, const int32_t* rrp,
+                    const int32_t* rci, double lambda, double delta, uint64_t seed, uint64_t K, int64_t vd,
+                    double eps, int64_t k, uint32_t* counts, uint32_t* count0_out, double* ln_inv_dl_out,
+                    double* ln_inv_du_out, int32_t* topk_out, uint32_t* count_pre_out, double* lam_l_out,
+                    double* lam_u_out, orc_result* res) {
   std::memset(res, 0, sizeof(*res));
   if (n < 2 || !(lambda > 0.0) || !(delta > 0.0) || !(delta < 1.0) || K == 0 || !(eps >= 0.0) ||
-      !(eps < 0.5)) {
+      !(eps < 0.5) || k < 0) {
     res->status = ORC_ERR_ARG;
     return ORC_ERR_ARG;
   }
@@ -722,25 +839,53 @@ int orc_run(int64_t n, const int32_t* rp, const int32_t* ci, int directed, const
 
   Work wk(n);
   Sample smp;
-
-  // warm-up (domain 1)
-  std::vector<uint32_t> count0(n, 0);
-  for (uint64_t i = 0; i < alpha; ++i) {
-    sample_one(g, seed, 1, i, wk, smp);
-    if (smp.status != ORC_OK) {
-      res->status = smp.status;
-      return smp.status;
+  // alpha samples of one RNG domain, hits of interior nodes into cnt
+  auto sample_into = [&](uint32_t domain, std::vector<uint32_t>& cnt) {
+    for (uint64_t i = 0; i < alpha; ++i) {
+      sample_one(g, seed, domain, i, wk, smp);
+      if (smp.status != ORC_OK) return smp.status;
+      for (size_t q = 1; q + 1 < smp.path.size(); ++q) cnt[smp.path[q]] += 1;
+      res->edges_warm += smp.st[ST_EDGES];
     }
-    for (size_t k = 1; k + 1 < smp.path.size(); ++k) count0[smp.path[k]] += 1;
-    res->edges_warm += smp.st[ST_EDGES];
+    return (int)ORC_OK;
+  };
+
+  // top-k: preliminary estimate (domain 2) and the Sec. 5 targets
+  std::vector<double> lamL(n, lambda), lamU(n, lambda);
+  std::vector<uint32_t> count_pre;
+  if (k > 0) {
+    count_pre.assign(n, 0);
+    int st = sample_into(2, count_pre);
+    if (st != ORC_OK) {
+      res->status = st;
+      return st;
+    }
+    topk_lambdas(n, count_pre.data(), alpha, k, lambda, lamL.data(), lamU.data());
+  }
+  // warm-up (domain 1) and computeDelta
+  std::vector<uint32_t> count0(n, 0);
+  {
+    int st = sample_into(1, count0);
+    if (st != ORC_OK) {
+      res->status = st;
+      return st;
+    }
   }
   std::vector<double> lnL(n), lnU(n);
-  res->C = compute_delta(n, count0.data(), alpha, res->omega, lambda, delta, eps, lnL.data(), lnU.data());
+  if (k > 0)
+    res->C = compute_delta_lv(n, count0.data(), alpha, res->omega, lamL.data(), lamU.data(), delta, eps,
+                              lnL.data(), lnU.data());
+  else
+    res->C = compute_delta(n, count0.data(), alpha, res->omega, lambda, delta, eps, lnL.data(), lnU.data());
 
   // main loop (domain 0)
   for (int64_t v = 0; v < n; ++v) counts[v] = 0;
   uint64_t tau = 0;
   const uint64_t cap = res->omega_cap;
+  auto stop_test = [&](double* mf, double* mg, int32_t* topk) {
+    if (k > 0) return check_stop_topk(n, counts, tau, res->omega, lnL.data(), lnU.data(), lambda, k, topk, mf, mg);
+    return check_stop(n, counts, tau, res->omega, lnL.data(), lnU.data(), lambda, mf, mg);
+  };
   for (;;) {
     uint64_t B = std::min<uint64_t>(K, cap - tau);
     for (uint64_t i = 0; i < B; ++i) {
@@ -749,25 +894,65 @@ int orc_run(int64_t n, const int32_t* rp, const int32_t* ci, int directed, const
         res->status = smp.status;
         return smp.status;
       }
-      for (size_t k = 1; k + 1 < smp.path.size(); ++k) counts[smp.path[k]] += 1;
+      for (size_t q = 1; q + 1 < smp.path.size(); ++q) counts[smp.path[q]] += 1;
       res->edges_main += smp.st[ST_EDGES];
     }
     tau += B;
     if (tau >= cap) break;
     res->checks++;
     double mf, mg;
-    if (check_stop(n, counts, tau, res->omega, lnL.data(), lnU.data(), lambda, &mf, &mg)) {
+    if (stop_test(&mf, &mg, nullptr)) {
       res->stopped_early = 1;
       break;
     }
   }
   res->tau = tau;
-  check_stop(n, counts, tau, res->omega, lnL.data(), lnU.data(), lambda, &res->max_f, &res->max_g);
+  stop_test(&res->max_f, &res->max_g, topk_out);
   if (count0_out) std::memcpy(count0_out, count0.data(), sizeof(uint32_t) * n);
   if (ln_inv_dl_out) std::memcpy(ln_inv_dl_out, lnL.data(), sizeof(double) * n);
   if (ln_inv_du_out) std::memcpy(ln_inv_du_out, lnU.data(), sizeof(double) * n);
+  if (k > 0 && count_pre_out) std::memcpy(count_pre_out, count_pre.data(), sizeof(uint32_t) * n);
+  if (lam_l_out) std::memcpy(lam_l_out, lamL.data(), sizeof(double) * n);
+  if (lam_u_out) std::memcpy(lam_u_out, lamU.data(), sizeof(double) * n);
   res->status = ORC_OK;
   return ORC_OK;
+}
+
+// Alg. 1 in all-nodes mode with the stop test every K samples.
+int orc_run(int64_t n, const int32_t* rp, const int32_t* ci, int directed, const int32_t* rrp, const int32_t* rci,
+            double lambda, double delta, uint64_t seed, uint64_t K, int64_t vd, double eps, uint32_t* counts,
+            uint32_t* count0_out, double* ln_inv_dl_out, double* ln_inv_du_out, orc_result* res) {
+  return run_impl(n, rp, ci, directed, rrp, rci, lambda, delta, seed, K, vd, eps, 0, counts, count0_out,
+                  ln_inv_dl_out, ln_inv_du_out, nullptr, nullptr, nullptr, nullptr, res);
+}
+
+// Alg. 1 in top-k mode (k >= 1): Sec. 5 targets, Alg. 2, Alg. 3 every K samples.
+int orc_run_topk(int64_t n, const int32_t* rp, const int32_t* ci, int directed, const int32_t* rrp,
+                 const int32_t* rci, double lambda, double delta, uint64_t seed, uint64_t K, int64_t vd, double eps,
+                 int64_t k, uint32_t* counts, uint32_t* count0_out, double* ln_inv_dl_out, double* ln_inv_du_out,
+                 int32_t* topk_out, uint32_t* count_pre_out, double* lam_l_out, double* lam_u_out, orc_result* res) {
+  if (k < 1) {
+    std::memset(res, 0, sizeof(*res));
+    res->status = ORC_ERR_ARG;
+    return ORC_ERR_ARG;
+  }
+  return run_impl(n, rp, ci, directed, rrp, rci, lambda, delta, seed, K, vd, eps, k, counts, count0_out,
+                  ln_inv_dl_out, ln_inv_du_out, topk_out, count_pre_out, lam_l_out, lam_u_out, res);
+}
+
+double orc_compute_delta_lv(int64_t n, const uint32_t* count0, uint64_t alpha, double omega, const double* lamL,
+                            const double* lamU, double delta, double eps, double* ln_inv_dl, double* ln_inv_du) {
+  return compute_delta_lv(n, count0, alpha, omega, lamL, lamU, delta, eps, ln_inv_dl, ln_inv_du);
+}
+
+void orc_topk_lambdas(int64_t n, const uint32_t* count_pre, uint64_t alpha_pre, int64_t k, double lambda,
+                      double* lamL, double* lamU) {
+  topk_lambdas(n, count_pre, alpha_pre, k, lambda, lamL, lamU);
+}
+
+int orc_check_stop_topk(int64_t n, const uint32_t* count, uint64_t tau, double omega, const double* lnL,
+                        const double* lnU, double lambda, int64_t k, int32_t* topk, double* max_f, double* max_g) {
+  return check_stop_topk(n, count, tau, omega, lnL, lnU, lambda, k, topk, max_f, max_g);
 }
 
 // Exact normalised betweenness bc(v) = 1/(n(n-1)) sum_{s!=v!=t} sigma_st(v)/sigma_st
