@@ -13,6 +13,7 @@ holds or ceil(omega) samples) on one graph.  Workloads (--workload):
         0.19, 0.19), self-loops and duplicate arcs removed, all 2^24 ids kept,
         forward and reverse CSR; all-nodes mode at lambda = 0.0025,
         delta = 0.1, stop test every 2^16 samples.
+    rmat_24_topk: the same graph in top-k mode (Sec. 5, Alg. 3), k = 10.
     batched: 64 Barabasi-Albert graphs of uneven sizes, one batched run
         against the same graphs run one at a time.
 
@@ -52,6 +53,8 @@ WORKLOADS = {
                            delta=0.1, check_interval=1000, sampler_dram_bytes=None),
     "rmat_24": dict(family="rmat", scale=24, edge_factor=16, a=0.57, b=0.19, c=0.19, graph_seed=1, lam=0.0025,
                     delta=0.1, check_interval=1 << 16, sampler_dram_bytes=None),
+    "rmat_24_topk": dict(family="rmat", scale=24, edge_factor=16, a=0.57, b=0.19, c=0.19, graph_seed=1, lam=0.0025,
+                         delta=0.1, check_interval=1 << 16, sampler_dram_bytes=None, k=10),
 }
 WORKLOAD = WORKLOADS["chung_lu_1m"]
 L2_FLUSH_BYTES = 512 << 20
@@ -70,6 +73,8 @@ def make_graph():
 def workload_name():
     w = WORKLOAD
     tail = f"lambda={w['lam']} delta={w['delta']} K={w['check_interval']}"
+    if w.get("k"):
+        tail = f"top-k k={w['k']}; " + tail
     if w["family"] == "chung_lu":
         return (f"chung_lu n={w['n']} beta={w['beta']} mean_deg={w['mean_deg']:g} max_deg={w['max_deg']:g} "
                 f"lcc; {tail}")
@@ -164,6 +169,20 @@ def algorithmic_bytes(totals, hits):
     backtracking."""
     t = totals
     return (8 * t[1] + 8 * t[0] + 12 * t[2] + 8 * t[3] + 4 * hits + 4 * t[6])
+
+
+def run_launches(r, w):
+    """Kernels one run launches.  All-nodes mode: the warm-up batch, the
+    warm-up count compaction (3), the main-loop batches, one stop test per
+    check, the final test and b~.  Top-k mode: the preliminary + warm-up
+    batch, the preliminary selection (2), the compaction (3), the fill and
+    scatter of ln(1/delta) (2), the main-loop batches, three kernels per
+    Alg. 3 test (checks + the final one) and b~."""
+    rounds = -(-int(r.tau) // w["check_interval"])
+    sb = sampler_launches_per_batch() * (1 + rounds)
+    if w.get("k"):
+        return sb + 2 + 3 + 2 + 3 * (int(r.checks) + 1) + 1
+    return sb + 3 + int(r.checks) + 1 + 1
 
 
 def sampler_launches_per_batch():
@@ -372,7 +391,8 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def step(seed):
-        return kd.kadabra_run(G, w["lam"], w["delta"], 0, seed, check_interval=w["check_interval"], stream=sp,
+        return kd.kadabra_run(G, w["lam"], w["delta"], w.get("k", 0), seed, check_interval=w["check_interval"],
+                              stream=sp,
                               d_counts=d_counts, d_btilde=d_btilde, want_host=False)
 
     # the clock sampler starts before the warm-up steps, so that its own
@@ -396,10 +416,7 @@ def main():
         ev1.synchronize()
         times.append(ev0.elapsed_time(ev1) / 1e3)
         paths += r.alpha + r.tau
-        # warm-up batch, warm-up count compaction (3), main-loop batches,
-        # stop tests, the final test and b~
-        rounds = -(-int(r.tau) // w["check_interval"])
-        launches += sampler_launches_per_batch() * (1 + rounds) + 3 + int(r.checks) + 1 + 1
+        launches += run_launches(r, w)
         results.append(r)
     torch.cuda.synchronize()
     barrier()
@@ -450,7 +467,7 @@ def main():
     t0 = time.perf_counter()
     for i in range(e2e_steps):
         Gh = kd.kadabra_load_csr(g)
-        r = kd.kadabra_run(Gh, w["lam"], w["delta"], 0, 500 + i, check_interval=K, counts=counts_h,
+        r = kd.kadabra_run(Gh, w["lam"], w["delta"], w.get("k", 0), 500 + i, check_interval=K, counts=counts_h,
                            btilde=btilde_h)
         Gh.free()
         e2e_paths += r.alpha + r.tau
@@ -472,6 +489,7 @@ def main():
                 "parallelism": "replicas" if world > 1 else "single",
                 "time_to_lambda_delta_ms": [round(1e3 * t, 3) for t in times],
                 "tau": [int(r.tau) for r in results], "alpha": int(r0.alpha), "omega": r0.omega,
+                **({"k": w["k"], "topk_first_step": [int(x) for x in r0.topk]} if w.get("k") else {}),
                 "checks": [int(r.checks) for r in results],
                 "edges_per_sample": float(tot_np[0]) / K,
             }),

@@ -108,7 +108,7 @@ typedef struct {
   double* btilde;      /* host, n: b~(v) = counts / tau                           */
   uint32_t* d_counts;  /* device, n                                               */
   double* d_btilde;    /* device, n                                               */
-  int32_t* topk;       /* host, k: reserved for top-k mode (k > 0)                */
+  int32_t* topk;       /* host, k: top-k mode's ranking (k > 0; may be NULL)      */
 } kadabra_result;
 
 /* Copies a host CSR to the device and prepares the graph (Sec. 2 graph
@@ -178,11 +178,16 @@ kadabra_status kadabra_graph_info(const kadabra_graph* g, int32_t* n, int64_t* m
 enum { KADABRA_FLAG_GLOBAL_TABLES = 1, KADABRA_FLAG_MEDIUM_TABLES = 2, KADABRA_FLAG_LARGE_SHARED_TABLES = 4 };
 kadabra_status kadabra_graph_set_flags(kadabra_graph* g, uint32_t flags);
 
-/* KADABRA, all-nodes mode (Alg. 1 with Alg. 2 and the rule f,g <= lambda
- * for every node): warm-up, computeDelta, then sample batches of K with a
- * stop test after each, until the test holds or ceil(omega) samples.
- * lambda in (0,1), delta in (0,1).  k must be 0 (top-k mode, Alg. 3, is
- * KADABRA_ERR_UNSUPPORTED).  cfg may be NULL.  Blocking. */
+/* KADABRA (Alg. 1): warm-up, computeDelta (Alg. 2), then sample batches
+ * of K with a stop test after each, until the test holds or ceil(omega)
+ * samples.  lambda in (0,1), delta in (0,1); cfg may be NULL.  Blocking.
+ *   k = 0: all-nodes mode, the rule f,g <= lambda for every node (Sec. 2).
+ *   1 <= k <= 256: the k most central nodes (Sec. 5): a preliminary
+ *     estimate of alpha samples (RNG domain 2) sets per-node targets
+ *     lambda_L(v), lambda_U(v); Alg. 2 runs with those targets; the stop
+ *     test is Alg. 3.  Nodes are ranked by b~ decreasing, ties by id;
+ *     out->topk (caller-owned, k entries) receives the min(k, n) first
+ *     nodes of the final ranking.  Other k: KADABRA_ERR_ARG. */
 kadabra_status kadabra_run(kadabra_graph* g, double lambda, double delta, int32_t k, uint64_t seed,
                            const kadabra_config* cfg, kadabra_result* out);
 

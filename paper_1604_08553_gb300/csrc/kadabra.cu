@@ -1444,6 +1444,9 @@ struct NzJob {
   uint32_t* out;     // non-zero values, node order
   unsigned* blk;     // per-block counts, then exclusive offsets (gridDim.x entries)
   unsigned* total;
+  uint32_t* out_idx; // optional: their node ids
+  const uint32_t* aux;  // optional: a second per-node array ...
+  uint32_t* out_aux;    // ... gathered at the same nodes
 };
 
 __global__ void __launch_bounds__(256) k_nz_count(const NzJob* __restrict__ jobs) {
@@ -1496,9 +1499,254 @@ __global__ void __launch_bounds__(256) k_nz_scatter(const NzJob* __restrict__ jo
       if (i < w) before += tmp[i];
       tot += tmp[i];
     }
-    if (x != 0) J.out[base + before + __popc(m & ((1u << lane) - 1u))] = x;
+    if (x != 0) {
+      const unsigned at = base + before + __popc(m & ((1u << lane) - 1u));
+      J.out[at] = x;
+      if (J.out_idx) J.out_idx[at] = (uint32_t)v;
+      if (J.aux) J.out_aux[at] = J.aux[v];
+    }
     base += tot;
     __syncthreads();
+  }
+}
+
+// ============================================================== top-k stop test (Alg. 3)
+// Nodes are ranked by b~ decreasing, ties by id increasing; with one tau for
+// all nodes that is the order of the 64-bit key (count << 32 | ~id), whose
+// values are distinct.  A check selects the k+1 largest keys in two stages
+// (per-block, then one block over the blocks' survivors), evaluates Alg. 3 on
+// them, then tests every other node against the k-th node's lower end.
+constexpr int TOPK_MAX = 256;   // largest k of top-k mode
+constexpr int TK_SORT = 2048;   // keys one block sorts at a time (power of two)
+constexpr int TK_BLOCKS = 304;  // first-stage selection blocks
+
+__device__ __forceinline__ unsigned long long rank_key(uint32_t count, int64_t v) {
+  return ((unsigned long long)count << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)v);
+}
+__device__ __forceinline__ uint32_t key_node(unsigned long long key) { return 0xFFFFFFFFu - (uint32_t)key; }
+__device__ __forceinline__ uint32_t key_count(unsigned long long key) { return (uint32_t)(key >> 32); }
+
+// Block-wide selection of the k1 largest keys.  buf[0, *nb) holds the best so
+// far (sorted, descending) followed by pending candidates; keys at or below
+// *thr (the k1-th best once k1 are known, else 0) are dropped on arrival.
+struct TopSel {
+  unsigned long long* buf;  // TK_SORT keys
+  int* nb;
+  unsigned long long* thr;
+  int k1;
+};
+
+// sorts buf descending (zero padding beyond *nb), keeps k1, updates thr
+__device__ void topsel_compact(const TopSel& S) {
+  const int n0 = *S.nb;
+  for (int i = n0 + threadIdx.x; i < TK_SORT; i += blockDim.x) S.buf[i] = 0ull;
+  __syncthreads();
+  for (int size = 2; size <= TK_SORT; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < TK_SORT / 2; i += blockDim.x) {
+        const int lo = 2 * i - (i & (stride - 1));
+        const int hi = lo + stride;
+        const bool desc = (lo & size) == 0;
+        const unsigned long long a = S.buf[lo], b = S.buf[hi];
+        if ((a < b) == desc) {
+          S.buf[lo] = b;
+          S.buf[hi] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x == 0) {
+    int keep = n0 < S.k1 ? n0 : S.k1;
+    while (keep > 0 && S.buf[keep - 1] == 0ull) --keep;  // padding is not a key
+    *S.nb = keep;
+    *S.thr = keep == S.k1 ? S.buf[S.k1 - 1] : 0ull;
+  }
+  __syncthreads();
+}
+
+// offers one key per thread (0 = none); all threads of the block call it
+__device__ void topsel_offer(const TopSel& S, unsigned long long key) {
+  const bool pass = key > *S.thr;
+  const unsigned m = __ballot_sync(FULL, pass);
+  int base = 0;
+  if ((threadIdx.x & 31) == 0 && m) base = atomicAdd(S.nb, __popc(m));
+  base = __shfl_sync(FULL, base, 0);
+  if (pass) S.buf[base + __popc(m & ((1u << (threadIdx.x & 31)) - 1u))] = key;
+  __syncthreads();
+  const int cur = *S.nb;
+  __syncthreads();  // every thread has read nb before the next offer adds to it
+  if (cur > TK_SORT - (int)blockDim.x) topsel_compact(S);
+}
+
+// stage 1: the k1 largest keys of a contiguous chunk of nodes per block
+__global__ void __launch_bounds__(256) k_topk_block(const uint32_t* __restrict__ counts, int64_t n, int k1,
+                                                    unsigned long long* __restrict__ out) {
+  __shared__ unsigned long long buf[TK_SORT];
+  __shared__ int nb;
+  __shared__ unsigned long long thr;
+  if (threadIdx.x == 0) {
+    nb = 0;
+    thr = 0ull;
+  }
+  __syncthreads();
+  const TopSel S{buf, &nb, &thr, k1};
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t a = min(n, (int64_t)blockIdx.x * chunk), b = min(n, a + chunk);
+  for (int64_t t0 = a; t0 < b; t0 += blockDim.x) {
+    const int64_t v = t0 + threadIdx.x;
+    topsel_offer(S, v < b ? rank_key(counts[v], v) : 0ull);
+  }
+  topsel_compact(S);
+  for (int i = threadIdx.x; i < k1; i += blockDim.x) out[(size_t)blockIdx.x * k1 + i] = i < nb ? buf[i] : 0ull;
+}
+
+struct TopkOut {
+  unsigned long long keys[TOPK_MAX + 1];  // the k1 first nodes of the ranking
+  int nk;                                 // how many (min(k + 1, n))
+  unsigned fail;                          // Alg. 3 returns false
+  unsigned long long max_f_bits, max_g_bits;
+  double lower_k;                         // b~(v_k) - f(v_k)
+  unsigned long long key_k;               // key of v_k
+};
+
+struct TopkJob {
+  const uint32_t* counts;
+  const double* lnL;
+  const double* lnU;
+  int64_t n;
+  uint64_t tau;
+  double omega;
+  double lambda;
+  int k;                                  // min(k, n)
+  int k1;                                 // min(k + 1, n)
+  const unsigned long long* cand;         // TK_BLOCKS * k1 keys of stage 1
+  int select_only;                        // 1: only the selection (keys, nk)
+  TopkOut* out;
+};
+
+// stage 2 (one block): the k1 first nodes, then Alg. 3's test of the k first
+__global__ void __launch_bounds__(256) k_topk_final(const TopkJob* __restrict__ jp) {
+  __shared__ unsigned long long buf[TK_SORT];
+  __shared__ int nb;
+  __shared__ unsigned long long thr;
+  __shared__ double sb[TOPK_MAX + 1], sf[TOPK_MAX + 1], sg[TOPK_MAX + 1];
+  const TopkJob J = *jp;
+  if (threadIdx.x == 0) {
+    nb = 0;
+    thr = 0ull;
+  }
+  __syncthreads();
+  const TopSel S{buf, &nb, &thr, J.k1};
+  const int total = TK_BLOCKS * J.k1;
+  for (int t0 = 0; t0 < total; t0 += blockDim.x) {
+    const int i = t0 + threadIdx.x;
+    topsel_offer(S, i < total ? J.cand[i] : 0ull);
+  }
+  topsel_compact(S);
+  const int nk = nb;
+  for (int i = threadIdx.x; i < nk; i += blockDim.x) J.out->keys[i] = buf[i];
+  if (threadIdx.x == 0) J.out->nk = nk;
+  if (J.select_only) return;
+  // f, g and b~ of the k1 first nodes
+  const double t = (double)J.tau;
+  for (int i = threadIdx.x; i < nk; i += blockDim.x) {
+    const uint32_t v = key_node(buf[i]), cnt = key_count(buf[i]);
+    double f, g;
+    f_and_g(cnt, t, J.omega, J.lnL[v], J.lnU[v], &f, &g);
+    sb[i] = (double)cnt / t;
+    sf[i] = f;
+    sg[i] = g;
+  }
+  __syncthreads();
+  // the k first nodes (Alg. 3 first loop); v_0 - f = +inf, v_{n+1} + g = -inf
+  for (int i = threadIdx.x; i < J.k && i < nk; i += blockDim.x) {
+    const bool loose = sf[i] > J.lambda || sg[i] > J.lambda;
+    bool bad = false;
+    if (loose) {
+      if (i > 0 && sb[i - 1] - sf[i - 1] < sb[i] + sg[i]) bad = true;
+      if (i + 1 < nk && sb[i] - sf[i] < sb[i + 1] + sg[i + 1]) bad = true;
+    }
+    if (bad) atomicOr(&J.out->fail, 1u);
+    atomicMax(&J.out->max_f_bits, (unsigned long long)__double_as_longlong(sf[i]));
+    atomicMax(&J.out->max_g_bits, (unsigned long long)__double_as_longlong(sg[i]));
+  }
+  if (threadIdx.x == 0 && J.k >= 1 && J.k <= nk) {
+    J.out->lower_k = sb[J.k - 1] - sf[J.k - 1];
+    J.out->key_k = buf[J.k - 1];
+  }
+}
+
+// the other nodes (Alg. 3 second loop): a node below v_k whose f or g exceeds
+// lambda must lie below b~(v_k) - f(v_k).  Unhit nodes have f = 0 and g
+// increasing in ln(1/delta_U), so each block evaluates g once for them, at
+// the largest ln(1/delta_U) among its unhit nodes.
+__global__ void __launch_bounds__(256) k_topk_rest(const TopkJob* __restrict__ jp) {
+  __shared__ unsigned long long s_u[8];
+  const TopkJob J = *jp;
+  const double t = (double)J.tau;
+  const double lower_k = J.out->lower_k;
+  const unsigned long long key_k = J.out->key_k;
+  unsigned long long mf = 0, mg = 0, mu = 0;
+  unsigned fail = 0;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < J.n; v += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t cnt = J.counts[v];
+    if (rank_key(cnt, v) >= key_k) continue;  // one of the k first nodes
+    if (cnt == 0) {
+      const unsigned long long ub = (unsigned long long)__double_as_longlong(J.lnU[v]);
+      mu = ub > mu ? ub : mu;
+      continue;
+    }
+    double f, g;
+    f_and_g(cnt, t, J.omega, J.lnL[v], J.lnU[v], &f, &g);
+    const double b = (double)cnt / t;
+    if ((f > J.lambda || g > J.lambda) && lower_k < b + g) fail = 1;
+    const unsigned long long fb = (unsigned long long)__double_as_longlong(f);
+    const unsigned long long gb = (unsigned long long)__double_as_longlong(g);
+    mf = fb > mf ? fb : mf;
+    mg = gb > mg ? gb : mg;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long a = __shfl_xor_sync(FULL, mf, o);
+    const unsigned long long b = __shfl_xor_sync(FULL, mg, o);
+    const unsigned long long u = __shfl_xor_sync(FULL, mu, o);
+    mf = a > mf ? a : mf;
+    mg = b > mg ? b : mg;
+    mu = u > mu ? u : mu;
+    fail |= __shfl_xor_sync(FULL, fail, o);
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) s_u[w] = mu;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long u = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) u = s_u[i] > u ? s_u[i] : u;
+    if (u) {
+      const double L = __longlong_as_double((long long)u);
+      double f0, g0;
+      f_and_g(0u, t, J.omega, L, L, &f0, &g0);
+      atomicMax(&J.out->max_g_bits, (unsigned long long)__double_as_longlong(g0));
+      if ((f0 > J.lambda || g0 > J.lambda) && lower_k < 0.0 + g0) atomicOr(&J.out->fail, 1u);
+    }
+  }
+  if (lane == 0) {
+    if (mf) atomicMax(&J.out->max_f_bits, mf);
+    if (mg) atomicMax(&J.out->max_g_bits, mg);
+    if (fail) atomicOr(&J.out->fail, 1u);
+  }
+}
+
+__global__ void k_fill2(double* __restrict__ a, double* __restrict__ b, int64_t n, double x) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    a[v] = b[v] = x;
+}
+
+__global__ void k_scatter2(double* __restrict__ a, double* __restrict__ b, const uint32_t* __restrict__ idx,
+                           const double* __restrict__ va, const double* __restrict__ vb, int64_t m) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    a[idx[i]] = va[i];
+    b[idx[i]] = vb[i];
   }
 }
 
@@ -1701,6 +1949,13 @@ struct kadabra_graph {
   long long* totals = nullptr;
   double* lntab = nullptr;  // computeDelta table, ln(1/delta) by warm-up count
   uint64_t lntab_cap = 0;
+  // top-k mode (allocated on first use)
+  uint32_t* count_pre = nullptr;     // preliminary-estimate hits (Sec. 5)
+  double *lnLv = nullptr, *lnUv = nullptr;  // per-node ln(1/delta_L), ln(1/delta_U)
+  unsigned long long* tk_cand = nullptr;    // first-stage selection survivors
+  void* tk_dev = nullptr;            // TopkJob + TopkOut
+  void* tk_stage = nullptr;          // scatter staging: ids, lnL, lnU values
+  size_t tk_stage_cap = 0;           // entries
   std::vector<void*> allocs;  // CSR copies and run buffers
 };
 
@@ -2358,6 +2613,327 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
   return KADABRA_OK;
 }
 
+
+// ---------------------------------------------------------------- top-k runner
+// Sec. 5 targets from the preliminary estimate, in the order the text gives
+// them (the k first nodes, the others, then small gaps; every target below
+// lambda raised to lambda).  top: the k1 first nodes' counts in ranking order.
+struct TopkTargets {
+  std::vector<double> L, U;  // for the k1 first nodes, in ranking order
+  double lower_base;         // b~(v_k) - lambda_L(v_k) before the small-gap rule
+  double a;                  // preliminary sample count
+  double lambda;
+  double others_U(uint32_t cnt) const {  // lambda_U of a node ranked below v_{k+1}
+    const double u = lower_base - (double)cnt / a;
+    return u >= lambda ? u : lambda;
+  }
+};
+
+TopkTargets topk_targets(const std::vector<uint32_t>& top, int64_t n, int k, uint64_t alpha, double lambda) {
+  TopkTargets T;
+  const int k1 = (int)top.size();
+  T.a = (double)alpha;
+  T.lambda = lambda;
+  T.L.assign(k1, 0.0);
+  T.U.assign(k1, 0.0);
+  auto bt = [&](int i) { return (double)top[i - 1] / T.a; };  // 1-based
+  for (int i = 1; i <= k; ++i) {
+    T.U[i - 1] = i == 1 ? 1.0 : (bt(i - 1) - bt(i)) / 2.0;
+    T.L[i - 1] = i == n ? 1.0 : (bt(i) - bt(i + 1)) / 2.0;
+  }
+  T.lower_base = bt(k) - T.L[k - 1];
+  for (int i = k + 1; i <= k1; ++i) {
+    T.L[i - 1] = 1.0;
+    T.U[i - 1] = bt(k) - T.L[k - 1] - bt(i);
+  }
+  for (int i = 1; i <= k && i + 1 <= n; ++i) {
+    if (bt(i) - bt(i + 1) < 2.0 * lambda) T.L[i - 1] = T.U[i - 1] = T.L[i] = T.U[i] = lambda;
+  }
+  for (int i = 0; i < k1; ++i) {
+    if (!(T.L[i] >= lambda)) T.L[i] = lambda;
+    if (!(T.U[i] >= lambda)) T.U[i] = lambda;
+  }
+  return T;
+}
+
+// Alg. 2 with per-node targets over the nodes with a warm-up hit (node order);
+// writes their ln(1/delta_L), ln(1/delta_U) and C; *l0 = the value of every
+// node without a hit.
+kadabra_status compute_delta_lv_host(int64_t n, const std::vector<double>& cL, const std::vector<double>& cU,
+                                     double delta, double eps, std::vector<double>& lnL, std::vector<double>& lnU,
+                                     double* C_out, double* l0) {
+  const size_t m = cL.size();
+  const double target = (delta / 2.0) - (eps * delta);
+  auto sum_at = [&](double C) {
+    double sum = 0.0;
+    for (size_t i = 0; i < m; ++i) {
+      const double eL = cL[i] > 0.0 ? std::exp(-C / cL[i]) : 0.0;
+      const double eU = cU[i] > 0.0 ? std::exp(-C / cU[i]) : 0.0;
+      sum += eL + eU;
+    }
+    return sum;
+  };
+  bool any = false;
+  for (size_t i = 0; i < m; ++i) any = any || cL[i] > 0.0 || cU[i] > 0.0;
+  double C = 0.0;
+  if (any) {
+    double lo = 0.0, hi = 1.0;
+    int guard = 0;
+    while (!(sum_at(hi) <= target)) {
+      lo = hi;
+      hi = 2.0 * hi;
+      if (++guard > 2100) return fail(KADABRA_ERR_INTERNAL, "computeDelta: no bracket for C");
+    }
+    for (guard = 0; guard < 4000; ++guard) {
+      const double mid = 0.5 * (lo + hi);
+      if (mid <= lo || mid >= hi) break;
+      if (sum_at(mid) <= target)
+        hi = mid;
+      else
+        lo = mid;
+    }
+    C = hi;
+  }
+  const double floor_term = (eps * delta) / (2.0 * (double)n);
+  lnL.resize(m);
+  lnU.resize(m);
+  for (size_t i = 0; i < m; ++i) {
+    lnL[i] = -std::log((cL[i] > 0.0 ? std::exp(-C / cL[i]) : 0.0) + floor_term);
+    lnU[i] = -std::log((cU[i] > 0.0 ? std::exp(-C / cU[i]) : 0.0) + floor_term);
+  }
+  *l0 = -std::log(0.0 + floor_term);
+  *C_out = C;
+  return KADABRA_OK;
+}
+
+kadabra_status ensure_topk_buffers(kadabra_graph* g, cudaStream_t st) {
+  if (g->count_pre) return KADABRA_OK;
+  KCK(cudaStreamSynchronize(st));
+  void* p;
+  KTRY(dev_alloc(g->allocs, &p, sizeof(uint32_t) * (size_t)g->n));
+  g->count_pre = (uint32_t*)p;
+  KTRY(dev_alloc(g->allocs, &p, sizeof(double) * (size_t)g->n));
+  g->lnLv = (double*)p;
+  KTRY(dev_alloc(g->allocs, &p, sizeof(double) * (size_t)g->n));
+  g->lnUv = (double*)p;
+  KTRY(dev_alloc(g->allocs, &p, sizeof(unsigned long long) * (size_t)TK_BLOCKS * (TOPK_MAX + 1)));
+  g->tk_cand = (unsigned long long*)p;
+  KTRY(dev_alloc(g->allocs, &p, sizeof(TopkJob) + sizeof(TopkOut)));
+  g->tk_dev = p;
+  return KADABRA_OK;
+}
+
+// Alg. 1 in top-k mode on one graph: preliminary estimate (domain 2) and
+// warm-up (domain 1) in one sampler launch, Sec. 5 targets, Alg. 2 with
+// those targets, then batches of K samples with Alg. 3 after each.
+kadabra_status run_topk(kadabra_graph* g, double lambda, double delta, int32_t k_in, uint64_t seed,
+                        const kadabra_config& cfg, kadabra_result* out) {
+  cudaStream_t st = as_stream(cfg.stream);
+  Workspace* w = g->ws;
+  const int64_t n = g->n;
+  const int k = (int)std::min<int64_t>(k_in, n), k1 = (int)std::min<int64_t>((int64_t)k_in + 1, n);
+  kadabra_result& r = *out;
+  r.vd = cfg.vd > 0 ? cfg.vd : g->vd;
+  r.omega = omega_host(lambda, delta, r.vd);
+  const double cap_d = std::ceil(r.omega);
+  if (!(cap_d >= 1.0 && cap_d < 1e15)) return fail(KADABRA_ERR_ARG, "omega out of range");
+  const uint64_t cap = r.omega_cap = (uint64_t)cap_d;
+  const uint64_t alpha = r.alpha = std::max<uint64_t>(1, (uint64_t)std::floor(r.omega / 100.0));
+  const uint64_t K = r.check_interval = cfg.check_interval ? cfg.check_interval : auto_check_interval(r.omega);
+  KTRY(ensure_ws(w, std::max(2 * alpha, std::min(K, cap)), 2));
+  KTRY(ensure_run_buffers(g));
+  KTRY(ensure_topk_buffers(g, st));
+  if (w->nz_cap < 1) {
+    KCK(cudaDeviceSynchronize());
+    void* p;
+    KTRY(dev_alloc(w->allocs, &p, sizeof(NzJob) + sizeof(unsigned) * (NZ_BLK + 1)));
+    w->d_nz = p;
+    w->nz_cap = 1;
+  }
+#define RCK(call)                                                                         \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) return fail(KADABRA_ERR_CUDA, cudaGetErrorString(e_));         \
+  } while (0)
+  TopkJob* d_job = static_cast<TopkJob*>(g->tk_dev);
+  TopkOut* d_out = reinterpret_cast<TopkOut*>(d_job + 1);
+  RCK(cudaMemsetAsync(g->totals, 0, sizeof(long long) * KADABRA_NSTAT, st));
+  RCK(cudaMemsetAsync(g->count_pre, 0, sizeof(uint32_t) * n, st));
+  RCK(cudaMemsetAsync(g->count0, 0, sizeof(uint32_t) * n, st));
+  RCK(cudaMemsetAsync(g->counts, 0, sizeof(uint32_t) * n, st));
+  auto job = [&](uint32_t domain, uint64_t first, uint64_t count, uint32_t* counts) {
+    Job j;
+    std::memset(&j, 0, sizeof(j));
+    j.g = graph_dev(g);
+    j.seed = seed;
+    j.domain = domain;
+    j.first_idx = first;
+    j.count = count;
+    j.counts = counts;
+    j.totals = g->totals;
+    return j;
+  };
+  // preliminary estimate and warm-up, one launch
+  {
+    Job jobs[2] = {job(2, 0, alpha, g->count_pre), job(1, 0, alpha, g->count0)};
+    jobs[0].work_begin = 0;
+    jobs[1].work_begin = alpha;
+    RCK(cudaMemcpyAsync(w->d_jobs, jobs, sizeof(jobs), cudaMemcpyHostToDevice, st));
+    SampleParams P = ws_params(w, g->flags);
+    P.total_work = 2 * alpha;
+    P.jobs = w->d_jobs;
+    P.njobs = 2;
+    KTRY(launch_sampler(w, P, st));
+  }
+  const int rest_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(4 * (int64_t)w->num_sms, (n + 255) / 256));
+  // selection (select_only) or Alg. 3 over `counts` at `tau`
+  TopkOut ho;
+  auto topk_pass = [&](const uint32_t* counts, uint64_t tau, int select_only) -> kadabra_status {
+    TopkJob J;
+    std::memset(&J, 0, sizeof(J));
+    J.counts = counts;
+    J.lnL = g->lnLv;
+    J.lnU = g->lnUv;
+    J.n = n;
+    J.tau = tau;
+    J.omega = r.omega;
+    J.lambda = lambda;
+    J.k = k;
+    J.k1 = k1;
+    J.cand = g->tk_cand;
+    J.select_only = select_only;
+    J.out = d_out;
+    RCK(cudaMemcpyAsync(d_job, &J, sizeof(J), cudaMemcpyHostToDevice, st));
+    RCK(cudaMemsetAsync(d_out, 0, sizeof(TopkOut), st));
+    k_topk_block<<<TK_BLOCKS, 256, 0, st>>>(counts, n, k1, g->tk_cand);
+    k_topk_final<<<1, 256, 0, st>>>(d_job);
+    if (!select_only) k_topk_rest<<<rest_blocks, 256, 0, st>>>(d_job);
+    RCK(cudaGetLastError());
+    RCK(cudaMemcpyAsync(&ho, d_out, sizeof(TopkOut), cudaMemcpyDeviceToHost, st));
+    return read_status(w, st);
+  };
+  // the k1 first nodes of the preliminary estimate
+  KTRY(topk_pass(g->count_pre, 1, 1));
+  if (ho.nk != k1) return fail(KADABRA_ERR_INTERNAL, "top-k selection returned too few nodes");
+  std::vector<uint32_t> top_cnt(k1), top_id(k1);
+  for (int i = 0; i < k1; ++i) {
+    top_cnt[i] = (uint32_t)(ho.keys[i] >> 32);
+    top_id[i] = 0xFFFFFFFFu - (uint32_t)ho.keys[i];
+  }
+  const TopkTargets TT = topk_targets(top_cnt, n, k, alpha, lambda);
+  std::unordered_map<uint32_t, int> rank_of;
+  for (int i = 0; i < k1; ++i) rank_of[top_id[i]] = i;
+  // nodes with a warm-up hit, in node order, with their preliminary hits
+  NzJob* d_nzj = static_cast<NzJob*>(w->d_nz);
+  unsigned* d_blk = reinterpret_cast<unsigned*>(d_nzj + 1);
+  unsigned* d_nzt = d_blk + NZ_BLK;
+  {
+    NzJob z;
+    std::memset(&z, 0, sizeof(z));
+    z.count0 = g->count0;
+    z.n = n;
+    z.out = reinterpret_cast<uint32_t*>(g->btilde);  // scratch
+    z.blk = d_blk;
+    z.total = d_nzt;
+    z.out_idx = reinterpret_cast<uint32_t*>(g->lnLv);  // scratch (filled below)
+    z.aux = g->count_pre;
+    z.out_aux = reinterpret_cast<uint32_t*>(g->lnUv);  // scratch
+    RCK(cudaMemcpyAsync(d_nzj, &z, sizeof(z), cudaMemcpyHostToDevice, st));
+    k_nz_count<<<dim3(NZ_BLK, 1), 256, 0, st>>>(d_nzj);
+    k_nz_offsets<<<1, 32, 0, st>>>(d_nzj, NZ_BLK);
+    k_nz_scatter<<<dim3(NZ_BLK, 1), 256, 0, st>>>(d_nzj);
+    RCK(cudaGetLastError());
+  }
+  unsigned nnz = 0;
+  RCK(cudaMemcpyAsync(&nnz, d_nzt, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  RCK(cudaStreamSynchronize(st));
+  std::vector<uint32_t> nz_c0(nnz), nz_id(nnz), nz_pre(nnz);
+  if (nnz) {
+    RCK(cudaMemcpyAsync(nz_c0.data(), g->btilde, sizeof(uint32_t) * nnz, cudaMemcpyDeviceToHost, st));
+    RCK(cudaMemcpyAsync(nz_id.data(), g->lnLv, sizeof(uint32_t) * nnz, cudaMemcpyDeviceToHost, st));
+    RCK(cudaMemcpyAsync(nz_pre.data(), g->lnUv, sizeof(uint32_t) * nnz, cudaMemcpyDeviceToHost, st));
+  }
+  RCK(cudaStreamSynchronize(st));
+  // c_L, c_U of those nodes (Alg. 2) with their Sec. 5 targets
+  std::vector<double> cL(nnz), cU(nnz), vL, vU;
+  for (unsigned i = 0; i < nnz; ++i) {
+    double lamL = 1.0, lamU;
+    auto it = rank_of.find(nz_id[i]);
+    if (it != rank_of.end()) {
+      lamL = TT.L[it->second];
+      lamU = TT.U[it->second];
+    } else {
+      lamU = TT.others_U(nz_pre[i]);
+    }
+    const double b0 = (double)nz_c0[i] / (double)alpha;
+    cL[i] = ((2.0 * b0) * r.omega) / (lamL * lamL);
+    cU[i] = ((2.0 * b0) * r.omega) / (lamU * lamU);
+  }
+  double l0 = 0.0;
+  KTRY(compute_delta_lv_host(n, cL, cU, delta, cfg.eps, vL, vU, &r.C, &l0));
+  // per-node ln(1/delta) arrays: l0 everywhere, then the hit nodes' values
+  if (g->tk_stage_cap < nnz) {
+    KCK(cudaStreamSynchronize(st));
+    dev_free(g->allocs, g->tk_stage);
+    void* p;
+    KTRY(dev_alloc(g->allocs, &p, (sizeof(uint32_t) + 2 * sizeof(double)) * (size_t)nnz));
+    g->tk_stage = p;
+    g->tk_stage_cap = nnz;
+  }
+  k_fill2<<<rest_blocks, 256, 0, st>>>(g->lnLv, g->lnUv, n, l0);
+  RCK(cudaGetLastError());
+  if (nnz) {
+    double* sL = static_cast<double*>(g->tk_stage);
+    double* sU = sL + nnz;
+    uint32_t* sI = reinterpret_cast<uint32_t*>(sU + nnz);
+    RCK(cudaMemcpyAsync(sI, nz_id.data(), sizeof(uint32_t) * nnz, cudaMemcpyHostToDevice, st));
+    RCK(cudaMemcpyAsync(sL, vL.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, st));
+    RCK(cudaMemcpyAsync(sU, vU.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, st));
+    k_scatter2<<<rest_blocks, 256, 0, st>>>(g->lnLv, g->lnUv, sI, sL, sU, nnz);
+    RCK(cudaGetLastError());
+    RCK(cudaStreamSynchronize(st));  // host vectors stay alive until the copies are done
+  }
+  // main loop (Alg. 1) with Alg. 3 every K samples
+  uint64_t tau = 0;
+  for (;;) {
+    const uint64_t B = std::min<uint64_t>(K, cap - tau);
+    SampleParams P = ws_params(w, g->flags);
+    P.total_work = B;
+    P.job0 = job(0, tau, B, g->counts);
+    KTRY(launch_sampler(w, P, st));
+    tau += B;
+    if (tau >= cap) break;
+    r.checks++;
+    KTRY(topk_pass(g->counts, tau, 0));
+    if (!ho.fail) {
+      r.stopped_early = 1;
+      break;
+    }
+  }
+  r.tau = tau;
+  KTRY(topk_pass(g->counts, tau, 0));
+  std::memcpy(&r.max_f, &ho.max_f_bits, sizeof(double));
+  std::memcpy(&r.max_g, &ho.max_g_bits, sizeof(double));
+  if (r.topk)
+    for (int i = 0; i < k; ++i) r.topk[i] = (int32_t)(0xFFFFFFFFu - (uint32_t)ho.keys[i]);
+  const int blocks = rest_blocks;
+  if (r.btilde || r.d_btilde) {
+    k_btilde<<<blocks, 256, 0, st>>>(g->counts, n, tau, r.d_btilde ? r.d_btilde : g->btilde);
+    RCK(cudaGetLastError());
+  }
+  if (r.d_counts) RCK(cudaMemcpyAsync(r.d_counts, g->counts, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st));
+  if (r.counts) RCK(cudaMemcpyAsync(r.counts, g->counts, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, st));
+  if (r.btilde)
+    RCK(cudaMemcpyAsync(r.btilde, r.d_btilde ? r.d_btilde : g->btilde, sizeof(double) * n, cudaMemcpyDeviceToHost,
+                        st));
+  long long tot[KADABRA_NSTAT];
+  RCK(cudaMemcpyAsync(tot, g->totals, sizeof(tot), cudaMemcpyDeviceToHost, st));
+  KTRY(read_status(w, st));
+  for (int q = 0; q < KADABRA_NSTAT; ++q) r.totals[q] = tot[q];
+#undef RCK
+  return KADABRA_OK;
+}
+
 // keeps the caller's buffer pointers, zeroes the rest of a result
 void reset_result(kadabra_result* r) {
   uint32_t* ch = r->counts;
@@ -2777,9 +3353,10 @@ kadabra_status kadabra_run(kadabra_graph* g, double lambda, double delta, int32_
     out->status = s;
     return s;
   };
-  if (k != 0) return finish(fail(KADABRA_ERR_UNSUPPORTED, "top-k mode (k > 0) is not implemented"));
+  if (k < 0 || k > TOPK_MAX) return finish(fail(KADABRA_ERR_ARG, "k must be in [0, 256]"));
   if (!(lambda > 0.0 && lambda < 1.0) || !(delta > 0.0 && delta < 1.0) || !(cfg.eps >= 0.0 && cfg.eps < 0.5))
     return finish(fail(KADABRA_ERR_ARG, "lambda and delta must be in (0,1), eps in [0,0.5)"));
+  if (k > 0) return finish(run_topk(g, lambda, delta, k, seed, cfg, out));
   const int64_t vd = cfg.vd;
   return finish(run_graphs(g->ws, &g, 1, &lambda, &delta, &seed, &vd, cfg, out));
 }

@@ -213,14 +213,17 @@ class RunResult:
     stopped_early: bool
     counts: Optional[np.ndarray]
     btilde: Optional[np.ndarray]
+    topk: Optional[np.ndarray] = None
 
 
 def kadabra_run(g: Graph, lam: float, delta: float, k: int = 0, seed: int = 0, *, vd: int = 0,
                 eps: float = 0.001, check_interval: int = 1000, stream: Optional[int] = None,
                 counts: Optional[np.ndarray] = None, btilde: Optional[np.ndarray] = None,
                 d_counts=None, d_btilde=None, want_host: bool = True) -> RunResult:
-    """Runs KADABRA (all-nodes mode).  Host outputs are numpy arrays (allocated
-    here unless given); device outputs are optional CUDA tensors."""
+    """Runs KADABRA: all-nodes mode (k = 0), or the k most central nodes
+    (k > 0; the ranking's k first nodes come back in `topk`).  Host outputs
+    are numpy arrays (allocated here unless given); device outputs are
+    optional CUDA tensors."""
     lib = load_library()
     cfg = config_default()
     cfg.vd = vd
@@ -239,10 +242,16 @@ def kadabra_run(g: Graph, lam: float, delta: float, k: int = 0, seed: int = 0, *
         res.d_counts = d_counts.data_ptr()
     if d_btilde is not None:
         res.d_btilde = d_btilde.data_ptr()
+    topk = None
+    if k > 0:
+        topk = np.full(k, -1, dtype=np.int32)
+        res.topk = topk.ctypes.data
     _raise(lib.kadabra_run(g.handle, lam, delta, k, seed, C.byref(cfg), C.byref(res)))
+    if topk is not None:
+        topk = topk[:min(k, g.n)]
     return RunResult(res.tau, res.check_interval, res.omega_cap, res.alpha, res.checks, res.vd, res.omega, res.C, res.max_f,
                      res.max_g, np.array(res.totals[:], dtype=np.int64), bool(res.stopped_early),
-                     counts if want_host else None, btilde if want_host else None)
+                     counts if want_host else None, btilde if want_host else None, topk)
 
 
 def kadabra_sample_batch(g: Graph, seed: int, domain: int, first_idx: int, count: int, d_counts,

@@ -283,12 +283,13 @@ def test_run_matches_oracle_small(kd, orc, gg, name, make, lam, K):
         assert got.counts.sum() == 0
 
 
-def test_run_rejects_topk_and_bad_args(kd, er2000):
+def test_run_rejects_bad_args(kd, er2000):
     G = kd.kadabra_load_csr(er2000)
     try:
-        with pytest.raises(kd.KadabraError) as e:
-            kd.kadabra_run(G, 0.01, 0.1, 10, 1)
-        assert e.value.status == kd.ERR_UNSUPPORTED
+        for k in (-1, 257):  # top-k mode takes 1 <= k <= 256
+            with pytest.raises(kd.KadabraError) as e:
+                kd.kadabra_run(G, 0.01, 0.1, k, 1)
+            assert e.value.status == kd.ERR_ARG
         for lam, delta in ((0.0, 0.1), (0.01, 1.0), (-1.0, 0.1)):
             with pytest.raises(kd.KadabraError):
                 kd.kadabra_run(G, lam, delta, 0, 1)
