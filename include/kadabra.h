@@ -109,6 +109,10 @@ typedef struct {
   uint32_t* d_counts;  /* device, n                                               */
   double* d_btilde;    /* device, n                                               */
   int32_t* topk;       /* host, k: top-k mode's ranking (k > 0; may be NULL)      */
+  /* serving (kadabra_submit / kadabra_poll): host monotonic clock, seconds   */
+  double t_submit;     /* submitted                                                */
+  double t_start;      /* admitted (device state allocated)                        */
+  double t_done;       /* result ready                                             */
 } kadabra_result;
 
 /* Copies a host CSR to the device and prepares the graph (Sec. 2 graph
@@ -163,6 +167,40 @@ kadabra_status kadabra_batch_graph(kadabra_batch* b, int32_t i, kadabra_graph** 
  * then one stop-test launch over all of them.  Blocking. */
 kadabra_status kadabra_run_batch(kadabra_batch* b, const double* lambda, const double* delta, const uint64_t* seed,
                                  const kadabra_config* cfg, kadabra_result* out);
+
+/* ---------------------------------------------------------------- serving
+ * Continuous batching of KADABRA runs (either mode of kadabra_run) on the
+ * graph's device.  A worker thread admits submitted jobs in arrival order
+ * while their device state (hit counters, computeDelta tables, scratch:
+ * about 12 bytes per node, 40 in top-k mode) fits the memory budget and a
+ * slot is free; each round samples the next batch of every admitted job in
+ * one sampler launch (a new job's warm-up, or its next K main-loop
+ * samples), then runs computeDelta for jobs whose warm-up is done and the
+ * stop tests of the others.  A job's result is identical to kadabra_run
+ * with the same arguments, whatever runs beside it.  The graph must stay
+ * loaded until its jobs are collected. */
+
+/* Sets the memory budget (bytes of job state on the device; 0 = a quarter
+ * of the free memory when the server starts) and the most jobs admitted at
+ * once.  Only before the first submit (KADABRA_ERR_ARG after). */
+kadabra_status kadabra_serve_configure(uint64_t budget_bytes, int32_t max_active);
+
+/* Queues one run of KADABRA on g (arguments as kadabra_run; cfg->stream and
+ * cfg->ctas_per_sm are ignored: the server has its own stream).  Returns at
+ * once with a job id in *job.  Argument errors are returned here. */
+kadabra_status kadabra_submit(kadabra_graph* g, double lambda, double delta, int32_t k, uint64_t seed,
+                              const kadabra_config* cfg, uint64_t* job);
+
+/* *done = 1 and the result in *out (same fields and caller-owned buffers as
+ * kadabra_run; t_submit, t_start, t_done set) once the job has finished, or
+ * *done = 0 at once if it has not and wait == 0; wait != 0 blocks until it
+ * has.  A finished job is collected by this call: its id is then unknown
+ * (KADABRA_ERR_ARG).  Returns the job's own status when done. */
+kadabra_status kadabra_poll(uint64_t job, int32_t wait, int32_t* done, kadabra_result* out);
+
+/* Finishes every admitted and queued job, stops the worker threads and
+ * frees their device memory; results not yet collected are dropped. */
+void kadabra_serve_shutdown(void);
 
 kadabra_status kadabra_graph_info(const kadabra_graph* g, int32_t* n, int64_t* m, int* directed, int64_t* vd);
 

@@ -35,7 +35,13 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <memory>
+#include <thread>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -2934,6 +2940,515 @@ kadabra_status run_topk(kadabra_graph* g, double lambda, double delta, int32_t k
   return KADABRA_OK;
 }
 
+
+// ================================================================ serving
+// Continuous batching of KADABRA runs (Alg. 1, either mode) on one device.
+// A worker thread admits submitted jobs in arrival order while the device
+// memory their state needs fits the budget (and a slot is free), allocating
+// that state stream-ordered; then, round after round, it samples the next
+// batch of every active job in one sampler launch (the warm-up of a job just
+// admitted, or its next K main-loop samples), runs each job's host step
+// (computeDelta after its warm-up) and the stop tests of all jobs that
+// sampled, and retires finished jobs.  A job's samples are keyed by its seed
+// and sample index and its batches are the same K as alone, so its result
+// does not depend on what runs beside it.
+double mono_seconds() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct SrvJob {
+  uint64_t id = 0;
+  kadabra_graph* g = nullptr;
+  double lambda = 0.0, delta = 0.0;
+  int k = 0, k1 = 0;  // top-k mode when k > 0 (k, k1 clamped to n)
+  uint64_t seed = 0;
+  kadabra_config cfg;
+  int64_t n = 0;
+  uint64_t alpha = 0, cap = 0, K = 0, tau = 0, B = 0;
+  int phase = 0;  // 0 admitted, 1 warm-up next, 2 main loop, 3 finished
+  bool final_due = false;
+  void* block = nullptr;  // one stream-ordered allocation for all device state
+  uint32_t *counts = nullptr, *count0 = nullptr, *count_pre = nullptr, *scratch = nullptr;
+  double *lntab = nullptr, *lnLv = nullptr, *lnUv = nullptr;
+  long long* totals = nullptr;
+  unsigned long long* cand = nullptr;
+  size_t footprint = 0;
+  kadabra_result res;
+  std::vector<uint32_t> h_counts;
+  std::vector<int32_t> h_topk;
+  kadabra_status status = KADABRA_OK;
+  std::string err;
+  bool finished = false;  // set under the server's lock
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// device bytes of a job's state (counters, compaction scratch, computeDelta
+// table or per-node arrays, top-k selection survivors)
+size_t srv_layout(SrvJob* J, bool carve) {
+  const size_t n = (size_t)J->n;
+  unsigned char* base = static_cast<unsigned char*>(J->block);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    void* p = carve ? base + off : nullptr;
+    off += align256(bytes);
+    return p;
+  };
+  J->counts = (uint32_t*)take(4 * n);
+  J->count0 = (uint32_t*)take(4 * n);
+  J->totals = (long long*)take(sizeof(long long) * KADABRA_NSTAT);
+  if (J->k > 0) {
+    J->count_pre = (uint32_t*)take(4 * n);
+    J->lnLv = (double*)take(8 * n);
+    J->lnUv = (double*)take(8 * n);
+    J->scratch = (uint32_t*)take(20 * n);  // compaction (3 x 4n), then staging (20 per entry)
+    J->cand = (unsigned long long*)take(sizeof(unsigned long long) * TK_BLOCKS * (TOPK_MAX + 1));
+  } else {
+    J->lntab = (double*)take(8 * (J->alpha + 1));
+    J->scratch = (uint32_t*)take(4 * n);
+  }
+  return off;
+}
+
+} // namespace
+
+struct kadabra_server {
+  int device = 0, num_sms = 0;
+  cudaStream_t st = nullptr;
+  std::unique_ptr<Workspace> ws;
+  size_t budget = 0, in_use = 0;
+  int max_active = 0;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<SrvJob*> pending;
+  std::vector<SrvJob*> active;
+  std::unordered_map<uint64_t, SrvJob*> jobs;
+  bool stopping = false;
+  std::thread th;
+  // device descriptors of a round's batched kernels
+  void* d_desc = nullptr;
+  size_t desc_bytes = 0;
+  TopkJob* d_tk = nullptr;
+  TopkOut* d_tko = nullptr;
+};
+
+namespace {
+
+std::atomic<uint64_t> g_next_job{1};
+std::mutex g_srv_mu;
+std::unordered_map<int, kadabra_server*> g_servers;
+std::unordered_map<uint64_t, kadabra_server*> g_job_owner;
+size_t g_srv_budget = 0;  // 0 = a quarter of the free device memory
+int g_srv_max_active = 256;
+
+#define SCK(call)                                                                         \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) return fail(KADABRA_ERR_CUDA, cudaGetErrorString(e_));         \
+  } while (0)
+
+kadabra_status srv_desc(kadabra_server* S, size_t bytes) {
+  if (S->desc_bytes >= bytes) return KADABRA_OK;
+  SCK(cudaStreamSynchronize(S->st));
+  if (S->d_desc) cudaFree(S->d_desc);
+  S->d_desc = nullptr;
+  S->desc_bytes = 0;
+  SCK(cudaMalloc(&S->d_desc, bytes));
+  S->desc_bytes = bytes;
+  return KADABRA_OK;
+}
+
+// the workspace must cover the largest graph of any job admitted
+kadabra_status srv_workspace(kadabra_server* S, const kadabra_graph* g) {
+  if (S->ws && S->ws->max_n >= g->n && S->ws->max_m >= g->m) return KADABRA_OK;
+  SCK(cudaStreamSynchronize(S->st));
+  auto w = std::make_unique<Workspace>();
+  w->device = S->device;
+  w->num_sms = S->num_sms;
+  w->max_n = std::max<int32_t>(g->n, S->ws ? S->ws->max_n : 0);
+  w->max_m = std::max<int64_t>(g->m, S->ws ? S->ws->max_m : 0);
+  S->ws = std::move(w);
+  return KADABRA_OK;
+}
+
+kadabra_status srv_start(kadabra_server* S, SrvJob* J) {
+  KTRY(srv_workspace(S, J->g));
+  SCK(cudaMallocAsync(&J->block, J->footprint, S->st));
+  srv_layout(J, true);
+  SCK(cudaMemsetAsync(J->counts, 0, 4 * (size_t)J->n, S->st));
+  SCK(cudaMemsetAsync(J->count0, 0, 4 * (size_t)J->n, S->st));
+  SCK(cudaMemsetAsync(J->totals, 0, sizeof(long long) * KADABRA_NSTAT, S->st));
+  if (J->k > 0) SCK(cudaMemsetAsync(J->count_pre, 0, 4 * (size_t)J->n, S->st));
+  J->phase = 1;
+  return KADABRA_OK;
+}
+
+Job srv_job(const SrvJob* J, uint32_t domain, uint64_t first, uint64_t count, uint32_t* counts) {
+  Job j;
+  std::memset(&j, 0, sizeof(j));
+  j.g = graph_dev(J->g);
+  j.seed = J->seed;
+  j.domain = domain;
+  j.first_idx = first;
+  j.count = count;
+  j.counts = counts;
+  j.totals = J->totals;
+  return j;
+}
+
+// selection (select_only) or Alg. 3 of one top-k job over its counts at tau
+kadabra_status srv_topk_pass(kadabra_server* S, SrvJob* J, const uint32_t* counts, int select_only, TopkOut* ho) {
+  TopkJob T;
+  std::memset(&T, 0, sizeof(T));
+  T.counts = counts;
+  T.lnL = J->lnLv;
+  T.lnU = J->lnUv;
+  T.n = J->n;
+  T.tau = J->tau;
+  T.omega = J->res.omega;
+  T.lambda = J->lambda;
+  T.k = J->k;
+  T.k1 = J->k1;
+  T.cand = J->cand;
+  T.select_only = select_only;
+  T.out = S->d_tko;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(4 * (int64_t)S->num_sms, (J->n + 255) / 256));
+  SCK(cudaMemcpyAsync(S->d_tk, &T, sizeof(T), cudaMemcpyHostToDevice, S->st));
+  SCK(cudaMemsetAsync(S->d_tko, 0, sizeof(TopkOut), S->st));
+  k_topk_block<<<TK_BLOCKS, 256, 0, S->st>>>(counts, J->n, J->k1, J->cand);
+  k_topk_final<<<1, 256, 0, S->st>>>(S->d_tk);
+  if (!select_only) k_topk_rest<<<blocks, 256, 0, S->st>>>(S->d_tk);
+  SCK(cudaGetLastError());
+  SCK(cudaMemcpyAsync(ho, S->d_tko, sizeof(TopkOut), cudaMemcpyDeviceToHost, S->st));
+  SCK(cudaStreamSynchronize(S->st));
+  return KADABRA_OK;
+}
+
+// computeDelta of jobs whose warm-up has just been sampled
+kadabra_status srv_compute_delta(kadabra_server* S, const std::vector<SrvJob*>& W) {
+  const int G = (int)W.size();
+  if (G == 0) return KADABRA_OK;
+  // top-k: the k1 first nodes of the preliminary estimate
+  std::vector<TopkTargets> TT(G);
+  std::vector<std::unordered_map<uint32_t, int>> rank_of(G);
+  for (int i = 0; i < G; ++i) {
+    SrvJob* J = W[i];
+    if (J->k == 0) continue;
+    TopkOut ho;
+    KTRY(srv_topk_pass(S, J, J->count_pre, 1, &ho));
+    if (ho.nk != J->k1) return fail(KADABRA_ERR_INTERNAL, "top-k selection returned too few nodes");
+    std::vector<uint32_t> top(J->k1);
+    for (int q = 0; q < J->k1; ++q) {
+      top[q] = (uint32_t)(ho.keys[q] >> 32);
+      rank_of[i][0xFFFFFFFFu - (uint32_t)ho.keys[q]] = q;
+    }
+    TT[i] = topk_targets(top, J->n, J->k, J->alpha, J->lambda);
+  }
+  // the warm-up hits of every job, compacted in node order (one launch set)
+  KTRY(srv_desc(S, (sizeof(NzJob) + sizeof(unsigned) * (NZ_BLK + 1)) * (size_t)G));
+  NzJob* d_nzj = static_cast<NzJob*>(S->d_desc);
+  unsigned* d_blk = reinterpret_cast<unsigned*>(d_nzj + G);
+  unsigned* d_nzt = d_blk + (size_t)NZ_BLK * G;
+  std::vector<NzJob> nzj(G);
+  for (int i = 0; i < G; ++i) {
+    SrvJob* J = W[i];
+    std::memset(&nzj[i], 0, sizeof(NzJob));
+    nzj[i].count0 = J->count0;
+    nzj[i].n = J->n;
+    nzj[i].out = J->scratch;
+    nzj[i].blk = d_blk + (size_t)NZ_BLK * i;
+    nzj[i].total = d_nzt + i;
+    if (J->k > 0) {
+      nzj[i].out_idx = J->scratch + J->n;
+      nzj[i].aux = J->count_pre;
+      nzj[i].out_aux = J->scratch + 2 * J->n;
+    }
+  }
+  SCK(cudaMemcpyAsync(d_nzj, nzj.data(), sizeof(NzJob) * G, cudaMemcpyHostToDevice, S->st));
+  k_nz_count<<<dim3(NZ_BLK, G), 256, 0, S->st>>>(d_nzj);
+  k_nz_offsets<<<G, 32, 0, S->st>>>(d_nzj, NZ_BLK);
+  k_nz_scatter<<<dim3(NZ_BLK, G), 256, 0, S->st>>>(d_nzj);
+  SCK(cudaGetLastError());
+  std::vector<unsigned> nnz(G);
+  SCK(cudaMemcpyAsync(nnz.data(), d_nzt, sizeof(unsigned) * G, cudaMemcpyDeviceToHost, S->st));
+  SCK(cudaStreamSynchronize(S->st));
+  std::vector<std::vector<uint32_t>> c0(G), ids(G), pre(G);
+  for (int i = 0; i < G; ++i) {
+    SrvJob* J = W[i];
+    c0[i].resize(nnz[i]);
+    if (!nnz[i]) continue;
+    SCK(cudaMemcpyAsync(c0[i].data(), J->scratch, 4 * (size_t)nnz[i], cudaMemcpyDeviceToHost, S->st));
+    if (J->k > 0) {
+      ids[i].resize(nnz[i]);
+      pre[i].resize(nnz[i]);
+      SCK(cudaMemcpyAsync(ids[i].data(), J->scratch + J->n, 4 * (size_t)nnz[i], cudaMemcpyDeviceToHost, S->st));
+      SCK(cudaMemcpyAsync(pre[i].data(), J->scratch + 2 * J->n, 4 * (size_t)nnz[i], cudaMemcpyDeviceToHost, S->st));
+    }
+  }
+  SCK(cudaStreamSynchronize(S->st));
+  std::vector<std::vector<double>> host_tab(G), hL(G), hU(G);
+  for (int i = 0; i < G; ++i) {
+    SrvJob* J = W[i];
+    const double eps = J->cfg.eps;
+    if (J->k == 0) {
+      host_tab[i].resize(J->alpha + 1);
+      KTRY(compute_delta_table(J->n, c0[i].data(), c0[i].size(), J->alpha, J->alpha, J->res.omega, J->lambda,
+                               J->delta, eps, host_tab[i].data(), &J->res.C));
+      SCK(cudaMemcpyAsync(J->lntab, host_tab[i].data(), sizeof(double) * host_tab[i].size(), cudaMemcpyHostToDevice,
+                          S->st));
+    } else {
+      const unsigned m = nnz[i];
+      std::vector<double> cL(m), cU(m);
+      for (unsigned q = 0; q < m; ++q) {
+        double lamL = 1.0, lamU;
+        auto it = rank_of[i].find(ids[i][q]);
+        if (it != rank_of[i].end()) {
+          lamL = TT[i].L[it->second];
+          lamU = TT[i].U[it->second];
+        } else {
+          lamU = TT[i].others_U(pre[i][q]);
+        }
+        const double b0 = (double)c0[i][q] / (double)J->alpha;
+        cL[q] = ((2.0 * b0) * J->res.omega) / (lamL * lamL);
+        cU[q] = ((2.0 * b0) * J->res.omega) / (lamU * lamU);
+      }
+      double l0 = 0.0;
+      KTRY(compute_delta_lv_host(J->n, cL, cU, J->delta, eps, hL[i], hU[i], &J->res.C, &l0));
+      const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(4 * (int64_t)S->num_sms, (J->n + 255) / 256));
+      k_fill2<<<blocks, 256, 0, S->st>>>(J->lnLv, J->lnUv, J->n, l0);
+      SCK(cudaGetLastError());
+      if (m) {
+        // staging in the compaction scratch (20 bytes per entry)
+        double* sL = reinterpret_cast<double*>(J->scratch);
+        double* sU = sL + m;
+        uint32_t* sI = reinterpret_cast<uint32_t*>(sU + m);
+        SCK(cudaMemcpyAsync(sI, ids[i].data(), 4 * (size_t)m, cudaMemcpyHostToDevice, S->st));
+        SCK(cudaMemcpyAsync(sL, hL[i].data(), 8 * (size_t)m, cudaMemcpyHostToDevice, S->st));
+        SCK(cudaMemcpyAsync(sU, hU[i].data(), 8 * (size_t)m, cudaMemcpyHostToDevice, S->st));
+        k_scatter2<<<blocks, 256, 0, S->st>>>(J->lnLv, J->lnUv, sI, sL, sU, m);
+        SCK(cudaGetLastError());
+      }
+    }
+    J->phase = 2;
+    J->tau = 0;
+  }
+  SCK(cudaStreamSynchronize(S->st));  // host tables stay alive until copied
+  return KADABRA_OK;
+}
+
+// stop tests (and final evaluations) of jobs that sampled this round
+kadabra_status srv_checks(kadabra_server* S, const std::vector<SrvJob*>& C) {
+  std::vector<SrvJob*> plain;
+  for (SrvJob* J : C)
+    if (J->k == 0) plain.push_back(J);
+  if (!plain.empty()) {
+    const int G = (int)plain.size();
+    KTRY(srv_desc(S, (sizeof(CheckTabJob) + sizeof(CheckOut)) * (size_t)G));
+    CheckTabJob* d_cj = static_cast<CheckTabJob*>(S->d_desc);
+    CheckOut* d_co = reinterpret_cast<CheckOut*>(d_cj + G);
+    std::vector<CheckTabJob> cj(G);
+    int64_t max_n = 1;
+    for (int i = 0; i < G; ++i) {
+      SrvJob* J = plain[i];
+      cj[i].counts = J->counts;
+      cj[i].count0 = J->count0;
+      cj[i].lnT = J->lntab;
+      cj[i].n = J->n;
+      cj[i].tau = J->tau;
+      cj[i].omega = J->res.omega;
+      cj[i].lambda = J->lambda;
+      cj[i].out = d_co + i;
+      max_n = std::max<int64_t>(max_n, J->n);
+    }
+    SCK(cudaMemcpyAsync(d_cj, cj.data(), sizeof(CheckTabJob) * G, cudaMemcpyHostToDevice, S->st));
+    SCK(cudaMemsetAsync(d_co, 0, sizeof(CheckOut) * G, S->st));
+    const int64_t want = (4 * (int64_t)S->num_sms + G - 1) / G;
+    const int bx = (int)std::max<int64_t>(1, std::min<int64_t>(want, (max_n + 255) / 256));
+    k_check_tab<<<dim3(bx, (unsigned)G), 256, 0, S->st>>>(d_cj);
+    SCK(cudaGetLastError());
+    std::vector<CheckOut> co(G);
+    SCK(cudaMemcpyAsync(co.data(), d_co, sizeof(CheckOut) * G, cudaMemcpyDeviceToHost, S->st));
+    SCK(cudaStreamSynchronize(S->st));
+    for (int i = 0; i < G; ++i) {
+      SrvJob* J = plain[i];
+      std::memcpy(&J->res.max_f, &co[i].max_f_bits, sizeof(double));
+      std::memcpy(&J->res.max_g, &co[i].max_g_bits, sizeof(double));
+      if (J->final_due) continue;  // reached ceil(omega): evaluation only
+      J->res.checks++;
+      if (!co[i].fail) {
+        J->res.stopped_early = 1;
+        J->final_due = true;
+      }
+    }
+  }
+  for (SrvJob* J : C) {
+    if (J->k == 0) continue;
+    TopkOut ho;
+    KTRY(srv_topk_pass(S, J, J->counts, 0, &ho));
+    std::memcpy(&J->res.max_f, &ho.max_f_bits, sizeof(double));
+    std::memcpy(&J->res.max_g, &ho.max_g_bits, sizeof(double));
+    J->h_topk.resize(J->k);
+    for (int q = 0; q < J->k; ++q) J->h_topk[q] = (int32_t)(0xFFFFFFFFu - (uint32_t)ho.keys[q]);
+    if (J->final_due) continue;
+    J->res.checks++;
+    if (!ho.fail) {
+      J->res.stopped_early = 1;
+      J->final_due = true;
+    }
+  }
+  return KADABRA_OK;
+}
+
+kadabra_status srv_finish(kadabra_server* S, SrvJob* J) {
+  J->res.tau = J->tau;
+  J->h_counts.resize(J->n);
+  long long tot[KADABRA_NSTAT];
+  SCK(cudaMemcpyAsync(J->h_counts.data(), J->counts, 4 * (size_t)J->n, cudaMemcpyDeviceToHost, S->st));
+  SCK(cudaMemcpyAsync(tot, J->totals, sizeof(tot), cudaMemcpyDeviceToHost, S->st));
+  SCK(cudaStreamSynchronize(S->st));
+  for (int q = 0; q < KADABRA_NSTAT; ++q) J->res.totals[q] = tot[q];
+  return KADABRA_OK;
+}
+
+void srv_release(kadabra_server* S, SrvJob* J) {
+  if (J->block) cudaFreeAsync(J->block, S->st);
+  J->block = nullptr;
+  J->phase = 3;
+  J->res.t_done = mono_seconds();
+}
+
+// one round over the active jobs; returns the jobs that finished
+kadabra_status srv_round(kadabra_server* S, std::vector<SrvJob*>& act, std::vector<SrvJob*>& done) {
+  std::vector<Job> jobs;
+  std::vector<SrvJob*> warm, main_j;
+  for (SrvJob* J : act) {
+    if (J->phase == 1) {
+      if (J->k > 0) jobs.push_back(srv_job(J, 2, 0, J->alpha, J->count_pre));
+      jobs.push_back(srv_job(J, 1, 0, J->alpha, J->count0));
+      warm.push_back(J);
+    } else if (J->phase == 2) {
+      J->B = std::min<uint64_t>(J->K, J->cap - J->tau);
+      jobs.push_back(srv_job(J, 0, J->tau, J->B, J->counts));
+      main_j.push_back(J);
+    }
+  }
+  if (jobs.empty()) return KADABRA_OK;
+  uint64_t work = 0;
+  for (Job& j : jobs) {
+    j.work_begin = work;
+    work += j.count;
+  }
+  Workspace* w = S->ws.get();
+  KTRY(ensure_ws(w, work, (int)jobs.size()));
+  SampleParams P = ws_params(w, 0);
+  P.total_work = work;
+  if (jobs.size() == 1) {
+    P.job0 = jobs[0];
+  } else {
+    SCK(cudaMemcpyAsync(w->d_jobs, jobs.data(), sizeof(Job) * jobs.size(), cudaMemcpyHostToDevice, S->st));
+    P.jobs = w->d_jobs;
+    P.njobs = (int)jobs.size();
+  }
+  KTRY(launch_sampler(w, P, S->st));
+  KTRY(read_status(w, S->st));
+  KTRY(srv_compute_delta(S, warm));
+  std::vector<SrvJob*> chk;
+  for (SrvJob* J : main_j) {
+    J->tau += J->B;
+    if (J->tau >= J->cap) J->final_due = true;
+    chk.push_back(J);
+  }
+  KTRY(srv_checks(S, chk));
+  for (SrvJob* J : main_j)
+    if (J->final_due) {
+      KTRY(srv_finish(S, J));
+      done.push_back(J);
+    }
+  return KADABRA_OK;
+}
+
+void srv_loop(kadabra_server* S) {
+  cudaSetDevice(S->device);
+  for (;;) {
+    std::vector<SrvJob*> act, admitted;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv.wait(lk, [&] { return S->stopping || !S->pending.empty() || !S->active.empty(); });
+      if (S->stopping && S->pending.empty() && S->active.empty()) return;
+      // admission in arrival order while memory and slots allow (a job larger
+      // than the whole budget is admitted when nothing else is active)
+      while (!S->pending.empty() && (int)S->active.size() < S->max_active) {
+        SrvJob* J = S->pending.front();
+        if (!S->active.empty() && S->in_use + J->footprint > S->budget) break;
+        S->pending.pop_front();
+        S->in_use += J->footprint;
+        S->active.push_back(J);
+        admitted.push_back(J);
+      }
+      act = S->active;
+    }
+    std::vector<SrvJob*> done;
+    for (SrvJob* J : admitted) {
+      J->res.t_start = mono_seconds();
+      const kadabra_status st = srv_start(S, J);
+      if (st != KADABRA_OK) {
+        J->status = st;
+        J->err = kadabra_last_error();
+        done.push_back(J);
+      }
+    }
+    std::vector<SrvJob*> live;
+    for (SrvJob* J : act)
+      if (std::find(done.begin(), done.end(), J) == done.end()) live.push_back(J);
+    const kadabra_status st = srv_round(S, live, done);
+    if (st != KADABRA_OK) {  // a device error of the round fails every job in it
+      const std::string msg = kadabra_last_error();
+      for (SrvJob* J : live)
+        if (std::find(done.begin(), done.end(), J) == done.end()) {
+          J->status = st;
+          J->err = msg;
+          done.push_back(J);
+        }
+    }
+    for (SrvJob* J : done) srv_release(S, J);
+    cudaStreamSynchronize(S->st);
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      for (SrvJob* J : done) {
+        S->in_use -= J->footprint;
+        S->active.erase(std::find(S->active.begin(), S->active.end(), J));
+        J->finished = true;
+      }
+    }
+    if (!done.empty()) S->cv.notify_all();
+  }
+}
+
+kadabra_status srv_get(int device, kadabra_server** out) {
+  std::lock_guard<std::mutex> lk(g_srv_mu);
+  auto it = g_servers.find(device);
+  if (it != g_servers.end()) {
+    *out = it->second;
+    return KADABRA_OK;
+  }
+  auto S = std::make_unique<kadabra_server>();
+  S->device = device;
+  SCK(cudaSetDevice(device));
+  SCK(cudaDeviceGetAttribute(&S->num_sms, cudaDevAttrMultiProcessorCount, device));
+  SCK(cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking));
+  size_t free_b = 0, total_b = 0;
+  SCK(cudaMemGetInfo(&free_b, &total_b));
+  S->budget = g_srv_budget ? g_srv_budget : free_b / 4;
+  S->max_active = g_srv_max_active;
+  SCK(cudaMalloc((void**)&S->d_tk, sizeof(TopkJob) + sizeof(TopkOut)));
+  S->d_tko = reinterpret_cast<TopkOut*>(S->d_tk + 1);
+  kadabra_server* raw = S.release();
+  raw->th = std::thread(srv_loop, raw);
+  g_servers[device] = raw;
+  *out = raw;
+  return KADABRA_OK;
+}
+
 // keeps the caller's buffer pointers, zeroes the rest of a result
 void reset_result(kadabra_result* r) {
   uint32_t* ch = r->counts;
@@ -3013,6 +3528,148 @@ kadabra_status noalloc_setup(int dev, NoAllocDevice** out) {
 
 // ================================================================ C ABI
 extern "C" {
+
+
+// ---------------------------------------------------------------- serving
+kadabra_status kadabra_serve_configure(uint64_t budget_bytes, int32_t max_active) {
+  if (max_active < 1) return fail(KADABRA_ERR_ARG, "max_active must be >= 1");
+  std::lock_guard<std::mutex> lk(g_srv_mu);
+  if (!g_servers.empty()) return fail(KADABRA_ERR_ARG, "the server is already running (configure before the first submit)");
+  g_srv_budget = (size_t)budget_bytes;
+  g_srv_max_active = max_active;
+  return KADABRA_OK;
+}
+
+kadabra_status kadabra_submit(kadabra_graph* g, double lambda, double delta, int32_t k, uint64_t seed,
+                              const kadabra_config* cfg_in, uint64_t* job) {
+  if (!g || !job) return fail(KADABRA_ERR_ARG, "graph or job is NULL");
+  if (g->is_view) return fail(KADABRA_ERR_ARG, "batch views cannot be submitted");
+  kadabra_config cfg;
+  kadabra_config_default(&cfg);
+  if (cfg_in) cfg = *cfg_in;
+  if (k < 0 || k > TOPK_MAX) return fail(KADABRA_ERR_ARG, "k must be in [0, 256]");
+  if (!(lambda > 0.0 && lambda < 1.0) || !(delta > 0.0 && delta < 1.0) || !(cfg.eps >= 0.0 && cfg.eps < 0.5))
+    return fail(KADABRA_ERR_ARG, "lambda and delta must be in (0,1), eps in [0,0.5)");
+  auto J = std::make_unique<SrvJob>();
+  std::memset(&J->res, 0, sizeof(J->res));
+  J->g = g;
+  J->lambda = lambda;
+  J->delta = delta;
+  J->seed = seed;
+  J->cfg = cfg;
+  J->n = g->n;
+  J->k = (int)std::min<int64_t>(k, g->n);
+  J->k1 = k > 0 ? (int)std::min<int64_t>((int64_t)k + 1, g->n) : 0;
+  kadabra_result& r = J->res;
+  r.vd = cfg.vd > 0 ? cfg.vd : g->vd;
+  r.omega = omega_host(lambda, delta, r.vd);
+  const double cap_d = std::ceil(r.omega);
+  if (!(cap_d >= 1.0 && cap_d < 1e15)) return fail(KADABRA_ERR_ARG, "omega out of range");
+  J->cap = r.omega_cap = (uint64_t)cap_d;
+  J->alpha = r.alpha = std::max<uint64_t>(1, (uint64_t)std::floor(r.omega / 100.0));
+  J->K = r.check_interval = cfg.check_interval ? cfg.check_interval : auto_check_interval(r.omega);
+  J->footprint = srv_layout(J.get(), false);
+  r.t_submit = mono_seconds();
+  kadabra_server* S = nullptr;
+  KTRY(srv_get(g->device, &S));
+  J->id = g_next_job.fetch_add(1);
+  *job = J->id;
+  {
+    std::lock_guard<std::mutex> lk(g_srv_mu);
+    g_job_owner[J->id] = S;
+  }
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->jobs[J->id] = J.get();
+    S->pending.push_back(J.release());
+  }
+  S->cv.notify_all();
+  return KADABRA_OK;
+}
+
+kadabra_status kadabra_poll(uint64_t job, int32_t wait, int32_t* done, kadabra_result* out) {
+  if (!done) return fail(KADABRA_ERR_ARG, "done is NULL");
+  *done = 0;
+  kadabra_server* S = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_srv_mu);
+    auto it = g_job_owner.find(job);
+    if (it == g_job_owner.end()) return fail(KADABRA_ERR_ARG, "unknown job (never submitted, or already collected)");
+    S = it->second;
+  }
+  SrvJob* J = nullptr;
+  {
+    std::unique_lock<std::mutex> lk(S->mu);
+    J = S->jobs.at(job);
+    if (!J->finished) {
+      if (!wait) return KADABRA_OK;
+      S->cv.wait(lk, [&] { return J->finished; });
+    }
+    S->jobs.erase(job);
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_srv_mu);
+    g_job_owner.erase(job);
+  }
+  std::unique_ptr<SrvJob> own(J);
+  *done = 1;
+  if (!out) return J->status == KADABRA_OK ? KADABRA_OK : fail(J->status, J->err);
+  kadabra_result keep = *out;
+  *out = J->res;
+  out->counts = keep.counts;
+  out->btilde = keep.btilde;
+  out->d_counts = keep.d_counts;
+  out->d_btilde = keep.d_btilde;
+  out->topk = keep.topk;
+  out->status = J->status;
+  if (J->status != KADABRA_OK) return fail(J->status, J->err);
+  const int64_t n = J->n;
+  const double t = (double)J->tau;
+  if (out->counts) std::memcpy(out->counts, J->h_counts.data(), 4 * (size_t)n);
+  if (out->btilde)
+    for (int64_t v = 0; v < n; ++v) out->btilde[v] = (double)J->h_counts[v] / t;
+  if (out->topk)
+    for (int q = 0; q < J->k && q < (int)J->h_topk.size(); ++q) out->topk[q] = J->h_topk[q];
+  if (out->d_counts || out->d_btilde) {
+    KCK(cudaSetDevice(S->device));
+    if (out->d_counts) KCK(cudaMemcpy(out->d_counts, J->h_counts.data(), 4 * (size_t)n, cudaMemcpyHostToDevice));
+    if (out->d_btilde) {
+      std::vector<double> b(n);
+      for (int64_t v = 0; v < n; ++v) b[v] = (double)J->h_counts[v] / t;
+      KCK(cudaMemcpy(out->d_btilde, b.data(), 8 * (size_t)n, cudaMemcpyHostToDevice));
+    }
+  }
+  return KADABRA_OK;
+}
+
+void kadabra_serve_shutdown(void) {
+  std::vector<kadabra_server*> all;
+  {
+    std::lock_guard<std::mutex> lk(g_srv_mu);
+    for (auto& kv : g_servers) all.push_back(kv.second);
+    g_servers.clear();
+  }
+  for (kadabra_server* S : all) {
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->stopping = true;
+    }
+    S->cv.notify_all();
+    if (S->th.joinable()) S->th.join();
+    cudaSetDevice(S->device);
+    cudaStreamSynchronize(S->st);
+    {
+      std::lock_guard<std::mutex> lk(g_srv_mu);
+      for (auto& kv : S->jobs) g_job_owner.erase(kv.first);
+    }
+    for (auto& kv : S->jobs) delete kv.second;
+    if (S->d_desc) cudaFree(S->d_desc);
+    if (S->d_tk) cudaFree(S->d_tk);
+    S->ws.reset();
+    cudaStreamDestroy(S->st);
+    delete S;
+  }
+}
 
 const char* kadabra_last_error(void) { return g_last_error.c_str(); }
 

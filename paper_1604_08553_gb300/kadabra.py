@@ -67,6 +67,7 @@ class kadabra_result(C.Structure):
         ("stopped_early", C.c_int32),
         ("status", C.c_int32), ("counts", C.c_void_p), ("btilde", C.c_void_p), ("d_counts", C.c_void_p),
         ("d_btilde", C.c_void_p), ("topk", C.c_void_p),
+        ("t_submit", C.c_double), ("t_start", C.c_double), ("t_done", C.c_double),
     ]
 
 
@@ -121,6 +122,14 @@ def load_library():
         lib.kadabra_batch_graph.restype = st
         lib.kadabra_run_batch.argtypes = [p, p, p, p, C.POINTER(kadabra_config), p]
         lib.kadabra_run_batch.restype = st
+        lib.kadabra_serve_configure.argtypes = [u64, i32]
+        lib.kadabra_serve_configure.restype = st
+        lib.kadabra_submit.argtypes = [p, dbl, dbl, i32, u64, C.POINTER(kadabra_config), C.POINTER(u64)]
+        lib.kadabra_submit.restype = st
+        lib.kadabra_poll.argtypes = [u64, i32, C.POINTER(i32), C.POINTER(kadabra_result)]
+        lib.kadabra_poll.restype = st
+        lib.kadabra_serve_shutdown.argtypes = []
+        lib.kadabra_serve_shutdown.restype = None
         _lib = lib
         return lib
 
@@ -252,6 +261,59 @@ def kadabra_run(g: Graph, lam: float, delta: float, k: int = 0, seed: int = 0, *
     return RunResult(res.tau, res.check_interval, res.omega_cap, res.alpha, res.checks, res.vd, res.omega, res.C, res.max_f,
                      res.max_g, np.array(res.totals[:], dtype=np.int64), bool(res.stopped_early),
                      counts if want_host else None, btilde if want_host else None, topk)
+
+
+def kadabra_serve_configure(budget_bytes: int = 0, max_active: int = 256) -> None:
+    """Memory budget and slot count of the serving engine (before the first submit)."""
+    _raise(load_library().kadabra_serve_configure(int(budget_bytes), int(max_active)))
+
+
+def kadabra_submit(g: Graph, lam: float, delta: float, k: int = 0, seed: int = 0, *, vd: int = 0,
+                   eps: float = 0.001, check_interval: int = 1000) -> int:
+    """Queues a run on the serving engine; returns its job id at once."""
+    lib = load_library()
+    cfg = config_default()
+    cfg.vd = vd
+    cfg.eps = eps
+    cfg.check_interval = check_interval
+    job = C.c_uint64()
+    _raise(lib.kadabra_submit(g.handle, lam, delta, k, seed, C.byref(cfg), C.byref(job)))
+    return job.value
+
+
+@dataclass
+class ServedResult(RunResult):
+    t_submit: float = 0.0
+    t_start: float = 0.0
+    t_done: float = 0.0
+
+
+def kadabra_poll(job: int, n: int, k: int = 0, wait: bool = True) -> Optional[ServedResult]:
+    """The job's result (collecting it), or None if it has not finished and
+    wait is False.  n is the graph's node count, k the job's k."""
+    lib = load_library()
+    res = kadabra_result()
+    counts = np.zeros(n, dtype=np.uint32)
+    btilde = np.zeros(n, dtype=np.float64)
+    res.counts = counts.ctypes.data
+    res.btilde = btilde.ctypes.data
+    topk = None
+    if k > 0:
+        topk = np.full(k, -1, dtype=np.int32)
+        res.topk = topk.ctypes.data
+    done = C.c_int32()
+    _raise(lib.kadabra_poll(job, int(bool(wait)), C.byref(done), C.byref(res)))
+    if not done.value:
+        return None
+    if topk is not None:
+        topk = topk[:min(k, n)]
+    return ServedResult(res.tau, res.check_interval, res.omega_cap, res.alpha, res.checks, res.vd, res.omega, res.C,
+                        res.max_f, res.max_g, np.array(res.totals[:], dtype=np.int64), bool(res.stopped_early),
+                        counts, btilde, topk, res.t_submit, res.t_start, res.t_done)
+
+
+def kadabra_serve_shutdown() -> None:
+    load_library().kadabra_serve_shutdown()
 
 
 def kadabra_sample_batch(g: Graph, seed: int, domain: int, first_idx: int, count: int, d_counts,
