@@ -334,6 +334,114 @@ def run_batched(args, kd, rank, world):
     B.free()
 
 
+SERVING = dict(jobs=2000, rate=50.0, graphs=16, n_lo=2_000, n_hi=4_000_000, lams=(0.02, 0.01, 0.005), delta=0.1,
+               seed=77)
+
+
+def make_serving_pool():
+    """Graph pool of the serving workload: Erdos-Renyi (mean degree 8),
+    Chung-Lu (beta 2.5, mean degree 16) and Barabasi-Albert (m in {4..16})
+    in turn, n log-uniform in [2*10^3, 4*10^6], one seed per graph."""
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_1604_08553_gb300 import graphgen
+    b = SERVING
+    rng = np.random.default_rng(b["seed"])
+    ns = np.exp(rng.uniform(np.log(b["n_lo"]), np.log(b["n_hi"]), b["graphs"])).astype(np.int64)
+    ms = rng.integers(4, 17, b["graphs"])
+
+    def make(i):
+        n, sd = int(ns[i]), b["seed"] + 1 + i
+        if i % 3 == 0:
+            return graphgen.erdos_renyi(n, 8.0, sd)
+        if i % 3 == 1:
+            return graphgen.chung_lu(n, 2.5, 16.0, float(min(10_000, max(50, n // 20))), sd)
+        return graphgen.barabasi_albert(n, int(ms[i]), sd)
+
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        return list(ex.map(make, range(b["graphs"])))
+
+
+def run_serving(args, kd, rank, world):
+    """Poisson arrivals of KADABRA jobs (all-nodes, or top-k with k in
+    {10, 50}; lambda in {0.02, 0.01, 0.005}; delta = 0.1) on a pool of
+    device-resident graphs, served by the continuous-batching engine.
+    Latency = result ready - submitted (the engine's clock)."""
+    import threading
+    b = SERVING
+    njobs = args.serve_jobs or b["jobs"]
+    graphs = make_serving_pool()
+    handles = [kd.kadabra_load_csr(g) for g in graphs]
+    rng = np.random.default_rng(b["seed"] + 1000)
+    gap = rng.exponential(1.0 / b["rate"], njobs)
+    spec = []
+    for i in range(njobs):
+        gi = int(rng.integers(0, len(graphs)))
+        mode = rng.random()
+        k = 0 if mode < 0.5 else (10 if mode < 0.75 else 50)
+        lam = float(b["lams"][int(rng.integers(0, len(b["lams"])))])
+        spec.append((gi, lam, k, 1 + i))
+    # warm-up: a few jobs through the engine (first launches, allocations)
+    for i in range(max(3, args.warmup)):
+        gi, lam, k, seed = spec[i % njobs]
+        jid = kd.kadabra_submit(handles[gi], lam, b["delta"], k, 10_000 + seed, check_interval=0)
+        kd.kadabra_poll(jid, graphs[gi].n, k, wait=True)
+    results = [None] * njobs
+    ids = [None] * njobs
+    submitted = threading.Semaphore(0)
+
+    def collect():
+        for i in range(njobs):
+            submitted.acquire()
+            gi, lam, k, seed = spec[i]
+            results[i] = kd.kadabra_poll(ids[i], graphs[gi].n, k, wait=True)
+
+    th = threading.Thread(target=collect)
+    th.start()
+    t0 = time.perf_counter()
+    t_next = t0
+    for i in range(njobs):
+        t_next += gap[i]
+        d = t_next - time.perf_counter()
+        if d > 0:
+            time.sleep(d)
+        gi, lam, k, seed = spec[i]
+        ids[i] = kd.kadabra_submit(handles[gi], lam, b["delta"], k, seed, check_interval=0)
+        submitted.release()
+    th.join()
+    wall = max(r.t_done for r in results) - min(r.t_submit for r in results)
+    lat = np.array([r.t_done - r.t_submit for r in results]) * 1e3
+    paths = sum(int(r.alpha) * (2 if spec[i][2] else 1) + int(r.tau) for i, r in enumerate(results))
+    # the same result alone as in the mix, for a few jobs
+    check = [int(x) for x in np.linspace(0, njobs - 1, 6)]
+    for i in check:
+        gi, lam, k, seed = spec[i]
+        alone = kd.kadabra_run(handles[gi], lam, b["delta"], k, seed, check_interval=0)
+        r = results[i]
+        assert alone.tau == r.tau and np.array_equal(alone.counts, r.counts), f"job {i} differs alone"
+        if k:
+            assert np.array_equal(alone.topk, r.topk), f"job {i} ranking differs alone"
+    kd.kadabra_serve_shutdown()
+    for h in handles:
+        h.free()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": paths / wall, "unit": "paths/s", "n_gpus": world, "steps": njobs,
+            "warmup": max(3, args.warmup), "ms_per_step": float(np.mean(lat)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64+f64", "data": "synthetic",
+            "config": {
+                "workload": (f"serving: {njobs} Poisson jobs at {b['rate']:g}/s on {len(graphs)} graphs "
+                             f"(Erdos-Renyi / Chung-Lu / Barabasi-Albert, n log-uniform in [{b['n_lo']}, "
+                             f"{b['n_hi']}]); all-nodes or top-k k in {{10, 50}}; lambda in {list(b['lams'])}, "
+                             f"delta={b['delta']}; check interval max(1024, ceil(omega/32))"),
+                "nodes_per_graph": [int(g.n) for g in graphs], "arcs_total": int(sum(g.m for g in graphs)),
+                "latency_p50_ms": float(np.percentile(lat, 50)), "latency_p99_ms": float(np.percentile(lat, 99)),
+                "latency_max_ms": float(lat.max()), "jobs_per_s": njobs / wall, "offered_jobs_per_s": b["rate"],
+                "wall_s": wall, "results": "6 jobs re-run alone: identical tau, counts, ranking",
+            },
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -343,7 +451,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sampler-only", type=int, default=0, metavar="LAUNCHES",
                     help="only time LAUNCHES sampler batches of K samples (for profilers)")
-    ap.add_argument("--workload", default="chung_lu_1m", choices=[*WORKLOADS, "batched"],
+    ap.add_argument("--serve-jobs", type=int, default=0, help="serving workload: jobs (default 2000)")
+    ap.add_argument("--workload", default="chung_lu_1m", choices=[*WORKLOADS, "batched", "serving"],
                     help="one-graph workload (default chung_lu_1m), or batched: 64 uneven Barabasi-Albert graphs, "
                          "batched run against one-graph-at-a-time runs")
     args = ap.parse_args()
@@ -367,6 +476,9 @@ def main():
     torch.cuda.set_device(local_rank)
     if args.workload == "batched":
         run_batched(args, kd, rank, world)
+        return
+    if args.workload == "serving":
+        run_serving(args, kd, rank, world)
         return
     dist = None
     if world > 1:
