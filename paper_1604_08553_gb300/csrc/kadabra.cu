@@ -85,6 +85,7 @@ constexpr int MED_LCAP = 16384;    //   level lists: 16384 nodes
 constexpr int MED_MAXD = 1022;     //   levels per side
 constexpr int GM_MAXD = 65534;     // tier L, global memory, hash >= 2n slots, lists of n
 constexpr int FAST_PCAP = 2048;    // candidate edges per warp, tiers S and M (global memory)
+constexpr int QUAD_PICK_MAX = 256;  // global-memory tiers: candidate sets ranked quadratically up to this size
 constexpr unsigned long long EMPTY = ~0ull;
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
@@ -329,6 +330,7 @@ struct Ctl {
   int side;
   int ecount;
   int done;       // 0 = continue, 1 = touch, 2 = disconnected
+  int bt_flag;    // backtracking: an invariant failed at this step
   int sel_warp;
   int pick, pick_pos;
   int mode;       // backtracking: 0 = scan the row of x, 1 = scan the previous level
@@ -336,6 +338,12 @@ struct Ctl {
   int cv, cw;     // chosen candidate edge (v on the s side, w on the t side)
   unsigned long long cur;
   unsigned long long ntotal;
+  // weighted radix selection (block_pick_radix)
+  unsigned long long rhist[256];
+  unsigned rcnt[256];
+  unsigned long long rsel_r;
+  int rsel_digit;
+  unsigned rsel_cnt;
 };
 
 // ============================================================== block helpers
@@ -573,38 +581,95 @@ __device__ __forceinline__ int block_pick_by_key(int n, unsigned long long r, Ct
   return c.pick;
 }
 
-// Sorts n (key, payload) pairs in global scratch by key (bitonic network,
-// +inf padding past n), then finds the pair whose prefix interval of
-// weights contains r.  For candidate sets too large for the quadratic pick.
-__device__ int block_pick_sorted(PiEntry* buf, int n, unsigned long long r, Ctl& c) {
-  const int tid = threadIdx.x;
+// Weighted choice among n candidate edges in the order of their keys
+// (x << 32 | y, distinct) without sorting them: most-significant-byte radix
+// selection.  Each pass sums, per value of the next key byte, the weights
+// (and the number) of the candidates that share the bytes fixed so far; the
+// byte whose cumulative weight first exceeds r is fixed and r is reduced by
+// the weight below it.  Once a single candidate shares the fixed bytes it is
+// the pick.  Each thread reads a contiguous run of candidates and adds to the
+// shared histogram once per run of equal bytes: candidates of one tail x are
+// contiguous and sorted by y, so runs are long.  Returns the candidate's
+// index (all threads), or -1 if r is not below the total weight.
+__device__ int block_pick_radix(const PiEntry* buf, int n, unsigned long long r, Ctl& c) {
+  const int tid = threadIdx.x, lane = lane_id();
   auto key = [&](int i) { return ((unsigned long long)(uint32_t)buf[i].x << 32) | (uint32_t)buf[i].y; };
-  int P2 = 1;
-  while (P2 < n) P2 <<= 1;
-  for (int k = 2; k <= P2; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int q = tid; q < (P2 >> 1); q += NT) {
-        int i, partner;
-        if (j == (k >> 1)) {  // mirror step of block size k
-          i = (q / j) * k + (q % j);
-          partner = i ^ (k - 1);
-        } else {
-          i = (q / j) * (2 * j) + (q % j);
-          partner = i + j;
+  const int chunk = (n + NT - 1) / NT;
+  const int a = min(n, tid * chunk), b = min(n, a + chunk);
+  unsigned long long fixed = 0;  // the key bytes above `shift` chosen so far
+  for (int shift = 56; shift >= 0; shift -= 8) {
+    for (int i = tid; i < 256; i += NT) {
+      c.rhist[i] = 0ull;
+      c.rcnt[i] = 0u;
+    }
+    __syncthreads();
+    int cur = -1;
+    unsigned long long acc = 0;
+    unsigned cnt = 0;
+    for (int i = a; i < b; ++i) {
+      const unsigned long long k = key(i);
+      if (shift < 56 && (k >> (shift + 8)) != fixed) continue;
+      const int d = (int)((k >> shift) & 255ull);
+      if (d != cur) {
+        if (cur >= 0) {
+          atomicAdd(&c.rhist[cur], acc);
+          atomicAdd(&c.rcnt[cur], cnt);
         }
-        if (partner < n && key(i) > key(partner)) {
-          const PiEntry a = buf[i];
-          buf[i] = buf[partner];
-          buf[partner] = a;
+        cur = d;
+        acc = 0;
+        cnt = 0;
+      }
+      acc += buf[i].w;
+      ++cnt;
+    }
+    if (cur >= 0) {
+      atomicAdd(&c.rhist[cur], acc);
+      atomicAdd(&c.rcnt[cur], cnt);
+    }
+    __syncthreads();
+    if (tid < 32) {  // warp 0: the byte whose cumulative weight first exceeds r
+      unsigned long long s8 = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) s8 += c.rhist[8 * lane + q];
+      unsigned long long incl = s8;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+      }
+      if (lane == 0) c.rsel_digit = -1;
+      __syncwarp();
+      const unsigned long long excl = incl - s8;
+      if (excl <= r && r < incl) {
+        unsigned long long below = excl;
+        for (int q = 0; q < 8; ++q) {
+          const unsigned long long h = c.rhist[8 * lane + q];
+          if (r < below + h) {
+            c.rsel_digit = 8 * lane + q;
+            c.rsel_r = r - below;
+            c.rsel_cnt = c.rcnt[8 * lane + q];
+            break;
+          }
+          below += h;
         }
       }
-      __syncthreads();
+      if (lane == 0) c.pick = -1;
     }
+    __syncthreads();
+    const int d = c.rsel_digit;
+    if (d < 0) return -1;
+    r = c.rsel_r;
+    fixed = (fixed << 8) | (unsigned long long)d;
+    if (c.rsel_cnt == 1u || shift == 0) {
+      for (int i = tid; i < n; i += NT)
+        if ((key(i) >> shift) == fixed) c.pick = i;
+      __syncthreads();
+      return c.pick;
+    }
+    // the next pass clears the histogram only: the selection fields read
+    // above are rewritten after two more barriers
   }
-  return block_pick(n, r, c, [&](int i0, int N, unsigned long long* w) {
-#pragma unroll
-    for (int k = 0; k < U; ++k) w[k] = (i0 + k < N) ? buf[i0 + k].w : 0ull;
-  });
+  return -1;
 }
 
 // All threads of the CTA call this with the same idx.  Flags in c.flags tell
@@ -628,6 +693,7 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
     c.stat[KADABRA_STAT_DIST] = -1;
     c.flags = 0;
     c.done = 0;
+    c.bt_flag = 0;
     uint32_t ps, pt;
     if (tab_insert(T, s, ent_word<PK>(s, pack_val(0, 0), 1ull), &ps) != 1) c.flags |= F_INTERNAL;
     if (tab_insert(T, t, ent_word<PK>(t, pack_val(1, 0), 1ull), &pt) != 1) c.flags |= F_INTERNAL;
@@ -694,6 +760,7 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
     const int E = c.ecount;
 
     // pass 1: touch test against the other search
+    int pass1_bad = 0;
     {
       int npi = 0;
       bool sigma_of = false;
@@ -724,13 +791,24 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
         }
         npi += __popc(m);
       });
-      if (__any_sync(FULL, sigma_of) && lane == 0) atomicOr(&c.flags, F_SIGMA);
+      int bad = 0;
+      if (__any_sync(FULL, sigma_of) && lane == 0) {
+        atomicOr(&c.flags, F_SIGMA);
+        bad = 1;
+      }
       if (lane == 0) {
         c.npi[wid] = npi;
-        if (npi > T.pcap) atomicOr(&c.flags, F_CAP);
+        if (npi > T.pcap) {
+          atomicOr(&c.flags, F_CAP);
+          bad = 1;
+        }
       }
+      // Decide from the barrier's own reduction, not by reading c.flags
+      // after it: a warp that has already moved on may set flags (the depth
+      // limit below, or pass 2) before a slower warp would have read them,
+      // and the two would then leave at different barriers.
+      pass1_bad = __syncthreads_or(bad);
     }
-    __syncthreads();
     if (tid == 0) {
       int tot = 0;
       for (int w = 0; w < NW; ++w) tot += c.npi[w];
@@ -740,7 +818,7 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
       }
     }
     __syncthreads();
-    if (c.flags) return;
+    if (pass1_bad) return;
     if (c.done) break;
 
     // pass 2: the next level.  The first discoverer of an unvisited head y
@@ -891,10 +969,11 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
     }
     __syncthreads();
     int pick;
-    // the frontier prefix array is free now: up to lcap/2 (key, weight)
-    // pairs fit in it, ranked there quadratically; larger sets are sorted
+    // the frontier prefix array is free now: small candidate sets are copied
+    // there as (key, weight) pairs and ranked quadratically; larger ones go
+    // through the radix selection
     unsigned long long* kw = reinterpret_cast<unsigned long long*>(T.pr);
-    if (total <= T.lcap / 2) {
+    if (total <= min(T.lcap / 2, PK ? T.lcap / 2 : QUAD_PICK_MAX)) {  // (key, weight) pairs fit in pr
       for (int i = tid; i < total; i += NT) {
         kw[2 * i] = ((unsigned long long)(uint32_t)buf[i].x << 32) | (uint32_t)buf[i].y;
         kw[2 * i + 1] = buf[i].w;
@@ -903,7 +982,7 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
       pick = block_pick_by_key(
           total, c.r, c, [&](int i) { return kw[2 * i]; }, [&](int i) { return kw[2 * i + 1]; });
     } else {
-      pick = block_pick_sorted(buf, total, c.r, c);
+      pick = block_pick_radix(buf, total, c.r, c);
     }
     if (pick < 0) {
       if (tid == 0) c.flags |= F_INTERNAL;
@@ -967,7 +1046,7 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
       if (tid == 0) {
         const int px = tab_find_pos(T, x);
         if (px < 0) {
-          c.flags |= F_INTERNAL;
+          c.bt_flag = 1;  // reported below, after every thread has decided
           c.r = 0;
         } else {
           c.r = below128(draw(J.seed, J.domain, idx, j), ent_sig<PK>(T, T.hkv[px], (uint32_t)px));
@@ -978,7 +1057,10 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
       }
       ++j;
       __syncthreads();
-      if (c.flags) return;
+      if (c.bt_flag) {
+        if (tid == 0) c.flags |= F_INTERNAL;
+        return;
+      }
       const unsigned long long r = c.r;
       if (c.mode == 1 && phi - plo == 1) {
         // a single node one level closer: it is x's only possible predecessor

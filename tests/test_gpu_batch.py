@@ -87,3 +87,28 @@ def test_auto_check_interval(kd, er2000):
     finally:
         G.free()
     assert r.check_interval == max(1024, int(np.ceil(r.omega / 32)))
+
+
+def test_batch_repeated_mixed_depths_match_plain(kd, gg):
+    """Many batched launches mixing deep searches (a path, a sparse directed
+    graph: some samples reach the shared-memory depth limit and move to the
+    global tables) with shallow ones.  Every run must equal the plain runs
+    of its graphs; a block whose warps ever left a sample at different
+    barriers would corrupt later samples of that block."""
+    graphs = [gg.barabasi_albert(3000, 3, 1), gg.path_graph(300), random_graph(gg, 400, 0.01, 9, directed=True),
+              gg.erdos_renyi(2000, 8.0, 1)]
+    G = len(graphs)
+    B = kd.Batch(graphs)
+    plain = {}
+    try:
+        for it in range(25):
+            seeds = [it * 10 + i for i in range(G)]
+            got = B.run([0.02] * G, [0.1] * G, seeds)
+            for i in (1, 2):  # the deep graphs, against plain runs
+                ref = plain.get((i, seeds[i]))
+                if ref is None:
+                    ref = kd.kadabra_run(B.views[i], 0.02, 0.1, 0, seeds[i], check_interval=got[i].check_interval)
+                    plain[(i, seeds[i])] = ref
+                assert got[i].tau == ref.tau and np.array_equal(got[i].counts, ref.counts), (it, i)
+    finally:
+        B.free()
