@@ -173,8 +173,8 @@ def algorithmic_bytes(totals, hits):
 
 def run_launches(r, w):
     """Kernels one run launches.  All-nodes mode: the warm-up batch, the
-    warm-up count compaction (3), the main-loop batches, one stop test per
-    check, the final test and b~.  Top-k mode: the preliminary + warm-up
+    warm-up count compaction (3), the main loop's rounds (CUDA graph), the
+    final test and b~.  Top-k mode: the preliminary + warm-up
     batch, the preliminary selection (2), the compaction (3), the fill and
     scatter of ln(1/delta) (2), the main-loop batches, three kernels per
     Alg. 3 test (checks + the final one) and b~."""
@@ -182,7 +182,9 @@ def run_launches(r, w):
     sb = sampler_launches_per_batch() * (1 + rounds)
     if w.get("k"):
         return sb + 2 + 3 + 2 + 3 * (int(r.checks) + 1) + 1
-    return sb + 3 + int(r.checks) + 1 + 1
+    # one-graph all-nodes runs loop on the device: per round a begin kernel,
+    # the sampler batch, the stop test and an end kernel
+    return sampler_launches_per_batch() + 3 + (sampler_launches_per_batch() + 3) * rounds + 1 + 1
 
 
 def sampler_launches_per_batch():

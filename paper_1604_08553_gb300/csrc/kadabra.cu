@@ -283,6 +283,7 @@ struct SampleParams {
   const Job* jobs;                  // device array of njobs jobs, or null (then job0)
   int njobs;
   uint64_t total_work;              // sum of the jobs' counts
+  const unsigned long long* total_dev;  // if set: the sum, read from device memory at launch
   unsigned long long* ctr;          // queue counters, Q_*
   unsigned long long* qb;           // sample indices queued for tier B
   unsigned long long* ql;           // sample indices queued for tier L
@@ -1320,7 +1321,7 @@ __global__ void __launch_bounds__(NT, KD_MIN_BLOCKS) k_sample(SampleParams P) {
   if (tid == 0) {
     for (int k = 0; k < KADABRA_NSTAT; ++k) c.tot[k] = 0;
     c.tot_job = -1;
-    c.ntotal = MODE == 0 ? P.total_work
+    c.ntotal = MODE == 0 ? (P.total_dev ? *P.total_dev : P.total_work)
                : MODE == 2 ? min(P.ctr[Q_SIZE_B], (unsigned long long)P.deferred_cap)
                            : min(P.ctr[Q_SIZE_L], (unsigned long long)P.deferred_cap);
   }
@@ -1522,6 +1523,49 @@ __global__ void __launch_bounds__(256) k_check_tab(const CheckTabJob* __restrict
     if (mg) atomicMax(&J.out->max_g_bits, mg);
     if (fail) atomicOr(&J.out->fail, 1u);
   }
+}
+
+// Device-driven main loop of one all-nodes run (Alg. 1): a CUDA graph whose
+// while node repeats {next batch of K samples, stop test} with the loop
+// state in device memory, so no host round trip separates the rounds.
+struct LoopState {
+  unsigned long long tau, cap, K, B, checks, total_work;
+  int64_t n;
+  unsigned stopped, pad;
+  CheckOut co;
+};
+
+// one thread: the next batch's job range, the queue counters, the test's tau
+__global__ void k_loop_begin(LoopState* s, Job* job, unsigned long long* ctr, CheckTabJob* cj) {
+  const unsigned long long rest = s->cap - s->tau;
+  const unsigned long long B = s->K < rest ? s->K : rest;
+  s->B = B;
+  s->total_work = B;
+  job->first_idx = s->tau;
+  job->count = B;
+  job->work_begin = 0;
+  for (int q = 0; q < Q_COUNT; ++q) ctr[q] = 0ull;
+  s->co.max_f_bits = 0ull;
+  s->co.max_g_bits = 0ull;
+  s->co.fail = 0u;
+  cj->tau = s->tau + B;
+  cj->n = (s->tau + B >= s->cap) ? 0 : s->n;  // no test once ceil(omega) is reached
+}
+
+// one thread: advance tau, count the test, decide whether to go on
+__global__ void k_loop_end(LoopState* s, const int32_t* status, cudaGraphConditionalHandle h) {
+  s->tau += s->B;
+  unsigned keep = 1u;
+  if (s->tau >= s->cap || *status != 0) {
+    keep = 0u;
+  } else {
+    s->checks += 1ull;
+    if (!s->co.fail) {
+      s->stopped = 1u;
+      keep = 0u;
+    }
+  }
+  cudaGraphSetConditional(h, keep);
 }
 
 // Stable compaction of the non-zero warm-up counts of several graphs, in
@@ -2044,6 +2088,17 @@ struct kadabra_graph {
   void* tk_dev = nullptr;            // TopkJob + TopkOut
   void* tk_stage = nullptr;          // scatter staging: ids, lnL, lnU values
   size_t tk_stage_cap = 0;           // entries
+  // device-driven main loop of all-nodes runs (a CUDA graph), built on first use
+  cudaGraph_t loop_graph = nullptr;
+  cudaGraphExec_t loop_exec = nullptr;
+  cudaStream_t loop_cap = nullptr;   // capture stream
+  void* loop_dev = nullptr;          // LoopState, Job, CheckTabJob
+  std::vector<unsigned char> loop_sig;  // launch parameters the graph was built with
+  ~kadabra_graph() {
+    if (loop_exec) cudaGraphExecDestroy(loop_exec);
+    if (loop_graph) cudaGraphDestroy(loop_graph);
+    if (loop_cap) cudaStreamDestroy(loop_cap);
+  }
   std::vector<void*> allocs;  // CSR copies and run buffers
 };
 
@@ -2215,8 +2270,7 @@ SampleParams base_params(kadabra_graph* g) {
 // launches the main sampler grid, then the large-table pass and the
 // n-sized-table pass for the samples queued by the launch before (each exits
 // at once when its queue is empty)
-kadabra_status launch_sampler(Workspace* w, SampleParams P, cudaStream_t st) {
-  KCK(cudaMemsetAsync(w->ctr, 0, Q_COUNT * sizeof(unsigned long long), st));
+kadabra_status launch_sampler_kernels(Workspace* w, SampleParams P, cudaStream_t st) {
   P.pi_base = w->pi_fast;
   P.pcap = FAST_PCAP;
   k_sample<0><<<w->grid_fast, NT, w->smem_fast, st>>>(P);
@@ -2228,6 +2282,11 @@ kadabra_status launch_sampler(Workspace* w, SampleParams P, cudaStream_t st) {
   k_sample<1><<<w->grid_gm, NT, sizeof(Ctl), st>>>(P);
   KCK(cudaGetLastError());
   return KADABRA_OK;
+}
+
+kadabra_status launch_sampler(Workspace* w, SampleParams P, cudaStream_t st) {
+  KCK(cudaMemsetAsync(w->ctr, 0, Q_COUNT * sizeof(unsigned long long), st));
+  return launch_sampler_kernels(w, P, st);
 }
 
 kadabra_status read_status(Workspace* w, cudaStream_t st) {
@@ -2457,6 +2516,104 @@ kadabra_status new_graph(int32_t n, int64_t m, int directed, kadabra_graph** out
 namespace {
 
 
+
+// ---------------------------------------------------------------- device-driven main loop
+// The main loop of one all-nodes run as a CUDA graph: a while node whose body
+// is {k_loop_begin, the three sampler launches, k_check_tab, k_loop_end}; the
+// end kernel sets the while condition.  Built once per graph object and
+// rebuilt only when the launch parameters it captured change (workspace
+// buffers that grew, another table tier flag).
+kadabra_status loop_graph_ready(kadabra_graph* g, Workspace* w, const SampleParams& P, int check_blocks) {
+  std::vector<unsigned char> sig(sizeof(SampleParams) + 4 * sizeof(int));
+  std::memcpy(sig.data(), &P, sizeof(SampleParams));
+  const int grids[4] = {w->grid_fast, w->grid_big, w->grid_gm, check_blocks};
+  std::memcpy(sig.data() + sizeof(SampleParams), grids, sizeof(grids));
+  if (g->loop_exec && sig == g->loop_sig) return KADABRA_OK;
+  if (g->loop_exec) cudaGraphExecDestroy(g->loop_exec);
+  if (g->loop_graph) cudaGraphDestroy(g->loop_graph);
+  g->loop_exec = nullptr;
+  g->loop_graph = nullptr;
+  if (!g->loop_cap) KCK(cudaStreamCreateWithFlags(&g->loop_cap, cudaStreamNonBlocking));
+  LoopState* d_state = static_cast<LoopState*>(g->loop_dev);
+  Job* d_job = reinterpret_cast<Job*>(d_state + 1);
+  CheckTabJob* d_cj = reinterpret_cast<CheckTabJob*>(d_job + 1);
+  KCK(cudaGraphCreate(&g->loop_graph, 0));
+  cudaGraphConditionalHandle h;
+  KCK(cudaGraphConditionalHandleCreate(&h, g->loop_graph, 1u, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};  // the rest zero
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  KCK(cudaGraphAddNode(&node, g->loop_graph, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  KCK(cudaStreamBeginCaptureToGraph(g->loop_cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  k_loop_begin<<<1, 1, 0, g->loop_cap>>>(d_state, d_job, w->ctr, d_cj);
+  kadabra_status st = launch_sampler_kernels(w, P, g->loop_cap);
+  k_check_tab<<<dim3(check_blocks, 1), 256, 0, g->loop_cap>>>(d_cj);
+  k_loop_end<<<1, 1, 0, g->loop_cap>>>(d_state, w->status, h);
+  cudaGraph_t captured = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(g->loop_cap, &captured);
+  if (st != KADABRA_OK) return st;
+  KCK(ec);
+  KCK(cudaGetLastError());
+  KCK(cudaGraphInstantiate(&g->loop_exec, g->loop_graph, 0));
+  g->loop_sig = sig;
+  return KADABRA_OK;
+}
+
+// Runs the main loop of one all-nodes run on the device; returns tau, the
+// number of tests and whether one held.
+kadabra_status run_loop_graph(kadabra_graph* g, Workspace* w, cudaStream_t st, uint64_t seed, uint64_t cap, uint64_t K,
+                              double omega, double lambda, uint64_t* tau, uint64_t* checks, int* stopped) {
+  if (!g->loop_dev) {
+    void* p;
+    KTRY(dev_alloc(g->allocs, &p, sizeof(LoopState) + sizeof(Job) + sizeof(CheckTabJob)));
+    g->loop_dev = p;
+  }
+  LoopState* d_state = static_cast<LoopState*>(g->loop_dev);
+  Job* d_job = reinterpret_cast<Job*>(d_state + 1);
+  CheckTabJob* d_cj = reinterpret_cast<CheckTabJob*>(d_job + 1);
+  SampleParams P = ws_params(w, g->flags);
+  P.jobs = d_job;
+  P.njobs = 1;
+  P.total_dev = &d_state->total_work;
+  const int64_t want = 4 * (int64_t)w->num_sms;
+  const int check_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, ((int64_t)g->n + 255) / 256));
+  KTRY(loop_graph_ready(g, w, P, check_blocks));
+  LoopState hs;
+  std::memset(&hs, 0, sizeof(hs));
+  hs.cap = cap;
+  hs.K = K;
+  hs.n = g->n;
+  Job hj;
+  std::memset(&hj, 0, sizeof(hj));
+  hj.g = graph_dev(g);
+  hj.seed = seed;
+  hj.domain = 0;
+  hj.counts = g->counts;
+  hj.totals = g->totals;
+  CheckTabJob hc;
+  std::memset(&hc, 0, sizeof(hc));
+  hc.counts = g->counts;
+  hc.count0 = g->count0;
+  hc.lnT = g->lntab;
+  hc.n = g->n;
+  hc.omega = omega;
+  hc.lambda = lambda;
+  hc.out = &d_state->co;
+  KCK(cudaMemcpyAsync(d_state, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
+  KCK(cudaMemcpyAsync(d_job, &hj, sizeof(hj), cudaMemcpyHostToDevice, st));
+  KCK(cudaMemcpyAsync(d_cj, &hc, sizeof(hc), cudaMemcpyHostToDevice, st));
+  KCK(cudaGraphLaunch(g->loop_exec, st));
+  KCK(cudaMemcpyAsync(&hs, d_state, sizeof(hs), cudaMemcpyDeviceToHost, st));
+  KTRY(read_status(w, st));
+  *tau = hs.tau;
+  *checks = hs.checks;
+  *stopped = (int)hs.stopped;
+  return KADABRA_OK;
+}
+
 // ---------------------------------------------------------------- Alg. 1 runner
 constexpr int NZ_BLK = 128;  // compaction blocks per graph
 
@@ -2633,7 +2790,17 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
     RCK(cudaMemcpyAsync(co.data(), d_co, sizeof(CheckOut) * cj.size(), cudaMemcpyDeviceToHost, st));
     return read_status(w, st);
   };
-  // main loop (Alg. 1)
+  // main loop (Alg. 1): on the device for one graph, rounds from the host
+  // for several
+  if (G == 1) {
+    uint64_t checks = 0;
+    int stopped = 0;
+    KTRY(run_loop_graph(S[0].g, w, st, seed[0], S[0].cap, S[0].K, out[0].omega, lambda[0], &S[0].tau, &checks,
+                        &stopped));
+    out[0].checks = checks;
+    out[0].stopped_early = stopped;
+    S[0].done = true;
+  }
   for (;;) {
     jobs.clear();
     std::vector<int> sampled;
@@ -4191,7 +4358,7 @@ void kadabra_free_batch(kadabra_batch* b) {
   for (kadabra_graph* g : b->views) {
     for (void* p : g->allocs)
       if (p) cudaFree(p);
-    delete g;
+    delete g;  // also releases its loop graph
   }
   if (b->arena) cudaFree(b->arena);
   delete b;
