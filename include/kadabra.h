@@ -80,7 +80,12 @@ typedef struct {
   uint64_t check_interval; /* K: samples between stop tests (default 1000; 0 = chosen
                               by the library from omega: max(1024, ceil(omega/32)))  */
   void* stream;            /* cudaStream_t for all work of the call (NULL = default) */
-  int32_t ctas_per_sm;     /* resident sampler CTAs per SM (0 = default)          */
+  int32_t ctas_per_sm;     /* shared-memory sampler tier, as resident CTAs per SM: 0 =
+                              autotuned per graph (a probe batch times both tables on
+                              the first one-graph run), or one of the two values the
+                              library offers (3: 4096-slot tables, 4: 2048-slot);
+                              any other value is KADABRA_ERR_ARG.  Results do not
+                              depend on it.  Batches and serving use the default.  */
   int32_t reserved[7];
 } kadabra_config;
 
@@ -113,6 +118,8 @@ typedef struct {
   double t_submit;     /* submitted                                                */
   double t_start;      /* admitted (device state allocated)                        */
   double t_done;       /* result ready                                             */
+  int32_t ctas_per_sm; /* shared-memory sampler tier used (resident CTAs per SM)   */
+  int32_t reserved_out;
 } kadabra_result;
 
 /* Copies a host CSR to the device and prepares the graph (Sec. 2 graph

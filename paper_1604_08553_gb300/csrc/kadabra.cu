@@ -79,6 +79,7 @@ constexpr int U = KD_U;            // independent items per thread per step (mem
 // global tables (tier L).  Every tier gives the same result.
 constexpr int FAST_HLOG = KD_FAST_HLOG;        // tier S: 2^FAST_HLOG hash slots
 constexpr int BIG_HLOG = FAST_HLOG + 1;        // tier B: twice as many
+constexpr int SMALL_HLOG = FAST_HLOG - 1;      // tier S, small variant: half the slots, one more CTA per SM
 constexpr int FAST_MAXD = 126;     // levels per side in shared memory (the packed entry's dist field)
 constexpr int MED_HLOG = 15;       // tier M, global memory per CTA: 32768 hash slots
 constexpr int MED_LCAP = 16384;    //   level lists: 16384 nodes
@@ -1300,13 +1301,16 @@ __device__ void clear_path_row(const SampleParams& P, int64_t out_i) {
 // MODE 0: every sample of the batch, on tier S; overflow -> tier-B queue.
 // MODE 2: the tier-B queue, on tier B, then tier M; overflow -> tier-L queue.
 // MODE 1: the tier-L queue, on tier L.
-template <int MODE>
-__global__ void __launch_bounds__(NT, KD_MIN_BLOCKS) k_sample(SampleParams P) {
+// SHL: the tier-S table size (2^SHL slots) of MODE 0; the small variant fits
+// one more CTA per SM and gives the same results (samples that outgrow it go
+// on to tier B as usual).
+template <int MODE, int SHL = FAST_HLOG>
+__global__ void __launch_bounds__(NT, SHL == FAST_HLOG ? KD_MIN_BLOCKS : KD_MIN_BLOCKS + 1) k_sample(SampleParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   Ctl& c = *reinterpret_cast<Ctl*>(smem);
   Tables TS, TM;
   PiEntry* pi = P.pi_base + (size_t)blockIdx.x * 2 * NW * P.pcap;
-  if (MODE == 0) TS = smem_tables<FAST_HLOG>(smem);
+  if (MODE == 0) TS = smem_tables<SHL>(smem);
   if (MODE == 2) {
     TS = smem_tables<BIG_HLOG>(smem);
     TM = gm_tables(P.med_base + (size_t)blockIdx.x * P.med_stride, MED_HLOG, MED_LCAP, MED_MAXD);
@@ -1404,6 +1408,7 @@ __global__ void __launch_bounds__(NT, KD_MIN_BLOCKS) k_sample(SampleParams P) {
 }
 
 size_t fast_smem_bytes() { return SLayout<FAST_HLOG>::BYTES; }
+size_t small_smem_bytes() { return SLayout<SMALL_HLOG>::BYTES; }
 size_t big_smem_bytes() { return SLayout<BIG_HLOG>::BYTES; }
 
 // ============================================================== stop test
@@ -2031,8 +2036,8 @@ struct Workspace {
   int device = 0, num_sms = 0;
   int32_t max_n = 0;
   int64_t max_m = 0;
-  int grid_fast = 0, grid_big = 0, grid_gm = 0;
-  size_t smem_fast = 0, smem_big = 0;
+  int grid_fast = 0, grid_big = 0, grid_gm = 0, grid_small = 0;
+  size_t smem_fast = 0, smem_big = 0, smem_small = 0;
   unsigned long long* ctr = nullptr;
   int32_t* status = nullptr;
   unsigned long long* qb = nullptr;  // queue for tier B
@@ -2088,6 +2093,7 @@ struct kadabra_graph {
   void* tk_dev = nullptr;            // TopkJob + TopkOut
   void* tk_stage = nullptr;          // scatter staging: ids, lnL, lnU values
   size_t tk_stage_cap = 0;           // entries
+  int tier_variant = -1;             // tier-S variant chosen by the autotuner (-1: not yet)
   // device-driven main loop of all-nodes runs (a CUDA graph), built on first use
   cudaGraph_t loop_graph = nullptr;
   cudaGraphExec_t loop_exec = nullptr;
@@ -2142,6 +2148,10 @@ kadabra_status ensure_ws(Workspace* w, uint64_t deferred_need, int njobs) {
     KCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample<0>, NT, w->smem_fast));
     if (per_sm < 1) return fail(KADABRA_ERR_CAPACITY, "sampler does not fit on an SM");
     w->grid_fast = w->num_sms * per_sm;
+    w->smem_small = small_smem_bytes();
+    KCK(cudaFuncSetAttribute(k_sample<0, SMALL_HLOG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->smem_small));
+    KCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample<0, SMALL_HLOG>, NT, w->smem_small));
+    w->grid_small = w->num_sms * std::max(per_sm, 1);
     w->smem_big = big_smem_bytes();
     KCK(cudaFuncSetAttribute(k_sample<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->smem_big));
     KCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample<2>, NT, w->smem_big));
@@ -2167,7 +2177,7 @@ kadabra_status ensure_ws(Workspace* w, uint64_t deferred_need, int njobs) {
     KTRY(dev_alloc(w->allocs, &p, sizeof(int32_t)));
     w->status = (int32_t*)p;
     KCK(cudaMemset(w->status, 0, sizeof(int32_t)));
-    KTRY(dev_alloc(w->allocs, &p, sizeof(PiEntry) * 2 * NW * (size_t)FAST_PCAP * w->grid_fast));
+    KTRY(dev_alloc(w->allocs, &p, sizeof(PiEntry) * 2 * NW * (size_t)FAST_PCAP * std::max(w->grid_fast, w->grid_small)));
     w->pi_fast = (PiEntry*)p;
     KTRY(dev_alloc(w->allocs, &p, sizeof(PiEntry) * 2 * NW * (size_t)w->pcap_gm * w->grid_gm));
     w->pi_gm = (PiEntry*)p;
@@ -2270,10 +2280,14 @@ SampleParams base_params(kadabra_graph* g) {
 // launches the main sampler grid, then the large-table pass and the
 // n-sized-table pass for the samples queued by the launch before (each exits
 // at once when its queue is empty)
-kadabra_status launch_sampler_kernels(Workspace* w, SampleParams P, cudaStream_t st) {
+// variant 1: the small tier-S table (SMALL_HLOG) with one more CTA per SM
+kadabra_status launch_sampler_kernels(Workspace* w, SampleParams P, cudaStream_t st, int variant = 0) {
   P.pi_base = w->pi_fast;
   P.pcap = FAST_PCAP;
-  k_sample<0><<<w->grid_fast, NT, w->smem_fast, st>>>(P);
+  if (variant == 1)
+    k_sample<0, SMALL_HLOG><<<w->grid_small, NT, w->smem_small, st>>>(P);
+  else
+    k_sample<0><<<w->grid_fast, NT, w->smem_fast, st>>>(P);
   KCK(cudaGetLastError());
   k_sample<2><<<w->grid_big, NT, w->smem_big, st>>>(P);
   KCK(cudaGetLastError());
@@ -2284,9 +2298,9 @@ kadabra_status launch_sampler_kernels(Workspace* w, SampleParams P, cudaStream_t
   return KADABRA_OK;
 }
 
-kadabra_status launch_sampler(Workspace* w, SampleParams P, cudaStream_t st) {
+kadabra_status launch_sampler(Workspace* w, SampleParams P, cudaStream_t st, int variant = 0) {
   KCK(cudaMemsetAsync(w->ctr, 0, Q_COUNT * sizeof(unsigned long long), st));
-  return launch_sampler_kernels(w, P, st);
+  return launch_sampler_kernels(w, P, st, variant);
 }
 
 kadabra_status read_status(Workspace* w, cudaStream_t st) {
@@ -2517,16 +2531,85 @@ namespace {
 
 
 
+
+// ---------------------------------------------------------------- tier-S autotuner
+// Picks, per graph, the tier-S table that samples it faster: 2^FAST_HLOG
+// slots at KD_MIN_BLOCKS CTAs per SM, or 2^SMALL_HLOG slots with one more CTA
+// per SM (small visited sets gain from the extra concurrency, large ones lose
+// to more escalations).  Both give identical results, so the choice only
+// changes speed.  It times a probe batch of samples in RNG domain 3 (results
+// discarded) with each, once per graph.  cfg.ctas_per_sm overrides it.
+constexpr uint64_t TUNE_PROBE = 4096;
+
+kadabra_status tier_variant(kadabra_graph* g, Workspace* w, cudaStream_t st, int32_t requested, int* variant) {
+  const int per_default = w->grid_fast / w->num_sms, per_small = w->grid_small / w->num_sms;
+  if (requested != 0) {
+    if (requested == per_default) *variant = 0;
+    else if (requested == per_small) *variant = 1;
+    else
+      return fail(KADABRA_ERR_ARG, "ctas_per_sm must be 0 (autotune), " + std::to_string(per_default) + " or " +
+                                       std::to_string(per_small));
+    return KADABRA_OK;
+  }
+  if (g->tier_variant >= 0) {
+    *variant = g->tier_variant;
+    return KADABRA_OK;
+  }
+  KTRY(ensure_ws(w, TUNE_PROBE, 1));
+  SampleParams P = ws_params(w, g->flags);
+  P.total_work = TUNE_PROBE;
+  std::memset(&P.job0, 0, sizeof(Job));
+  P.job0.g = graph_dev(g);
+  P.job0.seed = 0x5EEDu;
+  P.job0.domain = 3;
+  P.job0.count = TUNE_PROBE;  // counts and totals null: nothing is recorded
+  cudaEvent_t e0, e1;
+  KCK(cudaEventCreate(&e0));
+  KCK(cudaEventCreate(&e1));
+  float best[2] = {1e30f, 1e30f};
+  kadabra_status stt = KADABRA_OK;
+  for (int rep = 0; rep < 2 && stt == KADABRA_OK; ++rep)
+    for (int v = 0; v < 2 && stt == KADABRA_OK; ++v) {
+      cudaEventRecord(e0, st);
+      stt = launch_sampler(w, P, st, v);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) stt = fail(KADABRA_ERR_CUDA, "autotune probe");
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      best[v] = std::min(best[v], ms);
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  KTRY(stt);
+  int32_t h = 0;  // a probe sample's error (the run reports its own) only ends the tuning
+  KCK(cudaMemcpyAsync(&h, w->status, sizeof(h), cudaMemcpyDeviceToHost, st));
+  KCK(cudaStreamSynchronize(st));
+  if (h != 0) {
+    KCK(cudaMemsetAsync(w->status, 0, sizeof(int32_t), st));
+    KCK(cudaStreamSynchronize(st));
+    g->tier_variant = 0;
+  } else {
+    g->tier_variant = best[1] < 0.97f * best[0] ? 1 : 0;
+  }
+  *variant = g->tier_variant;
+  return KADABRA_OK;
+}
+
+int variant_ctas_per_sm(const Workspace* w, int variant) {
+  return (variant == 1 ? w->grid_small : w->grid_fast) / w->num_sms;
+}
+
 // ---------------------------------------------------------------- device-driven main loop
 // The main loop of one all-nodes run as a CUDA graph: a while node whose body
 // is {k_loop_begin, the three sampler launches, k_check_tab, k_loop_end}; the
 // end kernel sets the while condition.  Built once per graph object and
 // rebuilt only when the launch parameters it captured change (workspace
 // buffers that grew, another table tier flag).
-kadabra_status loop_graph_ready(kadabra_graph* g, Workspace* w, const SampleParams& P, int check_blocks) {
-  std::vector<unsigned char> sig(sizeof(SampleParams) + 4 * sizeof(int));
+kadabra_status loop_graph_ready(kadabra_graph* g, Workspace* w, const SampleParams& P, int check_blocks,
+                                int variant) {
+  std::vector<unsigned char> sig(sizeof(SampleParams) + 5 * sizeof(int));
   std::memcpy(sig.data(), &P, sizeof(SampleParams));
-  const int grids[4] = {w->grid_fast, w->grid_big, w->grid_gm, check_blocks};
+  const int grids[5] = {w->grid_fast, w->grid_big, w->grid_gm, check_blocks, variant};
   std::memcpy(sig.data() + sizeof(SampleParams), grids, sizeof(grids));
   if (g->loop_exec && sig == g->loop_sig) return KADABRA_OK;
   if (g->loop_exec) cudaGraphExecDestroy(g->loop_exec);
@@ -2549,7 +2632,7 @@ kadabra_status loop_graph_ready(kadabra_graph* g, Workspace* w, const SamplePara
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   KCK(cudaStreamBeginCaptureToGraph(g->loop_cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   k_loop_begin<<<1, 1, 0, g->loop_cap>>>(d_state, d_job, w->ctr, d_cj);
-  kadabra_status st = launch_sampler_kernels(w, P, g->loop_cap);
+  kadabra_status st = launch_sampler_kernels(w, P, g->loop_cap, variant);
   k_check_tab<<<dim3(check_blocks, 1), 256, 0, g->loop_cap>>>(d_cj);
   k_loop_end<<<1, 1, 0, g->loop_cap>>>(d_state, w->status, h);
   cudaGraph_t captured = nullptr;
@@ -2565,7 +2648,7 @@ kadabra_status loop_graph_ready(kadabra_graph* g, Workspace* w, const SamplePara
 // Runs the main loop of one all-nodes run on the device; returns tau, the
 // number of tests and whether one held.
 kadabra_status run_loop_graph(kadabra_graph* g, Workspace* w, cudaStream_t st, uint64_t seed, uint64_t cap, uint64_t K,
-                              double omega, double lambda, uint64_t* tau, uint64_t* checks, int* stopped) {
+                              double omega, double lambda, int variant, uint64_t* tau, uint64_t* checks, int* stopped) {
   if (!g->loop_dev) {
     void* p;
     KTRY(dev_alloc(g->allocs, &p, sizeof(LoopState) + sizeof(Job) + sizeof(CheckTabJob)));
@@ -2580,7 +2663,7 @@ kadabra_status run_loop_graph(kadabra_graph* g, Workspace* w, cudaStream_t st, u
   P.total_dev = &d_state->total_work;
   const int64_t want = 4 * (int64_t)w->num_sms;
   const int check_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, ((int64_t)g->n + 255) / 256));
-  KTRY(loop_graph_ready(g, w, P, check_blocks));
+  KTRY(loop_graph_ready(g, w, P, check_blocks, variant));
   LoopState hs;
   std::memset(&hs, 0, sizeof(hs));
   hs.cap = cap;
@@ -2686,6 +2769,11 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
     cudaError_t e_ = (call);                                                              \
     if (e_ != cudaSuccess) return fail(KADABRA_ERR_CUDA, cudaGetErrorString(e_));         \
   } while (0)
+  int variant = 0;  // tier-S variant of one-graph runs (several graphs share launches: the default)
+  if (G == 1) {
+    KTRY(tier_variant(gs[0], w, st, cfg.ctas_per_sm, &variant));
+    out[0].ctas_per_sm = variant_ctas_per_sm(w, variant);
+  }
   for (State& s : S) {
     RCK(cudaMemsetAsync(s.g->totals, 0, sizeof(long long) * KADABRA_NSTAT, st));
     RCK(cudaMemsetAsync(s.g->count0, 0, sizeof(uint32_t) * s.g->n, st));
@@ -2708,7 +2796,7 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
       P.jobs = w->d_jobs;
       P.njobs = (int)jobs.size();
     }
-    return launch_sampler(w, P, st);
+    return launch_sampler(w, P, st, variant);
   };
   auto make_job = [&](const State& s, uint32_t domain, uint64_t first, uint64_t count, uint32_t* counts,
                       uint64_t seed_i) {
@@ -2795,8 +2883,8 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
   if (G == 1) {
     uint64_t checks = 0;
     int stopped = 0;
-    KTRY(run_loop_graph(S[0].g, w, st, seed[0], S[0].cap, S[0].K, out[0].omega, lambda[0], &S[0].tau, &checks,
-                        &stopped));
+    KTRY(run_loop_graph(S[0].g, w, st, seed[0], S[0].cap, S[0].K, out[0].omega, lambda[0], variant, &S[0].tau,
+                        &checks, &stopped));
     out[0].checks = checks;
     out[0].stopped_early = stopped;
     S[0].done = true;
@@ -3016,6 +3104,9 @@ kadabra_status run_topk(kadabra_graph* g, double lambda, double delta, int32_t k
   RCK(cudaMemsetAsync(g->count_pre, 0, sizeof(uint32_t) * n, st));
   RCK(cudaMemsetAsync(g->count0, 0, sizeof(uint32_t) * n, st));
   RCK(cudaMemsetAsync(g->counts, 0, sizeof(uint32_t) * n, st));
+  int variant = 0;
+  KTRY(tier_variant(g, w, st, cfg.ctas_per_sm, &variant));
+  r.ctas_per_sm = variant_ctas_per_sm(w, variant);
   auto job = [&](uint32_t domain, uint64_t first, uint64_t count, uint32_t* counts) {
     Job j;
     std::memset(&j, 0, sizeof(j));
@@ -3038,7 +3129,7 @@ kadabra_status run_topk(kadabra_graph* g, double lambda, double delta, int32_t k
     P.total_work = 2 * alpha;
     P.jobs = w->d_jobs;
     P.njobs = 2;
-    KTRY(launch_sampler(w, P, st));
+    KTRY(launch_sampler(w, P, st, variant));
   }
   const int rest_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(4 * (int64_t)w->num_sms, (n + 255) / 256));
   // selection (select_only) or Alg. 3 over `counts` at `tau`
@@ -3155,7 +3246,7 @@ kadabra_status run_topk(kadabra_graph* g, double lambda, double delta, int32_t k
     SampleParams P = ws_params(w, g->flags);
     P.total_work = B;
     P.job0 = job(0, tau, B, g->counts);
-    KTRY(launch_sampler(w, P, st));
+    KTRY(launch_sampler(w, P, st, variant));
     tau += B;
     if (tau >= cap) break;
     r.checks++;

@@ -68,6 +68,7 @@ class kadabra_result(C.Structure):
         ("status", C.c_int32), ("counts", C.c_void_p), ("btilde", C.c_void_p), ("d_counts", C.c_void_p),
         ("d_btilde", C.c_void_p), ("topk", C.c_void_p),
         ("t_submit", C.c_double), ("t_start", C.c_double), ("t_done", C.c_double),
+        ("ctas_per_sm", C.c_int32), ("reserved_out", C.c_int32),
     ]
 
 
@@ -223,12 +224,13 @@ class RunResult:
     counts: Optional[np.ndarray]
     btilde: Optional[np.ndarray]
     topk: Optional[np.ndarray] = None
+    ctas_per_sm: int = 0
 
 
 def kadabra_run(g: Graph, lam: float, delta: float, k: int = 0, seed: int = 0, *, vd: int = 0,
                 eps: float = 0.001, check_interval: int = 1000, stream: Optional[int] = None,
                 counts: Optional[np.ndarray] = None, btilde: Optional[np.ndarray] = None,
-                d_counts=None, d_btilde=None, want_host: bool = True) -> RunResult:
+                d_counts=None, d_btilde=None, want_host: bool = True, ctas_per_sm: int = 0) -> RunResult:
     """Runs KADABRA: all-nodes mode (k = 0), or the k most central nodes
     (k > 0; the ranking's k first nodes come back in `topk`).  Host outputs
     are numpy arrays (allocated here unless given); device outputs are
@@ -239,6 +241,7 @@ def kadabra_run(g: Graph, lam: float, delta: float, k: int = 0, seed: int = 0, *
     cfg.eps = eps
     cfg.check_interval = check_interval
     cfg.stream = stream
+    cfg.ctas_per_sm = ctas_per_sm
     res = kadabra_result()
     if want_host:
         if counts is None:
@@ -260,7 +263,7 @@ def kadabra_run(g: Graph, lam: float, delta: float, k: int = 0, seed: int = 0, *
         topk = topk[:min(k, g.n)]
     return RunResult(res.tau, res.check_interval, res.omega_cap, res.alpha, res.checks, res.vd, res.omega, res.C, res.max_f,
                      res.max_g, np.array(res.totals[:], dtype=np.int64), bool(res.stopped_early),
-                     counts if want_host else None, btilde if want_host else None, topk)
+                     counts if want_host else None, btilde if want_host else None, topk, res.ctas_per_sm)
 
 
 def kadabra_serve_configure(budget_bytes: int = 0, max_active: int = 256) -> None:
@@ -309,7 +312,7 @@ def kadabra_poll(job: int, n: int, k: int = 0, wait: bool = True) -> Optional[Se
         topk = topk[:min(k, n)]
     return ServedResult(res.tau, res.check_interval, res.omega_cap, res.alpha, res.checks, res.vd, res.omega, res.C,
                         res.max_f, res.max_g, np.array(res.totals[:], dtype=np.int64), bool(res.stopped_early),
-                        counts, btilde, topk, res.t_submit, res.t_start, res.t_done)
+                        counts, btilde, topk, t_submit=res.t_submit, t_start=res.t_start, t_done=res.t_done)
 
 
 def kadabra_serve_shutdown() -> None:
