@@ -53,6 +53,9 @@ WORKLOADS = {
                            delta=0.1, check_interval=1000, sampler_dram_bytes=None),
     "rmat_24": dict(family="rmat", scale=24, edge_factor=16, a=0.57, b=0.19, c=0.19, graph_seed=1, lam=0.0025,
                     delta=0.1, check_interval=1 << 16, sampler_dram_bytes=None),
+    # the scale-22 graph of the same recipe: the size the ncu counters are captured at
+    "rmat_22": dict(family="rmat", scale=22, edge_factor=16, a=0.57, b=0.19, c=0.19, graph_seed=1, lam=0.0025,
+                    delta=0.1, check_interval=1 << 16, sampler_dram_bytes=None),
     "rmat_24_topk": dict(family="rmat", scale=24, edge_factor=16, a=0.57, b=0.19, c=0.19, graph_seed=1, lam=0.0025,
                          delta=0.1, check_interval=1 << 16, sampler_dram_bytes=None, k=10),
 }
