@@ -333,6 +333,7 @@ struct Ctl {
   int ecount;
   int done;       // 0 = continue, 1 = touch, 2 = disconnected
   int bt_flag;    // backtracking: an invariant failed at this step
+  uint4 draws[32];  // the sample's Philox blocks j = 0..31, drawn by warp 0 at its start
   int sel_warp;
   int pick, pick_pos;
   int mode;       // backtracking: 0 = scan the row of x, 1 = scan the previous level
@@ -682,8 +683,13 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
   const int tid = threadIdx.x, lane = lane_id(), wid = warp_id();
   const GraphDev& G = J.g;
 
+  // the first 32 Philox blocks of the sample ((s,t), candidate edge,
+  // backtracking steps), one per lane of warp 0, so the serial steps below
+  // only read them
+  if (wid == 0) c.draws[lane] = draw(J.seed, J.domain, idx, (uint32_t)lane);
+  __syncwarp();
   if (tid == 0) {
-    const uint4 b0 = draw(J.seed, J.domain, idx, 0);
+    const uint4 b0 = c.draws[0];
     const uint64_t u = (uint64_t)b0.x | ((uint64_t)b0.y << 32);
     const uint64_t u2 = (uint64_t)b0.z | ((uint64_t)b0.w << 32);
     const int s = (int)__umul64hi(u, (uint64_t)G.n);
@@ -840,6 +846,9 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
       const volatile int* nlist_now = &c.nlist;
       scan_level(T, fcount, E, cols, [&](int, bool ok, int p, int y) {
         if (!ok || cap) return;
+        // the head's row bounds (its degree joins the new frontier's cost if
+        // it is new), loaded before the probe so the load overlaps it
+        const int ylo = __ldg(&rowp[y]), yhi = __ldg(&rowp[y + 1]);
         const uint32_t px = T.lpos[f0 + p];
         const unsigned long long add = ent_sig<PK>(T, T.hkv[px], px);
         uint32_t pos = hash_pos(y, T.hlog);
@@ -863,7 +872,7 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
               T.lnode[slot] = y;
               T.lpos[slot] = pos;
               ++fresh;
-              cost += __ldg(&rowp[y + 1]) - __ldg(&rowp[y]);
+              cost += yhi - ylo;
               if (!PK && !ent_add<PK>(T, pos, add)) of = true;
               return;
             }
@@ -949,7 +958,7 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
     } else {
       c.stat[KADABRA_STAT_SIGMA_LO] = (long long)(lo & 0xFFFFFFFFull);
       c.stat[KADABRA_STAT_SIGMA_HI] = (long long)(lo >> 32);
-      c.r = below128(draw(J.seed, J.domain, idx, 1), lo);
+      c.r = below128(c.draws[1], lo);
     }
     int acc = 0;  // segment starts of the flat candidate index
     for (int w = 0; w < NW; ++w) {
@@ -1051,7 +1060,8 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
           c.bt_flag = 1;  // reported below, after every thread has decided
           c.r = 0;
         } else {
-          c.r = below128(draw(J.seed, J.domain, idx, j), ent_sig<PK>(T, T.hkv[px], (uint32_t)px));
+          c.r = below128(j < 32 ? c.draws[j] : draw(J.seed, J.domain, idx, j),
+                         ent_sig<PK>(T, T.hkv[px], (uint32_t)px));
         }
         // scan whichever is shorter: the row of x, or the previous level
         c.mode = ((long long)(phi - plo) * 16 < (long long)deg) ? 1 : 0;
