@@ -174,6 +174,25 @@ def algorithmic_bytes(totals, hits):
     return (8 * t[1] + 8 * t[0] + 12 * t[2] + 8 * t[3] + 4 * hits + 4 * t[6])
 
 
+def replica_seed(rank: int, step: int) -> int:
+    """Seed of a timed step on a rank: replicas sample different paths."""
+    return 1 + step + 7919 * rank
+
+
+def reduce_replicas(dist, seconds: float, paths: float, device: str):
+    """Whole-job figures of independent replicas, one per rank: the slowest
+    rank's time and the paths of all ranks.  Every rank calls it; dist is
+    torch.distributed (any backend) or None for a single process."""
+    if dist is None:
+        return float(seconds), float(paths)
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    p = torch.tensor([float(paths)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(p[0])
+
+
 def run_launches(r, w):
     """Kernels one run launches.  All-nodes mode: the warm-up batch, the
     warm-up count compaction (3), the main loop's rounds (CUDA graph), the
@@ -528,7 +547,7 @@ def main():
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        r = step(1 + i + 7919 * rank)
+        r = step(replica_seed(rank, i))
         ev1.record(stream)
         ev1.synchronize()
         times.append(ev0.elapsed_time(ev1) / 1e3)
@@ -538,13 +557,7 @@ def main():
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    total = sum(times)
-    if dist is not None:
-        t = torch.tensor([total, float(paths)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        total, paths = float(tmax[0]), float(t[1])
+    total, paths = reduce_replicas(dist, sum(times), paths, "cuda")
     value = paths / total
 
     # ---- dominant kernel: the sampler, timed per launch on its stream
@@ -590,7 +603,8 @@ def main():
         e2e_paths += r.alpha + r.tau
     torch.cuda.synchronize()
     e2e_dt = time.perf_counter() - t0
-    e2e_value = e2e_paths / e2e_dt * world
+    e2e_dt, e2e_paths = reduce_replicas(dist, e2e_dt, e2e_paths, "cuda")
+    e2e_value = e2e_paths / e2e_dt
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
