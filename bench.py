@@ -204,9 +204,13 @@ def run_launches(r, w):
     sb = sampler_launches_per_batch() * (1 + rounds)
     if w.get("k"):
         return sb + 2 + 3 + 2 + 3 * (int(r.checks) + 1) + 1
-    # one-graph all-nodes runs loop on the device: per round a begin kernel,
-    # the sampler batch, the stop test and an end kernel
-    return sampler_launches_per_batch() + 3 + (sampler_launches_per_batch() + 3) * rounds + 1 + 1
+    # one-graph all-nodes runs with more than 4 possible rounds loop on the
+    # device: per round a begin kernel, the sampler batch, the stop test and an
+    # end kernel; shorter runs take host rounds (batch, then a test if tau < cap)
+    cap_rounds = -(-int(r.omega_cap) // w["check_interval"])
+    if cap_rounds > 4:
+        return sampler_launches_per_batch() + 3 + (sampler_launches_per_batch() + 3) * rounds + 1 + 1
+    return sampler_launches_per_batch() * (1 + rounds) + 3 + int(r.checks) + 1 + 1
 
 
 def sampler_launches_per_batch():

@@ -227,8 +227,10 @@ kadabra_status kadabra_graph_set_flags(kadabra_graph* g, uint32_t flags);
  * of K with a stop test after each, until the test holds or ceil(omega)
  * samples.  lambda in (0,1), delta in (0,1); cfg may be NULL.  Blocking.
  *   k = 0: all-nodes mode, the rule f,g <= lambda for every node (Sec. 2).
- *     The main loop runs on the device as a CUDA graph (a while node over
- *     {next batch, stop test}); the host waits once for it.
+ *     When ceil(omega) allows more than 4 rounds of K samples, the main loop
+ *     runs on the device as a CUDA graph (a while node over {next batch,
+ *     stop test}) and the host waits once for it; otherwise the host runs
+ *     the rounds.  Results are the same either way.
  *   1 <= k <= 256: the k most central nodes (Sec. 5): a preliminary
  *     estimate of alpha samples (RNG domain 2) sets per-node targets
  *     lambda_L(v), lambda_U(v); Alg. 2 runs with those targets; the stop

@@ -1897,6 +1897,13 @@ __global__ void k_scatter2(double* __restrict__ a, double* __restrict__ b, const
   }
 }
 
+// 32 row offsets and 32 adjacency entries at evenly spaced positions
+__global__ void k_fingerprint(const int32_t* rp, const int32_t* ci, int32_t n, int64_t m, int32_t* out) {
+  const int i = threadIdx.x;
+  if (i < 32) out[i] = rp[(int64_t)n * i / 32];
+  else if (i < 64) out[i] = m > 0 ? ci[m * (i - 32) / 32] : 0;
+}
+
 __global__ void k_btilde(const uint32_t* __restrict__ counts, int64_t n, uint64_t tau, double* __restrict__ out) {
   const double t = (double)tau;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
@@ -2104,6 +2111,7 @@ struct kadabra_graph {
   void* tk_stage = nullptr;          // scatter staging: ids, lnL, lnU values
   size_t tk_stage_cap = 0;           // entries
   int tier_variant = -1;             // tier-S variant chosen by the autotuner (-1: not yet)
+  uint64_t fingerprint = 0;          // shape and sampled CSR entries (key of the autotuner's cache)
   // device-driven main loop of all-nodes runs (a CUDA graph), built on first use
   cudaGraph_t loop_graph = nullptr;
   cudaGraphExec_t loop_exec = nullptr;
@@ -2485,7 +2493,7 @@ kadabra_status compute_vd(kadabra_graph* g) {
 
 kadabra_status finish_load(kadabra_graph* g) {
   unsigned* err;
-  KCK(cudaMalloc(&err, sizeof(unsigned)));
+  KCK(cudaMalloc(&err, sizeof(unsigned) * 65));
   KCK(cudaMemset(err, 0, sizeof(unsigned)));
   const int blocks = std::max(1, std::min(16 * g->num_sms, (g->n + 7) / 8));
   k_validate_rows<<<blocks, 256>>>(g->rp, g->ci, g->n, g->m, err);
@@ -2497,6 +2505,23 @@ kadabra_status finish_load(kadabra_graph* g) {
     const int32_t* rci = g->directed ? g->rci : g->ci;
     k_validate_mirror<<<blocks, 256>>>(g->rp, g->ci, rrp, rci, g->n, err);
     KCK(cudaMemcpy(&h, err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  }
+  if (!h) {  // fingerprint: FNV-1a over the shape and 64 sampled entries
+    int32_t fp[64];
+    k_fingerprint<<<1, 64>>>(g->rp, g->ci, g->n, g->m, reinterpret_cast<int32_t*>(err + 1));
+    KCK(cudaMemcpy(fp, err + 1, sizeof(fp), cudaMemcpyDeviceToHost));
+    uint64_t x = 1469598103934665603ull;
+    auto mix = [&](uint64_t v) {
+      for (int b = 0; b < 8; ++b) {
+        x ^= (v >> (8 * b)) & 0xFF;
+        x *= 1099511628211ull;
+      }
+    };
+    mix((uint64_t)g->n);
+    mix((uint64_t)g->m);
+    mix((uint64_t)g->directed);
+    for (int i = 0; i < 64; ++i) mix((uint64_t)(uint32_t)fp[i]);
+    g->fingerprint = x;
   }
   cudaFree(err);
   if (h) {
@@ -2550,6 +2575,10 @@ namespace {
 // changes speed.  It times a probe batch of samples in RNG domain 3 (results
 // discarded) with each, once per graph.  cfg.ctas_per_sm overrides it.
 constexpr uint64_t TUNE_PROBE = 4096;
+// process-wide: graphs with the same fingerprint, device and flags (a graph
+// loaded again) reuse the probe's choice; a collision could only cost speed
+std::mutex g_tune_mu;
+std::unordered_map<uint64_t, int> g_tune_cache;
 
 kadabra_status tier_variant(kadabra_graph* g, Workspace* w, cudaStream_t st, int32_t requested, int* variant) {
   const int per_default = w->grid_fast / w->num_sms, per_small = w->grid_small / w->num_sms;
@@ -2564,6 +2593,16 @@ kadabra_status tier_variant(kadabra_graph* g, Workspace* w, cudaStream_t st, int
   if (g->tier_variant >= 0) {
     *variant = g->tier_variant;
     return KADABRA_OK;
+  }
+  const uint64_t key = g->fingerprint ^ ((uint64_t)g->device << 56) ^ ((uint64_t)g->flags << 48);
+  const bool cached = g->fingerprint != 0;  // graphs of a batch have none
+  if (cached) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      g->tier_variant = *variant = it->second;
+      return KADABRA_OK;
+    }
   }
   KTRY(ensure_ws(w, TUNE_PROBE, 1));
   SampleParams P = ws_params(w, g->flags);
@@ -2600,6 +2639,8 @@ kadabra_status tier_variant(kadabra_graph* g, Workspace* w, cudaStream_t st, int
     g->tier_variant = 0;
   } else {
     g->tier_variant = best[1] < 0.97f * best[0] ? 1 : 0;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (cached) g_tune_cache[key] = g->tier_variant;
   }
   *variant = g->tier_variant;
   return KADABRA_OK;
@@ -2610,6 +2651,8 @@ int variant_ctas_per_sm(const Workspace* w, int variant) {
 }
 
 // ---------------------------------------------------------------- device-driven main loop
+constexpr uint64_t LOOP_GRAPH_MIN_ROUNDS = 4;  // fewer possible rounds: host rounds cost as little
+
 // The main loop of one all-nodes run as a CUDA graph: a while node whose body
 // is {k_loop_begin, the three sampler launches, k_check_tab, k_loop_end}; the
 // end kernel sets the while condition.  Built once per graph object and
@@ -2888,9 +2931,10 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
     RCK(cudaMemcpyAsync(co.data(), d_co, sizeof(CheckOut) * cj.size(), cudaMemcpyDeviceToHost, st));
     return read_status(w, st);
   };
-  // main loop (Alg. 1): on the device for one graph, rounds from the host
-  // for several
-  if (G == 1) {
+  // main loop (Alg. 1): on the device for one graph with enough rounds to
+  // repay building its CUDA graph, rounds from the host otherwise (same
+  // results either way)
+  if (G == 1 && (S[0].cap + S[0].K - 1) / S[0].K > LOOP_GRAPH_MIN_ROUNDS) {
     uint64_t checks = 0;
     int stopped = 0;
     KTRY(run_loop_graph(S[0].g, w, st, seed[0], S[0].cap, S[0].K, out[0].omega, lambda[0], variant, &S[0].tau,
