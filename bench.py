@@ -240,6 +240,29 @@ def cpu_baseline(g, seconds_cap=20.0):
                       f"single-threaded oracle, {dt:.1f} s"}
 
 
+def cpu_baseline_multicore(g, rate_single: float, seconds: float = 3.0):
+    """The oracle's sampler over disjoint sample-index ranges on all host
+    cores (process pool started with spawn; counts are order-independent
+    sums, so the result equals one sequential pass), timed without the pool's
+    start-up."""
+    from oracle.parallel import accumulate_ranges
+    procs = max(1, os.cpu_count() or 1)
+    total = max(procs * 200, int(rate_single * seconds) * procs)
+    timing = {}
+    accumulate_ranges(g, 1, 0, [(0, total)], processes=procs, chunk=max(200, total // (4 * procs)), timing=timing)
+    return {"value": total / timing["work_s"], "unit": "paths/s", "cores": timing["processes"], "kind": "oracle",
+            "sample": f"main-loop samples 0..{total - 1} (seed 1) of the {workload_name()} workload, oracle over "
+                      f"disjoint index ranges in {timing['processes']} processes, {timing['work_s']:.1f} s"}
+
+
+def l2_read_peak_gbs():
+    """Read rate of an L2-resident 32 MB buffer, re-read 50 times in one
+    launch with L2-only loads (kadabra_l2_read_probe): the L2 roofline's
+    denominator."""
+    from paper_1604_08553_gb300 import kadabra as kd
+    return max(kd.kadabra_l2_read_probe(32 << 20, 50) for _ in range(3))
+
+
 def run_reference(args, rank, world):
     """The oracle on the host cores (the reference arm for this paper-only tier)."""
     g = make_graph()
@@ -545,7 +568,7 @@ def main():
     # ---- timed region: device-resident graph, one full adaptive run per step
     barrier()
     torch.cuda.synchronize()
-    times, paths, launches, results = [], 0, 0, []
+    times, paths, launches, results, edges = [], 0, 0, [], 0
     for i in range(args.steps):
         flush.fill_(float(i))
         ev0 = torch.cuda.Event(enable_timing=True)
@@ -556,6 +579,7 @@ def main():
         ev1.synchronize()
         times.append(ev0.elapsed_time(ev1) / 1e3)
         paths += r.alpha + r.tau
+        edges += int(r.totals[0])
         launches += run_launches(r, w)
         results.append(r)
     torch.cuda.synchronize()
@@ -610,9 +634,20 @@ def main():
     e2e_dt, e2e_paths = reduce_replicas(dist, e2e_dt, e2e_paths, "cuda")
     e2e_value = e2e_paths / e2e_dt
 
-    cpu = None
+    cpu = cpu_multi = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(g)
+        cpu_multi = cpu_baseline_multicore(g, cpu["value"])
+    # L2 roofline, for graphs whose CSR fits in L2
+    import torch
+    csr_bytes = (4 * (g.n + 1) + 4 * g.m) * (2 if g.directed else 1)
+    l2_size = torch.cuda.get_device_properties(torch.cuda.current_device()).L2_cache_size
+    roof_l2 = None
+    if csr_bytes < l2_size:
+        l2 = l2_read_peak_gbs()
+        roof_l2 = {"bound": "l2", "achieved": achieved, "peak": l2, "unit": "GB/s", "frac": achieved / l2,
+                   "peak_source": "measured here: kadabra_l2_read_probe, 32 MB L2-resident buffer read 50 times",
+                   "csr_bytes": csr_bytes, "l2_bytes": l2_size}
 
     if rank == 0:
         r0 = results[0]
@@ -626,6 +661,7 @@ def main():
                 "tau": [int(r.tau) for r in results], "alpha": int(r0.alpha), "omega": r0.omega,
                 **({"k": w["k"], "topk_first_step": [int(x) for x in r0.topk]} if w.get("k") else {}),
                 "checks": [int(r.checks) for r in results],
+                "edges_per_s": edges / total if world == 1 else None,
                 "edges_per_sample": float(tot_np[0]) / K,
             }),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -639,6 +675,10 @@ def main():
             line["clocks"] = clk
         if cpu:
             line["cpu_baseline"] = cpu
+        if cpu_multi:
+            line["cpu_baseline_multicore"] = cpu_multi
+        if roof_l2:
+            line["roofline_l2"] = roof_l2
         print(json.dumps(line), flush=True)
     G.free()
     if dist is not None:

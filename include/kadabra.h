@@ -175,6 +175,14 @@ kadabra_status kadabra_batch_graph(kadabra_batch* b, int32_t i, kadabra_graph** 
 kadabra_status kadabra_run_batch(kadabra_batch* b, const double* lambda, const double* delta, const uint64_t* seed,
                                  const kadabra_config* cfg, kadabra_result* out);
 
+/* Measurement helper (no counterpart in the paper): reads a zeroed device
+ * buffer of `bytes` bytes `reps` times in one launch with loads cached in L2
+ * only, after one warming pass, and returns the read rate in GB/s.  With a
+ * buffer that fits in L2 this is the denominator of the sampler's L2
+ * roofline.  Allocates and frees the buffer; synchronous on the current
+ * device.  KADABRA_ERR_ARG for bytes < 16 or reps < 1. */
+kadabra_status kadabra_l2_read_probe(uint64_t bytes, int32_t reps, double* gbs);
+
 /* ---------------------------------------------------------------- serving
  * Continuous batching of KADABRA runs (either mode of kadabra_run) on the
  * graph's device.  A worker thread admits submitted jobs in arrival order

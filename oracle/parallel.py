@@ -48,8 +48,12 @@ def _work(args):
     return key, rc, counts, totals
 
 
-def accumulate_ranges(g, seed: int, domain: int, ranges, processes: int | None = None, chunk: int = 2000):
-    """Returns [(counts, totals)] for each (first, count) in ranges."""
+def accumulate_ranges(g, seed: int, domain: int, ranges, processes: int | None = None, chunk: int = 2000,
+                      timing: dict | None = None):
+    """Returns [(counts, totals)] for each (first, count) in ranges.  If
+    timing is a dict, timing["work_s"] gets the wall time of the sampling
+    alone (workers started and warmed up before the clock starts) and
+    timing["processes"] the worker count."""
     processes = processes or max(1, min(os.cpu_count() or 1, 64))
     d = tempfile.mkdtemp(prefix="orc_graph_")
     try:
@@ -67,11 +71,19 @@ def accumulate_ranges(g, seed: int, domain: int, ranges, processes: int | None =
         out = [[np.zeros(g.n, dtype=np.uint64), np.zeros(11, dtype=np.int64)] for _ in ranges]
         ctx = mp.get_context("spawn")
         with ctx.Pool(processes, initializer=_init, initargs=(d,)) as pool:
+            if timing is not None:
+                import time
+                # one tiny task per worker: start-up and imports before the clock
+                pool.map(_work, [(0, seed, domain, 0, 1)] * processes, chunksize=1)
+                t0 = time.perf_counter()
             for key, rc, counts, totals in pool.imap_unordered(_work, tasks):
                 if rc != 0:
                     raise RuntimeError(f"oracle status {rc}")
                 out[key][0] += counts
                 out[key][1] += totals
+            if timing is not None:
+                timing["work_s"] = time.perf_counter() - t0
+                timing["processes"] = processes
         return [(c.astype(np.uint32), t) for c, t in out]
     finally:
         shutil.rmtree(d, ignore_errors=True)

@@ -1904,6 +1904,18 @@ __global__ void k_fingerprint(const int32_t* rp, const int32_t* ci, int32_t n, i
   else if (i < 64) out[i] = m > 0 ? ci[m * (i - 32) / 32] : 0;
 }
 
+// Measurement helper: re-reads a buffer `reps` times, caching in L2 only
+// (ld.global.cg), so a buffer that fits in L2 measures the L2's read rate.
+__global__ void k_l2_read(const float4* __restrict__ buf, size_t n4, int reps, float* sink) {
+  float acc = 0.f;
+  for (int r = 0; r < reps; ++r)
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
+      const float4 v = __ldcg(&buf[i]);
+      acc += (v.x + v.y) + (v.z + v.w);
+    }
+  if (acc == -1.f) sink[0] = acc;  // never true for the zero buffer; keeps the loads
+}
+
 __global__ void k_btilde(const uint32_t* __restrict__ counts, int64_t n, uint64_t tau, double* __restrict__ out) {
   const double t = (double)tau;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
@@ -4063,6 +4075,42 @@ void kadabra_serve_shutdown(void) {
     cudaStreamDestroy(S->st);
     delete S;
   }
+}
+
+
+// ---------------------------------------------------------------- measurement helper
+kadabra_status kadabra_l2_read_probe(uint64_t bytes, int32_t reps, double* gbs) {
+  if (!gbs || bytes < 16 || reps < 1) return fail(KADABRA_ERR_ARG, "bad probe arguments");
+  int dev = 0, sms = 0;
+  KCK(cudaGetDevice(&dev));
+  KCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const size_t n4 = (size_t)bytes / 16;
+  float4* buf = nullptr;
+  float* sink = nullptr;
+  KCK(cudaMalloc(&buf, n4 * 16));
+  if (cudaMalloc(&sink, sizeof(float)) != cudaSuccess) {
+    cudaFree(buf);
+    return fail(KADABRA_ERR_OOM, "probe sink");
+  }
+  cudaMemset(buf, 0, n4 * 16);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int grid = 8 * sms;
+  k_l2_read<<<grid, 256>>>(buf, n4, 2, sink);  // brings the buffer into L2
+  cudaEventRecord(e0);
+  k_l2_read<<<grid, 256>>>(buf, n4, reps, sink);
+  cudaEventRecord(e1);
+  const cudaError_t e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(buf);
+  cudaFree(sink);
+  if (e != cudaSuccess) return fail(KADABRA_ERR_CUDA, cudaGetErrorString(e));
+  *gbs = (double)n4 * 16.0 * (double)reps / ((double)ms * 1e-3) / 1e9;
+  return KADABRA_OK;
 }
 
 const char* kadabra_last_error(void) { return g_last_error.c_str(); }

@@ -129,6 +129,8 @@ def load_library():
         lib.kadabra_submit.restype = st
         lib.kadabra_poll.argtypes = [u64, i32, C.POINTER(i32), C.POINTER(kadabra_result)]
         lib.kadabra_poll.restype = st
+        lib.kadabra_l2_read_probe.argtypes = [u64, i32, C.POINTER(dbl)]
+        lib.kadabra_l2_read_probe.restype = st
         lib.kadabra_serve_shutdown.argtypes = []
         lib.kadabra_serve_shutdown.restype = None
         _lib = lib
@@ -313,6 +315,13 @@ def kadabra_poll(job: int, n: int, k: int = 0, wait: bool = True) -> Optional[Se
     return ServedResult(res.tau, res.check_interval, res.omega_cap, res.alpha, res.checks, res.vd, res.omega, res.C,
                         res.max_f, res.max_g, np.array(res.totals[:], dtype=np.int64), bool(res.stopped_early),
                         counts, btilde, topk, t_submit=res.t_submit, t_start=res.t_start, t_done=res.t_done)
+
+
+def kadabra_l2_read_probe(nbytes: int = 32 << 20, reps: int = 50) -> float:
+    """Read rate (GB/s) of an L2-resident buffer, for the L2 roofline."""
+    out = C.c_double()
+    _raise(load_library().kadabra_l2_read_probe(int(nbytes), int(reps), C.byref(out)))
+    return out.value
 
 
 def kadabra_serve_shutdown() -> None:
