@@ -86,7 +86,12 @@ typedef struct {
                               library offers (3: 4096-slot tables, 4: 2048-slot);
                               any other value is KADABRA_ERR_ARG.  Results do not
                               depend on it.  Batches and serving use the default.  */
-  int32_t reserved[7];
+  int32_t warp_tier;       /* one-warp-per-sample tier in front of tier S (samples whose
+                              search outgrows its 512-slot table go on to tier S):
+                              0 = autotuned together with ctas_per_sm, 1 = on,
+                              -1 = off; any other value is KADABRA_ERR_ARG.
+                              Results do not depend on it.                        */
+  int32_t reserved[6];
 } kadabra_config;
 
 void kadabra_config_default(kadabra_config* cfg);
@@ -119,7 +124,7 @@ typedef struct {
   double t_start;      /* admitted (device state allocated)                        */
   double t_done;       /* result ready                                             */
   int32_t ctas_per_sm; /* shared-memory sampler tier used (resident CTAs per SM)   */
-  int32_t reserved_out;
+  int32_t warp_tier;   /* 1 if the one-warp-per-sample tier ran first, else 0      */
 } kadabra_result;
 
 /* Copies a host CSR to the device and prepares the graph (Sec. 2 graph
@@ -227,8 +232,18 @@ kadabra_status kadabra_graph_info(const kadabra_graph* g, int32_t* n, int64_t* m
  * at the large shared-memory table, KADABRA_FLAG_MEDIUM_TABLES at the medium
  * global tables, KADABRA_FLAG_GLOBAL_TABLES at the n-sized tables.  They
  * exist to test those paths and for graphs whose searches are known to be
- * deep or wide.  Returns KADABRA_ERR_ARG for unknown bits. */
-enum { KADABRA_FLAG_GLOBAL_TABLES = 1, KADABRA_FLAG_MEDIUM_TABLES = 2, KADABRA_FLAG_LARGE_SHARED_TABLES = 4 };
+ * deep or wide.  KADABRA_FLAG_WARP_TIER makes every sample start one step
+ * earlier, at the one-warp-per-sample table (512 slots, 256 visited nodes,
+ * 128 candidate edges), in every entry point that takes the graph object;
+ * a batch or serving launch shared by several graphs runs that tier first if
+ * any of them has the flag (and ignores their other flags).  It has no effect
+ * together with one of the three flags above.  Returns KADABRA_ERR_ARG for unknown bits. */
+enum {
+  KADABRA_FLAG_GLOBAL_TABLES = 1,
+  KADABRA_FLAG_MEDIUM_TABLES = 2,
+  KADABRA_FLAG_LARGE_SHARED_TABLES = 4,
+  KADABRA_FLAG_WARP_TIER = 8
+};
 kadabra_status kadabra_graph_set_flags(kadabra_graph* g, uint32_t flags);
 
 /* KADABRA (Alg. 1): warm-up, computeDelta (Alg. 2), then sample batches

@@ -288,6 +288,7 @@ struct SampleParams {
   unsigned long long* ctr;          // queue counters, Q_*
   unsigned long long* qb;           // sample indices queued for tier B
   unsigned long long* ql;           // sample indices queued for tier L
+  unsigned long long* q0;           // if set: tier S takes its samples from this queue (filled by tier W)
   uint64_t deferred_cap;            // capacity of each queue
   int32_t* status;                  // run-wide error word (kadabra_status values)
   int tier_flags;                   // TF_* test switches for the table tiers
@@ -1249,6 +1250,7 @@ __device__ inline Tables smem_tables(unsigned char* smem) {
 constexpr int TF_SKIP_S = 1;
 constexpr int TF_SKIP_B = 2;
 constexpr int TF_SKIP_M = 4;
+constexpr int TF_WARP = 8;  // tier W first, whatever the launch's variant
 
 // queue counters in SampleParams::ctr
 constexpr int Q_NEXT_A = 0;   // next sample index of the batch
@@ -1256,6 +1258,8 @@ constexpr int Q_NEXT_B = 1;   // next entry of the tier-B queue
 constexpr int Q_SIZE_B = 2;   // entries in the tier-B queue
 constexpr int Q_NEXT_L = 3;   // next entry of the tier-L queue
 constexpr int Q_SIZE_L = 4;   // entries in the tier-L queue
+constexpr int Q_NEXT_W = 5;   // next sample index of tier W
+constexpr int Q_SIZE_S = 6;   // entries tier W queued for tier S
 constexpr int Q_COUNT = 8;
 
 __device__ void enqueue(const SampleParams& P, int size_ctr, unsigned long long* q, uint64_t idx) {
@@ -1335,7 +1339,8 @@ __global__ void __launch_bounds__(NT, SHL == FAST_HLOG ? KD_MIN_BLOCKS : KD_MIN_
   if (tid == 0) {
     for (int k = 0; k < KADABRA_NSTAT; ++k) c.tot[k] = 0;
     c.tot_job = -1;
-    c.ntotal = MODE == 0 ? (P.total_dev ? *P.total_dev : P.total_work)
+    c.ntotal = MODE == 0 ? (P.q0 ? min(P.ctr[Q_SIZE_S], (unsigned long long)P.deferred_cap)
+                                 : (P.total_dev ? *P.total_dev : P.total_work))
                : MODE == 2 ? min(P.ctr[Q_SIZE_B], (unsigned long long)P.deferred_cap)
                            : min(P.ctr[Q_SIZE_L], (unsigned long long)P.deferred_cap);
   }
@@ -1347,7 +1352,7 @@ __global__ void __launch_bounds__(NT, SHL == FAST_HLOG ? KD_MIN_BLOCKS : KD_MIN_
     __syncthreads();
     if (c.cur >= ntotal) break;
     // k: the sample's index in the launch's work space; its job and sample index
-    const unsigned long long k = MODE == 0 ? c.cur : MODE == 2 ? P.qb[c.cur] : P.ql[c.cur];
+    const unsigned long long k = MODE == 0 ? (P.q0 ? P.q0[c.cur] : c.cur) : MODE == 2 ? P.qb[c.cur] : P.ql[c.cur];
     if (tid == 0) {
       int j = 0;
       if (P.jobs) {
@@ -1416,6 +1421,432 @@ __global__ void __launch_bounds__(NT, SHL == FAST_HLOG ? KD_MIN_BLOCKS : KD_MIN_
   }
   if (tid == 0) flush_totals(P, c);
 }
+
+// ============================================================== tier W: one warp per sample
+// Eight independent samples per CTA, one per warp, each on a small packed
+// table in shared memory, synchronised by warp only.  For graphs whose
+// searches stay small, this gives more samples in flight and no block
+// barriers.  A sample that outgrows the table (more nodes, candidate edges
+// or levels than below, or a sigma beyond the packed field) is queued
+// for tier S, which gives the same result; hits are counted only in the
+// backtracking, which never escalates, so nothing is counted twice.
+constexpr int WT_HLOG = 9;
+constexpr int WT_HSIZE = 1 << WT_HLOG;  // 512 hash slots
+constexpr int WT_LCAP = 256;            // level-list nodes
+constexpr int WT_PCAP = 128;            // candidate edges
+constexpr int WT_MAXD = FAST_MAXD;      // levels per side (the packed dist field)
+constexpr int WT_WARPS = 8;             // samples per CTA
+
+struct WSlot {  // one warp's shared memory
+  unsigned long long hkv[WT_HSIZE];  // packed entries, as in tier S
+  int2 pr[WT_LCAP + 1];              // frontier: {degree prefix, row start}
+  int32_t lnode[WT_LCAP];
+  uint32_t lpos[WT_LCAP];
+  PiEntry pi[WT_PCAP];
+  Job job;
+  long long stat[KADABRA_NSTAT];
+  long long tot[KADABRA_NSTAT];
+  int tot_job;
+  int s, t;
+};
+
+__device__ __forceinline__ int wt_probe(const unsigned long long* h, int32_t v, unsigned long long* wo) {
+  uint32_t pos = hash_pos(v, WT_HLOG);
+  for (int k = 0; k < WT_HSIZE; ++k) {
+    const unsigned long long w = h[pos];
+    if (w == EMPTY) return -1;
+    if ((int32_t)(w >> 32) == v) {
+      *wo = w;
+      return (int)pos;
+    }
+    pos = (pos + 1) & (WT_HSIZE - 1);
+  }
+  return -1;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+
+// One sample by one warp (all lanes call it); the same search, choices and
+// random draws as run_sample.  Returns 0, or F_CAP (escalate to tier S), or
+// F_INTERNAL.  Leaves the work counters in S.stat.
+__device__ int run_sample_warp(const SampleParams& P, const Job& J, WSlot& S, uint64_t idx, int64_t out_i) {
+  const int lane = lane_id();
+  const unsigned lt = (1u << lane) - 1u;
+  const GraphDev& G = J.g;
+  const uint4 myd = draw(J.seed, J.domain, idx, (uint32_t)lane);  // this lane's block j = lane
+  auto dr = [&](uint32_t j) {  // block j, same j in all lanes
+    uint4 b;
+    if (j < 32u) {
+      b.x = __shfl_sync(FULL, myd.x, (int)j);
+      b.y = __shfl_sync(FULL, myd.y, (int)j);
+      b.z = __shfl_sync(FULL, myd.z, (int)j);
+      b.w = __shfl_sync(FULL, myd.w, (int)j);
+    } else {
+      b = draw(J.seed, J.domain, idx, j);
+    }
+    return b;
+  };
+  if (lane < KADABRA_NSTAT) S.stat[lane] = lane == KADABRA_STAT_DIST ? -1 : 0;
+  const uint4 b0 = dr(0);
+  const uint64_t u = (uint64_t)b0.x | ((uint64_t)b0.y << 32);
+  const uint64_t u2 = (uint64_t)b0.z | ((uint64_t)b0.w << 32);
+  const int s = (int)__umul64hi(u, (uint64_t)G.n);
+  const int tp = (int)__umul64hi(u2, (uint64_t)(G.n - 1));
+  const int t = tp + (tp >= s ? 1 : 0);
+  if (lane == 0) {
+    S.s = s;
+    S.t = t;
+    uint32_t ps = hash_pos(s, WT_HLOG);
+    while (S.hkv[ps] != EMPTY) ps = (ps + 1) & (WT_HSIZE - 1);
+    S.hkv[ps] = ent_word<true>(s, pack_val(0, 0), 1ull);
+    uint32_t pt = hash_pos(t, WT_HLOG);
+    while (S.hkv[pt] != EMPTY) pt = (pt + 1) & (WT_HSIZE - 1);
+    S.hkv[pt] = ent_word<true>(t, pack_val(1, 0), 1ull);
+    S.lnode[0] = s;
+    S.lpos[0] = ps;
+    S.lnode[1] = t;
+    S.lpos[1] = pt;
+  }
+  __syncwarp();
+  int dep[2] = {0, 0}, flo[2] = {0, 1}, fhi[2] = {1, 2};
+  long long cst[2] = {G.rp[s + 1] - G.rp[s], G.rrp[t + 1] - G.rrp[t]};
+  int nlist = 2, done = 0, side = 0, npi = 0;
+  long long n_lev = 0, n_exp = 0, n_edges = 0, n_new = 0, n_adds = 0;
+
+  // ------------------------------------------------ bb-BFS (Sec. 4)
+  for (int iter = 0; iter <= 2 * WT_MAXD + 2; ++iter) {
+    side = cst[0] <= cst[1] ? 0 : 1;
+    const int f0 = flo[side], fc = fhi[side] - f0;
+    ++n_lev;
+    n_exp += fc;
+    const int32_t* rowp = side == 0 ? G.rp : G.rrp;
+    const int32_t* cols = side == 0 ? G.ci : G.rci;
+    int E = 0;
+    for (int base = 0; base < fc; base += 32) {
+      const int i = base + lane;
+      int deg = 0, rs = 0;
+      if (i < fc) {
+        const int x = S.lnode[f0 + i];
+        rs = __ldg(&rowp[x]);
+        deg = __ldg(&rowp[x + 1]) - rs;
+      }
+      int inc = deg;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += y;
+      }
+      if (i < fc) S.pr[i] = make_int2(E + inc - deg, rs);
+      E += __shfl_sync(FULL, inc, 31);
+    }
+    if (lane == 0) S.pr[fc] = make_int2(E, 0);
+    __syncwarp();
+    n_edges += E;
+    // pass 1: touch test against the other search
+    npi = 0;
+    for (int base = 0; base < E; base += 32) {
+      const int e = base + lane;
+      bool touch = false;
+      int x = 0, y = 0;
+      unsigned long long wgt = 0;
+      if (e < E) {
+        const int p = frontier_pos(S.pr, fc, e);
+        const int2 q = S.pr[p];
+        y = __ldg(&cols[q.y + (e - q.x)]);
+        unsigned long long hy = 0;
+        if (wt_probe(S.hkv, y, &hy) >= 0 && val_side(ent_val<true>(hy)) != side) {
+          touch = true;
+          x = S.lnode[f0 + p];
+          wgt = (S.hkv[S.lpos[f0 + p]] & PK_SIG_MASK) * (hy & PK_SIG_MASK);  // < 2^48: no overflow
+        }
+      }
+      const unsigned m = __ballot_sync(FULL, touch);
+      if (touch) {
+        const int at = npi + __popc(m & lt);
+        if (at < WT_PCAP) {
+          S.pi[at].x = x;
+          S.pi[at].y = y;
+          S.pi[at].w = wgt;
+        }
+      }
+      npi += __popc(m);
+    }
+    if (npi > WT_PCAP) return F_CAP;
+    if (npi > 0) {
+      done = 1;
+      break;
+    }
+    // pass 2: the next level (first discoverer inserts, every discoverer adds sigma)
+    const int dnew = dep[side] + 1;
+    if (dnew > WT_MAXD) return F_CAP;
+    const uint32_t want_val = pack_val(side, dnew);
+    const int list_before = nlist;
+    long long fresh = 0, hits = 0, cost = 0;
+    bool cap = false;
+    for (int base = 0; base < E && !cap; base += 32) {
+      const int e = base + lane;
+      bool ins = false, bad = false;
+      uint32_t ipos = 0;
+      int yy = 0, ydeg = 0;
+      if (e < E) {
+        const int p = frontier_pos(S.pr, fc, e);
+        const int2 q = S.pr[p];
+        const int y = __ldg(&cols[q.y + (e - q.x)]);
+        const int ylo = __ldg(&rowp[y]), yhi = __ldg(&rowp[y + 1]);
+        const unsigned long long add = S.hkv[S.lpos[f0 + p]] & PK_SIG_MASK;
+        uint32_t pos = hash_pos(y, WT_HLOG);
+        int k = 0;
+        for (; k < WT_HSIZE; ++k) {
+          unsigned long long w = S.hkv[pos];
+          if (w == EMPTY) {
+            const unsigned long long old = atomicCAS(&S.hkv[pos], EMPTY, ent_word<true>(y, want_val, add));
+            if (old == EMPTY) {
+              ins = true;
+              ipos = pos;
+              yy = y;
+              ydeg = yhi - ylo;
+              break;
+            }
+            w = old;
+          }
+          if ((int32_t)(w >> 32) == y) {
+            if (ent_val<true>(w) == want_val) {  // also discovered at this level
+              ++hits;
+              const unsigned long long o = atomicAdd(&S.hkv[pos], add);
+              if ((o & PK_SIG_MASK) + add > PK_SIG_MASK) bad = true;  // sigma outgrew the packed field
+            }
+            break;
+          }
+          pos = (pos + 1) & (WT_HSIZE - 1);
+        }
+        if (k == WT_HSIZE) bad = true;  // table full
+      }
+      const unsigned m = __ballot_sync(FULL, ins);
+      if (ins) {
+        const int slot = nlist + __popc(m & lt);
+        if (slot < WT_LCAP) {
+          S.lnode[slot] = yy;
+          S.lpos[slot] = ipos;
+        } else {
+          bad = true;
+        }
+        ++fresh;
+        cost += ydeg;
+      }
+      nlist += __popc(m);
+      if (__any_sync(FULL, bad)) cap = true;
+    }
+    if (cap) return F_CAP;
+    fresh = (long long)warp_sum_u64((unsigned long long)fresh);
+    hits = (long long)warp_sum_u64((unsigned long long)hits);
+    cost = (long long)warp_sum_u64((unsigned long long)cost);
+    if (fresh == 0) {  // frontier exhausted: s and t are not connected
+      done = 2;
+      break;
+    }
+    dep[side] = dnew;
+    flo[side] = list_before;
+    fhi[side] = nlist;
+    cst[side] = cost;
+    n_new += fresh;
+    n_adds += hits;
+    __syncwarp();
+  }
+  if (done == 0) return F_CAP;
+  if (lane == 0) {
+    S.stat[KADABRA_STAT_LEVELS] = n_lev;
+    S.stat[KADABRA_STAT_EXPANDED] = n_exp;
+    S.stat[KADABRA_STAT_EDGES] = n_edges;
+    S.stat[KADABRA_STAT_NEW] = n_new;
+    S.stat[KADABRA_STAT_SIGMA_ADDS] = n_adds;
+    if (done == 1) S.stat[KADABRA_STAT_PI] = npi;
+  }
+  __syncwarp();
+  if (done == 2) return 0;  // disconnected: no hits
+
+  // ------------------------------------------------ candidate-edge choice
+  // Weights sigma_sv * sigma_wt < 2^48 each, at most WT_PCAP of them: the
+  // total fits 64 bits.  Candidates are ranked by (x, y), x on the expanding side.
+  unsigned long long tot = 0;
+  for (int i = lane; i < npi; i += 32) tot += S.pi[i].w;
+  tot = warp_sum_u64(tot);
+  if (lane == 0) {
+    S.stat[KADABRA_STAT_SIGMA_LO] = (long long)(tot & 0xFFFFFFFFull);
+    S.stat[KADABRA_STAT_SIGMA_HI] = (long long)(tot >> 32);
+  }
+  const unsigned long long r = below128(dr(1), tot);
+  int pick = -1;
+  for (int i = lane; i < npi; i += 32) {
+    const unsigned long long ki = ((unsigned long long)(uint32_t)S.pi[i].x << 32) | (uint32_t)S.pi[i].y;
+    const unsigned long long wi = S.pi[i].w;
+    unsigned long long below = 0;
+    for (int q = 0; q < npi; ++q) {
+      const unsigned long long kq = ((unsigned long long)(uint32_t)S.pi[q].x << 32) | (uint32_t)S.pi[q].y;
+      if (kq < ki) below += S.pi[q].w;
+    }
+    if (below <= r && r - below < wi) pick = i;
+  }
+  pick = (int)__reduce_max_sync(FULL, (unsigned)(pick + 1)) - 1;
+  if (pick < 0) return F_INTERNAL;
+  const int cv = side == 0 ? S.pi[pick].x : S.pi[pick].y;
+  const int cw = side == 0 ? S.pi[pick].y : S.pi[pick].x;
+
+  // ------------------------------------------------ backtracking
+  const int dv = dep[0], dw = dep[1];
+  const bool want_path = P.paths != nullptr && out_i >= 0;
+  int32_t* row = want_path ? P.paths + out_i * (int64_t)P.max_len : nullptr;
+  if (lane == 0) {
+    S.stat[KADABRA_STAT_DIST] = dv + 1 + dw;
+    S.stat[KADABRA_STAT_PATH_NODES] = dv + dw + 2;
+    if (want_path) {
+      if (dv < P.max_len) row[dv] = cv;
+      if (dv + 1 < P.max_len) row[dv + 1] = cw;
+    }
+    if (J.counts) {
+      if (dv > 0) atomicAdd(&J.counts[cv], 1u);
+      if (dw > 0) atomicAdd(&J.counts[cw], 1u);
+    }
+  }
+  uint32_t j = 2;
+  long long bts = 0;
+  for (int half = 0; half < 2; ++half) {
+    int x = half == 0 ? cv : cw;
+    int dx = half == 0 ? dv : dw;
+    const int32_t* brow = half == 0 ? G.rrp : G.rp;
+    const int32_t* bcol = half == 0 ? G.rci : G.ci;
+    while (dx > 0) {
+      const uint32_t want = pack_val(half, dx - 1);
+      unsigned long long hx = 0;
+      if (wt_probe(S.hkv, x, &hx) < 0) return F_INTERNAL;
+      const unsigned long long rr = below128(dr(j), hx & PK_SIG_MASK);
+      ++j;
+      const int r0 = __ldg(&brow[x]), deg = __ldg(&brow[x + 1]) - r0;
+      unsigned long long carry = 0;
+      int pk = -1;
+      for (int base = 0; base < deg && pk < 0; base += 32) {
+        const int i = base + lane;
+        unsigned long long w = 0;
+        if (i < deg) {
+          const int y = __ldg(&bcol[r0 + i]);
+          unsigned long long hw = 0;
+          if (wt_probe(S.hkv, y, &hw) >= 0 && ent_val<true>(hw) == want) w = hw & PK_SIG_MASK;
+        }
+        unsigned long long inc = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const unsigned long long v = __shfl_up_sync(FULL, inc, o);
+          if (lane >= o) inc += v;
+        }
+        const bool hit = w != 0 && carry + inc - w <= rr && rr < carry + inc;
+        const unsigned m = __ballot_sync(FULL, hit);
+        if (m) pk = base + __ffs(m) - 1;
+        carry += __shfl_sync(FULL, inc, 31);
+      }
+      if (pk < 0) return F_INTERNAL;
+      const int y = __ldg(&bcol[r0 + pk]);
+      bts += pk + 1;
+      const int dn = dx - 1;
+      if (lane == 0) {
+        if (dn > 0 && J.counts) atomicAdd(&J.counts[y], 1u);
+        if (want_path) {
+          const int at = half == 0 ? dn : (dv + 1) + (dw - dn);
+          if (at < P.max_len) row[at] = y;
+        }
+      }
+      x = y;
+      dx = dn;
+    }
+  }
+  if (lane == 0) S.stat[KADABRA_STAT_BT_SCANNED] = bts;
+  __syncwarp();
+  return 0;
+}
+
+__device__ void wt_flush(const SampleParams& P, WSlot& S) {  // lane 0
+  if (S.tot_job >= 0) {
+    long long* t = P.jobs ? P.jobs[S.tot_job].totals : P.job0.totals;
+    if (t)
+      for (int q = 0; q < KADABRA_NSTAT; ++q)
+        if (S.tot[q]) atomicAdd((unsigned long long*)&t[q], (unsigned long long)S.tot[q]);
+  }
+  for (int q = 0; q < KADABRA_NSTAT; ++q) S.tot[q] = 0;
+}
+
+__global__ void __launch_bounds__(32 * WT_WARPS) k_sample_warp(SampleParams P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  WSlot& S = reinterpret_cast<WSlot*>(smem)[warp_id()];
+  const int lane = lane_id();
+  for (int i = lane; i < WT_HSIZE; i += 32) S.hkv[i] = EMPTY;
+  if (lane == 0) {
+    S.tot_job = -1;
+    for (int q = 0; q < KADABRA_NSTAT; ++q) S.tot[q] = 0;
+  }
+  __syncwarp();
+  const unsigned long long ntotal = P.total_dev ? *P.total_dev : P.total_work;
+  for (;;) {
+    unsigned long long k = 0;
+    if (lane == 0) k = atomicAdd(&P.ctr[Q_NEXT_W], 1ull);
+    k = __shfl_sync(FULL, k, 0);
+    if (k >= ntotal) break;
+    if (lane == 0) {
+      int j = 0;
+      if (P.jobs) {
+        int lo = 0, hi = P.njobs;
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (P.jobs[mid].work_begin <= k)
+            lo = mid;
+          else
+            hi = mid;
+        }
+        j = lo;
+      }
+      if (j != S.tot_job) {
+        wt_flush(P, S);
+        S.tot_job = j;
+      }
+      S.job = P.jobs ? P.jobs[j] : P.job0;
+    }
+    __syncwarp();
+    const uint64_t idx = S.job.first_idx + (k - S.job.work_begin);
+    const int64_t out_i = P.st_out ? (int64_t)k : -1;
+    if (out_i >= 0 && P.paths)
+      for (int q = lane; q < P.max_len; q += 32) P.paths[out_i * (int64_t)P.max_len + q] = -1;
+    __syncwarp();
+    const int fl = run_sample_warp(P, S.job, S, idx, out_i);
+    __syncwarp();
+    if (lane == 0) {
+      if (fl == F_CAP) {
+        if (P.q0)
+          enqueue(P, Q_SIZE_S, P.q0, k);
+        else
+          atomicCAS(P.status, 0, (int)KADABRA_ERR_INTERNAL);
+      } else {
+        const int st = fl ? KADABRA_ERR_INTERNAL : KADABRA_OK;
+        if (st != KADABRA_OK) atomicCAS(P.status, 0, st);
+        for (int q = 0; q < KADABRA_NSTAT; ++q)
+          if (q != KADABRA_STAT_SIGMA_LO && q != KADABRA_STAT_SIGMA_HI && q != KADABRA_STAT_DIST) S.tot[q] += S.stat[q];
+        if (out_i >= 0) {
+          P.st_out[2 * out_i] = S.s;
+          P.st_out[2 * out_i + 1] = S.t;
+          if (P.path_len) P.path_len[out_i] = (int32_t)S.stat[KADABRA_STAT_PATH_NODES];
+          if (P.stats)
+            for (int q = 0; q < KADABRA_NSTAT; ++q) P.stats[out_i * KADABRA_NSTAT + q] = S.stat[q];
+          if (P.sstatus) P.sstatus[out_i] = st;
+        }
+      }
+    }
+    for (int i = lane; i < WT_HSIZE; i += 32) S.hkv[i] = EMPTY;
+    __syncwarp();
+  }
+  if (lane == 0) wt_flush(P, S);
+}
+
+size_t warp_tier_smem_bytes() { return sizeof(WSlot) * WT_WARPS; }
 
 size_t fast_smem_bytes() { return SLayout<FAST_HLOG>::BYTES; }
 size_t small_smem_bytes() { return SLayout<SMALL_HLOG>::BYTES; }
@@ -2065,12 +2496,13 @@ struct Workspace {
   int device = 0, num_sms = 0;
   int32_t max_n = 0;
   int64_t max_m = 0;
-  int grid_fast = 0, grid_big = 0, grid_gm = 0, grid_small = 0;
-  size_t smem_fast = 0, smem_big = 0, smem_small = 0;
+  int grid_fast = 0, grid_big = 0, grid_gm = 0, grid_small = 0, grid_warp = 0;
+  size_t smem_fast = 0, smem_big = 0, smem_small = 0, smem_warp = 0;
   unsigned long long* ctr = nullptr;
   int32_t* status = nullptr;
   unsigned long long* qb = nullptr;  // queue for tier B
   unsigned long long* ql = nullptr;  // queue for tier L
+  unsigned long long* qs = nullptr;  // queue for tier S (fed by tier W)
   uint64_t deferred_cap = 0;
   PiEntry* pi_fast = nullptr;
   PiEntry* pi_gm = nullptr;
@@ -2122,7 +2554,10 @@ struct kadabra_graph {
   void* tk_dev = nullptr;            // TopkJob + TopkOut
   void* tk_stage = nullptr;          // scatter staging: ids, lnL, lnU values
   size_t tk_stage_cap = 0;           // entries
-  int tier_variant = -1;             // tier-S variant chosen by the autotuner (-1: not yet)
+  struct TuneTable {  // autotuned setup by probe size class and allowed set (-1: not yet)
+    int v[14][16];
+    TuneTable() { std::memset(v, 0xFF, sizeof(v)); }
+  } tier_choice;
   uint64_t fingerprint = 0;          // shape and sampled CSR entries (key of the autotuner's cache)
   // device-driven main loop of all-nodes runs (a CUDA graph), built on first use
   cudaGraph_t loop_graph = nullptr;
@@ -2182,6 +2617,10 @@ kadabra_status ensure_ws(Workspace* w, uint64_t deferred_need, int njobs) {
     KCK(cudaFuncSetAttribute(k_sample<0, SMALL_HLOG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->smem_small));
     KCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample<0, SMALL_HLOG>, NT, w->smem_small));
     w->grid_small = w->num_sms * std::max(per_sm, 1);
+    w->smem_warp = warp_tier_smem_bytes();
+    KCK(cudaFuncSetAttribute(k_sample_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->smem_warp));
+    KCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample_warp, 32 * WT_WARPS, w->smem_warp));
+    w->grid_warp = w->num_sms * std::max(per_sm, 1);
     w->smem_big = big_smem_bytes();
     KCK(cudaFuncSetAttribute(k_sample<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->smem_big));
     KCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample<2>, NT, w->smem_big));
@@ -2228,13 +2667,16 @@ kadabra_status ensure_ws(Workspace* w, uint64_t deferred_need, int njobs) {
     KCK(cudaDeviceSynchronize());
     dev_free(w->allocs, w->qb);
     dev_free(w->allocs, w->ql);
-    w->qb = w->ql = nullptr;
+    dev_free(w->allocs, w->qs);
+    w->qb = w->ql = w->qs = nullptr;
     const uint64_t cap = std::max<uint64_t>(deferred_need, 1 << 16);
     void* p;
     KTRY(dev_alloc(w->allocs, &p, sizeof(unsigned long long) * cap));
     w->qb = (unsigned long long*)p;
     KTRY(dev_alloc(w->allocs, &p, sizeof(unsigned long long) * cap));
     w->ql = (unsigned long long*)p;
+    KTRY(dev_alloc(w->allocs, &p, sizeof(unsigned long long) * cap));
+    w->qs = (unsigned long long*)p;
     w->deferred_cap = cap;
   }
   if (njobs > w->jobs_cap) {
@@ -2298,6 +2740,7 @@ SampleParams ws_params(const Workspace* w, uint32_t flags) {
   if (flags & KADABRA_FLAG_GLOBAL_TABLES) P.tier_flags |= TF_SKIP_S | TF_SKIP_B | TF_SKIP_M;
   if (flags & KADABRA_FLAG_MEDIUM_TABLES) P.tier_flags |= TF_SKIP_S | TF_SKIP_B;
   if (flags & KADABRA_FLAG_LARGE_SHARED_TABLES) P.tier_flags |= TF_SKIP_S;
+  if (flags & KADABRA_FLAG_WARP_TIER) P.tier_flags |= TF_WARP;
   return P;
 }
 
@@ -2310,11 +2753,18 @@ SampleParams base_params(kadabra_graph* g) {
 // launches the main sampler grid, then the large-table pass and the
 // n-sized-table pass for the samples queued by the launch before (each exits
 // at once when its queue is empty)
-// variant 1: the small tier-S table (SMALL_HLOG) with one more CTA per SM
+// variant bit 0: the small tier-S table (SMALL_HLOG) with one more CTA per SM
+// variant bit 1: tier W (one warp per sample) first; tier S takes only the
+// samples it queues
 kadabra_status launch_sampler_kernels(Workspace* w, SampleParams P, cudaStream_t st, int variant = 0) {
   P.pi_base = w->pi_fast;
   P.pcap = FAST_PCAP;
-  if (variant == 1)
+  if (((variant & 2) || (P.tier_flags & TF_WARP)) && !(P.tier_flags & TF_SKIP_S)) {
+    P.q0 = w->qs;  // tier W's overflow queue, tier S's input
+    k_sample_warp<<<w->grid_warp, 32 * WT_WARPS, w->smem_warp, st>>>(P);
+    KCK(cudaGetLastError());
+  }
+  if (variant & 1)
     k_sample<0, SMALL_HLOG><<<w->grid_small, NT, w->smem_small, st>>>(P);
   else
     k_sample<0><<<w->grid_fast, NT, w->smem_fast, st>>>(P);
@@ -2579,58 +3029,87 @@ namespace {
 
 
 
-// ---------------------------------------------------------------- tier-S autotuner
-// Picks, per graph, the tier-S table that samples it faster: 2^FAST_HLOG
-// slots at KD_MIN_BLOCKS CTAs per SM, or 2^SMALL_HLOG slots with one more CTA
-// per SM (small visited sets gain from the extra concurrency, large ones lose
-// to more escalations).  Both give identical results, so the choice only
-// changes speed.  It times a probe batch of samples in RNG domain 3 (results
-// discarded) with each, once per graph.  cfg.ctas_per_sm overrides it.
+// ---------------------------------------------------------------- sampler autotuner
+// Picks, per graph, the shared-memory sampler setup that samples it fastest,
+// out of two independent choices: the tier-S table (2^FAST_HLOG slots at
+// KD_MIN_BLOCKS CTAs per SM, or 2^SMALL_HLOG slots with one more CTA per SM)
+// and whether tier W (one warp per sample) runs first.  Small searches gain
+// from more samples in flight, large ones lose to more escalations.  Every
+// setup gives identical results, so the choice only changes speed.  It times
+// a probe batch of samples in RNG domain 3 (results discarded) with each
+// allowed setup, once per graph; cfg.ctas_per_sm and cfg.warp_tier fix either
+// choice.  The probe batch is the run's own batch size K, capped at
+// TUNE_PROBE: small batches are bound by the slowest sample, large ones by
+// throughput, and the two can favour different setups.  A setup other than
+// the default is taken only if it is at least 3% faster.
 constexpr uint64_t TUNE_PROBE = 4096;
 // process-wide: graphs with the same fingerprint, device and flags (a graph
 // loaded again) reuse the probe's choice; a collision could only cost speed
 std::mutex g_tune_mu;
 std::unordered_map<uint64_t, int> g_tune_cache;
 
-kadabra_status tier_variant(kadabra_graph* g, Workspace* w, cudaStream_t st, int32_t requested, int* variant) {
+kadabra_status tier_variant(kadabra_graph* g, Workspace* w, cudaStream_t st, int32_t req_ctas, int32_t req_warp,
+                            uint64_t batch, int* variant) {
+  const uint64_t probe = std::max<uint64_t>(1, std::min<uint64_t>(batch, TUNE_PROBE));
+  const int size_class = probe >= TUNE_PROBE ? 0 : 1 + ceil_log2(probe);  // <= 13
   const int per_default = w->grid_fast / w->num_sms, per_small = w->grid_small / w->num_sms;
-  if (requested != 0) {
-    if (requested == per_default) *variant = 0;
-    else if (requested == per_small) *variant = 1;
-    else
-      return fail(KADABRA_ERR_ARG, "ctas_per_sm must be 0 (autotune), " + std::to_string(per_default) + " or " +
-                                       std::to_string(per_small));
+  unsigned s_ok, w_ok;  // allowed values of variant bit 0 and bit 1
+  if (req_ctas == 0)
+    s_ok = 3;
+  else if (req_ctas == per_default)
+    s_ok = 1;
+  else if (req_ctas == per_small)
+    s_ok = 2;
+  else
+    return fail(KADABRA_ERR_ARG, "ctas_per_sm must be 0 (autotune), " + std::to_string(per_default) + " or " +
+                                     std::to_string(per_small));
+  if (req_warp == 0)
+    w_ok = 3;
+  else if (req_warp == 1)
+    w_ok = 2;
+  else if (req_warp == -1)
+    w_ok = 1;
+  else
+    return fail(KADABRA_ERR_ARG, "warp_tier must be 0 (autotune), 1 (on) or -1 (off)");
+  unsigned allowed = 0;  // bit v: variant v may run
+  for (int v = 0; v < 4; ++v)
+    if ((s_ok >> (v & 1) & 1) && (w_ok >> (v >> 1) & 1)) allowed |= 1u << v;
+  if ((allowed & (allowed - 1)) == 0) {  // one setup: nothing to tune
+    *variant = __builtin_ctz(allowed);
     return KADABRA_OK;
   }
-  if (g->tier_variant >= 0) {
-    *variant = g->tier_variant;
+  int& choice = g->tier_choice.v[size_class][allowed];
+  if (choice >= 0) {
+    *variant = choice;
     return KADABRA_OK;
   }
-  const uint64_t key = g->fingerprint ^ ((uint64_t)g->device << 56) ^ ((uint64_t)g->flags << 48);
+  const uint64_t key = g->fingerprint ^ ((uint64_t)g->device << 56) ^ ((uint64_t)g->flags << 48) ^
+                       ((uint64_t)allowed << 40) ^ ((uint64_t)size_class << 32);
   const bool cached = g->fingerprint != 0;  // graphs of a batch have none
   if (cached) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
-      g->tier_variant = *variant = it->second;
+      choice = *variant = it->second;
       return KADABRA_OK;
     }
   }
-  KTRY(ensure_ws(w, TUNE_PROBE, 1));
+  KTRY(ensure_ws(w, probe, 1));
   SampleParams P = ws_params(w, g->flags);
-  P.total_work = TUNE_PROBE;
+  P.total_work = probe;
   std::memset(&P.job0, 0, sizeof(Job));
   P.job0.g = graph_dev(g);
   P.job0.seed = 0x5EEDu;
   P.job0.domain = 3;
-  P.job0.count = TUNE_PROBE;  // counts and totals null: nothing is recorded
+  P.job0.count = probe;  // counts and totals null: nothing is recorded
   cudaEvent_t e0, e1;
   KCK(cudaEventCreate(&e0));
   KCK(cudaEventCreate(&e1));
-  float best[2] = {1e30f, 1e30f};
+  float best[4] = {1e30f, 1e30f, 1e30f, 1e30f};
   kadabra_status stt = KADABRA_OK;
   for (int rep = 0; rep < 2 && stt == KADABRA_OK; ++rep)
-    for (int v = 0; v < 2 && stt == KADABRA_OK; ++v) {
+    for (int v = 0; v < 4 && stt == KADABRA_OK; ++v) {
+      if (!(allowed >> v & 1)) continue;
       cudaEventRecord(e0, st);
       stt = launch_sampler(w, P, st, v);
       cudaEventRecord(e1, st);
@@ -2645,21 +3124,25 @@ kadabra_status tier_variant(kadabra_graph* g, Workspace* w, cudaStream_t st, int
   int32_t h = 0;  // a probe sample's error (the run reports its own) only ends the tuning
   KCK(cudaMemcpyAsync(&h, w->status, sizeof(h), cudaMemcpyDeviceToHost, st));
   KCK(cudaStreamSynchronize(st));
+  const int first = __builtin_ctz(allowed);  // the default among the allowed setups
+  int pick = first;
   if (h != 0) {
     KCK(cudaMemsetAsync(w->status, 0, sizeof(int32_t), st));
     KCK(cudaStreamSynchronize(st));
-    g->tier_variant = 0;
   } else {
-    g->tier_variant = best[1] < 0.97f * best[0] ? 1 : 0;
+    int fastest = first;
+    for (int v = 0; v < 4; ++v)
+      if ((allowed >> v & 1) && best[v] < best[fastest]) fastest = v;
+    if (best[fastest] < 0.97f * best[first]) pick = fastest;
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    if (cached) g_tune_cache[key] = g->tier_variant;
+    if (cached) g_tune_cache[key] = pick;
   }
-  *variant = g->tier_variant;
+  choice = *variant = pick;
   return KADABRA_OK;
 }
 
 int variant_ctas_per_sm(const Workspace* w, int variant) {
-  return (variant == 1 ? w->grid_small : w->grid_fast) / w->num_sms;
+  return ((variant & 1) ? w->grid_small : w->grid_fast) / w->num_sms;
 }
 
 // ---------------------------------------------------------------- device-driven main loop
@@ -2836,8 +3319,9 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
   } while (0)
   int variant = 0;  // tier-S variant of one-graph runs (several graphs share launches: the default)
   if (G == 1) {
-    KTRY(tier_variant(gs[0], w, st, cfg.ctas_per_sm, &variant));
+    KTRY(tier_variant(gs[0], w, st, cfg.ctas_per_sm, cfg.warp_tier, std::min(S[0].K, S[0].cap), &variant));
     out[0].ctas_per_sm = variant_ctas_per_sm(w, variant);
+    out[0].warp_tier = variant >> 1;
   }
   for (State& s : S) {
     RCK(cudaMemsetAsync(s.g->totals, 0, sizeof(long long) * KADABRA_NSTAT, st));
@@ -2852,7 +3336,12 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
       work += j.count;
     }
     if (work == 0) return KADABRA_OK;
-    SampleParams P = ws_params(w, jobs.size() == 1 ? gs[0]->flags : 0);
+    // one graph: its flags; several share the launch: only the warp tier,
+    // if any of them asks for it (it changes no result)
+    uint32_t fl = G == 1 ? gs[0]->flags : 0;
+    if (G > 1)
+      for (int i = 0; i < G; ++i) fl |= gs[i]->flags & KADABRA_FLAG_WARP_TIER;
+    SampleParams P = ws_params(w, fl);
     P.total_work = work;
     if (jobs.size() == 1) {
       P.job0 = jobs[0];
@@ -3171,8 +3660,9 @@ kadabra_status run_topk(kadabra_graph* g, double lambda, double delta, int32_t k
   RCK(cudaMemsetAsync(g->count0, 0, sizeof(uint32_t) * n, st));
   RCK(cudaMemsetAsync(g->counts, 0, sizeof(uint32_t) * n, st));
   int variant = 0;
-  KTRY(tier_variant(g, w, st, cfg.ctas_per_sm, &variant));
+  KTRY(tier_variant(g, w, st, cfg.ctas_per_sm, cfg.warp_tier, K, &variant));
   r.ctas_per_sm = variant_ctas_per_sm(w, variant);
+  r.warp_tier = variant >> 1;
   auto job = [&](uint32_t domain, uint64_t first, uint64_t count, uint32_t* counts) {
     Job j;
     std::memset(&j, 0, sizeof(j));
@@ -3746,7 +4236,9 @@ kadabra_status srv_round(kadabra_server* S, std::vector<SrvJob*>& act, std::vect
   }
   Workspace* w = S->ws.get();
   KTRY(ensure_ws(w, work, (int)jobs.size()));
-  SampleParams P = ws_params(w, 0);
+  uint32_t fl = 0;  // the warp tier, if any job's graph asks for it (it changes no result)
+  for (SrvJob* J : act) fl |= J->g->flags & KADABRA_FLAG_WARP_TIER;
+  SampleParams P = ws_params(w, fl);
   P.total_work = work;
   if (jobs.size() == 1) {
     P.job0 = jobs[0];
@@ -4220,7 +4712,8 @@ void kadabra_free_graph(kadabra_graph* g) {
 
 kadabra_status kadabra_graph_set_flags(kadabra_graph* g, uint32_t flags) {
   if (!g) return fail(KADABRA_ERR_ARG, "graph is NULL");
-  if (flags & ~(uint32_t)(KADABRA_FLAG_GLOBAL_TABLES | KADABRA_FLAG_MEDIUM_TABLES | KADABRA_FLAG_LARGE_SHARED_TABLES))
+  if (flags & ~(uint32_t)(KADABRA_FLAG_GLOBAL_TABLES | KADABRA_FLAG_MEDIUM_TABLES | KADABRA_FLAG_LARGE_SHARED_TABLES |
+                          KADABRA_FLAG_WARP_TIER))
     return fail(KADABRA_ERR_ARG, "unknown flag");
   g->flags = flags;
   return KADABRA_OK;

@@ -44,6 +44,7 @@ NSTAT = len(STAT_NAMES)
 FLAG_GLOBAL_TABLES = 1
 FLAG_MEDIUM_TABLES = 2
 FLAG_LARGE_SHARED_TABLES = 4
+FLAG_WARP_TIER = 8
 
 
 class KadabraError(RuntimeError):
@@ -55,7 +56,7 @@ class KadabraError(RuntimeError):
 class kadabra_config(C.Structure):
     _fields_ = [
         ("vd", C.c_int64), ("eps", C.c_double), ("check_interval", C.c_uint64),
-        ("stream", C.c_void_p), ("ctas_per_sm", C.c_int32), ("reserved", C.c_int32 * 7),
+        ("stream", C.c_void_p), ("ctas_per_sm", C.c_int32), ("warp_tier", C.c_int32), ("reserved", C.c_int32 * 6),
     ]
 
 
@@ -68,7 +69,7 @@ class kadabra_result(C.Structure):
         ("status", C.c_int32), ("counts", C.c_void_p), ("btilde", C.c_void_p), ("d_counts", C.c_void_p),
         ("d_btilde", C.c_void_p), ("topk", C.c_void_p),
         ("t_submit", C.c_double), ("t_start", C.c_double), ("t_done", C.c_double),
-        ("ctas_per_sm", C.c_int32), ("reserved_out", C.c_int32),
+        ("ctas_per_sm", C.c_int32), ("warp_tier", C.c_int32),
     ]
 
 
@@ -227,12 +228,14 @@ class RunResult:
     btilde: Optional[np.ndarray]
     topk: Optional[np.ndarray] = None
     ctas_per_sm: int = 0
+    warp_tier: int = 0
 
 
 def kadabra_run(g: Graph, lam: float, delta: float, k: int = 0, seed: int = 0, *, vd: int = 0,
                 eps: float = 0.001, check_interval: int = 1000, stream: Optional[int] = None,
                 counts: Optional[np.ndarray] = None, btilde: Optional[np.ndarray] = None,
-                d_counts=None, d_btilde=None, want_host: bool = True, ctas_per_sm: int = 0) -> RunResult:
+                d_counts=None, d_btilde=None, want_host: bool = True, ctas_per_sm: int = 0,
+                warp_tier: int = 0) -> RunResult:
     """Runs KADABRA: all-nodes mode (k = 0), or the k most central nodes
     (k > 0; the ranking's k first nodes come back in `topk`).  Host outputs
     are numpy arrays (allocated here unless given); device outputs are
@@ -244,6 +247,7 @@ def kadabra_run(g: Graph, lam: float, delta: float, k: int = 0, seed: int = 0, *
     cfg.check_interval = check_interval
     cfg.stream = stream
     cfg.ctas_per_sm = ctas_per_sm
+    cfg.warp_tier = warp_tier
     res = kadabra_result()
     if want_host:
         if counts is None:
@@ -265,7 +269,8 @@ def kadabra_run(g: Graph, lam: float, delta: float, k: int = 0, seed: int = 0, *
         topk = topk[:min(k, g.n)]
     return RunResult(res.tau, res.check_interval, res.omega_cap, res.alpha, res.checks, res.vd, res.omega, res.C, res.max_f,
                      res.max_g, np.array(res.totals[:], dtype=np.int64), bool(res.stopped_early),
-                     counts if want_host else None, btilde if want_host else None, topk, res.ctas_per_sm)
+                     counts if want_host else None, btilde if want_host else None, topk, res.ctas_per_sm,
+                     res.warp_tier)
 
 
 def kadabra_serve_configure(budget_bytes: int = 0, max_active: int = 256) -> None:
