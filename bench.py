@@ -48,7 +48,7 @@ METRIC = "paths/sec & time-to-(lambda,delta) per graph, batched vs plain on GPU;
 WORKLOADS = {
     "chung_lu_1m": dict(family="chung_lu", n=1_000_000, beta=2.5, mean_deg=16.0, max_deg=10_000.0, graph_seed=1,
                         lcc=True, lam=0.005, delta=0.1, check_interval=1 << 16,
-                        sampler_dram_bytes=77_256_448 + 5_648_896 + 44_233_472 + 755_712 + 65_536),
+                        sampler_dram_bytes=76_954_368 + 5_679_104 + 45_001_472 + 606_720 + 65_792),
     "erdos_renyi_2k": dict(family="erdos_renyi", n=2000, mean_deg=8.0, graph_seed=1, lcc=True, lam=0.01,
                            delta=0.1, check_interval=1000, sampler_dram_bytes=None),
     "rmat_24": dict(family="rmat", scale=24, edge_factor=16, a=0.57, b=0.19, c=0.19, graph_seed=1, lam=0.0025,
@@ -201,7 +201,8 @@ def run_launches(r, w):
     scatter of ln(1/delta) (2), the main-loop batches, three kernels per
     Alg. 3 test (checks + the final one) and b~."""
     rounds = -(-int(r.tau) // w["check_interval"])
-    sb = sampler_launches_per_batch() * (1 + rounds)
+    spb = sampler_launches_per_batch(r)
+    sb = spb * (1 + rounds)
     if w.get("k"):
         return sb + 2 + 3 + 2 + 3 * (int(r.checks) + 1) + 1
     # one-graph all-nodes runs with more than 4 possible rounds loop on the
@@ -209,14 +210,15 @@ def run_launches(r, w):
     # end kernel; shorter runs take host rounds (batch, then a test if tau < cap)
     cap_rounds = -(-int(r.omega_cap) // w["check_interval"])
     if cap_rounds > 4:
-        return sampler_launches_per_batch() + 3 + (sampler_launches_per_batch() + 3) * rounds + 1 + 1
-    return sampler_launches_per_batch() * (1 + rounds) + 3 + int(r.checks) + 1 + 1
+        return spb + 3 + (spb + 3) * rounds + 1 + 1
+    return spb * (1 + rounds) + 3 + int(r.checks) + 1 + 1
 
 
-def sampler_launches_per_batch():
+def sampler_launches_per_batch(r=None):
     """Kernels of one sampler batch: the shared-memory tier and the two
-    escalation tiers (which exit at once when nothing was queued to them)."""
-    return 3
+    escalation tiers (which exit at once when nothing was queued to them),
+    plus the one-warp-per-sample tier in front when the run used it."""
+    return 3 + (1 if r is not None and getattr(r, "warp_tier", 0) else 0)
 
 
 def cpu_baseline(g, seconds_cap=20.0):
@@ -493,6 +495,47 @@ def run_serving(args, kd, rank, world):
         print(json.dumps(line), flush=True)
 
 
+def run_edge_exponent(args, kd, rank, world):
+    """Edges scanned per sample as a power of m (Sec. 4 theorem; the Sec. 6
+    figure plots alpha = log(m_avg) / log(m) per graph).  For a family of
+    graphs of growing size, 2^16 main-loop samples each on the GPU; m_avg =
+    arcs scanned by the bb-BFS per sample (work counter EDGES).  Prints the
+    per-graph alpha and the least-squares slope of log m_avg against log m:
+    the theorem gives 1/2 + o(1) for degrees with a finite second moment (ER)
+    and (4 - beta)/2 + o(1) for power-law degrees with 2 < beta < 3 (Chung-Lu,
+    beta = 2.5: 0.75).  Not a timing; rank 0 only."""
+    import torch
+    from paper_1604_08553_gb300 import graphgen
+    if rank != 0:
+        return
+    samples = 1 << 16
+    families = {
+        "erdos_renyi_d8": lambda n: graphgen.erdos_renyi(n, 8.0, 1),
+        # natural cutoff of the weights, n^(1/(beta-1)): 10^4 at n = 10^6 as in the Chung-Lu workload
+        "chung_lu_b2.5_d16": lambda n: graphgen.chung_lu(n, 2.5, 16.0, float(n) ** (1 / 1.5), 1),
+    }
+    out = {}
+    for fam, make in families.items():
+        rows = []
+        for lg in range(14, 22):
+            g = make(1 << lg)
+            G = kd.kadabra_load_csr(g)
+            c = torch.zeros(g.n, dtype=torch.int32, device="cuda")
+            t = torch.zeros(kd.NSTAT, dtype=torch.int64, device="cuda")
+            kd.kadabra_sample_batch(G, 1, 0, 0, samples, c, t)
+            kd.kadabra_sync_status(G)
+            G.free()
+            m_avg = int(t[0].item()) / samples
+            rows.append({"n": int(g.n), "m": int(g.m), "m_avg": round(m_avg, 2),
+                         "alpha": round(float(np.log(m_avg) / np.log(g.m)), 4)})
+        x = np.log([r["m"] for r in rows])
+        y = np.log([r["m_avg"] for r in rows])
+        slope = float(np.polyfit(x, y, 1)[0])
+        out[fam] = {"slope": round(slope, 4), "graphs": rows}
+    print(json.dumps({"metric": "edges scanned per sample as m^alpha (bb-BFS, Sec. 4)", "unit": "exponent",
+                      "samples_per_graph": samples, "data": "synthetic", "families": out}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -503,9 +546,11 @@ def main():
     ap.add_argument("--sampler-only", type=int, default=0, metavar="LAUNCHES",
                     help="only time LAUNCHES sampler batches of K samples (for profilers)")
     ap.add_argument("--serve-jobs", type=int, default=0, help="serving workload: jobs (default 2000)")
-    ap.add_argument("--workload", default="chung_lu_1m", choices=[*WORKLOADS, "batched", "serving"],
+    ap.add_argument("--workload", default="chung_lu_1m",
+                    choices=[*WORKLOADS, "batched", "serving", "edge_exponent"],
                     help="one-graph workload (default chung_lu_1m), or batched: 64 uneven Barabasi-Albert graphs, "
-                         "batched run against one-graph-at-a-time runs")
+                         "batched run against one-graph-at-a-time runs, or serving, or edge_exponent: the "
+                         "edges-per-sample exponent diagnostic (no timing)")
     args = ap.parse_args()
     global WORKLOAD
     if args.workload in WORKLOADS:
@@ -530,6 +575,9 @@ def main():
         return
     if args.workload == "serving":
         run_serving(args, kd, rank, world)
+        return
+    if args.workload == "edge_exponent":
+        run_edge_exponent(args, kd, rank, world)
         return
     dist = None
     if world > 1:
