@@ -140,10 +140,19 @@ kadabra_status kadabra_load_csr_device(int32_t n, int64_t m, const int32_t* d_ro
                                        int directed, const int32_t* d_rrow_ptr, const int32_t* d_rcol,
                                        kadabra_graph** out);
 
-/* Releases the graph and all device memory the library allocated for it.
- * Graph views of a batch (kadabra_batch_graph) are released with the batch;
- * passing one here does nothing. */
+/* Releases the graph and the device memory the library allocated for it,
+ * except its sampler workspace (tier tables, queues, scratch; up to about
+ * 1.5 GB for large graphs).  The library keeps one such workspace per device
+ * for the next graph object on that device whose node and arc counts fit in
+ * it, which spares that object the allocation and initialisation.
+ * kadabra_release_cached frees the kept workspaces.  Graph views of a batch
+ * (kadabra_batch_graph) are released with the batch; passing one here does
+ * nothing. */
 void kadabra_free_graph(kadabra_graph* g);
+
+/* Frees the sampler workspaces kept by kadabra_free_graph (all devices).
+ * Call it with no work of the library in flight. */
+void kadabra_release_cached(void);
 
 /* ---------------------------------------------------------------- batches
  * Several graphs sampled together (Alg. 1 for each graph, all graphs' sample

@@ -43,6 +43,7 @@
 #include <memory>
 #include <thread>
 #include <cstdint>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -2360,27 +2361,61 @@ __global__ void k_philox(uint64_t seed, uint32_t domain, uint32_t j, uint64_t fi
 
 // ============================================================== graph checks, VD
 // error bits: 1 offsets, 2 id range, 4 order/duplicate, 8 self-loop, 16 reverse mismatch
-// One warp per node; lanes check the row's entries in parallel.
-__global__ void k_validate_rows(const int32_t* rp, const int32_t* ci, int32_t n, int64_t m, unsigned* err) {
-  const int lane = threadIdx.x & 31;
-  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t v = w0; v < n; v += nw) {
+//
+// The arc checks run arc-parallel: each thread takes LOAD_CHUNK consecutive
+// arcs, finds the row of the first by binary search over the (already
+// validated) offsets and steps through the rows from there.  A hub's row is
+// thus spread over many threads instead of serialising one warp.
+constexpr int LOAD_CHUNK = 16;
+
+// offsets: 0 <= rp[v] <= rp[v+1] <= m (rp[0] = 0 and rp[n] = m are checked on the host)
+__global__ void k_validate_offsets(const int32_t* rp, int32_t n, int64_t m, unsigned* err) {
+  bool bad = false;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     const int32_t a = rp[v], b = rp[v + 1];
-    if (a < 0 || b < a || b > m) {
-      if (lane == 0) atomicOr(err, 1u);
-      continue;
-    }
-    unsigned bits = 0;
-    for (int32_t e = a + lane; e < b; e += 32) {
-      const int32_t y = ci[e];
-      if (y < 0 || y >= n) bits |= 2u;
-      if (e > a && y <= ci[e - 1]) bits |= 4u;
-      if (y == v) bits |= 8u;
-    }
-    bits = __reduce_or_sync(FULL, bits);
-    if (bits && lane == 0) atomicOr(err, bits);
+    if (a < 0 || b < a || b > m) bad = true;
   }
+  if (__any_sync(FULL, bad) && lane_id() == 0) atomicOr(err, 1u);
+}
+
+// the row u that holds arc e: the largest u with rp[u] <= e (rp monotone, e < rp[n])
+__device__ __forceinline__ int32_t row_of_arc(const int32_t* rp, int32_t n, int64_t e) {
+  int32_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int32_t mid = (int32_t)(((int64_t)lo + hi + 1) >> 1);
+    if (rp[mid] <= e)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// Calls f(u, e, v) for every arc e = (u, v) of the thread's chunks.
+template <class F>
+__device__ __forceinline__ void for_each_arc(const int32_t* rp, const int32_t* ci, int32_t n, int64_t m, F f) {
+  const int64_t chunks = (m + LOAD_CHUNK - 1) / LOAD_CHUNK;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < chunks; c += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e0 = c * LOAD_CHUNK, e1 = e0 + LOAD_CHUNK < m ? e0 + LOAD_CHUNK : m;
+    int32_t u = row_of_arc(rp, n, e0);
+    int64_t next = rp[u + 1];
+    for (int64_t e = e0; e < e1; ++e) {
+      while (e >= next) next = rp[++u + 1];
+      f(u, e, ci[e]);
+    }
+  }
+}
+
+// ids in range, rows strictly increasing (sorted, no repeats), no self-loops
+__global__ void k_validate_arcs(const int32_t* rp, const int32_t* ci, int32_t n, int64_t m, unsigned* err) {
+  unsigned bits = 0;
+  for_each_arc(rp, ci, n, m, [&](int32_t u, int64_t e, int32_t v) {
+    if (v < 0 || v >= n) bits |= 2u;
+    if (e > rp[u] && v <= ci[e - 1]) bits |= 4u;
+    if (v == u) bits |= 8u;
+  });
+  bits = __reduce_or_sync(FULL, bits);
+  if (bits && lane_id() == 0) atomicOr(err, bits);
 }
 
 __device__ __forceinline__ bool row_has(const int32_t* rp, const int32_t* ci, int32_t v, int32_t y) {
@@ -2397,54 +2432,102 @@ __device__ __forceinline__ bool row_has(const int32_t* rp, const int32_t* ci, in
   return false;
 }
 
-// every out-arc (u,y) must appear as in-arc of y (directed) or as (y,u)
-// (undirected); one warp per node u
+// Every arc (u, v) of the forward CSR must appear as u in row v of the
+// reverse CSR.  Both hold m arcs with no repeats (rows strictly increasing),
+// so this injection is a bijection and the two CSRs are mirrors.  An
+// undirected graph is its own mirror: there only arcs with u < v are looked
+// up, and the arcs with u < v and u > v are counted (lt_gt[0], lt_gt[1]);
+// equal counts make the injection from the first kind into the second a
+// bijection, which is symmetry.  For a directed graph the same pass counts,
+// per node u, the arcs (u, v) whose reverse arc (v, u) exists (recip[u]),
+// for the degree of u in the underlying undirected graph.
 __global__ void k_validate_mirror(const int32_t* rp, const int32_t* ci, const int32_t* rrp, const int32_t* rci,
-                                  int32_t n, unsigned* err) {
-  const int lane = threadIdx.x & 31;
-  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t u = w0; u < n; u += nw) {
-    bool bad = false;
-    for (int32_t e = rp[u] + lane; e < rp[u + 1]; e += 32)
-      if (!row_has(rrp, rci, ci[e], (int32_t)u)) bad = true;
-    if (__any_sync(FULL, bad) && lane == 0) atomicOr(err, 16u);
+                                  int32_t n, int64_t m, int undirected, unsigned* err, unsigned long long* lt_gt,
+                                  uint32_t* recip) {
+  unsigned long long lt = 0, gt = 0;
+  bool bad = false;
+  int32_t ru = -1;  // the node whose reciprocal arcs are being counted
+  uint32_t rc = 0;
+  for_each_arc(rp, ci, n, m, [&](int32_t u, int64_t, int32_t v) {
+    if (undirected && v < u) {
+      ++gt;
+      return;
+    }
+    ++lt;
+    if (!row_has(rrp, rci, v, u)) bad = true;
+    if (!undirected) {
+      if (u != ru) {
+        if (rc) atomicAdd(&recip[ru], rc);
+        ru = u;
+        rc = 0;
+      }
+      if (row_has(rrp, rci, u, v)) ++rc;
+    }
+  });
+  if (rc) atomicAdd(&recip[ru], rc);
+  if (__any_sync(FULL, bad) && lane_id() == 0) atomicOr(err, 16u);
+  if (undirected) {
+    lt = warp_sum_u64(lt);
+    gt = warp_sum_u64(gt);
+    if (lane_id() == 0) {
+      atomicAdd(&lt_gt[0], lt);
+      atomicAdd(&lt_gt[1], gt);
+    }
   }
 }
 
-__global__ void k_und_degree_key(const int32_t* rp, const int32_t* ci, const int32_t* rrp, const int32_t* rci,
-                                 int32_t n, int directed, unsigned long long* best) {
+// The root of the VD heuristic: the lowest-id node of maximum degree in the
+// underlying undirected graph, |out(v) U in(v)| = out + in - reciprocal arcs
+// (directed), as a key degree << 32 | ~id under atomicMax.
+__global__ void k_und_degree_key(const int32_t* rp, const int32_t* rrp, const uint32_t* recip, int32_t n,
+                                 int directed, unsigned long long* best) {
   unsigned long long mine = 0;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-    int64_t d;
-    if (!directed) {
-      d = rp[v + 1] - rp[v];
-    } else {  // |out(v) U in(v)| by merging the two sorted rows
-      int32_t a = rp[v], ae = rp[v + 1], b = rrp[v], be = rrp[v + 1];
-      d = 0;
-      while (a < ae || b < be) {
-        if (b >= be || (a < ae && ci[a] < rci[b]))
-          ++a;
-        else if (a >= ae || rci[b] < ci[a])
-          ++b;
-        else {
-          ++a;
-          ++b;
-        }
-        ++d;
-      }
-    }
+    int64_t d = rp[v + 1] - rp[v];
+    if (directed) d += (int64_t)(rrp[v + 1] - rrp[v]) - recip[v];
     const unsigned long long key = ((unsigned long long)d << 32) | (0xFFFFFFFFu - (uint32_t)v);
     mine = key > mine ? key : mine;
   }
   atomicMax(best, mine);
 }
 
-// one BFS level over the underlying undirected graph; one warp per frontier node
+// One level of the BFS over the underlying undirected graph (out-rows, and
+// in-rows too for a directed graph).  A warp expands one frontier node's row
+// of up to BFS_CHUNK arcs; a longer row is cut into BFS_CHUNK-arc items for
+// k_bfs_items, so that a hub's row is spread over many warps.
+constexpr int BFS_CHUNK = 1024;
+
+struct BfsItem {
+  int32_t pass, v, begin, end;
+};
+
+// scans arcs [a, b) of row c and appends the newly reached heads to next
+__device__ __forceinline__ void bfs_scan(const int32_t* c, int32_t a, int32_t b, int32_t* next, int32_t* nnext,
+                                         int32_t* dist, int32_t level) {
+  const int lane = lane_id();
+  for (int32_t base = a; base < b; base += 32) {  // bounds uniform in the warp
+    const int32_t e = base + lane;
+    int32_t y = 0;
+    bool mine = false;
+    if (e < b) {
+      y = c[e];
+      mine = dist[y] < 0 && atomicCAS(&dist[y], -1, level + 1) == -1;
+    }
+    // one queue reservation per warp and window, not per node
+    const unsigned got = __ballot_sync(FULL, mine);
+    if (got) {
+      int32_t at = 0;
+      if (lane == 0) at = atomicAdd(nnext, __popc(got));
+      at = __shfl_sync(FULL, at, 0);
+      if (mine) next[at + __popc(got & ((1u << lane) - 1u))] = y;
+    }
+  }
+}
+
 __global__ void k_bfs_level(const int32_t* rp, const int32_t* ci, const int32_t* rrp, const int32_t* rci, int directed,
                             const int32_t* front, int32_t nfront, int32_t* next, int32_t* nnext, int32_t* dist,
-                            int32_t level) {
-  const int lane = threadIdx.x & 31;
+                            int32_t level, BfsItem* items, int32_t* nitems, int32_t items_cap) {
+  const int lane = lane_id();
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = w0; i < nfront; i += nwarps) {
@@ -2452,11 +2535,35 @@ __global__ void k_bfs_level(const int32_t* rp, const int32_t* ci, const int32_t*
     for (int pass = 0; pass < (directed ? 2 : 1); ++pass) {
       const int32_t* r = pass ? rrp : rp;
       const int32_t* c = pass ? rci : ci;
-      for (int32_t e = r[v] + lane; e < r[v + 1]; e += 32) {
-        const int32_t y = c[e];
-        if (dist[y] < 0 && atomicCAS(&dist[y], -1, level + 1) == -1) next[atomicAdd(nnext, 1)] = y;
+      const int32_t a = r[v], b = r[v + 1];
+      if (b - a <= BFS_CHUNK) {
+        bfs_scan(c, a, b, next, nnext, dist, level);
+        continue;
       }
+      const int32_t k = (b - a + BFS_CHUNK - 1) / BFS_CHUNK;  // items of this row
+      int32_t at = 0;
+      if (lane == 0) at = atomicAdd(nitems, k);
+      at = __shfl_sync(FULL, at, 0);
+      for (int32_t q = lane; q < k; q += 32) {
+        if (at + q < items_cap) {
+          const int32_t s = a + q * BFS_CHUNK;
+          items[at + q] = BfsItem{pass, v, s, s + BFS_CHUNK < b ? s + BFS_CHUNK : b};
+        }
+      }
+      if (at + k > items_cap) bfs_scan(c, a + (items_cap > at ? items_cap - at : 0) * BFS_CHUNK, b, next, nnext,
+                                       dist, level);  // items beyond the buffer: this warp scans them
     }
+  }
+}
+
+__global__ void k_bfs_items(const int32_t* ci, const int32_t* rci, const BfsItem* items, const int32_t* nitems,
+                            int32_t items_cap, int32_t* next, int32_t* nnext, int32_t* dist, int32_t level) {
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int32_t k = *nitems < items_cap ? *nitems : items_cap;
+  for (int64_t i = w0; i < k; i += nwarps) {
+    const BfsItem it = items[i];
+    bfs_scan(it.pass ? rci : ci, it.begin, it.end, next, nnext, dist, level);
   }
 }
 
@@ -2902,76 +3009,146 @@ kadabra_status compute_delta_host(int64_t n, const uint32_t* count0, uint64_t al
   return KADABRA_OK;
 }
 
-kadabra_status compute_vd(kadabra_graph* g) {
+// Phase timing of graph loads on stderr when the environment variable
+// KADABRA_TRACE is set (each phase ends with a device synchronisation then).
+struct LoadTrace {
+  bool on;
+  std::chrono::steady_clock::time_point t0;
+  LoadTrace() : on(std::getenv("KADABRA_TRACE") != nullptr), t0(std::chrono::steady_clock::now()) {}
+  void mark(const char* phase) {
+    if (!on) return;
+    cudaDeviceSynchronize();
+    const auto t1 = std::chrono::steady_clock::now();
+    std::fprintf(stderr, "kadabra load: %-18s %8.3f ms\n", phase,
+                 std::chrono::duration<double, std::milli>(t1 - t0).count());
+    t0 = t1;
+  }
+};
+
+// Device scratch of one graph load, one allocation: the check results, the
+// reciprocal-arc counts (directed graphs) and the BFS state.
+struct LoadScratch {
+  unsigned* err;               // [0] error bits
+  unsigned long long* lt_gt;   // the mirror test's two arc counts
+  int32_t* fp;                 // 64 fingerprint entries
+  unsigned long long* best;    // the VD root's key
+  int32_t* cnt;                // [0] next frontier size, [1] BFS items
+  uint32_t* recip;             // n (directed graphs), else null
+  int32_t *dist, *qa, *qb;     // n each
+  BfsItem* items;
+  int32_t items_cap;
+  void* base;
+};
+
+kadabra_status load_scratch(const kadabra_graph* g, LoadScratch* S) {
+  const size_t n = (size_t)g->n;
+  const int64_t cap = std::min<int64_t>((int64_t)1 << 24, 4 * g->m / BFS_CHUNK + 64);
+  S->items_cap = (int32_t)cap;
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t o_head = 0, o_recip = up(1024), o_dist = o_recip + (g->directed ? up(4 * n) : 0);
+  const size_t o_qa = o_dist + up(4 * n), o_qb = o_qa + up(4 * n), o_items = o_qb + up(4 * n);
+  const size_t total = o_items + sizeof(BfsItem) * (size_t)cap;
+  KCK(cudaMalloc(&S->base, total));
+  unsigned char* b = static_cast<unsigned char*>(S->base);
+  S->err = reinterpret_cast<unsigned*>(b + o_head);
+  S->lt_gt = reinterpret_cast<unsigned long long*>(b + o_head + 8);
+  S->best = reinterpret_cast<unsigned long long*>(b + o_head + 24);
+  S->cnt = reinterpret_cast<int32_t*>(b + o_head + 32);
+  S->fp = reinterpret_cast<int32_t*>(b + o_head + 64);
+  S->recip = g->directed ? reinterpret_cast<uint32_t*>(b + o_recip) : nullptr;
+  S->dist = reinterpret_cast<int32_t*>(b + o_dist);
+  S->qa = reinterpret_cast<int32_t*>(b + o_qa);
+  S->qb = reinterpret_cast<int32_t*>(b + o_qb);
+  S->items = reinterpret_cast<BfsItem*>(b + o_items);
+  KCK(cudaMemset(S->base, 0, 64));
+  if (S->recip) KCK(cudaMemset(S->recip, 0, 4 * n));
+  return KADABRA_OK;
+}
+
+// VD heuristic (reading 9): 2 ecc(r) + 1 for the lowest-id node r of maximum
+// degree, eccentricities over the underlying undirected graph.
+kadabra_status compute_vd(kadabra_graph* g, LoadTrace& tr, const LoadScratch& S) {
   const int32_t n = g->n;
   const int32_t* rrp = g->directed ? g->rrp : g->rp;
   const int32_t* rci = g->directed ? g->rci : g->ci;
-  unsigned long long* best;
-  int32_t *dist, *qa, *qb, *cnt;
-  KCK(cudaMalloc(&best, sizeof(unsigned long long)));
-  KCK(cudaMalloc(&dist, sizeof(int32_t) * (size_t)n));
-  KCK(cudaMalloc(&qa, sizeof(int32_t) * (size_t)n));
-  KCK(cudaMalloc(&qb, sizeof(int32_t) * (size_t)n));
-  KCK(cudaMalloc(&cnt, sizeof(int32_t)));
-  kadabra_status st = KADABRA_OK;
-  do {
-    if (cudaMemset(best, 0, sizeof(unsigned long long)) != cudaSuccess) {
-      st = fail(KADABRA_ERR_CUDA, "memset");
-      break;
-    }
-    const int blocks = std::max(1, std::min(4 * g->num_sms, (n + 255) / 256));
-    k_und_degree_key<<<blocks, 256>>>(g->rp, g->ci, rrp, rci, n, g->directed, best);
-    unsigned long long hb = 0;
-    if (cudaMemcpy(&hb, best, sizeof(hb), cudaMemcpyDeviceToHost) != cudaSuccess) {
-      st = fail(KADABRA_ERR_CUDA, std::string("vd: ") + cudaGetErrorString(cudaGetLastError()));
-      break;
-    }
-    const int32_t r = (int32_t)(0xFFFFFFFFu - (uint32_t)(hb & 0xFFFFFFFFull));
-    cudaMemset(dist, 0xFF, sizeof(int32_t) * (size_t)n);
-    const int32_t zero = 0;
-    cudaMemcpy(dist + r, &zero, sizeof(int32_t), cudaMemcpyHostToDevice);
-    cudaMemcpy(qa, &r, sizeof(int32_t), cudaMemcpyHostToDevice);
-    int32_t nfront = 1, level = 0;
-    while (nfront > 0 && level <= n) {
-      cudaMemset(cnt, 0, sizeof(int32_t));
-      const int bl = std::max(1, std::min(8 * g->num_sms, (nfront * 32 + 255) / 256));
-      k_bfs_level<<<bl, 256>>>(g->rp, g->ci, rrp, rci, g->directed, qa, nfront, qb, cnt, dist, level);
-      if (cudaMemcpy(&nfront, cnt, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
-        st = fail(KADABRA_ERR_CUDA, std::string("vd bfs: ") + cudaGetErrorString(cudaGetLastError()));
-        break;
-      }
-      std::swap(qa, qb);
-      if (nfront > 0) ++level;
-    }
-    g->vd = 2 * (int64_t)level + 1;
-  } while (0);
-  cudaFree(best);
-  cudaFree(dist);
-  cudaFree(qa);
-  cudaFree(qb);
-  cudaFree(cnt);
-  return st;
+  const int blocks = std::max(1, std::min(4 * g->num_sms, (n + 255) / 256));
+  k_und_degree_key<<<blocks, 256>>>(g->rp, rrp, S.recip, n, g->directed, S.best);
+  unsigned long long hb = 0;
+  if (cudaMemcpy(&hb, S.best, sizeof(hb), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(KADABRA_ERR_CUDA, std::string("vd: ") + cudaGetErrorString(cudaGetLastError()));
+  const int32_t r = (int32_t)(0xFFFFFFFFu - (uint32_t)(hb & 0xFFFFFFFFull));
+  KCK(cudaMemset(S.dist, 0xFF, sizeof(int32_t) * (size_t)n));
+  const int32_t zero = 0;
+  KCK(cudaMemcpy(S.dist + r, &zero, sizeof(int32_t), cudaMemcpyHostToDevice));
+  KCK(cudaMemcpy(S.qa, &r, sizeof(int32_t), cudaMemcpyHostToDevice));
+  tr.mark("vd root");
+  int32_t *qa = S.qa, *qb = S.qb;
+  int32_t nfront = 1, level = 0;
+  while (nfront > 0 && level <= n) {
+    KCK(cudaMemsetAsync(S.cnt, 0, 2 * sizeof(int32_t)));
+    const int bl = std::max(1, std::min(8 * g->num_sms, (int)std::min<int64_t>(((int64_t)nfront * 32 + 255) / 256,
+                                                                                 1 << 30)));
+    k_bfs_level<<<bl, 256>>>(g->rp, g->ci, rrp, rci, g->directed, qa, nfront, qb, S.cnt, S.dist, level, S.items,
+                             S.cnt + 1, S.items_cap);
+    k_bfs_items<<<8 * g->num_sms, 256>>>(g->ci, rci, S.items, S.cnt + 1, S.items_cap, qb, S.cnt, S.dist, level);
+    if (cudaMemcpy(&nfront, S.cnt, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(KADABRA_ERR_CUDA, std::string("vd bfs: ") + cudaGetErrorString(cudaGetLastError()));
+    std::swap(qa, qb);
+    if (nfront > 0) ++level;
+  }
+  g->vd = 2 * (int64_t)level + 1;
+  tr.mark("vd bfs");
+  return KADABRA_OK;
 }
 
+// Validates a device CSR (offsets, ids, order, self-loops, mirror/symmetry),
+// takes its fingerprint and computes the VD heuristic.
 kadabra_status finish_load(kadabra_graph* g) {
-  unsigned* err;
-  KCK(cudaMalloc(&err, sizeof(unsigned) * 65));
-  KCK(cudaMemset(err, 0, sizeof(unsigned)));
-  const int blocks = std::max(1, std::min(16 * g->num_sms, (g->n + 7) / 8));
-  k_validate_rows<<<blocks, 256>>>(g->rp, g->ci, g->n, g->m, err);
-  if (g->directed) k_validate_rows<<<blocks, 256>>>(g->rrp, g->rci, g->n, g->m, err);
+  LoadTrace tr;
+  LoadScratch S;
+  KTRY(load_scratch(g, &S));
+  tr.mark("scratch");
+  const int32_t n = g->n;
+  const int64_t m = g->m;
+  const int bn = std::max(1, std::min(16 * g->num_sms, (n + 255) / 256));
+  const int ba = (int)std::max<int64_t>(1, std::min<int64_t>(16 * g->num_sms, ((m + LOAD_CHUNK - 1) / LOAD_CHUNK + 255) / 256));
+  const int32_t* rrp = g->directed ? g->rrp : g->rp;
+  const int32_t* rci = g->directed ? g->rci : g->ci;
   unsigned h = 0;
-  KCK(cudaMemcpy(&h, err, sizeof(unsigned), cudaMemcpyDeviceToHost));
-  if (!h) {
-    const int32_t* rrp = g->directed ? g->rrp : g->rp;
-    const int32_t* rci = g->directed ? g->rci : g->ci;
-    k_validate_mirror<<<blocks, 256>>>(g->rp, g->ci, rrp, rci, g->n, err);
-    KCK(cudaMemcpy(&h, err, sizeof(unsigned), cudaMemcpyDeviceToHost));
-  }
-  if (!h) {  // fingerprint: FNV-1a over the shape and 64 sampled entries
+  kadabra_status st = KADABRA_OK;
+  do {
+    k_validate_offsets<<<bn, 256>>>(g->rp, n, m, S.err);
+    if (g->directed) k_validate_offsets<<<bn, 256>>>(g->rrp, n, m, S.err);
+    if (cudaMemcpy(&h, S.err, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      st = fail(KADABRA_ERR_CUDA, "CSR check");
+      break;
+    }
+    if (h) break;  // the arc checks need valid offsets
+    k_validate_arcs<<<ba, 256>>>(g->rp, g->ci, n, m, S.err);
+    if (g->directed) k_validate_arcs<<<ba, 256>>>(g->rrp, g->rci, n, m, S.err);
+    if (cudaMemcpy(&h, S.err, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      st = fail(KADABRA_ERR_CUDA, "CSR check");
+      break;
+    }
+    tr.mark("validate rows");
+    if (h) break;  // the mirror test needs ids in range and sorted rows
+    k_validate_mirror<<<ba, 256>>>(g->rp, g->ci, rrp, rci, n, m, g->directed ? 0 : 1, S.err, S.lt_gt, S.recip);
+    unsigned long long c[2] = {0, 0};
+    if (cudaMemcpy(&h, S.err, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(c, S.lt_gt, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      st = fail(KADABRA_ERR_CUDA, "CSR check");
+      break;
+    }
+    if (!g->directed && c[0] != c[1]) h |= 16u;
+    tr.mark("validate mirror");
+    if (h) break;
+    // fingerprint: FNV-1a over the shape and 64 sampled entries
     int32_t fp[64];
-    k_fingerprint<<<1, 64>>>(g->rp, g->ci, g->n, g->m, reinterpret_cast<int32_t*>(err + 1));
-    KCK(cudaMemcpy(fp, err + 1, sizeof(fp), cudaMemcpyDeviceToHost));
+    k_fingerprint<<<1, 64>>>(g->rp, g->ci, n, m, S.fp);
+    if (cudaMemcpy(fp, S.fp, sizeof(fp), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      st = fail(KADABRA_ERR_CUDA, "fingerprint");
+      break;
+    }
     uint64_t x = 1469598103934665603ull;
     auto mix = [&](uint64_t v) {
       for (int b = 0; b < 8; ++b) {
@@ -2979,13 +3156,17 @@ kadabra_status finish_load(kadabra_graph* g) {
         x *= 1099511628211ull;
       }
     };
-    mix((uint64_t)g->n);
-    mix((uint64_t)g->m);
+    mix((uint64_t)n);
+    mix((uint64_t)m);
     mix((uint64_t)g->directed);
     for (int i = 0; i < 64; ++i) mix((uint64_t)(uint32_t)fp[i]);
     g->fingerprint = x;
-  }
-  cudaFree(err);
+    tr.mark("fingerprint");
+    st = compute_vd(g, tr, S);
+  } while (0);
+  cudaFree(S.base);
+  tr.mark("scratch free");
+  if (st != KADABRA_OK) return st;
   if (h) {
     std::string why;
     if (h & 1) why += " bad row offsets;";
@@ -2995,7 +3176,65 @@ kadabra_status finish_load(kadabra_graph* g) {
     if (h & 16) why += (g->directed ? " reverse CSR does not mirror the forward CSR;" : " adjacency not symmetric;");
     return fail(KADABRA_ERR_CSR, "invalid CSR:" + why);
   }
-  return compute_vd(g);
+  return KADABRA_OK;
+}
+
+// Idle workspaces of freed graph objects, at most one per device.  The next
+// graph object on that device takes it if it fits (its tables are sized for
+// up to max_n nodes and max_m arcs), which spares the allocation and the
+// table initialisation (about a millisecond for a 10^6-node graph) and the
+// matching frees.  kadabra_release_cached frees them.
+std::mutex g_ws_pool_mu;
+std::vector<Workspace*> g_ws_pool;
+
+Workspace* ws_acquire(int device, int num_sms, int32_t n, int64_t m) {
+  Workspace* w = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_ws_pool_mu);
+    for (size_t i = 0; i < g_ws_pool.size(); ++i)
+      if (g_ws_pool[i]->device == device && g_ws_pool[i]->max_n >= n && g_ws_pool[i]->max_m >= m) {
+        w = g_ws_pool[i];
+        g_ws_pool.erase(g_ws_pool.begin() + (std::ptrdiff_t)i);
+        break;
+      }
+  }
+  if (w) {
+    // a stale error of the previous owner must not reach the new one
+    if (w->ready && cudaMemset(w->status, 0, sizeof(int32_t)) != cudaSuccess) {
+      delete w;
+      w = nullptr;
+    } else {
+      return w;
+    }
+  }
+  w = new Workspace;
+  w->device = device;
+  w->num_sms = num_sms;
+  w->max_n = n;
+  w->max_m = m;
+  return w;
+}
+
+// Takes back the workspace of a freed graph object (no work in flight on it).
+void ws_release(Workspace* w) {
+  Workspace* drop = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_ws_pool_mu);
+    bool placed = false;
+    for (Workspace*& p : g_ws_pool)
+      if (p->device == w->device) {  // keep the one that fits more graphs
+        if (w->max_n >= p->max_n && w->max_m >= p->max_m) {
+          drop = p;
+          p = w;
+        } else {
+          drop = w;
+        }
+        placed = true;
+        break;
+      }
+    if (!placed) g_ws_pool.push_back(w);
+  }
+  delete drop;
 }
 
 kadabra_status new_graph(int32_t n, int64_t m, int directed, kadabra_graph** out, kadabra_graph** g_out) {
@@ -3012,11 +3251,7 @@ kadabra_status new_graph(int32_t n, int64_t m, int directed, kadabra_graph** out
     delete g;
     return fail(KADABRA_ERR_CUDA, "no CUDA device");
   }
-  g->ws = new Workspace;
-  g->ws->device = g->device;
-  g->ws->num_sms = g->num_sms;
-  g->ws->max_n = n;
-  g->ws->max_m = m;
+  g->ws = ws_acquire(g->device, g->num_sms, n, m);
   g->owns_ws = true;
   *g_out = g;
   return KADABRA_OK;
@@ -4706,8 +4941,20 @@ void kadabra_free_graph(kadabra_graph* g) {
   cudaDeviceSynchronize();
   for (void* p : g->allocs)
     if (p) cudaFree(p);
-  if (g->owns_ws) delete g->ws;
+  if (g->owns_ws) ws_release(g->ws);
   delete g;
+}
+
+void kadabra_release_cached(void) {
+  std::vector<Workspace*> all;
+  {
+    std::lock_guard<std::mutex> lk(g_ws_pool_mu);
+    all.swap(g_ws_pool);
+  }
+  for (Workspace* w : all) {
+    cudaSetDevice(w->device);
+    delete w;
+  }
 }
 
 kadabra_status kadabra_graph_set_flags(kadabra_graph* g, uint32_t flags) {

@@ -134,6 +134,8 @@ def load_library():
         lib.kadabra_l2_read_probe.restype = st
         lib.kadabra_serve_shutdown.argtypes = []
         lib.kadabra_serve_shutdown.restype = None
+        lib.kadabra_release_cached.argtypes = []
+        lib.kadabra_release_cached.restype = None
         _lib = lib
         return lib
 
@@ -331,6 +333,11 @@ def kadabra_l2_read_probe(nbytes: int = 32 << 20, reps: int = 50) -> float:
 
 def kadabra_serve_shutdown() -> None:
     load_library().kadabra_serve_shutdown()
+
+
+def kadabra_release_cached() -> None:
+    """Frees the sampler workspaces the library keeps for reuse after kadabra_free_graph."""
+    load_library().kadabra_release_cached()
 
 
 def kadabra_sample_batch(g: Graph, seed: int, domain: int, first_idx: int, count: int, d_counts,

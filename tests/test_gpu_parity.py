@@ -215,8 +215,19 @@ def test_invalid_csr_rejected(kd, gg):
         "self-loop": CSR(3, i32([0, 2, 3, 4]), i32([0, 1, 0, 1])),
         "id out of range": CSR(3, i32([0, 1, 3, 4]), i32([1, 0, 7, 1])),
         "asymmetric": CSR(3, i32([0, 1, 2, 2]), i32([1, 2])),
+        # every arc u -> v with u < v has its mirror, but 2 -> 0 has none
+        "asymmetric descending": CSR(3, i32([0, 1, 2, 3]), i32([1, 0, 0])),
         "duplicate": CSR(3, i32([0, 2, 3, 4]), i32([1, 1, 0, 1])),
     }
+    # a large symmetric graph with one arc v -> u (v > u) removed
+    er = gg.erdos_renyi(2000, 8.0, 1)
+    v = er.n - 1
+    a0, a1 = int(er.row_ptr[v]), int(er.row_ptr[v + 1])
+    assert int(er.col[a0]) < v
+    col = np.delete(er.col, a0)
+    rp = er.row_ptr.copy()
+    rp[v + 1:] -= 1
+    cases["asymmetric large"] = CSR(er.n, rp, col)
     for name, b in cases.items():
         with pytest.raises(kd.KadabraError) as e:
             kd.kadabra_load_csr(b)
@@ -227,6 +238,76 @@ def test_invalid_csr_rejected(kd, gg):
     with pytest.raises(kd.KadabraError) as e:
         kd.kadabra_load_csr(d)
     assert e.value.status == kd.ERR_CSR
+
+
+def test_vd_with_hub_rows_matches_oracle(kd, orc, gg):
+    """The VD heuristic's root and BFS on graphs whose rows exceed the BFS's
+    per-warp chunk (hubs of degree > 1024, split into work items), directed
+    graphs with and without reciprocal arcs (undirected degree = out + in -
+    reciprocal), and a graph with empty rows."""
+    rng = np.random.default_rng(5)
+    n = 6000
+    arcs = {(0, v) for v in range(1, n)} | {(v, 0) for v in range(1, n, 3)}  # hub 0, partly reciprocal
+    arcs |= {(int(a), int(b)) for a, b in rng.integers(1, n, size=(8000, 2)) if a != b}
+    cases = [
+        ("star5000", gg.star_graph(5000)),
+        ("ba20000", gg.barabasi_albert(20000, 5, 3)),
+        ("rmat14", gg.rmat(14, 16, 0.57, 0.19, 0.19, 2)),
+        ("directed hub", gg.from_edges(n, sorted(arcs), directed=True)),
+        ("isolated nodes", gg.from_edges(50, [(1, 2), (2, 3), (10, 11)])),
+    ]
+    for name, g in cases:
+        G = kd.kadabra_load_csr(g)
+        try:
+            assert G.vd == orc.vd_heuristic(g), name
+        finally:
+            G.free()
+
+
+def test_workspace_reuse_across_graph_objects(kd, orc, gg, er2000):
+    """A freed graph object's sampler workspace serves the next one that fits
+    in it: results stay identical to the oracle, an error left in the
+    workspace does not reach the next owner, and releasing the kept
+    workspaces changes nothing."""
+    import torch
+    big = gg.barabasi_albert(20000, 5, 3)
+    G = kd.kadabra_load_csr(big)
+    kd.kadabra_run(G, 0.02, 0.1, 0, 5, check_interval=1000)
+    G.free()
+    G = kd.kadabra_load_csr(er2000)  # smaller: takes the kept workspace
+    try:
+        got = kd.kadabra_sample_paths(G, 3, 0, 0, 2000)
+        r1 = kd.kadabra_run(G, 0.02, 0.1, 0, 9, check_interval=500)
+    finally:
+        G.free()
+    assert_samples_equal(got, orc.sample_paths(er2000, 3, 0, 0, 2000), "reused workspace")
+    ref = orc.run(er2000, 0.02, 0.1, 9, 500)
+    assert r1.tau == ref.tau and np.array_equal(r1.counts, ref.counts)
+    # a sigma overflow left unread in the workspace (no status sync before the free)
+    k = 80
+    edges = []
+    for i in range(k):
+        a, b, c, d = 3 * i, 3 * i + 1, 3 * i + 2, 3 * i + 3
+        edges += [(a, b), (a, c), (b, d), (c, d)]
+    dia = gg.from_edges(3 * k + 1, edges)
+    G = kd.kadabra_load_csr(dia)
+    c = torch.zeros(dia.n, dtype=torch.int32, device="cuda")
+    t = torch.zeros(kd.NSTAT, dtype=torch.int64, device="cuda")
+    kd.kadabra_sample_batch(G, 5, 0, 0, 3000, c, t)
+    G.free()
+    G = kd.kadabra_load_csr(er2000)
+    try:
+        r2 = kd.kadabra_run(G, 0.02, 0.1, 0, 9, check_interval=500)
+    finally:
+        G.free()
+    assert r2.tau == r1.tau and np.array_equal(r2.counts, r1.counts)
+    kd.kadabra_release_cached()
+    G = kd.kadabra_load_csr(er2000)
+    try:
+        r3 = kd.kadabra_run(G, 0.02, 0.1, 0, 9, check_interval=500)
+    finally:
+        G.free()
+    assert r3.tau == r1.tau and np.array_equal(r3.counts, r1.counts)
 
 
 # ------------------------------------------------------------------ stop test
