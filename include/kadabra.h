@@ -246,12 +246,19 @@ kadabra_status kadabra_graph_info(const kadabra_graph* g, int32_t* n, int64_t* m
  * 128 candidate edges), in every entry point that takes the graph object;
  * a batch or serving launch shared by several graphs runs that tier first if
  * any of them has the flag (and ignores their other flags).  It has no effect
- * together with one of the three flags above.  Returns KADABRA_ERR_ARG for unknown bits. */
+ * together with one of the three flags above.  KADABRA_FLAG_ASYNC_SCAN makes
+ * the level scans of the 4096- and 8192-slot shared-memory tables keep more
+ * arc loads in flight (asynchronous copies through shared memory).  The
+ * library does this by itself for graphs whose CSR (forward plus reverse)
+ * exceeds the device's L2, where those loads wait on HBM; the flag asks for it
+ * on any graph, and a shared launch takes it from any of its graphs.  No flag
+ * changes a result.  Returns KADABRA_ERR_ARG for unknown bits. */
 enum {
   KADABRA_FLAG_GLOBAL_TABLES = 1,
   KADABRA_FLAG_MEDIUM_TABLES = 2,
   KADABRA_FLAG_LARGE_SHARED_TABLES = 4,
-  KADABRA_FLAG_WARP_TIER = 8
+  KADABRA_FLAG_WARP_TIER = 8,
+  KADABRA_FLAG_ASYNC_SCAN = 16
 };
 kadabra_status kadabra_graph_set_flags(kadabra_graph* g, uint32_t flags);
 

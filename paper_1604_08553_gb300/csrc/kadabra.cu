@@ -72,6 +72,7 @@ namespace {
 constexpr int NT = KD_NT;          // threads per sampler CTA
 constexpr int NW = NT / 32;        // warps per sampler CTA
 constexpr int U = KD_U;            // independent items per thread per step (memory-level parallelism)
+constexpr int RING = 4;            // arc windows in flight per warp in the level scans (async copies)
 // Tiers of per-sample tables.  A sample starts in a small shared-memory
 // table (tier S, main launch, several CTAs per SM).  If it outgrows it, it is
 // queued for a second launch with one CTA per SM and a large shared-memory
@@ -343,6 +344,8 @@ struct Ctl {
   int cv, cw;     // chosen candidate edge (v on the s side, w on the t side)
   unsigned long long cur;
   unsigned long long ntotal;
+  // the level scans' async-copy ring: per warp RING windows of 32 heads
+  int ring[NW][RING][32];
   // weighted radix selection (block_pick_radix)
   unsigned long long rhist[256];
   unsigned rcnt[256];
@@ -515,16 +518,30 @@ __device__ __forceinline__ int block_pick(int N, unsigned long long r, Ctl& c, W
 }
 
 // ============================================================== one sample
-// Scans the arcs of the current frontier level: each warp takes a contiguous
-// slice of the flattened arc range and walks it in windows of 32 arcs, U
-// windows at a time so their loads overlap.  For every window position it
-// calls f(k, ok, p, y): ok = the lane holds an arc, p = frontier position of
-// its tail, y = its head.  All lanes of the warp call f together, in
-// increasing arc order (so f may use warp collectives).  The warp keeps the
-// frontier row of its current window in registers; only lanes whose arc
-// lies in a later row search the frontier prefix.
+// 4-byte asynchronous global -> shared copies (cp.async, sm_80 and later):
+// the loads of several windows stay in flight without holding registers.
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// The level scan for graphs whose CSR stays in L2: each warp takes a
+// contiguous slice of the flattened arc range and walks it in windows of 32
+// arcs, U windows at a time so their loads overlap (in registers; deeper
+// pipelining through shared memory costs more per window than the shorter
+// L2 latency gains).  For every window position it calls f(k, ok, p, y): ok =
+// the lane holds an arc, p = frontier position of its tail, y = its head.
+// All lanes of the warp call f together, in increasing arc order (so f may
+// use warp collectives).  The warp keeps the frontier row of its current
+// window in registers; only lanes whose arc lies in a later row search the
+// frontier prefix.
 template <class F>
-__device__ __forceinline__ void scan_level(const Tables& T, int fcount, int E, const int32_t* cols, F f) {
+__device__ __forceinline__ void scan_level_regs(const Tables& T, int fcount, int E, const int32_t* cols, F f) {
   const int lane = lane_id(), wid = warp_id();
   const int per = (E + NW - 1) / NW;
   const int c0 = min(E, wid * per), c1 = min(E, c0 + per);
@@ -563,6 +580,78 @@ __device__ __forceinline__ void scan_level(const Tables& T, int fcount, int E, c
 #pragma unroll
     for (int k = 0; k < U; ++k) f(k, oks[k], ps[k], ys[k]);
   }
+}
+
+// The level scan for graphs whose CSR does not fit in L2 (its loads wait on
+// HBM): each warp takes a contiguous slice of the flattened arc range and
+// walks it in windows of 32 arcs.  The heads of the next RING - 1 windows are copied asynchronously into the
+// warp's ring in shared memory while the current window is processed (each
+// lane copies and later reads its own entries, so its own wait orders
+// them).  For every window position it calls f(k, ok, p, y): ok = the lane
+// holds an arc, p = frontier position of its tail, y = its head.  All lanes
+// of the warp call f together, in increasing arc order (so f may use warp
+// collectives).  Two cursors (issue, process) keep the frontier row of their
+// window in registers; only lanes whose arc lies in a later row search the
+// frontier prefix.
+template <class F>
+__device__ __forceinline__ void scan_level_ring(const Tables& T, Ctl& c, int fcount, int E, const int32_t* cols, F f) {
+  const int lane = lane_id(), wid = warp_id();
+  const int per = (E + NW - 1) / NW;
+  const int c0 = min(E, wid * per), c1 = min(E, c0 + per);
+  if (c0 >= c1) return;
+  int* ring = &c.ring[wid][0][0];
+  const int nwin = (c1 - c0 + 31) >> 5;
+  int ip = frontier_pos(T.pr, fcount, c0);  // issue cursor (warp-uniform)
+  int2 icur = T.pr[ip];                      // {first arc index, row start}
+  int inxt = T.pr[ip + 1].x;                 // first arc index of the next row
+  int pp = ip, pnxt = inxt;                  // process cursor
+  auto issue = [&](int w) {
+    if (w < nwin) {
+      const int wb = c0 + 32 * w;
+      if (inxt <= wb) {  // the window starts in a later row
+        ip = ip + 1 + frontier_pos(T.pr + ip + 1, fcount - ip - 1, wb);
+        icur = T.pr[ip];
+        inxt = T.pr[ip + 1].x;
+      }
+      const int e = wb + lane;
+      if (e < c1) {
+        int2 q = icur;
+        if (e >= inxt) q = T.pr[ip + 1 + frontier_pos(T.pr + ip + 1, fcount - ip - 1, e)];
+        cp_async4(&ring[(w % RING) * 32 + lane], &cols[q.y + (e - q.x)]);
+      }
+    }
+    cp_async_commit();  // one group per window (empty past the end): uniform counts
+  };
+#pragma unroll
+  for (int w = 0; w < RING - 1; ++w) issue(w);
+  for (int w = 0; w < nwin; ++w) {
+    __syncwarp();              // the slot's last read (previous window) before its refill
+    issue(w + RING - 1);       // into the slot processed one step ago
+    cp_async_wait<RING - 1>();  // window w has landed
+    const int wb = c0 + 32 * w;
+    if (pnxt <= wb) {
+      pp = pp + 1 + frontier_pos(T.pr + pp + 1, fcount - pp - 1, wb);
+      pnxt = T.pr[pp + 1].x;
+    }
+    const int e = wb + lane;
+    bool ok = false;
+    int p = 0, y = 0;
+    if (e < c1) {
+      p = e >= pnxt ? pp + 1 + frontier_pos(T.pr + pp + 1, fcount - pp - 1, e) : pp;
+      y = ring[(w % RING) * 32 + lane];
+      ok = true;
+    }
+    f(0, ok, p, y);
+  }
+  cp_async_wait<0>();  // nothing left in flight (only empty groups remain)
+}
+
+template <bool RG, class F>
+__device__ __forceinline__ void scan_level(const Tables& T, Ctl& c, int fcount, int E, const int32_t* cols, F f) {
+  if constexpr (RG)
+    scan_level_ring(T, c, fcount, E, cols, f);
+  else
+    scan_level_regs(T, fcount, E, cols, f);
 }
 
 // Weighted choice among n items held in any order, in the order of their
@@ -679,7 +768,7 @@ __device__ int block_pick_radix(const PiEntry* buf, int n, unsigned long long r,
 
 // All threads of the CTA call this with the same idx.  Flags in c.flags tell
 // the caller what happened; the caller resets the tables afterwards.
-template <bool PK>
+template <bool PK, bool RG = false>
 __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, const Tables& T, Ctl& c, uint64_t idx,
                                            int64_t out_i) {
   const int tid = threadIdx.x, lane = lane_id(), wid = warp_id();
@@ -775,7 +864,7 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
       int npi = 0;
       bool sigma_of = false;
       PiEntry* seg = T.pi + (size_t)wid * T.pcap;
-      scan_level(T, fcount, E, cols, [&](int, bool ok, int p, int y) {
+      scan_level<RG>(T, c, fcount, E, cols, [&](int, bool ok, int p, int y) {
         bool touch = false;
         unsigned long long wgt = 0;
         if (ok) {
@@ -846,7 +935,7 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
       bool of = false, cap = false;
       const uint32_t want_val = pack_val(side, dnew);
       const volatile int* nlist_now = &c.nlist;
-      scan_level(T, fcount, E, cols, [&](int, bool ok, int p, int y) {
+      scan_level<RG>(T, c, fcount, E, cols, [&](int, bool ok, int p, int y) {
         if (!ok || cap) return;
         // the head's row bounds (its degree joins the new frontier's cost if
         // it is new), loaded before the probe so the load overlaps it
@@ -1252,6 +1341,7 @@ constexpr int TF_SKIP_S = 1;
 constexpr int TF_SKIP_B = 2;
 constexpr int TF_SKIP_M = 4;
 constexpr int TF_WARP = 8;  // tier W first, whatever the launch's variant
+constexpr int TF_RING = 16;  // level scans through the async-copy ring (tiers S and B)
 
 // queue counters in SampleParams::ctr
 constexpr int Q_NEXT_A = 0;   // next sample index of the batch
@@ -1318,8 +1408,9 @@ __device__ void clear_path_row(const SampleParams& P, int64_t out_i) {
 // MODE 1: the tier-L queue, on tier L.
 // SHL: the tier-S table size (2^SHL slots) of MODE 0; the small variant fits
 // one more CTA per SM and gives the same results (samples that outgrow it go
-// on to tier B as usual).
-template <int MODE, int SHL = FAST_HLOG>
+// on to tier B as usual).  RG: the level scans keep more loads in flight
+// through an async-copy ring (for graphs whose CSR exceeds L2); same results.
+template <int MODE, int SHL = FAST_HLOG, bool RG = false>
 __global__ void __launch_bounds__(NT, SHL == FAST_HLOG ? KD_MIN_BLOCKS : KD_MIN_BLOCKS + 1) k_sample(SampleParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   Ctl& c = *reinterpret_cast<Ctl*>(smem);
@@ -1381,7 +1472,7 @@ __global__ void __launch_bounds__(NT, SHL == FAST_HLOG ? KD_MIN_BLOCKS : KD_MIN_
     if (MODE == 0) {
       if (!(P.tier_flags & TF_SKIP_S)) {
         clear_path_row(P, out_i);
-        run_sample<true>(P, c.job, TS, c, idx, out_i);
+        run_sample<true, RG>(P, c.job, TS, c, idx, out_i);
         __syncthreads();
         done = c.flags != F_CAP;
         reset_tables<true>(TS, c, true);
@@ -1394,7 +1485,7 @@ __global__ void __launch_bounds__(NT, SHL == FAST_HLOG ? KD_MIN_BLOCKS : KD_MIN_
     } else if (MODE == 2) {
       if (!(P.tier_flags & TF_SKIP_B)) {
         clear_path_row(P, out_i);
-        run_sample<true>(P, c.job, TS, c, idx, out_i);
+        run_sample<true, RG>(P, c.job, TS, c, idx, out_i);
         __syncthreads();
         done = c.flags != F_CAP;
         reset_tables<true>(TS, c, true);
@@ -2642,6 +2733,7 @@ struct kadabra_graph {
   int directed = 0;
   int32_t *rp = nullptr, *ci = nullptr, *rrp = nullptr, *rci = nullptr;
   int64_t vd = 0;
+  bool csr_beyond_l2 = false;  // forward (+ reverse) CSR larger than the L2: ring scans
   int device = 0;
   int num_sms = 0;
   uint32_t flags = 0;
@@ -2680,6 +2772,17 @@ struct kadabra_graph {
   std::vector<void*> allocs;  // CSR copies and run buffers
 };
 
+namespace {
+// internal launch flag: the graph's CSR exceeds the L2, so its level scans
+// take the async-copy ring (KADABRA_FLAG_ASYNC_SCAN asks for it explicitly)
+constexpr uint32_t FLAG_RING_AUTO = 1u << 31;
+// the flags a launch shared by several graphs takes from any of them (they
+// change no result; the tier-skipping flags stay per graph)
+constexpr uint32_t SHARED_LAUNCH_FLAGS = KADABRA_FLAG_WARP_TIER | KADABRA_FLAG_ASYNC_SCAN | FLAG_RING_AUTO;
+
+uint32_t launch_flags(const kadabra_graph* g) { return g->flags | (g->csr_beyond_l2 ? FLAG_RING_AUTO : 0u); }
+}  // namespace
+
 // G graphs whose CSRs share one device arena
 struct kadabra_batch {
   int32_t G = 0;
@@ -2716,6 +2819,8 @@ kadabra_status ensure_ws(Workspace* w, uint64_t deferred_need, int njobs) {
     KCK(cudaSetDevice(w->device));
     w->smem_fast = fast_smem_bytes();
     KCK(cudaFuncSetAttribute(k_sample<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->smem_fast));
+    KCK(cudaFuncSetAttribute(k_sample<0, FAST_HLOG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)w->smem_fast));
     int per_sm = 0;
     KCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample<0>, NT, w->smem_fast));
     if (per_sm < 1) return fail(KADABRA_ERR_CAPACITY, "sampler does not fit on an SM");
@@ -2730,6 +2835,8 @@ kadabra_status ensure_ws(Workspace* w, uint64_t deferred_need, int njobs) {
     w->grid_warp = w->num_sms * std::max(per_sm, 1);
     w->smem_big = big_smem_bytes();
     KCK(cudaFuncSetAttribute(k_sample<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->smem_big));
+    KCK(cudaFuncSetAttribute(k_sample<2, FAST_HLOG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)w->smem_big));
     KCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample<2>, NT, w->smem_big));
     if (per_sm < 1) return fail(KADABRA_ERR_CAPACITY, "large-table sampler does not fit on an SM");
     w->grid_big = w->num_sms * per_sm;
@@ -2848,11 +2955,12 @@ SampleParams ws_params(const Workspace* w, uint32_t flags) {
   if (flags & KADABRA_FLAG_MEDIUM_TABLES) P.tier_flags |= TF_SKIP_S | TF_SKIP_B;
   if (flags & KADABRA_FLAG_LARGE_SHARED_TABLES) P.tier_flags |= TF_SKIP_S;
   if (flags & KADABRA_FLAG_WARP_TIER) P.tier_flags |= TF_WARP;
+  if (flags & (KADABRA_FLAG_ASYNC_SCAN | FLAG_RING_AUTO)) P.tier_flags |= TF_RING;
   return P;
 }
 
 SampleParams base_params(kadabra_graph* g) {
-  SampleParams P = ws_params(g->ws, g->flags);
+  SampleParams P = ws_params(g->ws, launch_flags(g));
   P.job0.g = graph_dev(g);
   return P;
 }
@@ -2871,12 +2979,18 @@ kadabra_status launch_sampler_kernels(Workspace* w, SampleParams P, cudaStream_t
     k_sample_warp<<<w->grid_warp, 32 * WT_WARPS, w->smem_warp, st>>>(P);
     KCK(cudaGetLastError());
   }
-  if (variant & 1)
+  const bool rg = (P.tier_flags & TF_RING) != 0;
+  if (variant & 1)  // the small table has no ring variant
     k_sample<0, SMALL_HLOG><<<w->grid_small, NT, w->smem_small, st>>>(P);
+  else if (rg)
+    k_sample<0, FAST_HLOG, true><<<w->grid_fast, NT, w->smem_fast, st>>>(P);
   else
     k_sample<0><<<w->grid_fast, NT, w->smem_fast, st>>>(P);
   KCK(cudaGetLastError());
-  k_sample<2><<<w->grid_big, NT, w->smem_big, st>>>(P);
+  if (rg)
+    k_sample<2, FAST_HLOG, true><<<w->grid_big, NT, w->smem_big, st>>>(P);
+  else
+    k_sample<2><<<w->grid_big, NT, w->smem_big, st>>>(P);
   KCK(cudaGetLastError());
   P.pi_base = w->pi_gm;
   P.pcap = w->pcap_gm;
@@ -3176,6 +3290,10 @@ kadabra_status finish_load(kadabra_graph* g) {
     if (h & 16) why += (g->directed ? " reverse CSR does not mirror the forward CSR;" : " adjacency not symmetric;");
     return fail(KADABRA_ERR_CSR, "invalid CSR:" + why);
   }
+  int l2 = 0;
+  if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, g->device) != cudaSuccess) l2 = 0;
+  const uint64_t csr = (4ull * ((uint64_t)n + 1) + 4ull * (uint64_t)m) * (g->directed ? 2 : 1);
+  g->csr_beyond_l2 = l2 > 0 && csr > (uint64_t)l2;
   return KADABRA_OK;
 }
 
@@ -3330,7 +3448,7 @@ kadabra_status tier_variant(kadabra_graph* g, Workspace* w, cudaStream_t st, int
     }
   }
   KTRY(ensure_ws(w, probe, 1));
-  SampleParams P = ws_params(w, g->flags);
+  SampleParams P = ws_params(w, launch_flags(g));
   P.total_work = probe;
   std::memset(&P.job0, 0, sizeof(Job));
   P.job0.g = graph_dev(g);
@@ -3440,7 +3558,7 @@ kadabra_status run_loop_graph(kadabra_graph* g, Workspace* w, cudaStream_t st, u
   LoopState* d_state = static_cast<LoopState*>(g->loop_dev);
   Job* d_job = reinterpret_cast<Job*>(d_state + 1);
   CheckTabJob* d_cj = reinterpret_cast<CheckTabJob*>(d_job + 1);
-  SampleParams P = ws_params(w, g->flags);
+  SampleParams P = ws_params(w, launch_flags(g));
   P.jobs = d_job;
   P.njobs = 1;
   P.total_dev = &d_state->total_work;
@@ -3573,9 +3691,9 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
     if (work == 0) return KADABRA_OK;
     // one graph: its flags; several share the launch: only the warp tier,
     // if any of them asks for it (it changes no result)
-    uint32_t fl = G == 1 ? gs[0]->flags : 0;
+    uint32_t fl = G == 1 ? launch_flags(gs[0]) : 0;
     if (G > 1)
-      for (int i = 0; i < G; ++i) fl |= gs[i]->flags & KADABRA_FLAG_WARP_TIER;
+      for (int i = 0; i < G; ++i) fl |= launch_flags(gs[i]) & SHARED_LAUNCH_FLAGS;
     SampleParams P = ws_params(w, fl);
     P.total_work = work;
     if (jobs.size() == 1) {
@@ -3916,7 +4034,7 @@ kadabra_status run_topk(kadabra_graph* g, double lambda, double delta, int32_t k
     jobs[0].work_begin = 0;
     jobs[1].work_begin = alpha;
     RCK(cudaMemcpyAsync(w->d_jobs, jobs, sizeof(jobs), cudaMemcpyHostToDevice, st));
-    SampleParams P = ws_params(w, g->flags);
+    SampleParams P = ws_params(w, launch_flags(g));
     P.total_work = 2 * alpha;
     P.jobs = w->d_jobs;
     P.njobs = 2;
@@ -4034,7 +4152,7 @@ kadabra_status run_topk(kadabra_graph* g, double lambda, double delta, int32_t k
   uint64_t tau = 0;
   for (;;) {
     const uint64_t B = std::min<uint64_t>(K, cap - tau);
-    SampleParams P = ws_params(w, g->flags);
+    SampleParams P = ws_params(w, launch_flags(g));
     P.total_work = B;
     P.job0 = job(0, tau, B, g->counts);
     KTRY(launch_sampler(w, P, st, variant));
@@ -4472,7 +4590,7 @@ kadabra_status srv_round(kadabra_server* S, std::vector<SrvJob*>& act, std::vect
   Workspace* w = S->ws.get();
   KTRY(ensure_ws(w, work, (int)jobs.size()));
   uint32_t fl = 0;  // the warp tier, if any job's graph asks for it (it changes no result)
-  for (SrvJob* J : act) fl |= J->g->flags & KADABRA_FLAG_WARP_TIER;
+  for (SrvJob* J : act) fl |= launch_flags(J->g) & SHARED_LAUNCH_FLAGS;
   SampleParams P = ws_params(w, fl);
   P.total_work = work;
   if (jobs.size() == 1) {
@@ -4960,7 +5078,7 @@ void kadabra_release_cached(void) {
 kadabra_status kadabra_graph_set_flags(kadabra_graph* g, uint32_t flags) {
   if (!g) return fail(KADABRA_ERR_ARG, "graph is NULL");
   if (flags & ~(uint32_t)(KADABRA_FLAG_GLOBAL_TABLES | KADABRA_FLAG_MEDIUM_TABLES | KADABRA_FLAG_LARGE_SHARED_TABLES |
-                          KADABRA_FLAG_WARP_TIER))
+                          KADABRA_FLAG_WARP_TIER | KADABRA_FLAG_ASYNC_SCAN))
     return fail(KADABRA_ERR_ARG, "unknown flag");
   g->flags = flags;
   return KADABRA_OK;

@@ -45,6 +45,7 @@ FLAG_GLOBAL_TABLES = 1
 FLAG_MEDIUM_TABLES = 2
 FLAG_LARGE_SHARED_TABLES = 4
 FLAG_WARP_TIER = 8
+FLAG_ASYNC_SCAN = 16
 
 
 class KadabraError(RuntimeError):
