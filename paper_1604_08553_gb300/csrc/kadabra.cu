@@ -2615,10 +2615,13 @@ __device__ __forceinline__ void bfs_scan(const int32_t* c, int32_t a, int32_t b,
   }
 }
 
+// The frontier's size is read on the device (*nfront_dev, or 1 for the root's
+// level when it is null), so the host can queue several levels at once.
 __global__ void k_bfs_level(const int32_t* rp, const int32_t* ci, const int32_t* rrp, const int32_t* rci, int directed,
-                            const int32_t* front, int32_t nfront, int32_t* next, int32_t* nnext, int32_t* dist,
-                            int32_t level, BfsItem* items, int32_t* nitems, int32_t items_cap) {
+                            const int32_t* front, const int32_t* nfront_dev, int32_t* next, int32_t* nnext,
+                            int32_t* dist, int32_t level, BfsItem* items, int32_t* nitems, int32_t items_cap) {
   const int lane = lane_id();
+  const int32_t nfront = nfront_dev ? *nfront_dev : 1;
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = w0; i < nfront; i += nwarps) {
@@ -3146,7 +3149,7 @@ struct LoadScratch {
   unsigned long long* lt_gt;   // the mirror test's two arc counts
   int32_t* fp;                 // 64 fingerprint entries
   unsigned long long* best;    // the VD root's key
-  int32_t* cnt;                // [0] next frontier size, [1] BFS items
+  int32_t* cnt;                // BFS level counters: slot l % 8 holds {next frontier size, items} of level l
   uint32_t* recip;             // n (directed graphs), else null
   int32_t *dist, *qa, *qb;     // n each
   BfsItem* items;
@@ -3167,7 +3170,7 @@ kadabra_status load_scratch(const kadabra_graph* g, LoadScratch* S) {
   S->err = reinterpret_cast<unsigned*>(b + o_head);
   S->lt_gt = reinterpret_cast<unsigned long long*>(b + o_head + 8);
   S->best = reinterpret_cast<unsigned long long*>(b + o_head + 24);
-  S->cnt = reinterpret_cast<int32_t*>(b + o_head + 32);
+  S->cnt = reinterpret_cast<int32_t*>(b + o_head + 512);
   S->fp = reinterpret_cast<int32_t*>(b + o_head + 64);
   S->recip = g->directed ? reinterpret_cast<uint32_t*>(b + o_recip) : nullptr;
   S->dist = reinterpret_cast<int32_t*>(b + o_dist);
@@ -3196,19 +3199,34 @@ kadabra_status compute_vd(kadabra_graph* g, LoadTrace& tr, const LoadScratch& S)
   KCK(cudaMemcpy(S.dist + r, &zero, sizeof(int32_t), cudaMemcpyHostToDevice));
   KCK(cudaMemcpy(S.qa, &r, sizeof(int32_t), cudaMemcpyHostToDevice));
   tr.mark("vd root");
-  int32_t *qa = S.qa, *qb = S.qb;
-  int32_t nfront = 1, level = 0;
-  while (nfront > 0 && level <= n) {
-    KCK(cudaMemsetAsync(S.cnt, 0, 2 * sizeof(int32_t)));
-    const int bl = std::max(1, std::min(8 * g->num_sms, (int)std::min<int64_t>(((int64_t)nfront * 32 + 255) / 256,
-                                                                                 1 << 30)));
-    k_bfs_level<<<bl, 256>>>(g->rp, g->ci, rrp, rci, g->directed, qa, nfront, qb, S.cnt, S.dist, level, S.items,
-                             S.cnt + 1, S.items_cap);
-    k_bfs_items<<<8 * g->num_sms, 256>>>(g->ci, rci, S.items, S.cnt + 1, S.items_cap, qb, S.cnt, S.dist, level);
-    if (cudaMemcpy(&nfront, S.cnt, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+  // Levels are queued BFS_BATCH at a time and their sizes read back once per
+  // batch; levels past the end find an empty frontier and do nothing.
+  constexpr int BFS_BATCH = 4, SLOTS = 8;
+  int32_t level = 0;  // levels with a non-empty next frontier so far
+  bool done = false;
+  for (int32_t l0 = 0; !done && l0 <= n; l0 += BFS_BATCH) {
+    for (int k = 0; k < BFS_BATCH; ++k)
+      KCK(cudaMemsetAsync(S.cnt + 2 * ((l0 + k) % SLOTS), 0, 2 * sizeof(int32_t)));
+    for (int k = 0; k < BFS_BATCH; ++k) {
+      const int32_t l = l0 + k;
+      int32_t* in_q = (l & 1) ? S.qb : S.qa;
+      int32_t* out_q = (l & 1) ? S.qa : S.qb;
+      int32_t* c = S.cnt + 2 * (l % SLOTS);
+      const int32_t* prev = l == 0 ? nullptr : S.cnt + 2 * ((l + SLOTS - 1) % SLOTS);
+      k_bfs_level<<<8 * g->num_sms, 256>>>(g->rp, g->ci, rrp, rci, g->directed, in_q, prev, out_q, c, S.dist, l,
+                                           S.items, c + 1, S.items_cap);
+      k_bfs_items<<<8 * g->num_sms, 256>>>(g->ci, rci, S.items, c + 1, S.items_cap, out_q, c, S.dist, l);
+    }
+    int32_t h[2 * SLOTS];
+    if (cudaMemcpy(h, S.cnt, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
       return fail(KADABRA_ERR_CUDA, std::string("vd bfs: ") + cudaGetErrorString(cudaGetLastError()));
-    std::swap(qa, qb);
-    if (nfront > 0) ++level;
+    for (int k = 0; k < BFS_BATCH; ++k) {
+      if (h[2 * ((l0 + k) % SLOTS)] == 0) {
+        done = true;
+        break;
+      }
+      ++level;
+    }
   }
   g->vd = 2 * (int64_t)level + 1;
   tr.mark("vd bfs");
