@@ -341,6 +341,8 @@ struct Ctl {
   int pick, pick_pos;
   int mode;       // backtracking: 0 = scan the row of x, 1 = scan the previous level
   int next_x;     // backtracking: the node picked at this step
+  int bt_half, bt_x, bt_dx;  // backtracking state between warp 0 and the block
+  uint32_t bt_j;             //   and the next Philox block
   int cv, cw;     // chosen candidate edge (v on the s side, w on the t side)
   unsigned long long cur;
   unsigned long long ntotal;
@@ -768,6 +770,119 @@ __device__ int block_pick_radix(const PiEntry* buf, int n, unsigned long long r,
 
 // All threads of the CTA call this with the same idx.  Flags in c.flags tell
 // the caller what happened; the caller resets the tables afterwards.
+// Backtracking state: after a step reaches depth 0 on one side, continue
+// with w on the t side; half 2 = done.
+__device__ __forceinline__ void bt_normalize(Ctl& c, int dw) {
+  while (c.bt_half < 2 && c.bt_dx == 0) {
+    ++c.bt_half;
+    if (c.bt_half == 1) {
+      c.bt_x = c.cw;
+      c.bt_dx = dw;
+    }
+  }
+}
+
+// Records a backtracking pick y (now at depth dn on side `half`, at position
+// pos of the scanned row): the work counter, its hit (interior nodes only)
+// and its place on the path.  One thread.
+template <bool PK>
+__device__ __forceinline__ void bt_record(const SampleParams& P, const Job& J, Ctl& c, int half, int dn, int y, int pos,
+                                          int64_t out_i, int dv, int dw, bool want_path) {
+  c.stat[KADABRA_STAT_BT_SCANNED] += pos + 1;
+  if (dn > 0 && J.counts) atomicAdd(&J.counts[y], 1u);
+  if (want_path) {
+    const int at = half == 0 ? dn : (dv + 1) + (dw - dn);
+    if (at < P.max_len) P.paths[out_i * (int64_t)P.max_len + at] = y;
+  }
+}
+
+constexpr int WARP_BT_ROW = 256;  // rows up to this length: the step stays with warp 0
+
+// Warp 0's backtracking steps, from the state in c.bt_* until the sample's
+// path is complete or a step with more candidates than it takes comes up
+// (left in c.bt_* for the block).  The draw, the candidate order and the
+// pick are those of the block's steps: the first predecessor in row order
+// whose cumulative sigma exceeds r.
+template <bool PK>
+__device__ void bt_warp_steps(const SampleParams& P, const Job& J, const Tables& T, Ctl& c, uint64_t idx,
+                              int64_t out_i, int dv, int dw, bool want_path) {
+  const int lane = lane_id();
+  const GraphDev& G = J.g;
+  int half = c.bt_half, x = c.bt_x, dx = c.bt_dx;
+  uint32_t j = c.bt_j;
+  while (half < 2) {
+    const int32_t* brow = half == 0 ? G.rrp : G.rp;
+    const int32_t* bcol = half == 0 ? G.rci : G.ci;
+    const int plo = lvl_lo(T, half, dx - 1), phi = lvl_hi(T, half, dx - 1);
+    const int r0 = __ldg(&brow[x]), deg = __ldg(&brow[x + 1]) - r0;
+    const bool single = phi - plo == 1;
+    if (!single && deg > WARP_BT_ROW) break;  // the block takes this step
+    const int px = tab_find_pos(T, x);
+    if (px < 0) {
+      if (lane == 0) c.bt_flag = 1;
+      return;
+    }
+    const unsigned long long r = below128(j < 32 ? c.draws[j] : draw(J.seed, J.domain, idx, j),
+                                          ent_sig<PK>(T, T.hkv[px], (uint32_t)px));
+    ++j;
+    int y = -1, pos = -1;
+    if (single) {
+      // a single node one level closer: it is x's only predecessor
+      y = T.lnode[plo];
+      pos = warp_lower_bound(bcol, r0, r0 + deg, y) - r0;
+    } else {
+      const uint32_t want = pack_val(half, dx - 1);
+      unsigned long long carry = 0;
+      for (int base = 0; base < deg; base += 32) {
+        const int i = base + lane;
+        unsigned long long w = 0;
+        if (i < deg) {
+          const int yy = __ldg(&bcol[r0 + i]);
+          const int q = tab_find_pos(T, yy);
+          if (q >= 0) {
+            const unsigned long long hw = T.hkv[q];
+            if (ent_val<PK>(hw) == want) w = ent_sig<PK>(T, hw, (uint32_t)q);
+          }
+        }
+        unsigned long long inc = w;  // inclusive scan (partial sums stay below sigma(x))
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const unsigned long long v = __shfl_up_sync(FULL, inc, o);
+          if (lane >= o) inc += v;
+        }
+        const bool hit = w != 0 && carry + inc - w <= r && r < carry + inc;
+        const unsigned m = __ballot_sync(FULL, hit);
+        if (m) {
+          pos = base + __ffs(m) - 1;
+          break;
+        }
+        carry += __shfl_sync(FULL, inc, 31);
+      }
+      if (pos >= 0) y = __ldg(&bcol[r0 + pos]);
+    }
+    if (y < 0) {
+      if (lane == 0) c.bt_flag = 1;
+      return;
+    }
+    if (lane == 0) bt_record<PK>(P, J, c, half, dx - 1, y, pos, out_i, dv, dw, want_path);
+    x = y;
+    dx -= 1;
+    while (half < 2 && dx == 0) {
+      ++half;
+      if (half == 1) {
+        x = c.cw;
+        dx = dw;
+      }
+    }
+  }
+  if (lane == 0) {
+    c.bt_half = half;
+    c.bt_x = x;
+    c.bt_dx = dx;
+    c.bt_j = j;
+  }
+}
+
 template <bool PK, bool RG = false>
 __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, const Tables& T, Ctl& c, uint64_t idx,
                                            int64_t out_i) {
@@ -1130,118 +1245,123 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
       if (dw > 0) atomicAdd(&J.counts[c.cw], 1u);
     }
   }
-  uint32_t j = 2;
-  for (int half = 0; half < 2; ++half) {
-    // half 0: v -> s over predecessors (weights sigma_s); half 1: w -> t over successors
-    int x = half == 0 ? c.cv : c.cw;
-    int dx = half == 0 ? dv : dw;
+  // Steps go one node at a time, v -> s over predecessors (half 0, weights
+  // sigma_s) and w -> t over successors (half 1).  Warp 0 takes the steps
+  // whose candidates are few (a single node one level closer, or a row of up
+  // to WARP_BT_ROW arcs) with warp scans only; a longer step goes to the whole
+  // block.  Both choose the same node with the same draw.  The state between
+  // them (half, node, depth, next draw) lives in c.bt_*.
+  if (tid == 0) {
+    c.bt_half = 0;
+    c.bt_x = c.cv;
+    c.bt_dx = dv;
+    c.bt_j = 2;
+    bt_normalize(c, dw);
+  }
+  __syncthreads();
+  for (;;) {
+    if (wid == 0) bt_warp_steps<PK>(P, J, T, c, idx, out_i, dv, dw, want_path);
+    __syncthreads();
+    if (c.bt_flag) {
+      if (tid == 0) c.flags |= F_INTERNAL;
+      return;
+    }
+    if (c.bt_half >= 2) break;
+    // one long step, by the whole block
+    const int half = c.bt_half, x = c.bt_x, dx = c.bt_dx;
+    const uint32_t j = c.bt_j;
     // the row of x that holds its neighbours one level closer to the root
     const int32_t* brow = half == 0 ? G.rrp : G.rp;
     const int32_t* bcol = half == 0 ? G.rci : G.ci;
     // the opposite direction, to test adjacency from a previous-level node
     const int32_t* frow = half == 0 ? G.rp : G.rrp;
     const int32_t* fcol = half == 0 ? G.ci : G.rci;
-    while (dx > 0) {
-      const int plo = lvl_lo(T, half, dx - 1), phi = lvl_hi(T, half, dx - 1);
-      const uint32_t want = pack_val(half, dx - 1);
-      const int r0 = __ldg(&brow[x]), deg = __ldg(&brow[x + 1]) - r0;
-      if (tid == 0) {
-        const int px = tab_find_pos(T, x);
-        if (px < 0) {
-          c.bt_flag = 1;  // reported below, after every thread has decided
-          c.r = 0;
-        } else {
-          c.r = below128(j < 32 ? c.draws[j] : draw(J.seed, J.domain, idx, j),
-                         ent_sig<PK>(T, T.hkv[px], (uint32_t)px));
-        }
-        // scan whichever is shorter: the row of x, or the previous level
-        c.mode = ((long long)(phi - plo) * 16 < (long long)deg) ? 1 : 0;
-        c.ecount = 0;  // candidates found in the previous level (mode 1)
-      }
-      ++j;
-      __syncthreads();
-      if (c.bt_flag) {
-        if (tid == 0) c.flags |= F_INTERNAL;
-        return;
-      }
-      const unsigned long long r = c.r;
-      if (c.mode == 1 && phi - plo == 1) {
-        // a single node one level closer: it is x's only possible predecessor
-        if (tid == 0) {
-          T.pr[0] = make_int2(T.lnode[plo], (int)T.lpos[plo]);
-          c.ecount = 1;
-        }
-        __syncthreads();
-      } else if (c.mode == 1) {
-        // previous-level nodes adjacent to x, collected as (node, hash position)
-        for (int i = plo + tid; i < phi; i += NT) {
-          const int y = T.lnode[i];
-          const int a = __ldg(&frow[y]), b = __ldg(&frow[y + 1]);
-          const int at = lower_bound_row(fcol, a, b, x);
-          if (at < b && __ldg(&fcol[at]) == x) {
-            const int q = atomicAdd(&c.ecount, 1);
-            if (q < T.lcap) T.pr[q] = make_int2(y, (int)T.lpos[i]);
-          }
-        }
-        __syncthreads();
-        if (c.ecount > min(T.lcap, 128)) {
-          if (tid == 0) c.mode = 0;  // many predecessors: scan the row instead
-          __syncthreads();
-        }
-      }
-      int y_pick = -1, pos_pick = 0;
-      if (c.mode == 1) {
-        const int nc = c.ecount;
-        const int pick = block_pick_by_key(
-            nc, r, c, [&](int i) { return (unsigned long long)(uint32_t)T.pr[i].x; },
-            [&](int i) {
-              const uint32_t q = (uint32_t)T.pr[i].y;
-              return ent_sig<PK>(T, T.hkv[q], q);
-            });
-        if (pick >= 0) y_pick = T.pr[pick].x;
-        if (wid == 0 && pick >= 0) pos_pick = warp_lower_bound(bcol, r0, r0 + deg, y_pick) - r0;
+    const int plo = lvl_lo(T, half, dx - 1), phi = lvl_hi(T, half, dx - 1);
+    const uint32_t want = pack_val(half, dx - 1);
+    const int r0 = __ldg(&brow[x]), deg = __ldg(&brow[x + 1]) - r0;
+    __syncthreads();  // every thread has read c.bt_* before thread 0 writes below
+    if (tid == 0) {
+      const int px = tab_find_pos(T, x);
+      if (px < 0) {
+        c.bt_flag = 1;  // reported below, after every thread has decided
+        c.r = 0;
       } else {
-        const int pick = block_pick(deg, r, c, [&](int i0, int N, unsigned long long* w) {
-          int ys[U];
+        c.r = below128(j < 32 ? c.draws[j] : draw(J.seed, J.domain, idx, j),
+                       ent_sig<PK>(T, T.hkv[px], (uint32_t)px));
+      }
+      // scan whichever is shorter: the row of x, or the previous level
+      c.mode = ((long long)(phi - plo) * 16 < (long long)deg) ? 1 : 0;
+      c.ecount = 0;  // candidates found in the previous level (mode 1)
+    }
+    __syncthreads();
+    if (c.bt_flag) {
+      if (tid == 0) c.flags |= F_INTERNAL;
+      return;
+    }
+    const unsigned long long r = c.r;
+    if (c.mode == 1) {
+      // previous-level nodes adjacent to x, collected as (node, hash position)
+      for (int i = plo + tid; i < phi; i += NT) {
+        const int y = T.lnode[i];
+        const int a = __ldg(&frow[y]), b = __ldg(&frow[y + 1]);
+        const int at = lower_bound_row(fcol, a, b, x);
+        if (at < b && __ldg(&fcol[at]) == x) {
+          const int q = atomicAdd(&c.ecount, 1);
+          if (q < T.lcap) T.pr[q] = make_int2(y, (int)T.lpos[i]);
+        }
+      }
+      __syncthreads();
+      if (c.ecount > min(T.lcap, 128)) {
+        if (tid == 0) c.mode = 0;  // many predecessors: scan the row instead
+        __syncthreads();
+      }
+    }
+    int y_pick = -1, pos_pick = 0;
+    if (c.mode == 1) {
+      const int nc = c.ecount;
+      const int pick = block_pick_by_key(
+          nc, r, c, [&](int i) { return (unsigned long long)(uint32_t)T.pr[i].x; },
+          [&](int i) {
+            const uint32_t q = (uint32_t)T.pr[i].y;
+            return ent_sig<PK>(T, T.hkv[q], q);
+          });
+      if (pick >= 0) y_pick = T.pr[pick].x;
+      if (wid == 0 && pick >= 0) pos_pick = warp_lower_bound(bcol, r0, r0 + deg, y_pick) - r0;
+    } else {
+      const int pick = block_pick(deg, r, c, [&](int i0, int N, unsigned long long* w) {
+        int ys[U];
 #pragma unroll
-          for (int k = 0; k < U; ++k) ys[k] = (i0 + k < N) ? __ldg(&bcol[r0 + i0 + k]) : -1;
+        for (int k = 0; k < U; ++k) ys[k] = (i0 + k < N) ? __ldg(&bcol[r0 + i0 + k]) : -1;
 #pragma unroll
-          for (int k = 0; k < U; ++k) {
-            w[k] = 0;
-            if (ys[k] >= 0) {
-              const int pos = tab_find_pos(T, ys[k]);
-              if (pos >= 0) {
-                const unsigned long long hw = T.hkv[pos];
-                if (ent_val<PK>(hw) == want) w[k] = ent_sig<PK>(T, hw, (uint32_t)pos);
-              }
+        for (int k = 0; k < U; ++k) {
+          w[k] = 0;
+          if (ys[k] >= 0) {
+            const int pos = tab_find_pos(T, ys[k]);
+            if (pos >= 0) {
+              const unsigned long long hw = T.hkv[pos];
+              if (ent_val<PK>(hw) == want) w[k] = ent_sig<PK>(T, hw, (uint32_t)pos);
             }
           }
-        });
-        if (pick >= 0) {
-          y_pick = __ldg(&bcol[r0 + pick]);
-          pos_pick = pick;
         }
+      });
+      if (pick >= 0) {
+        y_pick = __ldg(&bcol[r0 + pick]);
+        pos_pick = pick;
       }
-      if (y_pick < 0) {
-        if (tid == 0) c.flags |= F_INTERNAL;
-        __syncthreads();
-        return;
-      }
-      if (tid == 0) {
-        c.next_x = y_pick;
-        c.stat[KADABRA_STAT_BT_SCANNED] += pos_pick + 1;
-        const int dn = dx - 1;
-        if (dn > 0 && J.counts) atomicAdd(&J.counts[y_pick], 1u);
-        if (want_path) {
-          const int at = half == 0 ? dn : (dv + 1) + (dw - dn);
-          if (at < P.max_len) P.paths[out_i * (int64_t)P.max_len + at] = y_pick;
-        }
-      }
-      __syncthreads();
-      x = c.next_x;
-      dx -= 1;
-      __syncthreads();
     }
+    if (y_pick < 0) {
+      if (tid == 0) c.flags |= F_INTERNAL;
+      __syncthreads();
+      return;
+    }
+    if (tid == 0) {
+      bt_record<PK>(P, J, c, half, dx - 1, y_pick, pos_pick, out_i, dv, dw, want_path);
+      c.bt_x = y_pick;
+      c.bt_dx = dx - 1;
+      c.bt_j = j + 1;
+      bt_normalize(c, dw);
+    }
+    __syncthreads();
   }
 }
 
