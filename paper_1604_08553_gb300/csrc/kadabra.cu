@@ -147,9 +147,12 @@ struct Tables {
   uint32_t hmask;
   int hlog;
   int32_t* lnode;           // level lists: node ids
-  uint32_t* lpos;           // level lists: hash positions
-  int2* pr;                 // frontier: {degree prefix, row start}; lcap+1 entries
+  uint32_t* lpos;           // level lists: hash positions (global-memory tiers)
+  uint16_t* lpos16;         //   the same, 16 bits, in the shared-memory tiers (2^HLOG <= 2^16 slots)
+  int2* pr;                 // frontier: {degree prefix, row start}; frcap+1 entries
   int lcap;
+  int frcap;                // largest frontier (a larger one sends the sample on)
+  int* ring;                // the async-copy scan's per-warp ring (tier S only), else null
   int* lvl;                 // [side][lo|hi][maxd+2]
   int maxd;
   PiEntry* pi;              // 2*NW segments of pcap entries (the second half is scratch)
@@ -159,6 +162,19 @@ struct Tables {
 __device__ __forceinline__ int& lvl_lo(const Tables& T, int side, int d) { return T.lvl[(2 * side) * (T.maxd + 2) + d]; }
 __device__ __forceinline__ int& lvl_hi(const Tables& T, int side, int d) {
   return T.lvl[(2 * side + 1) * (T.maxd + 2) + d];
+}
+
+// list entry i's hash position (16-bit in the shared-memory tiers: PK)
+template <bool PK>
+__device__ __forceinline__ uint32_t lpos_get(const Tables& T, int i) {
+  return PK ? (uint32_t)T.lpos16[i] : T.lpos[i];
+}
+template <bool PK>
+__device__ __forceinline__ void lpos_set(const Tables& T, int i, uint32_t pos) {
+  if (PK)
+    T.lpos16[i] = (uint16_t)pos;
+  else
+    T.lpos[i] = pos;
 }
 
 __device__ __forceinline__ uint32_t pack_val(int side, int dist) { return ((uint32_t)side << 31) | (uint32_t)dist; }
@@ -346,8 +362,6 @@ struct Ctl {
   int cv, cw;     // chosen candidate edge (v on the s side, w on the t side)
   unsigned long long cur;
   unsigned long long ntotal;
-  // the level scans' async-copy ring: per warp RING windows of 32 heads
-  int ring[NW][RING][32];
   // weighted radix selection (block_pick_radix)
   unsigned long long rhist[256];
   unsigned rcnt[256];
@@ -601,7 +615,7 @@ __device__ __forceinline__ void scan_level_ring(const Tables& T, Ctl& c, int fco
   const int per = (E + NW - 1) / NW;
   const int c0 = min(E, wid * per), c1 = min(E, c0 + per);
   if (c0 >= c1) return;
-  int* ring = &c.ring[wid][0][0];
+  int* ring = T.ring + wid * RING * 32;
   const int nwin = (c1 - c0 + 31) >> 5;
   int ip = frontier_pos(T.pr, fcount, c0);  // issue cursor (warp-uniform)
   int2 icur = T.pr[ip];                      // {first arc index, row start}
@@ -796,7 +810,10 @@ __device__ __forceinline__ void bt_record(const SampleParams& P, const Job& J, C
   }
 }
 
-constexpr int WARP_BT_ROW = 256;  // rows up to this length: the step stays with warp 0
+#ifndef KD_WARP_BT_ROW
+#define KD_WARP_BT_ROW 256
+#endif
+constexpr int WARP_BT_ROW = KD_WARP_BT_ROW;  // rows up to this length: the step stays with warp 0
 
 // Warp 0's backtracking steps, from the state in c.bt_* until the sample's
 // path is complete or a step with more candidates than it takes comes up
@@ -916,9 +933,9 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
       T.hsig[pt] = 1ull;
     }
     T.lnode[0] = s;
-    T.lpos[0] = ps;
+    lpos_set<PK>(T, 0, ps);
     T.lnode[1] = t;
-    T.lpos[1] = pt;
+    lpos_set<PK>(T, 1, pt);
     c.nlist = 2;
     lvl_lo(T, 0, 0) = 0;
     lvl_hi(T, 0, 0) = 1;
@@ -948,30 +965,36 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
     const int32_t* rowp = side == 0 ? G.rp : G.rrp;
     const int32_t* cols = side == 0 ? G.ci : G.rci;
 
-    // degree prefix and row starts over the frontier
-    {
+    // Degree prefix and row starts over frontier nodes [fb, fb + cnt) into
+    // T.pr; returns their arc count (all threads).  A frontier of more than
+    // T.frcap nodes (tier B) is scanned in segments of T.frcap: the touch
+    // test and the insertion treat a level's arcs as a set, so segments give
+    // the same result.
+    auto build_prefix = [&](int fb, int cnt, bool count_edges) {
       int carry = 0;
-      for (int base = 0; base < fcount; base += NT) {
+      for (int base = 0; base < cnt; base += NT) {
         const int i = base + tid;
         int deg = 0, rs = 0;
-        if (i < fcount) {
-          const int x = T.lnode[f0 + i];
+        if (i < cnt) {
+          const int x = T.lnode[fb + i];
           rs = __ldg(&rowp[x]);
           deg = __ldg(&rowp[x + 1]) - rs;
         }
         int tot;
         const int ex = block_exscan(deg, c.scan_tmp, &tot);
-        if (i < fcount) T.pr[i] = make_int2(carry + ex, rs);
+        if (i < cnt) T.pr[i] = make_int2(carry + ex, rs);
         carry += tot;
       }
       if (tid == 0) {
-        T.pr[fcount] = make_int2(carry, 0);
+        T.pr[cnt] = make_int2(carry, 0);
         c.ecount = carry;
-        c.stat[KADABRA_STAT_EDGES] += carry;
+        if (count_edges) c.stat[KADABRA_STAT_EDGES] += carry;
       }
       __syncthreads();
-    }
-    const int E = c.ecount;
+      return c.ecount;
+    };
+    const int nseg = (fcount + T.frcap - 1) / T.frcap;
+    int E = 0;  // arc count of the last segment built
 
     // pass 1: touch test against the other search
     int pass1_bad = 0;
@@ -979,7 +1002,10 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
       int npi = 0;
       bool sigma_of = false;
       PiEntry* seg = T.pi + (size_t)wid * T.pcap;
-      scan_level<RG>(T, c, fcount, E, cols, [&](int, bool ok, int p, int y) {
+      for (int sg = 0; sg < nseg; ++sg) {
+      const int fb = f0 + sg * T.frcap, cnt = min(T.frcap, fcount - sg * T.frcap);
+      E = build_prefix(fb, cnt, true);
+      scan_level<RG>(T, c, cnt, E, cols, [&](int, bool ok, int p, int y) {
         bool touch = false;
         unsigned long long wgt = 0;
         if (ok) {
@@ -987,7 +1013,7 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
           const int pos = tab_probe(T, y, &hy);
           if (pos >= 0 && val_side(ent_val<PK>(hy)) != side) {
             touch = true;
-            const uint32_t px = T.lpos[f0 + p];
+            const uint32_t px = lpos_get<PK>(T, fb + p);
             const unsigned long long sx = ent_sig<PK>(T, T.hkv[px], px);
             const unsigned long long sy = ent_sig<PK>(T, hy, (uint32_t)pos);
             wgt = sx * sy;
@@ -998,13 +1024,15 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
         if (touch) {
           const int at = npi + __popc(m & ((1u << lane) - 1u));
           if (at < T.pcap) {
-            seg[at].x = T.lnode[f0 + p];
+            seg[at].x = T.lnode[fb + p];
             seg[at].y = y;
             seg[at].w = wgt;
           }
         }
         npi += __popc(m);
       });
+      if (sg + 1 < nseg) __syncthreads();  // the next segment's prefix overwrites T.pr
+      }
       int bad = 0;
       if (__any_sync(FULL, sigma_of) && lane == 0) {
         atomicOr(&c.flags, F_SIGMA);
@@ -1050,12 +1078,15 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
       bool of = false, cap = false;
       const uint32_t want_val = pack_val(side, dnew);
       const volatile int* nlist_now = &c.nlist;
-      scan_level<RG>(T, c, fcount, E, cols, [&](int, bool ok, int p, int y) {
+      for (int sg = 0; sg < nseg; ++sg) {
+      const int fb = f0 + sg * T.frcap, cnt = min(T.frcap, fcount - sg * T.frcap);
+      if (nseg > 1) E = build_prefix(fb, cnt, false);  // one segment: pass 1's prefix is still there
+      scan_level<RG>(T, c, cnt, E, cols, [&](int, bool ok, int p, int y) {
         if (!ok || cap) return;
         // the head's row bounds (its degree joins the new frontier's cost if
         // it is new), loaded before the probe so the load overlaps it
         const int ylo = __ldg(&rowp[y]), yhi = __ldg(&rowp[y + 1]);
-        const uint32_t px = T.lpos[f0 + p];
+        const uint32_t px = lpos_get<PK>(T, fb + p);
         const unsigned long long add = ent_sig<PK>(T, T.hkv[px], px);
         uint32_t pos = hash_pos(y, T.hlog);
         for (uint32_t k = 0; k <= T.hmask; ++k) {
@@ -1076,7 +1107,7 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
                 return;
               }
               T.lnode[slot] = y;
-              T.lpos[slot] = pos;
+              lpos_set<PK>(T, slot, pos);
               ++fresh;
               cost += yhi - ylo;
               if (!PK && !ent_add<PK>(T, pos, add)) of = true;
@@ -1100,6 +1131,8 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
         }
         cap = true;  // table full
       });
+      if (sg + 1 < nseg) __syncthreads();
+      }
       if (of) atomicOr(&c.flags, F_SIGMA);
       if (cap) atomicOr(&c.flags, F_CAP);
     }
@@ -1190,7 +1223,7 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
     // there as (key, weight) pairs and ranked quadratically; larger ones go
     // through the radix selection
     unsigned long long* kw = reinterpret_cast<unsigned long long*>(T.pr);
-    if (total <= min(T.lcap / 2, PK ? T.lcap / 2 : QUAD_PICK_MAX)) {  // (key, weight) pairs fit in pr
+    if (total <= min(T.frcap / 2, PK ? T.frcap / 2 : QUAD_PICK_MAX)) {  // (key, weight) pairs fit in pr
       for (int i = tid; i < total; i += NT) {
         kw[2 * i] = ((unsigned long long)(uint32_t)buf[i].x << 32) | (uint32_t)buf[i].y;
         kw[2 * i + 1] = buf[i].w;
@@ -1307,11 +1340,11 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
         const int at = lower_bound_row(fcol, a, b, x);
         if (at < b && __ldg(&fcol[at]) == x) {
           const int q = atomicAdd(&c.ecount, 1);
-          if (q < T.lcap) T.pr[q] = make_int2(y, (int)T.lpos[i]);
+          if (q < T.frcap) T.pr[q] = make_int2(y, (int)lpos_get<PK>(T, i));
         }
       }
       __syncthreads();
-      if (c.ecount > min(T.lcap, 128)) {
+      if (c.ecount > min(T.frcap, 128)) {
         if (tid == 0) c.mode = 0;  // many predecessors: scan the row instead
         __syncthreads();
       }
@@ -1380,7 +1413,7 @@ __device__ void reset_tables(const Tables& T, Ctl& c, bool whole) {
   } else {
     const int nl = min(c.nlist, T.lcap);
     for (int i = tid; i < nl; i += NT) {
-      const uint32_t pos = T.lpos[i];
+      const uint32_t pos = lpos_get<PK>(T, i);
       T.hkv[pos] = EMPTY;
       if (!PK) T.hsig[pos] = 0ull;
     }
@@ -1422,21 +1455,30 @@ __device__ inline Tables gm_tables(unsigned char* base, int hlog, int lcap, int 
   T.hlog = hlog;
   T.hmask = (1u << hlog) - 1u;
   T.lcap = lcap;
+  T.frcap = lcap;
+  T.lpos16 = nullptr;
+  T.ring = nullptr;
   T.maxd = maxd;
   return T;
 }
 
 // shared-memory layout of a packed tier with 2^HLOG hash slots and lists of
-// 2^(HLOG-1) nodes, after the control block
+// 2^(HLOG-1) nodes, after the control block.  Frontiers hold at most 2048
+// nodes (tier B: two CTAs per SM instead of one); tier S adds the async-copy
+// ring of its level scans.
 template <int HLOG>
 struct SLayout {
   static constexpr int LCAP = 1 << (HLOG - 1);
+  static constexpr int FRCAP = LCAP < 2048 ? LCAP : 2048;
+  static constexpr size_t RING_BYTES = HLOG == FAST_HLOG ? sizeof(int) * NW * RING * 32 : 0;
   static constexpr size_t HKV = (sizeof(Ctl) + 15) & ~size_t(15);
   static constexpr size_t PR = HKV + (sizeof(unsigned long long) << HLOG);
-  static constexpr size_t LNODE = PR + sizeof(int2) * (LCAP + 1);
+  static constexpr size_t LNODE = PR + sizeof(int2) * (FRCAP + 1);
   static constexpr size_t LPOS = LNODE + sizeof(int32_t) * LCAP;
-  static constexpr size_t LVL = LPOS + sizeof(uint32_t) * LCAP;
-  static constexpr size_t BYTES = LVL + sizeof(int) * 4 * (FAST_MAXD + 2);
+  static constexpr size_t LVL = LPOS + sizeof(uint16_t) * LCAP;
+  static constexpr size_t RINGO = (LVL + sizeof(int) * 4 * (FAST_MAXD + 2) + 15) & ~size_t(15);
+  static constexpr size_t BYTES = RINGO + RING_BYTES;
+  static_assert(HLOG <= 16, "16-bit list positions");
 };
 
 template <int HLOG>
@@ -1447,11 +1489,14 @@ __device__ inline Tables smem_tables(unsigned char* smem) {
   T.hsig = nullptr;  // packed entries
   T.pr = reinterpret_cast<int2*>(smem + L::PR);
   T.lnode = reinterpret_cast<int32_t*>(smem + L::LNODE);
-  T.lpos = reinterpret_cast<uint32_t*>(smem + L::LPOS);
+  T.lpos = nullptr;
+  T.lpos16 = reinterpret_cast<uint16_t*>(smem + L::LPOS);
   T.lvl = reinterpret_cast<int*>(smem + L::LVL);
+  T.ring = L::RING_BYTES ? reinterpret_cast<int*>(smem + L::RINGO) : nullptr;
   T.hlog = HLOG;
   T.hmask = (1u << HLOG) - 1u;
   T.lcap = L::LCAP;
+  T.frcap = L::FRCAP;
   T.maxd = FAST_MAXD;
   return T;
 }
@@ -1461,7 +1506,7 @@ constexpr int TF_SKIP_S = 1;
 constexpr int TF_SKIP_B = 2;
 constexpr int TF_SKIP_M = 4;
 constexpr int TF_WARP = 8;  // tier W first, whatever the launch's variant
-constexpr int TF_RING = 16;  // level scans through the async-copy ring (tiers S and B)
+constexpr int TF_RING = 16;  // tier S's level scans through the async-copy ring
 
 // queue counters in SampleParams::ctr
 constexpr int Q_NEXT_A = 0;   // next sample index of the batch
@@ -1528,10 +1573,12 @@ __device__ void clear_path_row(const SampleParams& P, int64_t out_i) {
 // MODE 1: the tier-L queue, on tier L.
 // SHL: the tier-S table size (2^SHL slots) of MODE 0; the small variant fits
 // one more CTA per SM and gives the same results (samples that outgrow it go
-// on to tier B as usual).  RG: the level scans keep more loads in flight
-// through an async-copy ring (for graphs whose CSR exceeds L2); same results.
+// on to tier B as usual).  RG (MODE 0 with the 4096-slot table only): the
+// level scans keep more loads in flight through an async-copy ring (for
+// graphs whose CSR exceeds L2); same results.
 template <int MODE, int SHL = FAST_HLOG, bool RG = false>
 __global__ void __launch_bounds__(NT, SHL == FAST_HLOG ? KD_MIN_BLOCKS : KD_MIN_BLOCKS + 1) k_sample(SampleParams P) {
+  static_assert(!RG || (MODE == 0 && SHL == FAST_HLOG), "the async-copy ring is laid out for tier S only");
   extern __shared__ __align__(16) unsigned char smem[];
   Ctl& c = *reinterpret_cast<Ctl*>(smem);
   Tables TS, TM;
@@ -2958,8 +3005,6 @@ kadabra_status ensure_ws(Workspace* w, uint64_t deferred_need, int njobs) {
     w->grid_warp = w->num_sms * std::max(per_sm, 1);
     w->smem_big = big_smem_bytes();
     KCK(cudaFuncSetAttribute(k_sample<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->smem_big));
-    KCK(cudaFuncSetAttribute(k_sample<2, FAST_HLOG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)w->smem_big));
     KCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample<2>, NT, w->smem_big));
     if (per_sm < 1) return fail(KADABRA_ERR_CAPACITY, "large-table sampler does not fit on an SM");
     w->grid_big = w->num_sms * per_sm;
@@ -3110,10 +3155,7 @@ kadabra_status launch_sampler_kernels(Workspace* w, SampleParams P, cudaStream_t
   else
     k_sample<0><<<w->grid_fast, NT, w->smem_fast, st>>>(P);
   KCK(cudaGetLastError());
-  if (rg)
-    k_sample<2, FAST_HLOG, true><<<w->grid_big, NT, w->smem_big, st>>>(P);
-  else
-    k_sample<2><<<w->grid_big, NT, w->smem_big, st>>>(P);
+  k_sample<2><<<w->grid_big, NT, w->smem_big, st>>>(P);  // tier B: register scans
   KCK(cudaGetLastError());
   P.pi_base = w->pi_gm;
   P.pcap = w->pcap_gm;
@@ -4352,6 +4394,7 @@ struct SrvJob {
   kadabra_config cfg;
   int64_t n = 0;
   uint64_t alpha = 0, cap = 0, K = 0, tau = 0, B = 0;
+  uint64_t taken = 0, chunk = 0;  // samples of the current batch already taken, and in this round
   int phase = 0;  // 0 admitted, 1 warm-up next, 2 main loop, 3 finished
   bool final_due = false;
   void* block = nullptr;  // one stream-ordered allocation for all device state
@@ -4705,17 +4748,30 @@ void srv_release(kadabra_server* S, SrvJob* J) {
 }
 
 // one round over the active jobs; returns the jobs that finished
+// Samples one round takes in all, shared among the active jobs: a job's
+// batch of K samples is taken in chunks of at least SRV_MIN_CHUNK over
+// several rounds when many jobs are active, and its stop test runs once the
+// K samples are in.  Sample indices and test points stay those of the job
+// alone, so results do not change; a round no longer lasts as long as the
+// largest job's batch, which would hold back the small jobs in it.
+constexpr uint64_t SRV_ROUND_SAMPLES = 16384;
+constexpr uint64_t SRV_MIN_CHUNK = 1024;
+
 kadabra_status srv_round(kadabra_server* S, std::vector<SrvJob*>& act, std::vector<SrvJob*>& done) {
   std::vector<Job> jobs;
   std::vector<SrvJob*> warm, main_j;
+  uint64_t nrun = 0;
+  for (SrvJob* J : act) nrun += (J->phase == 1 || J->phase == 2) ? 1 : 0;
+  const uint64_t quota = std::max<uint64_t>(SRV_MIN_CHUNK, SRV_ROUND_SAMPLES / std::max<uint64_t>(nrun, 1));
   for (SrvJob* J : act) {
     if (J->phase == 1) {
       if (J->k > 0) jobs.push_back(srv_job(J, 2, 0, J->alpha, J->count_pre));
       jobs.push_back(srv_job(J, 1, 0, J->alpha, J->count0));
       warm.push_back(J);
     } else if (J->phase == 2) {
-      J->B = std::min<uint64_t>(J->K, J->cap - J->tau);
-      jobs.push_back(srv_job(J, 0, J->tau, J->B, J->counts));
+      if (J->taken == 0) J->B = std::min<uint64_t>(J->K, J->cap - J->tau);  // the next batch
+      J->chunk = std::min<uint64_t>(J->B - J->taken, quota);
+      jobs.push_back(srv_job(J, 0, J->tau + J->taken, J->chunk, J->counts));
       main_j.push_back(J);
     }
   }
@@ -4743,12 +4799,15 @@ kadabra_status srv_round(kadabra_server* S, std::vector<SrvJob*>& act, std::vect
   KTRY(srv_compute_delta(S, warm));
   std::vector<SrvJob*> chk;
   for (SrvJob* J : main_j) {
+    J->taken += J->chunk;
+    if (J->taken < J->B) continue;  // the batch goes on next round
+    J->taken = 0;
     J->tau += J->B;
     if (J->tau >= J->cap) J->final_due = true;
     chk.push_back(J);
   }
   KTRY(srv_checks(S, chk));
-  for (SrvJob* J : main_j)
+  for (SrvJob* J : chk)
     if (J->final_due) {
       KTRY(srv_finish(S, J));
       done.push_back(J);
