@@ -356,7 +356,6 @@ struct Ctl {
   int sel_warp;
   int pick, pick_pos;
   int mode;       // backtracking: 0 = scan the row of x, 1 = scan the previous level
-  int next_x;     // backtracking: the node picked at this step
   int bt_half, bt_x, bt_dx;  // backtracking state between warp 0 and the block
   uint32_t bt_j;             //   and the next Philox block
   int cv, cw;     // chosen candidate edge (v on the s side, w on the t side)
@@ -3288,17 +3287,20 @@ kadabra_status compute_delta_host(int64_t n, const uint32_t* count0, uint64_t al
   return KADABRA_OK;
 }
 
-// Phase timing of graph loads on stderr when the environment variable
-// KADABRA_TRACE is set (each phase ends with a device synchronisation then).
+// Phase timing of graph loads and top-k runs on stderr when the environment
+// variable KADABRA_TRACE is set (each phase ends with a device
+// synchronisation then, which also slows the traced call).
 struct LoadTrace {
   bool on;
+  const char* what;
   std::chrono::steady_clock::time_point t0;
-  LoadTrace() : on(std::getenv("KADABRA_TRACE") != nullptr), t0(std::chrono::steady_clock::now()) {}
+  explicit LoadTrace(const char* w = "load")
+      : on(std::getenv("KADABRA_TRACE") != nullptr), what(w), t0(std::chrono::steady_clock::now()) {}
   void mark(const char* phase) {
     if (!on) return;
     cudaDeviceSynchronize();
     const auto t1 = std::chrono::steady_clock::now();
-    std::fprintf(stderr, "kadabra load: %-18s %8.3f ms\n", phase,
+    std::fprintf(stderr, "kadabra %s: %-18s %8.3f ms\n", what, phase,
                  std::chrono::duration<double, std::milli>(t1 - t0).count());
     t0 = t1;
   }
@@ -4095,11 +4097,43 @@ kadabra_status compute_delta_lv_host(int64_t n, const std::vector<double>& cL, c
                                      double* C_out, double* l0) {
   const size_t m = cL.size();
   const double target = (delta / 2.0) - (eps * delta);
+  // The c values repeat (they depend on a node's warm-up and preliminary
+  // counts and, for the few top-k nodes, its rank): each bisection step
+  // evaluates exp(-C / c) once per distinct c and then sums the nodes' terms
+  // in node order, so every term and the order of the additions are those of
+  // the plain per-node loop.
+  std::vector<double> vals;                   // distinct positive c values
+  std::vector<int32_t> iL(m, -1), iU(m, -1);  // each node's c_L, c_U in vals (-1: c <= 0)
+  {
+    size_t cap = 16;
+    while (cap < 4 * m + 16) cap <<= 1;
+    std::vector<uint64_t> keys(cap, 0);
+    std::vector<int32_t> slot(cap, -1);
+    auto intern = [&](double c) -> int32_t {
+      if (!(c > 0.0)) return -1;
+      uint64_t bits;
+      std::memcpy(&bits, &c, sizeof(bits));
+      size_t h = (size_t)((bits * 0x9E3779B97F4A7C15ull) >> 20) & (cap - 1);
+      while (slot[h] >= 0 && keys[h] != bits) h = (h + 1) & (cap - 1);
+      if (slot[h] < 0) {
+        keys[h] = bits;
+        slot[h] = (int32_t)vals.size();
+        vals.push_back(c);
+      }
+      return slot[h];
+    };
+    for (size_t i = 0; i < m; ++i) {
+      iL[i] = intern(cL[i]);
+      iU[i] = intern(cU[i]);
+    }
+  }
+  std::vector<double> ev(vals.size());
   auto sum_at = [&](double C) {
+    for (size_t u = 0; u < vals.size(); ++u) ev[u] = std::exp(-C / vals[u]);
     double sum = 0.0;
     for (size_t i = 0; i < m; ++i) {
-      const double eL = cL[i] > 0.0 ? std::exp(-C / cL[i]) : 0.0;
-      const double eU = cU[i] > 0.0 ? std::exp(-C / cU[i]) : 0.0;
+      const double eL = iL[i] >= 0 ? ev[iL[i]] : 0.0;
+      const double eU = iU[i] >= 0 ? ev[iU[i]] : 0.0;
       sum += eL + eU;
     }
     return sum;
@@ -4162,6 +4196,7 @@ kadabra_status run_topk(kadabra_graph* g, double lambda, double delta, int32_t k
   cudaStream_t st = as_stream(cfg.stream);
   Workspace* w = g->ws;
   const int64_t n = g->n;
+  LoadTrace tr("top-k run");
   const int k = (int)std::min<int64_t>(k_in, n), k1 = (int)std::min<int64_t>((int64_t)k_in + 1, n);
   kadabra_result& r = *out;
   r.vd = cfg.vd > 0 ? cfg.vd : g->vd;
@@ -4218,7 +4253,9 @@ kadabra_status run_topk(kadabra_graph* g, double lambda, double delta, int32_t k
     P.total_work = 2 * alpha;
     P.jobs = w->d_jobs;
     P.njobs = 2;
+    tr.mark("setup, tuning");
     KTRY(launch_sampler(w, P, st, variant));
+    tr.mark("warm-up samples");
   }
   const int rest_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(4 * (int64_t)w->num_sms, (n + 255) / 256));
   // selection (select_only) or Alg. 3 over `counts` at `tau`
@@ -4305,7 +4342,9 @@ kadabra_status run_topk(kadabra_graph* g, double lambda, double delta, int32_t k
     cU[i] = ((2.0 * b0) * r.omega) / (lamU * lamU);
   }
   double l0 = 0.0;
+  tr.mark("selection, targets");
   KTRY(compute_delta_lv_host(n, cL, cU, delta, cfg.eps, vL, vU, &r.C, &l0));
+  tr.mark("computeDelta");
   // per-node ln(1/delta) arrays: l0 everywhere, then the hit nodes' values
   if (g->tk_stage_cap < nnz) {
     KCK(cudaStreamSynchronize(st));
@@ -4329,6 +4368,7 @@ kadabra_status run_topk(kadabra_graph* g, double lambda, double delta, int32_t k
     RCK(cudaStreamSynchronize(st));  // host vectors stay alive until the copies are done
   }
   // main loop (Alg. 1) with Alg. 3 every K samples
+  tr.mark("delta arrays");
   uint64_t tau = 0;
   for (;;) {
     const uint64_t B = std::min<uint64_t>(K, cap - tau);
@@ -4336,10 +4376,12 @@ kadabra_status run_topk(kadabra_graph* g, double lambda, double delta, int32_t k
     P.total_work = B;
     P.job0 = job(0, tau, B, g->counts);
     KTRY(launch_sampler(w, P, st, variant));
+    tr.mark("main batch");
     tau += B;
     if (tau >= cap) break;
     r.checks++;
     KTRY(topk_pass(g->counts, tau, 0));
+    tr.mark("Alg. 3 test");
     if (!ho.fail) {
       r.stopped_early = 1;
       break;
