@@ -251,14 +251,19 @@ kadabra_status kadabra_graph_info(const kadabra_graph* g, int32_t* n, int64_t* m
  * arc loads in flight (asynchronous copies through shared memory).  The
  * library does this by itself for graphs whose CSR (forward plus reverse)
  * exceeds the device's L2, where those loads wait on HBM; the flag asks for it
- * on any graph, and a shared launch takes it from any of its graphs.  No flag
- * changes a result.  Returns KADABRA_ERR_ARG for unknown bits. */
+ * on any graph, and a shared launch takes it from any of its graphs.
+ * KADABRA_FLAG_FRONTIER_SEGMENTS makes the shared-memory tables scan every
+ * frontier in segments of 64 nodes, as they do for frontiers beyond their
+ * frontier array (2048 nodes); it exists to test that path and only slows
+ * sampling.  No flag changes a result.  Returns KADABRA_ERR_ARG for unknown
+ * bits. */
 enum {
   KADABRA_FLAG_GLOBAL_TABLES = 1,
   KADABRA_FLAG_MEDIUM_TABLES = 2,
   KADABRA_FLAG_LARGE_SHARED_TABLES = 4,
   KADABRA_FLAG_WARP_TIER = 8,
-  KADABRA_FLAG_ASYNC_SCAN = 16
+  KADABRA_FLAG_ASYNC_SCAN = 16,
+  KADABRA_FLAG_FRONTIER_SEGMENTS = 32
 };
 kadabra_status kadabra_graph_set_flags(kadabra_graph* g, uint32_t flags);
 

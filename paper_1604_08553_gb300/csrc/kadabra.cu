@@ -151,7 +151,7 @@ struct Tables {
   uint16_t* lpos16;         //   the same, 16 bits, in the shared-memory tiers (2^HLOG <= 2^16 slots)
   int2* pr;                 // frontier: {degree prefix, row start}; frcap+1 entries
   int lcap;
-  int frcap;                // largest frontier (a larger one sends the sample on)
+  int frcap;                // frontier nodes per scan segment (the frontier array's capacity)
   int* ring;                // the async-copy scan's per-warp ring (tier S only), else null
   int* lvl;                 // [side][lo|hi][maxd+2]
   int maxd;
@@ -1506,6 +1506,7 @@ constexpr int TF_SKIP_B = 2;
 constexpr int TF_SKIP_M = 4;
 constexpr int TF_WARP = 8;  // tier W first, whatever the launch's variant
 constexpr int TF_RING = 16;  // tier S's level scans through the async-copy ring
+constexpr int TF_SEG64 = 32;  // shared-memory tiers scan frontiers in 64-node segments (tests)
 
 // queue counters in SampleParams::ctr
 constexpr int Q_NEXT_A = 0;   // next sample index of the batch
@@ -1590,6 +1591,7 @@ __global__ void __launch_bounds__(NT, SHL == FAST_HLOG ? KD_MIN_BLOCKS : KD_MIN_
   if (MODE == 1) TM = gm_tables(P.gm_base + (size_t)blockIdx.x * P.gm_stride, P.gm_hlog, P.gm_lcap, GM_MAXD);
   TS.pi = TM.pi = pi;
   TS.pcap = TM.pcap = P.pcap;
+  if (MODE != 1 && (P.tier_flags & TF_SEG64)) TS.frcap = min(TS.frcap, 64);
 
   const int tid = threadIdx.x;
   if (MODE != 1)
@@ -3123,6 +3125,7 @@ SampleParams ws_params(const Workspace* w, uint32_t flags) {
   if (flags & KADABRA_FLAG_LARGE_SHARED_TABLES) P.tier_flags |= TF_SKIP_S;
   if (flags & KADABRA_FLAG_WARP_TIER) P.tier_flags |= TF_WARP;
   if (flags & (KADABRA_FLAG_ASYNC_SCAN | FLAG_RING_AUTO)) P.tier_flags |= TF_RING;
+  if (flags & KADABRA_FLAG_FRONTIER_SEGMENTS) P.tier_flags |= TF_SEG64;
   return P;
 }
 
@@ -5317,7 +5320,7 @@ void kadabra_release_cached(void) {
 kadabra_status kadabra_graph_set_flags(kadabra_graph* g, uint32_t flags) {
   if (!g) return fail(KADABRA_ERR_ARG, "graph is NULL");
   if (flags & ~(uint32_t)(KADABRA_FLAG_GLOBAL_TABLES | KADABRA_FLAG_MEDIUM_TABLES | KADABRA_FLAG_LARGE_SHARED_TABLES |
-                          KADABRA_FLAG_WARP_TIER | KADABRA_FLAG_ASYNC_SCAN))
+                          KADABRA_FLAG_WARP_TIER | KADABRA_FLAG_ASYNC_SCAN | KADABRA_FLAG_FRONTIER_SEGMENTS))
     return fail(KADABRA_ERR_ARG, "unknown flag");
   g->flags = flags;
   return KADABRA_OK;

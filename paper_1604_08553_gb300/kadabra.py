@@ -46,6 +46,7 @@ FLAG_MEDIUM_TABLES = 2
 FLAG_LARGE_SHARED_TABLES = 4
 FLAG_WARP_TIER = 8
 FLAG_ASYNC_SCAN = 16
+FLAG_FRONTIER_SEGMENTS = 32
 
 
 class KadabraError(RuntimeError):

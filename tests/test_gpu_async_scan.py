@@ -1,8 +1,10 @@
-"""The level scans through the async-copy ring (KADABRA_FLAG_ASYNC_SCAN; taken
-by itself for graphs whose CSR exceeds the L2) against the oracle and against
-the register scans (GPU only): per-sample pairs, paths, work counters and
-statuses bit-exact, whole runs identical.  The R-MAT scale-24 tests cover the
-automatic choice on a graph beyond the L2."""
+"""Variants of the level scans against the oracle (GPU only): the async-copy
+ring (KADABRA_FLAG_ASYNC_SCAN; taken by itself for graphs whose CSR exceeds
+the L2) and frontiers scanned in segments (KADABRA_FLAG_FRONTIER_SEGMENTS:
+64-node segments; by itself only for tier-B frontiers beyond 2048 nodes).
+Per-sample pairs, paths, work counters and statuses bit-exact, whole runs
+identical.  The R-MAT scale-24 tests cover the automatic ring on a graph
+beyond the L2."""
 
 import numpy as np
 import pytest
@@ -94,3 +96,33 @@ def test_async_scan_runs_identical(kd, gg, name, make, lam, k):
     assert np.array_equal(a.counts, b.counts) and np.array_equal(a.totals, b.totals), name
     if k:
         assert np.array_equal(a.topk, b.topk), name
+
+
+@pytest.mark.parametrize("name,make", GRAPHS, ids=[s[0] for s in GRAPHS])
+def test_frontier_segments_match_oracle(kd, orc, gg, name, make):
+    """Every frontier of more than 64 nodes scanned in segments, in tier S and
+    (all samples started there) in tier B, with either scan."""
+    g = make(gg)
+    ref = orc.sample_paths(g, 61, 0, 0, 2000, max_len=700)
+    for flag, tag in ((kd.FLAG_FRONTIER_SEGMENTS, "segments"),
+                      (kd.FLAG_FRONTIER_SEGMENTS | kd.FLAG_ASYNC_SCAN, "segments, ring"),
+                      (kd.FLAG_FRONTIER_SEGMENTS | kd.FLAG_LARGE_SHARED_TABLES, "segments, tier B")):
+        G = kd.kadabra_load_csr(g)
+        try:
+            G.set_flags(flag)
+            got, rc = kd.kadabra_sample_paths(G, 61, 0, 0, 2000, max_len=700, raise_on_error=False)
+        finally:
+            G.free()
+        assert rc == 0, (name, tag, rc)
+        _same_samples(got, ref, (name, tag))
+
+
+def test_frontier_segments_power_law(kd, orc, chung_lu_1m):
+    ref = orc.sample_paths(chung_lu_1m, 5, 0, 90_000, 1500)
+    G = kd.kadabra_load_csr(chung_lu_1m)
+    try:
+        G.set_flags(kd.FLAG_FRONTIER_SEGMENTS | kd.FLAG_LARGE_SHARED_TABLES)
+        got = kd.kadabra_sample_paths(G, 5, 0, 90_000, 1500)
+    finally:
+        G.free()
+    _same_samples(got, ref, "chung-lu segments, tier B")
