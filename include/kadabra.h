@@ -24,7 +24,9 @@
  *     host unless stated otherwise.
  *   - Randomness: Philox4x32-10 (Salmon et al., SC'11), key = seed, counter
  *     = (sample index lo, hi, draw, domain); domain 0 = main loop,
- *     1 = warm-up.  Results depend only on (graph, parameters, seed).
+ *     1 = warm-up, 2 = top-k preliminary estimate, 3 = the sampler
+ *     autotuner's probe batches (nothing recorded).  Results depend only on
+ *     (graph, parameters, seed).
  */
 #ifndef KADABRA_H
 #define KADABRA_H
