@@ -3303,7 +3303,7 @@ struct LoadTrace {
     if (!on) return;
     cudaDeviceSynchronize();
     const auto t1 = std::chrono::steady_clock::now();
-    std::fprintf(stderr, "kadabra %s: %-18s %8.3f ms\n", what, phase,
+    std::fprintf(stderr, "kadabra %s: %-34s %8.3f ms\n", what, phase,
                  std::chrono::duration<double, std::milli>(t1 - t0).count());
     t0 = t1;
   }
@@ -3794,6 +3794,7 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
                           const uint64_t* seed, const int64_t* vd_override, const kadabra_config& cfg,
                           kadabra_result* out) {
   cudaStream_t st = as_stream(cfg.stream);
+  LoadTrace tr(G == 1 ? "run" : "batch run");
   struct State {
     kadabra_graph* g;
     uint64_t cap, alpha, K, tau;
@@ -3906,7 +3907,9 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
   // warm-up of every graph in one launch (Alg. 2 lines 1-5)
   jobs.clear();
   for (int i = 0; i < G; ++i) jobs.push_back(make_job(S[i], 1, 0, S[i].alpha, S[i].g->count0, seed[i]));
+  tr.mark("setup, tuning");
   KTRY(launch_jobs());
+  tr.mark("warm-up samples");
   // the non-zero warm-up counts of every graph, in node order, to the host
   {
     std::vector<NzJob> nzj(G);
@@ -3941,6 +3944,7 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
                              lambda[i], delta[i], cfg.eps, tab[i].data(), &out[i].C));
     RCK(cudaMemcpyAsync(S[i].g->lntab, tab[i].data(), sizeof(double) * tab[i].size(), cudaMemcpyHostToDevice, st));
   }
+  tr.mark("compaction, Alg. 2");
   // stop tests of a set of graphs in one launch
   std::vector<CheckTabJob> cj;
   std::vector<CheckOut> co;
@@ -3994,6 +3998,13 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
     }
     if (sampled.empty()) break;
     KTRY(launch_jobs());
+    if (tr.on) {
+      uint64_t ns = 0;
+      for (const Job& j : jobs) ns += j.count;
+      char what[64];
+      std::snprintf(what, sizeof(what), "batch: %zu graphs, %llu samples", sampled.size(), (unsigned long long)ns);
+      tr.mark(what);
+    }
     std::vector<int> to_check;
     for (size_t q = 0; q < sampled.size(); ++q) {
       const int i = sampled[q];
@@ -4008,6 +4019,7 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
       continue;
     }
     KTRY(check(to_check));
+    tr.mark("stop tests");
     for (size_t q = 0; q < to_check.size(); ++q) {
       const int i = to_check[q];
       out[i].checks++;

@@ -455,8 +455,11 @@ class Batch:
             self.views.append(gv)
 
     def run(self, lam, delta, seed, *, check_interval: int = 0, eps: float = 0.001,
-            stream: Optional[int] = None):
-        """KADABRA on every graph; lam/delta/seed are sequences of length G."""
+            stream: Optional[int] = None, d_counts=None, d_btilde=None, want_host: bool = True):
+        """KADABRA on every graph; lam/delta/seed are sequences of length G.
+        Host outputs are numpy arrays allocated here (want_host); d_counts /
+        d_btilde are optional sequences of G CUDA tensors (n_i int32 / float64)
+        that receive the results on the device."""
         lib = load_library()
         G = self.G
         cfg = config_default()
@@ -464,11 +467,16 @@ class Batch:
         cfg.check_interval = check_interval
         cfg.stream = stream
         res = (kadabra_result * G)()
-        counts = [np.zeros(n, dtype=np.uint32) for n in self.n]
-        btilde = [np.zeros(n, dtype=np.float64) for n in self.n]
+        counts = [np.zeros(n, dtype=np.uint32) for n in self.n] if want_host else [None] * G
+        btilde = [np.zeros(n, dtype=np.float64) for n in self.n] if want_host else [None] * G
         for i in range(G):
-            res[i].counts = counts[i].ctypes.data
-            res[i].btilde = btilde[i].ctypes.data
+            if want_host:
+                res[i].counts = counts[i].ctypes.data
+                res[i].btilde = btilde[i].ctypes.data
+            if d_counts is not None:
+                res[i].d_counts = d_counts[i].data_ptr()
+            if d_btilde is not None:
+                res[i].d_btilde = d_btilde[i].data_ptr()
         L = (C.c_double * G)(*lam)
         D = (C.c_double * G)(*delta)
         S = (C.c_uint64 * G)(*seed)
