@@ -2167,6 +2167,9 @@ __global__ void __launch_bounds__(256) k_check(const uint32_t* __restrict__ coun
 // g = (L/t)(a_U + a_U), increasing in L, so the block evaluates g once, at
 // the largest L among its unhit nodes; hit nodes take the full formula.  The
 // maxima and the decision equal those of the per-node evaluation bit for bit.
+// fail_fast: the caller reads the maxima only if the test holds, so once a
+// node fails (here or in another block) the rest of the nodes are skipped;
+// a test that holds finds no failure and evaluates every node.
 struct CheckTabJob {
   const uint32_t* counts;
   const uint32_t* count0;
@@ -2176,6 +2179,7 @@ struct CheckTabJob {
   double omega;
   double lambda;
   CheckOut* out;
+  int fail_fast;
 };
 
 __global__ void __launch_bounds__(256) k_check_tab(const CheckTabJob* __restrict__ jobs) {
@@ -2184,7 +2188,15 @@ __global__ void __launch_bounds__(256) k_check_tab(const CheckTabJob* __restrict
   const double t = (double)J.tau;
   unsigned long long mf = 0, mg = 0, mu = 0;  // bit patterns of non-negative doubles
   unsigned fail = 0;
+  int it = 0;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < J.n; v += (int64_t)gridDim.x * blockDim.x) {
+    if (J.fail_fast) {
+      if (fail) {
+        atomicOr(&J.out->fail, 1u);
+        break;
+      }
+      if ((++it & 7) == 0 && *(volatile const unsigned*)&J.out->fail) break;
+    }
     const uint32_t cnt = J.counts[v];
     const double L = J.lnT[J.count0[v]];
     if (cnt == 0) {
@@ -3766,6 +3778,7 @@ kadabra_status run_loop_graph(kadabra_graph* g, Workspace* w, cudaStream_t st, u
   std::memset(&hc, 0, sizeof(hc));
   hc.counts = g->counts;
   hc.count0 = g->count0;
+  hc.fail_fast = 1;  // the loop reads only the decision; the run's final test is a full one
   hc.lnT = g->lntab;
   hc.n = g->n;
   hc.omega = omega;
@@ -3948,11 +3961,13 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
   // stop tests of a set of graphs in one launch
   std::vector<CheckTabJob> cj;
   std::vector<CheckOut> co;
-  auto check = [&](const std::vector<int>& which) -> kadabra_status {
+  // fail_fast: an intermediate test, whose maxima are read only if it holds
+  auto check = [&](const std::vector<int>& which, bool fail_fast) -> kadabra_status {
     cj.clear();
     int64_t max_n = 1;
     for (int i : which) {
       CheckTabJob c;
+      c.fail_fast = fail_fast ? 1 : 0;
       c.counts = S[i].g->counts;
       c.count0 = S[i].g->count0;
       c.lnT = S[i].g->lntab;
@@ -4018,7 +4033,7 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
       KTRY(read_status(w, st));
       continue;
     }
-    KTRY(check(to_check));
+    KTRY(check(to_check, true));
     tr.mark("stop tests");
     for (size_t q = 0; q < to_check.size(); ++q) {
       const int i = to_check[q];
@@ -4032,7 +4047,7 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
   // f and g maxima at each final tau; b~ = counts / tau (Alg. 1 last line)
   std::vector<int> all(G);
   for (int i = 0; i < G; ++i) all[i] = i;
-  KTRY(check(all));
+  KTRY(check(all, false));
   std::vector<long long> tot((size_t)G * KADABRA_NSTAT);
   for (int i = 0; i < G; ++i) {
     kadabra_result& r = out[i];
@@ -4745,6 +4760,7 @@ kadabra_status srv_checks(kadabra_server* S, const std::vector<SrvJob*>& C) {
       cj[i].omega = J->res.omega;
       cj[i].lambda = J->lambda;
       cj[i].out = d_co + i;
+      cj[i].fail_fast = J->final_due ? 0 : 1;  // at ceil(omega) the maxima are the result
       max_n = std::max<int64_t>(max_n, J->n);
     }
     SCK(cudaMemcpyAsync(d_cj, cj.data(), sizeof(CheckTabJob) * G, cudaMemcpyHostToDevice, S->st));
