@@ -2472,6 +2472,7 @@ struct TopkJob {
   int k1;                                 // min(k + 1, n)
   const unsigned long long* cand;         // TK_BLOCKS * k1 keys of stage 1
   int select_only;                        // 1: only the selection (keys, nk)
+  int fail_fast;                          // the maxima are read only if the test holds: stop at a failure
   TopkOut* out;
 };
 
@@ -2539,7 +2540,18 @@ __global__ void __launch_bounds__(256) k_topk_rest(const TopkJob* __restrict__ j
   const unsigned long long key_k = J.out->key_k;
   unsigned long long mf = 0, mg = 0, mu = 0;
   unsigned fail = 0;
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < J.n; v += (int64_t)gridDim.x * blockDim.x) {
+  int it = 0;
+  // fail_fast: nothing to do once the k first nodes or another block failed
+  const bool skip = J.fail_fast && *(volatile const unsigned*)&J.out->fail;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < J.n && !skip;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    if (J.fail_fast) {
+      if (fail) {
+        atomicOr(&J.out->fail, 1u);
+        break;
+      }
+      if ((++it & 7) == 0 && *(volatile const unsigned*)&J.out->fail) break;
+    }
     const uint32_t cnt = J.counts[v];
     if (rank_key(cnt, v) >= key_k) continue;  // one of the k first nodes
     if (cnt == 0) {
@@ -4290,7 +4302,7 @@ kadabra_status run_topk(kadabra_graph* g, double lambda, double delta, int32_t k
   const int rest_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(4 * (int64_t)w->num_sms, (n + 255) / 256));
   // selection (select_only) or Alg. 3 over `counts` at `tau`
   TopkOut ho;
-  auto topk_pass = [&](const uint32_t* counts, uint64_t tau, int select_only) -> kadabra_status {
+  auto topk_pass = [&](const uint32_t* counts, uint64_t tau, int select_only, int fail_fast = 0) -> kadabra_status {
     TopkJob J;
     std::memset(&J, 0, sizeof(J));
     J.counts = counts;
@@ -4304,6 +4316,7 @@ kadabra_status run_topk(kadabra_graph* g, double lambda, double delta, int32_t k
     J.k1 = k1;
     J.cand = g->tk_cand;
     J.select_only = select_only;
+    J.fail_fast = fail_fast;
     J.out = d_out;
     RCK(cudaMemcpyAsync(d_job, &J, sizeof(J), cudaMemcpyHostToDevice, st));
     RCK(cudaMemsetAsync(d_out, 0, sizeof(TopkOut), st));
@@ -4410,7 +4423,7 @@ kadabra_status run_topk(kadabra_graph* g, double lambda, double delta, int32_t k
     tau += B;
     if (tau >= cap) break;
     r.checks++;
-    KTRY(topk_pass(g->counts, tau, 0));
+    KTRY(topk_pass(g->counts, tau, 0, 1));  // the run's final pass below is a full one
     tr.mark("Alg. 3 test");
     if (!ho.fail) {
       r.stopped_early = 1;
@@ -4599,7 +4612,8 @@ Job srv_job(const SrvJob* J, uint32_t domain, uint64_t first, uint64_t count, ui
 }
 
 // selection (select_only) or Alg. 3 of one top-k job over its counts at tau
-kadabra_status srv_topk_pass(kadabra_server* S, SrvJob* J, const uint32_t* counts, int select_only, TopkOut* ho) {
+kadabra_status srv_topk_pass(kadabra_server* S, SrvJob* J, const uint32_t* counts, int select_only, TopkOut* ho,
+                             int fail_fast = 0) {
   TopkJob T;
   std::memset(&T, 0, sizeof(T));
   T.counts = counts;
@@ -4613,6 +4627,7 @@ kadabra_status srv_topk_pass(kadabra_server* S, SrvJob* J, const uint32_t* count
   T.k1 = J->k1;
   T.cand = J->cand;
   T.select_only = select_only;
+  T.fail_fast = fail_fast;
   T.out = S->d_tko;
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(4 * (int64_t)S->num_sms, (J->n + 255) / 256));
   SCK(cudaMemcpyAsync(S->d_tk, &T, sizeof(T), cudaMemcpyHostToDevice, S->st));
@@ -4787,7 +4802,7 @@ kadabra_status srv_checks(kadabra_server* S, const std::vector<SrvJob*>& C) {
   for (SrvJob* J : C) {
     if (J->k == 0) continue;
     TopkOut ho;
-    KTRY(srv_topk_pass(S, J, J->counts, 0, &ho));
+    KTRY(srv_topk_pass(S, J, J->counts, 0, &ho, J->final_due ? 0 : 1));
     std::memcpy(&J->res.max_f, &ho.max_f_bits, sizeof(double));
     std::memcpy(&J->res.max_g, &ho.max_g_bits, sizeof(double));
     J->h_topk.resize(J->k);
