@@ -207,11 +207,12 @@ def run_launches(r, w):
         return sb + 2 + 3 + 2 + 3 * (int(r.checks) + 1) + 1
     # one-graph all-nodes runs with more than 4 possible rounds loop on the
     # device: per round a begin kernel, the sampler batch, the stop test and an
-    # end kernel; shorter runs take host rounds (batch, then a test if tau < cap)
+    # end kernel; shorter runs take host rounds (batch, then a test if tau <
+    # cap), and their first batch shares the warm-up's launch
     cap_rounds = -(-int(r.omega_cap) // w["check_interval"])
     if cap_rounds > 4:
         return spb + 3 + (spb + 3) * rounds + 1 + 1
-    return spb * (1 + rounds) + 3 + int(r.checks) + 1 + 1
+    return spb * rounds + 3 + int(r.checks) + 1 + 1
 
 
 def sampler_launches_per_batch(r=None):

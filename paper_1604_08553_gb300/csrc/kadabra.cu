@@ -3823,6 +3823,7 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
   struct State {
     kadabra_graph* g;
     uint64_t cap, alpha, K, tau;
+    uint64_t pre;  // main-loop samples already taken with the warm-up, not yet in tau
     bool done;
   };
   std::vector<State> S(G);
@@ -3839,11 +3840,12 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
     s.alpha = r.alpha = std::max<uint64_t>(1, (uint64_t)std::floor(r.omega / 100.0));
     s.K = r.check_interval = cfg.check_interval ? cfg.check_interval : auto_check_interval(r.omega);
     s.tau = 0;
+    s.pre = 0;
     s.done = false;
     sum_alpha += s.alpha;
     sum_k += std::min(s.K, s.cap);
   }
-  KTRY(ensure_ws(w, std::max(sum_alpha, sum_k), G));
+  KTRY(ensure_ws(w, sum_alpha + sum_k, 2 * G));
   for (State& s : S) {
     KTRY(ensure_run_buffers(s.g));
     if (s.g->lntab_cap < s.alpha + 1) {
@@ -3929,9 +3931,19 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
     j.totals = s.g->totals;
     return j;
   };
-  // warm-up of every graph in one launch (Alg. 2 lines 1-5)
+  // Warm-up of every graph in one launch (Alg. 2 lines 1-5).  With host
+  // rounds the same launch also takes each graph's first main-loop batch:
+  // those samples depend only on their indices, not on computeDelta, which
+  // only the first stop test needs; so the warm-up's short launch does not
+  // run on its own.  (The device-driven loop samples its first batch itself.)
+  const bool loop_on_device = G == 1 && (S[0].cap + S[0].K - 1) / S[0].K > LOOP_GRAPH_MIN_ROUNDS;
   jobs.clear();
   for (int i = 0; i < G; ++i) jobs.push_back(make_job(S[i], 1, 0, S[i].alpha, S[i].g->count0, seed[i]));
+  if (!loop_on_device)
+    for (int i = 0; i < G; ++i) {
+      S[i].pre = std::min<uint64_t>(S[i].K, S[i].cap);
+      jobs.push_back(make_job(S[i], 0, 0, S[i].pre, S[i].g->counts, seed[i]));
+    }
   tr.mark("setup, tuning");
   KTRY(launch_jobs());
   tr.mark("warm-up samples");
@@ -4004,7 +4016,7 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
   // main loop (Alg. 1): on the device for one graph with enough rounds to
   // repay building its CUDA graph, rounds from the host otherwise (same
   // results either way)
-  if (G == 1 && (S[0].cap + S[0].K - 1) / S[0].K > LOOP_GRAPH_MIN_ROUNDS) {
+  if (loop_on_device) {
     uint64_t checks = 0;
     int stopped = 0;
     KTRY(run_loop_graph(S[0].g, w, st, seed[0], S[0].cap, S[0].K, out[0].omega, lambda[0], variant, &S[0].tau,
@@ -4016,15 +4028,22 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
   for (;;) {
     jobs.clear();
     std::vector<int> sampled;
+    std::vector<uint64_t> taken;
     for (int i = 0; i < G; ++i) {
       State& s = S[i];
       if (s.done) continue;
-      const uint64_t B = std::min<uint64_t>(s.K, s.cap - s.tau);
-      jobs.push_back(make_job(s, 0, s.tau, B, s.g->counts, seed[i]));
+      if (s.pre) {  // the first batch, sampled with the warm-up
+        taken.push_back(s.pre);
+        s.pre = 0;
+      } else {
+        const uint64_t B = std::min<uint64_t>(s.K, s.cap - s.tau);
+        jobs.push_back(make_job(s, 0, s.tau, B, s.g->counts, seed[i]));
+        taken.push_back(B);
+      }
       sampled.push_back(i);
     }
     if (sampled.empty()) break;
-    KTRY(launch_jobs());
+    if (!jobs.empty()) KTRY(launch_jobs());
     if (tr.on) {
       uint64_t ns = 0;
       for (const Job& j : jobs) ns += j.count;
@@ -4035,7 +4054,7 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
     std::vector<int> to_check;
     for (size_t q = 0; q < sampled.size(); ++q) {
       const int i = sampled[q];
-      S[i].tau += jobs[q].count;
+      S[i].tau += taken[q];
       if (S[i].tau >= S[i].cap)
         S[i].done = true;
       else
