@@ -202,16 +202,16 @@ def run_launches(r, w):
     Alg. 3 test (checks + the final one) and b~."""
     rounds = -(-int(r.tau) // w["check_interval"])
     spb = sampler_launches_per_batch(r)
-    sb = spb * (1 + rounds)
+    # the first main-loop batch shares the warm-up's launch
     if w.get("k"):
-        return sb + 2 + 3 + 2 + 3 * (int(r.checks) + 1) + 1
-    # one-graph all-nodes runs with more than 4 possible rounds loop on the
-    # device: per round a begin kernel, the sampler batch, the stop test and an
-    # end kernel; shorter runs take host rounds (batch, then a test if tau <
-    # cap), and their first batch shares the warm-up's launch
+        return spb * rounds + 2 + 3 + 2 + 3 * (int(r.checks) + 1) + 1
+    # one-graph all-nodes runs with more than 4 possible rounds test the first
+    # round from the host and loop on the device from the second: per round a
+    # begin kernel, the sampler batch, the stop test and an end kernel;
+    # shorter runs take host rounds (batch, then a test if tau < cap)
     cap_rounds = -(-int(r.omega_cap) // w["check_interval"])
     if cap_rounds > 4:
-        return spb + 3 + (spb + 3) * rounds + 1 + 1
+        return spb + 3 + 1 + (spb + 3) * (rounds - 1) + 1 + 1
     return spb * rounds + 3 + int(r.checks) + 1 + 1
 
 

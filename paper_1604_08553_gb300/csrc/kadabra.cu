@@ -3757,6 +3757,7 @@ kadabra_status loop_graph_ready(kadabra_graph* g, Workspace* w, const SamplePara
 
 // Runs the main loop of one all-nodes run on the device; returns tau, the
 // number of tests and whether one held.
+// *tau: the samples already taken on entry (a multiple of K), the final tau on return.
 kadabra_status run_loop_graph(kadabra_graph* g, Workspace* w, cudaStream_t st, uint64_t seed, uint64_t cap, uint64_t K,
                               double omega, double lambda, int variant, uint64_t* tau, uint64_t* checks, int* stopped) {
   if (!g->loop_dev) {
@@ -3776,6 +3777,7 @@ kadabra_status run_loop_graph(kadabra_graph* g, Workspace* w, cudaStream_t st, u
   KTRY(loop_graph_ready(g, w, P, check_blocks, variant));
   LoopState hs;
   std::memset(&hs, 0, sizeof(hs));
+  hs.tau = *tau;
   hs.cap = cap;
   hs.K = K;
   hs.n = g->n;
@@ -3931,19 +3933,19 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
     j.totals = s.g->totals;
     return j;
   };
-  // Warm-up of every graph in one launch (Alg. 2 lines 1-5).  With host
-  // rounds the same launch also takes each graph's first main-loop batch:
-  // those samples depend only on their indices, not on computeDelta, which
-  // only the first stop test needs; so the warm-up's short launch does not
-  // run on its own.  (The device-driven loop samples its first batch itself.)
+  // Warm-up of every graph in one launch (Alg. 2 lines 1-5).  The same
+  // launch also takes each graph's first main-loop batch: those samples
+  // depend only on their indices, not on computeDelta, which only the first
+  // stop test needs; so the warm-up's short launch does not run on its own.
+  // The first round's test runs from the host; a device-driven loop takes
+  // the later rounds.
   const bool loop_on_device = G == 1 && (S[0].cap + S[0].K - 1) / S[0].K > LOOP_GRAPH_MIN_ROUNDS;
   jobs.clear();
   for (int i = 0; i < G; ++i) jobs.push_back(make_job(S[i], 1, 0, S[i].alpha, S[i].g->count0, seed[i]));
-  if (!loop_on_device)
-    for (int i = 0; i < G; ++i) {
-      S[i].pre = std::min<uint64_t>(S[i].K, S[i].cap);
-      jobs.push_back(make_job(S[i], 0, 0, S[i].pre, S[i].g->counts, seed[i]));
-    }
+  for (int i = 0; i < G; ++i) {
+    S[i].pre = std::min<uint64_t>(S[i].K, S[i].cap);
+    jobs.push_back(make_job(S[i], 0, 0, S[i].pre, S[i].g->counts, seed[i]));
+  }
   tr.mark("setup, tuning");
   KTRY(launch_jobs());
   tr.mark("warm-up samples");
@@ -4016,16 +4018,17 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
   // main loop (Alg. 1): on the device for one graph with enough rounds to
   // repay building its CUDA graph, rounds from the host otherwise (same
   // results either way)
-  if (loop_on_device) {
-    uint64_t checks = 0;
-    int stopped = 0;
-    KTRY(run_loop_graph(S[0].g, w, st, seed[0], S[0].cap, S[0].K, out[0].omega, lambda[0], variant, &S[0].tau,
-                        &checks, &stopped));
-    out[0].checks = checks;
-    out[0].stopped_early = stopped;
-    S[0].done = true;
-  }
   for (;;) {
+    if (loop_on_device && S[0].tau > 0 && !S[0].done) {  // rounds 2, 3, ... on the device
+      uint64_t checks = 0;
+      int stopped = 0;
+      KTRY(run_loop_graph(S[0].g, w, st, seed[0], S[0].cap, S[0].K, out[0].omega, lambda[0], variant, &S[0].tau,
+                          &checks, &stopped));
+      out[0].checks += checks;
+      out[0].stopped_early = stopped;
+      S[0].done = true;
+      break;
+    }
     jobs.clear();
     std::vector<int> sampled;
     std::vector<uint64_t> taken;
@@ -4267,7 +4270,7 @@ kadabra_status run_topk(kadabra_graph* g, double lambda, double delta, int32_t k
   const uint64_t cap = r.omega_cap = (uint64_t)cap_d;
   const uint64_t alpha = r.alpha = std::max<uint64_t>(1, (uint64_t)std::floor(r.omega / 100.0));
   const uint64_t K = r.check_interval = cfg.check_interval ? cfg.check_interval : auto_check_interval(r.omega);
-  KTRY(ensure_ws(w, std::max(2 * alpha, std::min(K, cap)), 2));
+  KTRY(ensure_ws(w, 2 * alpha + std::min(K, cap), 3));
   KTRY(ensure_run_buffers(g));
   KTRY(ensure_topk_buffers(g, st));
   if (w->nz_cap < 1) {
@@ -4304,16 +4307,19 @@ kadabra_status run_topk(kadabra_graph* g, double lambda, double delta, int32_t k
     j.totals = g->totals;
     return j;
   };
-  // preliminary estimate and warm-up, one launch
+  // preliminary estimate, warm-up and the first main-loop batch, one launch
+  // (main-loop samples do not depend on the targets or computeDelta)
+  const uint64_t B0 = std::min<uint64_t>(K, cap);
   {
-    Job jobs[2] = {job(2, 0, alpha, g->count_pre), job(1, 0, alpha, g->count0)};
+    Job jobs[3] = {job(2, 0, alpha, g->count_pre), job(1, 0, alpha, g->count0), job(0, 0, B0, g->counts)};
     jobs[0].work_begin = 0;
     jobs[1].work_begin = alpha;
+    jobs[2].work_begin = 2 * alpha;
     RCK(cudaMemcpyAsync(w->d_jobs, jobs, sizeof(jobs), cudaMemcpyHostToDevice, st));
     SampleParams P = ws_params(w, launch_flags(g));
-    P.total_work = 2 * alpha;
+    P.total_work = 2 * alpha + B0;
     P.jobs = w->d_jobs;
-    P.njobs = 2;
+    P.njobs = 3;
     tr.mark("setup, tuning");
     KTRY(launch_sampler(w, P, st, variant));
     tr.mark("warm-up samples");
@@ -4434,11 +4440,13 @@ kadabra_status run_topk(kadabra_graph* g, double lambda, double delta, int32_t k
   uint64_t tau = 0;
   for (;;) {
     const uint64_t B = std::min<uint64_t>(K, cap - tau);
-    SampleParams P = ws_params(w, launch_flags(g));
-    P.total_work = B;
-    P.job0 = job(0, tau, B, g->counts);
-    KTRY(launch_sampler(w, P, st, variant));
-    tr.mark("main batch");
+    if (tau > 0) {  // the first batch came with the warm-up
+      SampleParams P = ws_params(w, launch_flags(g));
+      P.total_work = B;
+      P.job0 = job(0, tau, B, g->counts);
+      KTRY(launch_sampler(w, P, st, variant));
+      tr.mark("main batch");
+    }
     tau += B;
     if (tau >= cap) break;
     r.checks++;
