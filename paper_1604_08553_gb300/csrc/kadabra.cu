@@ -4878,11 +4878,19 @@ kadabra_status srv_round(kadabra_server* S, std::vector<SrvJob*>& act, std::vect
   uint64_t nrun = 0;
   for (SrvJob* J : act) nrun += (J->phase == 1 || J->phase == 2) ? 1 : 0;
   const uint64_t quota = std::max<uint64_t>(SRV_MIN_CHUNK, SRV_ROUND_SAMPLES / std::max<uint64_t>(nrun, 1));
+  std::vector<SrvJob*> first;  // new jobs whose first main-loop chunk rides with their warm-up
   for (SrvJob* J : act) {
     if (J->phase == 1) {
       if (J->k > 0) jobs.push_back(srv_job(J, 2, 0, J->alpha, J->count_pre));
       jobs.push_back(srv_job(J, 1, 0, J->alpha, J->count0));
       warm.push_back(J);
+      // main-loop samples do not depend on computeDelta: the first batch (or
+      // its first chunk) goes into the same launch
+      J->B = std::min<uint64_t>(J->K, J->cap - J->tau);
+      J->taken = 0;
+      J->chunk = std::min<uint64_t>(J->B, quota);
+      jobs.push_back(srv_job(J, 0, J->tau, J->chunk, J->counts));
+      first.push_back(J);
     } else if (J->phase == 2) {
       if (J->taken == 0) J->B = std::min<uint64_t>(J->K, J->cap - J->tau);  // the next batch
       J->chunk = std::min<uint64_t>(J->B - J->taken, quota);
@@ -4912,6 +4920,7 @@ kadabra_status srv_round(kadabra_server* S, std::vector<SrvJob*>& act, std::vect
   KTRY(launch_sampler(w, P, S->st));
   KTRY(read_status(w, S->st));
   KTRY(srv_compute_delta(S, warm));
+  main_j.insert(main_j.end(), first.begin(), first.end());  // now in the main loop, their chunk taken
   std::vector<SrvJob*> chk;
   for (SrvJob* J : main_j) {
     J->taken += J->chunk;
