@@ -48,7 +48,7 @@ METRIC = "paths/sec & time-to-(lambda,delta) per graph, batched vs plain on GPU;
 WORKLOADS = {
     "chung_lu_1m": dict(family="chung_lu", n=1_000_000, beta=2.5, mean_deg=16.0, max_deg=10_000.0, graph_seed=1,
                         lcc=True, lam=0.005, delta=0.1, check_interval=1 << 16,
-                        sampler_dram_bytes=76_713_984 + 5_561_856 + 46_348_800 + 2_607_616 + 65_536),
+                        sampler_dram_bytes=76_722_944 + 5_625_600 + 46_457_600 + 2_017_792 + 65_536),
     "erdos_renyi_2k": dict(family="erdos_renyi", n=2000, mean_deg=8.0, graph_seed=1, lcc=True, lam=0.01,
                            delta=0.1, check_interval=1000, sampler_dram_bytes=None),
     "rmat_24": dict(family="rmat", scale=24, edge_factor=16, a=0.57, b=0.19, c=0.19, graph_seed=1, lam=0.0025,

@@ -2774,6 +2774,13 @@ __global__ void k_und_degree_key(const int32_t* rp, const int32_t* rrp, const ui
   atomicMax(best, mine);
 }
 
+// the root r from its key (lowest id among the maximum degree): level 0 = {r}
+__global__ void k_bfs_root(const unsigned long long* best, int32_t* dist, int32_t* front) {
+  const int32_t r = (int32_t)(0xFFFFFFFFu - (uint32_t)(*best & 0xFFFFFFFFull));
+  dist[r] = 0;
+  front[0] = r;
+}
+
 // One level of the BFS over the underlying undirected graph (out-rows, and
 // in-rows too for a directed graph).  A warp expands one frontier node's row
 // of up to BFS_CHUNK arcs; a longer row is cut into BFS_CHUNK-arc items for
@@ -2809,11 +2816,45 @@ __device__ __forceinline__ void bfs_scan(const int32_t* c, int32_t a, int32_t b,
 
 // The frontier's size is read on the device (*nfront_dev, or 1 for the root's
 // level when it is null), so the host can queue several levels at once.
+// A frontier of more than n / BFS_BOTTOM_UP nodes is expanded bottom-up
+// (Beamer et al.'s direction-optimising BFS): every unvisited node looks for
+// a neighbour at the current level and stops at the first.  Either direction
+// yields the same next level, so the eccentricity does not depend on it.
+constexpr int BFS_BOTTOM_UP = 16;
+
 __global__ void k_bfs_level(const int32_t* rp, const int32_t* ci, const int32_t* rrp, const int32_t* rci, int directed,
                             const int32_t* front, const int32_t* nfront_dev, int32_t* next, int32_t* nnext,
-                            int32_t* dist, int32_t level, BfsItem* items, int32_t* nitems, int32_t items_cap) {
+                            int32_t* dist, int32_t level, BfsItem* items, int32_t* nitems, int32_t items_cap,
+                            int32_t n) {
   const int lane = lane_id();
   const int32_t nfront = nfront_dev ? *nfront_dev : 1;
+  if (nfront > n / BFS_BOTTOM_UP) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;  // a multiple of 32: warps stay whole
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+      const int64_t v = base + threadIdx.x;
+      bool mine = false;
+      if (v < n && dist[v] < 0) {
+        for (int pass = 0; pass < (directed ? 2 : 1) && !mine; ++pass) {
+          const int32_t* r = pass ? rrp : rp;
+          const int32_t* c = pass ? rci : ci;
+          for (int32_t e = r[v]; e < r[v + 1]; ++e)
+            if (dist[c[e]] == level) {
+              mine = true;
+              break;
+            }
+        }
+        if (mine) dist[v] = level + 1;  // only this thread writes v's entry
+      }
+      const unsigned got = __ballot_sync(FULL, mine);
+      if (got) {
+        int32_t at = 0;
+        if (lane == 0) at = atomicAdd(nnext, __popc(got));
+        at = __shfl_sync(FULL, at, 0);
+        if (mine) next[at + __popc(got & ((1u << lane) - 1u))] = (int32_t)v;
+      }
+    }
+    return;
+  }
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = w0; i < nfront; i += nwarps) {
@@ -3380,15 +3421,10 @@ kadabra_status compute_vd(kadabra_graph* g, LoadTrace& tr, const LoadScratch& S)
   const int32_t* rrp = g->directed ? g->rrp : g->rp;
   const int32_t* rci = g->directed ? g->rci : g->ci;
   const int blocks = std::max(1, std::min(4 * g->num_sms, (n + 255) / 256));
+  KCK(cudaMemsetAsync(S.dist, 0xFF, sizeof(int32_t) * (size_t)n));
   k_und_degree_key<<<blocks, 256>>>(g->rp, rrp, S.recip, n, g->directed, S.best);
-  unsigned long long hb = 0;
-  if (cudaMemcpy(&hb, S.best, sizeof(hb), cudaMemcpyDeviceToHost) != cudaSuccess)
-    return fail(KADABRA_ERR_CUDA, std::string("vd: ") + cudaGetErrorString(cudaGetLastError()));
-  const int32_t r = (int32_t)(0xFFFFFFFFu - (uint32_t)(hb & 0xFFFFFFFFull));
-  KCK(cudaMemset(S.dist, 0xFF, sizeof(int32_t) * (size_t)n));
-  const int32_t zero = 0;
-  KCK(cudaMemcpy(S.dist + r, &zero, sizeof(int32_t), cudaMemcpyHostToDevice));
-  KCK(cudaMemcpy(S.qa, &r, sizeof(int32_t), cudaMemcpyHostToDevice));
+  k_bfs_root<<<1, 1>>>(S.best, S.dist, S.qa);  // the root stays on the device
+  KCK(cudaGetLastError());
   tr.mark("vd root");
   // Levels are queued BFS_BATCH at a time and their sizes read back once per
   // batch; levels past the end find an empty frontier and do nothing.
@@ -3405,7 +3441,7 @@ kadabra_status compute_vd(kadabra_graph* g, LoadTrace& tr, const LoadScratch& S)
       int32_t* c = S.cnt + 2 * (l % SLOTS);
       const int32_t* prev = l == 0 ? nullptr : S.cnt + 2 * ((l + SLOTS - 1) % SLOTS);
       k_bfs_level<<<8 * g->num_sms, 256>>>(g->rp, g->ci, rrp, rci, g->directed, in_q, prev, out_q, c, S.dist, l,
-                                           S.items, c + 1, S.items_cap);
+                                           S.items, c + 1, S.items_cap, n);
       k_bfs_items<<<8 * g->num_sms, 256>>>(g->ci, rci, S.items, c + 1, S.items_cap, out_q, c, S.dist, l);
     }
     int32_t h[2 * SLOTS];
