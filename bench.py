@@ -174,6 +174,18 @@ def algorithmic_bytes(totals, hits):
     return (8 * t[1] + 8 * t[0] + 12 * t[2] + 8 * t[3] + 4 * hits + 4 * t[6])
 
 
+def sector_bytes(totals, hits):
+    """The same work at the granularity of 32 B sectors of L2 and DRAM: the
+    two offsets of an expanded node share one sector; its row's arcs are read
+    contiguously (4 B each plus about one partial sector per row); a hit
+    counter update moves one sector; backtracking reads one offset sector and
+    one partial row sector per path node plus 4 B per scanned position.  The
+    visited-set probes, level lists and sigma updates of the shared-memory
+    tiers cost no L2 or DRAM bytes."""
+    t = totals
+    return 64 * t[1] + 4 * t[0] + 32 * hits + 4 * t[6] + 64 * t[7]
+
+
 def replica_seed(rank: int, step: int) -> int:
     """Seed of a timed step on a rank: replicas sample different paths."""
     return 1 + step + 7919 * rank
@@ -648,7 +660,7 @@ def main():
     # ---- dominant kernel: the sampler, timed per launch on its stream
     K = w["check_interval"]
     d_tot = torch.zeros(kd.NSTAT, dtype=torch.int64, device="cuda")
-    samp_times, samp_bytes = [], []
+    samp_times, samp_bytes, samp_sectors = [], [], []
     for i in range(4):
         flush.fill_(float(i))
         d_counts.zero_()
@@ -665,8 +677,10 @@ def main():
         samp_times.append(ev0.elapsed_time(ev1) / 1e3)
         hits = int(d_counts.sum().item())
         samp_bytes.append(algorithmic_bytes(d_tot.cpu().numpy(), hits))
+        samp_sectors.append(sector_bytes(d_tot.cpu().numpy(), hits))
     avg_t = sum(samp_times) / len(samp_times)
     avg_b = sum(samp_bytes) / len(samp_bytes)
+    avg_s = sum(samp_sectors) / len(samp_sectors)
     peak, peak_src = peaks()
     achieved = avg_b / avg_t / 1e9
     tot_np = d_tot.cpu().numpy()
@@ -722,9 +736,11 @@ def main():
     roof_l2 = None
     if csr_bytes < l2_size:
         l2 = l2_read_peak_gbs()
+        sec = avg_s / avg_t / 1e9
         roof_l2 = {"bound": "l2", "achieved": achieved, "peak": l2, "unit": "GB/s", "frac": achieved / l2,
                    "peak_source": "measured here: kadabra_l2_read_probe, 32 MB L2-resident buffer read 50 times",
-                   "csr_bytes": csr_bytes, "l2_bytes": l2_size}
+                   "csr_bytes": csr_bytes, "l2_bytes": l2_size,
+                   "sector_bytes_per_launch": avg_s, "achieved_sector_granular": sec, "frac_sector_granular": sec / l2}
 
     if rank == 0:
         r0 = results[0]
