@@ -83,9 +83,11 @@ typedef struct {
                               by the library from omega: max(1024, ceil(omega/32)))  */
   void* stream;            /* cudaStream_t for all work of the call (NULL = default) */
   int32_t ctas_per_sm;     /* shared-memory sampler tier, as resident CTAs per SM: 0 =
-                              autotuned per graph (a probe batch times both tables on
-                              the first one-graph run), or one of the two values the
-                              library offers (3: 4096-slot tables, 4: 2048-slot);
+                              autotuned per graph (on the first one-graph run a probe
+                              batch of min(K, 4096) samples times every allowed setup
+                              of table and warp tier; the choice is cached per graph
+                              fingerprint), or one of the two values the library
+                              offers (3: 4096-slot tables, 4: 2048-slot);
                               any other value is KADABRA_ERR_ARG.  Results do not
                               depend on it.  Batches and serving use the default.  */
   int32_t warp_tier;       /* one-warp-per-sample tier in front of tier S (samples whose
@@ -216,9 +218,12 @@ kadabra_status kadabra_l2_read_probe(uint64_t bytes, int32_t reps, double* gbs);
  * once.  Only before the first submit (KADABRA_ERR_ARG after). */
 kadabra_status kadabra_serve_configure(uint64_t budget_bytes, int32_t max_active);
 
-/* Queues one run of KADABRA on g (arguments as kadabra_run; cfg->stream and
- * cfg->ctas_per_sm are ignored: the server has its own stream).  Returns at
- * once with a job id in *job.  Argument errors are returned here. */
+/* Queues one run of KADABRA on g (arguments as kadabra_run; cfg->stream,
+ * cfg->ctas_per_sm and cfg->warp_tier are ignored: the server has its own
+ * stream and shares launches between jobs).  Returns at once with a job id
+ * in *job.  Argument errors are returned here, including a batch's graph
+ * view (not accepted).  g must stay loaded until the job is collected by
+ * kadabra_poll or dropped by kadabra_serve_shutdown. */
 kadabra_status kadabra_submit(kadabra_graph* g, double lambda, double delta, int32_t k, uint64_t seed,
                               const kadabra_config* cfg, uint64_t* job);
 
@@ -249,8 +254,8 @@ kadabra_status kadabra_graph_info(const kadabra_graph* g, int32_t* n, int64_t* m
  * a batch or serving launch shared by several graphs runs that tier first if
  * any of them has the flag (and ignores their other flags).  It has no effect
  * together with one of the three flags above.  KADABRA_FLAG_ASYNC_SCAN makes
- * the level scans of the 4096- and 8192-slot shared-memory tables keep more
- * arc loads in flight (asynchronous copies through shared memory).  The
+ * the level scans of the 4096-slot shared-memory table keep more arc loads in
+ * flight (asynchronous copies through shared memory).  The
  * library does this by itself for graphs whose CSR (forward plus reverse)
  * exceeds the device's L2, where those loads wait on HBM; the flag asks for it
  * on any graph, and a shared launch takes it from any of its graphs.
