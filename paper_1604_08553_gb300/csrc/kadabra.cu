@@ -3793,9 +3793,11 @@ kadabra_status loop_graph_ready(kadabra_graph* g, Workspace* w, const SamplePara
 
 // Runs the main loop of one all-nodes run on the device; returns tau, the
 // number of tests and whether one held.
-// *tau: the samples already taken on entry (a multiple of K), the final tau on return.
+// *tau: the samples already taken on entry (a multiple of K), the final tau on
+// return; *co: the last round's test.
 kadabra_status run_loop_graph(kadabra_graph* g, Workspace* w, cudaStream_t st, uint64_t seed, uint64_t cap, uint64_t K,
-                              double omega, double lambda, int variant, uint64_t* tau, uint64_t* checks, int* stopped) {
+                              double omega, double lambda, int variant, uint64_t* tau, uint64_t* checks, int* stopped,
+                              CheckOut* co) {
   if (!g->loop_dev) {
     void* p;
     KTRY(dev_alloc(g->allocs, &p, sizeof(LoopState) + sizeof(Job) + sizeof(CheckTabJob)));
@@ -3843,6 +3845,7 @@ kadabra_status run_loop_graph(kadabra_graph* g, Workspace* w, cudaStream_t st, u
   *tau = hs.tau;
   *checks = hs.checks;
   *stopped = (int)hs.stopped;
+  *co = hs.co;
   return KADABRA_OK;
 }
 
@@ -3863,6 +3866,7 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
     uint64_t cap, alpha, K, tau;
     uint64_t pre;  // main-loop samples already taken with the warm-up, not yet in tau
     bool done;
+    bool have_max;  // max f, max g known: the test that held evaluated every node
   };
   std::vector<State> S(G);
   uint64_t sum_alpha = 0, sum_k = 0;
@@ -3880,6 +3884,7 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
     s.tau = 0;
     s.pre = 0;
     s.done = false;
+    s.have_max = false;
     sum_alpha += s.alpha;
     sum_k += std::min(s.K, s.cap);
   }
@@ -4058,10 +4063,16 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
     if (loop_on_device && S[0].tau > 0 && !S[0].done) {  // rounds 2, 3, ... on the device
       uint64_t checks = 0;
       int stopped = 0;
+      CheckOut lco;
       KTRY(run_loop_graph(S[0].g, w, st, seed[0], S[0].cap, S[0].K, out[0].omega, lambda[0], variant, &S[0].tau,
-                          &checks, &stopped));
+                          &checks, &stopped, &lco));
       out[0].checks += checks;
       out[0].stopped_early = stopped;
+      if (stopped) {  // the test that held found no failure, so its maxima are complete
+        std::memcpy(&out[0].max_f, &lco.max_f_bits, sizeof(double));
+        std::memcpy(&out[0].max_g, &lco.max_g_bits, sizeof(double));
+        S[0].have_max = true;
+      }
       S[0].done = true;
       break;
     }
@@ -4108,23 +4119,31 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
     for (size_t q = 0; q < to_check.size(); ++q) {
       const int i = to_check[q];
       out[i].checks++;
-      if (!co[q].fail) {
+      if (!co[q].fail) {  // held: no failure cut it short, so its maxima are complete
         out[i].stopped_early = 1;
         S[i].done = true;
+        std::memcpy(&out[i].max_f, &co[q].max_f_bits, sizeof(double));
+        std::memcpy(&out[i].max_g, &co[q].max_g_bits, sizeof(double));
+        S[i].have_max = true;
       }
     }
   }
-  // f and g maxima at each final tau; b~ = counts / tau (Alg. 1 last line)
-  std::vector<int> all(G);
-  for (int i = 0; i < G; ++i) all[i] = i;
-  KTRY(check(all, false));
+  // f and g maxima at each final tau (a full test for the runs that reached
+  // ceil(omega); the others keep those of the test that held); b~ = counts /
+  // tau (Alg. 1 last line)
+  std::vector<int> need;
+  for (int i = 0; i < G; ++i)
+    if (!S[i].have_max) need.push_back(i);
+  if (!need.empty()) KTRY(check(need, false));
+  for (size_t q = 0; q < need.size(); ++q) {
+    std::memcpy(&out[need[q]].max_f, &co[q].max_f_bits, sizeof(double));
+    std::memcpy(&out[need[q]].max_g, &co[q].max_g_bits, sizeof(double));
+  }
   std::vector<long long> tot((size_t)G * KADABRA_NSTAT);
   for (int i = 0; i < G; ++i) {
     kadabra_result& r = out[i];
     kadabra_graph* g = S[i].g;
     r.tau = S[i].tau;
-    std::memcpy(&r.max_f, &co[i].max_f_bits, sizeof(double));
-    std::memcpy(&r.max_g, &co[i].max_g_bits, sizeof(double));
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(4 * (int64_t)w->num_sms, (g->n + 255) / 256));
     if (r.btilde || r.d_btilde) {
       k_btilde<<<blocks, 256, 0, st>>>(g->counts, g->n, r.tau, r.d_btilde ? r.d_btilde : g->btilde);
