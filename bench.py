@@ -214,17 +214,19 @@ def run_launches(r, w):
     Alg. 3 test (checks + the final one) and b~."""
     rounds = -(-int(r.tau) // w["check_interval"])
     spb = sampler_launches_per_batch(r)
-    # the first main-loop batch shares the warm-up's launch
+    # the first main-loop batch shares the warm-up's launch; a final full test
+    # runs only when no test held (a test that held gave the maxima)
+    final = 0 if r.stopped_early else 1
     if w.get("k"):
-        return spb * rounds + 2 + 3 + 2 + 3 * (int(r.checks) + 1) + 1
+        return spb * rounds + 2 + 3 + 2 + 3 * int(r.checks) + 3 * final + 1
     # one-graph all-nodes runs with more than 4 possible rounds test the first
     # round from the host and loop on the device from the second: per round a
     # begin kernel, the sampler batch, the stop test and an end kernel;
     # shorter runs take host rounds (batch, then a test if tau < cap)
     cap_rounds = -(-int(r.omega_cap) // w["check_interval"])
     if cap_rounds > 4:
-        return spb + 3 + 1 + (spb + 3) * (rounds - 1) + 1 + 1
-    return spb * rounds + 3 + int(r.checks) + 1 + 1
+        return spb + 3 + 1 + (spb + 3) * (rounds - 1) + final + 1
+    return spb * rounds + 3 + int(r.checks) + final + 1
 
 
 def sampler_launches_per_batch(r=None):

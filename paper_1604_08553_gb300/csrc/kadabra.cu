@@ -4513,7 +4513,9 @@ kadabra_status run_topk(kadabra_graph* g, double lambda, double delta, int32_t k
     }
   }
   r.tau = tau;
-  KTRY(topk_pass(g->counts, tau, 0));
+  // a test that held found no failure, so its ranking and maxima are those of
+  // a full pass at this tau; a run that reached ceil(omega) gets one
+  if (!r.stopped_early) KTRY(topk_pass(g->counts, tau, 0));
   std::memcpy(&r.max_f, &ho.max_f_bits, sizeof(double));
   std::memcpy(&r.max_g, &ho.max_g_bits, sizeof(double));
   if (r.topk)
