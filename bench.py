@@ -220,12 +220,14 @@ def run_launches(r, w):
     if w.get("k"):
         return spb * rounds + 2 + 3 + 2 + 3 * int(r.checks) + 3 * final + 1
     # one-graph all-nodes runs with more than 4 possible rounds test the first
-    # round from the host and loop on the device from the second: per round a
-    # begin kernel, the sampler batch, the stop test and an end kernel;
-    # shorter runs take host rounds (batch, then a test if tau < cap)
+    # round from the host and loop on the device from the second: a setup
+    # kernel, then per round the sampler batch and the stop test (whose last
+    # block closes the round); shorter runs take host rounds (batch, then a
+    # test if tau < cap)
     cap_rounds = -(-int(r.omega_cap) // w["check_interval"])
     if cap_rounds > 4:
-        return spb + 3 + 1 + (spb + 3) * (rounds - 1) + final + 1
+        loop = 1 + (spb + 1) * (rounds - 1) if rounds > 1 else 0
+        return spb + 3 + 1 + loop + final + 1
     return spb * rounds + 3 + int(r.checks) + final + 1
 
 

@@ -2182,9 +2182,9 @@ struct CheckTabJob {
   int fail_fast;
 };
 
-__global__ void __launch_bounds__(256) k_check_tab(const CheckTabJob* __restrict__ jobs) {
+// one block's share of the test of graph J (blocks over blockIdx.x)
+__device__ __forceinline__ void check_tab_block(const CheckTabJob J) {
   __shared__ unsigned long long s_u[8];
-  const CheckTabJob J = jobs[blockIdx.y];
   const double t = (double)J.tau;
   unsigned long long mf = 0, mg = 0, mu = 0;  // bit patterns of non-negative doubles
   unsigned fail = 0;
@@ -2243,18 +2243,22 @@ __global__ void __launch_bounds__(256) k_check_tab(const CheckTabJob* __restrict
   }
 }
 
+__global__ void __launch_bounds__(256) k_check_tab(const CheckTabJob* __restrict__ jobs) {
+  check_tab_block(jobs[blockIdx.y]);
+}
+
 // Device-driven main loop of one all-nodes run (Alg. 1): a CUDA graph whose
 // while node repeats {next batch of K samples, stop test} with the loop
 // state in device memory, so no host round trip separates the rounds.
 struct LoopState {
   unsigned long long tau, cap, K, B, checks, total_work;
   int64_t n;
-  unsigned stopped, pad;
+  unsigned stopped, arrive;  // arrive: blocks of the round's test that have finished
   CheckOut co;
 };
 
-// one thread: the next batch's job range, the queue counters, the test's tau
-__global__ void k_loop_begin(LoopState* s, Job* job, unsigned long long* ctr, CheckTabJob* cj) {
+// the next batch's job range, the queue counters, the test's tau (one thread)
+__device__ void loop_begin(LoopState* s, Job* job, unsigned long long* ctr, CheckTabJob* cj) {
   const unsigned long long rest = s->cap - s->tau;
   const unsigned long long B = s->K < rest ? s->K : rest;
   s->B = B;
@@ -2270,19 +2274,39 @@ __global__ void k_loop_begin(LoopState* s, Job* job, unsigned long long* ctr, Ch
   cj->n = (s->tau + B >= s->cap) ? 0 : s->n;  // no test once ceil(omega) is reached
 }
 
-// one thread: advance tau, count the test, decide whether to go on
-__global__ void k_loop_end(LoopState* s, const int32_t* status, cudaGraphConditionalHandle h) {
+// the first round's setup, launched before the loop's graph
+__global__ void k_loop_begin(LoopState* s, Job* job, unsigned long long* ctr, CheckTabJob* cj) {
+  loop_begin(s, job, ctr, cj);
+}
+
+// The round's stop test; its last block to finish then closes the round
+// (advance tau, count the test, decide whether to go on) and sets up the
+// next one, so no single-thread kernels separate the rounds.  Each block
+// publishes its test results (atomics) before it signs in on `arrive`.
+__global__ void __launch_bounds__(256) k_loop_check(CheckTabJob* cj, LoopState* s, Job* job,
+                                                    unsigned long long* ctr, const int32_t* status,
+                                                    cudaGraphConditionalHandle h) {
+  check_tab_block(*cj);
+  __shared__ unsigned last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&s->arrive, 1u) == gridDim.x - 1 ? 1u : 0u;
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  s->arrive = 0u;
   s->tau += s->B;
   unsigned keep = 1u;
-  if (s->tau >= s->cap || *status != 0) {
+  if (s->tau >= s->cap || *(volatile const int32_t*)status != 0) {
     keep = 0u;
   } else {
     s->checks += 1ull;
-    if (!s->co.fail) {
+    if (!*(volatile const unsigned*)&s->co.fail) {
       s->stopped = 1u;
       keep = 0u;
     }
   }
+  if (keep) loop_begin(s, job, ctr, cj);
   cudaGraphSetConditional(h, keep);
 }
 
@@ -3747,8 +3771,9 @@ int variant_ctas_per_sm(const Workspace* w, int variant) {
 constexpr uint64_t LOOP_GRAPH_MIN_ROUNDS = 4;  // fewer possible rounds: host rounds cost as little
 
 // The main loop of one all-nodes run as a CUDA graph: a while node whose body
-// is {k_loop_begin, the three sampler launches, k_check_tab, k_loop_end}; the
-// end kernel sets the while condition.  Built once per graph object and
+// is {the sampler launches, k_loop_check}; the test's last block sets the
+// while condition and the next round's range (k_loop_begin, before the
+// graph, sets the first).  Built once per graph object and
 // rebuilt only when the launch parameters it captured change (workspace
 // buffers that grew, another table tier flag).
 kadabra_status loop_graph_ready(kadabra_graph* g, Workspace* w, const SampleParams& P, int check_blocks,
@@ -3777,10 +3802,8 @@ kadabra_status loop_graph_ready(kadabra_graph* g, Workspace* w, const SamplePara
   KCK(cudaGraphAddNode(&node, g->loop_graph, nullptr, nullptr, 0, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   KCK(cudaStreamBeginCaptureToGraph(g->loop_cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  k_loop_begin<<<1, 1, 0, g->loop_cap>>>(d_state, d_job, w->ctr, d_cj);
   kadabra_status st = launch_sampler_kernels(w, P, g->loop_cap, variant);
-  k_check_tab<<<dim3(check_blocks, 1), 256, 0, g->loop_cap>>>(d_cj);
-  k_loop_end<<<1, 1, 0, g->loop_cap>>>(d_state, w->status, h);
+  k_loop_check<<<check_blocks, 256, 0, g->loop_cap>>>(d_cj, d_state, d_job, w->ctr, w->status, h);
   cudaGraph_t captured = nullptr;
   const cudaError_t ec = cudaStreamEndCapture(g->loop_cap, &captured);
   if (st != KADABRA_OK) return st;
@@ -3839,6 +3862,8 @@ kadabra_status run_loop_graph(kadabra_graph* g, Workspace* w, cudaStream_t st, u
   KCK(cudaMemcpyAsync(d_state, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
   KCK(cudaMemcpyAsync(d_job, &hj, sizeof(hj), cudaMemcpyHostToDevice, st));
   KCK(cudaMemcpyAsync(d_cj, &hc, sizeof(hc), cudaMemcpyHostToDevice, st));
+  k_loop_begin<<<1, 1, 0, st>>>(d_state, d_job, w->ctr, d_cj);
+  KCK(cudaGetLastError());
   KCK(cudaGraphLaunch(g->loop_exec, st));
   KCK(cudaMemcpyAsync(&hs, d_state, sizeof(hs), cudaMemcpyDeviceToHost, st));
   KTRY(read_status(w, st));
