@@ -45,9 +45,10 @@ typedef enum {
   KADABRA_ERR_OOM = 3,            /* device allocation failed                       */
   KADABRA_ERR_SIGMA_OVERFLOW = 4, /* a shortest-path count exceeded 2^64-1          */
   KADABRA_ERR_CAPACITY = 5,       /* an internal bound was exceeded (see message)   */
-  KADABRA_ERR_TIMEOUT = 6,        /* a bounded device wait gave up                  */
+  KADABRA_ERR_TIMEOUT = 6,        /* reserved: no kernel of this library waits on a
+                                     flag or another CTA, so no call returns it     */
   KADABRA_ERR_CUDA = 7,           /* a CUDA runtime call failed                     */
-  KADABRA_ERR_UNSUPPORTED = 8,    /* requested mode not implemented                 */
+  KADABRA_ERR_UNSUPPORTED = 8,    /* reserved (every mode of the ABI is implemented) */
   KADABRA_ERR_INTERNAL = 9        /* an invariant of the method failed (a bug)      */
 } kadabra_status;
 
