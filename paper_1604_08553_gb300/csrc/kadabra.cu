@@ -1,36 +1,49 @@
-// KADABRA adaptive sampling loop for GB300 (sm_103a): kernels and C ABI.
+// KADABRA adaptive sampling loop for GB300 (sm_103a): kernels, host runtime
+// and C ABI.
 //
 // Paper: Borassi & Natale, "KADABRA is an ADaptive Algorithm for Betweenness
 // via Random Approximation".  The method (Alg. 1) samples shortest paths
 // between uniform node pairs and stops once every node's estimate b~(v) is
 // within lambda with probability 1-delta:
-//   * k_sample   -- one sample per CTA (Sec. 4): (s,t) draw, balanced
-//                   bidirectional BFS with exact uint64 sigma, candidate-edge
-//                   choice proportional to sigma_sv*sigma_wt, backtracking to
-//                   a uniform shortest path, hit counters (Alg. 1 l.5).
-//   * k_check    -- the all-nodes stop test: f and g of Thm. 2 in FP64 for
-//                   every node, rule f <= lambda and g <= lambda.
-//   * host code  -- omega (Alg. 1), computeDelta (Alg. 2, App. D), the
-//                   batch / check schedule, VD bound, CSR validation.
+//   * k_sample      -- one sample per CTA of 256 threads (Sec. 4): (s,t)
+//                      draw, balanced bidirectional BFS with exact uint64
+//                      sigma, candidate-edge choice proportional to
+//                      sigma_sv*sigma_wt, backtracking to a uniform shortest
+//                      path, hit counters (Alg. 1).
+//   * k_sample_warp -- the same sample by one warp, for small searches.
+//   * k_check_tab   -- the all-nodes stop test: f and g of Thm. 2 in FP64,
+//                      rule f <= lambda and g <= lambda; k_topk_* the
+//                      top-k test (Sec. 5, Alg. 3).
+//   * host code     -- omega (Alg. 1), computeDelta (Alg. 2, App. D), the
+//                      batch / test schedule (host rounds or a CUDA graph
+//                      loop), VD bound, CSR validation, the autotuner,
+//                      batched runs and the serving engine.
 //
 // Sampler design (GB300-first, not the paper's CPU design):
-//   * A CTA of 128 threads owns one sample at a time; CTAs pull sample
-//     indices from a device counter (persistent grid, sized to the SMs).
-//   * The visited set of both searches is an open-addressing hash table in
-//     shared memory (node -> side | dist | list slot), and sigma lives in
-//     per-level node lists, also in shared memory.  Most of a sample's arcs
-//     (over 90% on power-law graphs) lie in the level that touches the other
-//     search; that level only reads the hash table.  Every level runs as
-//     pass 1 = touch test, and only a level that does not touch runs pass 2
-//     (insert new nodes) and pass 3 (accumulate sigma).
-//   * Frontiers are kept sorted by node id, and each warp scans a contiguous
-//     slice of the level's flattened arc range, so candidate edges come out
-//     in the canonical (x, y) order without a sort.
-//   * A sample whose visited set outgrows its shared-memory table is re-run
-//     on bigger tables (a one-CTA-per-SM launch with a large shared-memory
-//     table, then global-memory tables), with identical results.
-//   * The RNG is counter-based Philox4x32-10 keyed by (seed, sample index),
-//     so results do not depend on scheduling; hit counts are integer atomics.
+//   * A persistent grid, sized to the SMs, pulls sample indices from a device
+//     counter; the counter-based Philox4x32-10 RNG keyed by (seed, sample
+//     index) makes results independent of the schedule, and hit counts are
+//     integer atomics.
+//   * Both searches' visited sets share one open-addressing hash table in
+//     shared memory, one packed 64-bit word per node (node | side | depth |
+//     sigma); level lists hold node ids and 16-bit hash positions.
+//   * Every level runs pass 1 (touch test against the other search; most
+//     arcs lie in the touching level, which only reads the table), and only
+//     a level that does not touch runs pass 2 (first discoverers insert with
+//     a CAS, every discoverer adds its sigma atomically).
+//   * Each warp scans a contiguous slice of the level's flattened arc range,
+//     in registers or, for graphs beyond the L2, through an async-copy ring.
+//     Candidate edges are chosen in (x, y) order without a sort (quadratic
+//     ranking or a weighted radix selection).
+//   * A sample that outgrows its table moves on to bigger tables (tier B in
+//     shared memory, then global-memory tiers M and L) with identical
+//     results.
+//
+// Sections: constants, Philox, tables, parameters, block helpers, one sample
+// (tiers S and B), tier W, stop test, top-k stop test, graph checks and VD,
+// host side (omega, computeDelta, autotuner, device-driven loop, Alg. 1
+// runner, top-k runner), serving, the sampler without device allocation, C
+// ABI.
 
 #include <cuda_runtime.h>
 
