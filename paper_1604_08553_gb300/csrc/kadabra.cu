@@ -87,11 +87,12 @@ constexpr int NW = NT / 32;        // warps per sampler CTA
 constexpr int U = KD_U;            // independent items per thread per step (memory-level parallelism)
 constexpr int RING = 4;            // arc windows in flight per warp in the level scans (async copies)
 // Tiers of per-sample tables.  A sample starts in a small shared-memory
-// table (tier S, main launch, several CTAs per SM).  If it outgrows it, it is
-// queued for a second launch with one CTA per SM and a large shared-memory
-// table (tier B); beyond that the same CTA retries it on medium global tables
-// (tier M), and beyond those it is queued for a last launch with n-sized
-// global tables (tier L).  Every tier gives the same result.
+// table (tier S, main launch, three or four CTAs per SM; optionally tier W,
+// one warp per sample, before it).  If it outgrows it, it is queued for a
+// second launch with two CTAs per SM and a large shared-memory table (tier
+// B); beyond that the same CTA retries it on medium global tables (tier M),
+// and beyond those it is queued for a last launch with n-sized global tables
+// (tier L).  Every tier gives the same result.
 constexpr int FAST_HLOG = KD_FAST_HLOG;        // tier S: 2^FAST_HLOG hash slots
 constexpr int BIG_HLOG = FAST_HLOG + 1;        // tier B: twice as many
 constexpr int SMALL_HLOG = FAST_HLOG - 1;      // tier S, small variant: half the slots, one more CTA per SM
