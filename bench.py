@@ -14,13 +14,22 @@ holds or ceil(omega) samples) on one graph.  Workloads (--workload):
         forward and reverse CSR; all-nodes mode at lambda = 0.0025,
         delta = 0.1, stop test every 2^16 samples.
     rmat_24_topk: the same graph in top-k mode (Sec. 5, Alg. 3), k = 10.
+    rmat_22: the scale-22 graph of the same recipe (for profiler captures).
     batched: 64 Barabasi-Albert graphs of uneven sizes, one batched run
-        against the same graphs run one at a time.
+        against the same graphs run one at a time (results on the device).
+    serving: 2000 Poisson-arriving jobs on 16 graphs through the serving
+        engine; latency percentiles and jobs/s.
+    edge_exponent: edges scanned per sample as a power of m on graphs of
+        growing size (a diagnostic of the Sec. 4 theorem, no timing).
 
 Prints ONE JSON line (rank 0).  `value` is sampled paths per second over the
 whole run (warm-up + main loop) with the graph resident on the device;
-`e2e` repeats the measurement through the C ABI with host buffers (CSR
-upload, run, host copy of the counts) inside the timed region.
+`e2e` repeats the measurement through the C ABI with host buffers (upload of
+the CSR from pinned host memory, run, copy of counts and b~ into pinned host
+memory) inside the timed region.  `roofline` relates the sampler batch's
+algorithmic bytes to the measured HBM peak, `roofline_l2` (graphs whose CSR
+fits in L2) to the measured L2 read rate, with the same work counted in 32 B
+sectors beside it; `cpu_baseline` times the oracle on the host's cores.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
