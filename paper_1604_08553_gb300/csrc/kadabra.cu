@@ -1608,8 +1608,6 @@ __global__ void __launch_bounds__(NT, SHL == FAST_HLOG ? KD_MIN_BLOCKS : KD_MIN_
   if (MODE != 1 && (P.tier_flags & TF_SEG64)) TS.frcap = min(TS.frcap, 64);
 
   const int tid = threadIdx.x;
-  if (MODE != 1)
-    for (uint32_t i = tid; i <= TS.hmask; i += NT) TS.hkv[i] = EMPTY;
   if (tid == 0) {
     for (int k = 0; k < KADABRA_NSTAT; ++k) c.tot[k] = 0;
     c.tot_job = -1;
@@ -1620,6 +1618,11 @@ __global__ void __launch_bounds__(NT, SHL == FAST_HLOG ? KD_MIN_BLOCKS : KD_MIN_
   }
   __syncthreads();
   const unsigned long long ntotal = c.ntotal;
+  if (ntotal == 0) return;  // nothing queued for this tier: skip the table set-up (the whole block)
+  if (MODE != 1) {
+    for (uint32_t i = tid; i <= TS.hmask; i += NT) TS.hkv[i] = EMPTY;
+    __syncthreads();
+  }
 
   for (;;) {
     if (tid == 0) c.cur = atomicAdd(&P.ctr[MODE == 0 ? Q_NEXT_A : MODE == 2 ? Q_NEXT_B : Q_NEXT_L], 1ull);
