@@ -131,14 +131,33 @@ class ClockSampler:
         self.lines = []
 
     def start(self):
-        try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        """Starts sampling every 20 ms (every 200 ms if that yields nothing)
+        and returns once the first sample has arrived, so that the sampler is
+        running before the timed region opens."""
+        for interval in ("20", "200"):
+            try:
+                self.proc = subprocess.Popen(
+                    ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                     "--format=csv,noheader,nounits", "-lms", interval],
+                    stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            except (FileNotFoundError, OSError):
+                self.proc = None
+                return
+            self.lines = []
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
-        except (FileNotFoundError, OSError):
-            self.proc = None
+            t0 = time.perf_counter()
+            while not self.lines and self.proc.poll() is None and time.perf_counter() - t0 < 3.0:
+                time.sleep(0.01)
+            if self.lines:
+                return
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=5)
+        self.proc = None
 
     def _read(self):
         for line in self.proc.stdout:
