@@ -556,7 +556,8 @@ def run_edge_exponent(args, kd, rank, world):
     per-graph alpha and the least-squares slope of log m_avg against log m:
     the theorem gives 1/2 + o(1) for degrees with a finite second moment (ER)
     and (4 - beta)/2 + o(1) for power-law degrees with 2 < beta < 3 (Chung-Lu,
-    beta = 2.5: 0.75).  Not a timing; rank 0 only."""
+    beta = 2.5: 0.75); the directed R-MAT family, outside the theorem's
+    models, is measured beside them.  Not a timing; rank 0 only."""
     import torch
     from paper_1604_08553_gb300 import graphgen
     if rank != 0:
@@ -566,6 +567,8 @@ def run_edge_exponent(args, kd, rank, world):
         "erdos_renyi_d8": lambda n: graphgen.erdos_renyi(n, 8.0, 1),
         # natural cutoff of the weights, n^(1/(beta-1)): 10^4 at n = 10^6 as in the Chung-Lu workload
         "chung_lu_b2.5_d16": lambda n: graphgen.chung_lu(n, 2.5, 16.0, float(n) ** (1 / 1.5), 1),
+        # directed, every id kept: many (s, t) pairs are disconnected and end early
+        "rmat_ef16_directed": lambda n: graphgen.rmat(int(n).bit_length() - 1, 16, 0.57, 0.19, 0.19, 1),
     }
     out = {}
     for fam, make in families.items():
