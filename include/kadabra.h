@@ -77,8 +77,12 @@ typedef struct kadabra_graph kadabra_graph;
 /* Optional knobs (kadabra_config_default fills the defaults). */
 typedef struct {
   int64_t vd;              /* vertex-diameter bound VD for omega; 0 = the library's
-                              heuristic 2*ecc(r)+1 (r = lowest-id max-degree node,
-                              underlying undirected graph)                        */
+                              bound, computed at load: the heaviest path of the
+                              condensation into strongly connected components,
+                              each weighing its node count, except the component
+                              of r (lowest-id node of maximum undirected degree):
+                              e_in + e_out + 1, its largest distances to and from
+                              r (2*ecc(r)+1 for a connected undirected graph)     */
   double eps;              /* computeDelta epsilon (App. D; default 0.001)        */
   uint64_t check_interval; /* K: samples between stop tests (default 1000; 0 = chosen
                               by the library from omega: max(1024, ceil(omega/32)))  */

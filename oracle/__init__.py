@@ -9,6 +9,8 @@ Function-by-function citations (Borassi & Natale, KADABRA):
   * ``sample_paths`` / ``sample_fixed_pair`` -- Sec. 4 balanced bidirectional
     BFS, candidate-edge choice and backtracking; Sec. 2 hit variables.
   * ``omega``            -- Alg. 1 first line (omega with c = 0.5).
+  * ``vd_bound``         -- the vertex-diameter bound omega needs (Alg. 1,
+    Sec. 2), from the condensation into strongly connected components.
   * ``compute_delta``    -- Alg. 2 and App. D.
   * ``f_and_g`` / ``check_stop`` -- Thm. 2 (f, g) and the all-nodes rule.
   * ``run``              -- Alg. 1 with the stop test every K samples.
@@ -88,8 +90,8 @@ def _load():
         lib.orc_accumulate.argtypes = graph + [u64, u32, u64, i64, p, p]
         lib.orc_omega.argtypes = [dbl, dbl, i64]
         lib.orc_omega.restype = dbl
-        lib.orc_vd_heuristic.argtypes = graph
-        lib.orc_vd_heuristic.restype = i64
+        lib.orc_vd_bound.argtypes = graph
+        lib.orc_vd_bound.restype = i64
         lib.orc_compute_delta.argtypes = [i64, p, u64, dbl, dbl, dbl, dbl, p, p]
         lib.orc_compute_delta.restype = dbl
         lib.orc_f_and_g.argtypes = [u32, u64, dbl, dbl, dbl, p, p]
@@ -203,9 +205,12 @@ def omega(lam: float, delta: float, vd: int) -> float:
     return float(_load().orc_omega(lam, delta, vd))
 
 
-def vd_heuristic(g) -> int:
+def vd_bound(g) -> int:
+    """Upper bound on the vertex diameter (the most nodes on a shortest path)
+    from the condensation into strongly connected components; omega's VD
+    (Alg. 1, Sec. 2)."""
     keep, ga = _gargs(g)
-    r = int(_load().orc_vd_heuristic(*ga))
+    r = int(_load().orc_vd_bound(*ga))
     del keep
     return r
 

@@ -15,6 +15,8 @@
 //                      hit variables X_i(v) (1 iff v on the path, v != s,t).
 //   omega_of           Alg. 1 first line and Sec. 2: omega = c/lambda^2 *
 //                      (floor(log2(VD-2)) + 1 + ln(2/delta)), c = 0.5.
+//   vd_bound           the upper bound on VD that omega needs (Alg. 1,
+//                      Sec. 2); the paper does not say how it is obtained.
 //   compute_delta      Alg. 2 and App. D (warm-up of omega/100 samples,
 //                      c_L, c_U, bisection for C, delta_L, delta_U).
 //   check_stop         Thm. 2 (functions f and g) and the all-nodes stopping
@@ -49,8 +51,10 @@
 //     nodes it discovered on its own side play no further part.
 //   * sigma is an exact uint64; any overflow, or sigma_st > 2^64-1, fails the
 //     sample with status SIGMA_OVERFLOW.
-//   * VD when not given: 2*ecc(r)+1 on the underlying undirected graph, r the
-//     lowest-id node of maximum degree.
+//   * VD when not given: a bound from the condensation into strongly
+//     connected components (vd_bound), r the lowest-id node of maximum
+//     degree in the underlying undirected graph; 2*ecc(r)+1 for a connected
+//     undirected graph.
 //   * alpha = max(1, floor(omega/100)); eps = configurable (paper: 0.001 in
 //     App. D text, 0.0001 in Alg. 2).
 //   * The bisection for C keeps the upper end so sum(delta) <= delta/2 and
@@ -446,8 +450,9 @@ double omega_of(double lambda, double delta, int64_t vd) {
   return (0.5 / (lambda * lambda)) * ((double)(fl + 1) + std::log(2.0 / delta));
 }
 
-int64_t vd_heuristic(const Graph& g) {
-  // underlying undirected degree: |out(v) U in(v)|, rows are sorted
+// The root of the VD bound: the lowest-id node of maximum degree in the
+// underlying undirected graph, |out(v) U in(v)| (rows are sorted).
+int32_t vd_root(const Graph& g) {
   auto und_deg = [&](int32_t v) {
     int64_t a = g.rp[v], ae = g.rp[v + 1], b = g.rrp[v], be = g.rrp[v + 1];
     if (g.rp == g.rrp) return ae - a;
@@ -474,25 +479,119 @@ int64_t vd_heuristic(const Graph& g) {
       r = v;
     }
   }
-  std::vector<int32_t> dist(g.n, -1), q;
+  return r;
+}
+
+// Distances from r along the arcs of one CSR (out-arcs: from r; in-arcs: to r).
+std::vector<int32_t> bfs_dist(int64_t n, const int32_t* rp, const int32_t* ci, int32_t r) {
+  std::vector<int32_t> dist(n, -1), q;
   dist[r] = 0;
   q.push_back(r);
-  int32_t ecc = 0;
   for (size_t h = 0; h < q.size(); ++h) {
     int32_t v = q[h];
-    ecc = std::max(ecc, dist[v]);
-    for (int32_t e = g.rp[v]; e < g.rp[v + 1]; ++e)
-      if (dist[g.ci[e]] < 0) {
-        dist[g.ci[e]] = dist[v] + 1;
-        q.push_back(g.ci[e]);
-      }
-    for (int32_t e = g.rrp[v]; e < g.rrp[v + 1]; ++e)
-      if (dist[g.rci[e]] < 0) {
-        dist[g.rci[e]] = dist[v] + 1;
-        q.push_back(g.rci[e]);
+    for (int32_t e = rp[v]; e < rp[v + 1]; ++e)
+      if (dist[ci[e]] < 0) {
+        dist[ci[e]] = dist[v] + 1;
+        q.push_back(ci[e]);
       }
   }
-  return 2 * (int64_t)ecc + 1;
+  return dist;
+}
+
+// Strongly connected components over the out-arcs (Tarjan, with an explicit
+// stack).  comp[v] is the component's index; components come out in reverse
+// topological order: an arc from component a to component b != a has b < a.
+// For an undirected graph they are its connected components.
+int64_t tarjan_scc(const Graph& g, std::vector<int64_t>& comp) {
+  const int64_t n = g.n;
+  std::vector<int64_t> index(n, -1), low(n, 0);
+  std::vector<char> on_stack(n, 0);
+  std::vector<int32_t> stack;
+  std::vector<std::pair<int32_t, int32_t>> call;  // (node, next arc)
+  comp.assign(n, -1);
+  int64_t next_index = 0, ncomp = 0;
+  for (int32_t root = 0; root < n; ++root) {
+    if (index[root] >= 0) continue;
+    call.push_back({root, g.rp[root]});
+    index[root] = low[root] = next_index++;
+    stack.push_back(root);
+    on_stack[root] = 1;
+    while (!call.empty()) {
+      int32_t v = call.back().first;
+      int32_t& e = call.back().second;
+      if (e < g.rp[v + 1]) {
+        int32_t w = g.ci[e++];
+        if (index[w] < 0) {
+          index[w] = low[w] = next_index++;
+          stack.push_back(w);
+          on_stack[w] = 1;
+          call.push_back({w, g.rp[w]});
+        } else if (on_stack[w]) {
+          low[v] = std::min(low[v], index[w]);
+        }
+        continue;
+      }
+      call.pop_back();
+      if (!call.empty()) {
+        int32_t u = call.back().first;
+        low[u] = std::min(low[u], low[v]);
+      }
+      if (low[v] == index[v]) {
+        int32_t w;
+        do {
+          w = stack.back();
+          stack.pop_back();
+          on_stack[w] = 0;
+          comp[w] = ncomp;
+        } while (w != v);
+        ++ncomp;
+      }
+    }
+  }
+  return ncomp;
+}
+
+// Upper bound on the vertex diameter VD (the most nodes on any shortest
+// path), which omega needs (Alg. 1; Sec. 2).  The paper does not say how
+// KADABRA bounds VD.  A shortest path visits the strongly connected
+// components in the order of a path of the condensation, each one in a
+// contiguous stretch that is a shortest path inside it.  A stretch inside a
+// component C has at most |C| nodes; inside the component C_r of the root r
+// it has at most d(u,r) + d(r,v) + 1 <= e_in + e_out + 1 nodes, with e_out
+// and e_in the largest distances from and to r within C_r.  The bound is the
+// largest sum of these weights along a path of the condensation.  For a
+// connected undirected graph it is 2 ecc(r) + 1.
+int64_t vd_bound(const Graph& g) {
+  const int32_t r = vd_root(g);
+  std::vector<int64_t> comp;
+  const int64_t ncomp = tarjan_scc(g, comp);
+  std::vector<int32_t> dout = bfs_dist(g.n, g.rp, g.ci, r);
+  std::vector<int32_t> din = bfs_dist(g.n, g.rrp, g.rci, r);
+  int64_t e_out = 0, e_in = 0;
+  std::vector<int64_t> w(ncomp, 0);
+  for (int32_t v = 0; v < g.n; ++v) {
+    w[comp[v]] += 1;
+    if (comp[v] == comp[r]) {
+      e_out = std::max<int64_t>(e_out, dout[v]);
+      e_in = std::max<int64_t>(e_in, din[v]);
+    }
+  }
+  w[comp[r]] = e_out + e_in + 1;
+  // longest weighted path of the condensation, starting at each component:
+  // every component an arc leads to has a smaller index, so is done already
+  std::vector<int64_t> from(ncomp, 0);
+  std::vector<std::vector<int32_t>> members(ncomp);
+  for (int32_t v = 0; v < g.n; ++v) members[comp[v]].push_back(v);
+  int64_t best = 0;
+  for (int64_t c = 0; c < ncomp; ++c) {
+    int64_t tail = 0;
+    for (int32_t v : members[c])
+      for (int32_t e = g.rp[v]; e < g.rp[v + 1]; ++e)
+        if (comp[g.ci[e]] != c) tail = std::max(tail, from[comp[g.ci[e]]]);
+    from[c] = w[c] + tail;
+    best = std::max(best, from[c]);
+  }
+  return best;
 }
 
 // ---------------------------------------------------------------- computeDelta
@@ -792,10 +891,10 @@ int orc_accumulate(int64_t n, const int32_t* rp, const int32_t* ci, int directed
 
 double orc_omega(double lambda, double delta, int64_t vd) { return omega_of(lambda, delta, vd); }
 
-int64_t orc_vd_heuristic(int64_t n, const int32_t* rp, const int32_t* ci, int directed, const int32_t* rrp,
-                         const int32_t* rci) {
+int64_t orc_vd_bound(int64_t n, const int32_t* rp, const int32_t* ci, int directed, const int32_t* rrp,
+                     const int32_t* rci) {
   Graph g = make_graph(n, rp, ci, directed, rrp, rci);
-  return vd_heuristic(g);
+  return vd_bound(g);
 }
 
 double orc_compute_delta(int64_t n, const uint32_t* count0, uint64_t alpha, double omega, double lambda,
@@ -830,7 +929,7 @@ static int run_impl(int64_t n, const int32_t* rp, const int32_t* ci, int directe
     return ORC_ERR_ARG;
   }
   Graph g = make_graph(n, rp, ci, directed, rrp, rci);
-  res->vd = vd > 0 ? vd : vd_heuristic(g);
+  res->vd = vd > 0 ? vd : vd_bound(g);
   res->omega = omega_of(lambda, delta, res->vd);
   res->omega_cap = (uint64_t)std::ceil(res->omega);
   uint64_t alpha = (uint64_t)std::floor(res->omega / 100.0);

@@ -16,7 +16,8 @@
 //                      top-k test (Sec. 5, Alg. 3).
 //   * host code     -- omega (Alg. 1), computeDelta (Alg. 2, App. D), the
 //                      batch / test schedule (host rounds or a CUDA graph
-//                      loop), VD bound, CSR validation, the autotuner,
+//                      loop), VD bound (condensation into strongly
+//                      connected components), CSR validation, the autotuner,
 //                      batched runs and the serving engine.
 //
 // Sampler design (GB300-first, not the paper's CPU design):
@@ -2800,7 +2801,7 @@ __global__ void k_validate_mirror(const int32_t* rp, const int32_t* ci, const in
   }
 }
 
-// The root of the VD heuristic: the lowest-id node of maximum degree in the
+// The root r of the VD bound: the lowest-id node of maximum degree in the
 // underlying undirected graph, |out(v) U in(v)| = out + in - reciprocal arcs
 // (directed), as a key degree << 32 | ~id under atomicMax.
 __global__ void k_und_degree_key(const int32_t* rp, const int32_t* rrp, const uint32_t* recip, int32_t n,
@@ -2815,21 +2816,26 @@ __global__ void k_und_degree_key(const int32_t* rp, const int32_t* rrp, const ui
   atomicMax(best, mine);
 }
 
-// the root r from its key (lowest id among the maximum degree): level 0 = {r}
+__device__ __forceinline__ int32_t key_root(unsigned long long key) {
+  return (int32_t)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull));
+}
+
+// the root r from its key: level 0 = {r}
 __global__ void k_bfs_root(const unsigned long long* best, int32_t* dist, int32_t* front) {
-  const int32_t r = (int32_t)(0xFFFFFFFFu - (uint32_t)(*best & 0xFFFFFFFFull));
+  const int32_t r = key_root(*best);
   dist[r] = 0;
   front[0] = r;
 }
 
-// One level of the BFS over the underlying undirected graph (out-rows, and
-// in-rows too for a directed graph).  A warp expands one frontier node's row
-// of up to BFS_CHUNK arcs; a longer row is cut into BFS_CHUNK-arc items for
-// k_bfs_items, so that a hub's row is spread over many warps.
+// One level of a BFS from r along the arcs of one CSR: out-arcs for the
+// distances from r, in-arcs for the distances to r.  Top-down, a warp
+// expands one frontier node's row (tr, tc) of up to BFS_CHUNK arcs; a longer
+// row is cut into BFS_CHUNK-arc items for k_bfs_items, so that a hub's row
+// is spread over many warps.
 constexpr int BFS_CHUNK = 1024;
 
 struct BfsItem {
-  int32_t pass, v, begin, end;
+  int32_t v, begin, end, pad;
 };
 
 // scans arcs [a, b) of row c and appends the newly reached heads to next
@@ -2858,12 +2864,12 @@ __device__ __forceinline__ void bfs_scan(const int32_t* c, int32_t a, int32_t b,
 // The frontier's size is read on the device (*nfront_dev, or 1 for the root's
 // level when it is null), so the host can queue several levels at once.
 // A frontier of more than n / BFS_BOTTOM_UP nodes is expanded bottom-up
-// (Beamer et al.'s direction-optimising BFS): every unvisited node looks for
-// a neighbour at the current level and stops at the first.  Either direction
-// yields the same next level, so the eccentricity does not depend on it.
+// (Beamer et al.'s direction-optimising BFS): every unvisited node looks in
+// its row of the opposite CSR (br, bc) for a node at the current level and
+// stops at the first.  Either direction yields the same next level.
 constexpr int BFS_BOTTOM_UP = 16;
 
-__global__ void k_bfs_level(const int32_t* rp, const int32_t* ci, const int32_t* rrp, const int32_t* rci, int directed,
+__global__ void k_bfs_level(const int32_t* tr, const int32_t* tc, const int32_t* br, const int32_t* bc,
                             const int32_t* front, const int32_t* nfront_dev, int32_t* next, int32_t* nnext,
                             int32_t* dist, int32_t level, BfsItem* items, int32_t* nitems, int32_t items_cap,
                             int32_t n) {
@@ -2875,15 +2881,11 @@ __global__ void k_bfs_level(const int32_t* rp, const int32_t* ci, const int32_t*
       const int64_t v = base + threadIdx.x;
       bool mine = false;
       if (v < n && dist[v] < 0) {
-        for (int pass = 0; pass < (directed ? 2 : 1) && !mine; ++pass) {
-          const int32_t* r = pass ? rrp : rp;
-          const int32_t* c = pass ? rci : ci;
-          for (int32_t e = r[v]; e < r[v + 1]; ++e)
-            if (dist[c[e]] == level) {
-              mine = true;
-              break;
-            }
-        }
+        for (int32_t e = br[v]; e < br[v + 1]; ++e)
+          if (dist[bc[e]] == level) {
+            mine = true;
+            break;
+          }
         if (mine) dist[v] = level + 1;  // only this thread writes v's entry
       }
       const unsigned got = __ballot_sync(FULL, mine);
@@ -2900,38 +2902,289 @@ __global__ void k_bfs_level(const int32_t* rp, const int32_t* ci, const int32_t*
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = w0; i < nfront; i += nwarps) {
     const int32_t v = front[i];
-    for (int pass = 0; pass < (directed ? 2 : 1); ++pass) {
-      const int32_t* r = pass ? rrp : rp;
-      const int32_t* c = pass ? rci : ci;
-      const int32_t a = r[v], b = r[v + 1];
-      if (b - a <= BFS_CHUNK) {
-        bfs_scan(c, a, b, next, nnext, dist, level);
-        continue;
-      }
-      const int32_t k = (b - a + BFS_CHUNK - 1) / BFS_CHUNK;  // items of this row
-      int32_t at = 0;
-      if (lane == 0) at = atomicAdd(nitems, k);
-      at = __shfl_sync(FULL, at, 0);
-      for (int32_t q = lane; q < k; q += 32) {
-        if (at + q < items_cap) {
-          const int32_t s = a + q * BFS_CHUNK;
-          items[at + q] = BfsItem{pass, v, s, s + BFS_CHUNK < b ? s + BFS_CHUNK : b};
-        }
-      }
-      if (at + k > items_cap) bfs_scan(c, a + (items_cap > at ? items_cap - at : 0) * BFS_CHUNK, b, next, nnext,
-                                       dist, level);  // items beyond the buffer: this warp scans them
+    const int32_t a = tr[v], b = tr[v + 1];
+    if (b - a <= BFS_CHUNK) {
+      bfs_scan(tc, a, b, next, nnext, dist, level);
+      continue;
     }
+    const int32_t k = (b - a + BFS_CHUNK - 1) / BFS_CHUNK;  // items of this row
+    int32_t at = 0;
+    if (lane == 0) at = atomicAdd(nitems, k);
+    at = __shfl_sync(FULL, at, 0);
+    for (int32_t q = lane; q < k; q += 32) {
+      if (at + q < items_cap) {
+        const int32_t s = a + q * BFS_CHUNK;
+        items[at + q] = BfsItem{v, s, s + BFS_CHUNK < b ? s + BFS_CHUNK : b, 0};
+      }
+    }
+    if (at + k > items_cap) bfs_scan(tc, a + (items_cap > at ? items_cap - at : 0) * BFS_CHUNK, b, next, nnext,
+                                     dist, level);  // items beyond the buffer: this warp scans them
   }
 }
 
-__global__ void k_bfs_items(const int32_t* ci, const int32_t* rci, const BfsItem* items, const int32_t* nitems,
-                            int32_t items_cap, int32_t* next, int32_t* nnext, int32_t* dist, int32_t level) {
+__global__ void k_bfs_items(const int32_t* tc, const BfsItem* items, const int32_t* nitems, int32_t items_cap,
+                            int32_t* next, int32_t* nnext, int32_t* dist, int32_t level) {
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int32_t k = *nitems < items_cap ? *nitems : items_cap;
   for (int64_t i = w0; i < k; i += nwarps) {
     const BfsItem it = items[i];
-    bfs_scan(it.pass ? rci : ci, it.begin, it.end, next, nnext, dist, level);
+    bfs_scan(tc, it.begin, it.end, next, nnext, dist, level);
+  }
+}
+
+// ---- VD bound from the condensation into strongly connected components.
+// A shortest path visits the components along a path of the condensation,
+// each in a contiguous stretch that is a shortest path inside it: at most
+// |C| nodes, or e_in + e_out + 1 inside the root's component C_r (e_out and
+// e_in its largest distances from and to r).  The bound is the heaviest path
+// of the condensation under these weights.  Components get a label, the id
+// of one of their nodes: r for C_r (reached from r and reaching r), the node
+// itself for one trimmed away (no successor or no predecessor left among the
+// unlabelled nodes), the largest id of the component for the rest (colour
+// propagation: a node's colour is the largest id that reaches it; the nodes
+// of a root's colour that reach the root form its component).
+struct VdCore {
+  unsigned long long size;  // |C_r|
+  int32_t e_out, e_in;
+};
+
+__global__ void k_vd_core(const int32_t* df, const int32_t* db, int32_t n, VdCore* out) {
+  unsigned long long cnt = 0;
+  int32_t eo = 0, ei = 0;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t a = df[v], b = db[v];
+    if (a >= 0 && b >= 0) {
+      ++cnt;
+      eo = a > eo ? a : eo;
+      ei = b > ei ? b : ei;
+    }
+  }
+  cnt = warp_sum_u64(cnt);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    eo = max(eo, __shfl_xor_sync(FULL, eo, o));
+    ei = max(ei, __shfl_xor_sync(FULL, ei, o));
+  }
+  if (lane_id() == 0) {
+    if (cnt) atomicAdd(&out->size, cnt);
+    atomicMax(&out->e_out, eo);
+    atomicMax(&out->e_in, ei);
+  }
+}
+
+#define VD_FOR_NODES(v) \
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+
+__global__ void k_vd_label_init(const int32_t* df, const int32_t* db, int32_t n, const unsigned long long* best,
+                                int32_t* lab) {
+  const int32_t r = key_root(*best);
+  VD_FOR_NODES(v) lab[v] = (df[v] >= 0 && db[v] >= 0) ? r : -1;
+}
+
+// One trimming round.  A node of a component with two or more nodes keeps an
+// unlabelled successor and predecessor inside it, so it is never trimmed;
+// labels written by other threads in the same round may or may not be seen,
+// and either reading is valid.
+__global__ void k_vd_trim(const int32_t* rp, const int32_t* ci, const int32_t* rrp, const int32_t* rci, int32_t n,
+                          int32_t* lab, int32_t* changed) {
+  bool any = false;
+  VD_FOR_NODES(v) {
+    if (lab[v] >= 0) continue;
+    bool out = false, in = false;
+    for (int32_t e = rp[v]; e < rp[v + 1] && !out; ++e) out = lab[ci[e]] < 0;
+    if (out)
+      for (int32_t e = rrp[v]; e < rrp[v + 1] && !in; ++e) in = lab[rci[e]] < 0;
+    if (!out || !in) {
+      lab[v] = (int32_t)v;
+      any = true;
+    }
+  }
+  if (__any_sync(FULL, any) && lane_id() == 0) *changed = 1;
+}
+
+// unlabelled nodes: colour = own id, not yet known to reach their root
+__global__ void k_vd_color_init(const int32_t* lab, int32_t n, int32_t* col, int32_t* reach, int32_t* left) {
+  bool any = false;
+  VD_FOR_NODES(v) if (lab[v] < 0) {
+    col[v] = (int32_t)v;
+    reach[v] = 0;
+    any = true;
+  }
+  if (__any_sync(FULL, any) && lane_id() == 0) *left = 1;
+}
+
+// colour <- the largest colour among unlabelled predecessors (monotone; a
+// round without a change is the fixed point)
+__global__ void k_vd_color(const int32_t* rrp, const int32_t* rci, int32_t n, const int32_t* lab, int32_t* col,
+                           int32_t* changed) {
+  bool any = false;
+  VD_FOR_NODES(v) {
+    if (lab[v] >= 0) continue;
+    int32_t c = col[v];
+    for (int32_t e = rrp[v]; e < rrp[v + 1]; ++e) {
+      const int32_t u = rci[e];
+      if (lab[u] < 0) {
+        const int32_t cu = col[u];
+        c = cu > c ? cu : c;
+      }
+    }
+    if (c > col[v]) {
+      col[v] = c;
+      any = true;
+    }
+  }
+  if (__any_sync(FULL, any) && lane_id() == 0) *changed = 1;
+}
+
+__global__ void k_vd_reach_roots(const int32_t* lab, const int32_t* col, int32_t n, int32_t* reach) {
+  VD_FOR_NODES(v) if (lab[v] < 0 && col[v] == (int32_t)v) reach[v] = 1;
+}
+
+// a node reaches its root if a successor of the same colour does
+__global__ void k_vd_reach(const int32_t* rp, const int32_t* ci, int32_t n, const int32_t* lab, const int32_t* col,
+                           int32_t* reach, int32_t* changed) {
+  bool any = false;
+  VD_FOR_NODES(v) {
+    if (lab[v] >= 0 || reach[v]) continue;
+    const int32_t c = col[v];
+    for (int32_t e = rp[v]; e < rp[v + 1]; ++e) {
+      const int32_t u = ci[e];
+      if (lab[u] < 0 && col[u] == c && reach[u]) {
+        reach[v] = 1;
+        any = true;
+        break;
+      }
+    }
+  }
+  if (__any_sync(FULL, any) && lane_id() == 0) *changed = 1;
+}
+
+__global__ void k_vd_assign(const int32_t* col, const int32_t* reach, int32_t n, int32_t* lab) {
+  VD_FOR_NODES(v) if (lab[v] < 0 && reach[v]) lab[v] = col[v];
+}
+
+// component sizes, and the arcs entering each component from another
+__global__ void k_vd_sizes(const int32_t* lab, int32_t n, int32_t* sz) {
+  VD_FOR_NODES(v) atomicAdd(&sz[lab[v]], 1);
+}
+
+__global__ void k_vd_indeg(const int32_t* rp, const int32_t* ci, int32_t n, int64_t m, const int32_t* lab,
+                           int32_t* cnt) {
+  for_each_arc(rp, ci, n, m, [&](int32_t u, int64_t, int32_t v) {
+    const int32_t lv = lab[v];
+    if (lab[u] != lv) atomicAdd(&cnt[lv], 1);
+  });
+}
+
+// The heaviest path of the condensation, level by level in topological order
+// (Kahn): a component is ready once every arc entering it has been
+// processed; its heaviest path ending in it weighs w + best[label].
+// Single-node components join the node frontier; a larger component ready at
+// level l is marked rdy[label] = l and its nodes are found by a pass over
+// all nodes at that level.  slot[0] of level l: the next frontier's size;
+// slot[1]: a larger component is ready at level l + 1.
+struct VdKahn {
+  const int32_t *rp, *ci, *lab, *sz;
+  int32_t* cnt;
+  long long* best;
+  int32_t* rdy;
+  int32_t n;
+  int32_t root_label;
+  long long root_w;
+  long long* vd;
+};
+
+__device__ __forceinline__ long long vd_weight(const VdKahn& K, int32_t L) {
+  return L == K.root_label ? K.root_w : (long long)K.sz[L];
+}
+
+// all nodes whose label has no entering arc: level 0 (slot prev of level 0)
+__global__ void k_vd_kahn_init(VdKahn K, int32_t* front, int32_t* slot) {
+  const int32_t n = K.n;
+  const int lane = lane_id();
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = base + threadIdx.x;
+    bool mine = false;
+    if (v < n) {
+      const int32_t L = K.lab[v];
+      if (K.cnt[L] == 0) {
+        if (K.sz[L] == 1)
+          mine = true;
+        else if (L == (int32_t)v) {
+          K.rdy[L] = 0;
+          slot[1] = 1;
+        }
+      }
+    }
+    const unsigned got = __ballot_sync(FULL, mine);
+    if (got) {
+      int32_t at = 0;
+      if (lane == 0) at = atomicAdd(&slot[0], __popc(got));
+      at = __shfl_sync(FULL, at, 0);
+      if (mine) front[at + __popc(got & ((1u << lane) - 1u))] = (int32_t)v;
+    }
+  }
+}
+
+// one ready node u, by a warp: its path weight, then its arcs into other components
+__device__ void vd_kahn_node(const VdKahn& K, int32_t u, int32_t level, int32_t* next, int32_t* slot) {
+  const int lane = lane_id();
+  const int32_t L = K.lab[u];
+  const long long w = vd_weight(K, L) + K.best[L];
+  if (lane == 0) atomicMax(K.vd, w);
+  const int32_t a = K.rp[u], b = K.rp[u + 1];
+  for (int32_t base = a; base < b; base += 32) {
+    const int32_t e = base + lane;
+    bool push = false;
+    int32_t y = 0;
+    if (e < b) {
+      y = K.ci[e];
+      const int32_t Ly = K.lab[y];
+      if (Ly != L) {
+        atomicMax(&K.best[Ly], w);
+        if (atomicSub(&K.cnt[Ly], 1) == 1) {
+          if (K.sz[Ly] == 1) {
+            push = true;
+          } else {
+            K.rdy[Ly] = level + 1;
+            slot[1] = 1;
+          }
+        }
+      }
+    }
+    const unsigned got = __ballot_sync(FULL, push);
+    if (got) {
+      int32_t at = 0;
+      if (lane == 0) at = atomicAdd(&slot[0], __popc(got));
+      at = __shfl_sync(FULL, at, 0);
+      if (push) next[at + __popc(got & ((1u << lane) - 1u))] = y;
+    }
+  }
+}
+
+__global__ void k_vd_kahn_level(VdKahn K, const int32_t* front, const int32_t* prev, int32_t* next, int32_t* slot,
+                                int32_t level) {
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int32_t nfront = prev[0];
+  for (int64_t i = w0; i < nfront; i += nwarps) vd_kahn_node(K, front[i], level, next, slot);
+  if (!prev[1]) return;
+  // larger components ready at this level: their nodes, 32 ids per warp step
+  const int lane = lane_id();
+  for (int64_t base = w0 * 32; base < K.n; base += nwarps * 32) {
+    const int64_t v = base + lane;
+    bool mine = false;
+    if (v < K.n) {
+      const int32_t L = K.lab[v];
+      mine = K.sz[L] > 1 && K.rdy[L] == level;
+    }
+    unsigned got = __ballot_sync(FULL, mine);
+    while (got) {
+      const int q = __ffs(got) - 1;
+      got &= got - 1;
+      vd_kahn_node(K, (int32_t)(base + q), level, next, slot);
+    }
   }
 }
 
@@ -3424,7 +3677,9 @@ struct LoadScratch {
   unsigned long long* best;    // the VD root's key
   int32_t* cnt;                // BFS level counters: slot l % 8 holds {next frontier size, items} of level l
   uint32_t* recip;             // n (directed graphs), else null
-  int32_t *dist, *qa, *qb;     // n each
+  VdCore* core;                // the root's component: size, e_out, e_in
+  int32_t *dist, *qa, *qb;     // n each: distances from r, BFS queues
+  int32_t* dist_b;             // n (directed graphs): distances to r, else null
   BfsItem* items;
   int32_t items_cap;
   void* base;
@@ -3436,7 +3691,8 @@ kadabra_status load_scratch(const kadabra_graph* g, LoadScratch* S) {
   S->items_cap = (int32_t)cap;
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t o_head = 0, o_recip = up(1024), o_dist = o_recip + (g->directed ? up(4 * n) : 0);
-  const size_t o_qa = o_dist + up(4 * n), o_qb = o_qa + up(4 * n), o_items = o_qb + up(4 * n);
+  const size_t o_qa = o_dist + up(4 * n), o_qb = o_qa + up(4 * n), o_distb = o_qb + up(4 * n);
+  const size_t o_items = o_distb + (g->directed ? up(4 * n) : 0);
   const size_t total = o_items + sizeof(BfsItem) * (size_t)cap;
   KCK(cudaMalloc(&S->base, total));
   unsigned char* b = static_cast<unsigned char*>(S->base);
@@ -3446,7 +3702,9 @@ kadabra_status load_scratch(const kadabra_graph* g, LoadScratch* S) {
   S->cnt = reinterpret_cast<int32_t*>(b + o_head + 512);
   S->fp = reinterpret_cast<int32_t*>(b + o_head + 64);
   S->recip = g->directed ? reinterpret_cast<uint32_t*>(b + o_recip) : nullptr;
+  S->core = reinterpret_cast<VdCore*>(b + o_head + 768);
   S->dist = reinterpret_cast<int32_t*>(b + o_dist);
+  S->dist_b = g->directed ? reinterpret_cast<int32_t*>(b + o_distb) : nullptr;
   S->qa = reinterpret_cast<int32_t*>(b + o_qa);
   S->qb = reinterpret_cast<int32_t*>(b + o_qb);
   S->items = reinterpret_cast<BfsItem*>(b + o_items);
@@ -3455,22 +3713,16 @@ kadabra_status load_scratch(const kadabra_graph* g, LoadScratch* S) {
   return KADABRA_OK;
 }
 
-// VD heuristic (reading 9): 2 ecc(r) + 1 for the lowest-id node r of maximum
-// degree, eccentricities over the underlying undirected graph.
-kadabra_status compute_vd(kadabra_graph* g, LoadTrace& tr, const LoadScratch& S) {
+// Queues a BFS from the root along (tr, tc) into dist (bottom-up levels look
+// in (br, bc)).  Levels are queued BFS_BATCH at a time and their sizes read
+// back once per batch; levels past the end find an empty frontier and do
+// nothing.
+kadabra_status vd_bfs(kadabra_graph* g, const LoadScratch& S, const int32_t* tr, const int32_t* tc,
+                      const int32_t* br, const int32_t* bc, int32_t* dist) {
   const int32_t n = g->n;
-  const int32_t* rrp = g->directed ? g->rrp : g->rp;
-  const int32_t* rci = g->directed ? g->rci : g->ci;
-  const int blocks = std::max(1, std::min(4 * g->num_sms, (n + 255) / 256));
-  KCK(cudaMemsetAsync(S.dist, 0xFF, sizeof(int32_t) * (size_t)n));
-  k_und_degree_key<<<blocks, 256>>>(g->rp, rrp, S.recip, n, g->directed, S.best);
-  k_bfs_root<<<1, 1>>>(S.best, S.dist, S.qa);  // the root stays on the device
-  KCK(cudaGetLastError());
-  tr.mark("vd root");
-  // Levels are queued BFS_BATCH at a time and their sizes read back once per
-  // batch; levels past the end find an empty frontier and do nothing.
   constexpr int BFS_BATCH = 4, SLOTS = 8;
-  int32_t level = 0;  // levels with a non-empty next frontier so far
+  k_bfs_root<<<1, 1>>>(S.best, dist, S.qa);  // the root stays on the device
+  KCK(cudaGetLastError());
   bool done = false;
   for (int32_t l0 = 0; !done && l0 <= n; l0 += BFS_BATCH) {
     for (int k = 0; k < BFS_BATCH; ++k)
@@ -3481,28 +3733,162 @@ kadabra_status compute_vd(kadabra_graph* g, LoadTrace& tr, const LoadScratch& S)
       int32_t* out_q = (l & 1) ? S.qa : S.qb;
       int32_t* c = S.cnt + 2 * (l % SLOTS);
       const int32_t* prev = l == 0 ? nullptr : S.cnt + 2 * ((l + SLOTS - 1) % SLOTS);
-      k_bfs_level<<<8 * g->num_sms, 256>>>(g->rp, g->ci, rrp, rci, g->directed, in_q, prev, out_q, c, S.dist, l,
-                                           S.items, c + 1, S.items_cap, n);
-      k_bfs_items<<<8 * g->num_sms, 256>>>(g->ci, rci, S.items, c + 1, S.items_cap, out_q, c, S.dist, l);
+      k_bfs_level<<<8 * g->num_sms, 256>>>(tr, tc, br, bc, in_q, prev, out_q, c, dist, l, S.items, c + 1,
+                                           S.items_cap, n);
+      k_bfs_items<<<8 * g->num_sms, 256>>>(tc, S.items, c + 1, S.items_cap, out_q, c, dist, l);
     }
     int32_t h[2 * SLOTS];
     if (cudaMemcpy(h, S.cnt, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
       return fail(KADABRA_ERR_CUDA, std::string("vd bfs: ") + cudaGetErrorString(cudaGetLastError()));
-    for (int k = 0; k < BFS_BATCH; ++k) {
+    for (int k = 0; k < BFS_BATCH; ++k)
       if (h[2 * ((l0 + k) % SLOTS)] == 0) {
         done = true;
         break;
       }
-      ++level;
+  }
+  return KADABRA_OK;
+}
+
+// The condensation's heaviest path when the root's component is not the
+// whole graph (kernels k_vd_*): labels by trimming and colour propagation,
+// then a level-by-level pass in topological order.
+kadabra_status vd_condensation(kadabra_graph* g, LoadTrace& tr, const LoadScratch& S, const int32_t* db,
+                               long long root_w, int64_t* vd_out) {
+  const int32_t n = g->n;
+  const int64_t m = g->m;
+  const int32_t* rrp = g->directed ? g->rrp : g->rp;
+  const int32_t* rci = g->directed ? g->rci : g->ci;
+  const int bn = std::max(1, std::min(16 * g->num_sms, (n + 255) / 256));
+  const int ba = (int)std::max<int64_t>(1, std::min<int64_t>(16 * g->num_sms, ((m + LOAD_CHUNK - 1) / LOAD_CHUNK + 255) / 256));
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t N4 = up(4 * (size_t)n), N8 = up(8 * (size_t)n);
+  void* base = nullptr;
+  KCK(cudaMalloc(&base, 256 + 6 * N4 + N8));
+  struct Free {
+    void* p;
+    ~Free() { cudaFree(p); }
+  } guard{base};
+  unsigned char* b = static_cast<unsigned char*>(base);
+  int32_t* flag = reinterpret_cast<int32_t*>(b);              // [0] a change, [1] an unlabelled node
+  int32_t* slots = reinterpret_cast<int32_t*>(b + 64);        // 8 level slots of 2
+  long long* vd = reinterpret_cast<long long*>(b + 128);
+  int32_t* lab = reinterpret_cast<int32_t*>(b + 256);
+  int32_t* col = reinterpret_cast<int32_t*>(b + 256 + N4);
+  int32_t* reach = reinterpret_cast<int32_t*>(b + 256 + 2 * N4);
+  int32_t* sz = reinterpret_cast<int32_t*>(b + 256 + 3 * N4);
+  int32_t* cnt = reinterpret_cast<int32_t*>(b + 256 + 4 * N4);
+  int32_t* rdy = reinterpret_cast<int32_t*>(b + 256 + 5 * N4);
+  long long* best = reinterpret_cast<long long*>(b + 256 + 6 * N4);
+  k_vd_label_init<<<bn, 256>>>(S.dist, db, n, S.best, lab);
+  KCK(cudaGetLastError());
+  // repeats a kernel (4 queued rounds per read-back) until a round changes nothing
+  auto until_stable = [&](auto&& round) -> kadabra_status {
+    for (int64_t it = 0; it <= (int64_t)n; it += 4) {
+      KCK(cudaMemsetAsync(flag, 0, sizeof(int32_t)));
+      for (int k = 0; k < 4; ++k) round();
+      int32_t h = 0;
+      if (cudaMemcpy(&h, flag, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(KADABRA_ERR_CUDA, std::string("vd bound: ") + cudaGetErrorString(cudaGetLastError()));
+      if (!h) return KADABRA_OK;
+    }
+    return fail(KADABRA_ERR_INTERNAL, "vd bound: no fixed point");
+  };
+  for (int64_t outer = 0;; ++outer) {
+    if (outer > (int64_t)n) return fail(KADABRA_ERR_INTERNAL, "vd bound: components not all labelled");
+    KTRY(until_stable([&] { k_vd_trim<<<bn, 256>>>(g->rp, g->ci, rrp, rci, n, lab, flag); }));
+    KCK(cudaMemsetAsync(flag + 1, 0, sizeof(int32_t)));
+    k_vd_color_init<<<bn, 256>>>(lab, n, col, reach, flag + 1);
+    int32_t left = 0;
+    if (cudaMemcpy(&left, flag + 1, sizeof(left), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(KADABRA_ERR_CUDA, "vd bound");
+    if (!left) break;
+    KTRY(until_stable([&] { k_vd_color<<<bn, 256>>>(rrp, rci, n, lab, col, flag); }));
+    k_vd_reach_roots<<<bn, 256>>>(lab, col, n, reach);
+    KTRY(until_stable([&] { k_vd_reach<<<bn, 256>>>(g->rp, g->ci, n, lab, col, reach, flag); }));
+    k_vd_assign<<<bn, 256>>>(col, reach, n, lab);
+  }
+  tr.mark("vd components");
+  KCK(cudaMemsetAsync(sz, 0, 2 * N4));  // sz, cnt
+  KCK(cudaMemsetAsync(rdy, 0xFF, N4));
+  KCK(cudaMemsetAsync(best, 0, N8));
+  KCK(cudaMemsetAsync(b + 64, 0, 192));  // slots, vd
+  k_vd_sizes<<<bn, 256>>>(lab, n, sz);
+  k_vd_indeg<<<ba, 256>>>(g->rp, g->ci, n, m, lab, cnt);
+  unsigned long long key = 0;
+  if (cudaMemcpy(&key, S.best, sizeof(key), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(KADABRA_ERR_CUDA, "vd bound");
+  VdKahn K{g->rp, g->ci, lab, sz, cnt, best, rdy, n, (int32_t)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull)),
+           root_w, vd};
+  constexpr int SLOTS = 8, BATCH = 4;
+  k_vd_kahn_init<<<bn, 256>>>(K, S.qa, slots + 2 * (SLOTS - 1));  // the slot level 0 reads
+  KCK(cudaGetLastError());
+  bool done = false;
+  for (int32_t l0 = 0; !done; l0 += BATCH) {
+    if (l0 > n) return fail(KADABRA_ERR_INTERNAL, "vd bound: condensation levels");
+    for (int k = 0; k < BATCH; ++k) KCK(cudaMemsetAsync(slots + 2 * ((l0 + k) % SLOTS), 0, 2 * sizeof(int32_t)));
+    for (int k = 0; k < BATCH; ++k) {
+      const int32_t l = l0 + k;
+      k_vd_kahn_level<<<8 * g->num_sms, 256>>>(K, (l & 1) ? S.qb : S.qa, slots + 2 * ((l + SLOTS - 1) % SLOTS),
+                                               (l & 1) ? S.qa : S.qb, slots + 2 * (l % SLOTS), l);
+    }
+    int32_t h[2 * SLOTS];
+    if (cudaMemcpy(h, slots, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(KADABRA_ERR_CUDA, std::string("vd bound: ") + cudaGetErrorString(cudaGetLastError()));
+    for (int k = 0; k < BATCH; ++k) {
+      const int32_t* sl = h + 2 * ((l0 + k) % SLOTS);
+      if (sl[0] == 0 && sl[1] == 0) {
+        done = true;
+        break;
+      }
     }
   }
-  g->vd = 2 * (int64_t)level + 1;
+  long long hv = 0;
+  if (cudaMemcpy(&hv, vd, sizeof(hv), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(KADABRA_ERR_CUDA, "vd bound");
+  *vd_out = hv;
+  tr.mark("vd condensation");
+  return KADABRA_OK;
+}
+
+// VD bound (omega of Alg. 1; Sec. 2): BFS from the root r forward (and,
+// for a directed graph, backward) gives the root's component C_r and its
+// weight e_out + e_in + 1 (2 ecc(r) + 1 undirected).  When C_r is the whole
+// graph that is the bound; otherwise the condensation decides it.
+kadabra_status compute_vd(kadabra_graph* g, LoadTrace& tr, const LoadScratch& S) {
+  const int32_t n = g->n;
+  const int32_t* rrp = g->directed ? g->rrp : g->rp;
+  const int32_t* rci = g->directed ? g->rci : g->ci;
+  const int blocks = std::max(1, std::min(4 * g->num_sms, (n + 255) / 256));
+  KCK(cudaMemsetAsync(S.dist, 0xFF, sizeof(int32_t) * (size_t)n));
+  if (g->directed) KCK(cudaMemsetAsync(S.dist_b, 0xFF, sizeof(int32_t) * (size_t)n));
+  KCK(cudaMemsetAsync(S.core, 0, sizeof(VdCore)));
+  k_und_degree_key<<<blocks, 256>>>(g->rp, rrp, S.recip, n, g->directed, S.best);
+  KCK(cudaGetLastError());
+  tr.mark("vd root");
+  KTRY(vd_bfs(g, S, g->rp, g->ci, rrp, rci, S.dist));
+  const int32_t* db = S.dist;
+  if (g->directed) {
+    KTRY(vd_bfs(g, S, rrp, rci, g->rp, g->ci, S.dist_b));
+    db = S.dist_b;
+  }
+  k_vd_core<<<blocks, 256>>>(S.dist, db, n, S.core);
+  VdCore core;
+  if (cudaMemcpy(&core, S.core, sizeof(core), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(KADABRA_ERR_CUDA, std::string("vd: ") + cudaGetErrorString(cudaGetLastError()));
   tr.mark("vd bfs");
+  const long long root_w = (long long)core.e_out + core.e_in + 1;
+  if (core.size == (unsigned long long)n) {
+    g->vd = root_w;
+    return KADABRA_OK;
+  }
+  int64_t vd = 0;
+  KTRY(vd_condensation(g, tr, S, db, root_w, &vd));
+  g->vd = vd;
   return KADABRA_OK;
 }
 
 // Validates a device CSR (offsets, ids, order, self-loops, mirror/symmetry),
-// takes its fingerprint and computes the VD heuristic.
+// takes its fingerprint and computes the VD bound.
 kadabra_status finish_load(kadabra_graph* g) {
   LoadTrace tr;
   LoadScratch S;

@@ -62,7 +62,7 @@ def _assert_delta_equal(kd, orc, count0, alpha, omega, lam, delta, eps):
 
 def test_compute_delta_matches_oracle_bitwise(kd, orc, er2000):
     lam, delta, eps = 0.01, 0.1, 0.001
-    vd = orc.vd_heuristic(er2000)
+    vd = orc.vd_bound(er2000)
     omega = orc.omega(lam, delta, vd)
     alpha = max(1, int(omega // 100))
     rc, count0, _ = orc.accumulate(er2000, seed=1, domain=1, first_idx=0, count=alpha)

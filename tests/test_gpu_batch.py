@@ -112,3 +112,26 @@ def test_batch_repeated_mixed_depths_match_plain(kd, gg):
                 assert got[i].tau == ref.tau and np.array_equal(got[i].counts, ref.counts), (it, i)
     finally:
         B.free()
+
+
+@pytest.mark.slow
+def test_batched_workload_largest_graphs_match_oracle(kd, orc):
+    """The 64-graph uneven Barabasi-Albert workload of the benchmark, run as
+    one batch; each of its 8 largest graphs (n up to 2 * 10^6) must equal the
+    oracle's run replayed over index ranges (same K)."""
+    import bench
+    from replay import replay_run
+    graphs = bench.make_batched_graphs()
+    b = bench.BATCHED
+    G = len(graphs)
+    seeds = [7 + i for i in range(G)]
+    B = kd.Batch(graphs)
+    try:
+        got = B.run([b["lam"]] * G, [b["delta"]] * G, seeds)
+        for i in range(G):
+            assert got[i].vd == B.views[i].vd
+    finally:
+        B.free()
+    for i in sorted(range(G), key=lambda i: -graphs[i].n)[:8]:
+        assert got[i].vd == orc.vd_bound(graphs[i])
+        replay_run(orc, graphs[i], got[i], b["lam"], b["delta"], got[i].check_interval, seeds[i])

@@ -200,7 +200,7 @@ def test_load_csr_device_tensors(kd, orc, er2000):
     G = kd.kadabra_load_csr_device(er2000.n, rp, ci)
     try:
         got = kd.kadabra_sample_paths(G, 2, 0, 0, 500)
-        assert G.vd == orc.vd_heuristic(er2000)
+        assert G.vd == orc.vd_bound(er2000)
     finally:
         G.free()
     assert_samples_equal(got, orc.sample_paths(er2000, 2, 0, 0, 500), "device csr")
@@ -241,7 +241,7 @@ def test_invalid_csr_rejected(kd, gg):
 
 
 def test_vd_with_hub_rows_matches_oracle(kd, orc, gg):
-    """The VD heuristic's root and BFS on graphs whose rows exceed the BFS's
+    """The VD bound's root and BFS on graphs whose rows exceed the BFS's
     per-warp chunk (hubs of degree > 1024, split into work items), directed
     graphs with and without reciprocal arcs (undirected degree = out + in -
     reciprocal), and a graph with empty rows."""
@@ -259,9 +259,54 @@ def test_vd_with_hub_rows_matches_oracle(kd, orc, gg):
     for name, g in cases:
         G = kd.kadabra_load_csr(g)
         try:
-            assert G.vd == orc.vd_heuristic(g), name
+            assert G.vd == orc.vd_bound(g), name
         finally:
             G.free()
+
+
+def _scc_chain(gg, k, size, seed):
+    """k directed cycles of `size` nodes in a chain (an arc from each cycle to
+    the next) plus random arcs forward along the chain: components with two or
+    more nodes that become ready at different levels of the condensation."""
+    rng = np.random.default_rng(seed)
+    e = set()
+    for c in range(k):
+        b = c * size
+        e |= {(b + i, b + (i + 1) % size) for i in range(size)}
+        if c + 1 < k:
+            e.add((b + int(rng.integers(size)), b + size + int(rng.integers(size))))
+    for _ in range(3 * k):
+        a, b = sorted(rng.integers(0, k * size, size=2))
+        if a // size < b // size:
+            e.add((int(a), int(b)))
+    return gg.from_edges(k * size, sorted(e), directed=True, name=f"scc_chain{k}x{size}")
+
+
+def test_vd_bound_condensation_matches_oracle(kd, orc, gg):
+    """Graphs whose root component is not the whole graph, so the bound comes
+    from the condensation: directed graphs with many components (trimmed
+    singletons, components found by colour propagation, components ready at
+    different levels), the chain with a hub whose undirected-eccentricity
+    rule under-counts, and undirected graphs with several components.  The
+    GPU bound equals the oracle's and bounds every shortest path."""
+    import networkx as nx
+    from test_oracle_pins import hub_sink_graph, _true_vd
+    cases = [random_graph(gg, n, p, seed, directed=True)
+             for (n, p, seed) in ((30, 0.05, 2), (60, 0.02, 5), (200, 0.012, 7), (400, 0.004, 8), (300, 0.02, 9))]
+    cases += [hub_sink_graph(gg, 40), gg.directed_cycle(11), _scc_chain(gg, 12, 5, 3), _scc_chain(gg, 40, 3, 4),
+              gg.from_edges(10, [(i, i + 1) for i in range(9)], directed=True, name="dpath10"),
+              gg.from_edges(25, [(i, i + 1) for i in range(4)] + [(i, i + 1) for i in range(5, 24)], name="p5+p20"),
+              random_graph(gg, 300, 0.006, 11), gg.rmat(12, 16, 0.57, 0.19, 0.19, 1),
+              gg.rmat(16, 8, 0.57, 0.19, 0.19, 3)]
+    for g in cases:
+        G = kd.kadabra_load_csr(g)
+        try:
+            got = G.vd
+        finally:
+            G.free()
+        assert got == orc.vd_bound(g), g.name
+        if g.n <= 400:
+            assert got >= _true_vd(g), g.name
 
 
 def test_workspace_reuse_across_graph_objects(kd, orc, gg, er2000):
@@ -392,7 +437,7 @@ def test_run_chung_lu_full_size_matches_oracle(kd, orc, chung_lu_1m):
         vd_gpu = G.vd
     finally:
         G.free()
-    assert vd_gpu == orc.vd_heuristic(g) == got.vd
+    assert vd_gpu == orc.vd_bound(g) == got.vd
     assert got.omega == orc.omega(lam, delta, got.vd)
     assert got.alpha == max(1, math.floor(got.omega / 100))
     bounds = list(range(0, got.tau, K)) + [got.tau]

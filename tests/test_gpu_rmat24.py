@@ -1,7 +1,10 @@
 """The R-MAT scale-24 benchmark graph (directed, 2^24 ids, about 2.6 * 10^8
-arcs, forward and reverse CSR) at full size: per-sample parity with the
-oracle on sampled index ranges of both RNG domains, and a full top-k run
-whose ranking must be the order of its own counts (GPU only, slow)."""
+arcs, forward and reverse CSR) at full size: the VD bound against the
+oracle's, per-sample parity with the oracle on sampled index ranges of both
+RNG domains, and full runs in all-nodes and top-k mode (lambda = 0.0025,
+delta = 0.1, K = 2^16) replayed by the oracle over index ranges: C, every
+stop decision, tau, the hit counts, max f, max g and the ranking (GPU only,
+slow)."""
 
 import numpy as np
 import pytest
@@ -40,6 +43,25 @@ def test_rmat24_samples_match_oracle(kd, orc, rmat24, G, domain, first, count):
     assert np.array_equal(got.path_len[ok], ref.path_len[ok])
     assert np.array_equal(got.paths[ok], ref.paths[ok])
     assert np.array_equal(got.stats[ok], ref.stats[ok])
+
+
+def test_rmat24_vd_bound_matches_oracle(orc, rmat24, G):
+    assert G.vd == orc.vd_bound(rmat24)
+
+
+def test_rmat24_run_matches_oracle(kd, orc, rmat24, G):
+    from replay import replay_run
+    K = 1 << 16
+    got = kd.kadabra_run(G, 0.0025, 0.1, 0, 1, check_interval=K)
+    assert got.vd == G.vd
+    replay_run(orc, rmat24, got, 0.0025, 0.1, K, 1)
+
+
+def test_rmat24_topk_run_matches_oracle(kd, orc, rmat24, G):
+    from replay import replay_run
+    K = 1 << 16
+    got = kd.kadabra_run(G, 0.0025, 0.1, 10, 1, check_interval=K)
+    replay_run(orc, rmat24, got, 0.0025, 0.1, K, 1, k=10)
 
 
 def test_rmat24_topk_run_ranking(kd, rmat24, G):

@@ -127,20 +127,86 @@ def test_omega_reproduces_printed_rk_counts(orc):
     assert orc.omega(0.01, 0.1, 2) == orc.omega(0.01, 0.1, 3)  # VD-2 < 1 uses 0
 
 
-def test_vd_heuristic_is_an_upper_bound(orc, gg):
-    """VD = 2 ecc(r) + 1 bounds the node count of every shortest path."""
+def _nx_graph(g):
     import networkx as nx
-    for g in (gg.path_graph(9), gg.star_graph(8), gg.grid_graph(5, 7), random_graph(gg, 40, 0.08, 1)):
-        vd = orc.vd_heuristic(g)
-        G = nx.Graph()
-        G.add_nodes_from(range(g.n))
-        for v in range(g.n):
-            for w in g.col[g.row_ptr[v]:g.row_ptr[v + 1]]:
-                G.add_edge(v, int(w))
-        longest = max(max(d.values()) for _, d in nx.all_pairs_shortest_path_length(G))
-        assert vd >= longest + 1
-    # path P9: max degree 2 at node 1 (lowest id), ecc(1) = 7
-    assert orc.vd_heuristic(gg.path_graph(9)) == 15
+    G = nx.DiGraph() if g.directed else nx.Graph()
+    G.add_nodes_from(range(g.n))
+    for v in range(g.n):
+        for w in g.col[g.row_ptr[v]:g.row_ptr[v + 1]]:
+            G.add_edge(v, int(w))
+    return G
+
+
+def _true_vd(g):
+    """The most nodes on any shortest path, from networkx's all-pairs BFS."""
+    import networkx as nx
+    return 1 + max(max(d.values()) for _, d in nx.all_pairs_shortest_path_length(_nx_graph(g)))
+
+
+def hub_sink_graph(gg, L):
+    """Directed path 0 -> 1 -> ... -> L plus a hub h = L + 1 with an arc i -> h
+    from every path node.  Its longest shortest path is the chain itself (L + 1
+    nodes), yet 2 ecc(h) + 1 on the underlying undirected graph is 3."""
+    e = [(i, i + 1) for i in range(L)] + [(i, L + 1) for i in range(L + 1)]
+    return gg.from_edges(L + 2, e, directed=True, name=f"hub_sink{L}")
+
+
+def _vd_graphs(gg):
+    und = [gg.path_graph(9), gg.star_graph(8), gg.grid_graph(5, 7), random_graph(gg, 40, 0.08, 1),
+           gg.from_edges(25, [(i, i + 1) for i in range(4)] + [(i, i + 1) for i in range(5, 24)], name="p5+p20"),
+           random_graph(gg, 60, 0.02, 7)]
+    dirg = [random_graph(gg, n, p, seed, directed=True)
+            for (n, p, seed) in ((30, 0.05, 2), (40, 0.03, 3), (50, 0.04, 4), (60, 0.02, 5), (45, 0.08, 6))]
+    dirg += [hub_sink_graph(gg, 12), gg.directed_cycle(11),
+             gg.from_edges(10, [(i, i + 1) for i in range(9)], directed=True, name="dpath10")]
+    return und + dirg
+
+
+def test_vd_bound_is_an_upper_bound(orc, gg):
+    """The VD bound omega rests on (Alg. 1, Sec. 2) bounds the node count of
+    every shortest path, on undirected graphs (connected or not) and directed
+    ones (networkx all-pairs BFS)."""
+    for g in _vd_graphs(gg):
+        assert orc.vd_bound(g) >= _true_vd(g), g.name
+
+
+def test_vd_bound_closed_forms(orc, gg):
+    # undirected P9: max degree 2 at node 1 (lowest id), ecc(1) = 7
+    assert orc.vd_bound(gg.path_graph(9)) == 15
+    # P5 + P20: 2 ecc + 1 = 7 for the root's component, the other has 20 nodes
+    g = gg.from_edges(25, [(i, i + 1) for i in range(4)] + [(i, i + 1) for i in range(5, 24)], name="p5+p20")
+    assert orc.vd_bound(g) == 20 == _true_vd(g)
+    # directed path 0 -> ... -> 9: singleton components along a chain of 10
+    g = gg.from_edges(10, [(i, i + 1) for i in range(9)], directed=True, name="dpath10")
+    assert orc.vd_bound(g) == 10 == _true_vd(g)
+    # directed n-cycle: one component, e_out = e_in = n - 1
+    assert orc.vd_bound(gg.directed_cycle(11)) == 21
+    # hub-sink: the chain 0..L then the hub, L + 2 >= L + 1 (the heuristic gave 3)
+    g = hub_sink_graph(gg, 40)
+    assert _true_vd(g) == 41 and orc.vd_bound(g) == 42
+
+
+def test_vd_bound_is_the_condensation_longest_path(orc, gg):
+    """The bound's definition recomputed with networkx: components by
+    networkx's condensation, weights |C| except e_in + e_out + 1 for the
+    root's component, the heaviest path by a DP in topological order."""
+    import networkx as nx
+    for g in _vd_graphs(gg):
+        G = _nx_graph(g)
+        D = G if g.directed else G.to_directed()
+        und_deg = [len(set(D.successors(v)) | set(D.predecessors(v))) for v in range(g.n)]
+        r = min(range(g.n), key=lambda v: (-und_deg[v], v))
+        C = nx.condensation(D)
+        cr = C.graph["mapping"][r]
+        members = C.nodes[cr]["members"]
+        dout = nx.single_source_shortest_path_length(D, r)
+        din = nx.single_source_shortest_path_length(D.reverse(copy=False), r)
+        wt = {c: len(C.nodes[c]["members"]) for c in C.nodes}
+        wt[cr] = max(dout[v] for v in members) + max(din[v] for v in members) + 1
+        best = {}
+        for c in reversed(list(nx.topological_sort(C))):
+            best[c] = wt[c] + max((best[d] for d in C.successors(c)), default=0)
+        assert orc.vd_bound(g) == max(best.values()), g.name
 
 
 # ------------------------------------------------------------------ Brandes
@@ -415,10 +481,13 @@ def test_compute_delta_general(orc):
 @pytest.mark.slow
 def test_lambda_delta_guarantee_over_seeds(orc, gg):
     """Thm. 1: P(exists v: |b~(v) - bc(v)| > lambda) <= delta.  200 seeds on
-    five small graphs at lambda in {0.05, 0.02}; one-sided binomial test."""
+    six small graphs at lambda in {0.05, 0.02}; one-sided binomial test."""
     from scipy.stats import binomtest
+    # hub_sink_graph(gg, 30): a directed graph on which 2 ecc(r) + 1 over the
+    # underlying undirected graph (3) is far below its vertex diameter (31)
     graphs = [random_graph(gg, 30, 0.1, 41), random_graph(gg, 26, 0.13, 42, directed=True),
-              gg.grid_graph(5, 6), gg.star_graph(25), gg.barabasi_albert(40, 2, 43)]
+              gg.grid_graph(5, 6), gg.star_graph(25), gg.barabasi_albert(40, 2, 43), hub_sink_graph(gg, 30)]
+    assert orc.vd_bound(graphs[-1]) >= _true_vd(graphs[-1]) == 31
     delta = 0.1
     for lam in (0.05, 0.02):
         fails = trials = 0
