@@ -92,7 +92,7 @@ typedef struct {
                               batch of min(K, 4096) samples times every allowed setup
                               of table and warp tier; the choice is cached per graph
                               fingerprint), or one of the two values the library
-                              offers (3: 4096-slot tables, 4: 2048-slot);
+                              offers (4: 4096-slot tables, 5: 2048-slot on GB300);
                               any other value is KADABRA_ERR_ARG.  Results do not
                               depend on it.  Batches and serving use the default.  */
   int32_t warp_tier;       /* one-warp-per-sample tier in front of tier S (samples whose

@@ -81,7 +81,7 @@ namespace {
 #define KD_FAST_HLOG 12
 #endif
 #ifndef KD_MIN_BLOCKS
-#define KD_MIN_BLOCKS 3
+#define KD_MIN_BLOCKS 4
 #endif
 constexpr int NT = KD_NT;          // threads per sampler CTA
 constexpr int NW = NT / 32;        // warps per sampler CTA
@@ -161,7 +161,7 @@ struct Tables {
   unsigned long long* hsig; // sigma of the node at the same position
   uint32_t hmask;
   int hlog;
-  int32_t* lnode;           // level lists: node ids
+  int32_t* lnode;           // level lists: node ids (global-memory tiers; null in the packed tiers)
   uint32_t* lpos;           // level lists: hash positions (global-memory tiers)
   uint16_t* lpos16;         //   the same, 16 bits, in the shared-memory tiers (2^HLOG <= 2^16 slots)
   int2* pr;                 // frontier: {degree prefix, row start}; frcap+1 entries
@@ -183,6 +183,13 @@ __device__ __forceinline__ int& lvl_hi(const Tables& T, int side, int d) {
 template <bool PK>
 __device__ __forceinline__ uint32_t lpos_get(const Tables& T, int i) {
   return PK ? (uint32_t)T.lpos16[i] : T.lpos[i];
+}
+// list entry i's node: the packed tiers keep no id list and read it from the
+// entry's hash word (its high half never changes once published)
+template <bool PK>
+__device__ __forceinline__ int32_t list_node(const Tables& T, int i) {
+  if (PK) return (int32_t)(T.hkv[T.lpos16[i]] >> 32);
+  return T.lnode[i];
 }
 template <bool PK>
 __device__ __forceinline__ void lpos_set(const Tables& T, int i, uint32_t pos) {
@@ -371,14 +378,13 @@ struct Ctl {
   int sel_warp;
   int pick, pick_pos;
   int mode;       // backtracking: 0 = scan the row of x, 1 = scan the previous level
-  int bt_half, bt_x, bt_dx;  // backtracking state between warp 0 and the block
-  uint32_t bt_j;             //   and the next Philox block
+  int bt_x[2], bt_dx[2];     // backtracking walkers (0: v -> s, 1: w -> t): node, depth
+  uint32_t bt_j[2];          //   and the next Philox block of each
   int cv, cw;     // chosen candidate edge (v on the s side, w on the t side)
   unsigned long long cur;
   unsigned long long ntotal;
-  // weighted radix selection (block_pick_radix)
-  unsigned long long rhist[256];
-  unsigned rcnt[256];
+  // weighted radix selection (block_pick_radix; its histogram lives in the
+  // frontier array, which is free while a candidate edge is chosen)
   unsigned long long rsel_r;
   int rsel_digit;
   unsigned rsel_cnt;
@@ -715,7 +721,8 @@ __device__ __forceinline__ int block_pick_by_key(int n, unsigned long long r, Ct
 // shared histogram once per run of equal bytes: candidates of one tail x are
 // contiguous and sorted by y, so runs are long.  Returns the candidate's
 // index (all threads), or -1 if r is not below the total weight.
-__device__ int block_pick_radix(const PiEntry* buf, int n, unsigned long long r, Ctl& c) {
+__device__ int block_pick_radix(const PiEntry* buf, int n, unsigned long long r, Ctl& c,
+                                unsigned long long* rhist, unsigned* rcnt) {
   const int tid = threadIdx.x, lane = lane_id();
   auto key = [&](int i) { return ((unsigned long long)(uint32_t)buf[i].x << 32) | (uint32_t)buf[i].y; };
   const int chunk = (n + NT - 1) / NT;
@@ -723,8 +730,8 @@ __device__ int block_pick_radix(const PiEntry* buf, int n, unsigned long long r,
   unsigned long long fixed = 0;  // the key bytes above `shift` chosen so far
   for (int shift = 56; shift >= 0; shift -= 8) {
     for (int i = tid; i < 256; i += NT) {
-      c.rhist[i] = 0ull;
-      c.rcnt[i] = 0u;
+      rhist[i] = 0ull;
+      rcnt[i] = 0u;
     }
     __syncthreads();
     int cur = -1;
@@ -736,8 +743,8 @@ __device__ int block_pick_radix(const PiEntry* buf, int n, unsigned long long r,
       const int d = (int)((k >> shift) & 255ull);
       if (d != cur) {
         if (cur >= 0) {
-          atomicAdd(&c.rhist[cur], acc);
-          atomicAdd(&c.rcnt[cur], cnt);
+          atomicAdd(&rhist[cur], acc);
+          atomicAdd(&rcnt[cur], cnt);
         }
         cur = d;
         acc = 0;
@@ -747,14 +754,14 @@ __device__ int block_pick_radix(const PiEntry* buf, int n, unsigned long long r,
       ++cnt;
     }
     if (cur >= 0) {
-      atomicAdd(&c.rhist[cur], acc);
-      atomicAdd(&c.rcnt[cur], cnt);
+      atomicAdd(&rhist[cur], acc);
+      atomicAdd(&rcnt[cur], cnt);
     }
     __syncthreads();
     if (tid < 32) {  // warp 0: the byte whose cumulative weight first exceeds r
       unsigned long long s8 = 0;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) s8 += c.rhist[8 * lane + q];
+      for (int q = 0; q < 8; ++q) s8 += rhist[8 * lane + q];
       unsigned long long incl = s8;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -767,11 +774,11 @@ __device__ int block_pick_radix(const PiEntry* buf, int n, unsigned long long r,
       if (excl <= r && r < incl) {
         unsigned long long below = excl;
         for (int q = 0; q < 8; ++q) {
-          const unsigned long long h = c.rhist[8 * lane + q];
+          const unsigned long long h = rhist[8 * lane + q];
           if (r < below + h) {
             c.rsel_digit = 8 * lane + q;
             c.rsel_r = r - below;
-            c.rsel_cnt = c.rcnt[8 * lane + q];
+            c.rsel_cnt = rcnt[8 * lane + q];
             break;
           }
           below += h;
@@ -796,27 +803,13 @@ __device__ int block_pick_radix(const PiEntry* buf, int n, unsigned long long r,
   return -1;
 }
 
-// All threads of the CTA call this with the same idx.  Flags in c.flags tell
-// the caller what happened; the caller resets the tables afterwards.
-// Backtracking state: after a step reaches depth 0 on one side, continue
-// with w on the t side; half 2 = done.
-__device__ __forceinline__ void bt_normalize(Ctl& c, int dw) {
-  while (c.bt_half < 2 && c.bt_dx == 0) {
-    ++c.bt_half;
-    if (c.bt_half == 1) {
-      c.bt_x = c.cw;
-      c.bt_dx = dw;
-    }
-  }
-}
-
 // Records a backtracking pick y (now at depth dn on side `half`, at position
 // pos of the scanned row): the work counter, its hit (interior nodes only)
 // and its place on the path.  One thread.
 template <bool PK>
 __device__ __forceinline__ void bt_record(const SampleParams& P, const Job& J, Ctl& c, int half, int dn, int y, int pos,
                                           int64_t out_i, int dv, int dw, bool want_path) {
-  c.stat[KADABRA_STAT_BT_SCANNED] += pos + 1;
+  atomicAdd(reinterpret_cast<unsigned long long*>(&c.stat[KADABRA_STAT_BT_SCANNED]), (unsigned long long)(pos + 1));
   if (dn > 0 && J.counts) atomicAdd(&J.counts[y], 1u);
   if (want_path) {
     const int at = half == 0 ? dn : (dv + 1) + (dw - dn);
@@ -829,21 +822,22 @@ __device__ __forceinline__ void bt_record(const SampleParams& P, const Job& J, C
 #endif
 constexpr int WARP_BT_ROW = KD_WARP_BT_ROW;  // rows up to this length: the step stays with warp 0
 
-// Warp 0's backtracking steps, from the state in c.bt_* until the sample's
-// path is complete or a step with more candidates than it takes comes up
-// (left in c.bt_* for the block).  The draw, the candidate order and the
-// pick are those of the block's steps: the first predecessor in row order
-// whose cumulative sigma exceeds r.
+// One warp's backtracking steps for walker `half` (0: from v towards s over
+// predecessors, 1: from w towards t over successors), from its state in
+// c.bt_*[half] until it reaches its root or a step with more candidates than
+// a warp takes comes up (left in c.bt_*[half] for the block).  The draw, the
+// candidate order and the pick are those of the block's steps: the first
+// neighbour one level closer, in row order, whose cumulative sigma exceeds r.
 template <bool PK>
 __device__ void bt_warp_steps(const SampleParams& P, const Job& J, const Tables& T, Ctl& c, uint64_t idx,
-                              int64_t out_i, int dv, int dw, bool want_path) {
+                              int64_t out_i, int dv, int dw, bool want_path, int half) {
   const int lane = lane_id();
   const GraphDev& G = J.g;
-  int half = c.bt_half, x = c.bt_x, dx = c.bt_dx;
-  uint32_t j = c.bt_j;
-  while (half < 2) {
-    const int32_t* brow = half == 0 ? G.rrp : G.rp;
-    const int32_t* bcol = half == 0 ? G.rci : G.ci;
+  int x = c.bt_x[half], dx = c.bt_dx[half];
+  uint32_t j = c.bt_j[half];
+  const int32_t* brow = half == 0 ? G.rrp : G.rp;
+  const int32_t* bcol = half == 0 ? G.rci : G.ci;
+  while (dx > 0) {
     const int plo = lvl_lo(T, half, dx - 1), phi = lvl_hi(T, half, dx - 1);
     const int r0 = __ldg(&brow[x]), deg = __ldg(&brow[x + 1]) - r0;
     const bool single = phi - plo == 1;
@@ -859,7 +853,7 @@ __device__ void bt_warp_steps(const SampleParams& P, const Job& J, const Tables&
     int y = -1, pos = -1;
     if (single) {
       // a single node one level closer: it is x's only predecessor
-      y = T.lnode[plo];
+      y = list_node<PK>(T, plo);
       pos = warp_lower_bound(bcol, r0, r0 + deg, y) - r0;
     } else {
       const uint32_t want = pack_val(half, dx - 1);
@@ -898,19 +892,11 @@ __device__ void bt_warp_steps(const SampleParams& P, const Job& J, const Tables&
     if (lane == 0) bt_record<PK>(P, J, c, half, dx - 1, y, pos, out_i, dv, dw, want_path);
     x = y;
     dx -= 1;
-    while (half < 2 && dx == 0) {
-      ++half;
-      if (half == 1) {
-        x = c.cw;
-        dx = dw;
-      }
-    }
   }
   if (lane == 0) {
-    c.bt_half = half;
-    c.bt_x = x;
-    c.bt_dx = dx;
-    c.bt_j = j;
+    c.bt_x[half] = x;
+    c.bt_dx[half] = dx;
+    c.bt_j[half] = j;
   }
 }
 
@@ -946,9 +932,11 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
       T.hsig[ps] = 1ull;
       T.hsig[pt] = 1ull;
     }
-    T.lnode[0] = s;
+    if (!PK) {
+      T.lnode[0] = s;
+      T.lnode[1] = t;
+    }
     lpos_set<PK>(T, 0, ps);
-    T.lnode[1] = t;
     lpos_set<PK>(T, 1, pt);
     c.nlist = 2;
     lvl_lo(T, 0, 0) = 0;
@@ -990,7 +978,7 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
         const int i = base + tid;
         int deg = 0, rs = 0;
         if (i < cnt) {
-          const int x = T.lnode[fb + i];
+          const int x = list_node<PK>(T, fb + i);
           rs = __ldg(&rowp[x]);
           deg = __ldg(&rowp[x + 1]) - rs;
         }
@@ -1022,23 +1010,26 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
       scan_level<RG>(T, c, cnt, E, cols, [&](int, bool ok, int p, int y) {
         bool touch = false;
         unsigned long long wgt = 0;
+        int32_t xnode = 0;
         if (ok) {
           unsigned long long hy = 0;
           const int pos = tab_probe(T, y, &hy);
           if (pos >= 0 && val_side(ent_val<PK>(hy)) != side) {
             touch = true;
             const uint32_t px = lpos_get<PK>(T, fb + p);
-            const unsigned long long sx = ent_sig<PK>(T, T.hkv[px], px);
+            const unsigned long long hx = T.hkv[px];
+            const unsigned long long sx = ent_sig<PK>(T, hx, px);
             const unsigned long long sy = ent_sig<PK>(T, hy, (uint32_t)pos);
             wgt = sx * sy;
             if (__umul64hi(sx, sy) != 0ull) sigma_of = true;
+            xnode = (int32_t)(hx >> 32);
           }
         }
         const unsigned m = __ballot_sync(FULL, touch);
         if (touch) {
           const int at = npi + __popc(m & ((1u << lane) - 1u));
           if (at < T.pcap) {
-            seg[at].x = T.lnode[fb + p];
+            seg[at].x = xnode;
             seg[at].y = y;
             seg[at].w = wgt;
           }
@@ -1120,7 +1111,7 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
                 cap = true;
                 return;
               }
-              T.lnode[slot] = y;
+              if (!PK) T.lnode[slot] = y;
               lpos_set<PK>(T, slot, pos);
               ++fresh;
               cost += yhi - ylo;
@@ -1246,7 +1237,8 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
       pick = block_pick_by_key(
           total, c.r, c, [&](int i) { return kw[2 * i]; }, [&](int i) { return kw[2 * i + 1]; });
     } else {
-      pick = block_pick_radix(buf, total, c.r, c);
+      // histogram: 256 u64 weights then 256 counts in the frontier array
+      pick = block_pick_radix(buf, total, c.r, c, kw, reinterpret_cast<unsigned*>(kw + 256));
     }
     if (pick < 0) {
       if (tid == 0) c.flags |= F_INTERNAL;
@@ -1292,31 +1284,36 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
       if (dw > 0) atomicAdd(&J.counts[c.cw], 1u);
     }
   }
-  // Steps go one node at a time, v -> s over predecessors (half 0, weights
-  // sigma_s) and w -> t over successors (half 1).  Warp 0 takes the steps
-  // whose candidates are few (a single node one level closer, or a row of up
-  // to WARP_BT_ROW arcs) with warp scans only; a longer step goes to the whole
-  // block.  Both choose the same node with the same draw.  The state between
-  // them (half, node, depth, next draw) lives in c.bt_*.
+  // Steps go one node at a time, v -> s over predecessors (walker 0, weights
+  // sigma_s) and w -> t over successors (walker 1).  The s side takes the
+  // Philox blocks 2 .. dv + 1 and the t side the next dw, so the two walkers
+  // are independent: warp 0 walks the first and warp 1 the second, at the
+  // same time, taking the steps whose candidates are few (a single node one
+  // level closer, or a row of up to WARP_BT_ROW arcs) with warp scans only.
+  // A longer step goes to the whole block.  Both choose the same node with
+  // the same draw.  The state between them (node, depth, next draw) lives in
+  // c.bt_*[walker].
   if (tid == 0) {
-    c.bt_half = 0;
-    c.bt_x = c.cv;
-    c.bt_dx = dv;
-    c.bt_j = 2;
-    bt_normalize(c, dw);
+    c.bt_x[0] = c.cv;
+    c.bt_dx[0] = dv;
+    c.bt_j[0] = 2;
+    c.bt_x[1] = c.cw;
+    c.bt_dx[1] = dw;
+    c.bt_j[1] = 2 + (uint32_t)dv;
   }
   __syncthreads();
   for (;;) {
-    if (wid == 0) bt_warp_steps<PK>(P, J, T, c, idx, out_i, dv, dw, want_path);
+    if (wid < 2) bt_warp_steps<PK>(P, J, T, c, idx, out_i, dv, dw, want_path, wid);
     __syncthreads();
     if (c.bt_flag) {
       if (tid == 0) c.flags |= F_INTERNAL;
       return;
     }
-    if (c.bt_half >= 2) break;
-    // one long step, by the whole block
-    const int half = c.bt_half, x = c.bt_x, dx = c.bt_dx;
-    const uint32_t j = c.bt_j;
+    const int half = c.bt_dx[0] > 0 ? 0 : c.bt_dx[1] > 0 ? 1 : -1;
+    if (half < 0) break;
+    // one long step of that walker, by the whole block
+    const int x = c.bt_x[half], dx = c.bt_dx[half];
+    const uint32_t j = c.bt_j[half];
     // the row of x that holds its neighbours one level closer to the root
     const int32_t* brow = half == 0 ? G.rrp : G.rp;
     const int32_t* bcol = half == 0 ? G.rci : G.ci;
@@ -1326,7 +1323,7 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
     const int plo = lvl_lo(T, half, dx - 1), phi = lvl_hi(T, half, dx - 1);
     const uint32_t want = pack_val(half, dx - 1);
     const int r0 = __ldg(&brow[x]), deg = __ldg(&brow[x + 1]) - r0;
-    __syncthreads();  // every thread has read c.bt_* before thread 0 writes below
+    __syncthreads();  // every thread has read c.bt_*[half] before thread 0 writes below
     if (tid == 0) {
       const int px = tab_find_pos(T, x);
       if (px < 0) {
@@ -1349,7 +1346,7 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
     if (c.mode == 1) {
       // previous-level nodes adjacent to x, collected as (node, hash position)
       for (int i = plo + tid; i < phi; i += NT) {
-        const int y = T.lnode[i];
+        const int y = list_node<PK>(T, i);
         const int a = __ldg(&frow[y]), b = __ldg(&frow[y + 1]);
         const int at = lower_bound_row(fcol, a, b, x);
         if (at < b && __ldg(&fcol[at]) == x) {
@@ -1403,10 +1400,9 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
     }
     if (tid == 0) {
       bt_record<PK>(P, J, c, half, dx - 1, y_pick, pos_pick, out_i, dv, dw, want_path);
-      c.bt_x = y_pick;
-      c.bt_dx = dx - 1;
-      c.bt_j = j + 1;
-      bt_normalize(c, dw);
+      c.bt_x[half] = y_pick;
+      c.bt_dx[half] = dx - 1;
+      c.bt_j[half] = j + 1;
     }
     __syncthreads();
   }
@@ -1477,32 +1473,38 @@ __device__ inline Tables gm_tables(unsigned char* base, int hlog, int lcap, int 
 }
 
 // shared-memory layout of a packed tier with 2^HLOG hash slots and lists of
-// 2^(HLOG-1) nodes, after the control block.  Frontiers hold at most 2048
-// nodes (tier B: two CTAs per SM instead of one); tier S adds the async-copy
-// ring of its level scans.
-template <int HLOG>
+// 2^(HLOG-1) hash positions, after the control block.  A frontier is scanned
+// in segments of at most FRONTIER_SEG nodes (the frontier array's capacity);
+// the async-copy variant (RG) adds the ring of its level scans.
+#ifndef KD_FRONTIER_SEG
+#define KD_FRONTIER_SEG 1024
+#endif
+constexpr int FRONTIER_SEG = KD_FRONTIER_SEG;
+template <int HLOG, bool RG = false>
 struct SLayout {
   static constexpr int LCAP = 1 << (HLOG - 1);
-  static constexpr int FRCAP = LCAP < 2048 ? LCAP : 2048;
-  static constexpr size_t RING_BYTES = HLOG == FAST_HLOG ? sizeof(int) * NW * RING * 32 : 0;
+  static constexpr int FRCAP = LCAP < FRONTIER_SEG ? LCAP : FRONTIER_SEG;
+  static constexpr size_t RING_BYTES = RG ? sizeof(int) * NW * RING * 32 : 0;
   static constexpr size_t HKV = (sizeof(Ctl) + 15) & ~size_t(15);
   static constexpr size_t PR = HKV + (sizeof(unsigned long long) << HLOG);
-  static constexpr size_t LNODE = PR + sizeof(int2) * (FRCAP + 1);
-  static constexpr size_t LPOS = LNODE + sizeof(int32_t) * LCAP;
+  static constexpr size_t LPOS = PR + sizeof(int2) * (FRCAP + 1);
   static constexpr size_t LVL = LPOS + sizeof(uint16_t) * LCAP;
   static constexpr size_t RINGO = (LVL + sizeof(int) * 4 * (FAST_MAXD + 2) + 15) & ~size_t(15);
   static constexpr size_t BYTES = RINGO + RING_BYTES;
   static_assert(HLOG <= 16, "16-bit list positions");
+  // the radix selection's histogram (256 u64 + 256 u32) in the frontier array
+  static_assert(sizeof(int2) * (FRCAP + 1) >= 256 * (sizeof(unsigned long long) + sizeof(unsigned)),
+                "frontier array holds the selection histogram");
 };
 
-template <int HLOG>
+template <int HLOG, bool RG = false>
 __device__ inline Tables smem_tables(unsigned char* smem) {
-  using L = SLayout<HLOG>;
+  using L = SLayout<HLOG, RG>;
   Tables T;
   T.hkv = reinterpret_cast<unsigned long long*>(smem + L::HKV);
   T.hsig = nullptr;  // packed entries
   T.pr = reinterpret_cast<int2*>(smem + L::PR);
-  T.lnode = reinterpret_cast<int32_t*>(smem + L::LNODE);
+  T.lnode = nullptr;  // node ids come from the hash words
   T.lpos = nullptr;
   T.lpos16 = reinterpret_cast<uint16_t*>(smem + L::LPOS);
   T.lvl = reinterpret_cast<int*>(smem + L::LVL);
@@ -1592,13 +1594,14 @@ __device__ void clear_path_row(const SampleParams& P, int64_t out_i) {
 // level scans keep more loads in flight through an async-copy ring (for
 // graphs whose CSR exceeds L2); same results.
 template <int MODE, int SHL = FAST_HLOG, bool RG = false>
-__global__ void __launch_bounds__(NT, SHL == FAST_HLOG ? KD_MIN_BLOCKS : KD_MIN_BLOCKS + 1) k_sample(SampleParams P) {
+__global__ void __launch_bounds__(NT, MODE != 0 ? 2 : SHL == FAST_HLOG ? KD_MIN_BLOCKS : KD_MIN_BLOCKS + 1)
+    k_sample(SampleParams P) {
   static_assert(!RG || (MODE == 0 && SHL == FAST_HLOG), "the async-copy ring is laid out for tier S only");
   extern __shared__ __align__(16) unsigned char smem[];
   Ctl& c = *reinterpret_cast<Ctl*>(smem);
   Tables TS, TM;
   PiEntry* pi = P.pi_base + (size_t)blockIdx.x * 2 * NW * P.pcap;
-  if (MODE == 0) TS = smem_tables<SHL>(smem);
+  if (MODE == 0) TS = smem_tables<SHL, RG>(smem);
   if (MODE == 2) {
     TS = smem_tables<BIG_HLOG>(smem);
     TM = gm_tables(P.med_base + (size_t)blockIdx.x * P.med_stride, MED_HLOG, MED_LCAP, MED_MAXD);
@@ -2127,6 +2130,7 @@ __global__ void __launch_bounds__(32 * WT_WARPS) k_sample_warp(SampleParams P) {
 size_t warp_tier_smem_bytes() { return sizeof(WSlot) * WT_WARPS; }
 
 size_t fast_smem_bytes() { return SLayout<FAST_HLOG>::BYTES; }
+size_t ring_smem_bytes() { return SLayout<FAST_HLOG, true>::BYTES; }
 size_t small_smem_bytes() { return SLayout<SMALL_HLOG>::BYTES; }
 size_t big_smem_bytes() { return SLayout<BIG_HLOG>::BYTES; }
 
@@ -3350,7 +3354,7 @@ kadabra_status ensure_ws(Workspace* w, uint64_t deferred_need, int njobs) {
     w->smem_fast = fast_smem_bytes();
     KCK(cudaFuncSetAttribute(k_sample<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->smem_fast));
     KCK(cudaFuncSetAttribute(k_sample<0, FAST_HLOG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)w->smem_fast));
+                             (int)ring_smem_bytes()));
     int per_sm = 0;
     KCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample<0>, NT, w->smem_fast));
     if (per_sm < 1) return fail(KADABRA_ERR_CAPACITY, "sampler does not fit on an SM");
@@ -3512,7 +3516,7 @@ kadabra_status launch_sampler_kernels(Workspace* w, SampleParams P, cudaStream_t
   if (variant & 1)  // the small table has no ring variant
     k_sample<0, SMALL_HLOG><<<w->grid_small, NT, w->smem_small, st>>>(P);
   else if (rg)
-    k_sample<0, FAST_HLOG, true><<<w->grid_fast, NT, w->smem_fast, st>>>(P);
+    k_sample<0, FAST_HLOG, true><<<w->grid_fast, NT, ring_smem_bytes(), st>>>(P);
   else
     k_sample<0><<<w->grid_fast, NT, w->smem_fast, st>>>(P);
   KCK(cudaGetLastError());

@@ -142,14 +142,14 @@ def test_warp_tier_runs_identical(kd, orc, gg, name, make, lam, k):
     try:
         off = kd.kadabra_run(G, lam, 0.1, k, 3, check_interval=1000, warp_tier=-1)
         on = kd.kadabra_run(G, lam, 0.1, k, 3, check_interval=1000, warp_tier=1)
-        on4 = kd.kadabra_run(G, lam, 0.1, k, 3, check_interval=1000, warp_tier=1, ctas_per_sm=4)
+        on4 = kd.kadabra_run(G, lam, 0.1, k, 3, check_interval=1000, warp_tier=1, ctas_per_sm=5)
         auto = kd.kadabra_run(G, lam, 0.1, k, 3, check_interval=1000)
         with pytest.raises(kd.KadabraError):
             kd.kadabra_run(G, lam, 0.1, k, 3, warp_tier=2)
     finally:
         G.free()
-    assert (off.warp_tier, on.warp_tier, on4.warp_tier, on4.ctas_per_sm) == (0, 1, 1, 4)
-    assert auto.warp_tier in (0, 1) and auto.ctas_per_sm in (3, 4)
+    assert (off.warp_tier, on.warp_tier, on4.warp_tier, on4.ctas_per_sm) == (0, 1, 1, 5)
+    assert auto.warp_tier in (0, 1) and auto.ctas_per_sm in (4, 5)
     for r in (on, on4, auto):
         assert (r.tau, r.checks, r.C, r.max_f, r.max_g) == (off.tau, off.checks, off.C, off.max_f, off.max_g), name
         assert np.array_equal(r.counts, off.counts) and np.array_equal(r.totals, off.totals), name
