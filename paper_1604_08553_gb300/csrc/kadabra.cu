@@ -75,7 +75,7 @@ namespace {
 #define KD_NT 256
 #endif
 #ifndef KD_U
-#define KD_U 2
+#define KD_U 1
 #endif
 #ifndef KD_FAST_HLOG
 #define KD_FAST_HLOG 12
@@ -168,6 +168,7 @@ struct Tables {
   int lcap;
   int frcap;                // frontier nodes per scan segment (the frontier array's capacity)
   int* ring;                // the async-copy scan's per-warp ring (tier S only), else null
+  uint32_t* bits;           // filter of the other side's frontier (shared-memory tiers), else null
   int* lvl;                 // [side][lo|hi][maxd+2]
   int maxd;
   PiEntry* pi;              // 2*NW segments of pcap entries (the second half is scratch)
@@ -244,6 +245,20 @@ __device__ __forceinline__ bool ent_add(const Tables& T, uint32_t pos, unsigned 
 
 __device__ __forceinline__ uint32_t hash_pos(int32_t v, int hlog) {
   return ((uint32_t)v * 2654435761u) >> (32 - hlog);
+}
+
+// A level can touch the other search only at nodes of the other side's
+// current frontier: a node the other side reached earlier was expanded by it
+// before this side reached x, and would have touched then (or claimed x).
+// The shared-memory tiers keep a one-bit-per-slot filter of that frontier
+// (2^FILTER_LOG slots, a different hash than the table's), so that most heads
+// of a scanned arc are rejected by one shared load instead of a probe.
+constexpr int FILTER_LOG = 15;
+constexpr int FILTER_WORDS = (1 << FILTER_LOG) / 32;
+__device__ __forceinline__ uint32_t filter_slot(int32_t v) { return ((uint32_t)v * 0x9E3779B1u) >> (32 - FILTER_LOG); }
+__device__ __forceinline__ bool filter_has(const uint32_t* bits, int32_t v) {
+  const uint32_t h = filter_slot(v);
+  return (bits[h >> 5] >> (h & 31)) & 1u;
 }
 
 // position of v's entry (its word in *wout), or -1
@@ -371,6 +386,7 @@ struct Ctl {
   int nlist;
   int flags;
   int side;
+  int fside, fdepth;  // the frontier the filter in T.bits was built for (fside -1: none)
   int ecount;
   int done;       // 0 = continue, 1 = touch, 2 = disconnected
   int bt_flag;    // backtracking: an invariant failed at this step
@@ -478,6 +494,25 @@ __device__ __forceinline__ int frontier_pos(const int2* pr, int cnt, int e) {
       hi = mid;
   }
   return lo;
+}
+
+// largest p in [a, cnt) with pr[p].x <= e, given pr[a].x <= e < pr[cnt].x:
+// a window of 32 arcs from a row start reaches at most 32 rows further unless
+// rows are empty, so the next 32 rows are searched first
+__device__ __forceinline__ int frontier_next(const int2* pr, int a, int cnt, int e) {
+  int b = min(a + 32, cnt);
+  if (pr[b].x <= e) {
+    a = b;
+    b = cnt;
+  }
+  while (b - a > 1) {
+    const int mid = (a + b) >> 1;
+    if (pr[mid].x <= e)
+      a = mid;
+    else
+      b = mid;
+  }
+  return a;
 }
 
 // first position of y in the sorted row col[a, b) (b if absent)
@@ -595,7 +630,7 @@ __device__ __forceinline__ void scan_level_regs(const Tables& T, int fcount, int
       ys[k] = ps[k] = 0;
       if (wb < c1) {
         if (nxt <= wb) {  // the window starts in a later row
-          pcur = pcur + 1 + frontier_pos(T.pr + pcur + 1, fcount - pcur - 1, wb);
+          pcur = frontier_next(T.pr, pcur + 1, fcount, wb);
           cur = T.pr[pcur];
           nxt = T.pr[pcur + 1].x;
         }
@@ -604,7 +639,7 @@ __device__ __forceinline__ void scan_level_regs(const Tables& T, int fcount, int
           int p = pcur;
           int2 q = cur;
           if (e >= nxt) {
-            p = pcur + 1 + frontier_pos(T.pr + pcur + 1, fcount - pcur - 1, e);
+            p = frontier_next(T.pr, pcur + 1, fcount, e);
             q = T.pr[p];
           }
           ps[k] = p;
@@ -645,14 +680,14 @@ __device__ __forceinline__ void scan_level_ring(const Tables& T, Ctl& c, int fco
     if (w < nwin) {
       const int wb = c0 + 32 * w;
       if (inxt <= wb) {  // the window starts in a later row
-        ip = ip + 1 + frontier_pos(T.pr + ip + 1, fcount - ip - 1, wb);
+        ip = frontier_next(T.pr, ip + 1, fcount, wb);
         icur = T.pr[ip];
         inxt = T.pr[ip + 1].x;
       }
       const int e = wb + lane;
       if (e < c1) {
         int2 q = icur;
-        if (e >= inxt) q = T.pr[ip + 1 + frontier_pos(T.pr + ip + 1, fcount - ip - 1, e)];
+        if (e >= inxt) q = T.pr[frontier_next(T.pr, ip + 1, fcount, e)];
         cp_async4(&ring[(w % RING) * 32 + lane], &cols[q.y + (e - q.x)]);
       }
     }
@@ -666,14 +701,14 @@ __device__ __forceinline__ void scan_level_ring(const Tables& T, Ctl& c, int fco
     cp_async_wait<RING - 1>();  // window w has landed
     const int wb = c0 + 32 * w;
     if (pnxt <= wb) {
-      pp = pp + 1 + frontier_pos(T.pr + pp + 1, fcount - pp - 1, wb);
+      pp = frontier_next(T.pr, pp + 1, fcount, wb);
       pnxt = T.pr[pp + 1].x;
     }
     const int e = wb + lane;
     bool ok = false;
     int p = 0, y = 0;
     if (e < c1) {
-      p = e >= pnxt ? pp + 1 + frontier_pos(T.pr + pp + 1, fcount - pp - 1, e) : pp;
+      p = e >= pnxt ? frontier_next(T.pr, pp + 1, fcount, e) : pp;
       y = ring[(w % RING) * 32 + lane];
       ok = true;
     }
@@ -721,7 +756,7 @@ __device__ __forceinline__ int block_pick_by_key(int n, unsigned long long r, Ct
 // shared histogram once per run of equal bytes: candidates of one tail x are
 // contiguous and sorted by y, so runs are long.  Returns the candidate's
 // index (all threads), or -1 if r is not below the total weight.
-__device__ int block_pick_radix(const PiEntry* buf, int n, unsigned long long r, Ctl& c,
+__device__ __noinline__ int block_pick_radix(const PiEntry* buf, int n, unsigned long long r, Ctl& c,
                                 unsigned long long* rhist, unsigned* rcnt) {
   const int tid = threadIdx.x, lane = lane_id();
   auto key = [&](int i) { return ((unsigned long long)(uint32_t)buf[i].x << 32) | (uint32_t)buf[i].y; };
@@ -945,6 +980,7 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
     lvl_hi(T, 1, 0) = 2;
     c.depth[0] = 0;
     c.depth[1] = 0;
+    c.fside = -1;
     c.cost[0] = G.rp[s + 1] - G.rp[s];
     c.cost[1] = G.rrp[t + 1] - G.rrp[t];
   }
@@ -966,6 +1002,23 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
     }
     const int32_t* rowp = side == 0 ? G.rp : G.rrp;
     const int32_t* cols = side == 0 ? G.ci : G.rci;
+    if constexpr (PK) {
+      // the filter of the other side's frontier, unless it is still current
+      const int os = 1 - side, od = c.depth[os];
+      if (c.fside != os || c.fdepth != od) {
+        for (int i = tid; i < FILTER_WORDS; i += NT) T.bits[i] = 0u;
+        __syncthreads();
+        for (int i = lvl_lo(T, os, od) + tid; i < lvl_hi(T, os, od); i += NT) {
+          const uint32_t h = filter_slot(list_node<PK>(T, i));
+          atomicOr(&T.bits[h >> 5], 1u << (h & 31));
+        }
+        __syncthreads();
+        if (tid == 0) {
+          c.fside = os;
+          c.fdepth = od;
+        }
+      }
+    }
 
     // Degree prefix and row starts over frontier nodes [fb, fb + cnt) into
     // T.pr; returns their arc count (all threads).  A frontier of more than
@@ -1011,7 +1064,7 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
         bool touch = false;
         unsigned long long wgt = 0;
         int32_t xnode = 0;
-        if (ok) {
+        if (ok && (!PK || filter_has(T.bits, y))) {
           unsigned long long hy = 0;
           const int pos = tab_probe(T, y, &hy);
           if (pos >= 0 && val_side(ent_val<PK>(hy)) != side) {
@@ -1468,6 +1521,7 @@ __device__ inline Tables gm_tables(unsigned char* base, int hlog, int lcap, int 
   T.frcap = lcap;
   T.lpos16 = nullptr;
   T.ring = nullptr;
+  T.bits = nullptr;
   T.maxd = maxd;
   return T;
 }
@@ -1489,7 +1543,8 @@ struct SLayout {
   static constexpr size_t PR = HKV + (sizeof(unsigned long long) << HLOG);
   static constexpr size_t LPOS = PR + sizeof(int2) * (FRCAP + 1);
   static constexpr size_t LVL = LPOS + sizeof(uint16_t) * LCAP;
-  static constexpr size_t RINGO = (LVL + sizeof(int) * 4 * (FAST_MAXD + 2) + 15) & ~size_t(15);
+  static constexpr size_t BITS = (LVL + sizeof(int) * 4 * (FAST_MAXD + 2) + 15) & ~size_t(15);
+  static constexpr size_t RINGO = BITS + sizeof(uint32_t) * FILTER_WORDS;
   static constexpr size_t BYTES = RINGO + RING_BYTES;
   static_assert(HLOG <= 16, "16-bit list positions");
   // the radix selection's histogram (256 u64 + 256 u32) in the frontier array
@@ -1509,6 +1564,7 @@ __device__ inline Tables smem_tables(unsigned char* smem) {
   T.lpos16 = reinterpret_cast<uint16_t*>(smem + L::LPOS);
   T.lvl = reinterpret_cast<int*>(smem + L::LVL);
   T.ring = L::RING_BYTES ? reinterpret_cast<int*>(smem + L::RINGO) : nullptr;
+  T.bits = reinterpret_cast<uint32_t*>(smem + L::BITS);
   T.hlog = HLOG;
   T.hmask = (1u << HLOG) - 1u;
   T.lcap = L::LCAP;
@@ -3230,6 +3286,7 @@ struct Workspace {
   int64_t max_m = 0;
   int grid_fast = 0, grid_big = 0, grid_gm = 0, grid_small = 0, grid_warp = 0;
   size_t smem_fast = 0, smem_big = 0, smem_small = 0, smem_warp = 0;
+  int grid_ring = 0;  // the async-copy variant of tier S (its ring costs occupancy)
   unsigned long long* ctr = nullptr;
   int32_t* status = nullptr;
   unsigned long long* qb = nullptr;  // queue for tier B
@@ -3356,6 +3413,8 @@ kadabra_status ensure_ws(Workspace* w, uint64_t deferred_need, int njobs) {
     KCK(cudaFuncSetAttribute(k_sample<0, FAST_HLOG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)ring_smem_bytes()));
     int per_sm = 0;
+    KCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample<0, FAST_HLOG, true>, NT, ring_smem_bytes()));
+    w->grid_ring = w->num_sms * std::max(per_sm, 1);
     KCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample<0>, NT, w->smem_fast));
     if (per_sm < 1) return fail(KADABRA_ERR_CAPACITY, "sampler does not fit on an SM");
     w->grid_fast = w->num_sms * per_sm;
@@ -3516,7 +3575,7 @@ kadabra_status launch_sampler_kernels(Workspace* w, SampleParams P, cudaStream_t
   if (variant & 1)  // the small table has no ring variant
     k_sample<0, SMALL_HLOG><<<w->grid_small, NT, w->smem_small, st>>>(P);
   else if (rg)
-    k_sample<0, FAST_HLOG, true><<<w->grid_fast, NT, ring_smem_bytes(), st>>>(P);
+    k_sample<0, FAST_HLOG, true><<<w->grid_ring, NT, ring_smem_bytes(), st>>>(P);
   else
     k_sample<0><<<w->grid_fast, NT, w->smem_fast, st>>>(P);
   KCK(cudaGetLastError());
