@@ -94,7 +94,8 @@ typedef struct {
                               fingerprint), or one of the two values the library
                               offers (4: 4096-slot tables, 5: 2048-slot on GB300);
                               any other value is KADABRA_ERR_ARG.  Results do not
-                              depend on it.  Batches and serving use the default.  */
+                              depend on it.  A batch run tunes it on its largest
+                              graph; serving uses the default.                    */
   int32_t warp_tier;       /* one-warp-per-sample tier in front of tier S (samples whose
                               search outgrows its 512-slot table go on to tier S):
                               0 = autotuned together with ctas_per_sm, 1 = on,
@@ -190,11 +191,16 @@ kadabra_status kadabra_batch_graph(kadabra_batch* b, int32_t i, kadabra_graph** 
 
 /* KADABRA on every graph of the batch (all-nodes mode), graph i with
  * lambda[i], delta[i], seed[i].  cfg (may be NULL) gives eps, the check
- * interval (0 = per graph from its omega, see kadabra_config) and the
- * stream; cfg->vd must be 0 (each graph uses its own VD bound).  out[i]
- * receives graph i's result (set its buffer pointers as for kadabra_run).
- * Rounds: one sampler launch over the next batch of every unfinished graph,
- * then one stop-test launch over all of them.  Blocking. */
+ * interval (0 = per graph from its omega, see kadabra_config), the sampler
+ * setup (ctas_per_sm, warp_tier; autotuned on the batch's largest graph when
+ * 0) and the stream; cfg->vd must be 0 (each graph uses its own VD bound).
+ * out[i] receives graph i's result (set its buffer pointers as for
+ * kadabra_run).  Rounds: one sampler launch over the next batch of every
+ * unfinished graph, then one stop-test launch over all of them; after the
+ * first round (sampled with the warm-up) the rounds run on the device as a
+ * CUDA graph (a while loop), with one host wait for the rest of the run when
+ * some graph allows more than four rounds.  Results do not depend on the
+ * sampler setup or on where the rounds run.  Blocking. */
 kadabra_status kadabra_run_batch(kadabra_batch* b, const double* lambda, const double* delta, const uint64_t* seed,
                                  const kadabra_config* cfg, kadabra_result* out);
 

@@ -2325,66 +2325,101 @@ __global__ void __launch_bounds__(256) k_check_tab(const CheckTabJob* __restrict
   check_tab_block(jobs[blockIdx.y]);
 }
 
-// Device-driven main loop of one all-nodes run (Alg. 1): a CUDA graph whose
-// while node repeats {next batch of K samples, stop test} with the loop
-// state in device memory, so no host round trip separates the rounds.
+// Device-driven main loop of all-nodes runs (Alg. 1) on G graphs at once: a
+// CUDA graph whose while node repeats {one sampler launch over every
+// unfinished graph's next batch, one stop-test launch over those graphs},
+// with the loop state in device memory, so no host round trip separates the
+// rounds.  Device memory: LoopState, then G LoopGraph, G Job, G CheckTabJob.
 struct LoopState {
-  unsigned long long tau, cap, K, B, checks, total_work;
+  unsigned long long total_work;  // samples of the round over all graphs (the sampler reads it)
+  int G;
+  unsigned arrive;  // blocks of the round's test that have finished
+};
+struct LoopGraph {
+  unsigned long long tau, cap, K, B, checks;
   int64_t n;
-  unsigned stopped, arrive;  // arrive: blocks of the round's test that have finished
+  unsigned stopped, done;
   CheckOut co;
 };
 
-// the next batch's job range, the queue counters, the test's tau (one thread)
-__device__ void loop_begin(LoopState* s, Job* job, unsigned long long* ctr, CheckTabJob* cj) {
-  const unsigned long long rest = s->cap - s->tau;
-  const unsigned long long B = s->K < rest ? s->K : rest;
-  s->B = B;
-  s->total_work = B;
-  job->first_idx = s->tau;
-  job->count = B;
-  job->work_begin = 0;
+__device__ __forceinline__ LoopGraph* loop_graphs(LoopState* s) { return reinterpret_cast<LoopGraph*>(s + 1); }
+__device__ __forceinline__ Job* loop_jobs(LoopState* s) {
+  return reinterpret_cast<Job*>(loop_graphs(s) + s->G);
+}
+__device__ __forceinline__ CheckTabJob* loop_checks(LoopState* s) {
+  return reinterpret_cast<CheckTabJob*>(loop_jobs(s) + s->G);
+}
+
+// the next round's sample ranges, test descriptors and queue counters (one thread)
+__device__ void loop_begin(LoopState* s, unsigned long long* ctr) {
+  LoopGraph* lg = loop_graphs(s);
+  Job* job = loop_jobs(s);
+  CheckTabJob* cj = loop_checks(s);
+  unsigned long long total = 0;
+  for (int i = 0; i < s->G; ++i) {
+    LoopGraph& L = lg[i];
+    job[i].work_begin = total;
+    if (L.done) {
+      L.B = 0ull;
+      job[i].count = 0ull;
+      cj[i].n = 0;
+      continue;
+    }
+    const unsigned long long rest = L.cap - L.tau;
+    const unsigned long long B = L.K < rest ? L.K : rest;
+    L.B = B;
+    job[i].first_idx = L.tau;
+    job[i].count = B;
+    total += B;
+    L.co.max_f_bits = 0ull;
+    L.co.max_g_bits = 0ull;
+    L.co.fail = 0u;
+    cj[i].tau = L.tau + B;
+    cj[i].n = (L.tau + B >= L.cap) ? 0 : L.n;  // no test once ceil(omega) is reached
+  }
+  s->total_work = total;
   for (int q = 0; q < Q_COUNT; ++q) ctr[q] = 0ull;
-  s->co.max_f_bits = 0ull;
-  s->co.max_g_bits = 0ull;
-  s->co.fail = 0u;
-  cj->tau = s->tau + B;
-  cj->n = (s->tau + B >= s->cap) ? 0 : s->n;  // no test once ceil(omega) is reached
 }
 
 // the first round's setup, launched before the loop's graph
-__global__ void k_loop_begin(LoopState* s, Job* job, unsigned long long* ctr, CheckTabJob* cj) {
-  loop_begin(s, job, ctr, cj);
-}
+__global__ void k_loop_begin(LoopState* s, unsigned long long* ctr) { loop_begin(s, ctr); }
 
-// The round's stop test; its last block to finish then closes the round
-// (advance tau, count the test, decide whether to go on) and sets up the
-// next one, so no single-thread kernels separate the rounds.  Each block
-// publishes its test results (atomics) before it signs in on `arrive`.
-__global__ void __launch_bounds__(256) k_loop_check(CheckTabJob* cj, LoopState* s, Job* job,
-                                                    unsigned long long* ctr, const int32_t* status,
+// The round's stop tests (graph blockIdx.y); the last block to finish then
+// closes the round for every graph (advance tau, count the test, decide
+// whether it goes on) and sets up the next one, so no single-thread kernels
+// separate the rounds.  Each block publishes its test results (atomics)
+// before it signs in on `arrive`.
+__global__ void __launch_bounds__(256) k_loop_check(LoopState* s, unsigned long long* ctr, const int32_t* status,
                                                     cudaGraphConditionalHandle h) {
-  check_tab_block(*cj);
+  check_tab_block(loop_checks(s)[blockIdx.y]);
   __shared__ unsigned last;
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(&s->arrive, 1u) == gridDim.x - 1 ? 1u : 0u;
+  if (threadIdx.x == 0) last = atomicAdd(&s->arrive, 1u) == gridDim.x * gridDim.y - 1 ? 1u : 0u;
   __syncthreads();
   if (!last || threadIdx.x != 0) return;
   __threadfence();
   s->arrive = 0u;
-  s->tau += s->B;
-  unsigned keep = 1u;
-  if (s->tau >= s->cap || *(volatile const int32_t*)status != 0) {
-    keep = 0u;
-  } else {
-    s->checks += 1ull;
-    if (!*(volatile const unsigned*)&s->co.fail) {
-      s->stopped = 1u;
-      keep = 0u;
+  LoopGraph* lg = loop_graphs(s);
+  unsigned keep = 0u;
+  for (int i = 0; i < s->G; ++i) {
+    LoopGraph& L = lg[i];
+    if (L.done) continue;
+    L.tau += L.B;
+    if (L.tau >= L.cap) {
+      L.done = 1u;
+      continue;
     }
+    L.checks += 1ull;
+    if (!*(volatile const unsigned*)&L.co.fail) {
+      L.stopped = 1u;
+      L.done = 1u;
+      continue;
+    }
+    keep = 1u;
   }
-  if (keep) loop_begin(s, job, ctr, cj);
+  if (*(volatile const int32_t*)status != 0) keep = 0u;
+  if (keep) loop_begin(s, ctr);
   cudaGraphSetConditional(h, keep);
 }
 
@@ -3279,6 +3314,29 @@ namespace {
 // Sampler workspace: everything a sampler launch needs besides the graph and
 // its outputs.  A standalone graph owns one; the graphs of a batch share the
 // batch's, sized for its largest graph (their calls must not overlap).
+// A device-driven main loop (CUDA graph) and its device state, rebuilt only
+// when the launch parameters it was captured with change.
+struct LoopCache {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap = nullptr;      // capture stream
+  void* dev = nullptr;             // LoopState, G LoopGraph, G Job, G CheckTabJob
+  size_t dev_bytes = 0;
+  std::vector<unsigned char> sig;  // launch parameters the graph was built with
+  void drop_graph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+    sig.clear();
+  }
+  ~LoopCache() {
+    drop_graph();
+    if (cap) cudaStreamDestroy(cap);
+    if (dev) cudaFree(dev);
+  }
+};
+
 struct Workspace {
   bool ready = false;
   int device = 0, num_sms = 0;
@@ -3308,6 +3366,7 @@ struct Workspace {
   int checks_cap = 0;
   void* d_nz = nullptr;  // warm-up count compaction descriptors of runs
   int nz_cap = 0;
+  LoopCache loop;  // device-driven loop of batched runs (one-graph runs keep theirs in the graph object)
   std::vector<void*> allocs;
   ~Workspace() {
     for (void* p : allocs)
@@ -3349,17 +3408,8 @@ struct kadabra_graph {
     TuneTable() { std::memset(v, 0xFF, sizeof(v)); }
   } tier_choice;
   uint64_t fingerprint = 0;          // shape and sampled CSR entries (key of the autotuner's cache)
-  // device-driven main loop of all-nodes runs (a CUDA graph), built on first use
-  cudaGraph_t loop_graph = nullptr;
-  cudaGraphExec_t loop_exec = nullptr;
-  cudaStream_t loop_cap = nullptr;   // capture stream
-  void* loop_dev = nullptr;          // LoopState, Job, CheckTabJob
-  std::vector<unsigned char> loop_sig;  // launch parameters the graph was built with
-  ~kadabra_graph() {
-    if (loop_exec) cudaGraphExecDestroy(loop_exec);
-    if (loop_graph) cudaGraphDestroy(loop_graph);
-    if (loop_cap) cudaStreamDestroy(loop_cap);
-  }
+  // device-driven main loop of one-graph all-nodes runs (a CUDA graph), built on first use
+  LoopCache loop;
   std::vector<void*> allocs;  // CSR copies and run buffers
 };
 
@@ -4242,101 +4292,118 @@ constexpr uint64_t LOOP_GRAPH_MIN_ROUNDS = 4;  // fewer possible rounds: host ro
 // graph, sets the first).  Built once per graph object and
 // rebuilt only when the launch parameters it captured change (workspace
 // buffers that grew, another table tier flag).
-kadabra_status loop_graph_ready(kadabra_graph* g, Workspace* w, const SampleParams& P, int check_blocks,
+kadabra_status loop_graph_ready(LoopCache& L, Workspace* w, const SampleParams& P, int check_blocks, int G,
                                 int variant) {
-  std::vector<unsigned char> sig(sizeof(SampleParams) + 5 * sizeof(int));
+  std::vector<unsigned char> sig(sizeof(SampleParams) + 7 * sizeof(int64_t));
   std::memcpy(sig.data(), &P, sizeof(SampleParams));
-  const int grids[5] = {w->grid_fast, w->grid_big, w->grid_gm, check_blocks, variant};
-  std::memcpy(sig.data() + sizeof(SampleParams), grids, sizeof(grids));
-  if (g->loop_exec && sig == g->loop_sig) return KADABRA_OK;
-  if (g->loop_exec) cudaGraphExecDestroy(g->loop_exec);
-  if (g->loop_graph) cudaGraphDestroy(g->loop_graph);
-  g->loop_exec = nullptr;
-  g->loop_graph = nullptr;
-  if (!g->loop_cap) KCK(cudaStreamCreateWithFlags(&g->loop_cap, cudaStreamNonBlocking));
-  LoopState* d_state = static_cast<LoopState*>(g->loop_dev);
-  Job* d_job = reinterpret_cast<Job*>(d_state + 1);
-  CheckTabJob* d_cj = reinterpret_cast<CheckTabJob*>(d_job + 1);
-  KCK(cudaGraphCreate(&g->loop_graph, 0));
+  const int64_t more[7] = {w->grid_fast, w->grid_big, w->grid_gm, check_blocks, variant, G,
+                           (int64_t)(uintptr_t)L.dev};
+  std::memcpy(sig.data() + sizeof(SampleParams), more, sizeof(more));
+  if (L.exec && sig == L.sig) return KADABRA_OK;
+  L.drop_graph();
+  if (!L.cap) KCK(cudaStreamCreateWithFlags(&L.cap, cudaStreamNonBlocking));
+  LoopState* d_state = static_cast<LoopState*>(L.dev);
+  KCK(cudaGraphCreate(&L.graph, 0));
   cudaGraphConditionalHandle h;
-  KCK(cudaGraphConditionalHandleCreate(&h, g->loop_graph, 1u, cudaGraphCondAssignDefault));
+  KCK(cudaGraphConditionalHandleCreate(&h, L.graph, 1u, cudaGraphCondAssignDefault));
   cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};  // the rest zero
   cp.conditional.handle = h;
   cp.conditional.type = cudaGraphCondTypeWhile;
   cp.conditional.size = 1;
   cudaGraphNode_t node;
-  KCK(cudaGraphAddNode(&node, g->loop_graph, nullptr, nullptr, 0, &cp));
+  KCK(cudaGraphAddNode(&node, L.graph, nullptr, nullptr, 0, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
-  KCK(cudaStreamBeginCaptureToGraph(g->loop_cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  kadabra_status st = launch_sampler_kernels(w, P, g->loop_cap, variant);
-  k_loop_check<<<check_blocks, 256, 0, g->loop_cap>>>(d_cj, d_state, d_job, w->ctr, w->status, h);
+  KCK(cudaStreamBeginCaptureToGraph(L.cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  kadabra_status st = launch_sampler_kernels(w, P, L.cap, variant);
+  k_loop_check<<<dim3(check_blocks, G), 256, 0, L.cap>>>(d_state, w->ctr, w->status, h);
   cudaGraph_t captured = nullptr;
-  const cudaError_t ec = cudaStreamEndCapture(g->loop_cap, &captured);
+  const cudaError_t ec = cudaStreamEndCapture(L.cap, &captured);
   if (st != KADABRA_OK) return st;
   KCK(ec);
   KCK(cudaGetLastError());
-  KCK(cudaGraphInstantiate(&g->loop_exec, g->loop_graph, 0));
-  g->loop_sig = sig;
+  KCK(cudaGraphInstantiate(&L.exec, L.graph, 0));
+  L.sig = sig;
   return KADABRA_OK;
 }
 
-// Runs the main loop of one all-nodes run on the device; returns tau, the
-// number of tests and whether one held.
-// *tau: the samples already taken on entry (a multiple of K), the final tau on
-// return; *co: the last round's test.
-kadabra_status run_loop_graph(kadabra_graph* g, Workspace* w, cudaStream_t st, uint64_t seed, uint64_t cap, uint64_t K,
-                              double omega, double lambda, int variant, uint64_t* tau, uint64_t* checks, int* stopped,
-                              CheckOut* co) {
-  if (!g->loop_dev) {
-    void* p;
-    KTRY(dev_alloc(g->allocs, &p, sizeof(LoopState) + sizeof(Job) + sizeof(CheckTabJob)));
-    g->loop_dev = p;
+// One graph of a device-driven main loop: its state on entry (tau a
+// multiple of K, or done), and on return its final tau, the number of tests
+// the loop ran, whether one held, and the last test's result.
+struct LoopRun {
+  kadabra_graph* g;
+  uint64_t seed, tau, cap, K, checks;
+  double omega, lambda;
+  bool done;
+  int stopped;
+  CheckOut co;
+};
+
+// Runs the main loops of several all-nodes runs on the device until each
+// graph's test holds or it reaches ceil(omega).
+kadabra_status run_loop_graph(LoopCache& L, Workspace* w, cudaStream_t st, std::vector<LoopRun>& R, uint32_t flags,
+                              int variant) {
+  const int G = (int)R.size();
+  const size_t bytes = sizeof(LoopState) + (size_t)G * (sizeof(LoopGraph) + sizeof(Job) + sizeof(CheckTabJob));
+  if (L.dev_bytes < bytes) {
+    KCK(cudaStreamSynchronize(st));
+    L.drop_graph();
+    if (L.dev) cudaFree(L.dev);
+    L.dev = nullptr;
+    L.dev_bytes = 0;
+    KCK(cudaMalloc(&L.dev, bytes));
+    L.dev_bytes = bytes;
   }
-  LoopState* d_state = static_cast<LoopState*>(g->loop_dev);
-  Job* d_job = reinterpret_cast<Job*>(d_state + 1);
-  CheckTabJob* d_cj = reinterpret_cast<CheckTabJob*>(d_job + 1);
-  SampleParams P = ws_params(w, launch_flags(g));
+  LoopState* d_state = static_cast<LoopState*>(L.dev);
+  LoopGraph* d_lg = reinterpret_cast<LoopGraph*>(d_state + 1);
+  Job* d_job = reinterpret_cast<Job*>(d_lg + G);
+  SampleParams P = ws_params(w, flags);
   P.jobs = d_job;
-  P.njobs = 1;
+  P.njobs = G;
   P.total_dev = &d_state->total_work;
-  const int64_t want = 4 * (int64_t)w->num_sms;
-  const int check_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, ((int64_t)g->n + 255) / 256));
-  KTRY(loop_graph_ready(g, w, P, check_blocks, variant));
-  LoopState hs;
-  std::memset(&hs, 0, sizeof(hs));
-  hs.tau = *tau;
-  hs.cap = cap;
-  hs.K = K;
-  hs.n = g->n;
-  Job hj;
-  std::memset(&hj, 0, sizeof(hj));
-  hj.g = graph_dev(g);
-  hj.seed = seed;
-  hj.domain = 0;
-  hj.counts = g->counts;
-  hj.totals = g->totals;
-  CheckTabJob hc;
-  std::memset(&hc, 0, sizeof(hc));
-  hc.counts = g->counts;
-  hc.count0 = g->count0;
-  hc.fail_fast = 1;  // the loop reads only the decision; the run's final test is a full one
-  hc.lnT = g->lntab;
-  hc.n = g->n;
-  hc.omega = omega;
-  hc.lambda = lambda;
-  hc.out = &d_state->co;
-  KCK(cudaMemcpyAsync(d_state, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
-  KCK(cudaMemcpyAsync(d_job, &hj, sizeof(hj), cudaMemcpyHostToDevice, st));
-  KCK(cudaMemcpyAsync(d_cj, &hc, sizeof(hc), cudaMemcpyHostToDevice, st));
-  k_loop_begin<<<1, 1, 0, st>>>(d_state, d_job, w->ctr, d_cj);
+  int64_t max_n = 1;
+  for (const LoopRun& r : R) max_n = std::max<int64_t>(max_n, r.g->n);
+  const int64_t want = (4 * (int64_t)w->num_sms + G - 1) / G;
+  const int check_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (max_n + 255) / 256));
+  KTRY(loop_graph_ready(L, w, P, check_blocks, G, variant));
+  std::vector<unsigned char> host(bytes, 0);
+  LoopState* hs = reinterpret_cast<LoopState*>(host.data());
+  LoopGraph* hl = reinterpret_cast<LoopGraph*>(hs + 1);
+  Job* hj = reinterpret_cast<Job*>(hl + G);
+  CheckTabJob* hc = reinterpret_cast<CheckTabJob*>(hj + G);
+  hs->G = G;
+  for (int i = 0; i < G; ++i) {
+    const LoopRun& r = R[i];
+    hl[i].tau = r.tau;
+    hl[i].cap = r.cap;
+    hl[i].K = r.K;
+    hl[i].n = r.g->n;
+    hl[i].done = r.done ? 1u : 0u;
+    hj[i].g = graph_dev(r.g);
+    hj[i].seed = r.seed;
+    hj[i].domain = 0;
+    hj[i].counts = r.g->counts;
+    hj[i].totals = r.g->totals;
+    hc[i].counts = r.g->counts;
+    hc[i].count0 = r.g->count0;
+    hc[i].fail_fast = 1;  // the loop reads only the decision; a test that holds finds no failure
+    hc[i].lnT = r.g->lntab;
+    hc[i].n = r.g->n;
+    hc[i].omega = r.omega;
+    hc[i].lambda = r.lambda;
+    hc[i].out = &d_lg[i].co;
+  }
+  KCK(cudaMemcpyAsync(L.dev, host.data(), bytes, cudaMemcpyHostToDevice, st));
+  k_loop_begin<<<1, 1, 0, st>>>(d_state, w->ctr);
   KCK(cudaGetLastError());
-  KCK(cudaGraphLaunch(g->loop_exec, st));
-  KCK(cudaMemcpyAsync(&hs, d_state, sizeof(hs), cudaMemcpyDeviceToHost, st));
-  KTRY(read_status(w, st));
-  *tau = hs.tau;
-  *checks = hs.checks;
-  *stopped = (int)hs.stopped;
-  *co = hs.co;
+  KCK(cudaGraphLaunch(L.exec, st));
+  KCK(cudaMemcpyAsync(hl, d_lg, sizeof(LoopGraph) * (size_t)G, cudaMemcpyDeviceToHost, st));
+  KTRY(read_status(w, st));  // synchronises the stream, so hl (host memory that outlives the call) is filled
+  for (int i = 0; i < G; ++i) {
+    R[i].tau = hl[i].tau;
+    R[i].checks = hl[i].checks;
+    R[i].stopped = (int)hl[i].stopped;
+    R[i].co = hl[i].co;
+  }
   return KADABRA_OK;
 }
 
@@ -4417,11 +4484,19 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
     cudaError_t e_ = (call);                                                              \
     if (e_ != cudaSuccess) return fail(KADABRA_ERR_CUDA, cudaGetErrorString(e_));         \
   } while (0)
-  int variant = 0;  // tier-S variant of one-graph runs (several graphs share launches: the default)
-  if (G == 1) {
-    KTRY(tier_variant(gs[0], w, st, cfg.ctas_per_sm, cfg.warp_tier, std::min(S[0].K, S[0].cap), &variant));
-    out[0].ctas_per_sm = variant_ctas_per_sm(w, variant);
-    out[0].warp_tier = variant >> 1;
+  // The tier-S setup of the launches: autotuned on the graph (one-graph
+  // runs), or on the batch's largest graph, whose samples take most of each
+  // shared launch (it changes no result).
+  int variant = 0;
+  {
+    int big = 0;
+    for (int i = 1; i < G; ++i)
+      if (gs[i]->m > gs[big]->m) big = i;
+    KTRY(tier_variant(gs[big], w, st, cfg.ctas_per_sm, cfg.warp_tier, std::min(S[big].K, S[big].cap), &variant));
+    for (int i = 0; i < G; ++i) {
+      out[i].ctas_per_sm = variant_ctas_per_sm(w, variant);
+      out[i].warp_tier = variant >> 1;
+    }
   }
   for (State& s : S) {
     RCK(cudaMemsetAsync(s.g->totals, 0, sizeof(long long) * KADABRA_NSTAT, st));
@@ -4429,6 +4504,11 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
     RCK(cudaMemsetAsync(s.g->counts, 0, sizeof(uint32_t) * s.g->n, st));
   }
   std::vector<Job> jobs;
+  // one graph: its flags; several share the launch: only the warp tier, if
+  // any of them asks for it (it changes no result)
+  uint32_t fl = G == 1 ? launch_flags(gs[0]) : 0;
+  if (G > 1)
+    for (int i = 0; i < G; ++i) fl |= launch_flags(gs[i]) & SHARED_LAUNCH_FLAGS;
   auto launch_jobs = [&]() -> kadabra_status {
     uint64_t work = 0;
     for (Job& j : jobs) {
@@ -4436,11 +4516,6 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
       work += j.count;
     }
     if (work == 0) return KADABRA_OK;
-    // one graph: its flags; several share the launch: only the warp tier,
-    // if any of them asks for it (it changes no result)
-    uint32_t fl = G == 1 ? launch_flags(gs[0]) : 0;
-    if (G > 1)
-      for (int i = 0; i < G; ++i) fl |= launch_flags(gs[i]) & SHARED_LAUNCH_FLAGS;
     SampleParams P = ws_params(w, fl);
     P.total_work = work;
     if (jobs.size() == 1) {
@@ -4471,7 +4546,8 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
   // stop test needs; so the warm-up's short launch does not run on its own.
   // The first round's test runs from the host; a device-driven loop takes
   // the later rounds.
-  const bool loop_on_device = G == 1 && (S[0].cap + S[0].K - 1) / S[0].K > LOOP_GRAPH_MIN_ROUNDS;
+  bool loop_on_device = false;
+  for (const State& s : S) loop_on_device |= (s.cap + s.K - 1) / s.K > LOOP_GRAPH_MIN_ROUNDS;
   jobs.clear();
   for (int i = 0; i < G; ++i) jobs.push_back(make_job(S[i], 1, 0, S[i].alpha, S[i].g->count0, seed[i]));
   for (int i = 0; i < G; ++i) {
@@ -4547,24 +4623,37 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
     RCK(cudaMemcpyAsync(co.data(), d_co, sizeof(CheckOut) * cj.size(), cudaMemcpyDeviceToHost, st));
     return read_status(w, st);
   };
-  // main loop (Alg. 1): on the device for one graph with enough rounds to
-  // repay building its CUDA graph, rounds from the host otherwise (same
-  // results either way)
-  for (;;) {
-    if (loop_on_device && S[0].tau > 0 && !S[0].done) {  // rounds 2, 3, ... on the device
-      uint64_t checks = 0;
-      int stopped = 0;
-      CheckOut lco;
-      KTRY(run_loop_graph(S[0].g, w, st, seed[0], S[0].cap, S[0].K, out[0].omega, lambda[0], variant, &S[0].tau,
-                          &checks, &stopped, &lco));
-      out[0].checks += checks;
-      out[0].stopped_early = stopped;
-      if (stopped) {  // the test that held found no failure, so its maxima are complete
-        std::memcpy(&out[0].max_f, &lco.max_f_bits, sizeof(double));
-        std::memcpy(&out[0].max_g, &lco.max_g_bits, sizeof(double));
-        S[0].have_max = true;
+  // main loop (Alg. 1): after the first round, on the device when some
+  // graph has enough rounds left to repay building the CUDA graph, rounds
+  // from the host otherwise (same results either way)
+  for (bool first = true;; first = false) {
+    bool left = false;
+    for (const State& s : S) left |= !s.done;
+    if (loop_on_device && !first && left) {  // rounds 2, 3, ... on the device
+      std::vector<LoopRun> R(G);
+      for (int i = 0; i < G; ++i) {
+        R[i].g = S[i].g;
+        R[i].seed = seed[i];
+        R[i].tau = S[i].tau;
+        R[i].cap = S[i].cap;
+        R[i].K = S[i].K;
+        R[i].omega = out[i].omega;
+        R[i].lambda = lambda[i];
+        R[i].done = S[i].done;
       }
-      S[0].done = true;
+      KTRY(run_loop_graph(G == 1 ? gs[0]->loop : w->loop, w, st, R, fl, variant));
+      for (int i = 0; i < G; ++i) {
+        if (S[i].done) continue;
+        S[i].tau = R[i].tau;
+        out[i].checks += R[i].checks;
+        out[i].stopped_early = R[i].stopped;
+        if (R[i].stopped) {  // the test that held found no failure, so its maxima are complete
+          std::memcpy(&out[i].max_f, &R[i].co.max_f_bits, sizeof(double));
+          std::memcpy(&out[i].max_g, &R[i].co.max_g_bits, sizeof(double));
+          S[i].have_max = true;
+        }
+        S[i].done = true;
+      }
       break;
     }
     jobs.clear();
