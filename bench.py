@@ -57,14 +57,15 @@ METRIC = "paths/sec & time-to-(lambda,delta) per graph, batched vs plain on GPU;
 WORKLOADS = {
     "chung_lu_1m": dict(family="chung_lu", n=1_000_000, beta=2.5, mean_deg=16.0, max_deg=10_000.0, graph_seed=1,
                         lcc=True, lam=0.005, delta=0.1, check_interval=1 << 16,
-                        sampler_dram_bytes=76_722_944 + 5_625_600 + 46_457_600 + 2_017_792 + 65_536),
+                        sampler_dram_bytes=80_739_328 + 7_304_960 + 46_139_648 + 1_922_560 + 65_792),
     "erdos_renyi_2k": dict(family="erdos_renyi", n=2000, mean_deg=8.0, graph_seed=1, lcc=True, lam=0.01,
                            delta=0.1, check_interval=1000, sampler_dram_bytes=None),
     "rmat_24": dict(family="rmat", scale=24, edge_factor=16, a=0.57, b=0.19, c=0.19, graph_seed=1, lam=0.0025,
                     delta=0.1, check_interval=1 << 16, sampler_dram_bytes=None),
     # the scale-22 graph of the same recipe: the size the ncu counters are captured at
     "rmat_22": dict(family="rmat", scale=22, edge_factor=16, a=0.57, b=0.19, c=0.19, graph_seed=1, lam=0.0025,
-                    delta=0.1, check_interval=1 << 16, sampler_dram_bytes=None),
+                    delta=0.1, check_interval=1 << 16,
+                    sampler_dram_bytes=688_819_712 + 36_917_248 + 495_883_520 + 205_097_472 + 60_928),
     "rmat_24_topk": dict(family="rmat", scale=24, edge_factor=16, a=0.57, b=0.19, c=0.19, graph_seed=1, lam=0.0025,
                          delta=0.1, check_interval=1 << 16, sampler_dram_bytes=None, k=10),
 }
@@ -212,6 +213,18 @@ def sector_bytes(totals, hits):
     tiers cost no L2 or DRAM bytes."""
     t = totals
     return 64 * t[1] + 4 * t[0] + 32 * hits + 4 * t[6] + 64 * t[7]
+
+
+def step_spread(times, results):
+    """Per final tau (the check schedule fixes a few values of tau, and the
+    step time follows it): the median step time and the slowest step over
+    that median."""
+    by = {}
+    for t, r in zip(times, results):
+        by.setdefault(int(r.tau), []).append(1e3 * t)
+    med = {tau: statistics.median(v) for tau, v in by.items()}
+    return {"step_ms_median_by_tau": {str(k): round(v, 3) for k, v in sorted(med.items())},
+            "step_max_over_median": round(max(max(v) / med[k] for k, v in by.items()), 3)}
 
 
 def replica_seed(rank: int, step: int) -> int:
@@ -374,19 +387,17 @@ def make_batched_graphs():
                            range(b["graphs"])))
 
 
-def run_batched(args, kd, rank, world):
-    """Time-to-(lambda, delta) of the whole uneven multi-graph workload: one
-    batched run (all graphs per launch) against the same graphs run one at a
-    time on the same device arena, with identical results required."""
+def batched_vs_plain(kd, graphs, warmup: int, steps: int):
+    """Time-to-(lambda, delta) of the uneven multi-graph workload: one batched
+    run (all graphs per launch) against the same graphs run one at a time on
+    the same device arena, results on the device in both arms and compared
+    after each timed pair (identical per graph: tau and counts)."""
     import torch
     b = BATCHED
-    graphs = make_batched_graphs()
     G = len(graphs)
     B = kd.Batch(graphs)
     lam, delta = [b["lam"]] * G, [b["delta"]] * G
     stream = torch.cuda.current_stream()
-    # results stay on the device in both arms (as in the one-graph workloads);
-    # they are compared on the host after each timed pair
     dc_b = [torch.zeros(g.n, dtype=torch.int32, device="cuda") for g in graphs]
     db_b = [torch.zeros(g.n, dtype=torch.float64, device="cuda") for g in graphs]
     dc_p = [torch.zeros(g.n, dtype=torch.int32, device="cuda") for g in graphs]
@@ -401,11 +412,11 @@ def run_batched(args, kd, rank, world):
                                stream=stream.cuda_stream, d_counts=dc_p[i], d_btilde=db_p[i], want_host=False)
                 for i in range(G)]
 
-    for i in range(args.warmup):
+    for i in range(warmup):
         batched(100 * (i + 1))
         plain(100 * (i + 1))
-    tb, tp, paths = [], [], 0
-    for i in range(args.steps):
+    tb, tp, paths, same = [], [], 0, True
+    for i in range(steps):
         seed0 = 7 + 1000 * i
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -416,28 +427,89 @@ def run_batched(args, kd, rank, world):
         rp = plain(seed0)
         torch.cuda.synchronize()
         tp.append(time.perf_counter() - t0)
-        for i, (x, y) in enumerate(zip(rb, rp)):
-            assert x.tau == y.tau and torch.equal(dc_b[i], dc_p[i]), "batched and plain runs differ"
+        for q, (x, y) in enumerate(zip(rb, rp)):
+            same = same and x.tau == y.tau and bool(torch.equal(dc_b[q], dc_p[q]))
         paths += sum(r.alpha + r.tau for r in rb)
-    value = paths / sum(tb)
+    B.free()
+    return {"graphs": G, "nodes": int(sum(g.n for g in graphs)), "arcs": int(sum(g.m for g in graphs)),
+            "time_to_lambda_delta_batched_ms": [round(1e3 * t, 2) for t in tb],
+            "time_to_lambda_delta_plain_ms": [round(1e3 * t, 2) for t in tp],
+            "batched_speedup": sum(tp) / sum(tb), "paths_per_s_batched": paths / sum(tb),
+            "identical_results": same}
+
+
+def batched_workload_name():
+    b = BATCHED
+    return (f"batched: {b['graphs']} Barabasi-Albert graphs, n log-uniform in [{b['n_lo']}, {b['n_hi']}], "
+            f"m uniform in {{{b['m_lo']}..{b['m_hi']}}}; lambda={b['lam']} delta={b['delta']}; "
+            "check interval max(1024, ceil(omega/32))")
+
+
+def run_batched(args, kd, rank, world):
+    """The batched workload alone: one JSON line whose value is the batched
+    arm's paths/s."""
+    graphs = make_batched_graphs()
+    r = batched_vs_plain(kd, graphs, args.warmup, args.steps)
+    if not r["identical_results"]:
+        raise RuntimeError("batched and plain runs differ")
     if rank == 0:
+        tb = r["time_to_lambda_delta_batched_ms"]
         line = {
-            "metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * sum(tb) / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u64+f64", "data": "synthetic",
+            "metric": METRIC, "value": r["paths_per_s_batched"], "unit": "paths/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sum(tb) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64+f64", "data": "synthetic",
             "config": {
-                "workload": (f"batched: {G} Barabasi-Albert graphs, n log-uniform in [{b['n_lo']}, {b['n_hi']}], "
-                             f"m uniform in {{{b['m_lo']}..{b['m_hi']}}}; lambda={b['lam']} delta={b['delta']}; "
-                             "check interval max(1024, ceil(omega/32))"),
-                "nodes": int(sum(g.n for g in graphs)), "arcs": int(sum(g.m for g in graphs)),
-                "time_to_lambda_delta_batched_ms": [round(1e3 * t, 2) for t in tb],
-                "time_to_lambda_delta_plain_ms": [round(1e3 * t, 2) for t in tp],
-                "batched_speedup": sum(tp) / sum(tb),
+                "workload": batched_workload_name(),
+                "nodes": r["nodes"], "arcs": r["arcs"],
+                "time_to_lambda_delta_batched_ms": tb,
+                "time_to_lambda_delta_plain_ms": r["time_to_lambda_delta_plain_ms"],
+                "batched_speedup": r["batched_speedup"],
                 "results": "identical per graph (tau, counts) in batched and plain runs; results kept on the device",
             },
         }
         print(json.dumps(line), flush=True)
-    B.free()
+
+
+def rmat24_roofline(kd, launches: int = 4):
+    """The HBM-bound configuration's sampler roofline: R-MAT scale 24 (forward
+    and reverse CSR, 2.2 GB, beyond L2), batches of 2^16 main-loop samples
+    timed with CUDA events on the launching stream, algorithmic bytes from
+    the work counters, against the measured HBM copy rate."""
+    import torch
+    global WORKLOAD
+    saved = WORKLOAD
+    WORKLOAD = WORKLOADS["rmat_24"]
+    try:
+        g = make_graph()
+        G = kd.kadabra_load_csr(g)
+        K = WORKLOAD["check_interval"]
+        stream = torch.cuda.current_stream()
+        d_counts = torch.zeros(g.n, dtype=torch.int32, device="cuda")
+        d_tot = torch.zeros(kd.NSTAT, dtype=torch.int64, device="cuda")
+        ts, bs = [], []
+        for i in range(launches + 1):
+            d_counts.zero_()
+            d_tot.zero_()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            kd.kadabra_sample_batch(G, 1, 0, i * K, K, d_counts, d_tot, stream=stream.cuda_stream)
+            ev1.record(stream)
+            ev1.synchronize()
+            kd.kadabra_sync_status(G, stream.cuda_stream)
+            if i == 0:
+                continue
+            ts.append(ev0.elapsed_time(ev1) / 1e3)
+            bs.append(algorithmic_bytes(d_tot.cpu().numpy(), int(d_counts.sum().item())))
+        G.free()
+        peak, src = peaks()
+        t, by = sum(ts) / len(ts), sum(bs) / len(bs)
+        return {"workload": workload_name(), "nodes": int(g.n), "arcs": int(g.m), "bound": "hbm",
+                "achieved": by / t / 1e9, "peak": peak, "unit": "GB/s", "frac": by / t / 1e9 / peak,
+                "traffic": WORKLOAD["sampler_dram_bytes"], "bytes_per_launch": by, "launch_ms": 1e3 * t,
+                "samples_per_launch": K, "paths_per_s": K / t, "peak_source": src}
+    finally:
+        WORKLOAD = saved
 
 
 SERVING = dict(jobs=2000, rate=50.0, graphs=16, n_lo=2_000, n_hi=4_000_000, lams=(0.02, 0.01, 0.005), delta=0.1,
@@ -602,6 +674,8 @@ def main():
     ap.add_argument("--sampler-only", type=int, default=0, metavar="LAUNCHES",
                     help="only time LAUNCHES sampler batches of K samples (for profilers)")
     ap.add_argument("--serve-jobs", type=int, default=0, help="serving workload: jobs (default 2000)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload only: skip the batched-vs-plain and R-MAT 24 roofline measurements")
     ap.add_argument("--workload", default="chung_lu_1m",
                     choices=[*WORKLOADS, "batched", "serving", "edge_exponent"],
                     help="one-graph workload (default chung_lu_1m), or batched: 64 uneven Barabasi-Albert graphs, "
@@ -760,6 +834,14 @@ def main():
     e2e_dt, e2e_paths = reduce_replicas(dist, e2e_dt, e2e_paths, "cuda")
     e2e_value = e2e_paths / e2e_dt
 
+    # the metric's batched-vs-plain comparison and the HBM-bound roofline,
+    # measured on the same box after the timed steps (default workload, N=1)
+    extras = {}
+    if world == 1 and args.workload == "chung_lu_1m" and not args.no_extras:
+        extras["batched_vs_plain"] = batched_vs_plain(kd, make_batched_graphs(), 1, 3)
+        extras["batched_vs_plain"]["workload"] = batched_workload_name()
+        extras["roofline_rmat_24"] = rmat24_roofline(kd)
+
     cpu = cpu_multi = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(g)
@@ -789,6 +871,7 @@ def main():
                 "tau": [int(r.tau) for r in results], "alpha": int(r0.alpha), "omega": r0.omega,
                 **({"k": w["k"], "topk_first_step": [int(x) for x in r0.topk]} if w.get("k") else {}),
                 "checks": [int(r.checks) for r in results],
+                **step_spread(times, results),
                 "edges_per_s": edges / total if world == 1 else None,
                 "edges_per_sample": float(tot_np[0]) / K,
             }),
@@ -807,6 +890,7 @@ def main():
             line["cpu_baseline_multicore"] = cpu_multi
         if roof_l2:
             line["roofline_l2"] = roof_l2
+        line.update(extras)
         print(json.dumps(line), flush=True)
     G.free()
     if dist is not None:

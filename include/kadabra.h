@@ -321,8 +321,9 @@ kadabra_status kadabra_sample_batch(kadabra_graph* g, uint64_t seed, uint32_t do
  * counters), from a CSR the caller already holds on the device (the arrays
  * of kadabra_load_csr_device, assumed valid: this call does not check them).
  * The library's scratch for this call is one file-scope device array of
- * about 21 MiB, which every GPU that loads the library holds until the
- * process exits.  Limits:
+ * about 41 MiB (candidate-edge buffers for up to 608 CTAs, 4 per SM on a
+ * 152-SM GPU, and two queues of 65536 entries), which every GPU that loads
+ * the library holds until the process exits.  Limits:
  *   - count <= 65536 samples per call (larger counts: KADABRA_ERR_CAPACITY);
  *   - only the two shared-memory table tiers are used: if any sample's
  *     visited set outgrows them (more than 4096 nodes before the touching

@@ -5677,7 +5677,7 @@ void reset_result(kadabra_result* r) {
 // A variant of the sampler batch for callers that cannot allocate device
 // memory.  Its scratch is one file-scope device array; see the ABI comment of
 // kadabra_sample_batch_noalloc for the limits.
-constexpr int NA_MAX_CTAS = 304;              // main-grid CTAs at most
+constexpr int NA_MAX_CTAS = 608;              // CTAs per launch at most (4 per SM on 152 SMs, as the main path)
 constexpr int NA_PCAP = 256;                  // candidate edges per warp
 constexpr uint64_t NA_MAX_BATCH = 65536;      // samples per call
 constexpr size_t NA_OFF_CTR = 0;              // Q_COUNT counters, then the status word

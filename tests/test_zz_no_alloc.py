@@ -75,3 +75,34 @@ def test_noalloc_rejects_oversized_batches(kd, gg):
         kd.kadabra_sample_batch_noalloc(g.n, rp, ci, 1, 0, 0, 65537, c)
     assert e.value.status == kd.ERR_CAPACITY
     assert int(c.sum().item()) == 0
+
+
+def test_noalloc_capacity_error_then_recovers(kd, gg):
+    """A batch whose samples outgrow both shared-memory tiers (a path of 1500
+    nodes: searches deeper than the 126 levels a shared table holds per side)
+    is refused with KADABRA_ERR_CAPACITY; the next call, on an ordinary graph,
+    starts from a cleared scratch header and equals kadabra_sample_batch
+    again."""
+    path = gg.path_graph(1500)
+    with pytest.raises(kd.KadabraError) as e:
+        _noalloc(kd, path, 3, 0, 0, 4096)
+    assert e.value.status == kd.ERR_CAPACITY
+    g = gg.erdos_renyi(2000, 8.0, 1)
+    c_new, t_new = _noalloc(kd, g, 4, 0, 0, 8192)
+    c_ref, t_ref = _reference(kd, g, 4, 0, 0, 8192)
+    assert np.array_equal(c_new, c_ref)
+    assert np.array_equal(t_new, t_ref)
+
+
+def test_noalloc_without_totals(kd, gg):
+    """d_totals may be NULL: the hit counts are the same."""
+    import torch
+    g = gg.rmat(12, 8, 0.57, 0.19, 0.19, 10)
+    rp = torch.from_numpy(np.ascontiguousarray(g.row_ptr)).cuda()
+    ci = torch.from_numpy(np.ascontiguousarray(g.col)).cuda()
+    rrp = torch.from_numpy(np.ascontiguousarray(g.rrow_ptr)).cuda()
+    rci = torch.from_numpy(np.ascontiguousarray(g.rcol)).cuda()
+    c = torch.zeros(g.n, dtype=torch.int32, device="cuda")
+    kd.kadabra_sample_batch_noalloc(g.n, rp, ci, 5, 0, 100, 20_000, c, None, directed=True, rrow_ptr=rrp, rcol=rci)
+    c_ref, _ = _reference(kd, g, 5, 0, 100, 20_000)
+    assert np.array_equal(c.cpu().numpy(), c_ref)
