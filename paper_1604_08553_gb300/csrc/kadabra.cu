@@ -97,7 +97,10 @@ constexpr int RING = 4;            // arc windows in flight per warp in the leve
 constexpr int FAST_HLOG = KD_FAST_HLOG;        // tier S: 2^FAST_HLOG hash slots
 constexpr int BIG_HLOG = FAST_HLOG + 1;        // tier B: twice as many
 constexpr int SMALL_HLOG = FAST_HLOG - 1;      // tier S, small variant: half the slots, one more CTA per SM
-constexpr int FAST_MAXD = 126;     // levels per side in shared memory (the packed entry's dist field)
+#ifndef KD_FAST_MAXD
+#define KD_FAST_MAXD 126
+#endif
+constexpr int FAST_MAXD = KD_FAST_MAXD;  // levels per side in shared memory (at most 126: the packed entry's dist field)
 constexpr int MED_HLOG = 15;       // tier M, global memory per CTA: 32768 hash slots
 constexpr int MED_LCAP = 16384;    //   level lists: 16384 nodes
 constexpr int MED_MAXD = 1022;     //   levels per side
@@ -253,7 +256,10 @@ __device__ __forceinline__ uint32_t hash_pos(int32_t v, int hlog) {
 // The shared-memory tiers keep a one-bit-per-slot filter of that frontier
 // (2^FILTER_LOG slots, a different hash than the table's), so that most heads
 // of a scanned arc are rejected by one shared load instead of a probe.
-constexpr int FILTER_LOG = 15;
+#ifndef KD_FILTER_LOG
+#define KD_FILTER_LOG 15
+#endif
+constexpr int FILTER_LOG = KD_FILTER_LOG;
 constexpr int FILTER_WORDS = (1 << FILTER_LOG) / 32;
 __device__ __forceinline__ uint32_t filter_slot(int32_t v) { return ((uint32_t)v * 0x9E3779B1u) >> (32 - FILTER_LOG); }
 __device__ __forceinline__ bool filter_has(const uint32_t* bits, int32_t v) {
@@ -1527,16 +1533,22 @@ __device__ inline Tables gm_tables(unsigned char* base, int hlog, int lcap, int 
 }
 
 // shared-memory layout of a packed tier with 2^HLOG hash slots and lists of
-// 2^(HLOG-1) hash positions, after the control block.  A frontier is scanned
+// 3/4 * 2^HLOG hash positions, after the control block.  A frontier is scanned
 // in segments of at most FRONTIER_SEG nodes (the frontier array's capacity);
 // the async-copy variant (RG) adds the ring of its level scans.
 #ifndef KD_FRONTIER_SEG
 #define KD_FRONTIER_SEG 1024
 #endif
 constexpr int FRONTIER_SEG = KD_FRONTIER_SEG;
+#ifndef KD_LOAD_QUARTERS
+#define KD_LOAD_QUARTERS 3
+#endif
 template <int HLOG, bool RG = false>
 struct SLayout {
-  static constexpr int LCAP = 1 << (HLOG - 1);
+  // nodes a table takes before the sample moves on to the next tier:
+  // KD_LOAD_QUARTERS quarters of the slots (the probes stay short)
+  static constexpr int LCAP = (KD_LOAD_QUARTERS << HLOG) / 4;
+  static_assert(LCAP + NT < (1 << HLOG), "a full list leaves free slots");
   static constexpr int FRCAP = LCAP < FRONTIER_SEG ? LCAP : FRONTIER_SEG;
   static constexpr size_t RING_BYTES = RG ? sizeof(int) * NW * RING * 32 : 0;
   static constexpr size_t HKV = (sizeof(Ctl) + 15) & ~size_t(15);
