@@ -321,14 +321,16 @@ kadabra_status kadabra_sample_batch(kadabra_graph* g, uint64_t seed, uint32_t do
  * counters), from a CSR the caller already holds on the device (the arrays
  * of kadabra_load_csr_device, assumed valid: this call does not check them).
  * The library's scratch for this call is one file-scope device array of
- * about 41 MiB (candidate-edge buffers for up to 608 CTAs, 4 per SM on a
- * 152-SM GPU, and two queues of 65536 entries), which every GPU that loads
- * the library holds until the process exits.  Limits:
+ * 63.5 MiB (candidate-edge buffers for up to 304 CTAs, 2 per SM on a 152-SM
+ * GPU, 512 edges per warp; 32 medium hash tables in global memory; two
+ * queues of 65536 entries), which every GPU that loads the library holds
+ * until the process exits.  Limits:
  *   - count <= 65536 samples per call (larger counts: KADABRA_ERR_CAPACITY);
- *   - only the two shared-memory table tiers are used: if any sample's
- *     visited set outgrows them (more than 4096 nodes before the touching
- *     level, or more than 256 candidate edges found by one warp), the call
- *     returns KADABRA_ERR_CAPACITY and its counts are incomplete.
+ *   - the shared-memory tiers and one global-memory tier are used (no
+ *     n-sized tables): if any sample outgrows them (more than 16384 nodes
+ *     before the touching level, more than 1022 levels per side, or more
+ *     than 512 candidate edges found by one warp), the call returns
+ *     KADABRA_ERR_CAPACITY and its counts are incomplete.
  * The first call on a device sets that device up (kernel attributes and the
  * scratch array's device address); make that first call before any stream
  * capture.  Every call shares the one scratch array, which keeps the last

@@ -5689,8 +5689,15 @@ void reset_result(kadabra_result* r) {
 // A variant of the sampler batch for callers that cannot allocate device
 // memory.  Its scratch is one file-scope device array; see the ABI comment of
 // kadabra_sample_batch_noalloc for the limits.
-constexpr int NA_MAX_CTAS = 608;              // CTAs per launch at most (4 per SM on 152 SMs, as the main path)
-constexpr int NA_PCAP = 256;                  // candidate edges per warp
+#ifndef KD_NA_MAX_CTAS
+#define KD_NA_MAX_CTAS 304
+#endif
+#ifndef KD_NA_PCAP
+#define KD_NA_PCAP 512
+#endif
+constexpr int NA_MAX_CTAS = KD_NA_MAX_CTAS;   // CTAs per launch at most (2 per SM on 152 SMs)
+constexpr int NA_PCAP = KD_NA_PCAP;           // candidate edges per warp
+constexpr int NA_MED_CTAS = 32;               // CTAs of the large-table launch (each with one tier-M table)
 constexpr uint64_t NA_MAX_BATCH = 65536;      // samples per call
 constexpr size_t NA_OFF_CTR = 0;              // Q_COUNT counters, then the status word
 constexpr size_t NA_OFF_STATUS = sizeof(unsigned long long) * Q_COUNT;
@@ -5698,7 +5705,13 @@ constexpr size_t NA_HEADER = 256;             // cleared on every call
 constexpr size_t NA_OFF_QB = NA_HEADER;
 constexpr size_t NA_OFF_QL = NA_OFF_QB + sizeof(unsigned long long) * NA_MAX_BATCH;
 constexpr size_t NA_OFF_PI = NA_OFF_QL + sizeof(unsigned long long) * NA_MAX_BATCH;
-constexpr size_t NA_BYTES = NA_OFF_PI + sizeof(PiEntry) * (size_t)NA_MAX_CTAS * 2 * NW * NA_PCAP;
+constexpr size_t NA_OFF_MED = NA_OFF_PI + sizeof(PiEntry) * (size_t)NA_MAX_CTAS * 2 * NW * NA_PCAP;
+// one tier-M table (gm_layout of MED_HLOG, MED_LCAP, MED_MAXD), 256-byte aligned
+constexpr size_t NA_MED_STRIDE =
+    ((((2 * sizeof(unsigned long long)) << MED_HLOG) + sizeof(int2) * ((size_t)MED_LCAP + 1) +
+      sizeof(int32_t) * (size_t)MED_LCAP + sizeof(uint32_t) * (size_t)MED_LCAP + sizeof(int) * 4 * (size_t)(MED_MAXD + 2)) +
+     255) & ~size_t(255);
+constexpr size_t NA_BYTES = NA_OFF_MED + NA_MED_STRIDE * NA_MED_CTAS;
 static_assert(NA_OFF_STATUS + sizeof(int32_t) <= NA_HEADER, "no-alloc header");
 
 // Shared by every call on a device; the host never names it directly except
@@ -5733,12 +5746,23 @@ kadabra_status noalloc_setup(int dev, NoAllocDevice** out) {
     d.grid_s = std::min(sms * per_sm, NA_MAX_CTAS);
     KCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample<2>, NT, d.smem_b));
     if (per_sm < 1) return fail(KADABRA_ERR_CAPACITY, "large-table sampler does not fit on an SM");
-    d.grid_b = std::min(sms * per_sm, NA_MAX_CTAS);
+    d.grid_b = std::min(sms * per_sm, NA_MED_CTAS);
     void* ptr = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
     if (e != cudaSuccess || ptr == nullptr)
       return fail(KADABRA_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
     d.scratch = static_cast<unsigned char*>(ptr);
+    {
+      size_t a, b, c2, e2;
+      if (gm_layout(MED_HLOG, MED_LCAP, MED_MAXD, &a, &b, &c2, &e2) != NA_MED_STRIDE)
+        return fail(KADABRA_ERR_INTERNAL, "tier-M table layout");
+    }
+    // the tier-M tables start empty (every key word EMPTY, sigma 0); each
+    // sample clears what it used, so they stay so from call to call
+    KCK(cudaMemset(d.scratch + NA_OFF_MED, 0, NA_MED_STRIDE * NA_MED_CTAS));
+    for (int b = 0; b < NA_MED_CTAS; ++b)
+      KCK(cudaMemset(d.scratch + NA_OFF_MED + (size_t)b * NA_MED_STRIDE, 0xFF, sizeof(unsigned long long) << MED_HLOG));
+    KCK(cudaDeviceSynchronize());
     d.ready = true;
   }
   *out = &d;
@@ -6119,7 +6143,9 @@ kadabra_status kadabra_sample_batch_noalloc(int32_t n, int64_t m, const int32_t*
   P.deferred_cap = NA_MAX_BATCH;
   P.pi_base = reinterpret_cast<PiEntry*>(d->scratch + NA_OFF_PI);
   P.pcap = NA_PCAP;
-  P.tier_flags = TF_SKIP_M;  // no global tables: only the two shared-memory tiers
+  P.med_base = d->scratch + NA_OFF_MED;  // tier M for the large-table launch's CTAs
+  P.med_stride = NA_MED_STRIDE;
+  P.tier_flags = 0;  // tiers S, B and M; samples beyond tier M end the call with KADABRA_ERR_CAPACITY
   KCK(cudaMemsetAsync(d->scratch, 0, NA_HEADER, st));
   k_sample<0><<<d->grid_s, NT, d->smem_s, st>>>(P);
   KCK(cudaGetLastError());
@@ -6136,7 +6162,7 @@ kadabra_status kadabra_sample_batch_noalloc(int32_t n, int64_t m, const int32_t*
                                             : "the sampler reported a capacity or internal error");
   if (left != 0)
     return fail(KADABRA_ERR_CAPACITY, std::to_string(left) +
-                                          " samples outgrew the shared-memory tables and were not counted; "
+                                          " samples outgrew the tables of this call and were not counted; "
                                           "use kadabra_sample_batch for this graph");
   return KADABRA_OK;
 }

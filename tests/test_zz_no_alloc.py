@@ -53,8 +53,12 @@ def _noalloc(kd, g, seed, domain, first, count):
 
 
 def test_noalloc_matches_sample_batch_twice(kd, gg):
+    # the Chung-Lu graph and the path send samples on to the global-memory
+    # tier of the call (larger or deeper searches than the shared tables hold;
+    # on a path equal costs expand the s side, so its search runs up to 899
+    # levels deep)
     graphs = [gg.erdos_renyi(2000, 8.0, 1), gg.rmat(12, 8, 0.57, 0.19, 0.19, 10),
-              gg.chung_lu(100_000, 2.5, 16.0, 2_000.0, 3)]
+              gg.chung_lu(100_000, 2.5, 16.0, 2_000.0, 3), gg.path_graph(900)]
     for g in graphs:
         calls = [(1, 0, 0, 20_000), (2, 1, 777, 20_000)]  # two calls in a row on the shared scratch
         for seed, domain, first, count in calls:
@@ -78,12 +82,12 @@ def test_noalloc_rejects_oversized_batches(kd, gg):
 
 
 def test_noalloc_capacity_error_then_recovers(kd, gg):
-    """A batch whose samples outgrow both shared-memory tiers (a path of 1500
-    nodes: searches deeper than the 126 levels a shared table holds per side)
+    """A batch whose samples outgrow every table of the call (a path of 6000
+    nodes: s-side searches deeper than the 1022 levels of the largest one)
     is refused with KADABRA_ERR_CAPACITY; the next call, on an ordinary graph,
     starts from a cleared scratch header and equals kadabra_sample_batch
     again."""
-    path = gg.path_graph(1500)
+    path = gg.path_graph(6000)
     with pytest.raises(kd.KadabraError) as e:
         _noalloc(kd, path, 3, 0, 0, 4096)
     assert e.value.status == kd.ERR_CAPACITY
