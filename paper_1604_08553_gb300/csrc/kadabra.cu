@@ -27,11 +27,16 @@
 //     integer atomics.
 //   * Both searches' visited sets share one open-addressing hash table in
 //     shared memory, one packed 64-bit word per node (node | side | depth |
-//     sigma); level lists hold node ids and 16-bit hash positions.
+//     sigma); level lists hold 16-bit hash positions (the node id is in the
+//     hash word).  Four CTAs of 256 threads fit per SM.
 //   * Every level runs pass 1 (touch test against the other search; most
-//     arcs lie in the touching level, which only reads the table), and only
-//     a level that does not touch runs pass 2 (first discoverers insert with
-//     a CAS, every discoverer adds its sigma atomically).
+//     arcs lie in the touching level, which only reads the table, and a bit
+//     filter of the other side's frontier rejects most heads before the
+//     probe), and only a level that does not touch runs pass 2 (first
+//     discoverers insert with a CAS, every discoverer adds its sigma
+//     atomically).
+//   * The two backtracking walks (v -> s, w -> t) take disjoint Philox
+//     blocks, so two warps walk them at the same time.
 //   * Each warp scans a contiguous slice of the level's flattened arc range,
 //     in registers or, for graphs beyond the L2, through an async-copy ring.
 //     Candidate edges are chosen in (x, y) order without a sort (quadratic
@@ -86,9 +91,12 @@ namespace {
 constexpr int NT = KD_NT;          // threads per sampler CTA
 constexpr int NW = NT / 32;        // warps per sampler CTA
 constexpr int U = KD_U;            // independent items per thread per step (memory-level parallelism)
-constexpr int RING = 4;            // arc windows in flight per warp in the level scans (async copies)
+#ifndef KD_RING
+#define KD_RING 2
+#endif
+constexpr int RING = KD_RING;      // arc windows in flight per warp in the level scans (async copies)
 // Tiers of per-sample tables.  A sample starts in a small shared-memory
-// table (tier S, main launch, three or four CTAs per SM; optionally tier W,
+// table (tier S, main launch, four or five CTAs per SM; optionally tier W,
 // one warp per sample, before it).  If it outgrows it, it is queued for a
 // second launch with two CTAs per SM and a large shared-memory table (tier
 // B); beyond that the same CTA retries it on medium global tables (tier M),
@@ -3171,26 +3179,44 @@ __global__ void k_vd_assign(const int32_t* col, const int32_t* reach, int32_t n,
   VD_FOR_NODES(v) if (lab[v] < 0 && reach[v]) lab[v] = col[v];
 }
 
-// component sizes, and the arcs entering each component from another
+// component sizes, and the arcs entering each component from another.  The
+// lanes of a warp that add to the same label add once (most nodes and most
+// entering arcs of a directed power-law graph belong to the root's label).
 __global__ void k_vd_sizes(const int32_t* lab, int32_t n, int32_t* sz) {
-  VD_FOR_NODES(v) atomicAdd(&sz[lab[v]], 1);
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = base + threadIdx.x;
+    const int32_t L = v < n ? lab[v] : -1;
+    const unsigned same = __match_any_sync(FULL, L);
+    if (L >= 0 && lane_id() == __ffs(same) - 1) atomicAdd(&sz[L], __popc(same));
+  }
 }
 
 __global__ void k_vd_indeg(const int32_t* rp, const int32_t* ci, int32_t n, int64_t m, const int32_t* lab,
                            int32_t* cnt) {
+  // each thread counts a run of arcs into one label before it adds
+  int32_t cur = -1, k = 0;
   for_each_arc(rp, ci, n, m, [&](int32_t u, int64_t, int32_t v) {
     const int32_t lv = lab[v];
-    if (lab[u] != lv) atomicAdd(&cnt[lv], 1);
+    if (lab[u] == lv) return;
+    if (lv != cur) {
+      if (k) atomicAdd(&cnt[cur], k);
+      cur = lv;
+      k = 0;
+    }
+    ++k;
   });
+  if (k) atomicAdd(&cnt[cur], k);
 }
 
 // The heaviest path of the condensation, level by level in topological order
 // (Kahn): a component is ready once every arc entering it has been
 // processed; its heaviest path ending in it weighs w + best[label].
 // Single-node components join the node frontier; a larger component ready at
-// level l is marked rdy[label] = l and its nodes are found by a pass over
-// all nodes at that level.  slot[0] of level l: the next frontier's size;
-// slot[1]: a larger component is ready at level l + 1.
+// level l is marked rdy[label] = l, and at that level a pass over all arcs
+// (balanced, whatever the rows' lengths) takes its nodes' arcs.  slot[0] of
+// level l: the next frontier's size; slot[1]: a larger component is ready at
+// level l + 1.
+
 struct VdKahn {
   const int32_t *rp, *ci, *lab, *sz;
   int32_t* cnt;
@@ -3239,24 +3265,28 @@ __device__ void vd_kahn_node(const VdKahn& K, int32_t u, int32_t level, int32_t*
   const int lane = lane_id();
   const int32_t L = K.lab[u];
   const long long w = vd_weight(K, L) + K.best[L];
-  if (lane == 0) atomicMax(K.vd, w);
+  if (lane == 0 && L == u) atomicMax(K.vd, w);  // once per component: its representative
   const int32_t a = K.rp[u], b = K.rp[u + 1];
   for (int32_t base = a; base < b; base += 32) {
     const int32_t e = base + lane;
     bool push = false;
     int32_t y = 0;
+    int32_t Ly = L;  // this lane's arc enters no other component unless set below
     if (e < b) {
       y = K.ci[e];
-      const int32_t Ly = K.lab[y];
-      if (Ly != L) {
-        atomicMax(&K.best[Ly], w);
-        if (atomicSub(&K.cnt[Ly], 1) == 1) {
-          if (K.sz[Ly] == 1) {
-            push = true;
-          } else {
-            K.rdy[Ly] = level + 1;
-            slot[1] = 1;
-          }
+      Ly = K.lab[y];
+    }
+    // lanes whose arcs enter the same component update it once
+    const unsigned same = __match_any_sync(FULL, Ly);
+    if (Ly != L && lane == __ffs(same) - 1) {
+      atomicMax(&K.best[Ly], w);
+      const int k = __popc(same);
+      if (atomicSub(&K.cnt[Ly], k) == k) {
+        if (K.sz[Ly] == 1) {
+          push = true;  // a single-node component: its node is y (only one arc can enter it last)
+        } else {
+          K.rdy[Ly] = level + 1;
+          slot[1] = 1;
         }
       }
     }
@@ -3270,29 +3300,49 @@ __device__ void vd_kahn_node(const VdKahn& K, int32_t u, int32_t level, int32_t*
   }
 }
 
-__global__ void k_vd_kahn_level(VdKahn K, const int32_t* front, const int32_t* prev, int32_t* next, int32_t* slot,
-                                int32_t level) {
+// an arc u -> y of a component that is ready (path weight w to its end)
+__device__ __forceinline__ void vd_kahn_arc(const VdKahn& K, int32_t L, long long w, int32_t y, int32_t level,
+                                            int32_t* next, int32_t* slot) {
+  const int32_t Ly = K.lab[y];
+  if (Ly == L) return;
+  atomicMax(&K.best[Ly], w);
+  if (atomicSub(&K.cnt[Ly], 1) == 1) {
+    if (K.sz[Ly] == 1) {
+      next[atomicAdd(&slot[0], 1)] = y;
+    } else {
+      K.rdy[Ly] = level + 1;
+      slot[1] = 1;
+    }
+  }
+}
+
+__global__ void k_vd_kahn_level(VdKahn K, int64_t m, const int32_t* front, const int32_t* prev, int32_t* next,
+                                int32_t* slot, int32_t level) {
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int32_t nfront = prev[0];
   for (int64_t i = w0; i < nfront; i += nwarps) vd_kahn_node(K, front[i], level, next, slot);
   if (!prev[1]) return;
-  // larger components ready at this level: their nodes, 32 ids per warp step
-  const int lane = lane_id();
-  for (int64_t base = w0 * 32; base < K.n; base += nwarps * 32) {
-    const int64_t v = base + lane;
-    bool mine = false;
-    if (v < K.n) {
-      const int32_t L = K.lab[v];
-      mine = K.sz[L] > 1 && K.rdy[L] == level;
-    }
-    unsigned got = __ballot_sync(FULL, mine);
-    while (got) {
-      const int q = __ffs(got) - 1;
-      got &= got - 1;
-      vd_kahn_node(K, (int32_t)(base + q), level, next, slot);
-    }
+  // larger components ready at this level: their representatives' path
+  // weights, then every arc leaving one of their nodes
+  const int32_t n = K.n;
+  VD_FOR_NODES(v) {
+    const int32_t L = K.lab[v];
+    if (L == (int32_t)v && K.sz[L] > 1 && K.rdy[L] == level) atomicMax(K.vd, vd_weight(K, L) + K.best[L]);
   }
+  int32_t cu = -1;
+  bool on = false;
+  int32_t L = 0;
+  long long w = 0;
+  for_each_arc(K.rp, K.ci, n, m, [&](int32_t u, int64_t, int32_t y) {
+    if (u != cu) {
+      cu = u;
+      L = K.lab[u];
+      on = K.sz[L] > 1 && K.rdy[L] == level;
+      if (on) w = vd_weight(K, L) + K.best[L];
+    }
+    if (on) vd_kahn_arc(K, L, w, y, level, next, slot);
+  });
 }
 
 // ============================================================== host side
@@ -3953,7 +4003,7 @@ kadabra_status vd_condensation(kadabra_graph* g, LoadTrace& tr, const LoadScratc
     for (int k = 0; k < BATCH; ++k) KCK(cudaMemsetAsync(slots + 2 * ((l0 + k) % SLOTS), 0, 2 * sizeof(int32_t)));
     for (int k = 0; k < BATCH; ++k) {
       const int32_t l = l0 + k;
-      k_vd_kahn_level<<<8 * g->num_sms, 256>>>(K, (l & 1) ? S.qb : S.qa, slots + 2 * ((l + SLOTS - 1) % SLOTS),
+      k_vd_kahn_level<<<8 * g->num_sms, 256>>>(K, m, (l & 1) ? S.qb : S.qa, slots + 2 * ((l + SLOTS - 1) % SLOTS),
                                                (l & 1) ? S.qa : S.qb, slots + 2 * (l % SLOTS), l);
     }
     int32_t h[2 * SLOTS];
