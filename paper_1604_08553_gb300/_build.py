@@ -50,6 +50,21 @@ def build_kadabra(force: bool = False, extra=()) -> str:
     return CU_LIB
 
 
+CU_LIB_CHECKED = os.path.join(HERE, "libkadabra_checked.so")
+
+
+def build_checked(force: bool = False) -> str:
+    """The same library with KADABRA_CHECKED: every list, frontier-array,
+    level-bound, adjacency and hit-counter index of the sampler is checked
+    (tests only; the checks record the failing site and fail the sample)."""
+    if force or _stale(CU_LIB_CHECKED, CU_SRC, HEADER):
+        tmp = CU_LIB_CHECKED + f".tmp{os.getpid()}"
+        cmd = [nvcc(), *NVCC_FLAGS, "-DKADABRA_CHECKED", CU_SRC, "-o", tmp]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, CU_LIB_CHECKED)
+    return CU_LIB_CHECKED
+
+
 def build_all(force: bool = False) -> None:
     from . import graphgen
     with ThreadPoolExecutor(max_workers=2) as ex:

@@ -157,6 +157,25 @@ __device__ __forceinline__ uint64_t below128(uint4 b, uint64_t S) {
   return hh + (sum < hl ? 1ull : 0ull);
 }
 
+// ============================================================== checked build
+// With KADABRA_CHECKED defined, the sampler checks the index of every list,
+// frontier-array, level-bound, adjacency and hit-counter access.  A failing
+// check records (site << 40 | index) in g_checked once, redirects the access
+// to index 0 (so nothing outside the arrays is touched), and the sample then
+// fails with KADABRA_ERR_INTERNAL, whose message names the site and index.
+// Without the flag the checks compile to nothing.
+#ifdef KADABRA_CHECKED
+__device__ unsigned long long g_checked;
+__device__ __forceinline__ int64_t kchk(int64_t i, int64_t bound, int site) {
+  if (i >= 0 && i < bound) return i;
+  atomicCAS(&g_checked, 0ull, ((unsigned long long)site << 40) | ((unsigned long long)i & ((1ull << 40) - 1)));
+  return 0;
+}
+#define KIDX(i, bound, site) ((decltype(i))kchk((int64_t)(i), (int64_t)(bound), (site)))
+#else
+#define KIDX(i, bound, site) (i)
+#endif
+
 // ============================================================== tables
 struct PiEntry {
   int32_t x, y;          // x on the expanding side, y the scanned neighbour
@@ -186,29 +205,31 @@ struct Tables {
   int pcap;
 };
 
-__device__ __forceinline__ int& lvl_lo(const Tables& T, int side, int d) { return T.lvl[(2 * side) * (T.maxd + 2) + d]; }
+__device__ __forceinline__ int& lvl_lo(const Tables& T, int side, int d) {
+  return T.lvl[KIDX((2 * side) * (T.maxd + 2) + d, 4 * (T.maxd + 2), 1)];
+}
 __device__ __forceinline__ int& lvl_hi(const Tables& T, int side, int d) {
-  return T.lvl[(2 * side + 1) * (T.maxd + 2) + d];
+  return T.lvl[KIDX((2 * side + 1) * (T.maxd + 2) + d, 4 * (T.maxd + 2), 2)];
 }
 
 // list entry i's hash position (16-bit in the shared-memory tiers: PK)
 template <bool PK>
 __device__ __forceinline__ uint32_t lpos_get(const Tables& T, int i) {
-  return PK ? (uint32_t)T.lpos16[i] : T.lpos[i];
+  return PK ? (uint32_t)T.lpos16[KIDX(i, T.lcap, 3)] : T.lpos[KIDX(i, T.lcap, 3)];
 }
 // list entry i's node: the packed tiers keep no id list and read it from the
 // entry's hash word (its high half never changes once published)
 template <bool PK>
 __device__ __forceinline__ int32_t list_node(const Tables& T, int i) {
-  if (PK) return (int32_t)(T.hkv[T.lpos16[i]] >> 32);
-  return T.lnode[i];
+  if (PK) return (int32_t)(T.hkv[KIDX((uint32_t)T.lpos16[KIDX(i, T.lcap, 5)], T.hmask + 1u, 6)] >> 32);
+  return T.lnode[KIDX(i, T.lcap, 5)];
 }
 template <bool PK>
 __device__ __forceinline__ void lpos_set(const Tables& T, int i, uint32_t pos) {
   if (PK)
-    T.lpos16[i] = (uint16_t)pos;
+    T.lpos16[KIDX(i, T.lcap, 4)] = (uint16_t)pos;
   else
-    T.lpos[i] = pos;
+    T.lpos[KIDX(i, T.lcap, 4)] = pos;
 }
 
 __device__ __forceinline__ uint32_t pack_val(int side, int dist) { return ((uint32_t)side << 31) | (uint32_t)dist; }
@@ -626,14 +647,15 @@ __device__ __forceinline__ void cp_async_wait() {
 // window in registers; only lanes whose arc lies in a later row search the
 // frontier prefix.
 template <class F>
-__device__ __forceinline__ void scan_level_regs(const Tables& T, int fcount, int E, const int32_t* cols, F f) {
+__device__ __forceinline__ void scan_level_regs(const Tables& T, int fcount, int E, const int32_t* cols, int64_t ncols,
+                                                F f) {
   const int lane = lane_id(), wid = warp_id();
   const int per = (E + NW - 1) / NW;
   const int c0 = min(E, wid * per), c1 = min(E, c0 + per);
   if (c0 >= c1) return;
   int pcur = frontier_pos(T.pr, fcount, c0);  // warp-uniform
-  int2 cur = T.pr[pcur];                      // {first arc index, row start}
-  int nxt = T.pr[pcur + 1].x;                 // first arc index of the next row
+  int2 cur = T.pr[KIDX(pcur, T.frcap + 1, 7)];  // {first arc index, row start}
+  int nxt = T.pr[KIDX(pcur + 1, T.frcap + 1, 7)].x;  // first arc index of the next row
   for (int base = c0; base < c1; base += 32 * U) {
     int ys[U], ps[U];
     bool oks[U];
@@ -645,8 +667,8 @@ __device__ __forceinline__ void scan_level_regs(const Tables& T, int fcount, int
       if (wb < c1) {
         if (nxt <= wb) {  // the window starts in a later row
           pcur = frontier_next(T.pr, pcur + 1, fcount, wb);
-          cur = T.pr[pcur];
-          nxt = T.pr[pcur + 1].x;
+          cur = T.pr[KIDX(pcur, T.frcap + 1, 7)];
+          nxt = T.pr[KIDX(pcur + 1, T.frcap + 1, 7)].x;
         }
         const int e = wb + lane;
         if (e < c1) {
@@ -654,10 +676,10 @@ __device__ __forceinline__ void scan_level_regs(const Tables& T, int fcount, int
           int2 q = cur;
           if (e >= nxt) {
             p = frontier_next(T.pr, pcur + 1, fcount, e);
-            q = T.pr[p];
+            q = T.pr[KIDX(p, T.frcap + 1, 7)];
           }
           ps[k] = p;
-          ys[k] = __ldg(&cols[q.y + (e - q.x)]);
+          ys[k] = __ldg(&cols[KIDX((int64_t)q.y + (e - q.x), ncols, 8)]);
           oks[k] = true;
         }
       }
@@ -679,7 +701,8 @@ __device__ __forceinline__ void scan_level_regs(const Tables& T, int fcount, int
 // window in registers; only lanes whose arc lies in a later row search the
 // frontier prefix.
 template <class F>
-__device__ __forceinline__ void scan_level_ring(const Tables& T, Ctl& c, int fcount, int E, const int32_t* cols, F f) {
+__device__ __forceinline__ void scan_level_ring(const Tables& T, Ctl& c, int fcount, int E, const int32_t* cols,
+                                                int64_t ncols, F f) {
   const int lane = lane_id(), wid = warp_id();
   const int per = (E + NW - 1) / NW;
   const int c0 = min(E, wid * per), c1 = min(E, c0 + per);
@@ -702,7 +725,7 @@ __device__ __forceinline__ void scan_level_ring(const Tables& T, Ctl& c, int fco
       if (e < c1) {
         int2 q = icur;
         if (e >= inxt) q = T.pr[frontier_next(T.pr, ip + 1, fcount, e)];
-        cp_async4(&ring[(w % RING) * 32 + lane], &cols[q.y + (e - q.x)]);
+        cp_async4(&ring[(w % RING) * 32 + lane], &cols[KIDX((int64_t)q.y + (e - q.x), ncols, 8)]);
       }
     }
     cp_async_commit();  // one group per window (empty past the end): uniform counts
@@ -732,11 +755,12 @@ __device__ __forceinline__ void scan_level_ring(const Tables& T, Ctl& c, int fco
 }
 
 template <bool RG, class F>
-__device__ __forceinline__ void scan_level(const Tables& T, Ctl& c, int fcount, int E, const int32_t* cols, F f) {
+__device__ __forceinline__ void scan_level(const Tables& T, Ctl& c, int fcount, int E, const int32_t* cols,
+                                           int64_t ncols, F f) {
   if constexpr (RG)
-    scan_level_ring(T, c, fcount, E, cols, f);
+    scan_level_ring(T, c, fcount, E, cols, ncols, f);
   else
-    scan_level_regs(T, fcount, E, cols, f);
+    scan_level_regs(T, fcount, E, cols, ncols, f);
 }
 
 // Weighted choice among n items held in any order, in the order of their
@@ -859,7 +883,7 @@ template <bool PK>
 __device__ __forceinline__ void bt_record(const SampleParams& P, const Job& J, Ctl& c, int half, int dn, int y, int pos,
                                           int64_t out_i, int dv, int dw, bool want_path) {
   atomicAdd(reinterpret_cast<unsigned long long*>(&c.stat[KADABRA_STAT_BT_SCANNED]), (unsigned long long)(pos + 1));
-  if (dn > 0 && J.counts) atomicAdd(&J.counts[y], 1u);
+  if (dn > 0 && J.counts) atomicAdd(&J.counts[KIDX(y, J.g.n, 11)], 1u);
   if (want_path) {
     const int at = half == 0 ? dn : (dv + 1) + (dw - dn);
     if (at < P.max_len) P.paths[out_i * (int64_t)P.max_len + at] = y;
@@ -911,7 +935,7 @@ __device__ void bt_warp_steps(const SampleParams& P, const Job& J, const Tables&
         const int i = base + lane;
         unsigned long long w = 0;
         if (i < deg) {
-          const int yy = __ldg(&bcol[r0 + i]);
+          const int yy = __ldg(&bcol[KIDX((int64_t)r0 + i, G.m, 12)]);
           const int q = tab_find_pos(T, yy);
           if (q >= 0) {
             const unsigned long long hw = T.hkv[q];
@@ -932,7 +956,7 @@ __device__ void bt_warp_steps(const SampleParams& P, const Job& J, const Tables&
         }
         carry += __shfl_sync(FULL, inc, 31);
       }
-      if (pos >= 0) y = __ldg(&bcol[r0 + pos]);
+      if (pos >= 0) y = __ldg(&bcol[KIDX((int64_t)r0 + pos, G.m, 12)]);
     }
     if (y < 0) {
       if (lane == 0) c.bt_flag = 1;
@@ -1045,17 +1069,17 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
         const int i = base + tid;
         int deg = 0, rs = 0;
         if (i < cnt) {
-          const int x = list_node<PK>(T, fb + i);
+          const int x = KIDX(list_node<PK>(T, fb + i), G.n, 9);
           rs = __ldg(&rowp[x]);
           deg = __ldg(&rowp[x + 1]) - rs;
         }
         int tot;
         const int ex = block_exscan(deg, c.scan_tmp, &tot);
-        if (i < cnt) T.pr[i] = make_int2(carry + ex, rs);
+        if (i < cnt) T.pr[KIDX(i, T.frcap + 1, 10)] = make_int2(carry + ex, rs);
         carry += tot;
       }
       if (tid == 0) {
-        T.pr[cnt] = make_int2(carry, 0);
+        T.pr[KIDX(cnt, T.frcap + 1, 10)] = make_int2(carry, 0);
         c.ecount = carry;
         if (count_edges) c.stat[KADABRA_STAT_EDGES] += carry;
       }
@@ -1074,7 +1098,7 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
       for (int sg = 0; sg < nseg; ++sg) {
       const int fb = f0 + sg * T.frcap, cnt = min(T.frcap, fcount - sg * T.frcap);
       E = build_prefix(fb, cnt, true);
-      scan_level<RG>(T, c, cnt, E, cols, [&](int, bool ok, int p, int y) {
+      scan_level<RG>(T, c, cnt, E, cols, G.m, [&](int, bool ok, int p, int y) {
         bool touch = false;
         unsigned long long wgt = 0;
         int32_t xnode = 0;
@@ -1153,11 +1177,11 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
       for (int sg = 0; sg < nseg; ++sg) {
       const int fb = f0 + sg * T.frcap, cnt = min(T.frcap, fcount - sg * T.frcap);
       if (nseg > 1) E = build_prefix(fb, cnt, false);  // one segment: pass 1's prefix is still there
-      scan_level<RG>(T, c, cnt, E, cols, [&](int, bool ok, int p, int y) {
+      scan_level<RG>(T, c, cnt, E, cols, G.m, [&](int, bool ok, int p, int y) {
         if (!ok || cap) return;
         // the head's row bounds (its degree joins the new frontier's cost if
         // it is new), loaded before the probe so the load overlaps it
-        const int ylo = __ldg(&rowp[y]), yhi = __ldg(&rowp[y + 1]);
+        const int ylo = __ldg(&rowp[KIDX(y, G.n, 13)]), yhi = __ldg(&rowp[KIDX(y, G.n, 13) + 1]);
         const uint32_t px = lpos_get<PK>(T, fb + p);
         const unsigned long long add = ent_sig<PK>(T, T.hkv[px], px);
         uint32_t pos = hash_pos(y, T.hlog);
@@ -1347,8 +1371,8 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
       if (dv + 1 < P.max_len) row[dv + 1] = c.cw;
     }
     if (J.counts) {
-      if (dv > 0) atomicAdd(&J.counts[c.cv], 1u);
-      if (dw > 0) atomicAdd(&J.counts[c.cw], 1u);
+      if (dv > 0) atomicAdd(&J.counts[KIDX(c.cv, J.g.n, 11)], 1u);
+      if (dw > 0) atomicAdd(&J.counts[KIDX(c.cw, J.g.n, 11)], 1u);
     }
   }
   // Steps go one node at a time, v -> s over predecessors (walker 0, weights
@@ -1632,6 +1656,9 @@ __device__ void flush_totals(const SampleParams& P, Ctl& c) {
 
 // Records the outcome of one sample (per-sample outputs, totals, status).
 __device__ void finish_sample(const SampleParams& P, Ctl& c, uint64_t idx, int64_t out_i) {
+#ifdef KADABRA_CHECKED
+  if (*(volatile unsigned long long*)&g_checked) c.flags |= F_INTERNAL;
+#endif
   const int flags = c.flags;
   int st = KADABRA_OK;
   if (flags & F_INTERNAL)
@@ -3712,9 +3739,15 @@ kadabra_status read_status(Workspace* w, cudaStream_t st) {
   if (h != 0) {
     KCK(cudaMemsetAsync(w->status, 0, sizeof(int32_t), st));
     KCK(cudaStreamSynchronize(st));
-    const char* what = h == KADABRA_ERR_SIGMA_OVERFLOW ? "a shortest-path count exceeded 2^64-1"
+    std::string what = h == KADABRA_ERR_SIGMA_OVERFLOW ? "a shortest-path count exceeded 2^64-1"
                        : h == KADABRA_ERR_CAPACITY     ? "a sampler capacity bound was exceeded"
                                                        : "the sampler reported an internal error";
+#ifdef KADABRA_CHECKED
+    unsigned long long ck = 0;
+    if (cudaMemcpyFromSymbol(&ck, g_checked, sizeof(ck)) == cudaSuccess && ck)
+      what += " (checked build: index check " + std::to_string(ck >> 40) + " failed at index " +
+              std::to_string(ck & ((1ull << 40) - 1)) + ")";
+#endif
     return fail((kadabra_status)h, what);
   }
   return KADABRA_OK;
