@@ -638,9 +638,10 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // The level scan for graphs whose CSR stays in L2: each warp takes a
 // contiguous slice of the flattened arc range and walks it in windows of 32
-// arcs, U windows at a time so their loads overlap (in registers; deeper
-// pipelining through shared memory costs more per window than the shorter
-// L2 latency gains).  For every window position it calls f(k, ok, p, y): ok =
+// arcs, software-pipelined: the loads of the next window are issued before the
+// current window is processed, so their L2 latency overlaps its probes
+// (deeper pipelining through shared memory costs more per window than the
+// shorter L2 latency gains).  For every window position it calls f(k, ok, p, y): ok =
 // the lane holds an arc, p = frontier position of its tail, y = its head.
 // All lanes of the warp call f together, in increasing arc order (so f may
 // use warp collectives).  The warp keeps the frontier row of its current
@@ -656,36 +657,37 @@ __device__ __forceinline__ void scan_level_regs(const Tables& T, int fcount, int
   int pcur = frontier_pos(T.pr, fcount, c0);  // warp-uniform
   int2 cur = T.pr[KIDX(pcur, T.frcap + 1, 7)];  // {first arc index, row start}
   int nxt = T.pr[KIDX(pcur + 1, T.frcap + 1, 7)].x;  // first arc index of the next row
-  for (int base = c0; base < c1; base += 32 * U) {
-    int ys[U], ps[U];
-    bool oks[U];
-#pragma unroll
-    for (int k = 0; k < U; ++k) {
-      const int wb = base + 32 * k;
-      oks[k] = false;
-      ys[k] = ps[k] = 0;
-      if (wb < c1) {
-        if (nxt <= wb) {  // the window starts in a later row
-          pcur = frontier_next(T.pr, pcur + 1, fcount, wb);
-          cur = T.pr[KIDX(pcur, T.frcap + 1, 7)];
-          nxt = T.pr[KIDX(pcur + 1, T.frcap + 1, 7)].x;
-        }
-        const int e = wb + lane;
-        if (e < c1) {
-          int p = pcur;
-          int2 q = cur;
-          if (e >= nxt) {
-            p = frontier_next(T.pr, pcur + 1, fcount, e);
-            q = T.pr[KIDX(p, T.frcap + 1, 7)];
-          }
-          ps[k] = p;
-          ys[k] = __ldg(&cols[KIDX((int64_t)q.y + (e - q.x), ncols, 8)]);
-          oks[k] = true;
-        }
-      }
+  // the window at wb: its lanes' frontier positions and heads (loads issued)
+  auto fetch = [&](int wb, bool& ok, int& p, int& y) {
+    ok = false;
+    p = y = 0;
+    if (wb >= c1) return;
+    if (nxt <= wb) {  // the window starts in a later row
+      pcur = frontier_next(T.pr, pcur + 1, fcount, wb);
+      cur = T.pr[KIDX(pcur, T.frcap + 1, 7)];
+      nxt = T.pr[KIDX(pcur + 1, T.frcap + 1, 7)].x;
     }
-#pragma unroll
-    for (int k = 0; k < U; ++k) f(k, oks[k], ps[k], ys[k]);
+    const int e = wb + lane;
+    if (e < c1) {
+      int2 q = cur;
+      p = pcur;
+      if (e >= nxt) {
+        p = frontier_next(T.pr, pcur + 1, fcount, e);
+        q = T.pr[KIDX(p, T.frcap + 1, 7)];
+      }
+      y = __ldg(&cols[KIDX((int64_t)q.y + (e - q.x), ncols, 8)]);
+      ok = true;
+    }
+  };
+  bool ok0, ok1;
+  int p0, p1, y0, y1;
+  fetch(c0, ok0, p0, y0);
+  for (int wb = c0; wb < c1; wb += 32) {
+    fetch(wb + 32, ok1, p1, y1);
+    f(0, ok0, p0, y0);
+    ok0 = ok1;
+    p0 = p1;
+    y0 = y1;
   }
 }
 
