@@ -61,6 +61,7 @@
 #include <deque>
 #include <memory>
 #include <thread>
+#include <type_traits>
 #include <cstdint>
 #include <cstdlib>
 #include <cstdio>
@@ -109,8 +110,8 @@ constexpr int SMALL_HLOG = FAST_HLOG - 1;      // tier S, small variant: half th
 #define KD_FAST_MAXD 126
 #endif
 constexpr int FAST_MAXD = KD_FAST_MAXD;  // levels per side in shared memory (at most 126: the packed entry's dist field)
-constexpr int MED_HLOG = 15;       // tier M, global memory per CTA: 32768 hash slots
-constexpr int MED_LCAP = 16384;    //   level lists: 16384 nodes
+constexpr int MED_HLOG = 16;       // tier M, global memory per CTA: 65536 hash slots
+constexpr int MED_LCAP = 32768;    //   level lists: 32768 nodes
 constexpr int MED_MAXD = 1022;     //   levels per side
 constexpr int GM_MAXD = 65534;     // tier L, global memory, hash >= 2n slots, lists of n
 constexpr int FAST_PCAP = 2048;    // candidate edges per warp, tiers S and M (global memory)
@@ -171,7 +172,7 @@ __device__ __forceinline__ int64_t kchk(int64_t i, int64_t bound, int site) {
   atomicCAS(&g_checked, 0ull, ((unsigned long long)site << 40) | ((unsigned long long)i & ((1ull << 40) - 1)));
   return 0;
 }
-#define KIDX(i, bound, site) ((decltype(i))kchk((int64_t)(i), (int64_t)(bound), (site)))
+#define KIDX(i, bound, site) ((std::decay_t<decltype(i)>)kchk((int64_t)(i), (int64_t)(bound), (site)))
 #else
 #define KIDX(i, bound, site) (i)
 #endif
@@ -392,8 +393,9 @@ struct SampleParams {
   // tables
   PiEntry* pi_base;                 // per CTA: NW * pcap
   int pcap;
-  unsigned char* med_base;          // tier M tables, per CTA of the main grid
+  unsigned char* med_base;          // tier M tables, per CTA of the large-table launch
   size_t med_stride;
+  int med_hlog, med_lcap;           //   their hash slots (log2) and list capacity
   unsigned char* gm_base;           // tier L tables, per CTA of the deferred launch
   size_t gm_stride;
   int gm_hlog;
@@ -1709,7 +1711,7 @@ __global__ void __launch_bounds__(NT, MODE != 0 ? 2 : SHL == FAST_HLOG ? KD_MIN_
   if (MODE == 0) TS = smem_tables<SHL, RG>(smem);
   if (MODE == 2) {
     TS = smem_tables<BIG_HLOG>(smem);
-    TM = gm_tables(P.med_base + (size_t)blockIdx.x * P.med_stride, MED_HLOG, MED_LCAP, MED_MAXD);
+    TM = gm_tables(P.med_base + (size_t)blockIdx.x * P.med_stride, P.med_hlog, P.med_lcap, MED_MAXD);
   }
   if (MODE == 1) TM = gm_tables(P.gm_base + (size_t)blockIdx.x * P.gm_stride, P.gm_hlog, P.gm_lcap, GM_MAXD);
   TS.pi = TM.pi = pi;
@@ -3678,6 +3680,8 @@ SampleParams ws_params(const Workspace* w, uint32_t flags) {
   P.status = w->status;
   P.med_base = w->med_base;
   P.med_stride = w->med_stride;
+  P.med_hlog = MED_HLOG;
+  P.med_lcap = MED_LCAP;
   P.gm_base = w->gm_base;
   P.gm_stride = w->gm_stride;
   P.gm_hlog = w->gm_hlog;
@@ -5791,10 +5795,13 @@ constexpr size_t NA_OFF_QB = NA_HEADER;
 constexpr size_t NA_OFF_QL = NA_OFF_QB + sizeof(unsigned long long) * NA_MAX_BATCH;
 constexpr size_t NA_OFF_PI = NA_OFF_QL + sizeof(unsigned long long) * NA_MAX_BATCH;
 constexpr size_t NA_OFF_MED = NA_OFF_PI + sizeof(PiEntry) * (size_t)NA_MAX_CTAS * 2 * NW * NA_PCAP;
-// one tier-M table (gm_layout of MED_HLOG, MED_LCAP, MED_MAXD), 256-byte aligned
+constexpr int NA_MED_HLOG = 15;               // its tier-M tables: 32768 hash slots,
+constexpr int NA_MED_LCAP = 16384;            //   lists of 16384 nodes
+// one tier-M table (gm_layout of NA_MED_HLOG, NA_MED_LCAP, MED_MAXD), 256-byte aligned
 constexpr size_t NA_MED_STRIDE =
-    ((((2 * sizeof(unsigned long long)) << MED_HLOG) + sizeof(int2) * ((size_t)MED_LCAP + 1) +
-      sizeof(int32_t) * (size_t)MED_LCAP + sizeof(uint32_t) * (size_t)MED_LCAP + sizeof(int) * 4 * (size_t)(MED_MAXD + 2)) +
+    ((((2 * sizeof(unsigned long long)) << NA_MED_HLOG) + sizeof(int2) * ((size_t)NA_MED_LCAP + 1) +
+      sizeof(int32_t) * (size_t)NA_MED_LCAP + sizeof(uint32_t) * (size_t)NA_MED_LCAP +
+      sizeof(int) * 4 * (size_t)(MED_MAXD + 2)) +
      255) & ~size_t(255);
 constexpr size_t NA_BYTES = NA_OFF_MED + NA_MED_STRIDE * NA_MED_CTAS;
 static_assert(NA_OFF_STATUS + sizeof(int32_t) <= NA_HEADER, "no-alloc header");
@@ -5839,14 +5846,15 @@ kadabra_status noalloc_setup(int dev, NoAllocDevice** out) {
     d.scratch = static_cast<unsigned char*>(ptr);
     {
       size_t a, b, c2, e2;
-      if (gm_layout(MED_HLOG, MED_LCAP, MED_MAXD, &a, &b, &c2, &e2) != NA_MED_STRIDE)
+      if (gm_layout(NA_MED_HLOG, NA_MED_LCAP, MED_MAXD, &a, &b, &c2, &e2) != NA_MED_STRIDE)
         return fail(KADABRA_ERR_INTERNAL, "tier-M table layout");
     }
     // the tier-M tables start empty (every key word EMPTY, sigma 0); each
     // sample clears what it used, so they stay so from call to call
     KCK(cudaMemset(d.scratch + NA_OFF_MED, 0, NA_MED_STRIDE * NA_MED_CTAS));
     for (int b = 0; b < NA_MED_CTAS; ++b)
-      KCK(cudaMemset(d.scratch + NA_OFF_MED + (size_t)b * NA_MED_STRIDE, 0xFF, sizeof(unsigned long long) << MED_HLOG));
+      KCK(cudaMemset(d.scratch + NA_OFF_MED + (size_t)b * NA_MED_STRIDE, 0xFF,
+                     sizeof(unsigned long long) << NA_MED_HLOG));
     KCK(cudaDeviceSynchronize());
     d.ready = true;
   }
@@ -6230,6 +6238,8 @@ kadabra_status kadabra_sample_batch_noalloc(int32_t n, int64_t m, const int32_t*
   P.pcap = NA_PCAP;
   P.med_base = d->scratch + NA_OFF_MED;  // tier M for the large-table launch's CTAs
   P.med_stride = NA_MED_STRIDE;
+  P.med_hlog = NA_MED_HLOG;
+  P.med_lcap = NA_MED_LCAP;
   P.tier_flags = 0;  // tiers S, B and M; samples beyond tier M end the call with KADABRA_ERR_CAPACITY
   KCK(cudaMemsetAsync(d->scratch, 0, NA_HEADER, st));
   k_sample<0><<<d->grid_s, NT, d->smem_s, st>>>(P);
