@@ -265,11 +265,12 @@ kadabra_status kadabra_graph_info(const kadabra_graph* g, int32_t* n, int64_t* m
  * a batch or serving launch shared by several graphs runs that tier first if
  * any of them has the flag (and ignores their other flags).  It has no effect
  * together with one of the three flags above.  KADABRA_FLAG_ASYNC_SCAN makes
- * the level scans of the 4096-slot shared-memory table keep more arc loads in
- * flight (asynchronous copies through shared memory).  The
- * library does this by itself for graphs whose CSR (forward plus reverse)
- * exceeds the device's L2, where those loads wait on HBM; the flag asks for it
- * on any graph, and a shared launch takes it from any of its graphs.
+ * the level scans of the 4096-slot shared-memory table read every stretch of
+ * at least 131 arcs inside one row with 16-byte loads (128 arcs per warp
+ * load).  The library does this by itself for graphs whose CSR (forward plus
+ * reverse) exceeds the device's L2, where each load waits on HBM; the flag
+ * asks for it on any graph, and a shared launch takes it from any of its
+ * graphs.
  * KADABRA_FLAG_FRONTIER_SEGMENTS makes the shared-memory tables scan every
  * frontier in segments of 64 nodes, as they do for frontiers beyond their
  * frontier array (2048 nodes); it exists to test that path and only slows

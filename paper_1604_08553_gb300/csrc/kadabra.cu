@@ -38,7 +38,9 @@
 //   * The two backtracking walks (v -> s, w -> t) take disjoint Philox
 //     blocks, so two warps walk them at the same time.
 //   * Each warp scans a contiguous slice of the level's flattened arc range,
-//     in registers or, for graphs beyond the L2, through an async-copy ring.
+//     one window of 32 arcs in flight (the next one's loads issued before
+//     the current one is processed) or, for graphs beyond the L2, with
+//     16-byte loads along long row stretches.
 //     Candidate edges are chosen in (x, y) order without a sort (quadratic
 //     ranking or a weighted radix selection).
 //   * A sample that outgrows its table moves on to bigger tables (tier B in
@@ -92,10 +94,6 @@ namespace {
 constexpr int NT = KD_NT;          // threads per sampler CTA
 constexpr int NW = NT / 32;        // warps per sampler CTA
 constexpr int U = KD_U;            // independent items per thread per step (memory-level parallelism)
-#ifndef KD_RING
-#define KD_RING 2
-#endif
-constexpr int RING = KD_RING;      // arc windows in flight per warp in the level scans (async copies)
 // Tiers of per-sample tables.  A sample starts in a small shared-memory
 // table (tier S, main launch, four or five CTAs per SM; optionally tier W,
 // one warp per sample, before it).  If it outgrows it, it is queued for a
@@ -198,7 +196,6 @@ struct Tables {
   int2* pr;                 // frontier: {degree prefix, row start}; frcap+1 entries
   int lcap;
   int frcap;                // frontier nodes per scan segment (the frontier array's capacity)
-  int* ring;                // the async-copy scan's per-warp ring (tier S only), else null
   uint32_t* bits;           // filter of the other side's frontier (shared-memory tiers), else null
   int* lvl;                 // [side][lo|hi][maxd+2]
   int maxd;
@@ -626,18 +623,6 @@ __device__ __forceinline__ int block_pick(int N, unsigned long long r, Ctl& c, W
 }
 
 // ============================================================== one sample
-// 4-byte asynchronous global -> shared copies (cp.async, sm_80 and later):
-// the loads of several windows stay in flight without holding registers.
-__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
 // The level scan for graphs whose CSR stays in L2: each warp takes a
 // contiguous slice of the flattened arc range and walks it in windows of 32
 // arcs, software-pipelined: the loads of the next window are issued before the
@@ -694,75 +679,74 @@ __device__ __forceinline__ void scan_level_regs(const Tables& T, int fcount, int
 }
 
 // The level scan for graphs whose CSR does not fit in L2 (its loads wait on
-// HBM): each warp takes a contiguous slice of the flattened arc range and
-// walks it in windows of 32 arcs.  The heads of the next RING - 1 windows are copied asynchronously into the
-// warp's ring in shared memory while the current window is processed (each
-// lane copies and later reads its own entries, so its own wait orders
-// them).  For every window position it calls f(k, ok, p, y): ok = the lane
-// holds an arc, p = frontier position of its tail, y = its head.  All lanes
-// of the warp call f together, in increasing arc order (so f may use warp
-// collectives).  Two cursors (issue, process) keep the frontier row of their
-// window in registers; only lanes whose arc lies in a later row search the
-// frontier prefix.
+// HBM): each warp takes a contiguous slice of the flattened arc range.  A
+// stretch of at least 131 arcs inside one row (hub rows hold most arcs of a
+// power-law graph's touching level) is read with 16-byte loads, 128 arcs per
+// warp load, so a hub row takes a quarter of the dependent round trips; no
+// lane has to find its row there.  Elsewhere the warp takes windows of 32 arcs, keeping
+// the current frontier row in registers; only lanes whose arc lies in a
+// later row search the frontier prefix.  For every arc it calls f(k, ok, p,
+// y): ok = the lane holds an arc, p = frontier position of its tail, y = its
+// head.  All lanes of the warp call f together (so f may use warp
+// collectives); the arcs come in no particular order.
 template <class F>
-__device__ __forceinline__ void scan_level_ring(const Tables& T, Ctl& c, int fcount, int E, const int32_t* cols,
-                                                int64_t ncols, F f) {
+__device__ __forceinline__ void scan_level_vec(const Tables& T, int fcount, int E, const int32_t* cols, int64_t ncols,
+                                                F f) {
   const int lane = lane_id(), wid = warp_id();
   const int per = (E + NW - 1) / NW;
   const int c0 = min(E, wid * per), c1 = min(E, c0 + per);
   if (c0 >= c1) return;
-  int* ring = T.ring + wid * RING * 32;
-  const int nwin = (c1 - c0 + 31) >> 5;
-  int ip = frontier_pos(T.pr, fcount, c0);  // issue cursor (warp-uniform)
-  int2 icur = T.pr[ip];                      // {first arc index, row start}
-  int inxt = T.pr[ip + 1].x;                 // first arc index of the next row
-  int pp = ip, pnxt = inxt;                  // process cursor
-  auto issue = [&](int w) {
-    if (w < nwin) {
-      const int wb = c0 + 32 * w;
-      if (inxt <= wb) {  // the window starts in a later row
-        ip = frontier_next(T.pr, ip + 1, fcount, wb);
-        icur = T.pr[ip];
-        inxt = T.pr[ip + 1].x;
-      }
+  int pcur = frontier_pos(T.pr, fcount, c0);  // warp-uniform
+  int2 cur = T.pr[KIDX(pcur, T.frcap + 1, 7)];  // {first arc index, row start}
+  int nxt = T.pr[KIDX(pcur + 1, T.frcap + 1, 7)].x;  // first arc index of the next row
+  // Each step yields a group of one to four arcs per lane (v, with ok and p
+  // for all of them); the callback is called for each in one place, so its
+  // code is inlined once.
+  int wb = c0;
+  while (wb < c1) {
+    if (nxt <= wb) {  // the next arc lies in a later row
+      pcur = frontier_next(T.pr, pcur + 1, fcount, wb);
+      cur = T.pr[KIDX(pcur, T.frcap + 1, 7)];
+      nxt = T.pr[KIDX(pcur + 1, T.frcap + 1, 7)].x;
+    }
+    const int room = min(nxt, c1) - wb;                // arcs of this row left in the slice
+    const int64_t a0 = (int64_t)cur.y + (wb - cur.x);  // address of arc wb
+    const int mis = (int)(((uintptr_t)(cols + a0) >> 2) & 3);  // 4-byte steps past a 16-byte boundary
+    int4 v = make_int4(0, 0, 0, 0);
+    int nk = 1, p = pcur;
+    bool ok = false;
+    if (room >= 131 && mis == 0) {  // 128 arcs of one row: 16-byte loads
+      v = __ldg(reinterpret_cast<const int4*>(cols + KIDX(a0, ncols - 127, 8)) + lane);
+      ok = true;
+      nk = 4;
+      wb += 128;
+    } else if (room >= 131) {  // up to 3 arcs to the next 16-byte boundary
+      ok = lane < 4 - mis;
+      if (ok) v.x = __ldg(&cols[KIDX(a0 + lane, ncols, 8)]);
+      wb += 4 - mis;
+    } else {  // a window of 32 arcs, perhaps across rows
       const int e = wb + lane;
       if (e < c1) {
-        int2 q = icur;
-        if (e >= inxt) q = T.pr[frontier_next(T.pr, ip + 1, fcount, e)];
-        cp_async4(&ring[(w % RING) * 32 + lane], &cols[KIDX((int64_t)q.y + (e - q.x), ncols, 8)]);
+        int2 q = cur;
+        if (e >= nxt) {
+          p = frontier_next(T.pr, pcur + 1, fcount, e);
+          q = T.pr[KIDX(p, T.frcap + 1, 7)];
+        }
+        v.x = __ldg(&cols[KIDX((int64_t)q.y + (e - q.x), ncols, 8)]);
+        ok = true;
       }
+      wb += 32;
     }
-    cp_async_commit();  // one group per window (empty past the end): uniform counts
-  };
-#pragma unroll
-  for (int w = 0; w < RING - 1; ++w) issue(w);
-  for (int w = 0; w < nwin; ++w) {
-    __syncwarp();              // the slot's last read (previous window) before its refill
-    issue(w + RING - 1);       // into the slot processed one step ago
-    cp_async_wait<RING - 1>();  // window w has landed
-    const int wb = c0 + 32 * w;
-    if (pnxt <= wb) {
-      pp = frontier_next(T.pr, pp + 1, fcount, wb);
-      pnxt = T.pr[pp + 1].x;
-    }
-    const int e = wb + lane;
-    bool ok = false;
-    int p = 0, y = 0;
-    if (e < c1) {
-      p = e >= pnxt ? frontier_next(T.pr, pp + 1, fcount, e) : pp;
-      y = ring[(w % RING) * 32 + lane];
-      ok = true;
-    }
-    f(0, ok, p, y);
+#pragma unroll 1
+    for (int k = 0; k < nk; ++k) f(k, ok, p, k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w);
   }
-  cp_async_wait<0>();  // nothing left in flight (only empty groups remain)
 }
 
 template <bool RG, class F>
 __device__ __forceinline__ void scan_level(const Tables& T, Ctl& c, int fcount, int E, const int32_t* cols,
                                            int64_t ncols, F f) {
   if constexpr (RG)
-    scan_level_ring(T, c, fcount, E, cols, ncols, f);
+    scan_level_vec(T, fcount, E, cols, ncols, f);
   else
     scan_level_regs(T, fcount, E, cols, ncols, f);
 }
@@ -1562,7 +1546,6 @@ __device__ inline Tables gm_tables(unsigned char* base, int hlog, int lcap, int 
   T.lcap = lcap;
   T.frcap = lcap;
   T.lpos16 = nullptr;
-  T.ring = nullptr;
   T.bits = nullptr;
   T.maxd = maxd;
   return T;
@@ -1571,7 +1554,7 @@ __device__ inline Tables gm_tables(unsigned char* base, int hlog, int lcap, int 
 // shared-memory layout of a packed tier with 2^HLOG hash slots and lists of
 // 3/4 * 2^HLOG hash positions, after the control block.  A frontier is scanned
 // in segments of at most FRONTIER_SEG nodes (the frontier array's capacity);
-// the async-copy variant (RG) adds the ring of its level scans.
+// the scan variant for graphs beyond the L2 has the same layout.
 #ifndef KD_FRONTIER_SEG
 #define KD_FRONTIER_SEG 1024
 #endif
@@ -1579,30 +1562,28 @@ constexpr int FRONTIER_SEG = KD_FRONTIER_SEG;
 #ifndef KD_LOAD_QUARTERS
 #define KD_LOAD_QUARTERS 3
 #endif
-template <int HLOG, bool RG = false>
+template <int HLOG>
 struct SLayout {
   // nodes a table takes before the sample moves on to the next tier:
   // KD_LOAD_QUARTERS quarters of the slots (the probes stay short)
   static constexpr int LCAP = (KD_LOAD_QUARTERS << HLOG) / 4;
   static_assert(LCAP + NT < (1 << HLOG), "a full list leaves free slots");
   static constexpr int FRCAP = LCAP < FRONTIER_SEG ? LCAP : FRONTIER_SEG;
-  static constexpr size_t RING_BYTES = RG ? sizeof(int) * NW * RING * 32 : 0;
   static constexpr size_t HKV = (sizeof(Ctl) + 15) & ~size_t(15);
   static constexpr size_t PR = HKV + (sizeof(unsigned long long) << HLOG);
   static constexpr size_t LPOS = PR + sizeof(int2) * (FRCAP + 1);
   static constexpr size_t LVL = LPOS + sizeof(uint16_t) * LCAP;
   static constexpr size_t BITS = (LVL + sizeof(int) * 4 * (FAST_MAXD + 2) + 15) & ~size_t(15);
-  static constexpr size_t RINGO = BITS + sizeof(uint32_t) * FILTER_WORDS;
-  static constexpr size_t BYTES = RINGO + RING_BYTES;
+  static constexpr size_t BYTES = BITS + sizeof(uint32_t) * FILTER_WORDS;
   static_assert(HLOG <= 16, "16-bit list positions");
   // the radix selection's histogram (256 u64 + 256 u32) in the frontier array
   static_assert(sizeof(int2) * (FRCAP + 1) >= 256 * (sizeof(unsigned long long) + sizeof(unsigned)),
                 "frontier array holds the selection histogram");
 };
 
-template <int HLOG, bool RG = false>
+template <int HLOG>
 __device__ inline Tables smem_tables(unsigned char* smem) {
-  using L = SLayout<HLOG, RG>;
+  using L = SLayout<HLOG>;
   Tables T;
   T.hkv = reinterpret_cast<unsigned long long*>(smem + L::HKV);
   T.hsig = nullptr;  // packed entries
@@ -1611,7 +1592,6 @@ __device__ inline Tables smem_tables(unsigned char* smem) {
   T.lpos = nullptr;
   T.lpos16 = reinterpret_cast<uint16_t*>(smem + L::LPOS);
   T.lvl = reinterpret_cast<int*>(smem + L::LVL);
-  T.ring = L::RING_BYTES ? reinterpret_cast<int*>(smem + L::RINGO) : nullptr;
   T.bits = reinterpret_cast<uint32_t*>(smem + L::BITS);
   T.hlog = HLOG;
   T.hmask = (1u << HLOG) - 1u;
@@ -1626,7 +1606,7 @@ constexpr int TF_SKIP_S = 1;
 constexpr int TF_SKIP_B = 2;
 constexpr int TF_SKIP_M = 4;
 constexpr int TF_WARP = 8;  // tier W first, whatever the launch's variant
-constexpr int TF_RING = 16;  // tier S's level scans through the async-copy ring
+constexpr int TF_VEC = 16;  // tier S's level scans read long row stretches with 16-byte loads
 constexpr int TF_SEG64 = 32;  // shared-memory tiers scan frontiers in 64-node segments (tests)
 
 // queue counters in SampleParams::ctr
@@ -1698,17 +1678,17 @@ __device__ void clear_path_row(const SampleParams& P, int64_t out_i) {
 // SHL: the tier-S table size (2^SHL slots) of MODE 0; the small variant fits
 // one more CTA per SM and gives the same results (samples that outgrow it go
 // on to tier B as usual).  RG (MODE 0 with the 4096-slot table only): the
-// level scans keep more loads in flight through an async-copy ring (for
+// level scans read long row stretches with 16-byte loads (for
 // graphs whose CSR exceeds L2); same results.
 template <int MODE, int SHL = FAST_HLOG, bool RG = false>
 __global__ void __launch_bounds__(NT, MODE != 0 ? 2 : SHL == FAST_HLOG ? KD_MIN_BLOCKS : KD_MIN_BLOCKS + 1)
     k_sample(SampleParams P) {
-  static_assert(!RG || (MODE == 0 && SHL == FAST_HLOG), "the async-copy ring is laid out for tier S only");
+  static_assert(!RG || (MODE == 0 && SHL == FAST_HLOG), "the beyond-L2 scan has a tier-S instance only");
   extern __shared__ __align__(16) unsigned char smem[];
   Ctl& c = *reinterpret_cast<Ctl*>(smem);
   Tables TS, TM;
   PiEntry* pi = P.pi_base + (size_t)blockIdx.x * 2 * NW * P.pcap;
-  if (MODE == 0) TS = smem_tables<SHL, RG>(smem);
+  if (MODE == 0) TS = smem_tables<SHL>(smem);
   if (MODE == 2) {
     TS = smem_tables<BIG_HLOG>(smem);
     TM = gm_tables(P.med_base + (size_t)blockIdx.x * P.med_stride, P.med_hlog, P.med_lcap, MED_MAXD);
@@ -2237,7 +2217,6 @@ __global__ void __launch_bounds__(32 * WT_WARPS) k_sample_warp(SampleParams P) {
 size_t warp_tier_smem_bytes() { return sizeof(WSlot) * WT_WARPS; }
 
 size_t fast_smem_bytes() { return SLayout<FAST_HLOG>::BYTES; }
-size_t ring_smem_bytes() { return SLayout<FAST_HLOG, true>::BYTES; }
 size_t small_smem_bytes() { return SLayout<SMALL_HLOG>::BYTES; }
 size_t big_smem_bytes() { return SLayout<BIG_HLOG>::BYTES; }
 
@@ -3437,7 +3416,6 @@ struct Workspace {
   int64_t max_m = 0;
   int grid_fast = 0, grid_big = 0, grid_gm = 0, grid_small = 0, grid_warp = 0;
   size_t smem_fast = 0, smem_big = 0, smem_small = 0, smem_warp = 0;
-  int grid_ring = 0;  // the async-copy variant of tier S (its ring costs occupancy)
   unsigned long long* ctr = nullptr;
   int32_t* status = nullptr;
   unsigned long long* qb = nullptr;  // queue for tier B
@@ -3476,7 +3454,7 @@ struct kadabra_graph {
   int directed = 0;
   int32_t *rp = nullptr, *ci = nullptr, *rrp = nullptr, *rci = nullptr;
   int64_t vd = 0;
-  bool csr_beyond_l2 = false;  // forward (+ reverse) CSR larger than the L2: ring scans
+  bool csr_beyond_l2 = false;  // forward (+ reverse) CSR larger than the L2: 16-byte scans of long rows
   int device = 0;
   int num_sms = 0;
   uint32_t flags = 0;
@@ -3508,13 +3486,14 @@ struct kadabra_graph {
 
 namespace {
 // internal launch flag: the graph's CSR exceeds the L2, so its level scans
-// take the async-copy ring (KADABRA_FLAG_ASYNC_SCAN asks for it explicitly)
-constexpr uint32_t FLAG_RING_AUTO = 1u << 31;
+// read long row stretches with 16-byte loads (KADABRA_FLAG_ASYNC_SCAN asks
+// for that scan explicitly)
+constexpr uint32_t FLAG_VEC_AUTO = 1u << 31;
 // the flags a launch shared by several graphs takes from any of them (they
 // change no result; the tier-skipping flags stay per graph)
-constexpr uint32_t SHARED_LAUNCH_FLAGS = KADABRA_FLAG_WARP_TIER | KADABRA_FLAG_ASYNC_SCAN | FLAG_RING_AUTO;
+constexpr uint32_t SHARED_LAUNCH_FLAGS = KADABRA_FLAG_WARP_TIER | KADABRA_FLAG_ASYNC_SCAN | FLAG_VEC_AUTO;
 
-uint32_t launch_flags(const kadabra_graph* g) { return g->flags | (g->csr_beyond_l2 ? FLAG_RING_AUTO : 0u); }
+uint32_t launch_flags(const kadabra_graph* g) { return g->flags | (g->csr_beyond_l2 ? FLAG_VEC_AUTO : 0u); }
 }  // namespace
 
 // G graphs whose CSRs share one device arena
@@ -3554,10 +3533,8 @@ kadabra_status ensure_ws(Workspace* w, uint64_t deferred_need, int njobs) {
     w->smem_fast = fast_smem_bytes();
     KCK(cudaFuncSetAttribute(k_sample<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->smem_fast));
     KCK(cudaFuncSetAttribute(k_sample<0, FAST_HLOG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)ring_smem_bytes()));
+                             (int)w->smem_fast));
     int per_sm = 0;
-    KCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample<0, FAST_HLOG, true>, NT, ring_smem_bytes()));
-    w->grid_ring = w->num_sms * std::max(per_sm, 1);
     KCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample<0>, NT, w->smem_fast));
     if (per_sm < 1) return fail(KADABRA_ERR_CAPACITY, "sampler does not fit on an SM");
     w->grid_fast = w->num_sms * per_sm;
@@ -3691,7 +3668,7 @@ SampleParams ws_params(const Workspace* w, uint32_t flags) {
   if (flags & KADABRA_FLAG_MEDIUM_TABLES) P.tier_flags |= TF_SKIP_S | TF_SKIP_B;
   if (flags & KADABRA_FLAG_LARGE_SHARED_TABLES) P.tier_flags |= TF_SKIP_S;
   if (flags & KADABRA_FLAG_WARP_TIER) P.tier_flags |= TF_WARP;
-  if (flags & (KADABRA_FLAG_ASYNC_SCAN | FLAG_RING_AUTO)) P.tier_flags |= TF_RING;
+  if (flags & (KADABRA_FLAG_ASYNC_SCAN | FLAG_VEC_AUTO)) P.tier_flags |= TF_VEC;
   if (flags & KADABRA_FLAG_FRONTIER_SEGMENTS) P.tier_flags |= TF_SEG64;
   return P;
 }
@@ -3716,11 +3693,11 @@ kadabra_status launch_sampler_kernels(Workspace* w, SampleParams P, cudaStream_t
     k_sample_warp<<<w->grid_warp, 32 * WT_WARPS, w->smem_warp, st>>>(P);
     KCK(cudaGetLastError());
   }
-  const bool rg = (P.tier_flags & TF_RING) != 0;
-  if (variant & 1)  // the small table has no ring variant
+  const bool rg = (P.tier_flags & TF_VEC) != 0;
+  if (variant & 1)  // the small table has no beyond-L2 variant
     k_sample<0, SMALL_HLOG><<<w->grid_small, NT, w->smem_small, st>>>(P);
   else if (rg)
-    k_sample<0, FAST_HLOG, true><<<w->grid_ring, NT, ring_smem_bytes(), st>>>(P);
+    k_sample<0, FAST_HLOG, true><<<w->grid_fast, NT, w->smem_fast, st>>>(P);
   else
     k_sample<0><<<w->grid_fast, NT, w->smem_fast, st>>>(P);
   KCK(cudaGetLastError());

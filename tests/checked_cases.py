@@ -1,7 +1,7 @@
 """Parity cases run against the KADABRA_CHECKED build of the library (test
 infrastructure; run in a child process by test_gpu_checked.py, since one
 process loads one build).  Every table tier, the one-warp tier, the
-async-copy scans and the segmented frontier scans are forced in turn on
+16-byte-load scans and the segmented frontier scans are forced in turn on
 undirected and directed graphs; per-sample results must equal the oracle's
 and no index check may fail (a failure makes the call return
 KADABRA_ERR_INTERNAL naming the check)."""

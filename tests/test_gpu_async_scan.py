@@ -1,9 +1,10 @@
-"""Variants of the level scans against the oracle (GPU only): the async-copy
-ring (KADABRA_FLAG_ASYNC_SCAN; taken by itself for graphs whose CSR exceeds
-the L2) and frontiers scanned in segments (KADABRA_FLAG_FRONTIER_SEGMENTS:
+"""Variants of the level scans against the oracle (GPU only): 16-byte loads
+along long row stretches (KADABRA_FLAG_ASYNC_SCAN; taken by itself for graphs
+whose CSR exceeds the L2; the star, Barabasi-Albert, R-MAT and Chung-Lu
+graphs have rows long enough, with heads at every 16-byte misalignment) and frontiers scanned in segments (KADABRA_FLAG_FRONTIER_SEGMENTS:
 64-node segments; by itself only for tier-B frontiers beyond 2048 nodes).
 Per-sample pairs, paths, work counters and statuses bit-exact, whole runs
-identical.  The R-MAT scale-24 tests cover the automatic ring on a graph
+identical.  The R-MAT scale-24 tests cover the automatic choice on a graph
 beyond the L2."""
 
 import numpy as np
@@ -53,8 +54,8 @@ GRAPHS = [
 def test_async_scan_sample_paths_match_oracle(kd, orc, gg, name, make):
     g = make(gg)
     ref = orc.sample_paths(g, 51, 0, 0, 3000, max_len=700)
-    for flag, tag in ((kd.FLAG_ASYNC_SCAN, "ring"),
-                      (kd.FLAG_ASYNC_SCAN | kd.FLAG_LARGE_SHARED_TABLES, "ring, tier B first")):
+    for flag, tag in ((kd.FLAG_ASYNC_SCAN, "vector"),
+                      (kd.FLAG_ASYNC_SCAN | kd.FLAG_LARGE_SHARED_TABLES, "vector, tier B first")):
         G = kd.kadabra_load_csr(g)
         try:
             G.set_flags(flag)
@@ -105,7 +106,7 @@ def test_frontier_segments_match_oracle(kd, orc, gg, name, make):
     g = make(gg)
     ref = orc.sample_paths(g, 61, 0, 0, 2000, max_len=700)
     for flag, tag in ((kd.FLAG_FRONTIER_SEGMENTS, "segments"),
-                      (kd.FLAG_FRONTIER_SEGMENTS | kd.FLAG_ASYNC_SCAN, "segments, ring"),
+                      (kd.FLAG_FRONTIER_SEGMENTS | kd.FLAG_ASYNC_SCAN, "segments, vector"),
                       (kd.FLAG_FRONTIER_SEGMENTS | kd.FLAG_LARGE_SHARED_TABLES, "segments, tier B")):
         G = kd.kadabra_load_csr(g)
         try:
