@@ -681,14 +681,19 @@ __device__ __forceinline__ void scan_level_regs(const Tables& T, int fcount, int
 // The level scan for graphs whose CSR does not fit in L2 (its loads wait on
 // HBM): each warp takes a contiguous slice of the flattened arc range.  A
 // stretch of at least 131 arcs inside one row (hub rows hold most arcs of a
-// power-law graph's touching level) is read with 16-byte loads, 128 arcs per
-// warp load, so a hub row takes a quarter of the dependent round trips; no
-// lane has to find its row there.  Elsewhere the warp takes windows of 32 arcs, keeping
+// power-law graph's touching level) is read with 16-byte loads, up to
+// VEC_DEPTH of them per lane at once (128 arcs per warp load), so a hub row
+// takes a sixteenth of the dependent round trips; no lane has to find its
+// row there.  Elsewhere the warp takes windows of 32 arcs, keeping
 // the current frontier row in registers; only lanes whose arc lies in a
 // later row search the frontier prefix.  For every arc it calls f(k, ok, p,
 // y): ok = the lane holds an arc, p = frontier position of its tail, y = its
 // head.  All lanes of the warp call f together (so f may use warp
 // collectives); the arcs come in no particular order.
+#ifndef KD_VEC_DEPTH
+#define KD_VEC_DEPTH 4
+#endif
+constexpr int VEC_DEPTH = KD_VEC_DEPTH;  // 16-byte loads in flight per lane in the beyond-L2 scan
 template <class F>
 __device__ __forceinline__ void scan_level_vec(const Tables& T, int fcount, int E, const int32_t* cols, int64_t ncols,
                                                 F f) {
@@ -712,17 +717,23 @@ __device__ __forceinline__ void scan_level_vec(const Tables& T, int fcount, int 
     const int room = min(nxt, c1) - wb;                // arcs of this row left in the slice
     const int64_t a0 = (int64_t)cur.y + (wb - cur.x);  // address of arc wb
     const int mis = (int)(((uintptr_t)(cols + a0) >> 2) & 3);  // 4-byte steps past a 16-byte boundary
-    int4 v = make_int4(0, 0, 0, 0);
+    int4 v[VEC_DEPTH];
+#pragma unroll
+    for (int d = 0; d < VEC_DEPTH; ++d) v[d] = make_int4(0, 0, 0, 0);
     int nk = 1, p = pcur;
     bool ok = false;
-    if (room >= 131 && mis == 0) {  // 128 arcs of one row: 16-byte loads
-      v = __ldg(reinterpret_cast<const int4*>(cols + KIDX(a0, ncols - 127, 8)) + lane);
+    if (room >= 131 && mis == 0) {  // 128 arcs of one row (or more): 16-byte loads
+      const int nd = min(VEC_DEPTH, room >> 7);
+      const int4* src = reinterpret_cast<const int4*>(cols + KIDX(a0, ncols - 127, 8)) + lane;
+#pragma unroll
+      for (int d = 0; d < VEC_DEPTH; ++d)
+        if (d < nd) v[d] = __ldg(src + 32 * d);
       ok = true;
-      nk = 4;
-      wb += 128;
+      nk = 4 * nd;
+      wb += 128 * nd;
     } else if (room >= 131) {  // up to 3 arcs to the next 16-byte boundary
       ok = lane < 4 - mis;
-      if (ok) v.x = __ldg(&cols[KIDX(a0 + lane, ncols, 8)]);
+      if (ok) v[0].x = __ldg(&cols[KIDX(a0 + lane, ncols, 8)]);
       wb += 4 - mis;
     } else {  // a window of 32 arcs, perhaps across rows
       const int e = wb + lane;
@@ -732,13 +743,21 @@ __device__ __forceinline__ void scan_level_vec(const Tables& T, int fcount, int 
           p = frontier_next(T.pr, pcur + 1, fcount, e);
           q = T.pr[KIDX(p, T.frcap + 1, 7)];
         }
-        v.x = __ldg(&cols[KIDX((int64_t)q.y + (e - q.x), ncols, 8)]);
+        v[0].x = __ldg(&cols[KIDX((int64_t)q.y + (e - q.x), ncols, 8)]);
         ok = true;
       }
       wb += 32;
     }
 #pragma unroll 1
-    for (int k = 0; k < nk; ++k) f(k, ok, p, k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w);
+    for (int k = 0; k < nk; ++k) {
+      int y = 0;
+#pragma unroll
+      for (int d = 0; d < VEC_DEPTH; ++d) {
+        const int4 w = v[d];
+        if ((k >> 2) == d) y = (k & 3) == 0 ? w.x : (k & 3) == 1 ? w.y : (k & 3) == 2 ? w.z : w.w;
+      }
+      f(k & 3, ok, p, y);
+    }
   }
 }
 
@@ -1510,10 +1529,11 @@ __device__ void reset_tables(const Tables& T, Ctl& c, bool whole) {
   __syncthreads();
 }
 
-// global-memory tiers share one body compiled once, outside the kernel
+// global-memory tiers share one body per scan kind, compiled outside the kernel
+template <bool RG>
 __device__ __noinline__ void run_sample_global(const SampleParams& P, const Job& J, const Tables& T, Ctl& c,
                                                uint64_t idx, int64_t out_i) {
-  run_sample<false>(P, J, T, c, idx, out_i);
+  run_sample<false, RG>(P, J, T, c, idx, out_i);
 }
 
 // layout of one CTA's tables in global memory (tiers M and L)
@@ -1683,7 +1703,7 @@ __device__ void clear_path_row(const SampleParams& P, int64_t out_i) {
 template <int MODE, int SHL = FAST_HLOG, bool RG = false>
 __global__ void __launch_bounds__(NT, MODE != 0 ? 2 : SHL == FAST_HLOG ? KD_MIN_BLOCKS : KD_MIN_BLOCKS + 1)
     k_sample(SampleParams P) {
-  static_assert(!RG || (MODE == 0 && SHL == FAST_HLOG), "the beyond-L2 scan has a tier-S instance only");
+  static_assert(!RG || SHL == FAST_HLOG, "the beyond-L2 scan has no small-table instance");
   extern __shared__ __align__(16) unsigned char smem[];
   Ctl& c = *reinterpret_cast<Ctl*>(smem);
   Tables TS, TM;
@@ -1768,7 +1788,7 @@ __global__ void __launch_bounds__(NT, MODE != 0 ? 2 : SHL == FAST_HLOG ? KD_MIN_
       }
       if (!done && !(P.tier_flags & TF_SKIP_M)) {
         clear_path_row(P, out_i);
-        run_sample_global(P, c.job, TM, c, idx, out_i);
+        run_sample_global<RG>(P, c.job, TM, c, idx, out_i);
         __syncthreads();
         done = c.flags != F_CAP;
         reset_tables<false>(TM, c, false);
@@ -1780,7 +1800,7 @@ __global__ void __launch_bounds__(NT, MODE != 0 ? 2 : SHL == FAST_HLOG ? KD_MIN_
       }
     } else {
       clear_path_row(P, out_i);
-      run_sample_global(P, c.job, TM, c, idx, out_i);
+      run_sample_global<RG>(P, c.job, TM, c, idx, out_i);
       __syncthreads();
       reset_tables<false>(TM, c, false);
     }
@@ -3548,6 +3568,8 @@ kadabra_status ensure_ws(Workspace* w, uint64_t deferred_need, int njobs) {
     w->grid_warp = w->num_sms * std::max(per_sm, 1);
     w->smem_big = big_smem_bytes();
     KCK(cudaFuncSetAttribute(k_sample<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->smem_big));
+    KCK(cudaFuncSetAttribute(k_sample<2, FAST_HLOG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)w->smem_big));
     KCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample<2>, NT, w->smem_big));
     if (per_sm < 1) return fail(KADABRA_ERR_CAPACITY, "large-table sampler does not fit on an SM");
     w->grid_big = w->num_sms * per_sm;
@@ -3701,11 +3723,17 @@ kadabra_status launch_sampler_kernels(Workspace* w, SampleParams P, cudaStream_t
   else
     k_sample<0><<<w->grid_fast, NT, w->smem_fast, st>>>(P);
   KCK(cudaGetLastError());
-  k_sample<2><<<w->grid_big, NT, w->smem_big, st>>>(P);  // tier B: register scans
+  if (rg)  // tier B (and M): the scan kind of tier S
+    k_sample<2, FAST_HLOG, true><<<w->grid_big, NT, w->smem_big, st>>>(P);
+  else
+    k_sample<2><<<w->grid_big, NT, w->smem_big, st>>>(P);
   KCK(cudaGetLastError());
   P.pi_base = w->pi_gm;
   P.pcap = w->pcap_gm;
-  k_sample<1><<<w->grid_gm, NT, sizeof(Ctl), st>>>(P);
+  if (rg)
+    k_sample<1, FAST_HLOG, true><<<w->grid_gm, NT, sizeof(Ctl), st>>>(P);
+  else
+    k_sample<1><<<w->grid_gm, NT, sizeof(Ctl), st>>>(P);
   KCK(cudaGetLastError());
   return KADABRA_OK;
 }
