@@ -57,7 +57,7 @@ METRIC = "paths/sec & time-to-(lambda,delta) per graph, batched vs plain on GPU;
 WORKLOADS = {
     "chung_lu_1m": dict(family="chung_lu", n=1_000_000, beta=2.5, mean_deg=16.0, max_deg=10_000.0, graph_seed=1,
                         lcc=True, lam=0.005, delta=0.1, check_interval=1 << 16,
-                        sampler_dram_bytes=80_739_328 + 7_304_960 + 46_139_648 + 1_922_560 + 65_792),
+                        sampler_dram_bytes=82_563_584 + 7_809_280 + 13_459_200 + 3_840 + 66_304),
     "erdos_renyi_2k": dict(family="erdos_renyi", n=2000, mean_deg=8.0, graph_seed=1, lcc=True, lam=0.01,
                            delta=0.1, check_interval=1000, sampler_dram_bytes=None),
     "rmat_24": dict(family="rmat", scale=24, edge_factor=16, a=0.57, b=0.19, c=0.19, graph_seed=1, lam=0.0025,
@@ -65,7 +65,7 @@ WORKLOADS = {
     # the scale-22 graph of the same recipe: the size the ncu counters are captured at
     "rmat_22": dict(family="rmat", scale=22, edge_factor=16, a=0.57, b=0.19, c=0.19, graph_seed=1, lam=0.0025,
                     delta=0.1, check_interval=1 << 16,
-                    sampler_dram_bytes=688_819_712 + 36_917_248 + 495_883_520 + 205_097_472 + 60_928),
+                    sampler_dram_bytes=701_204_736 + 39_124_992 + 126_966_272 + 34_907_904 + 66_560),
     "rmat_24_topk": dict(family="rmat", scale=24, edge_factor=16, a=0.57, b=0.19, c=0.19, graph_seed=1, lam=0.0025,
                          delta=0.1, check_interval=1 << 16, sampler_dram_bytes=None, k=10),
 }
