@@ -400,6 +400,33 @@ struct SampleParams {
 };
 
 // per-CTA control block in shared memory
+// Long rows of a level (the scan variant for graphs beyond the L2 only).
+// Every arc that can touch joins the two current frontiers, so a frontier
+// row x of deg arcs holds a touch arc for each node of the other frontier
+// (k nodes) that it contains.  Rows are sorted, so k searches in the row
+// find them all; pass 1 takes them instead of scanning the row when
+// deg > k * log2(deg) * W / 16.  A search's loads depend on one another while
+// a scan streams, so W = 16 (measured: R-MAT scale 22, W = 4, 8, 16 gave
+// 2.70, 2.61, 2.52 ms per batch against 2.98 ms with no searches; on the
+// L2-resident Chung-Lu graph searches gained nothing and the extra code cost
+// 4 %).  Up to one row per 32 nodes of a frontier segment and LONG_CAP in
+// all; the work counter still counts every arc.
+#ifndef KD_LONG_CAP
+#define KD_LONG_CAP 32
+#endif
+#ifndef KD_MEMB_W
+#define KD_MEMB_W 16
+#endif
+#ifndef KD_LONG_MIN
+#define KD_LONG_MIN 32
+#endif
+constexpr int LONG_CAP = KD_LONG_CAP;
+__device__ __forceinline__ bool row_is_long(int deg, int k) {
+  if (KD_MEMB_W <= 0 || k <= 0 || deg < KD_LONG_MIN) return false;
+  const int lg = 32 - __clz(deg);  // bits of deg: the search steps
+  return (long long)deg * 16 > (long long)k * lg * KD_MEMB_W;
+}
+
 struct Ctl {
   Job job;        // the job of the current sample
   int job_id;
@@ -421,6 +448,11 @@ struct Ctl {
   int flags;
   int side;
   int fside, fdepth;  // the frontier the filter in T.bits was built for (fside -1: none)
+  int nlong;           // frontier rows of the current segment searched instead of scanned
+  long long ldeg_sum;  //   and their arcs (for the work counter)
+  int lrow[LONG_CAP];  //   segment position, row start and degree of each
+  int lrs[LONG_CAP];
+  int ldeg[LONG_CAP];
   int ecount;
   int done;       // 0 = continue, 1 = touch, 2 = disconnected
   int bt_flag;    // backtracking: an invariant failed at this step
@@ -559,6 +591,66 @@ __device__ __forceinline__ int lower_bound_row(const int32_t* col, int a, int b,
       b = mid;
   }
   return a;
+}
+
+// One round of a four-way lower-bound search: pivots v1..v3 at a + s,
+// a + 2s, a + 3s (s = (b - a) / 4 > 0) narrow [a, b] to a quarter.
+__device__ __forceinline__ void lb4_update(int& a, int& b, int s, int32_t v1, int32_t v2, int32_t v3, int32_t y) {
+  if (v3 < y) {
+    a += 3 * s + 1;
+  } else if (v2 < y) {
+    b = a + 3 * s;
+    a += 2 * s + 1;
+  } else if (v1 < y) {
+    b = a + 2 * s;
+    a += s + 1;
+  } else {
+    b = a + s;
+  }
+}
+
+// First positions of y0 in the sorted row col[a0, b0) and of y1 in
+// col[a1, b1) (the row end if absent), searched together: each round loads
+// three pivots of each range, six independent loads, and narrows both
+// four-fold, so a 10^4-arc row takes seven rounds of one L2 round trip each
+// instead of fourteen dependent loads per search.
+__device__ __forceinline__ void lower_bound_rows2(const int32_t* col, int& a0, int b0, int32_t y0, int& a1, int b1,
+                                                  int32_t y1) {
+  for (;;) {
+    const bool w0 = b0 - a0 > 3, w1 = b1 - a1 > 3;
+    if (!w0 && !w1) break;
+    const int s0 = (b0 - a0) >> 2, s1 = (b1 - a1) >> 2;
+    int32_t u1 = 0, u2 = 0, u3 = 0, v1 = 0, v2 = 0, v3 = 0;
+    if (w0) {
+      u1 = __ldg(&col[a0 + s0]);
+      u2 = __ldg(&col[a0 + 2 * s0]);
+      u3 = __ldg(&col[a0 + 3 * s0]);
+    }
+    if (w1) {
+      v1 = __ldg(&col[a1 + s1]);
+      v2 = __ldg(&col[a1 + 2 * s1]);
+      v3 = __ldg(&col[a1 + 3 * s1]);
+    }
+    if (w0) lb4_update(a0, b0, s0, u1, u2, u3, y0);
+    if (w1) lb4_update(a1, b1, s1, v1, v2, v3, y1);
+  }
+  while (a0 < b0 || a1 < b1) {  // at most two more rounds
+    const int m0 = (a0 + b0) >> 1, m1 = (a1 + b1) >> 1;
+    const bool w0 = a0 < b0, w1 = a1 < b1;
+    const int32_t u = w0 ? __ldg(&col[m0]) : 0, v = w1 ? __ldg(&col[m1]) : 0;
+    if (w0) {
+      if (u < y0)
+        a0 = m0 + 1;
+      else
+        b0 = m0;
+    }
+    if (w1) {
+      if (v < y1)
+        a1 = m1 + 1;
+      else
+        b1 = m1;
+    }
+  }
 }
 
 // lower_bound over a sorted row by one warp: 32 pivots per round narrow the
@@ -980,6 +1072,78 @@ __device__ void bt_warp_steps(const SampleParams& P, const Job& J, const Tables&
   }
 }
 
+// The touch arcs of the long rows of a frontier segment (c.lrow.., nl of
+// them): item q = (row q / kother, node q % kother of the other frontier,
+// list entries [ob, ob + kother)); a thread searches two items at a time.
+// Appends them to the warp's candidate segment like the scan does (npi,
+// sigma_of as there).  All lanes of every warp call it.
+#ifdef KD_MEMB_NOINLINE
+#define KD_MEMB_ATTR __device__ __noinline__
+#else
+#define KD_MEMB_ATTR __device__ __forceinline__
+#endif
+template <bool PK>
+KD_MEMB_ATTR void search_long_rows(const Tables& T, const Ctl& c, const int32_t* cols, int64_t m, int fb, int ob,
+                                   int kother, int nl, PiEntry* seg, int& npi, bool& sigma_of) {
+  const int lane = lane_id(), wid = warp_id();
+  const long long items = (long long)nl * kother;
+  auto emit = [&](bool touch, int32_t xnode, int32_t y, unsigned long long wgt) {
+    const unsigned msk = __ballot_sync(FULL, touch);
+    if (touch) {
+      const int at = npi + __popc(msk & ((1u << lane) - 1u));
+      if (at < T.pcap) {
+        seg[at].x = xnode;
+        seg[at].y = y;
+        seg[at].w = wgt;
+      }
+    }
+    npi += __popc(msk);
+  };
+  for (long long qb = (long long)wid * 32; qb < items; qb += 2 * NT) {
+    int r[2], a[2], e[2];
+    uint32_t py[2];
+    unsigned long long hy[2];
+    int32_t y[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const long long q = qb + h * NT + lane;
+      r[h] = -1;
+      a[h] = e[h] = 0;
+      y[h] = 0;
+      py[h] = 0;
+      hy[h] = 0;
+      if (q < items) {
+        r[h] = (int)(q / kother);
+        const int yi = (int)(q - (long long)r[h] * kother);
+        py[h] = lpos_get<PK>(T, ob + yi);
+        hy[h] = T.hkv[KIDX(py[h], T.hmask + 1u, 14)];
+        y[h] = (int32_t)(hy[h] >> 32);
+        a[h] = c.lrs[r[h]];
+        e[h] = a[h] + c.ldeg[r[h]];
+      }
+    }
+    int b0 = e[0], b1 = e[1];
+    lower_bound_rows2(cols, a[0], b0, y[0], a[1], b1, y[1]);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      bool touch = false;
+      unsigned long long wgt = 0;
+      int32_t xnode = 0;
+      if (r[h] >= 0 && a[h] < e[h] && __ldg(&cols[KIDX((int64_t)a[h], m, 8)]) == y[h]) {
+        touch = true;
+        const uint32_t px = lpos_get<PK>(T, fb + c.lrow[r[h]]);
+        const unsigned long long hx = T.hkv[px];
+        const unsigned long long sx = ent_sig<PK>(T, hx, px);
+        const unsigned long long sy = ent_sig<PK>(T, hy[h], py[h]);
+        wgt = sx * sy;
+        if (__umul64hi(sx, sy) != 0ull) sigma_of = true;
+        xnode = (int32_t)(hx >> 32);
+      }
+      emit(touch, xnode, y[h], wgt);
+    }
+  }
+}
+
 template <bool PK, bool RG = false>
 __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, const Tables& T, Ctl& c, uint64_t idx,
                                            int64_t out_i) {
@@ -1026,6 +1190,8 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
     c.depth[0] = 0;
     c.depth[1] = 0;
     c.fside = -1;
+    c.nlong = 0;
+    c.ldeg_sum = 0;
     c.cost[0] = G.rp[s + 1] - G.rp[s];
     c.cost[1] = G.rrp[t + 1] - G.rrp[t];
   }
@@ -1070,7 +1236,12 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
     // T.frcap nodes (tier B) is scanned in segments of T.frcap: the touch
     // test and the insertion treat a level's arcs as a set, so segments give
     // the same result.
-    auto build_prefix = [&](int fb, int cnt, bool count_edges) {
+    // With kother > 0 (pass 1), rows that row_is_long picks for searches of
+    // the other frontier's kother nodes go to c.lrow.. (long_cap at most:
+    // one per 32 nodes of a segment, up to LONG_CAP; c.nlong must be 0) and
+    // count 0 arcs in the prefix.
+    const int long_cap = min(LONG_CAP, max(1, T.frcap >> 5));
+    auto build_prefix = [&](int fb, int cnt, bool count_edges, int kother) {
       int carry = 0;
       for (int base = 0; base < cnt; base += NT) {
         const int i = base + tid;
@@ -1079,6 +1250,16 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
           const int x = KIDX(list_node<PK>(T, fb + i), G.n, 9);
           rs = __ldg(&rowp[x]);
           deg = __ldg(&rowp[x + 1]) - rs;
+          if (row_is_long(deg, kother)) {
+            const int q = atomicAdd(&c.nlong, 1);
+            if (q < long_cap) {
+              c.lrow[q] = i;
+              c.lrs[q] = rs;
+              c.ldeg[q] = deg;
+              atomicAdd(reinterpret_cast<unsigned long long*>(&c.ldeg_sum), (unsigned long long)deg);
+              deg = 0;
+            }
+          }
         }
         int tot;
         const int ex = block_exscan(deg, c.scan_tmp, &tot);
@@ -1088,7 +1269,7 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
       if (tid == 0) {
         T.pr[KIDX(cnt, T.frcap + 1, 10)] = make_int2(carry, 0);
         c.ecount = carry;
-        if (count_edges) c.stat[KADABRA_STAT_EDGES] += carry;
+        if (count_edges) c.stat[KADABRA_STAT_EDGES] += carry + c.ldeg_sum;
       }
       __syncthreads();
       return c.ecount;
@@ -1098,13 +1279,30 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
 
     // pass 1: touch test against the other search
     int pass1_bad = 0;
+    bool had_long = false;  // pass 1 searched rows that pass 2 must scan
     {
       int npi = 0;
       bool sigma_of = false;
       PiEntry* seg = T.pi + (size_t)wid * T.pcap;
+      // appends the warp's touch arcs (x, y) of weight sigma_x * sigma_y
+      auto emit = [&](bool touch, int32_t xnode, int32_t y, unsigned long long wgt) {
+        const unsigned m = __ballot_sync(FULL, touch);
+        if (touch) {
+          const int at = npi + __popc(m & ((1u << lane) - 1u));
+          if (at < T.pcap) {
+            seg[at].x = xnode;
+            seg[at].y = y;
+            seg[at].w = wgt;
+          }
+        }
+        npi += __popc(m);
+      };
+      // the other side's current frontier: the only nodes a touch arc reaches
+      const int ob = lvl_lo(T, 1 - side, c.depth[1 - side]);
+      const int kother = lvl_hi(T, 1 - side, c.depth[1 - side]) - ob;
       for (int sg = 0; sg < nseg; ++sg) {
       const int fb = f0 + sg * T.frcap, cnt = min(T.frcap, fcount - sg * T.frcap);
-      E = build_prefix(fb, cnt, true);
+      E = build_prefix(fb, cnt, true, RG ? kother : 0);
       scan_level<RG>(T, c, cnt, E, cols, G.m, [&](int, bool ok, int p, int y) {
         bool touch = false;
         unsigned long long wgt = 0;
@@ -1123,18 +1321,24 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
             xnode = (int32_t)(hx >> 32);
           }
         }
-        const unsigned m = __ballot_sync(FULL, touch);
-        if (touch) {
-          const int at = npi + __popc(m & ((1u << lane) - 1u));
-          if (at < T.pcap) {
-            seg[at].x = xnode;
-            seg[at].y = y;
-            seg[at].w = wgt;
-          }
-        }
-        npi += __popc(m);
+        emit(touch, xnode, y, wgt);
       });
-      if (sg + 1 < nseg) __syncthreads();  // the next segment's prefix overwrites T.pr
+      // the long rows: one search per (row, other-frontier node)
+      if constexpr (RG) {
+        const int nl = min(c.nlong, long_cap);
+        if (nl > 0) {
+          had_long = true;
+          search_long_rows<PK>(T, c, cols, G.m, fb, ob, kother, nl, seg, npi, sigma_of);
+        }
+      }
+      if (sg + 1 < nseg) {
+        __syncthreads();  // the next segment's prefix overwrites T.pr and the long rows
+        if (tid == 0) {
+          c.nlong = 0;
+          c.ldeg_sum = 0;
+        }
+        __syncthreads();
+      }
       }
       int bad = 0;
       if (__any_sync(FULL, sigma_of) && lane == 0) {
@@ -1163,6 +1367,10 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
       }
     }
     __syncthreads();
+    if (tid == 0) {  // every thread has passed its last read of the long rows
+      c.nlong = 0;
+      c.ldeg_sum = 0;
+    }
     if (pass1_bad) return;
     if (c.done) break;
 
@@ -1183,7 +1391,8 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
       const volatile int* nlist_now = &c.nlist;
       for (int sg = 0; sg < nseg; ++sg) {
       const int fb = f0 + sg * T.frcap, cnt = min(T.frcap, fcount - sg * T.frcap);
-      if (nseg > 1) E = build_prefix(fb, cnt, false);  // one segment: pass 1's prefix is still there
+      // one segment without long rows: pass 1's prefix is still there
+      if (nseg > 1 || had_long) E = build_prefix(fb, cnt, false, 0);
       scan_level<RG>(T, c, cnt, E, cols, G.m, [&](int, bool ok, int p, int y) {
         if (!ok || cap) return;
         // the head's row bounds (its degree joins the new frontier's cost if

@@ -152,6 +152,22 @@ def test_global_tables_er_and_power_law(kd, orc, er2000, chung_lu_1m):
                          flag=kd.FLAG_LARGE_SHARED_TABLES)
 
 
+def test_searched_rows_match_oracle(kd, orc, gg):
+    """A dense Barabasi-Albert graph (n = 2000, 30 arcs per new node) with the
+    scan for graphs beyond the L2 forced on: frontier rows that are long next
+    to a small other frontier are searched for that frontier's nodes instead
+    of scanned, and levels that searched rows without a touch are scanned
+    again to insert.  Every table tier; with 64-node frontier segments a
+    segment takes two searched rows at most, so levels with more scan the
+    rest.  The default scan (no searches) gives the same samples."""
+    g = gg.barabasi_albert(2000, 30, 3)
+    compare_paths(kd, orc, g, 41, 0, 0, 3000, tag="ba2000x30")
+    for flag, tag in ((0, "searched rows"), (kd.FLAG_LARGE_SHARED_TABLES, "large-shared"),
+                      (kd.FLAG_MEDIUM_TABLES, "medium"), (kd.FLAG_GLOBAL_TABLES, "global"),
+                      (kd.FLAG_FRONTIER_SEGMENTS, "segments")):
+        compare_paths_global(kd, orc, g, 42, 0, 0, 1500, tag="ba2000x30/" + tag, flag=flag | kd.FLAG_ASYNC_SCAN)
+
+
 def test_run_with_forced_tiers_matches_plain(kd, er2000):
     """Whole runs give identical results whichever table tier holds the samples."""
     out = []
