@@ -193,6 +193,12 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# What the algorithmic bytes count (reported beside each roofline)
+BYTES_BASIS = ("work counters of the paper's search: every arc of each expanded row and every adjacency position "
+               "up to each backtracking pick; the kernel reads fewer (bisected backtracking steps, and on graphs "
+               "beyond L2 long touching-level rows searched instead of scanned)")
+
+
 def algorithmic_bytes(totals, hits):
     """Bytes the sampler must touch (per batch): 8 B per expanded node (two
     offsets), 4 B per scanned arc (adjacency) + 4 B per scanned arc (visited
@@ -507,7 +513,7 @@ def rmat24_roofline(kd, launches: int = 4):
         return {"workload": workload_name(), "nodes": int(g.n), "arcs": int(g.m), "bound": "hbm",
                 "achieved": by / t / 1e9, "peak": peak, "unit": "GB/s", "frac": by / t / 1e9 / peak,
                 "traffic": WORKLOAD["sampler_dram_bytes"], "bytes_per_launch": by, "launch_ms": 1e3 * t,
-                "samples_per_launch": K, "paths_per_s": K / t, "peak_source": src}
+                "samples_per_launch": K, "paths_per_s": K / t, "peak_source": src, "bytes_basis": BYTES_BASIS}
     finally:
         WORKLOAD = saved
 
@@ -878,7 +884,7 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": w["sampler_dram_bytes"], "kernel": "k_sample (sampler batch)",
                          "bytes_per_launch": avg_b, "launch_ms": 1e3 * avg_t, "samples_per_launch": K,
-                         "peak_source": peak_src},
+                         "peak_source": peak_src, "bytes_basis": BYTES_BASIS},
             "e2e": {"value": e2e_value, "unit": "paths/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
         }

@@ -89,10 +89,11 @@ typedef struct {
   void* stream;            /* cudaStream_t for all work of the call (NULL = default) */
   int32_t ctas_per_sm;     /* shared-memory sampler tier, as resident CTAs per SM: 0 =
                               autotuned per graph (on the first one-graph run a probe
-                              batch of min(K, 4096) samples times every allowed setup
+                              batch of min(K, 16384) samples times every allowed setup
                               of table and warp tier; the choice is cached per graph
                               fingerprint), or one of the two values the library
-                              offers (4: 4096-slot tables, 5: 2048-slot on GB300);
+                              offers (4: 4096-slot tables, lists of 3072 nodes; 5:
+                              the compact layout, lists of 2048 nodes; on GB300);
                               any other value is KADABRA_ERR_ARG.  Results do not
                               depend on it.  A batch run tunes it on its largest
                               graph; serving uses the default.                    */
@@ -273,8 +274,9 @@ kadabra_status kadabra_graph_info(const kadabra_graph* g, int32_t* n, int64_t* m
  * graphs.
  * KADABRA_FLAG_FRONTIER_SEGMENTS makes the shared-memory tables scan every
  * frontier in segments of 64 nodes, as they do for frontiers beyond their
- * frontier array (2048 nodes); it exists to test that path and only slows
- * sampling.  No flag changes a result.  Returns KADABRA_ERR_ARG for unknown
+ * frontier array (1024 nodes, 512 in the compact tier-S layout), and
+ * to take at most two searched long rows per segment; it exists to test
+ * those paths and only slows sampling.  No flag changes a result.  Returns KADABRA_ERR_ARG for unknown
  * bits. */
 enum {
   KADABRA_FLAG_GLOBAL_TABLES = 1,

@@ -103,7 +103,6 @@ constexpr int U = KD_U;            // independent items per thread per step (mem
 // (tier L).  Every tier gives the same result.
 constexpr int FAST_HLOG = KD_FAST_HLOG;        // tier S: 2^FAST_HLOG hash slots
 constexpr int BIG_HLOG = FAST_HLOG + 1;        // tier B: twice as many
-constexpr int SMALL_HLOG = FAST_HLOG - 1;      // tier S, small variant: half the slots, one more CTA per SM
 #ifndef KD_FAST_MAXD
 #define KD_FAST_MAXD 126
 #endif
@@ -197,6 +196,7 @@ struct Tables {
   int lcap;
   int frcap;                // frontier nodes per scan segment (the frontier array's capacity)
   uint32_t* bits;           // filter of the other side's frontier (shared-memory tiers), else null
+  int fwords, fshift;       //   its 32-bit words and 32 - log2(its bits)
   int* lvl;                 // [side][lo|hi][maxd+2]
   int maxd;
   PiEntry* pi;              // 2*NW segments of pcap entries (the second half is scratch)
@@ -286,11 +286,11 @@ __device__ __forceinline__ uint32_t hash_pos(int32_t v, int hlog) {
 #ifndef KD_FILTER_LOG
 #define KD_FILTER_LOG 15
 #endif
-constexpr int FILTER_LOG = KD_FILTER_LOG;
-constexpr int FILTER_WORDS = (1 << FILTER_LOG) / 32;
-__device__ __forceinline__ uint32_t filter_slot(int32_t v) { return ((uint32_t)v * 0x9E3779B1u) >> (32 - FILTER_LOG); }
-__device__ __forceinline__ bool filter_has(const uint32_t* bits, int32_t v) {
-  const uint32_t h = filter_slot(v);
+constexpr int FILTER_LOG = KD_FILTER_LOG;  // the default layout's filter: 2^FILTER_LOG bits
+// fshift = 32 - log2(the filter's bits)
+__device__ __forceinline__ uint32_t filter_slot(int32_t v, int fshift) { return ((uint32_t)v * 0x9E3779B1u) >> fshift; }
+__device__ __forceinline__ bool filter_has(const uint32_t* bits, int32_t v, int fshift) {
+  const uint32_t h = filter_slot(v, fshift);
   return (bits[h >> 5] >> (h & 31)) & 1u;
 }
 
@@ -410,7 +410,8 @@ struct SampleParams {
 // 2.70, 2.61, 2.52 ms per batch against 2.98 ms with no searches; on the
 // L2-resident Chung-Lu graph searches gained nothing and the extra code cost
 // 4 %).  Up to one row per 32 nodes of a frontier segment and LONG_CAP in
-// all; the work counter still counts every arc.
+// all (16 rows in all measured 2 % slower on R-MAT scale 22); the work
+// counter still counts every arc.
 #ifndef KD_LONG_CAP
 #define KD_LONG_CAP 32
 #endif
@@ -1217,10 +1218,10 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
       // the filter of the other side's frontier, unless it is still current
       const int os = 1 - side, od = c.depth[os];
       if (c.fside != os || c.fdepth != od) {
-        for (int i = tid; i < FILTER_WORDS; i += NT) T.bits[i] = 0u;
+        for (int i = tid; i < T.fwords; i += NT) T.bits[i] = 0u;
         __syncthreads();
         for (int i = lvl_lo(T, os, od) + tid; i < lvl_hi(T, os, od); i += NT) {
-          const uint32_t h = filter_slot(list_node<PK>(T, i));
+          const uint32_t h = filter_slot(list_node<PK>(T, i), T.fshift);
           atomicOr(&T.bits[h >> 5], 1u << (h & 31));
         }
         __syncthreads();
@@ -1307,7 +1308,7 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
         bool touch = false;
         unsigned long long wgt = 0;
         int32_t xnode = 0;
-        if (ok && (!PK || filter_has(T.bits, y))) {
+        if (ok && (!PK || filter_has(T.bits, y, T.fshift))) {
           unsigned long long hy = 0;
           const int pos = tab_probe(T, y, &hy);
           if (pos >= 0 && val_side(ent_val<PK>(hy)) != side) {
@@ -1776,14 +1777,17 @@ __device__ inline Tables gm_tables(unsigned char* base, int hlog, int lcap, int 
   T.frcap = lcap;
   T.lpos16 = nullptr;
   T.bits = nullptr;
+  T.fwords = 0;
+  T.fshift = 32;
   T.maxd = maxd;
   return T;
 }
 
-// shared-memory layout of a packed tier with 2^HLOG hash slots and lists of
-// 3/4 * 2^HLOG hash positions, after the control block.  A frontier is scanned
-// in segments of at most FRONTIER_SEG nodes (the frontier array's capacity);
-// the scan variant for graphs beyond the L2 has the same layout.
+// shared-memory layout of a packed tier after the control block: 2^HLOG
+// hash slots, lists of LQ quarters of the slots (hash positions), frontier
+// segments of FSEG nodes (the frontier array's capacity), a 2^FLOG-bit
+// filter and MAXD levels per side.  The scan variant for graphs beyond the
+// L2 has the same layout.
 #ifndef KD_FRONTIER_SEG
 #define KD_FRONTIER_SEG 1024
 #endif
@@ -1791,28 +1795,41 @@ constexpr int FRONTIER_SEG = KD_FRONTIER_SEG;
 #ifndef KD_LOAD_QUARTERS
 #define KD_LOAD_QUARTERS 3
 #endif
-template <int HLOG>
+template <int HLOG, int LQ, int FSEG, int FLOG, int MAXD>
 struct SLayout {
-  // nodes a table takes before the sample moves on to the next tier:
-  // KD_LOAD_QUARTERS quarters of the slots (the probes stay short)
-  static constexpr int LCAP = (KD_LOAD_QUARTERS << HLOG) / 4;
+  static constexpr int SLOTS_LOG = HLOG;
+  // nodes a table takes before the sample moves on to the next tier (the
+  // probes stay short)
+  static constexpr int LCAP = (LQ << HLOG) / 4;
   static_assert(LCAP + NT < (1 << HLOG), "a full list leaves free slots");
-  static constexpr int FRCAP = LCAP < FRONTIER_SEG ? LCAP : FRONTIER_SEG;
+  static constexpr int FRCAP = LCAP < FSEG ? LCAP : FSEG;
+  static constexpr int FWORDS = (1 << FLOG) / 32;
+  static constexpr int FSHIFT = 32 - FLOG;
+  static constexpr int LEVELS = MAXD;
+  static_assert(MAXD <= 126, "the packed entry's dist field");
   static constexpr size_t HKV = (sizeof(Ctl) + 15) & ~size_t(15);
   static constexpr size_t PR = HKV + (sizeof(unsigned long long) << HLOG);
   static constexpr size_t LPOS = PR + sizeof(int2) * (FRCAP + 1);
   static constexpr size_t LVL = LPOS + sizeof(uint16_t) * LCAP;
-  static constexpr size_t BITS = (LVL + sizeof(int) * 4 * (FAST_MAXD + 2) + 15) & ~size_t(15);
-  static constexpr size_t BYTES = BITS + sizeof(uint32_t) * FILTER_WORDS;
+  static constexpr size_t BITS = (LVL + sizeof(int) * 4 * (MAXD + 2) + 15) & ~size_t(15);
+  static constexpr size_t BYTES = BITS + sizeof(uint32_t) * FWORDS;
   static_assert(HLOG <= 16, "16-bit list positions");
   // the radix selection's histogram (256 u64 + 256 u32) in the frontier array
   static_assert(sizeof(int2) * (FRCAP + 1) >= 256 * (sizeof(unsigned long long) + sizeof(unsigned)),
                 "frontier array holds the selection histogram");
 };
+// tier S at KD_MIN_BLOCKS CTAs per SM; tier S compact (one more CTA per SM:
+// half-full lists, 512-node segments, a 2^14-bit filter, 46 levels per
+// side); tier B (twice the slots, two CTAs per SM)
+using FastLayout = SLayout<FAST_HLOG, KD_LOAD_QUARTERS, FRONTIER_SEG, FILTER_LOG, FAST_MAXD>;
+using CompactLayout = SLayout<FAST_HLOG, 2, 512, 14, 46>;
+using BigLayout = SLayout<BIG_HLOG, KD_LOAD_QUARTERS, FRONTIER_SEG, FILTER_LOG, FAST_MAXD>;
+// the tier-S layout a k_sample instance uses (SL)
+constexpr int SL_FAST = 0;
+constexpr int SL_COMPACT = 1;
 
-template <int HLOG>
+template <class L>
 __device__ inline Tables smem_tables(unsigned char* smem) {
-  using L = SLayout<HLOG>;
   Tables T;
   T.hkv = reinterpret_cast<unsigned long long*>(smem + L::HKV);
   T.hsig = nullptr;  // packed entries
@@ -1822,11 +1839,13 @@ __device__ inline Tables smem_tables(unsigned char* smem) {
   T.lpos16 = reinterpret_cast<uint16_t*>(smem + L::LPOS);
   T.lvl = reinterpret_cast<int*>(smem + L::LVL);
   T.bits = reinterpret_cast<uint32_t*>(smem + L::BITS);
-  T.hlog = HLOG;
-  T.hmask = (1u << HLOG) - 1u;
+  T.fwords = L::FWORDS;
+  T.fshift = L::FSHIFT;
+  T.hlog = L::SLOTS_LOG;
+  T.hmask = (1u << L::SLOTS_LOG) - 1u;
   T.lcap = L::LCAP;
   T.frcap = L::FRCAP;
-  T.maxd = FAST_MAXD;
+  T.maxd = L::LEVELS;
   return T;
 }
 
@@ -1904,22 +1923,22 @@ __device__ void clear_path_row(const SampleParams& P, int64_t out_i) {
 // MODE 0: every sample of the batch, on tier S; overflow -> tier-B queue.
 // MODE 2: the tier-B queue, on tier B, then tier M; overflow -> tier-L queue.
 // MODE 1: the tier-L queue, on tier L.
-// SHL: the tier-S table size (2^SHL slots) of MODE 0; the small variant fits
-// one more CTA per SM and gives the same results (samples that outgrow it go
-// on to tier B as usual).  RG (MODE 0 with the 4096-slot table only): the
-// level scans read long row stretches with 16-byte loads (for
-// graphs whose CSR exceeds L2); same results.
-template <int MODE, int SHL = FAST_HLOG, bool RG = false>
-__global__ void __launch_bounds__(NT, MODE != 0 ? 2 : SHL == FAST_HLOG ? KD_MIN_BLOCKS : KD_MIN_BLOCKS + 1)
+// SL: the tier-S layout of MODE 0; the compact one fits one more CTA per SM
+// and gives the same results (samples that outgrow it go on to tier B as
+// usual).  RG (the default layout only): the level scans read long row
+// stretches with 16-byte loads and search long rows (for graphs whose CSR
+// exceeds L2); same results.
+template <int MODE, int SL = SL_FAST, bool RG = false>
+__global__ void __launch_bounds__(NT, MODE != 0 ? 2 : SL == SL_FAST ? KD_MIN_BLOCKS : KD_MIN_BLOCKS + 1)
     k_sample(SampleParams P) {
-  static_assert(!RG || SHL == FAST_HLOG, "the beyond-L2 scan has no small-table instance");
+  static_assert(!RG || SL == SL_FAST, "the beyond-L2 scan has no compact-layout instance");
   extern __shared__ __align__(16) unsigned char smem[];
   Ctl& c = *reinterpret_cast<Ctl*>(smem);
   Tables TS, TM;
   PiEntry* pi = P.pi_base + (size_t)blockIdx.x * 2 * NW * P.pcap;
-  if (MODE == 0) TS = smem_tables<SHL>(smem);
+  if (MODE == 0) TS = smem_tables<std::conditional_t<SL == SL_FAST, FastLayout, CompactLayout>>(smem);
   if (MODE == 2) {
-    TS = smem_tables<BIG_HLOG>(smem);
+    TS = smem_tables<BigLayout>(smem);
     TM = gm_tables(P.med_base + (size_t)blockIdx.x * P.med_stride, P.med_hlog, P.med_lcap, MED_MAXD);
   }
   if (MODE == 1) TM = gm_tables(P.gm_base + (size_t)blockIdx.x * P.gm_stride, P.gm_hlog, P.gm_lcap, GM_MAXD);
@@ -2445,9 +2464,9 @@ __global__ void __launch_bounds__(32 * WT_WARPS) k_sample_warp(SampleParams P) {
 
 size_t warp_tier_smem_bytes() { return sizeof(WSlot) * WT_WARPS; }
 
-size_t fast_smem_bytes() { return SLayout<FAST_HLOG>::BYTES; }
-size_t small_smem_bytes() { return SLayout<SMALL_HLOG>::BYTES; }
-size_t big_smem_bytes() { return SLayout<BIG_HLOG>::BYTES; }
+size_t fast_smem_bytes() { return FastLayout::BYTES; }
+size_t compact_smem_bytes() { return CompactLayout::BYTES; }
+size_t big_smem_bytes() { return BigLayout::BYTES; }
 
 // ============================================================== stop test
 struct CheckOut {
@@ -3643,8 +3662,8 @@ struct Workspace {
   int device = 0, num_sms = 0;
   int32_t max_n = 0;
   int64_t max_m = 0;
-  int grid_fast = 0, grid_big = 0, grid_gm = 0, grid_small = 0, grid_warp = 0;
-  size_t smem_fast = 0, smem_big = 0, smem_small = 0, smem_warp = 0;
+  int grid_fast = 0, grid_big = 0, grid_gm = 0, grid_compact = 0, grid_warp = 0;
+  size_t smem_fast = 0, smem_big = 0, smem_compact = 0, smem_warp = 0;
   unsigned long long* ctr = nullptr;
   int32_t* status = nullptr;
   unsigned long long* qb = nullptr;  // queue for tier B
@@ -3704,7 +3723,7 @@ struct kadabra_graph {
   void* tk_stage = nullptr;          // scatter staging: ids, lnL, lnU values
   size_t tk_stage_cap = 0;           // entries
   struct TuneTable {  // autotuned setup by probe size class and allowed set (-1: not yet)
-    int v[14][16];
+    int v[16][16];
     TuneTable() { std::memset(v, 0xFF, sizeof(v)); }
   } tier_choice;
   uint64_t fingerprint = 0;          // shape and sampled CSR entries (key of the autotuner's cache)
@@ -3761,23 +3780,23 @@ kadabra_status ensure_ws(Workspace* w, uint64_t deferred_need, int njobs) {
     KCK(cudaSetDevice(w->device));
     w->smem_fast = fast_smem_bytes();
     KCK(cudaFuncSetAttribute(k_sample<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->smem_fast));
-    KCK(cudaFuncSetAttribute(k_sample<0, FAST_HLOG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    KCK(cudaFuncSetAttribute(k_sample<0, SL_FAST, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)w->smem_fast));
     int per_sm = 0;
     KCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample<0>, NT, w->smem_fast));
     if (per_sm < 1) return fail(KADABRA_ERR_CAPACITY, "sampler does not fit on an SM");
     w->grid_fast = w->num_sms * per_sm;
-    w->smem_small = small_smem_bytes();
-    KCK(cudaFuncSetAttribute(k_sample<0, SMALL_HLOG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->smem_small));
-    KCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample<0, SMALL_HLOG>, NT, w->smem_small));
-    w->grid_small = w->num_sms * std::max(per_sm, 1);
+    w->smem_compact = compact_smem_bytes();
+    KCK(cudaFuncSetAttribute(k_sample<0, SL_COMPACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->smem_compact));
+    KCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample<0, SL_COMPACT>, NT, w->smem_compact));
+    w->grid_compact = w->num_sms * std::max(per_sm, 1);
     w->smem_warp = warp_tier_smem_bytes();
     KCK(cudaFuncSetAttribute(k_sample_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->smem_warp));
     KCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample_warp, 32 * WT_WARPS, w->smem_warp));
     w->grid_warp = w->num_sms * std::max(per_sm, 1);
     w->smem_big = big_smem_bytes();
     KCK(cudaFuncSetAttribute(k_sample<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w->smem_big));
-    KCK(cudaFuncSetAttribute(k_sample<2, FAST_HLOG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    KCK(cudaFuncSetAttribute(k_sample<2, SL_FAST, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)w->smem_big));
     KCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample<2>, NT, w->smem_big));
     if (per_sm < 1) return fail(KADABRA_ERR_CAPACITY, "large-table sampler does not fit on an SM");
@@ -3802,7 +3821,7 @@ kadabra_status ensure_ws(Workspace* w, uint64_t deferred_need, int njobs) {
     KTRY(dev_alloc(w->allocs, &p, sizeof(int32_t)));
     w->status = (int32_t*)p;
     KCK(cudaMemset(w->status, 0, sizeof(int32_t)));
-    KTRY(dev_alloc(w->allocs, &p, sizeof(PiEntry) * 2 * NW * (size_t)FAST_PCAP * std::max(w->grid_fast, w->grid_small)));
+    KTRY(dev_alloc(w->allocs, &p, sizeof(PiEntry) * 2 * NW * (size_t)FAST_PCAP * std::max(w->grid_fast, w->grid_compact)));
     w->pi_fast = (PiEntry*)p;
     KTRY(dev_alloc(w->allocs, &p, sizeof(PiEntry) * 2 * NW * (size_t)w->pcap_gm * w->grid_gm));
     w->pi_gm = (PiEntry*)p;
@@ -3913,7 +3932,7 @@ SampleParams base_params(kadabra_graph* g) {
 // launches the main sampler grid, then the large-table pass and the
 // n-sized-table pass for the samples queued by the launch before (each exits
 // at once when its queue is empty)
-// variant bit 0: the small tier-S table (SMALL_HLOG) with one more CTA per SM
+// variant bit 0: the compact tier-S layout with one more CTA per SM
 // variant bit 1: tier W (one warp per sample) first; tier S takes only the
 // samples it queues
 kadabra_status launch_sampler_kernels(Workspace* w, SampleParams P, cudaStream_t st, int variant = 0) {
@@ -3925,22 +3944,22 @@ kadabra_status launch_sampler_kernels(Workspace* w, SampleParams P, cudaStream_t
     KCK(cudaGetLastError());
   }
   const bool rg = (P.tier_flags & TF_VEC) != 0;
-  if (variant & 1)  // the small table has no beyond-L2 variant
-    k_sample<0, SMALL_HLOG><<<w->grid_small, NT, w->smem_small, st>>>(P);
+  if (variant & 1)  // the compact layout has no beyond-L2 variant
+    k_sample<0, SL_COMPACT><<<w->grid_compact, NT, w->smem_compact, st>>>(P);
   else if (rg)
-    k_sample<0, FAST_HLOG, true><<<w->grid_fast, NT, w->smem_fast, st>>>(P);
+    k_sample<0, SL_FAST, true><<<w->grid_fast, NT, w->smem_fast, st>>>(P);
   else
     k_sample<0><<<w->grid_fast, NT, w->smem_fast, st>>>(P);
   KCK(cudaGetLastError());
   if (rg)  // tier B (and M): the scan kind of tier S
-    k_sample<2, FAST_HLOG, true><<<w->grid_big, NT, w->smem_big, st>>>(P);
+    k_sample<2, SL_FAST, true><<<w->grid_big, NT, w->smem_big, st>>>(P);
   else
     k_sample<2><<<w->grid_big, NT, w->smem_big, st>>>(P);
   KCK(cudaGetLastError());
   P.pi_base = w->pi_gm;
   P.pcap = w->pcap_gm;
   if (rg)
-    k_sample<1, FAST_HLOG, true><<<w->grid_gm, NT, sizeof(Ctl), st>>>(P);
+    k_sample<1, SL_FAST, true><<<w->grid_gm, NT, sizeof(Ctl), st>>>(P);
   else
     k_sample<1><<<w->grid_gm, NT, sizeof(Ctl), st>>>(P);
   KCK(cudaGetLastError());
@@ -4485,7 +4504,7 @@ namespace {
 // ---------------------------------------------------------------- sampler autotuner
 // Picks, per graph, the shared-memory sampler setup that samples it fastest,
 // out of two independent choices: the tier-S table (2^FAST_HLOG slots at
-// KD_MIN_BLOCKS CTAs per SM, or 2^SMALL_HLOG slots with one more CTA per SM)
+// KD_MIN_BLOCKS CTAs per SM, or the compact layout with one more CTA per SM)
 // and whether tier W (one warp per sample) runs first.  Small searches gain
 // from more samples in flight, large ones lose to more escalations.  Every
 // setup gives identical results, so the choice only changes speed.  It times
@@ -4494,8 +4513,10 @@ namespace {
 // choice.  The probe batch is the run's own batch size K, capped at
 // TUNE_PROBE: small batches are bound by the slowest sample, large ones by
 // throughput, and the two can favour different setups.  A setup other than
-// the default is taken only if it is at least 3% faster.
-constexpr uint64_t TUNE_PROBE = 4096;
+// the default is taken only if it is at least 2% faster.  A probe of 4096
+// samples saw the compact layout's 3.5 % gain on the Chung-Lu graph's
+// 65,536-sample batches as a loss (tails of a few samples per CTA).
+constexpr uint64_t TUNE_PROBE = 16384;
 // process-wide: graphs with the same fingerprint, device and flags (a graph
 // loaded again) reuse the probe's choice; a collision could only cost speed
 std::mutex g_tune_mu;
@@ -4504,18 +4525,18 @@ std::unordered_map<uint64_t, int> g_tune_cache;
 kadabra_status tier_variant(kadabra_graph* g, Workspace* w, cudaStream_t st, int32_t req_ctas, int32_t req_warp,
                             uint64_t batch, int* variant) {
   const uint64_t probe = std::max<uint64_t>(1, std::min<uint64_t>(batch, TUNE_PROBE));
-  const int size_class = probe >= TUNE_PROBE ? 0 : 1 + ceil_log2(probe);  // <= 13
-  const int per_default = w->grid_fast / w->num_sms, per_small = w->grid_small / w->num_sms;
+  const int size_class = probe >= TUNE_PROBE ? 0 : 1 + ceil_log2(probe);  // <= 15
+  const int per_default = w->grid_fast / w->num_sms, per_compact = w->grid_compact / w->num_sms;
   unsigned s_ok, w_ok;  // allowed values of variant bit 0 and bit 1
   if (req_ctas == 0)
     s_ok = 3;
   else if (req_ctas == per_default)
     s_ok = 1;
-  else if (req_ctas == per_small)
+  else if (req_ctas == per_compact)
     s_ok = 2;
   else
     return fail(KADABRA_ERR_ARG, "ctas_per_sm must be 0 (autotune), " + std::to_string(per_default) + " or " +
-                                     std::to_string(per_small));
+                                     std::to_string(per_compact));
   if (req_warp == 0)
     w_ok = 3;
   else if (req_warp == 1)
@@ -4586,7 +4607,7 @@ kadabra_status tier_variant(kadabra_graph* g, Workspace* w, cudaStream_t st, int
     int fastest = first;
     for (int v = 0; v < 4; ++v)
       if ((allowed >> v & 1) && best[v] < best[fastest]) fastest = v;
-    if (best[fastest] < 0.97f * best[first]) pick = fastest;
+    if (best[fastest] < 0.98f * best[first]) pick = fastest;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     if (cached) g_tune_cache[key] = pick;
   }
@@ -4595,7 +4616,7 @@ kadabra_status tier_variant(kadabra_graph* g, Workspace* w, cudaStream_t st, int
 }
 
 int variant_ctas_per_sm(const Workspace* w, int variant) {
-  return ((variant & 1) ? w->grid_small : w->grid_fast) / w->num_sms;
+  return ((variant & 1) ? w->grid_compact : w->grid_fast) / w->num_sms;
 }
 
 // ---------------------------------------------------------------- device-driven main loop

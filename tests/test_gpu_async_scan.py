@@ -2,7 +2,8 @@
 along long row stretches (KADABRA_FLAG_ASYNC_SCAN; taken by itself for graphs
 whose CSR exceeds the L2; the star, Barabasi-Albert, R-MAT and Chung-Lu
 graphs have rows long enough, with heads at every 16-byte misalignment) and frontiers scanned in segments (KADABRA_FLAG_FRONTIER_SEGMENTS:
-64-node segments; by itself only for tier-B frontiers beyond 2048 nodes).
+64-node segments; by itself only for frontiers beyond the frontier array, 1024 nodes or 512 in the compact
+tier-S layout).
 Per-sample pairs, paths, work counters and statuses bit-exact, whole runs
 identical.  The R-MAT scale-24 tests cover the automatic choice on a graph
 beyond the L2."""
