@@ -422,6 +422,9 @@ struct SampleParams {
 #define KD_LONG_MIN 32
 #endif
 constexpr int LONG_CAP = KD_LONG_CAP;
+#ifndef KD_PREFIX_WARP
+#define KD_PREFIX_WARP 1  // frontiers of at most 32 nodes: the degree prefix by one warp
+#endif
 __device__ __forceinline__ bool row_is_long(int deg, int k) {
   if (KD_MEMB_W <= 0 || k <= 0 || deg < KD_LONG_MIN) return false;
   const int lg = 32 - __clz(deg);  // bits of deg: the search steps
@@ -451,7 +454,7 @@ struct Ctl {
   int fside, fdepth;  // the frontier the filter in T.bits was built for (fside -1: none)
   int nlong;           // frontier rows of the current segment searched instead of scanned
   long long ldeg_sum;  //   and their arcs (for the work counter)
-  int lrow[LONG_CAP];  //   segment position, row start and degree of each
+  uint16_t lrow[LONG_CAP];  //   segment position, row start and degree of each
   int lrs[LONG_CAP];
   int ldeg[LONG_CAP];
   int ecount;
@@ -1243,6 +1246,44 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
     // count 0 arcs in the prefix.
     const int long_cap = min(LONG_CAP, max(1, T.frcap >> 5));
     auto build_prefix = [&](int fb, int cnt, bool count_edges, int kother) {
+#if KD_PREFIX_WARP
+      if (cnt <= 32) {  // one warp: shuffles only, one barrier
+        if (wid == 0) {
+          int deg = 0, rs = 0;
+          if (lane < cnt) {
+            const int x = KIDX(list_node<PK>(T, fb + lane), G.n, 9);
+            rs = __ldg(&rowp[x]);
+            deg = __ldg(&rowp[x + 1]) - rs;
+            if (row_is_long(deg, kother)) {
+              const int q = atomicAdd(&c.nlong, 1);
+              if (q < long_cap) {
+                c.lrow[q] = (uint16_t)lane;
+                c.lrs[q] = rs;
+                c.ldeg[q] = deg;
+                atomicAdd(reinterpret_cast<unsigned long long*>(&c.ldeg_sum), (unsigned long long)deg);
+                deg = 0;
+              }
+            }
+          }
+          int v = deg;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(FULL, v, o);
+            if (lane >= o) v += u;
+          }
+          if (lane < cnt) T.pr[KIDX(lane, T.frcap + 1, 10)] = make_int2(v - deg, rs);
+          const int tot = __shfl_sync(FULL, v, 31);
+          __syncwarp();
+          if (lane == 0) {
+            T.pr[KIDX(cnt, T.frcap + 1, 10)] = make_int2(tot, 0);
+            c.ecount = tot;
+            if (count_edges) c.stat[KADABRA_STAT_EDGES] += tot + c.ldeg_sum;
+          }
+        }
+        __syncthreads();
+        return c.ecount;
+      }
+#endif
       int carry = 0;
       for (int base = 0; base < cnt; base += NT) {
         const int i = base + tid;
@@ -1254,7 +1295,7 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
           if (row_is_long(deg, kother)) {
             const int q = atomicAdd(&c.nlong, 1);
             if (q < long_cap) {
-              c.lrow[q] = i;
+              c.lrow[q] = (uint16_t)i;
               c.lrs[q] = rs;
               c.ldeg[q] = deg;
               atomicAdd(reinterpret_cast<unsigned long long*>(&c.ldeg_sum), (unsigned long long)deg);
@@ -1819,10 +1860,10 @@ struct SLayout {
                 "frontier array holds the selection histogram");
 };
 // tier S at KD_MIN_BLOCKS CTAs per SM; tier S compact (one more CTA per SM:
-// half-full lists, 512-node segments, a 2^14-bit filter, 46 levels per
-// side); tier B (twice the slots, two CTAs per SM)
+// half-full lists, 512-node segments, a 2^14-bit filter, 38 levels per
+// side; 5 x 45,408 B fit an SM's shared memory, 5 x 45,600 B did not); tier B (twice the slots, two CTAs per SM)
 using FastLayout = SLayout<FAST_HLOG, KD_LOAD_QUARTERS, FRONTIER_SEG, FILTER_LOG, FAST_MAXD>;
-using CompactLayout = SLayout<FAST_HLOG, 2, 512, 14, 46>;
+using CompactLayout = SLayout<FAST_HLOG, 2, 512, 14, 38>;
 using BigLayout = SLayout<BIG_HLOG, KD_LOAD_QUARTERS, FRONTIER_SEG, FILTER_LOG, FAST_MAXD>;
 // the tier-S layout a k_sample instance uses (SL)
 constexpr int SL_FAST = 0;
