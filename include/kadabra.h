@@ -310,7 +310,9 @@ kadabra_status kadabra_run(kadabra_graph* g, double lambda, double delta, int32_
  * hits into d_counts (device, n) and the work counters into d_totals
  * (device, KADABRA_NSTAT int64, may be NULL).  Asynchronous on `stream`;
  * errors found on the device (sigma overflow, capacity) are reported by the
- * next kadabra_sync_status. */
+ * next kadabra_sync_status.  It takes the sampler setup that an autotuned
+ * kadabra_run on the same graph object chose for batches of this size (the
+ * default setup if none has); results do not depend on it. */
 kadabra_status kadabra_sample_batch(kadabra_graph* g, uint64_t seed, uint32_t domain, uint64_t first_idx,
                                     uint64_t count, uint32_t* d_counts, int64_t* d_totals, void* stream);
 

@@ -4656,6 +4656,15 @@ kadabra_status tier_variant(kadabra_graph* g, Workspace* w, cudaStream_t st, int
   return KADABRA_OK;
 }
 
+// The setup an autotuned run on g chose for batches of `batch` samples (every
+// setup allowed), or the default if no run has tuned that size class; no probe.
+int tuned_variant(const kadabra_graph* g, uint64_t batch) {
+  const uint64_t probe = std::max<uint64_t>(1, std::min<uint64_t>(batch, TUNE_PROBE));
+  const int size_class = probe >= TUNE_PROBE ? 0 : 1 + ceil_log2(probe);
+  const int v = g->tier_choice.v[size_class][15];
+  return v >= 0 ? v : 0;
+}
+
 int variant_ctas_per_sm(const Workspace* w, int variant) {
   return ((variant & 1) ? w->grid_compact : w->grid_fast) / w->num_sms;
 }
@@ -6469,7 +6478,7 @@ kadabra_status kadabra_sample_batch(kadabra_graph* g, uint64_t seed, uint32_t do
   P.job0.counts = d_counts;
   P.job0.totals = reinterpret_cast<long long*>(d_totals);
   P.total_work = count;
-  return launch_sampler(g->ws, P, as_stream(stream));
+  return launch_sampler(g->ws, P, as_stream(stream), tuned_variant(g, count));
 }
 
 kadabra_status kadabra_sample_batch_noalloc(int32_t n, int64_t m, const int32_t* d_row_ptr, const int32_t* d_col,
