@@ -102,7 +102,12 @@ constexpr int U = KD_U;            // independent items per thread per step (mem
 // and beyond those it is queued for a last launch with n-sized global tables
 // (tier L).  Every tier gives the same result.
 constexpr int FAST_HLOG = KD_FAST_HLOG;        // tier S: 2^FAST_HLOG hash slots
-constexpr int BIG_HLOG = FAST_HLOG + 1;        // tier B: twice as many
+// tier B: 2^KD_BIG_EXTRA times tier S's slots (4 times, at one CTA per SM: R-MAT scale 24 batch 5.38 ->
+// 5.44 ms, scale 22 2.48 -> 2.56 ms; fewer samples reached tier M, but tier B ran on half the CTAs)
+#ifndef KD_BIG_EXTRA
+#define KD_BIG_EXTRA 1
+#endif
+constexpr int BIG_HLOG = FAST_HLOG + KD_BIG_EXTRA;
 #ifndef KD_FAST_MAXD
 #define KD_FAST_MAXD 126
 #endif

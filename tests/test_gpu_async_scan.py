@@ -128,3 +128,28 @@ def test_frontier_segments_power_law(kd, orc, chung_lu_1m):
     finally:
         G.free()
     _same_samples(got, ref, "chung-lu segments, tier B")
+
+
+def test_vector_scan_in_deferred_tiers(kd, orc, gg, chung_lu_1m):
+    """The scan for graphs beyond the L2 in the tiers after tier S: deep
+    searches (a path and a cycle, beyond tier S's levels: tiers B, M and L)
+    and the power-law graph's large samples (tier B); per-sample results as
+    the oracle's."""
+    for name, g, count, ml in (("path1500", gg.path_graph(1500), 300, 1600),
+                               ("cycle2001", gg.cycle_graph(2001), 300, 1100)):
+        ref = orc.sample_paths(g, 3, 0, 0, count, max_len=ml)
+        G = kd.kadabra_load_csr(g)
+        try:
+            G.set_flags(kd.FLAG_ASYNC_SCAN)
+            got = kd.kadabra_sample_paths(G, 3, 0, 0, count, max_len=ml)
+        finally:
+            G.free()
+        _same_samples(got, ref, name)
+    ref = orc.sample_paths(chung_lu_1m, 9, 0, 40_000, 3000)
+    G = kd.kadabra_load_csr(chung_lu_1m)
+    try:
+        G.set_flags(kd.FLAG_ASYNC_SCAN)
+        got = kd.kadabra_sample_paths(G, 9, 0, 40_000, 3000)
+    finally:
+        G.free()
+    _same_samples(got, ref, "chung-lu, deferred samples")
