@@ -89,7 +89,7 @@ typedef struct {
   void* stream;            /* cudaStream_t for all work of the call (NULL = default) */
   int32_t ctas_per_sm;     /* shared-memory sampler tier, as resident CTAs per SM: 0 =
                               autotuned per graph (on the first one-graph run a probe
-                              batch of min(K, 16384) samples times every allowed setup
+                              batch of min(K, 65536) samples times every allowed setup
                               of table and warp tier; the choice is cached per graph
                               fingerprint), or one of the two values the library
                               offers (4: 4096-slot tables, lists of 3072 nodes; 5:

@@ -1830,7 +1830,7 @@ __device__ inline Tables gm_tables(unsigned char* base, int hlog, int lcap, int 
 }
 
 // shared-memory layout of a packed tier after the control block: 2^HLOG
-// hash slots, lists of LQ quarters of the slots (hash positions), frontier
+// hash slots, lists of L8 eighths of the slots (hash positions), frontier
 // segments of FSEG nodes (the frontier array's capacity), a 2^FLOG-bit
 // filter and MAXD levels per side.  The scan variant for graphs beyond the
 // L2 has the same layout.
@@ -1841,12 +1841,12 @@ constexpr int FRONTIER_SEG = KD_FRONTIER_SEG;
 #ifndef KD_LOAD_QUARTERS
 #define KD_LOAD_QUARTERS 3
 #endif
-template <int HLOG, int LQ, int FSEG, int FLOG, int MAXD>
+template <int HLOG, int L8, int FSEG, int FLOG, int MAXD>
 struct SLayout {
   static constexpr int SLOTS_LOG = HLOG;
   // nodes a table takes before the sample moves on to the next tier (the
   // probes stay short)
-  static constexpr int LCAP = (LQ << HLOG) / 4;
+  static constexpr int LCAP = (L8 << HLOG) / 8;
   static_assert(LCAP + NT < (1 << HLOG), "a full list leaves free slots");
   static constexpr int FRCAP = LCAP < FSEG ? LCAP : FSEG;
   static constexpr int FWORDS = (1 << FLOG) / 32;
@@ -1867,9 +1867,18 @@ struct SLayout {
 // tier S at KD_MIN_BLOCKS CTAs per SM; tier S compact (one more CTA per SM:
 // half-full lists, 512-node segments, a 2^14-bit filter, 38 levels per
 // side; 5 x 45,408 B fit an SM's shared memory, 5 x 45,600 B did not); tier B (twice the slots, two CTAs per SM)
-using FastLayout = SLayout<FAST_HLOG, KD_LOAD_QUARTERS, FRONTIER_SEG, FILTER_LOG, FAST_MAXD>;
-using CompactLayout = SLayout<FAST_HLOG, 2, 512, 14, 38>;
-using BigLayout = SLayout<BIG_HLOG, KD_LOAD_QUARTERS, FRONTIER_SEG, FILTER_LOG, FAST_MAXD>;
+#ifndef KD_CMP_L8
+#define KD_CMP_L8 4
+#endif
+#ifndef KD_CMP_FLOG
+#define KD_CMP_FLOG 14
+#endif
+#ifndef KD_CMP_MAXD
+#define KD_CMP_MAXD 38
+#endif
+using FastLayout = SLayout<FAST_HLOG, 2 * KD_LOAD_QUARTERS, FRONTIER_SEG, FILTER_LOG, FAST_MAXD>;
+using CompactLayout = SLayout<FAST_HLOG, KD_CMP_L8, 512, KD_CMP_FLOG, KD_CMP_MAXD>;
+using BigLayout = SLayout<BIG_HLOG, 2 * KD_LOAD_QUARTERS, FRONTIER_SEG, FILTER_LOG, FAST_MAXD>;
 // the tier-S layout a k_sample instance uses (SL)
 constexpr int SL_FAST = 0;
 constexpr int SL_COMPACT = 1;
@@ -3769,7 +3778,7 @@ struct kadabra_graph {
   void* tk_stage = nullptr;          // scatter staging: ids, lnL, lnU values
   size_t tk_stage_cap = 0;           // entries
   struct TuneTable {  // autotuned setup by probe size class and allowed set (-1: not yet)
-    int v[16][16];
+    int v[18][16];
     TuneTable() { std::memset(v, 0xFF, sizeof(v)); }
   } tier_choice;
   uint64_t fingerprint = 0;          // shape and sampled CSR entries (key of the autotuner's cache)
@@ -4561,8 +4570,9 @@ namespace {
 // throughput, and the two can favour different setups.  A setup other than
 // the default is taken only if it is at least 2% faster.  A probe of 4096
 // samples saw the compact layout's 3.5 % gain on the Chung-Lu graph's
-// 65,536-sample batches as a loss (tails of a few samples per CTA).
-constexpr uint64_t TUNE_PROBE = 16384;
+// 65,536-sample batches as a loss (tails of a few samples per CTA), and one
+// of 16,384 picked either setup from run to run.
+constexpr uint64_t TUNE_PROBE = 65536;
 // process-wide: graphs with the same fingerprint, device and flags (a graph
 // loaded again) reuse the probe's choice; a collision could only cost speed
 std::mutex g_tune_mu;
@@ -4571,7 +4581,7 @@ std::unordered_map<uint64_t, int> g_tune_cache;
 kadabra_status tier_variant(kadabra_graph* g, Workspace* w, cudaStream_t st, int32_t req_ctas, int32_t req_warp,
                             uint64_t batch, int* variant) {
   const uint64_t probe = std::max<uint64_t>(1, std::min<uint64_t>(batch, TUNE_PROBE));
-  const int size_class = probe >= TUNE_PROBE ? 0 : 1 + ceil_log2(probe);  // <= 15
+  const int size_class = probe >= TUNE_PROBE ? 0 : 1 + ceil_log2(probe);  // <= 17
   const int per_default = w->grid_fast / w->num_sms, per_compact = w->grid_compact / w->num_sms;
   unsigned s_ok, w_ok;  // allowed values of variant bit 0 and bit 1
   if (req_ctas == 0)
