@@ -427,6 +427,10 @@ struct SampleParams {
 #define KD_LONG_MIN 32
 #endif
 constexpr int LONG_CAP = KD_LONG_CAP;
+#ifndef KD_FUSE_MAX
+#define KD_FUSE_MAX 256
+#endif
+constexpr int FUSE_MAX = KD_FUSE_MAX;  // levels of at most this many arcs insert and test for touches in one pass
 #ifndef KD_PREFIX_WARP
 #define KD_PREFIX_WARP 1  // frontiers of at most 32 nodes: the degree prefix by one warp
 #endif
@@ -1153,7 +1157,9 @@ KD_MEMB_ATTR void search_long_rows(const Tables& T, const Ctl& c, const int32_t*
   }
 }
 
-template <bool PK, bool RG = false>
+// FU: small levels take the fused pass (off in the compact tier-S layout,
+// whose 48 registers it would spill)
+template <bool PK, bool RG = false, bool FU = true>
 __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, const Tables& T, Ctl& c, uint64_t idx,
                                            int64_t out_i) {
   const int tid = threadIdx.x, lane = lane_id(), wid = warp_id();
@@ -1222,23 +1228,26 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
     }
     const int32_t* rowp = side == 0 ? G.rp : G.rrp;
     const int32_t* cols = side == 0 ? G.ci : G.rci;
-    if constexpr (PK) {
-      // the filter of the other side's frontier, unless it is still current
-      const int os = 1 - side, od = c.depth[os];
-      if (c.fside != os || c.fdepth != od) {
-        for (int i = tid; i < T.fwords; i += NT) T.bits[i] = 0u;
-        __syncthreads();
-        for (int i = lvl_lo(T, os, od) + tid; i < lvl_hi(T, os, od); i += NT) {
-          const uint32_t h = filter_slot(list_node<PK>(T, i), T.fshift);
-          atomicOr(&T.bits[h >> 5], 1u << (h & 31));
-        }
-        __syncthreads();
-        if (tid == 0) {
-          c.fside = os;
-          c.fdepth = od;
+    // the filter of the other side's frontier for pass 1, unless it is
+    // still current (all threads)
+    auto ensure_filter = [&]() {
+      if constexpr (PK) {
+        const int os = 1 - side, od = c.depth[os];
+        if (c.fside != os || c.fdepth != od) {
+          for (int i = tid; i < T.fwords; i += NT) T.bits[i] = 0u;
+          __syncthreads();
+          for (int i = lvl_lo(T, os, od) + tid; i < lvl_hi(T, os, od); i += NT) {
+            const uint32_t h = filter_slot(list_node<PK>(T, i), T.fshift);
+            atomicOr(&T.bits[h >> 5], 1u << (h & 31));
+          }
+          __syncthreads();
+          if (tid == 0) {
+            c.fside = os;
+            c.fdepth = od;
+          }
         }
       }
-    }
+    };
 
     // Degree prefix and row starts over frontier nodes [fb, fb + cnt) into
     // T.pr; returns their arc count (all threads).  A frontier of more than
@@ -1324,9 +1333,12 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
     const int nseg = (fcount + T.frcap - 1) / T.frcap;
     int E = 0;  // arc count of the last segment built
 
-    // pass 1: touch test against the other search
+    // pass 1: touch test against the other search.  A level of at most
+    // FUSE_MAX arcs that cannot fill the lists skips it: pass 2 then tests
+    // for touches while it inserts, and undoes its insertions if it finds one.
     int pass1_bad = 0;
     bool had_long = false;  // pass 1 searched rows that pass 2 must scan
+    bool fused = false;
     {
       int npi = 0;
       bool sigma_of = false;
@@ -1350,6 +1362,11 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
       for (int sg = 0; sg < nseg; ++sg) {
       const int fb = f0 + sg * T.frcap, cnt = min(T.frcap, fcount - sg * T.frcap);
       E = build_prefix(fb, cnt, true, RG ? kother : 0);
+      if (FU && nseg == 1 && c.nlong == 0 && E <= FUSE_MAX && c.nlist + E <= T.lcap) {
+        fused = true;
+        break;
+      }
+      ensure_filter();
       scan_level<RG>(T, c, cnt, E, cols, G.m, [&](int, bool ok, int p, int y) {
         bool touch = false;
         unsigned long long wgt = 0;
@@ -1387,39 +1404,43 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
         __syncthreads();
       }
       }
-      int bad = 0;
-      if (__any_sync(FULL, sigma_of) && lane == 0) {
-        atomicOr(&c.flags, F_SIGMA);
-        bad = 1;
-      }
-      if (lane == 0) {
-        c.npi[wid] = npi;
-        if (npi > T.pcap) {
-          atomicOr(&c.flags, F_CAP);
+      if (!fused) {
+        int bad = 0;
+        if (__any_sync(FULL, sigma_of) && lane == 0) {
+          atomicOr(&c.flags, F_SIGMA);
           bad = 1;
         }
+        if (lane == 0) {
+          c.npi[wid] = npi;
+          if (npi > T.pcap) {
+            atomicOr(&c.flags, F_CAP);
+            bad = 1;
+          }
+        }
+        // Decide from the barrier's own reduction, not by reading c.flags
+        // after it: a warp that has already moved on may set flags (the depth
+        // limit below, or pass 2) before a slower warp would have read them,
+        // and the two would then leave at different barriers.
+        pass1_bad = __syncthreads_or(bad);
       }
-      // Decide from the barrier's own reduction, not by reading c.flags
-      // after it: a warp that has already moved on may set flags (the depth
-      // limit below, or pass 2) before a slower warp would have read them,
-      // and the two would then leave at different barriers.
-      pass1_bad = __syncthreads_or(bad);
     }
-    if (tid == 0) {
-      int tot = 0;
-      for (int w = 0; w < NW; ++w) tot += c.npi[w];
-      if (tot > 0) {
-        c.done = 1;
-        c.stat[KADABRA_STAT_PI] = tot;
+    if (!fused) {
+      if (tid == 0) {
+        int tot = 0;
+        for (int w = 0; w < NW; ++w) tot += c.npi[w];
+        if (tot > 0) {
+          c.done = 1;
+          c.stat[KADABRA_STAT_PI] = tot;
+        }
       }
+      __syncthreads();
+      if (tid == 0) {  // every thread has passed its last read of the long rows
+        c.nlong = 0;
+        c.ldeg_sum = 0;
+      }
+      if (pass1_bad) return;
+      if (c.done) break;
     }
-    __syncthreads();
-    if (tid == 0) {  // every thread has passed its last read of the long rows
-      c.nlong = 0;
-      c.ldeg_sum = 0;
-    }
-    if (pass1_bad) return;
-    if (c.done) break;
 
     // pass 2: the next level.  The first discoverer of an unvisited head y
     // publishes (y, side, dist) with one CAS and appends y to the level
@@ -1436,12 +1457,18 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
       bool of = false, cap = false;
       const uint32_t want_val = pack_val(side, dnew);
       const volatile int* nlist_now = &c.nlist;
+      int ftouch = 0;  // fused level: 1 = a touch arc seen, 2 = its weight overflowed
+      PiEntry* fseg = T.pi + (size_t)wid * T.pcap;
+      if (fused) {
+        if (lane == 0) c.npi[wid] = 0;
+        __syncwarp();
+      }
       for (int sg = 0; sg < nseg; ++sg) {
       const int fb = f0 + sg * T.frcap, cnt = min(T.frcap, fcount - sg * T.frcap);
       // one segment without long rows: pass 1's prefix is still there
       if (nseg > 1 || had_long) E = build_prefix(fb, cnt, false, 0);
       scan_level<RG>(T, c, cnt, E, cols, G.m, [&](int, bool ok, int p, int y) {
-        if (!ok || cap) return;
+        if (!ok || (cap && !fused)) return;
         // the head's row bounds (its degree joins the new frontier's cost if
         // it is new), loaded before the probe so the load overlaps it
         const int ylo = __ldg(&rowp[KIDX(y, G.n, 13)]), yhi = __ldg(&rowp[KIDX(y, G.n, 13) + 1]);
@@ -1475,7 +1502,8 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
             w = old;
           }
           if ((int32_t)(w >> 32) == y) {
-            if (ent_val<PK>(w) == want_val) {  // also discovered at this level
+            const uint32_t v = ent_val<PK>(w);
+            if (v == want_val) {  // also discovered at this level
               ++hits;
               if (!ent_add<PK>(T, pos, add)) {
                 if (PK)
@@ -1483,6 +1511,16 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
                 else
                   of = true;
               }
+            } else if (fused && val_side(v) != side) {  // a touch arc (x, y)
+              const unsigned long long sy = ent_sig<PK>(T, w, pos);
+              if (__umul64hi(add, sy) != 0ull) ftouch |= 2;
+              const int at = atomicAdd(&c.npi[wid], 1);
+              if (at < T.pcap) {
+                fseg[at].x = (int32_t)(T.hkv[px] >> 32);
+                fseg[at].y = y;
+                fseg[at].w = add * sy;
+              }
+              ftouch |= 1;
             }
             return;
           }
@@ -1491,6 +1529,31 @@ __device__ __forceinline__ void run_sample(const SampleParams& P, const Job& J, 
         cap = true;  // table full
       });
       if (sg + 1 < nseg) __syncthreads();
+      }
+      if (fused && __syncthreads_or(ftouch & 1)) {
+        // the level touches: undo its insertions (slots that were empty
+        // before it) and choose among its touch arcs, as after pass 1
+        const int sig_of = __syncthreads_or(ftouch & 2);
+        for (int i = list_before + tid; i < c.nlist; i += NT) {
+          const uint32_t q = lpos_get<PK>(T, i);
+          T.hkv[q] = EMPTY;
+          if (!PK) T.hsig[q] = 0ull;
+        }
+        __syncthreads();
+        if (tid == 0) {
+          c.nlist = list_before;
+          int tot = 0;
+          for (int w = 0; w < NW; ++w) {
+            tot += c.npi[w];
+            if (c.npi[w] > T.pcap) c.flags |= F_CAP;
+          }
+          if (sig_of) c.flags |= F_SIGMA;
+          c.done = 1;
+          c.stat[KADABRA_STAT_PI] = tot;
+        }
+        __syncthreads();
+        if (c.flags) return;
+        break;
       }
       if (of) atomicOr(&c.flags, F_SIGMA);
       if (cap) atomicOr(&c.flags, F_CAP);
@@ -2051,7 +2114,7 @@ __global__ void __launch_bounds__(NT, MODE != 0 ? 2 : SL == SL_FAST ? KD_MIN_BLO
     if (MODE == 0) {
       if (!(P.tier_flags & TF_SKIP_S)) {
         clear_path_row(P, out_i);
-        run_sample<true, RG>(P, c.job, TS, c, idx, out_i);
+        run_sample<true, RG, SL == SL_FAST>(P, c.job, TS, c, idx, out_i);
         __syncthreads();
         done = c.flags != F_CAP;
         reset_tables<true>(TS, c, true);
@@ -4637,7 +4700,10 @@ kadabra_status tier_variant(kadabra_graph* g, Workspace* w, cudaStream_t st, int
   KCK(cudaEventCreate(&e1));
   float best[4] = {1e30f, 1e30f, 1e30f, 1e30f};
   kadabra_status stt = KADABRA_OK;
-  for (int rep = 0; rep < 2 && stt == KADABRA_OK; ++rep)
+  // best of several rounds over the setups: two for large probes, up to
+  // eight for small ones, whose times (tens of microseconds) vary more
+  const int reps = (int)std::min<uint64_t>(8, std::max<uint64_t>(2, 16384 / probe));
+  for (int rep = 0; rep < reps && stt == KADABRA_OK; ++rep)
     for (int v = 0; v < 4 && stt == KADABRA_OK; ++v) {
       if (!(allowed >> v & 1)) continue;
       cudaEventRecord(e0, st);
