@@ -57,7 +57,7 @@ METRIC = "paths/sec & time-to-(lambda,delta) per graph, batched vs plain on GPU;
 WORKLOADS = {
     "chung_lu_1m": dict(family="chung_lu", n=1_000_000, beta=2.5, mean_deg=16.0, max_deg=10_000.0, graph_seed=1,
                         lcc=True, lam=0.005, delta=0.1, check_interval=1 << 16,
-                        sampler_dram_bytes=100_345_600 + 23_808_597 + 65_792),
+                        sampler_dram_bytes=99_782_571 + 23_815_338 + 64_768),
     "erdos_renyi_2k": dict(family="erdos_renyi", n=2000, mean_deg=8.0, graph_seed=1, lcc=True, lam=0.01,
                            delta=0.1, check_interval=1000, sampler_dram_bytes=None),
     "rmat_24": dict(family="rmat", scale=24, edge_factor=16, a=0.57, b=0.19, c=0.19, graph_seed=1, lam=0.0025,
@@ -65,7 +65,7 @@ WORKLOADS = {
     # the scale-22 graph of the same recipe: the size the ncu counters are captured at
     "rmat_22": dict(family="rmat", scale=22, edge_factor=16, a=0.57, b=0.19, c=0.19, graph_seed=1, lam=0.0025,
                     delta=0.1, check_interval=1 << 16,
-                    sampler_dram_bytes=624_171_520 + 151_155_797 + 65_621),
+                    sampler_dram_bytes=632_693_077 + 149_157_888 + 65_792),
     "rmat_24_topk": dict(family="rmat", scale=24, edge_factor=16, a=0.57, b=0.19, c=0.19, graph_seed=1, lam=0.0025,
                          delta=0.1, check_interval=1 << 16, sampler_dram_bytes=None, k=10),
 }
