@@ -430,6 +430,9 @@ constexpr int LONG_CAP = KD_LONG_CAP;
 #ifndef KD_FUSE_MAX
 #define KD_FUSE_MAX 256
 #endif
+#ifndef KD_FU_RG
+#define KD_FU_RG 1  // the fused pass in tier S's beyond-L2 scan variant
+#endif
 constexpr int FUSE_MAX = KD_FUSE_MAX;  // levels of at most this many arcs insert and test for touches in one pass
 #ifndef KD_PREFIX_WARP
 #define KD_PREFIX_WARP 1  // frontiers of at most 32 nodes: the degree prefix by one warp
@@ -2114,7 +2117,7 @@ __global__ void __launch_bounds__(NT, MODE != 0 ? 2 : SL == SL_FAST ? KD_MIN_BLO
     if (MODE == 0) {
       if (!(P.tier_flags & TF_SKIP_S)) {
         clear_path_row(P, out_i);
-        run_sample<true, RG, SL == SL_FAST>(P, c.job, TS, c, idx, out_i);
+        run_sample<true, RG, SL == SL_FAST && (KD_FU_RG || !RG)>(P, c.job, TS, c, idx, out_i);
         __syncthreads();
         done = c.flags != F_CAP;
         reset_tables<true>(TS, c, true);
