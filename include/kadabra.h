@@ -276,15 +276,19 @@ kadabra_status kadabra_graph_info(const kadabra_graph* g, int32_t* n, int64_t* m
  * frontier in segments of 64 nodes, as they do for frontiers beyond their
  * frontier array (1024 nodes, 512 in the compact tier-S layout), and
  * to take at most two searched long rows per segment; it exists to test
- * those paths and only slows sampling.  No flag changes a result.  Returns KADABRA_ERR_ARG for unknown
- * bits. */
+ * those paths and only slows sampling.  KADABRA_FLAG_COMPACT_TABLES runs tier
+ * S in the compact layout (the autotuner's 5-CTA setup: lists of 2048 nodes,
+ * 38 levels per side) whatever the tuned setup, except with the 16-byte
+ * scans, which have no compact variant.  No flag changes a result.  Returns
+ * KADABRA_ERR_ARG for unknown bits. */
 enum {
   KADABRA_FLAG_GLOBAL_TABLES = 1,
   KADABRA_FLAG_MEDIUM_TABLES = 2,
   KADABRA_FLAG_LARGE_SHARED_TABLES = 4,
   KADABRA_FLAG_WARP_TIER = 8,
   KADABRA_FLAG_ASYNC_SCAN = 16,
-  KADABRA_FLAG_FRONTIER_SEGMENTS = 32
+  KADABRA_FLAG_FRONTIER_SEGMENTS = 32,
+  KADABRA_FLAG_COMPACT_TABLES = 64
 };
 kadabra_status kadabra_graph_set_flags(kadabra_graph* g, uint32_t flags);
 

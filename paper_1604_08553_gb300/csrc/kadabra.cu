@@ -1977,6 +1977,7 @@ constexpr int TF_SKIP_M = 4;
 constexpr int TF_WARP = 8;  // tier W first, whatever the launch's variant
 constexpr int TF_VEC = 16;  // tier S's level scans read long row stretches with 16-byte loads
 constexpr int TF_SEG64 = 32;  // shared-memory tiers scan frontiers in 64-node segments (tests)
+constexpr int TF_COMPACT = 64;  // tier S in the compact layout, whatever the launch's variant
 
 // queue counters in SampleParams::ctr
 constexpr int Q_NEXT_A = 0;   // next sample index of the batch
@@ -4041,6 +4042,7 @@ SampleParams ws_params(const Workspace* w, uint32_t flags) {
   if (flags & KADABRA_FLAG_WARP_TIER) P.tier_flags |= TF_WARP;
   if (flags & (KADABRA_FLAG_ASYNC_SCAN | FLAG_VEC_AUTO)) P.tier_flags |= TF_VEC;
   if (flags & KADABRA_FLAG_FRONTIER_SEGMENTS) P.tier_flags |= TF_SEG64;
+  if (flags & KADABRA_FLAG_COMPACT_TABLES) P.tier_flags |= TF_COMPACT;
   return P;
 }
 
@@ -4065,7 +4067,7 @@ kadabra_status launch_sampler_kernels(Workspace* w, SampleParams P, cudaStream_t
     KCK(cudaGetLastError());
   }
   const bool rg = (P.tier_flags & TF_VEC) != 0;
-  if (variant & 1)  // the compact layout has no beyond-L2 variant
+  if ((variant & 1) || ((P.tier_flags & TF_COMPACT) && !rg))  // the compact layout has no beyond-L2 variant
     k_sample<0, SL_COMPACT><<<w->grid_compact, NT, w->smem_compact, st>>>(P);
   else if (rg)
     k_sample<0, SL_FAST, true><<<w->grid_fast, NT, w->smem_fast, st>>>(P);
@@ -6534,7 +6536,8 @@ void kadabra_release_cached(void) {
 kadabra_status kadabra_graph_set_flags(kadabra_graph* g, uint32_t flags) {
   if (!g) return fail(KADABRA_ERR_ARG, "graph is NULL");
   if (flags & ~(uint32_t)(KADABRA_FLAG_GLOBAL_TABLES | KADABRA_FLAG_MEDIUM_TABLES | KADABRA_FLAG_LARGE_SHARED_TABLES |
-                          KADABRA_FLAG_WARP_TIER | KADABRA_FLAG_ASYNC_SCAN | KADABRA_FLAG_FRONTIER_SEGMENTS))
+                          KADABRA_FLAG_WARP_TIER | KADABRA_FLAG_ASYNC_SCAN | KADABRA_FLAG_FRONTIER_SEGMENTS |
+                          KADABRA_FLAG_COMPACT_TABLES))
     return fail(KADABRA_ERR_ARG, "unknown flag");
   g->flags = flags;
   return KADABRA_OK;

@@ -47,6 +47,7 @@ FLAG_LARGE_SHARED_TABLES = 4
 FLAG_WARP_TIER = 8
 FLAG_ASYNC_SCAN = 16
 FLAG_FRONTIER_SEGMENTS = 32
+FLAG_COMPACT_TABLES = 64
 
 
 class KadabraError(RuntimeError):

@@ -168,6 +168,22 @@ def test_searched_rows_match_oracle(kd, orc, gg):
         compare_paths_global(kd, orc, g, 42, 0, 0, 1500, tag="ba2000x30/" + tag, flag=flag | kd.FLAG_ASYNC_SCAN)
 
 
+@pytest.mark.parametrize("name,make", [s for s in SMALL if s[0] in ("Q6", "drand300", "ba3000", "rmat12", "star30", "cycle200")],
+                         ids=["Q6", "drand300", "ba3000", "rmat12", "star30", "cycle200"])
+def test_compact_tier_s_chain_matches_oracle(kd, orc, gg, name, make):
+    """Tier S in the compact layout (lists of 2048 nodes, 38 levels per side):
+    per-sample results as the oracle's (the cycle's long searches and the
+    power-law graphs' large ones move on to tier B)."""
+    g = make(gg)
+    compare_paths_global(kd, orc, g, 43, 0, 0, 2000, max_len=256, tag=name + "/compact", flag=kd.FLAG_COMPACT_TABLES)
+
+
+def test_compact_tier_s_chain_power_law(kd, orc, gg, chung_lu_1m):
+    compare_paths_global(kd, orc, chung_lu_1m, 44, 0, 20_000, 3000, tag="chung-lu/compact", flag=kd.FLAG_COMPACT_TABLES)
+    compare_paths_global(kd, orc, gg.path_graph(300), 45, 0, 0, 500, max_len=320, tag="path300/compact",
+                         flag=kd.FLAG_COMPACT_TABLES)
+
+
 def test_run_with_forced_tiers_matches_plain(kd, er2000):
     """Whole runs give identical results whichever table tier holds the samples."""
     out = []

@@ -31,12 +31,16 @@ def test_tier_variants_give_identical_runs(kd, gg, name, make, lam, k):
         auto = kd.kadabra_run(G, lam, 0.1, k, 3, check_interval=1000)
         again = kd.kadabra_run(G, lam, 0.1, k, 3, check_interval=1000)  # cached choice
         forced = [kd.kadabra_run(G, lam, 0.1, k, 3, check_interval=1000, ctas_per_sm=c) for c in (4, 5)]
+        # every setup by itself: both layouts, with and without tier W
+        forced += [kd.kadabra_run(G, lam, 0.1, k, 3, check_interval=1000, ctas_per_sm=c, warp_tier=wt)
+                   for c in (4, 5) for wt in (-1, 1)]
         with pytest.raises(kd.KadabraError):
             kd.kadabra_run(G, lam, 0.1, k, 3, ctas_per_sm=7)
     finally:
         G.free()
     assert auto.ctas_per_sm in (4, 5) and again.ctas_per_sm == auto.ctas_per_sm
-    assert [r.ctas_per_sm for r in forced] == [4, 5]
+    assert [r.ctas_per_sm for r in forced] == [4, 5, 4, 4, 5, 5]
+    assert [r.warp_tier for r in forced[2:]] == [0, 1, 0, 1]
     for r in [again] + forced:
         assert r.tau == auto.tau and r.checks == auto.checks and r.C == auto.C
         assert np.array_equal(r.counts, auto.counts) and (r.max_f, r.max_g) == (auto.max_f, auto.max_g)
