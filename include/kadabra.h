@@ -156,13 +156,17 @@ kadabra_status kadabra_load_csr_device(int32_t n, int64_t m, const int32_t* d_ro
  * 1.5 GB for large graphs).  The library keeps one such workspace per device
  * for the next graph object on that device whose node and arc counts fit in
  * it, which spares that object the allocation and initialisation.
- * kadabra_release_cached frees the kept workspaces.  Graph views of a batch
- * (kadabra_batch_graph) are released with the batch; passing one here does
- * nothing. */
+ * kadabra_release_cached frees the kept workspaces.  The graph's own buffers
+ * (its CSR copies, counters, load scratch) come from the device's default
+ * stream-ordered memory pool, which this library sets to keep freed memory
+ * (no release threshold): the next load reuses it without a driver call.
+ * Graph views of a batch (kadabra_batch_graph) are released with the batch;
+ * passing one here does nothing. */
 void kadabra_free_graph(kadabra_graph* g);
 
-/* Frees the sampler workspaces kept by kadabra_free_graph (all devices).
- * Call it with no work of the library in flight. */
+/* Frees the sampler workspaces kept by kadabra_free_graph (all devices) and
+ * returns the free memory of the current device's default pool to the
+ * driver.  Call it with no work of the library in flight. */
 void kadabra_release_cached(void);
 
 /* ---------------------------------------------------------------- batches

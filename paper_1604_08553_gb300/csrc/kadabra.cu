@@ -3897,6 +3897,55 @@ void dev_free(std::vector<void*>& allocs, void* p) {
   cudaFree(p);
 }
 
+// Allocations of graph objects and graph loads come from the device's
+// default memory pool with no release threshold, so that memory freed by
+// one load is handed to the next without a trip through the driver (graphs
+// are loaded and freed once per end-to-end run).  Allocated in order on the
+// legacy stream, which is synchronized before the memory is used elsewhere;
+// freed after the device is idle.  kadabra_release_cached returns the
+// pool's free memory to the driver.
+void pool_setup(int dev) {
+  static std::mutex mu;
+  static std::vector<int> done;
+  std::lock_guard<std::mutex> lk(mu);
+  for (int d : done)
+    if (d == dev) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  done.push_back(dev);
+}
+
+kadabra_status pool_alloc(void** p, size_t bytes) {
+  int dev = 0;
+  KCK(cudaGetDevice(&dev));
+  pool_setup(dev);
+  cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, 0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+  if (e != cudaSuccess)
+    return fail(KADABRA_ERR_OOM, std::string("cudaMallocAsync(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+  return KADABRA_OK;
+}
+
+void pool_free(void* p) {
+  if (p) cudaFreeAsync(p, 0);
+}
+
+kadabra_status gdev_alloc(std::vector<void*>& allocs, void** p, size_t bytes) {
+  KTRY(pool_alloc(p, bytes));
+  allocs.push_back(*p);
+  return KADABRA_OK;
+}
+
+void gdev_free(std::vector<void*>& allocs, void* p) {
+  if (!p) return;
+  for (auto& a : allocs)
+    if (a == p) a = nullptr;
+  pool_free(p);
+}
+
 kadabra_status ensure_ws(Workspace* w, uint64_t deferred_need, int njobs) {
   if (!w->ready) {
     KCK(cudaSetDevice(w->device));
@@ -3991,13 +4040,13 @@ kadabra_status ensure_ws(Workspace* w, uint64_t deferred_need, int njobs) {
 kadabra_status ensure_run_buffers(kadabra_graph* g) {
   if (g->counts) return KADABRA_OK;
   void* p;
-  KTRY(dev_alloc(g->allocs, &p, sizeof(uint32_t) * (size_t)g->n));
+  KTRY(gdev_alloc(g->allocs, &p, sizeof(uint32_t) * (size_t)g->n));
   g->counts = (uint32_t*)p;
-  KTRY(dev_alloc(g->allocs, &p, sizeof(uint32_t) * (size_t)g->n));
+  KTRY(gdev_alloc(g->allocs, &p, sizeof(uint32_t) * (size_t)g->n));
   g->count0 = (uint32_t*)p;
-  KTRY(dev_alloc(g->allocs, &p, sizeof(double) * (size_t)g->n));
+  KTRY(gdev_alloc(g->allocs, &p, sizeof(double) * (size_t)g->n));
   g->btilde = (double*)p;
-  KTRY(dev_alloc(g->allocs, &p, sizeof(long long) * KADABRA_NSTAT));
+  KTRY(gdev_alloc(g->allocs, &p, sizeof(long long) * KADABRA_NSTAT));
   g->totals = (long long*)p;
   return KADABRA_OK;
 }
@@ -4264,7 +4313,7 @@ kadabra_status load_scratch(const kadabra_graph* g, LoadScratch* S) {
   const size_t o_qa = o_dist + up(4 * n), o_qb = o_qa + up(4 * n), o_distb = o_qb + up(4 * n);
   const size_t o_items = o_distb + (g->directed ? up(4 * n) : 0);
   const size_t total = o_items + sizeof(BfsItem) * (size_t)cap;
-  KCK(cudaMalloc(&S->base, total));
+  KTRY(pool_alloc(&S->base, total));
   unsigned char* b = static_cast<unsigned char*>(S->base);
   S->err = reinterpret_cast<unsigned*>(b + o_head);
   S->lt_gt = reinterpret_cast<unsigned long long*>(b + o_head + 8);
@@ -4520,7 +4569,7 @@ kadabra_status finish_load(kadabra_graph* g) {
     tr.mark("fingerprint");
     st = compute_vd(g, tr, S);
   } while (0);
-  cudaFree(S.base);
+  pool_free(S.base);
   tr.mark("scratch free");
   if (st != KADABRA_OK) return st;
   if (h) {
@@ -4923,9 +4972,9 @@ kadabra_status run_graphs(Workspace* w, kadabra_graph* const* gs, int G, const d
     KTRY(ensure_run_buffers(s.g));
     if (s.g->lntab_cap < s.alpha + 1) {
       KCK(cudaStreamSynchronize(st));
-      dev_free(s.g->allocs, s.g->lntab);
+      gdev_free(s.g->allocs, s.g->lntab);
       void* p;
-      KTRY(dev_alloc(s.g->allocs, &p, sizeof(double) * (s.alpha + 1)));
+      KTRY(gdev_alloc(s.g->allocs, &p, sizeof(double) * (s.alpha + 1)));
       s.g->lntab = (double*)p;
       s.g->lntab_cap = s.alpha + 1;
     }
@@ -5346,15 +5395,15 @@ kadabra_status ensure_topk_buffers(kadabra_graph* g, cudaStream_t st) {
   if (g->count_pre) return KADABRA_OK;
   KCK(cudaStreamSynchronize(st));
   void* p;
-  KTRY(dev_alloc(g->allocs, &p, sizeof(uint32_t) * (size_t)g->n));
+  KTRY(gdev_alloc(g->allocs, &p, sizeof(uint32_t) * (size_t)g->n));
   g->count_pre = (uint32_t*)p;
-  KTRY(dev_alloc(g->allocs, &p, sizeof(double) * (size_t)g->n));
+  KTRY(gdev_alloc(g->allocs, &p, sizeof(double) * (size_t)g->n));
   g->lnLv = (double*)p;
-  KTRY(dev_alloc(g->allocs, &p, sizeof(double) * (size_t)g->n));
+  KTRY(gdev_alloc(g->allocs, &p, sizeof(double) * (size_t)g->n));
   g->lnUv = (double*)p;
-  KTRY(dev_alloc(g->allocs, &p, sizeof(unsigned long long) * (size_t)TK_BLOCKS * (TOPK_MAX + 1)));
+  KTRY(gdev_alloc(g->allocs, &p, sizeof(unsigned long long) * (size_t)TK_BLOCKS * (TOPK_MAX + 1)));
   g->tk_cand = (unsigned long long*)p;
-  KTRY(dev_alloc(g->allocs, &p, sizeof(TopkJob) + sizeof(TopkOut)));
+  KTRY(gdev_alloc(g->allocs, &p, sizeof(TopkJob) + sizeof(TopkOut)));
   g->tk_dev = p;
   return KADABRA_OK;
 }
@@ -5523,9 +5572,9 @@ kadabra_status run_topk(kadabra_graph* g, double lambda, double delta, int32_t k
   // per-node ln(1/delta) arrays: l0 everywhere, then the hit nodes' values
   if (g->tk_stage_cap < nnz) {
     KCK(cudaStreamSynchronize(st));
-    dev_free(g->allocs, g->tk_stage);
+    gdev_free(g->allocs, g->tk_stage);
     void* p;
-    KTRY(dev_alloc(g->allocs, &p, (sizeof(uint32_t) + 2 * sizeof(double)) * (size_t)nnz));
+    KTRY(gdev_alloc(g->allocs, &p, (sizeof(uint32_t) + 2 * sizeof(double)) * (size_t)nnz));
     g->tk_stage = p;
     g->tk_stage_cap = nnz;
   }
@@ -6443,9 +6492,9 @@ kadabra_status kadabra_load_csr(int32_t n, int64_t m, const int32_t* row_ptr, co
   kadabra_status st = KADABRA_OK;
   void* p;
   const size_t rb = sizeof(int32_t) * ((size_t)n + 1), cb = sizeof(int32_t) * (size_t)m;
-  if ((st = dev_alloc(g->allocs, &p, rb)) != KADABRA_OK) goto bad;
+  if ((st = gdev_alloc(g->allocs, &p, rb)) != KADABRA_OK) goto bad;
   g->rp = (int32_t*)p;
-  if ((st = dev_alloc(g->allocs, &p, cb)) != KADABRA_OK) goto bad;
+  if ((st = gdev_alloc(g->allocs, &p, cb)) != KADABRA_OK) goto bad;
   g->ci = (int32_t*)p;
   if (cudaMemcpy(g->rp, row_ptr, rb, cudaMemcpyHostToDevice) != cudaSuccess ||
       (m > 0 && cudaMemcpy(g->ci, col, cb, cudaMemcpyHostToDevice) != cudaSuccess)) {
@@ -6453,9 +6502,9 @@ kadabra_status kadabra_load_csr(int32_t n, int64_t m, const int32_t* row_ptr, co
     goto bad;
   }
   if (directed) {
-    if ((st = dev_alloc(g->allocs, &p, rb)) != KADABRA_OK) goto bad;
+    if ((st = gdev_alloc(g->allocs, &p, rb)) != KADABRA_OK) goto bad;
     g->rrp = (int32_t*)p;
-    if ((st = dev_alloc(g->allocs, &p, cb)) != KADABRA_OK) goto bad;
+    if ((st = gdev_alloc(g->allocs, &p, cb)) != KADABRA_OK) goto bad;
     g->rci = (int32_t*)p;
     if (cudaMemcpy(g->rrp, rrow_ptr, rb, cudaMemcpyHostToDevice) != cudaSuccess ||
         (m > 0 && cudaMemcpy(g->rci, rcol, cb, cudaMemcpyHostToDevice) != cudaSuccess)) {
@@ -6515,8 +6564,7 @@ kadabra_status kadabra_load_csr_device(int32_t n, int64_t m, const int32_t* d_ro
 void kadabra_free_graph(kadabra_graph* g) {
   if (!g || g->is_view) return;
   cudaDeviceSynchronize();
-  for (void* p : g->allocs)
-    if (p) cudaFree(p);
+  for (void* p : g->allocs) pool_free(p);
   if (g->owns_ws) ws_release(g->ws);
   delete g;
 }
@@ -6530,6 +6578,13 @@ void kadabra_release_cached(void) {
   for (Workspace* w : all) {
     cudaSetDevice(w->device);
     delete w;
+  }
+  // the free memory of the graph allocations' pool, on the current device
+  int dev = 0;
+  cudaMemPool_t pool;
+  if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    cudaDeviceSynchronize();
+    cudaMemPoolTrimTo(pool, 0);
   }
 }
 
@@ -6870,8 +6925,7 @@ void kadabra_free_batch(kadabra_batch* b) {
   if (!b) return;
   cudaDeviceSynchronize();
   for (kadabra_graph* g : b->views) {
-    for (void* p : g->allocs)
-      if (p) cudaFree(p);
+    for (void* p : g->allocs) pool_free(p);
     delete g;  // also releases its loop graph
   }
   if (b->arena) cudaFree(b->arena);
