@@ -341,6 +341,30 @@ def test_vd_bound_condensation_matches_oracle(kd, orc, gg):
             assert got >= _true_vd(g), g.name
 
 
+def test_graph_memory_reused_across_loads(kd, orc, gg):
+    """Graph buffers come from a pool that keeps freed memory: loading and
+    freeing the same graph again does not grow the device's used memory,
+    results stay the oracle's, and releasing the cached memory returns it."""
+    import torch
+    g = gg.barabasi_albert(50000, 6, 11)
+    ref = orc.sample_paths(g, 8, 0, 0, 1000)
+    used = []
+    for _ in range(4):
+        G = kd.kadabra_load_csr(g)
+        try:
+            got = kd.kadabra_sample_paths(G, 8, 0, 0, 1000)
+        finally:
+            G.free()
+        assert_samples_equal(got, ref, "pooled load")
+        torch.cuda.synchronize()
+        free_b, total_b = torch.cuda.mem_get_info()
+        used.append(total_b - free_b)
+    assert max(used[1:]) <= used[0] + (8 << 20), used
+    kd.kadabra_release_cached()
+    free_b, total_b = torch.cuda.mem_get_info()
+    assert total_b - free_b <= used[-1], (total_b - free_b, used)
+
+
 def test_workspace_reuse_across_graph_objects(kd, orc, gg, er2000):
     """A freed graph object's sampler workspace serves the next one that fits
     in it: results stay identical to the oracle, an error left in the
