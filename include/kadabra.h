@@ -159,14 +159,14 @@ kadabra_status kadabra_load_csr_device(int32_t n, int64_t m, const int32_t* d_ro
  * kadabra_release_cached frees the kept workspaces.  The graph's own buffers
  * (its CSR copies, counters, load scratch) come from the device's default
  * stream-ordered memory pool, which this library sets to keep freed memory
- * (no release threshold): the next load reuses it without a driver call.
+ * (no release threshold): the next load reuses it without cudaMalloc.
  * Graph views of a batch (kadabra_batch_graph) are released with the batch;
  * passing one here does nothing. */
 void kadabra_free_graph(kadabra_graph* g);
 
 /* Frees the sampler workspaces kept by kadabra_free_graph (all devices) and
- * returns the free memory of the current device's default pool to the
- * driver.  Call it with no work of the library in flight. */
+ * trims the current device's default memory pool to its memory in use.
+ * Call it with no work of the library in flight. */
 void kadabra_release_cached(void);
 
 /* ---------------------------------------------------------------- batches

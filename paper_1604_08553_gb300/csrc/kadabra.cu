@@ -3899,11 +3899,11 @@ void dev_free(std::vector<void*>& allocs, void* p) {
 
 // Allocations of graph objects and graph loads come from the device's
 // default memory pool with no release threshold, so that memory freed by
-// one load is handed to the next without a trip through the driver (graphs
+// one load is handed to the next without cudaMalloc or cudaFree (graphs
 // are loaded and freed once per end-to-end run).  Allocated in order on the
 // legacy stream, which is synchronized before the memory is used elsewhere;
 // freed after the device is idle.  kadabra_release_cached returns the
-// pool's free memory to the driver.
+// pool's free memory to the device (cudaMemPoolTrimTo).
 void pool_setup(int dev) {
   static std::mutex mu;
   static std::vector<int> done;
