@@ -39,6 +39,26 @@ def test_library_exports_every_declared_symbol(kd):
     assert not missing, missing
 
 
+def header_enum(prefix):
+    """name -> value of the header's enumerators KADABRA_<prefix>..."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"\bKADABRA_(" + prefix + r"[A-Z0-9_]*)\s*=\s*(\d+)", text)}
+
+
+def test_binding_constants_match_the_header(kd):
+    """Every status, flag and work-counter constant of the binding has the
+    header's value, and the binding names all of them."""
+    for prefix in ("ERR_", "FLAG_"):
+        enum = header_enum(prefix)
+        assert enum, prefix
+        for name, value in enum.items():
+            assert getattr(kd, name) == value, name
+    stats = header_enum("STAT_")
+    assert len(kd.STAT_NAMES) == kd.NSTAT == len(stats)
+    for name, value in stats.items():
+        assert kd.STAT_NAMES[value] == name[len("STAT_"):].lower(), name
+
+
 def test_config_defaults(kd):
     cfg = kd.config_default()
     assert cfg.eps == 0.001 and cfg.check_interval == 1000 and cfg.vd == 0 and not cfg.stream
